@@ -1,0 +1,195 @@
+/*
+ * ttgbf.h -- C ABI of the tensor-train grid-based (point-mass) filter on GB300.
+ *
+ * The library runs the Bayesian recursion of arXiv 2501.07942 (Sec. 1,
+ * Eqs. asx/asz; Alg. 2 and Alg. 3) for a batch of independent filters that
+ * share one grid and one linear-Gaussian dynamic model: each filter's density
+ * is a tensor train (Sec. 3, Eq. ttd_exact) over an equidistant,
+ * cell-centred grid (Sec. 2, Eq. pdf_pm).  One filter step is
+ *     ttgbf_predict  (Chapman-Kolmogorov, Eqs. pdf_predII / tpmconvFFT),
+ *     ttgbf_update   (Bayes rule, Eqs. pmf_filtrace_a/b), and
+ *     ttgbf_estimate (mean, covariance, log normaliser).
+ * Every step of the path runs in the library's own CUDA kernels (sm_103a).
+ *
+ * Conventions for every entry point:
+ *  - Return value 0 (TTGBF_OK) or a negative TTGBF_E* code.
+ *  - Arguments are validated on the host before anything is enqueued; on
+ *    TTGBF_EINVAL / TTGBF_ENONFINITE / TTGBF_ECAPACITY / TTGBF_ESINGULAR the
+ *    filter state is unchanged.
+ *  - After a CUDA error the context is poisoned: every later call except
+ *    ttgbf_free returns TTGBF_EPOISONED.
+ *  - Host arrays passed in are owned by the caller and are read (or copied)
+ *    before the call returns.  Device pointers passed in are owned by the
+ *    caller and must stay valid until the work enqueued on the context's
+ *    stream has passed them.
+ *  - Work is enqueued asynchronously on the stream given at init.  Calls that
+ *    return host data (ttgbf_estimate, ttgbf_ranks, ttgbf_stats,
+ *    ttgbf_export_cores) synchronise that stream.
+ *  - Thread safety: a context is used by one host thread at a time.
+ */
+#ifndef TTGBF_H
+#define TTGBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TTGBF_OK 0
+#define TTGBF_EINVAL (-1)     /* bad shape, mode, size or option           */
+#define TTGBF_ENONFINITE (-2) /* NaN or Inf in F, Q, R, z, grid or prior   */
+#define TTGBF_ENOMEM (-3)     /* device allocation failed or workspace too small */
+#define TTGBF_ECUDA (-4)      /* a CUDA call failed; the context is poisoned */
+#define TTGBF_ECAPACITY (-5)  /* a shear needs a larger rank expansion than max_shift_span */
+#define TTGBF_ESINGULAR (-6)  /* F has no LDU factorisation without pivoting */
+#define TTGBF_EPOISONED (-7)  /* an earlier CUDA error poisoned the context */
+
+typedef struct ttgbf_ctx ttgbf_ctx;
+
+/* Equidistant cell-centred grid (Sec. 2, Eq. pdf_pm; Sec. 4, first bullet).
+ * Mode m has n[m] cells on [lo[m], hi[m]]; cell i is centred at
+ * lo + (i + 1/2) (hi - lo)/n.  All three arrays are host arrays of d entries. */
+typedef struct {
+  int32_t d;
+  const int32_t* n;
+  const double* lo;
+  const double* hi;
+} ttgbf_grid;
+
+/* Gaussian prior with diagonal covariance (Alg. 2 step 1): each filter starts
+ * from the rank-1 tensor prod_m N(xi_m; mean[m], var[m]), normalised.
+ * Host arrays of d entries. */
+typedef struct {
+  const double* mean;
+  const double* var;
+} ttgbf_prior;
+
+typedef struct {
+  int32_t batch;          /* number of independent filters (>= 1) */
+  int32_t rank_cap;       /* maximal TT rank R^max after rounding (Sec. 3.2); >= 1 */
+  double eps;             /* rounding tolerance: ||A - round(A)||_F <= eps ||A||_F when the cap does not bind */
+  int32_t max_shift_span; /* largest rank expansion S one re-gridding shear may need; 0 = 10 */
+  void* stream;           /* cudaStream_t for all work; NULL = legacy default stream */
+  void* workspace;        /* caller-owned device memory of ttgbf_workspace_bytes() bytes, 256-byte
+                             aligned, or NULL to let the library cudaMalloc it (freed by ttgbf_free) */
+  size_t workspace_bytes; /* size of `workspace` when it is given */
+} ttgbf_opts;
+
+/* One measurement component z_c = h_c(x_m [, x_n]) + v_c that depends on one
+ * mode or on two adjacent modes (Sec. 4, fourth bullet: the likelihood
+ * tensor).  htab is a caller-owned DEVICE array with h_c evaluated at the grid
+ * points: n[m] floats, or n[m]*n[n] floats row-major [i_m][i_n].  Two-mode
+ * components need n == m + 1 and m == 0 or n == d-1 (one side of the pair
+ * carries TT rank 1), and n[m] (m == 0) or n[n] (n == d-1) <= rank_cap *
+ * max_shift_span. */
+typedef struct {
+  int32_t nmodes;
+  int32_t modes[2];
+  const float* htab;
+} ttgbf_meas_comp;
+
+typedef struct {
+  int32_t b;                   /* number of components */
+  const ttgbf_meas_comp* comp; /* host array of b components */
+} ttgbf_meas;
+
+/* Per-filter diagnostics of the most recent step. */
+typedef struct {
+  double tail_sum;     /* sum over roundings of the discarded relative Frobenius tail */
+  double tail_max;     /* largest single discarded relative tail */
+  double mass_pred;    /* mass of the predictive density before normalisation */
+  double log_c;        /* log of the normaliser c of Eq. pmf_filtrace_b, this step */
+  double log_lik;      /* cumulative sum of log c */
+  int32_t max_rank;    /* largest TT rank after the step */
+  int32_t cap_hits;    /* roundings in which the rank cap bound */
+} ttgbf_step_stats;
+
+/* Bytes of device workspace needed by ttgbf_init for this grid and options. */
+size_t ttgbf_workspace_bytes(const ttgbf_grid* grid, const ttgbf_opts* opts);
+
+/* Create a context holding `opts->batch` filters, each initialised to the
+ * prior.  Copies grid, prior and options.  *out is set on success only. */
+int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior,
+               const ttgbf_opts* opts);
+
+/* Predictive step with the re-gridded transition (Eq. pdf_predII through the
+ * FFT-form of Eq. tpmconvFFT on a fixed grid): x+ = F x + w, w ~ N(0, Q).
+ * F: host d*d row-major; Q: host d*d row-major, must be diagonal and
+ * positive.  F = L D U (LDU without pivoting) is applied as elementary
+ * shears and axis scalings with hat weights, each shear followed by TT
+ * rounding, then the per-mode Gaussian convolution with
+ * kappa_m(t) = D_m N(D_m t; 0, Q_mm) over each core's grid index, then
+ * normalisation (Alg. 2 step 4).  Same F and Q for every filter. */
+int ttgbf_predict(ttgbf_ctx* ctx, const double* F, const double* Q);
+
+/* Bayes update (Eqs. pmf_filtrace_a/b; Alg. 2 step 2): P <- L P / c with the
+ * likelihood L(i) = prod_c N(z_c; h_c(x_i), R_cc), then TT rounding and
+ * normalisation; log c is accumulated into the log-likelihood.
+ * R: host b*b row-major, diagonal and positive.  z: HOST array [batch][b]
+ * (float64), one measurement vector per filter, copied to the device. */
+int ttgbf_update(ttgbf_ctx* ctx, const ttgbf_meas* h, const double* R, const double* z);
+
+/* Same as ttgbf_update with z a DEVICE array [batch][b] of float32. */
+int ttgbf_update_dev(ttgbf_ctx* ctx, const ttgbf_meas* h, const double* R, const float* z_dev);
+
+/* Point-mass moments of every filter's current density by TT contraction
+ * (Alg. 2 step 3, "power, dot"): mean [batch][d], cov [batch][d][d],
+ * log_c [batch] (this step's log normaliser), log_lik [batch] (cumulative).
+ * HOST outputs (any may be NULL); synchronises the stream. */
+int ttgbf_estimate(ttgbf_ctx* ctx, double* mean, double* cov, double* log_c, double* log_lik);
+
+/* Same with DEVICE outputs (float64), asynchronous. */
+int ttgbf_estimate_dev(ttgbf_ctx* ctx, double* mean, double* cov, double* log_c, double* log_lik);
+
+/* Release the context and any memory the library allocated. NULL is a no-op. */
+int ttgbf_free(ttgbf_ctx* ctx);
+
+/* Static message for an error code. */
+const char* ttgbf_strerror(int code);
+
+/* ---- diagnostics, checkpoint / resume and single-operation hooks ---------- */
+
+/* Current TT ranks, host [batch][d+1] (r_0 = r_d = 1). Synchronises. */
+int ttgbf_ranks(ttgbf_ctx* ctx, int32_t* ranks);
+
+/* Per-filter statistics of the last step, host [batch]. Synchronises. */
+int ttgbf_stats(ttgbf_ctx* ctx, ttgbf_step_stats* out);
+
+/* Cell-centre coordinates, host array of n[0] + ... + n[d-1] doubles. */
+int ttgbf_grid_axes(const ttgbf_ctx* ctx, double* axes);
+
+/* Copy filter f's cores to host memory: concatenated cores, each row-major
+ * [r_{k-1}][n_k][r_k] (float32).  ranks_out: host int32[d+1].  cap is the size
+ * of buf in floats; TTGBF_ENOMEM if too small.  Synchronises. */
+int ttgbf_export_cores(ttgbf_ctx* ctx, int32_t f, float* buf, size_t cap, int32_t* ranks_out);
+
+/* Replace filter f's cores (same layout as export); ranks[k] <= rank_cap for
+ * interior links.  Resets f's log-likelihood to log_lik. */
+int ttgbf_import_cores(ttgbf_ctx* ctx, int32_t f, const float* buf, const int32_t* ranks,
+                       double log_lik);
+
+/* Apply one elementary re-gridding shear x_m += a x_n (m != n) with hat
+ * weights to every filter, then round if do_round != 0.  Without rounding the
+ * ranks of links between m and n grow by the shift span S. */
+int ttgbf_shear(ttgbf_ctx* ctx, int32_t m, int32_t n, double a, int32_t do_round);
+
+/* Apply x_m <- lam x_m (cloud-in-cell) to every filter; ranks unchanged. */
+int ttgbf_scale(ttgbf_ctx* ctx, int32_t m, double lam);
+
+/* Apply the separable Gaussian convolution with variances q[0..d-1] (host)
+ * over every core's grid index; ranks unchanged; no normalisation. */
+int ttgbf_convolve(ttgbf_ctx* ctx, const double* q);
+
+/* TT rounding (right-to-left orthogonalisation, left-to-right truncated SVD)
+ * of every filter at the context's eps and rank cap. */
+int ttgbf_round(ttgbf_ctx* ctx);
+
+/* Normalise every filter to unit mass (sum(P) * cell volume = 1). */
+int ttgbf_normalise(ttgbf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTGBF_H */

@@ -161,19 +161,16 @@ def shear(P: np.ndarray, grid: Grid, m: int, n: int, a: float) -> np.ndarray:
     fractional shift s carry weight."""
     if m == n:
         raise ValueError("a shear couples two different modes")
-    out = np.zeros_like(P)
+    # Work on a copy with mode n first so that each i_n slice is contiguous.
+    src_all = np.ascontiguousarray(np.moveaxis(P, n, 0))
+    out = np.zeros_like(src_all)
+    ax = m if m < n else m - 1   # axis m inside a slice with axis n removed
     for i_n in range(grid.shape[n]):
         s = a * grid.axes[n][i_n] / grid.delta_axis[m]
         k = math.floor(s)
-        sel = [slice(None)] * P.ndim
-        sel[n] = i_n
-        sel = tuple(sel)
-        src = P[sel]
-        acc = out[sel]
-        ax = m if m < n else m - 1   # axis m inside the slice with axis n removed
         for t in (k, k + 1):
-            _shifted_add(acc, src, ax, t, float(hat(t - s)))
-    return out
+            _shifted_add(out[i_n], src_all[i_n], ax, t, float(hat(t - s)))
+    return np.ascontiguousarray(np.moveaxis(out, 0, n))
 
 
 def cic_matrix(grid: Grid, m: int, lam: float) -> np.ndarray:

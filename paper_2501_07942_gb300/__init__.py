@@ -1,0 +1,286 @@
+"""ttgbf: tensor-train grid-based (point-mass) filtering on GB300.
+
+Python binding of the C ABI in ``include/ttgbf.h`` (library ``libttgbf.so``
+built in-tree by ``paper_2501_07942_gb300.build``).  The binding only
+marshals arguments: every step of the filter runs in the library's CUDA
+kernels.  PyTorch supplies device memory (the workspace and the measurement
+tables) and the CUDA stream.
+
+Method names follow the C entry points (``ttgbf_<name>``): ``predict``,
+``update``, ``update_dev``, ``estimate``, ``estimate_dev``, ``free``,
+``ranks``, ``stats``, ``grid_axes``, ``export_cores``, ``import_cores``,
+``shear``, ``scale``, ``convolve``, ``round``, ``normalise``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttgbf.so")
+
+TTGBF_OK = 0
+ERRORS = {
+    -1: "TTGBF_EINVAL", -2: "TTGBF_ENONFINITE", -3: "TTGBF_ENOMEM", -4: "TTGBF_ECUDA",
+    -5: "TTGBF_ECAPACITY", -6: "TTGBF_ESINGULAR", -7: "TTGBF_EPOISONED",
+}
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTED = [
+    "ttgbf_workspace_bytes", "ttgbf_init", "ttgbf_predict", "ttgbf_update", "ttgbf_update_dev",
+    "ttgbf_estimate", "ttgbf_estimate_dev", "ttgbf_free", "ttgbf_strerror", "ttgbf_ranks",
+    "ttgbf_stats", "ttgbf_grid_axes", "ttgbf_export_cores", "ttgbf_import_cores", "ttgbf_shear",
+    "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise",
+]
+
+
+class TTGBFError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({strerror(code)})")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("n", ctypes.POINTER(ctypes.c_int32)),
+                ("lo", ctypes.POINTER(ctypes.c_double)), ("hi", ctypes.POINTER(ctypes.c_double))]
+
+
+class Prior(ctypes.Structure):
+    _fields_ = [("mean", ctypes.POINTER(ctypes.c_double)), ("var", ctypes.POINTER(ctypes.c_double))]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("max_shift_span", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class MeasComp(ctypes.Structure):
+    _fields_ = [("nmodes", ctypes.c_int32), ("modes", ctypes.c_int32 * 2),
+                ("htab", ctypes.c_void_p)]
+
+
+class Meas(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int32), ("comp", ctypes.POINTER(MeasComp))]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("tail_sum", ctypes.c_double), ("tail_max", ctypes.c_double),
+                ("mass_pred", ctypes.c_double), ("log_c", ctypes.c_double),
+                ("log_lik", ctypes.c_double), ("max_rank", ctypes.c_int32),
+                ("cap_hits", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libttgbf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2501_07942_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, VP = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    dp = P(ctypes.c_double)
+    lib.ttgbf_workspace_bytes.restype = ctypes.c_size_t
+    lib.ttgbf_workspace_bytes.argtypes = [P(Grid), P(Opts)]
+    lib.ttgbf_init.argtypes = [P(VP), P(Grid), P(Prior), P(Opts)]
+    lib.ttgbf_predict.argtypes = [VP, dp, dp]
+    lib.ttgbf_update.argtypes = [VP, P(Meas), dp, dp]
+    lib.ttgbf_update_dev.argtypes = [VP, P(Meas), dp, VP]
+    lib.ttgbf_estimate.argtypes = [VP, dp, dp, dp, dp]
+    lib.ttgbf_estimate_dev.argtypes = [VP, VP, VP, VP, VP]
+    lib.ttgbf_free.argtypes = [VP]
+    lib.ttgbf_strerror.restype = ctypes.c_char_p
+    lib.ttgbf_strerror.argtypes = [I]
+    lib.ttgbf_ranks.argtypes = [VP, P(ctypes.c_int32)]
+    lib.ttgbf_stats.argtypes = [VP, P(StepStats)]
+    lib.ttgbf_grid_axes.argtypes = [VP, dp]
+    lib.ttgbf_export_cores.argtypes = [VP, ctypes.c_int32, P(ctypes.c_float), ctypes.c_size_t,
+                                       P(ctypes.c_int32)]
+    lib.ttgbf_import_cores.argtypes = [VP, ctypes.c_int32, P(ctypes.c_float), P(ctypes.c_int32), D]
+    lib.ttgbf_shear.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, D, ctypes.c_int32]
+    lib.ttgbf_scale.argtypes = [VP, ctypes.c_int32, D]
+    lib.ttgbf_convolve.argtypes = [VP, dp]
+    lib.ttgbf_round.argtypes = [VP]
+    lib.ttgbf_normalise.argtypes = [VP]
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().ttgbf_strerror(int(code)).decode()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _check(rc: int, where: str):
+    if rc != TTGBF_OK:
+        raise TTGBFError(rc, where)
+
+
+def _grid(lo, hi, n):
+    n = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+    lo, hi = _f64(lo), _f64(hi)
+    g = Grid(len(n), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(lo), _dptr(hi))
+    return g, (n, lo, hi)
+
+
+def workspace_bytes(lo, hi, n, batch=1, rank_cap=16, eps=1e-6, max_shift_span=0) -> int:
+    g, keep = _grid(lo, hi, n)
+    o = Opts(batch, rank_cap, eps, max_shift_span, None, None, 0)
+    return int(load().ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o)))
+
+
+class TTFilter:
+    """A batch of TT point-mass filters sharing one grid and model
+    (``ttgbf_init``).  Device memory comes from a torch uint8 workspace."""
+
+    def __init__(self, lo, hi, n, prior_mean, prior_var, batch=1, rank_cap=16, eps=1e-6,
+                 max_shift_span=0, stream=None, device="cuda"):
+        import torch
+        self._lib = load()
+        self.d = len(n)
+        self.n = [int(v) for v in n]
+        self.batch = int(batch)
+        g, self._gkeep = _grid(lo, hi, n)
+        self._stream = torch.cuda.current_stream(device) if stream is None else stream
+        o = Opts(self.batch, int(rank_cap), float(eps), int(max_shift_span),
+                 ctypes.c_void_p(self._stream.cuda_stream), None, 0)
+        nbytes = self._lib.ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
+        if nbytes == 0:
+            raise TTGBFError(-1, "ttgbf_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        o.workspace = ctypes.c_void_p(self.workspace.data_ptr())
+        o.workspace_bytes = int(nbytes)
+        pm, pv = _f64(prior_mean), _f64(prior_var)
+        pr = Prior(_dptr(pm), _dptr(pv))
+        self._ctx = ctypes.c_void_p()
+        _check(self._lib.ttgbf_init(ctypes.byref(self._ctx), ctypes.byref(g), ctypes.byref(pr),
+                                    ctypes.byref(o)), "ttgbf_init")
+
+    # ----------------------------------------------------------- hot path
+    def predict(self, F, Q):
+        F, Q = _f64(F), _f64(Q)
+        _check(self._lib.ttgbf_predict(self._ctx, _dptr(F), _dptr(Q)), "ttgbf_predict")
+
+    @staticmethod
+    def _meas(comps):
+        arr = (MeasComp * len(comps))()
+        for i, (modes, tab) in enumerate(comps):
+            arr[i].nmodes = len(modes)
+            arr[i].modes[0] = int(modes[0])
+            arr[i].modes[1] = int(modes[1]) if len(modes) > 1 else -1
+            arr[i].htab = ctypes.c_void_p(tab.data_ptr())
+        return Meas(len(comps), arr), arr
+
+    def update(self, comps, R, z):
+        """comps: [(modes, device float32 table)]; R: (b, b); z: host (batch, b)."""
+        m, keep = self._meas(comps)
+        R, z = _f64(R), _f64(z)
+        _check(self._lib.ttgbf_update(self._ctx, ctypes.byref(m), _dptr(R), _dptr(z)), "ttgbf_update")
+
+    def update_dev(self, comps, R, z_dev):
+        """z_dev: device float32 tensor (batch, b)."""
+        m, keep = self._meas(comps)
+        R = _f64(R)
+        _check(self._lib.ttgbf_update_dev(self._ctx, ctypes.byref(m), _dptr(R),
+                                          ctypes.c_void_p(z_dev.data_ptr())), "ttgbf_update_dev")
+
+    def estimate(self):
+        mean = np.zeros((self.batch, self.d))
+        cov = np.zeros((self.batch, self.d, self.d))
+        lc = np.zeros(self.batch)
+        ll = np.zeros(self.batch)
+        _check(self._lib.ttgbf_estimate(self._ctx, _dptr(mean), _dptr(cov), _dptr(lc), _dptr(ll)),
+               "ttgbf_estimate")
+        return mean, cov, lc, ll
+
+    def estimate_dev(self, mean, cov, log_c, log_lik):
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(self._lib.ttgbf_estimate_dev(self._ctx, ptr(mean), ptr(cov), ptr(log_c), ptr(log_lik)),
+               "ttgbf_estimate_dev")
+
+    # -------------------------------------------------------- diagnostics
+    def ranks(self) -> np.ndarray:
+        r = np.zeros((self.batch, self.d + 1), dtype=np.int32)
+        _check(self._lib.ttgbf_ranks(self._ctx, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+               "ttgbf_ranks")
+        return r
+
+    def stats(self):
+        arr = (StepStats * self.batch)()
+        _check(self._lib.ttgbf_stats(self._ctx, arr), "ttgbf_stats")
+        keys = [f[0] for f in StepStats._fields_]
+        return [{k: getattr(s, k) for k in keys} for s in arr]
+
+    def grid_axes(self):
+        a = np.zeros(sum(self.n))
+        _check(self._lib.ttgbf_grid_axes(self._ctx, _dptr(a)), "ttgbf_grid_axes")
+        out, at = [], 0
+        for nk in self.n:
+            out.append(a[at:at + nk].copy())
+            at += nk
+        return out
+
+    def export_cores(self, f=0):
+        r = np.zeros(self.d + 1, dtype=np.int32)
+        cap = sum(self.n) * 160 * 160 + 16
+        buf = np.zeros(cap, dtype=np.float32)
+        _check(self._lib.ttgbf_export_cores(self._ctx, int(f),
+                                            buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            cap, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+               "ttgbf_export_cores")
+        cores, at = [], 0
+        for k in range(self.d):
+            cnt = int(r[k]) * self.n[k] * int(r[k + 1])
+            cores.append(buf[at:at + cnt].reshape(int(r[k]), self.n[k], int(r[k + 1])).copy())
+            at += cnt
+        return cores
+
+    def import_cores(self, f, cores, log_lik=0.0):
+        r = np.array([1] + [int(c.shape[2]) for c in cores], dtype=np.int32)
+        buf = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float32).ravel()
+                                                   for c in cores]))
+        _check(self._lib.ttgbf_import_cores(self._ctx, int(f),
+                                            buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            float(log_lik)), "ttgbf_import_cores")
+
+    def shear(self, m, n, a, do_round=True):
+        _check(self._lib.ttgbf_shear(self._ctx, int(m), int(n), float(a), int(bool(do_round))),
+               "ttgbf_shear")
+
+    def scale(self, m, lam):
+        _check(self._lib.ttgbf_scale(self._ctx, int(m), float(lam)), "ttgbf_scale")
+
+    def convolve(self, q):
+        q = _f64(q)
+        _check(self._lib.ttgbf_convolve(self._ctx, _dptr(q)), "ttgbf_convolve")
+
+    def round(self):
+        _check(self._lib.ttgbf_round(self._ctx), "ttgbf_round")
+
+    def normalise(self):
+        _check(self._lib.ttgbf_normalise(self._ctx), "ttgbf_normalise")
+
+    def free(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.ttgbf_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

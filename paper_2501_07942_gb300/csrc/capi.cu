@@ -1,0 +1,1009 @@
+// capi.cu -- host orchestration of the TT point-mass filter and the C ABI
+// declared in include/ttgbf.h.
+//
+// Step structure (arXiv 2501.07942, Alg. 3 on a fixed axis-aligned grid):
+//   predict: F = L D U (no pivoting) -> U's shears (each: TT-operator
+//            expansion + rounding) -> D's scalings fused with the Gaussian
+//            kernel per mode (when L = I) -> L's shears -> normalise
+//   update : one-mode likelihood factors scale core slices; a two-mode
+//            component on modes (0,1) multiplies the 2-site supercore, which
+//            is then split by a truncated SVD inside the TT rounding sweep;
+//            log c is taken before the rounding; normalise afterwards
+//   estimate: moments by TT contraction
+// All data-dependent sizes (TT ranks) stay on the device; the host enqueues a
+// fixed sequence of kernels per call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "ttgbf.h"
+
+using namespace ttgbf;
+
+namespace {
+
+constexpr int kMaxComps = 16;
+
+struct Arena {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    const size_t at = (off + 255) & ~size_t(255);
+    off = at + count * sizeof(T);
+    return at;
+  }
+};
+
+// Offsets of every device buffer inside the workspace.
+struct Layout {
+  size_t core[2][kMaxD];
+  size_t ranks, axes, pmean, pvar;
+  size_t normA, tail_sum, tail_max, mass, mass_pred, log_c, log_lik, logoff, mean, cov;
+  size_t cap_hits, newrank, lik_off;
+  size_t tsqr_prob, tsqr_off, stack[2];
+  size_t P1, P2, gdesc, gtiles, awork, W, opmats, zbuf;
+  size_t total;
+  long long core_cap[kMaxD];
+  long long stack_cap, W_cap, opmats_floats, awork_stride;
+  int gdesc_cap, levels, capr;
+};
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+int tsqr_levels_for(long long M, int n) {
+  long long C = kSmemFloats / n;
+  if (C > M) C = M;
+  long long rows = M, Cl = C;
+  int L = 0;
+  for (;; ++L) {
+    const long long nch = (rows + Cl - 1) / Cl;
+    if (nch <= 1) break;
+    rows = nch * n;
+    Cl = (C / n) * n;
+  }
+  return L + 1;
+}
+
+long long tsqr_stack_for(long long M, int n) {
+  long long C = kSmemFloats / n;
+  if (C > M) C = M;
+  const long long nch = (M + C - 1) / C;
+  return nch * (long long)n * n;
+}
+
+int validate_grid(const ttgbf_grid* g) {
+  if (!g || g->d < 1 || g->d > kMaxD || !g->n || !g->lo || !g->hi) return TTGBF_EINVAL;
+  for (int k = 0; k < g->d; ++k) {
+    if (g->n[k] < 2 || g->n[k] > 4096) return TTGBF_EINVAL;
+    if (!std::isfinite(g->lo[k]) || !std::isfinite(g->hi[k])) return TTGBF_ENONFINITE;
+    if (!(g->hi[k] > g->lo[k])) return TTGBF_EINVAL;
+  }
+  return TTGBF_OK;
+}
+
+int validate_opts(const ttgbf_opts* o) {
+  if (!o || o->batch < 1 || o->rank_cap < 1) return TTGBF_EINVAL;
+  if (!std::isfinite(o->eps)) return TTGBF_ENONFINITE;
+  if (o->eps < 0.0) return TTGBF_EINVAL;
+  const int smax = o->max_shift_span > 0 ? o->max_shift_span : 10;
+  if ((long long)o->rank_cap * smax > kMaxN || smax < 2) return TTGBF_ECAPACITY;
+  return TTGBF_OK;
+}
+
+Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
+  Layout L{};
+  Arena a;
+  const int d = g->d, B = o->batch;
+  const int smax = o->max_shift_span > 0 ? o->max_shift_span : 10;
+  const int capr = o->rank_cap * smax;
+  L.capr = capr;
+  int nmax = 0;
+  long long nsum = 0;
+  for (int k = 0; k < d; ++k) {
+    nmax = std::max(nmax, (int)g->n[k]);
+    nsum += g->n[k];
+    const long long cl = (k == 0) ? 1 : capr, cr = (k == d - 1) ? 1 : capr;
+    L.core_cap[k] = std::max<long long>(cl * g->n[k] * cr, 1);
+  }
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < d; ++k) L.core[s][k] = a.take<float>((size_t)B * L.core_cap[k]);
+  L.ranks = a.take<int>((size_t)B * (d + 1));
+  L.axes = a.take<double>(nsum);
+  L.pmean = a.take<double>(d);
+  L.pvar = a.take<double>(d);
+  L.normA = a.take<double>(B);
+  L.tail_sum = a.take<double>(B);
+  L.tail_max = a.take<double>(B);
+  L.mass = a.take<double>(B);
+  L.mass_pred = a.take<double>(B);
+  L.log_c = a.take<double>(B);
+  L.log_lik = a.take<double>(B);
+  L.logoff = a.take<double>(B);
+  L.mean = a.take<double>((size_t)B * d);
+  L.cov = a.take<double>((size_t)B * d * d);
+  L.cap_hits = a.take<int>(B);
+  L.newrank = a.take<int>(B);
+  L.lik_off = a.take<float>(B);
+  L.tsqr_prob = a.take<TsqrProblem>(B);
+  L.tsqr_off = a.take<int>((size_t)kMaxLevels * (B + 1));
+  // tall matrices: rows <= capr * nmax, columns <= max(capr, n0)
+  const long long Mmax = (long long)capr * nmax;
+  const int nsplit = (d >= 2) ? std::min<int>(g->n[0], kMaxN) : 1;
+  long long stack = 0;
+  int levels = 1;
+  for (int n = 1; n <= std::max(capr, nsplit); ++n) {
+    stack = std::max(stack, tsqr_stack_for(Mmax, n));
+    levels = std::max(levels, tsqr_levels_for(Mmax, n));
+  }
+  L.stack_cap = stack;
+  L.levels = levels;
+  L.stack[0] = a.take<float>((size_t)B * stack);
+  L.stack[1] = a.take<float>((size_t)B * stack);
+  L.P1 = a.take<float>((size_t)B * kMaxN * kMaxN);
+  L.P2 = a.take<float>((size_t)B * kMaxN * kMaxN);
+  L.gdesc_cap = std::max(2 * B, B * capr);
+  L.gdesc = a.take<GemmDesc>(L.gdesc_cap);
+  L.gtiles = a.take<int>(L.gdesc_cap + 1);
+  L.awork_stride = (long long)(d + 1) * 3 * kMaxN * kMaxN;
+  L.awork = a.take<double>((size_t)B * L.awork_stride);
+  L.W_cap = (d >= 2) ? (long long)g->n[0] * g->n[1] * o->rank_cap : 1;
+  L.W = a.take<float>((size_t)B * L.W_cap);
+  long long nn = 0;
+  for (int k = 0; k < d; ++k) nn += (long long)g->n[k] * g->n[k];
+  L.opmats_floats = 2 * nn + (long long)d * d * (smax + 2) * nmax;
+  L.opmats = a.take<float>(L.opmats_floats);
+  L.zbuf = a.take<float>((size_t)B * kMaxComps);
+  L.total = a.off + 256;
+  return L;
+}
+
+// One elementary re-gridding operation (the order of application is fixed).
+struct Op {
+  int kind;  // 0 shear, 1 scale
+  int m, n;
+  double a;
+};
+
+}  // namespace
+
+struct ttgbf_ctx {
+  int B = 0, d = 0;
+  std::vector<int> n;
+  std::vector<double> lo, hi, dx, axes;
+  std::vector<int> axoff;
+  int rank_cap = 0, smax = 0, capr = 0;
+  double eps = 0.0, delta = 1.0;
+  cudaStream_t st = nullptr;
+  Layout L{};
+  char* base = nullptr;
+  bool owns = false;
+  TTGeom geom{};
+  float* buf[2][kMaxD] = {};
+  int cur[kMaxD] = {};
+  int* ranks = nullptr;
+  double *axes_d = nullptr, *pmean = nullptr, *pvar = nullptr;
+  double *normA, *tail_sum, *tail_max, *mass, *mass_pred, *log_c, *log_lik, *logoff, *mean, *cov;
+  int *cap_hits, *newrank;
+  float* lik_off;
+  TsqrWork tw{};
+  float* stack[2];
+  float *P1, *P2;
+  GemmDesc* gdesc;
+  int* gtiles;
+  double* awork;
+  float* W;
+  float* opmats;
+  float* zbuf;
+  // pinned host staging
+  float* stage_ops = nullptr;
+  float* stage_z = nullptr;
+  cudaEvent_t ev_ops = nullptr, ev_z = nullptr;
+  bool ev_ops_used = false, ev_z_used = false;
+  // cached predict operators
+  std::vector<double> lastF, lastQ;
+  std::vector<Op> ops;
+  std::vector<int> op_S, op_tmin;
+  std::vector<long long> op_woff;  // float offsets of shear weight tables in opmats
+  std::vector<long long> mat_off;  // per mode: fused (or conv) matrix offset
+  std::vector<long long> scale_off;  // per mode: CIC matrix (only used when L != I), -1 if none
+  bool fuse = true;
+  bool poisoned = false;
+  bool expanded = false;  // ranks may exceed rank_cap (after an unrounded shear or import)
+  int sms = 148;
+};
+
+namespace {
+
+int cuda_fail(ttgbf_ctx* c) {
+  c->poisoned = true;
+  return TTGBF_ECUDA;
+}
+
+int check(ttgbf_ctx* c) {
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(c);
+  }
+  return TTGBF_OK;
+}
+
+float* curp(ttgbf_ctx* c, int k) { return c->buf[c->cur[k]][k]; }
+float* altp(ttgbf_ctx* c, int k) { return c->buf[c->cur[k] ^ 1][k]; }
+
+RoundState round_state(ttgbf_ctx* c) {
+  return RoundState{c->normA, c->tail_sum, c->tail_max, c->cap_hits, c->newrank};
+}
+
+GemmWork gemm_work(ttgbf_ctx* c, int ndesc) { return GemmWork{c->gdesc, c->gtiles, ndesc}; }
+
+// One stage of the rounding sweep: R factor, SVD, rank choice, factor application.
+void stage(ttgbf_ctx* c, int mode, int k, int first) {
+  const int B = c->B;
+  const float* src = (mode == kStageSplit) ? c->W : curp(c, k);
+  launch_plan_stage(c->st, B, mode, k, c->geom, c->ranks, src, c->W, c->L.W_cap, c->n[0],
+                    c->d > 1 ? c->n[1] : 1, c->tw, c->stack[0], c->stack[1], c->L.stack_cap);
+  launch_tsqr(c->st, c->tw, B, c->L.levels, c->sms);
+  float* core0_alt = (mode == kStageSplit) ? altp(c, 0) : nullptr;
+  launch_jacobi(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1, c->P2,
+                core0_alt, c->L.core_cap[0]);
+  int ka, kb, ndesc = 2 * B;
+  if (mode == kStageRight) {
+    ka = k;
+    kb = k - 1;
+  } else if (mode == kStageLeft) {
+    ka = k;
+    kb = k + 1;
+  } else {
+    ka = 0;
+    kb = 1;
+    ndesc = B;
+  }
+  GemmWork gw = gemm_work(c, ndesc);
+  launch_plan_gemm_stage(c->st, B, mode, k, c->geom, c->ranks, c->newrank, curp(c, ka), altp(c, ka),
+                         curp(c, kb), altp(c, kb), c->P1, c->P2, c->W, c->L.W_cap,
+                         c->d > 1 ? c->n[1] : 1, gw);
+  launch_gemm(c->st, gw, c->sms * 8);
+  c->cur[ka] ^= 1;
+  c->cur[kb] ^= 1;
+}
+
+// TT rounding: right-to-left orthogonalisation, left-to-right truncation.
+void enqueue_round(ttgbf_ctx* c) {
+  if (c->d < 2) return;
+  for (int k = c->d - 1; k >= 1; --k) stage(c, kStageRight, k, 0);
+  for (int k = 0; k <= c->d - 2; ++k) stage(c, kStageLeft, k, k == 0);
+  c->expanded = false;
+}
+
+MomentArgs tt_moment_args(ttgbf_ctx* c, int with_moments, int scale) {
+  MomentArgs a{};
+  a.ncores = c->d;
+  for (int k = 0; k < c->d; ++k) {
+    a.n[k] = c->n[k];
+    a.core[k] = curp(c, k);
+    a.cap[k] = c->L.core_cap[k];
+    a.axes[k] = c->axes_d + c->axoff[k];
+    a.centre[k] = 0.5 * (c->lo[k] + c->hi[k]);
+  }
+  for (int k = 0; k <= c->d; ++k) a.ridx[k] = k;
+  a.delta = c->delta;
+  a.with_moments = with_moments;
+  if (scale) {
+    a.scale_core = curp(c, c->d - 1);
+    a.scale_cap = c->L.core_cap[c->d - 1];
+    a.scale_idx = c->d - 1;
+  }
+  return a;
+}
+
+void enqueue_normalise(ttgbf_ctx* c, double* mass_out) {
+  MomentArgs a = tt_moment_args(c, 0, 1);
+  launch_moments(c->st, c->B, a, c->ranks, c->d + 1, c->awork, c->L.awork_stride, mass_out, nullptr,
+                 nullptr);
+}
+
+void mode_apply(ttgbf_ctx* c, int k, const float* M) {
+  GemmWork gw = gemm_work(c, c->B * c->capr);
+  launch_plan_mode_apply(c->st, c->B, k, c->geom, c->ranks, M, curp(c, k), altp(c, k), gw, c->capr);
+  launch_gemm(c->st, gw, c->sms * 8);
+  c->cur[k] ^= 1;
+}
+
+double hatf(double t) { return std::max(0.0, 1.0 - std::fabs(t)); }
+
+// Shear x_m += a x_n: integer shift range and hat-weight table.
+void shear_table(ttgbf_ctx* c, int m, int n, double a, int* S, int* tmin, std::vector<float>* w) {
+  const int Nn = c->n[n];
+  std::vector<double> s(Nn);
+  int lo = 1 << 30, hi = -(1 << 30);
+  for (int i = 0; i < Nn; ++i) {
+    s[i] = a * c->axes[c->axoff[n] + i] / c->dx[m];
+    const int f = (int)std::floor(s[i]);
+    lo = std::min(lo, f);
+    hi = std::max(hi, f);
+  }
+  *tmin = lo;
+  *S = hi - lo + 2;
+  w->assign((size_t)(*S) * Nn, 0.f);
+  for (int u = 0; u < *S; ++u)
+    for (int i = 0; i < Nn; ++i) (*w)[(size_t)u * Nn + i] = (float)hatf(lo + u - s[i]);
+}
+
+void cic_matrix(ttgbf_ctx* c, int m, double lam, std::vector<double>* W) {
+  const int N = c->n[m];
+  W->assign((size_t)N * N, 0.0);
+  for (int i = 0; i < N; ++i) {
+    const double u = (lam * c->axes[c->axoff[m] + i] - c->lo[m]) / c->dx[m] - 0.5;
+    for (int j = 0; j < N; ++j) (*W)[(size_t)j * N + i] = hatf(j - u);
+  }
+}
+
+void conv_matrix(ttgbf_ctx* c, int m, double q, std::vector<double>* K) {
+  const int N = c->n[m];
+  const double D = c->dx[m];
+  K->assign((size_t)N * N, 0.0);
+  const double norm = D / std::sqrt(2.0 * M_PI * q);
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < N; ++i) {
+      const double t = (double)(j - i) * D;
+      (*K)[(size_t)j * N + i] = norm * std::exp(-0.5 * t * t / q);
+    }
+}
+
+int ldu(const double* F, int d, std::vector<double>* Lm, std::vector<double>* D, std::vector<double>* U) {
+  Lm->assign((size_t)d * d, 0.0);
+  U->assign((size_t)d * d, 0.0);
+  D->assign(d, 0.0);
+  double scale = 1.0;
+  for (int i = 0; i < d * d; ++i) scale = std::max(scale, std::fabs(F[i]));
+  for (int k = 0; k < d; ++k) {
+    (*Lm)[(size_t)k * d + k] = 1.0;
+    (*U)[(size_t)k * d + k] = 1.0;
+  }
+  for (int k = 0; k < d; ++k) {
+    double s = F[(size_t)k * d + k];
+    for (int j = 0; j < k; ++j) s -= (*Lm)[(size_t)k * d + j] * (*D)[j] * (*U)[(size_t)j * d + k];
+    (*D)[k] = s;
+    if (std::fabs(s) <= 1e-12 * scale) return TTGBF_ESINGULAR;
+    for (int i = k + 1; i < d; ++i) {
+      double sl = F[(size_t)i * d + k], su = F[(size_t)k * d + i];
+      for (int j = 0; j < k; ++j) {
+        sl -= (*Lm)[(size_t)i * d + j] * (*D)[j] * (*U)[(size_t)j * d + k];
+        su -= (*Lm)[(size_t)k * d + j] * (*D)[j] * (*U)[(size_t)j * d + i];
+      }
+      (*Lm)[(size_t)i * d + k] = sl / s;
+      (*U)[(size_t)k * d + i] = su / s;
+    }
+  }
+  return TTGBF_OK;
+}
+
+void wait_stage(cudaEvent_t ev, bool* used) {
+  if (*used) cudaEventSynchronize(ev);
+  *used = false;
+}
+
+// Build and upload every operator of a predict call with this F and Q.
+int prepare_predict(ttgbf_ctx* c, const double* F, const double* Q) {
+  const int d = c->d;
+  std::vector<double> Lm, D, U;
+  const int rc = ldu(F, d, &Lm, &D, &U);
+  if (rc != TTGBF_OK) return rc;
+  std::vector<Op> ops;
+  for (int m = 0; m < d; ++m)
+    for (int n = m + 1; n < d; ++n)
+      if (U[(size_t)m * d + n] != 0.0) ops.push_back({0, m, n, U[(size_t)m * d + n]});
+  for (int m = 0; m < d; ++m)
+    if (D[m] != 1.0) ops.push_back({1, m, m, D[m]});
+  bool lower = false;
+  for (int m = d - 1; m >= 0; --m)
+    for (int n = 0; n < m; ++n)
+      if (Lm[(size_t)m * d + n] != 0.0) {
+        ops.push_back({0, m, n, Lm[(size_t)m * d + n]});
+        lower = true;
+      }
+  std::vector<float> host((size_t)c->L.opmats_floats, 0.f);
+  long long at = 0;
+  std::vector<int> S_list, t_list;
+  std::vector<long long> woff;
+  for (const Op& op : ops) {
+    if (op.kind != 0) {
+      S_list.push_back(0);
+      t_list.push_back(0);
+      woff.push_back(-1);
+      continue;
+    }
+    int S, tmin;
+    std::vector<float> w;
+    shear_table(c, op.m, op.n, op.a, &S, &tmin, &w);
+    if (S > c->smax) return TTGBF_ECAPACITY;
+    if (at + (long long)w.size() > c->L.opmats_floats) return TTGBF_ECAPACITY;
+    std::copy(w.begin(), w.end(), host.begin() + at);
+    S_list.push_back(S);
+    t_list.push_back(tmin);
+    woff.push_back(at);
+    at += (long long)w.size();
+  }
+  std::vector<long long> moff(d), soff(d, -1);
+  for (int m = 0; m < d; ++m) {
+    std::vector<double> K, Wc;
+    conv_matrix(c, m, Q[(size_t)m * d + m], &K);
+    const int N = c->n[m];
+    const bool has_scale = D[m] != 1.0;
+    if (has_scale) cic_matrix(c, m, D[m], &Wc);
+    if (has_scale && !lower) {
+      // fused operator K_m W_m (the scaling precedes the kernel on this mode)
+      std::vector<double> M((size_t)N * N, 0.0);
+      for (int j = 0; j < N; ++j)
+        for (int l = 0; l < N; ++l) {
+          const double kjl = K[(size_t)j * N + l];
+          if (kjl == 0.0) continue;
+          for (int i = 0; i < N; ++i) M[(size_t)j * N + i] += kjl * Wc[(size_t)l * N + i];
+        }
+      K.swap(M);
+    } else if (has_scale) {
+      soff[m] = at;
+      for (size_t t = 0; t < Wc.size(); ++t) host[at + t] = (float)Wc[t];
+      at += (long long)Wc.size();
+    }
+    moff[m] = at;
+    for (size_t t = 0; t < K.size(); ++t) host[at + t] = (float)K[t];
+    at += (long long)K.size();
+  }
+  wait_stage(c->ev_ops, &c->ev_ops_used);
+  std::memcpy(c->stage_ops, host.data(), sizeof(float) * at);
+  cudaMemcpyAsync(c->opmats, c->stage_ops, sizeof(float) * at, cudaMemcpyHostToDevice, c->st);
+  cudaEventRecord(c->ev_ops, c->st);
+  c->ev_ops_used = true;
+  c->ops = ops;
+  c->op_S = S_list;
+  c->op_tmin = t_list;
+  c->op_woff = woff;
+  c->mat_off = moff;
+  c->scale_off = soff;
+  c->fuse = !lower;
+  c->lastF.assign(F, F + (size_t)d * d);
+  c->lastQ.assign(Q, Q + (size_t)d * d);
+  return TTGBF_OK;
+}
+
+void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts, bool do_round) {
+  float* curv[kMaxD];
+  float* altv[kMaxD];
+  for (int k = 0; k < c->d; ++k) {
+    curv[k] = curp(c, k);
+    altv[k] = altp(c, k);
+  }
+  launch_shear_expand(c->st, c->B, c->geom, m, n, S, tmin, wts, curv, altv, c->ranks);
+  const int lo = std::min(m, n), hi = std::max(m, n);
+  launch_rank_scale(c->st, c->B, c->d, c->ranks, lo, hi, S);
+  for (int k = lo; k <= hi; ++k) c->cur[k] ^= 1;
+  c->expanded = true;
+  if (do_round) enqueue_round(c);
+}
+
+int guard(ttgbf_ctx* c) {
+  if (!c) return TTGBF_EINVAL;
+  if (c->poisoned) return TTGBF_EPOISONED;
+  return TTGBF_OK;
+}
+
+int validate_meas(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, int* two_mode) {
+  if (!h || h->b < 1 || h->b > kMaxComps || !h->comp || !R) return TTGBF_EINVAL;
+  if (!finite_all(R, (size_t)h->b * h->b)) return TTGBF_ENONFINITE;
+  *two_mode = -1;
+  for (int i = 0; i < h->b; ++i) {
+    for (int j = 0; j < h->b; ++j)
+      if (i != j && R[(size_t)i * h->b + j] != 0.0) return TTGBF_EINVAL;
+    if (!(R[(size_t)i * h->b + i] > 0.0)) return TTGBF_EINVAL;
+    const ttgbf_meas_comp& cp = h->comp[i];
+    if (!cp.htab) return TTGBF_EINVAL;
+    if (cp.nmodes == 1) {
+      if (cp.modes[0] < 0 || cp.modes[0] >= c->d) return TTGBF_EINVAL;
+    } else if (cp.nmodes == 2) {
+      if (cp.modes[0] != 0 || cp.modes[1] != 1 || c->d < 2) return TTGBF_EINVAL;
+      if (c->n[0] > kMaxN) return TTGBF_ECAPACITY;
+      if (*two_mode >= 0) return TTGBF_EINVAL;
+      *two_mode = i;
+    } else {
+      return TTGBF_EINVAL;
+    }
+  }
+  return TTGBF_OK;
+}
+
+int enqueue_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z, int zstride,
+                   int two_mode) {
+  const int B = c->B, d = c->d;
+  if (c->expanded) enqueue_round(c);
+  cudaMemsetAsync(c->logoff, 0, sizeof(double) * B, c->st);
+  for (int i = 0; i < h->b; ++i) {
+    const ttgbf_meas_comp& cp = h->comp[i];
+    if (cp.nmodes != 1) continue;
+    const int k = cp.modes[0];
+    const double r = R[(size_t)i * h->b + i];
+    launch_lik_offset(c->st, B, cp.htab, c->n[k], z, zstride, i, r, c->lik_off, c->logoff);
+    launch_lik_apply_1d(c->st, B, curp(c, k), c->L.core_cap[k], c->n[k], k, d, c->ranks, cp.htab, z,
+                        zstride, i, r, c->lik_off);
+  }
+  if (two_mode >= 0) {
+    const ttgbf_meas_comp& cp = h->comp[two_mode];
+    const double r = R[(size_t)two_mode * h->b + two_mode];
+    for (int k = d - 1; k >= 2; --k) stage(c, kStageRight, k, 0);
+    GemmWork gw = gemm_work(c, B);
+    launch_plan_supercore(c->st, B, c->geom, c->ranks, curp(c, 0), curp(c, 1), c->W, c->L.W_cap, gw);
+    launch_gemm(c->st, gw, c->sms * 8);
+    launch_lik_offset(c->st, B, cp.htab, c->n[0] * c->n[1], z, zstride, two_mode, r, c->lik_off,
+                      c->logoff);
+    launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, cp.htab, z, zstride,
+                        two_mode, r, c->lik_off);
+    // log c before rounding: mass of the TT [W (modes 0,1 merged), core 2, ...]
+    MomentArgs a{};
+    a.ncores = d - 1;
+    a.n[0] = c->n[0] * c->n[1];
+    a.core[0] = c->W;
+    a.cap[0] = c->L.W_cap;
+    a.ridx[0] = 0;
+    for (int k = 2; k < d; ++k) {
+      a.n[k - 1] = c->n[k];
+      a.core[k - 1] = curp(c, k);
+      a.cap[k - 1] = c->L.core_cap[k];
+    }
+    for (int kk = 1; kk <= d - 1; ++kk) a.ridx[kk] = kk + 1;
+    a.delta = c->delta;
+    launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
+    launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+    stage(c, kStageSplit, 0, 1);
+    for (int k = 1; k <= d - 2; ++k) stage(c, kStageLeft, k, 0);
+  } else {
+    MomentArgs a = tt_moment_args(c, 0, 0);
+    launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
+    launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+  }
+  enqueue_normalise(c, c->mass);
+  return check(c);
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* ttgbf_strerror(int code) {
+  switch (code) {
+    case TTGBF_OK: return "ok";
+    case TTGBF_EINVAL: return "invalid argument";
+    case TTGBF_ENONFINITE: return "non-finite input";
+    case TTGBF_ENOMEM: return "out of device memory or workspace too small";
+    case TTGBF_ECUDA: return "CUDA error (context poisoned)";
+    case TTGBF_ECAPACITY: return "rank expansion exceeds rank_cap * max_shift_span";
+    case TTGBF_ESINGULAR: return "F has no LDU factorisation without pivoting";
+    case TTGBF_EPOISONED: return "context poisoned by an earlier CUDA error";
+    default: return "unknown error";
+  }
+}
+
+size_t ttgbf_workspace_bytes(const ttgbf_grid* grid, const ttgbf_opts* opts) {
+  if (validate_grid(grid) != TTGBF_OK || validate_opts(opts) != TTGBF_OK) return 0;
+  return make_layout(grid, opts).total;
+}
+
+int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf_opts* opts) {
+  if (!out) return TTGBF_EINVAL;
+  int rc = validate_grid(grid);
+  if (rc != TTGBF_OK) return rc;
+  rc = validate_opts(opts);
+  if (rc != TTGBF_OK) return rc;
+  if (!prior || !prior->mean || !prior->var) return TTGBF_EINVAL;
+  const int d = grid->d;
+  if (!finite_all(prior->mean, d) || !finite_all(prior->var, d)) return TTGBF_ENONFINITE;
+  for (int k = 0; k < d; ++k)
+    if (!(prior->var[k] > 0.0)) return TTGBF_EINVAL;
+  static bool attrs = false;
+  if (!attrs) {
+    set_kernel_attributes();
+    set_ttops_attributes();
+    attrs = true;
+  }
+  ttgbf_ctx* c = new (std::nothrow) ttgbf_ctx();
+  if (!c) return TTGBF_ENOMEM;
+  c->B = opts->batch;
+  c->d = d;
+  c->rank_cap = opts->rank_cap;
+  c->smax = opts->max_shift_span > 0 ? opts->max_shift_span : 10;
+  c->capr = c->rank_cap * c->smax;
+  c->eps = opts->eps;
+  c->st = (cudaStream_t)opts->stream;
+  c->n.assign(grid->n, grid->n + d);
+  c->lo.assign(grid->lo, grid->lo + d);
+  c->hi.assign(grid->hi, grid->hi + d);
+  c->dx.resize(d);
+  c->axoff.resize(d);
+  int off = 0;
+  for (int k = 0; k < d; ++k) {
+    c->dx[k] = (c->hi[k] - c->lo[k]) / c->n[k];
+    c->delta *= c->dx[k];
+    c->axoff[k] = off;
+    for (int i = 0; i < c->n[k]; ++i) c->axes.push_back(c->lo[k] + (i + 0.5) * c->dx[k]);
+    off += c->n[k];
+  }
+  c->L = make_layout(grid, opts);
+  if (opts->workspace) {
+    if (opts->workspace_bytes < c->L.total || ((uintptr_t)opts->workspace & 255)) {
+      delete c;
+      return TTGBF_ENOMEM;
+    }
+    c->base = (char*)opts->workspace;
+  } else {
+    if (cudaMalloc(&c->base, c->L.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return TTGBF_ENOMEM;
+    }
+    c->owns = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  const Layout& L = c->L;
+  char* b = c->base;
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < d; ++k) c->buf[s][k] = (float*)(b + L.core[s][k]);
+  c->geom.d = d;
+  for (int k = 0; k < d; ++k) {
+    c->geom.n[k] = c->n[k];
+    c->geom.cap[k] = L.core_cap[k];
+  }
+  c->ranks = (int*)(b + L.ranks);
+  c->axes_d = (double*)(b + L.axes);
+  c->pmean = (double*)(b + L.pmean);
+  c->pvar = (double*)(b + L.pvar);
+  c->normA = (double*)(b + L.normA);
+  c->tail_sum = (double*)(b + L.tail_sum);
+  c->tail_max = (double*)(b + L.tail_max);
+  c->mass = (double*)(b + L.mass);
+  c->mass_pred = (double*)(b + L.mass_pred);
+  c->log_c = (double*)(b + L.log_c);
+  c->log_lik = (double*)(b + L.log_lik);
+  c->logoff = (double*)(b + L.logoff);
+  c->mean = (double*)(b + L.mean);
+  c->cov = (double*)(b + L.cov);
+  c->cap_hits = (int*)(b + L.cap_hits);
+  c->newrank = (int*)(b + L.newrank);
+  c->lik_off = (float*)(b + L.lik_off);
+  c->tw.prob = (TsqrProblem*)(b + L.tsqr_prob);
+  c->tw.offset = (int*)(b + L.tsqr_off);
+  c->stack[0] = (float*)(b + L.stack[0]);
+  c->stack[1] = (float*)(b + L.stack[1]);
+  c->P1 = (float*)(b + L.P1);
+  c->P2 = (float*)(b + L.P2);
+  c->gdesc = (GemmDesc*)(b + L.gdesc);
+  c->gtiles = (int*)(b + L.gtiles);
+  c->awork = (double*)(b + L.awork);
+  c->W = (float*)(b + L.W);
+  c->opmats = (float*)(b + L.opmats);
+  c->zbuf = (float*)(b + L.zbuf);
+  if (cudaMallocHost(&c->stage_ops, sizeof(float) * L.opmats_floats) != cudaSuccess ||
+      cudaMallocHost(&c->stage_z, sizeof(float) * (size_t)c->B * kMaxComps) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_ops, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_z, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ttgbf_free(c);
+    return TTGBF_ENOMEM;
+  }
+  // constants and the prior
+  cudaMemcpyAsync(c->axes_d, c->axes.data(), sizeof(double) * c->axes.size(), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->pmean, prior->mean, sizeof(double) * d, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->pvar, prior->var, sizeof(double) * d, cudaMemcpyHostToDevice, c->st);
+  cudaMemsetAsync(c->log_lik, 0, sizeof(double) * c->B, c->st);
+  cudaMemsetAsync(c->log_c, 0, sizeof(double) * c->B, c->st);
+  cudaMemsetAsync(c->tail_sum, 0, sizeof(double) * c->B, c->st);
+  cudaMemsetAsync(c->tail_max, 0, sizeof(double) * c->B, c->st);
+  cudaMemsetAsync(c->cap_hits, 0, sizeof(int) * c->B, c->st);
+  cudaMemsetAsync(c->mass_pred, 0, sizeof(double) * c->B, c->st);
+  launch_prior(c->st, c->B, c->geom, c->buf[0], c->ranks, c->axes_d, c->pmean, c->pvar);
+  enqueue_normalise(c, c->mass);
+  // synchronous: prior values come from host memory the caller may free
+  if (cudaStreamSynchronize(c->st) != cudaSuccess || check(c) != TTGBF_OK) {
+    cudaGetLastError();
+    ttgbf_free(c);
+    return TTGBF_ECUDA;
+  }
+  *out = c;
+  return TTGBF_OK;
+}
+
+int ttgbf_predict(ttgbf_ctx* c, const double* F, const double* Q) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!F || !Q) return TTGBF_EINVAL;
+  const int d = c->d;
+  if (!finite_all(F, (size_t)d * d) || !finite_all(Q, (size_t)d * d)) return TTGBF_ENONFINITE;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      if (i != j && Q[(size_t)i * d + j] != 0.0) return TTGBF_EINVAL;
+      if (i == j && !(Q[(size_t)i * d + j] > 0.0)) return TTGBF_EINVAL;
+    }
+  const bool same = c->lastF.size() == (size_t)d * d &&
+                    std::equal(c->lastF.begin(), c->lastF.end(), F) &&
+                    std::equal(c->lastQ.begin(), c->lastQ.end(), Q);
+  if (!same) {
+    rc = prepare_predict(c, F, Q);
+    if (rc) return rc;
+  }
+  if (c->expanded) enqueue_round(c);
+  cudaMemsetAsync(c->tail_sum, 0, sizeof(double) * c->B, c->st);
+  cudaMemsetAsync(c->tail_max, 0, sizeof(double) * c->B, c->st);
+  cudaMemsetAsync(c->cap_hits, 0, sizeof(int) * c->B, c->st);
+  for (size_t i = 0; i < c->ops.size(); ++i) {
+    const Op& op = c->ops[i];
+    if (op.kind == 0) {
+      enqueue_shear(c, op.m, op.n, c->op_S[i], c->op_tmin[i], c->opmats + c->op_woff[i], true);
+    } else if (!c->fuse) {
+      mode_apply(c, op.m, c->opmats + c->scale_off[op.m]);
+    }
+  }
+  for (int k = 0; k < d; ++k) mode_apply(c, k, c->opmats + c->mat_off[k]);
+  enqueue_normalise(c, c->mass_pred);
+  return check(c);
+}
+
+int ttgbf_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z) {
+  int rc = guard(c);
+  if (rc) return rc;
+  int two = -1;
+  rc = validate_meas(c, h, R, &two);
+  if (rc) return rc;
+  if (!z) return TTGBF_EINVAL;
+  if (!finite_all(z, (size_t)c->B * h->b)) return TTGBF_ENONFINITE;
+  wait_stage(c->ev_z, &c->ev_z_used);
+  for (size_t i = 0; i < (size_t)c->B * h->b; ++i) c->stage_z[i] = (float)z[i];
+  cudaMemcpyAsync(c->zbuf, c->stage_z, sizeof(float) * (size_t)c->B * h->b, cudaMemcpyHostToDevice, c->st);
+  cudaEventRecord(c->ev_z, c->st);
+  c->ev_z_used = true;
+  return enqueue_update(c, h, R, c->zbuf, h->b, two);
+}
+
+int ttgbf_update_dev(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z_dev) {
+  int rc = guard(c);
+  if (rc) return rc;
+  int two = -1;
+  rc = validate_meas(c, h, R, &two);
+  if (rc) return rc;
+  if (!z_dev) return TTGBF_EINVAL;
+  return enqueue_update(c, h, R, z_dev, h->b, two);
+}
+
+static int estimate_common(ttgbf_ctx* c) {
+  MomentArgs a = tt_moment_args(c, 1, 0);
+  launch_moments(c->st, c->B, a, c->ranks, c->d + 1, c->awork, c->L.awork_stride, c->mass, c->mean,
+                 c->cov);
+  return check(c);
+}
+
+int ttgbf_estimate(ttgbf_ctx* c, double* mean, double* cov, double* log_c, double* log_lik) {
+  int rc = guard(c);
+  if (rc) return rc;
+  rc = estimate_common(c);
+  if (rc) return rc;
+  const int B = c->B, d = c->d;
+  if (mean) cudaMemcpyAsync(mean, c->mean, sizeof(double) * B * d, cudaMemcpyDeviceToHost, c->st);
+  if (cov) cudaMemcpyAsync(cov, c->cov, sizeof(double) * B * d * d, cudaMemcpyDeviceToHost, c->st);
+  if (log_c) cudaMemcpyAsync(log_c, c->log_c, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  if (log_lik) cudaMemcpyAsync(log_lik, c->log_lik, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  return check(c);
+}
+
+int ttgbf_estimate_dev(ttgbf_ctx* c, double* mean, double* cov, double* log_c, double* log_lik) {
+  int rc = guard(c);
+  if (rc) return rc;
+  rc = estimate_common(c);
+  if (rc) return rc;
+  const int B = c->B, d = c->d;
+  if (mean) cudaMemcpyAsync(mean, c->mean, sizeof(double) * B * d, cudaMemcpyDeviceToDevice, c->st);
+  if (cov) cudaMemcpyAsync(cov, c->cov, sizeof(double) * B * d * d, cudaMemcpyDeviceToDevice, c->st);
+  if (log_c) cudaMemcpyAsync(log_c, c->log_c, sizeof(double) * B, cudaMemcpyDeviceToDevice, c->st);
+  if (log_lik) cudaMemcpyAsync(log_lik, c->log_lik, sizeof(double) * B, cudaMemcpyDeviceToDevice, c->st);
+  return check(c);
+}
+
+int ttgbf_free(ttgbf_ctx* c) {
+  if (!c) return TTGBF_OK;
+  if (c->st || c->base) cudaStreamSynchronize(c->st);
+  if (c->owns && c->base) cudaFree(c->base);
+  if (c->stage_ops) cudaFreeHost(c->stage_ops);
+  if (c->stage_z) cudaFreeHost(c->stage_z);
+  if (c->ev_ops) cudaEventDestroy(c->ev_ops);
+  if (c->ev_z) cudaEventDestroy(c->ev_z);
+  cudaGetLastError();
+  delete c;
+  return TTGBF_OK;
+}
+
+int ttgbf_ranks(ttgbf_ctx* c, int32_t* ranks) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!ranks) return TTGBF_EINVAL;
+  cudaMemcpyAsync(ranks, c->ranks, sizeof(int) * (size_t)c->B * (c->d + 1), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  return check(c);
+}
+
+int ttgbf_stats(ttgbf_ctx* c, ttgbf_step_stats* out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!out) return TTGBF_EINVAL;
+  const int B = c->B, d = c->d;
+  std::vector<double> ts(B), tm(B), mp(B), lc(B), ll(B);
+  std::vector<int> ch(B), rk((size_t)B * (d + 1));
+  cudaMemcpyAsync(ts.data(), c->tail_sum, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(tm.data(), c->tail_max, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(mp.data(), c->mass_pred, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(lc.data(), c->log_c, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(ll.data(), c->log_lik, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(ch.data(), c->cap_hits, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(rk.data(), c->ranks, sizeof(int) * rk.size(), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  for (int b = 0; b < B; ++b) {
+    int mr = 0;
+    for (int k = 0; k <= d; ++k) mr = std::max(mr, rk[(size_t)b * (d + 1) + k]);
+    out[b] = ttgbf_step_stats{ts[b], tm[b], mp[b], lc[b], ll[b], mr, ch[b]};
+  }
+  return check(c);
+}
+
+int ttgbf_grid_axes(const ttgbf_ctx* c, double* axes) {
+  if (!c || !axes) return TTGBF_EINVAL;
+  std::copy(c->axes.begin(), c->axes.end(), axes);
+  return TTGBF_OK;
+}
+
+int ttgbf_export_cores(ttgbf_ctx* c, int32_t f, float* buf, size_t cap, int32_t* ranks_out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!buf || !ranks_out || f < 0 || f >= c->B) return TTGBF_EINVAL;
+  const int d = c->d;
+  cudaMemcpyAsync(ranks_out, c->ranks + (size_t)f * (d + 1), sizeof(int) * (d + 1), cudaMemcpyDeviceToHost,
+                  c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  size_t need = 0;
+  for (int k = 0; k < d; ++k) need += (size_t)ranks_out[k] * c->n[k] * ranks_out[k + 1];
+  if (need > cap) return TTGBF_ENOMEM;
+  size_t at = 0;
+  for (int k = 0; k < d; ++k) {
+    const size_t cnt = (size_t)ranks_out[k] * c->n[k] * ranks_out[k + 1];
+    cudaMemcpyAsync(buf + at, curp(c, k) + (size_t)f * c->L.core_cap[k], sizeof(float) * cnt,
+                    cudaMemcpyDeviceToHost, c->st);
+    at += cnt;
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  return check(c);
+}
+
+int ttgbf_import_cores(ttgbf_ctx* c, int32_t f, const float* buf, const int32_t* ranks, double log_lik) {
+  int rc = guard(c);
+  if (rc) return rc;
+  const int d = c->d;
+  if (!buf || !ranks || f < 0 || f >= c->B) return TTGBF_EINVAL;
+  if (ranks[0] != 1 || ranks[d] != 1) return TTGBF_EINVAL;
+  if (!std::isfinite(log_lik)) return TTGBF_ENONFINITE;
+  bool over = false;
+  for (int k = 1; k < d; ++k) {
+    if (ranks[k] < 1 || ranks[k] > c->capr) return TTGBF_EINVAL;
+    if (ranks[k] > c->rank_cap) over = true;
+  }
+  size_t at = 0;
+  for (int k = 0; k < d; ++k) {
+    const size_t cnt = (size_t)ranks[k] * c->n[k] * ranks[k + 1];
+    for (size_t t = 0; t < cnt; ++t)
+      if (!std::isfinite(buf[at + t])) return TTGBF_ENONFINITE;
+    at += cnt;
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  at = 0;
+  for (int k = 0; k < d; ++k) {
+    const size_t cnt = (size_t)ranks[k] * c->n[k] * ranks[k + 1];
+    cudaMemcpy(curp(c, k) + (size_t)f * c->L.core_cap[k], buf + at, sizeof(float) * cnt, cudaMemcpyHostToDevice);
+    at += cnt;
+  }
+  cudaMemcpy(c->ranks + (size_t)f * (d + 1), ranks, sizeof(int) * (d + 1), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->log_lik + f, &log_lik, sizeof(double), cudaMemcpyHostToDevice);
+  if (over) c->expanded = true;
+  return check(c);
+}
+
+int ttgbf_shear(ttgbf_ctx* c, int32_t m, int32_t n, double a, int32_t do_round) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (m < 0 || n < 0 || m >= c->d || n >= c->d || m == n) return TTGBF_EINVAL;
+  if (!std::isfinite(a)) return TTGBF_ENONFINITE;
+  int S, tmin;
+  std::vector<float> w;
+  shear_table(c, m, n, a, &S, &tmin, &w);
+  if (S > c->smax) return TTGBF_ECAPACITY;
+  if (c->expanded) enqueue_round(c);
+  wait_stage(c->ev_ops, &c->ev_ops_used);
+  std::copy(w.begin(), w.end(), c->stage_ops);
+  cudaMemcpyAsync(c->opmats, c->stage_ops, sizeof(float) * w.size(), cudaMemcpyHostToDevice, c->st);
+  cudaEventRecord(c->ev_ops, c->st);
+  c->ev_ops_used = true;
+  c->lastF.clear();  // the operator area no longer holds a predict's operators
+  enqueue_shear(c, m, n, S, tmin, c->opmats, do_round != 0);
+  return check(c);
+}
+
+static int upload_mats(ttgbf_ctx* c, const std::vector<std::vector<double>>& mats) {
+  size_t tot = 0;
+  for (const auto& m : mats) tot += m.size();
+  if ((long long)tot > c->L.opmats_floats) return TTGBF_ECAPACITY;
+  wait_stage(c->ev_ops, &c->ev_ops_used);
+  size_t at = 0;
+  for (const auto& m : mats)
+    for (double v : m) c->stage_ops[at++] = (float)v;
+  cudaMemcpyAsync(c->opmats, c->stage_ops, sizeof(float) * tot, cudaMemcpyHostToDevice, c->st);
+  cudaEventRecord(c->ev_ops, c->st);
+  c->ev_ops_used = true;
+  c->lastF.clear();
+  return TTGBF_OK;
+}
+
+int ttgbf_scale(ttgbf_ctx* c, int32_t m, double lam) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (m < 0 || m >= c->d) return TTGBF_EINVAL;
+  if (!std::isfinite(lam)) return TTGBF_ENONFINITE;
+  std::vector<std::vector<double>> mats(1);
+  cic_matrix(c, m, lam, &mats[0]);
+  rc = upload_mats(c, mats);
+  if (rc) return rc;
+  mode_apply(c, m, c->opmats);
+  return check(c);
+}
+
+int ttgbf_convolve(ttgbf_ctx* c, const double* q) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!q) return TTGBF_EINVAL;
+  if (!finite_all(q, c->d)) return TTGBF_ENONFINITE;
+  std::vector<std::vector<double>> mats(c->d);
+  for (int k = 0; k < c->d; ++k) {
+    if (!(q[k] > 0.0)) return TTGBF_EINVAL;
+    conv_matrix(c, k, q[k], &mats[k]);
+  }
+  rc = upload_mats(c, mats);
+  if (rc) return rc;
+  size_t at = 0;
+  for (int k = 0; k < c->d; ++k) {
+    mode_apply(c, k, c->opmats + at);
+    at += mats[k].size();
+  }
+  return check(c);
+}
+
+int ttgbf_round(ttgbf_ctx* c) {
+  int rc = guard(c);
+  if (rc) return rc;
+  enqueue_round(c);
+  return check(c);
+}
+
+int ttgbf_normalise(ttgbf_ctx* c) {
+  int rc = guard(c);
+  if (rc) return rc;
+  enqueue_normalise(c, c->mass);
+  return check(c);
+}
+
+}  // extern "C"

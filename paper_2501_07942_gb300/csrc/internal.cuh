@@ -1,0 +1,145 @@
+// internal.cuh -- shared declarations of the ttgbf CUDA path (not part of the C ABI).
+//
+// Data layout in HBM (float32 unless noted):
+//   * TT core k of filter b lives in one of two ping-pong buffers per core,
+//     at buf[s][k] + b * core_cap[k], row-major [r_k][n_k][r_{k+1}] with the
+//     filter's ACTUAL ranks packed at the start of its capacity slot.
+//   * ranks: int32 [batch][d+1] on the device.  Every kernel reads the ranks
+//     it needs from there, so a filter step needs no host synchronisation and
+//     can be captured in a CUDA graph.
+//   * Small dense factors (Jacobi output P1/P2) use leading dimension kMaxN.
+//
+// The rounding of Sec. 4.1 ("round") is built from three generic pieces
+// driven by device-side work lists: a tree QR (TSQR) that returns only the R
+// factor of a tall matrix, a one-sided Jacobi SVD of that R, and a grouped
+// GEMM that applies the resulting small factors to the cores.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttgbf {
+
+constexpr int kSmemFloats = 51200;  // 200 KiB dynamic shared memory per TSQR CTA
+constexpr int kMaxN = 160;          // largest column count of a TSQR / SVD problem
+constexpr int kJacobiSmemFloats = 2 * kMaxN * kMaxN + 4 * kMaxN;
+constexpr int kMaxLevels = 20;      // TSQR reduction levels
+constexpr int kMaxD = 16;           // largest state dimension
+constexpr int kTile = 64;           // GEMM tile edge
+
+// A strided matrix view: element (i, j) at p[i * rs + j * cs], i < M, j < n.
+struct MatView {
+  const float* p;
+  long long rs, cs;
+  int M, n;
+};
+
+// One TSQR problem: the R factor of a tall matrix by a tree of Householder
+// QRs of row chunks.  Level 0 reads `src`; level L >= 1 reads the stack of
+// n x n R blocks written by level L-1 (stack0 at odd L-1 ... see tsqr_rows).
+struct TsqrProblem {
+  MatView src;
+  int chunk;  // rows per level-0 chunk; level >= 1 chunks hold floor(chunk/n) blocks
+  int nlev;   // levels this problem needs (>= 1); the R factor ends in stack[(nlev-1)&1]
+  float* stack0;
+  float* stack1;
+};
+
+struct TsqrWork {
+  TsqrProblem* prob;  // [B]
+  int* offset;        // [kMaxLevels][B+1] exclusive prefix of chunk counts per level
+};
+
+// Row-major GEMM C (m x n) = A (m x k) * B (k x n).
+struct GemmDesc {
+  const float* A;
+  const float* B;
+  float* C;
+  int m, n, k, lda, ldb, ldc;
+};
+
+struct GemmWork {
+  GemmDesc* desc;  // [ndesc]
+  int* tiles;      // [ndesc + 1] exclusive prefix of kTile x kTile tile counts
+  int ndesc;
+};
+
+enum StageMode : int { kStageRight = 0, kStageLeft = 1, kStageSplit = 2 };
+
+// Per-filter state of the rounding in progress.
+struct RoundState {
+  double* normA;     // [B] ||A||_F at the start of the truncation sweep
+  double* tail_sum;  // [B] sum of discarded relative tails
+  double* tail_max;  // [B]
+  int* cap_hits;     // [B]
+  int* newrank;      // [B] rank chosen by the last Jacobi stage
+};
+
+// Geometry of the TT shared by all filters.
+struct TTGeom {
+  int d;
+  int n[kMaxD];
+  long long cap[kMaxD];  // floats per filter per core
+};
+
+// ------------------------------------------------------------ launchers
+// linalg.cu
+void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
+                       const float* core_k, const float* W, long long W_cap, int N0, int N1,
+                       TsqrWork w, float* stack0, float* stack1, long long stack_cap);
+void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid);
+void launch_jacobi(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
+                   int first, RoundState rs, float* P1, float* P2, float* core0_out,
+                   long long core0_cap);
+void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
+                            const int* newrank, const float* cur_a, float* alt_a,
+                            const float* cur_b, float* alt_b, const float* P1, const float* P2,
+                            const float* W, long long W_cap, int N1, GemmWork gw);
+void launch_gemm(cudaStream_t st, GemmWork gw, int grid);
+// Tile prefix for descriptors already written to gw.desc (ndesc entries).
+void launch_scan_tiles(cudaStream_t st, GemmWork gw);
+
+// ttops.cu
+void launch_prior(cudaStream_t st, int B, const TTGeom& g, float* const* cores, int* ranks,
+                  const double* axes, const double* mean, const double* var);
+void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, int S, int tmin,
+                         const float* weights, float* const* cur, float* const* alt,
+                         const int* ranks);
+void launch_rank_scale(cudaStream_t st, int B, int d, int* ranks, int lo, int hi, int S);
+void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, const int* ranks,
+                            const float* M, const float* cur, float* alt, GemmWork gw, int cap_in);
+void launch_plan_supercore(cudaStream_t st, int B, const TTGeom& g, const int* ranks,
+                           const float* c0, const float* c1, float* W, long long W_cap,
+                           GemmWork gw);
+void launch_lik_offset(cudaStream_t st, int B, const float* htab, int ntab, const float* z,
+                       int zstride, int zc, double R, float* off, double* logoff);
+void launch_lik_apply_2d(cudaStream_t st, int B, float* W, long long W_cap, int N0, int N1,
+                         const int* ranks, int d, const float* htab, const float* z, int zstride,
+                         int zc, double R, const float* off);
+void launch_lik_apply_1d(cudaStream_t st, int B, float* core, long long cap, int N, int k, int d,
+                         const int* ranks, const float* htab, const float* z, int zstride, int zc,
+                         double R, const float* off);
+void launch_logc(cudaStream_t st, int B, const double* mass, const double* logoff, double* log_c,
+                 double* log_lik);
+// Moments of a TT given by per-core base pointers (filter stride cap[kk]) and
+// rank indices: core kk has ranks (ranks[b][ridx[kk]], ranks[b][ridx[kk+1]]).
+struct MomentArgs {
+  int ncores;
+  int n[kMaxD + 1];
+  int ridx[kMaxD + 2];
+  const float* core[kMaxD + 1];
+  long long cap[kMaxD + 1];
+  const double* axes[kMaxD + 1];  // per-core coordinates (nullptr when mass only)
+  double centre[kMaxD + 1];
+  double delta;       // cell volume
+  int with_moments;   // 0: mass only
+  float* scale_core;  // core scaled by 1/mass after the moments (nullptr: none)
+  long long scale_cap;
+  int scale_idx;      // index kk of scale_core
+};
+void launch_moments(cudaStream_t st, int B, const MomentArgs& a, const int* ranks, int rstride,
+                    double* Awork, long long awork_stride, double* mass, double* mean, double* cov);
+// Function attributes (large dynamic shared memory); call once per process.
+void set_kernel_attributes();
+void set_ttops_attributes();
+
+}  // namespace ttgbf

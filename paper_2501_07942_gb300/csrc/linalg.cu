@@ -1,0 +1,583 @@
+// linalg.cu -- batched tall-skinny QR (R factor only), one-sided Jacobi SVD and
+// grouped GEMM used by TT rounding (Sec. 4.1 "round"; Alg. 2 steps 2 and 4).
+//
+// One rounding stage (one core of the right-to-left orthogonalisation sweep,
+// or one link of the left-to-right truncation sweep) is:
+//   plan    -> per filter, the tall matrix whose R factor is needed
+//   TSQR    -> R (n x n) by a tree of in-shared-memory Householder QRs
+//   Jacobi  -> R = U S V^T, rank choice, small factors P1, P2
+//   plan2   -> GEMM descriptors for "new core = unfolding * P" and
+//              "neighbour core = P * neighbour"
+//   GEMM    -> grouped SIMT FP32 GEMM over all filters
+// Every problem size is read from the device rank array.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace ttgbf {
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Rows of the source of problem p at level L, and the chunk size used there.
+__device__ __forceinline__ void tsqr_level_shape(const TsqrProblem& p, int L, int* rows, int* chunk) {
+  const int n = p.src.n;
+  int r = p.src.M;
+  int C = p.chunk;
+  for (int l = 0; l < L; ++l) {
+    const int nch = (r + C - 1) / C;
+    r = nch * n;
+    C = (p.chunk / n) * n;
+  }
+  *rows = r;
+  *chunk = C;
+}
+
+// In-place exclusive scan of o[0..n) by one CTA of at most 1024 threads;
+// writes the total to o[n].
+__device__ void block_scan_inplace(int* o, int n) {
+  __shared__ int s_carry;
+  __shared__ int s_tmp[1024];
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = (i < n) ? o[i] : 0;
+    s_tmp[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 1; s < (int)blockDim.x; s <<= 1) {
+      const int t = (threadIdx.x >= (unsigned)s) ? s_tmp[threadIdx.x - s] : 0;
+      __syncthreads();
+      s_tmp[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < n) o[i] = s_carry + s_tmp[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += s_tmp[blockDim.x - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) o[n] = s_carry;
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ TSQR
+// Householder QR of a rows x n chunk held column-major in shared memory
+// (sm[j * rows + i]); writes the n x n R factor (zeros below the diagonal and
+// below row min(rows, n)) row-major to `out`.  Reflectors use the scaled form
+// H = I - tau v v^T with v_j = 1, tau = (beta - alpha) / beta and norms
+// computed after scaling by the column maximum, so tiny or huge columns
+// neither underflow nor overflow.
+__device__ void householder_chunk(float* sm, int rows, int n, float* out) {
+  __shared__ float s_beta[kMaxN];
+  __shared__ float s_tau;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int kmax = rows < n ? rows : n;
+  for (int j = 0; j < kmax; ++j) {
+    float* colj = sm + (long long)j * rows;
+    if (warp == 0) {
+      float mx = 0.f;
+      for (int i = j + 1 + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(colj[i]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      float s = 0.f;
+      if (mx > 0.f) {
+        const float inv = 1.f / mx;
+        for (int i = j + 1 + lane; i < rows; i += 32) {
+          const float x = colj[i] * inv;
+          s += x * x;
+        }
+      }
+      s = warp_sum(s);
+      const float alpha = colj[j];
+      const float tail = mx * sqrtf(s);  // ||x_{j+1:}||
+      float tau = 0.f, beta = alpha, scl = 0.f;
+      if (tail > 0.f) {
+        const float big = fmaxf(fabsf(alpha), tail);
+        const float ra = alpha / big, rt = tail / big;
+        const float norm = big * sqrtf(ra * ra + rt * rt);
+        beta = alpha >= 0.f ? -norm : norm;
+        tau = (beta - alpha) / beta;
+        scl = 1.f / (alpha - beta);
+      }
+      if (tau != 0.f)
+        for (int i = j + 1 + lane; i < rows; i += 32) colj[i] *= scl;
+      __syncwarp();
+      if (lane == 0) {
+        s_tau = tau;
+        s_beta[j] = beta;
+        colj[j] = 1.f;
+      }
+    }
+    __syncthreads();
+    const float tau = s_tau;
+    if (tau != 0.f) {
+      for (int c = j + 1 + warp; c < n; c += nwarps) {
+        float* colc = sm + (long long)c * rows;
+        float dot = 0.f;
+        for (int i = j + lane; i < rows; i += 32) dot += colj[i] * colc[i];
+        dot = warp_sum(dot) * tau;
+        for (int i = j + lane; i < rows; i += 32) colc[i] -= dot * colj[i];
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, c = t - i * n;
+    float v = 0.f;
+    if (i < kmax && c >= i) v = (c == i) ? s_beta[i] : sm[(long long)c * rows + i];
+    out[t] = v;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) k_tsqr_level(TsqrWork w, int B, int L) {
+  extern __shared__ float sm[];
+  const int* off = w.offset + (long long)L * (B + 1);
+  const int total = off[B];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int lo = 0, hi = B;  // off[lo] <= item < off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int b = lo;
+    const int c = item - off[b];
+    const TsqrProblem p = w.prob[b];
+    const int n = p.src.n;
+    int rowsL, C;
+    tsqr_level_shape(p, L, &rowsL, &C);
+    const int r0 = c * C;
+    const int rows = min(C, rowsL - r0);
+    const float* base;
+    long long rs, cs;
+    if (L == 0) {
+      base = p.src.p;
+      rs = p.src.rs;
+      cs = p.src.cs;
+    } else {
+      base = ((L - 1) & 1) ? p.stack1 : p.stack0;
+      rs = n;
+      cs = 1;
+    }
+    float* out = ((L & 1) ? p.stack1 : p.stack0) + (long long)c * n * n;
+    const long long cnt = (long long)rows * n;
+    if (cs == 1) {
+      for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t - (long long)i * n);
+        sm[(long long)j * rows + i] = base[(r0 + i) * rs + j];
+      }
+    } else {
+      for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int j = (int)(t / rows), i = (int)(t - (long long)j * rows);
+        sm[(long long)j * rows + i] = base[(r0 + i) * rs + j * cs];
+      }
+    }
+    __syncthreads();
+    householder_chunk(sm, rows, n, out);
+  }
+}
+
+// ------------------------------------------------------------ Jacobi SVD
+// Pair k of round r of the circle method on npad (even) columns.
+__device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int* q) {
+  const int m = npad - 1;
+  if (k == 0) {
+    *p = 0;
+    *q = 1 + (r % m);
+  } else {
+    *p = 1 + ((k + r) % m);
+    *q = 1 + ((m - k + r) % m);
+  }
+}
+
+// One-sided (Hestenes) Jacobi SVD of the n x n R factor of problem b, then the
+// stage's rank choice and factor output.  One CTA per filter.
+__global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int rank_cap, double eps,
+                                                int d, int first, RoundState rs, float* P1, float* P2,
+                                                float* core0_out, long long core0_cap) {
+  extern __shared__ float sm[];
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const TsqrProblem p = w.prob[b];
+  const int n = p.src.n;
+  const float* R = ((p.nlev - 1) & 1) ? p.stack1 : p.stack0;
+  float* A = sm;                              // column-major n x n: A[c * n + i]
+  float* V = sm + kMaxN * kMaxN;              // column-major n x n
+  float* nrm = sm + 2 * kMaxN * kMaxN;        // [kMaxN]
+  float* sig = nrm + kMaxN;                   // [kMaxN] sorted singular values
+  int* perm = (int*)(sig + kMaxN);            // [kMaxN]
+  __shared__ int s_rot;
+  __shared__ int s_rank;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, c = t - i * n;
+    A[c * n + i] = R[t];
+    V[c * n + i] = (i == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int npad = (n + 1) & ~1;
+  const float tol = 5e-7f * sqrtf((float)n);
+  for (int sweep = 0; sweep < 40 && npad >= 2; ++sweep) {
+    for (int c = warp; c < n; c += nwarps) {
+      float s = 0.f;
+      for (int i = lane; i < n; i += 32) s += A[c * n + i] * A[c * n + i];
+      s = warp_sum(s);
+      if (lane == 0) nrm[c] = s;
+    }
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < npad - 1; ++r) {
+      for (int k = warp; k < npad / 2; k += nwarps) {
+        int pp, qq;
+        jacobi_pair(k, r, npad, &pp, &qq);
+        if (pp >= n || qq >= n) continue;
+        float* ap = A + pp * n;
+        float* aq = A + qq * n;
+        float g = 0.f;
+        for (int i = lane; i < n; i += 32) g += ap[i] * aq[i];
+        g = warp_sum(g);
+        const float al = nrm[pp], be = nrm[qq];
+        if (g == 0.f || !(fabsf(g) > tol * sqrtf(al * be))) continue;
+        const float zeta = (be - al) / (2.f * g);
+        const float az = fabsf(zeta);
+        const float t = (az > 1e15f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta))) *
+                        (zeta >= 0.f ? 1.f : -1.f);
+        const float cth = rsqrtf(1.f + t * t);
+        const float sth = cth * t;
+        for (int i = lane; i < n; i += 32) {
+          const float x = ap[i], y = aq[i];
+          ap[i] = cth * x - sth * y;
+          aq[i] = sth * x + cth * y;
+        }
+        float* vp = V + pp * n;
+        float* vq = V + qq * n;
+        for (int i = lane; i < n; i += 32) {
+          const float x = vp[i], y = vq[i];
+          vp[i] = cth * x - sth * y;
+          vq[i] = sth * x + cth * y;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          nrm[pp] = al - t * g;
+          nrm[qq] = be + t * g;
+          atomicAdd(&s_rot, 1);
+        }
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  // exact column norms, then sort descending
+  for (int c = warp; c < n; c += nwarps) {
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += (double)A[c * n + i] * (double)A[c * n + i];
+    s = warp_sum_d(s);
+    if (lane == 0) nrm[c] = (float)sqrt(s);
+  }
+  __syncthreads();
+  // non-finite norms (only from non-finite input) sort last as zeros, so every
+  // position 0..n-1 receives exactly one column
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    if (!(nrm[c] >= 0.f) || isinf(nrm[c])) nrm[c] = -1.f;
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const float v = nrm[c];
+    int pos = 0;
+    for (int e = 0; e < n; ++e) {
+      const float u = nrm[e];
+      pos += (u > v) || (u == v && e < c);
+    }
+    sig[pos] = v < 0.f ? 0.f : v;
+    perm[pos] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int r;
+    if (mode == kStageRight) {
+      const float s0 = sig[0];
+      r = 0;
+      while (r < n && sig[r] > 1e-7f * s0) ++r;
+      if (r < 1) r = 1;
+    } else {
+      double tot = 0.0;
+      for (int j = 0; j < n; ++j) tot += (double)sig[j] * (double)sig[j];
+      double normA;
+      if (first) {
+        normA = sqrt(tot);
+        rs.normA[b] = normA;
+      } else {
+        normA = rs.normA[b];
+      }
+      const double delta = (d > 1) ? eps * normA / sqrt((double)(d - 1)) : 0.0;
+      // tail[r] = sqrt(sum_{j >= r} sig_j^2); smallest r >= 1 with tail[r] <= delta
+      double acc = 0.0;
+      int reps = n;
+      for (int j = n - 1; j >= 1; --j) {
+        acc += (double)sig[j] * (double)sig[j];
+        if (sqrt(acc) <= delta) reps = j; else break;
+      }
+      r = reps < rank_cap ? reps : rank_cap;
+      if (r < 1) r = 1;
+      double tail = 0.0;
+      for (int j = r; j < n; ++j) tail += (double)sig[j] * (double)sig[j];
+      const double rel = normA > 0.0 ? sqrt(tail) / normA : 0.0;
+      rs.tail_sum[b] += rel;
+      if (rel > rs.tail_max[b]) rs.tail_max[b] = rel;
+      if (reps > rank_cap) rs.cap_hits[b] += 1;
+    }
+    s_rank = r;
+    rs.newrank[b] = r;
+  }
+  __syncthreads();
+  const int r = s_rank;
+  float* p1 = P1 + (long long)b * kMaxN * kMaxN;
+  float* p2 = P2 + (long long)b * kMaxN * kMaxN;
+  for (int t = threadIdx.x; t < n * r; t += blockDim.x) {
+    const int i = t / r, j = t - i * r;  // i < n (row of V), j < r (singular index)
+    const float v = V[perm[j] * n + i];
+    const float s = sig[j];
+    const float inv = s > 1e-30f ? 1.f / s : 0.f;
+    if (mode == kStageRight) {
+      p1[j * kMaxN + i] = v * inv;  // P1 = S^-1 V^T  (r x n)
+      p2[i * kMaxN + j] = v * s;    // P2 = V S       (n x r)
+    } else if (mode == kStageLeft) {
+      p1[i * kMaxN + j] = v * inv;  // P1 = V S^-1    (n x r)
+      p2[j * kMaxN + i] = v * s;    // P2 = S V^T     (r x n)
+    } else {
+      core0_out[(long long)b * core0_cap + (long long)i * r + j] = v;  // core 0 = V_r (n x r)
+      p2[j * kMaxN + i] = v;                                          // P2 = V_r^T   (r x n)
+    }
+  }
+}
+
+// ------------------------------------------------------------------ GEMM
+__global__ void __launch_bounds__(256) k_gemm_grouped(GemmWork w) {
+  __shared__ float As[16][kTile + 4];
+  __shared__ float Bs[16][kTile + 4];
+  const int total = w.tiles[w.ndesc];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = w.ndesc;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (w.tiles[mid] <= t) lo = mid; else hi = mid;
+    }
+    const GemmDesc g = w.desc[lo];
+    const int tn_count = (g.n + kTile - 1) / kTile;
+    const int local = t - w.tiles[lo];
+    const int tm = local / tn_count, tn = local - tm * tn_count;
+    const int row0 = tm * kTile, col0 = tn * kTile;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < g.k; k0 += 16) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int ar = e >> 4, ak = e & 15;
+        const int gr = row0 + ar, gk = k0 + ak;
+        As[ak][ar] = (gr < g.m && gk < g.k) ? g.A[(long long)gr * g.lda + gk] : 0.f;
+        const int bk = e >> 6, bc = e & 63;
+        const int hk = k0 + bk, hc = col0 + bc;
+        Bs[bk][bc] = (hk < g.k && hc < g.n) ? g.B[(long long)hk * g.ldb + hc] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        float a[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = row0 + ty * 4 + i;
+      if (r >= g.m) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = col0 + tx * 4 + j;
+        if (c < g.n) g.C[(long long)r * g.ldc + c] = acc[i][j];
+      }
+    }
+  }
+}
+
+__global__ void k_scan_tiles(GemmWork w) {
+  for (int i = threadIdx.x; i < w.ndesc; i += blockDim.x) {
+    const GemmDesc g = w.desc[i];
+    w.tiles[i] = (g.m > 0 && g.n > 0) ? ((g.m + kTile - 1) / kTile) * ((g.n + kTile - 1) / kTile) : 0;
+  }
+  __syncthreads();
+  block_scan_inplace(w.tiles, w.ndesc);
+}
+
+// ----------------------------------------------------------------- plans
+// Per filter: the tall matrix of this stage and its TSQR schedule.
+__global__ void k_plan_stage(TsqrWork w, int B, int mode, int k, TTGeom g, const int* ranks,
+                             const float* core_k, const float* W, long long W_cap, int N0, int N1,
+                             float* stack0, float* stack1, long long stack_cap) {
+  const int d = g.d;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int* rk = ranks + (long long)b * (d + 1);
+    TsqrProblem p;
+    if (mode == kStageRight) {
+      // X = core k as r_k x (n_k r_{k+1}); the R factor of X^T
+      const int r0 = rk[k], r1 = rk[k + 1];
+      const long long cols = (long long)g.n[k] * r1;
+      p.src.p = core_k + (long long)b * g.cap[k];
+      p.src.rs = 1;
+      p.src.cs = cols;
+      p.src.M = (int)cols;
+      p.src.n = r0;
+    } else if (mode == kStageLeft) {
+      // Y = core k as (r_k n_k) x r_{k+1}
+      const int r0 = rk[k], r1 = rk[k + 1];
+      p.src.p = core_k + (long long)b * g.cap[k];
+      p.src.rs = r1;
+      p.src.cs = 1;
+      p.src.M = r0 * g.n[k];
+      p.src.n = r1;
+    } else {
+      // W = supercore of modes 0,1 as N0 x (N1 r_2); the R factor of W^T
+      const long long cols = (long long)N1 * rk[2];
+      p.src.p = W + (long long)b * W_cap;
+      p.src.rs = 1;
+      p.src.cs = cols;
+      p.src.M = (int)cols;
+      p.src.n = N0;
+    }
+    const int n = p.src.n;
+    int C = kSmemFloats / n;
+    if (C > p.src.M) C = p.src.M;
+    if (C < 1) C = 1;
+    p.chunk = C;
+    p.stack0 = stack0 + (long long)b * stack_cap;
+    p.stack1 = stack1 + (long long)b * stack_cap;
+    int rows = p.src.M, Cl = C, L = 0;
+    for (;; ++L) {
+      const int nch = (rows + Cl - 1) / Cl;
+      w.offset[(long long)L * (B + 1) + b] = nch;  // counts, scanned below
+      if (nch == 1 || L == kMaxLevels - 1) break;
+      rows = nch * n;
+      Cl = (C / n) * n;
+    }
+    p.nlev = L + 1;
+    for (int l = L + 1; l < kMaxLevels; ++l) w.offset[(long long)l * (B + 1) + b] = 0;
+    w.prob[b] = p;
+  }
+  __syncthreads();
+  for (int L = 0; L < kMaxLevels; ++L) block_scan_inplace(w.offset + (long long)L * (B + 1), B);
+}
+
+// Per filter: GEMM descriptors that apply the stage's small factors, then
+// the rank update.
+__global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, const int* newrank,
+                                  const float* cur_a, float* alt_a, const float* cur_b, float* alt_b,
+                                  const float* P1, const float* P2, const float* W, long long W_cap,
+                                  int N1, GemmWork gw) {
+  const int d = g.d;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    int* rk = ranks + (long long)b * (d + 1);
+    const int rn = newrank[b];
+    const float* p1 = P1 + (long long)b * kMaxN * kMaxN;
+    const float* p2 = P2 + (long long)b * kMaxN * kMaxN;
+    if (mode == kStageRight) {
+      // a = core k (r_k x n_k r_{k+1}), b = core k-1 ((r_{k-1} n_{k-1}) x r_k)
+      const int rkk = rk[k], r1 = rk[k + 1], rm = rk[k - 1];
+      const int cols = g.n[k] * r1;
+      GemmDesc x{p1, cur_a + (long long)b * g.cap[k], alt_a + (long long)b * g.cap[k], rn, cols, rkk,
+                 kMaxN, cols, cols};
+      GemmDesc y{cur_b + (long long)b * g.cap[k - 1], p2, alt_b + (long long)b * g.cap[k - 1],
+                 rm * g.n[k - 1], rn, rkk, rkk, kMaxN, rn};
+      gw.desc[2 * b] = x;
+      gw.desc[2 * b + 1] = y;
+      rk[k] = rn;
+    } else if (mode == kStageLeft) {
+      // a = core k ((r_k n_k) x r_{k+1}), b = core k+1 (r_{k+1} x n_{k+1} r_{k+2})
+      const int r0 = rk[k], r1 = rk[k + 1], r2 = rk[k + 2];
+      const int cols = g.n[k + 1] * r2;
+      GemmDesc x{cur_a + (long long)b * g.cap[k], p1, alt_a + (long long)b * g.cap[k], r0 * g.n[k], rn,
+                 r1, r1, kMaxN, rn};
+      GemmDesc y{p2, cur_b + (long long)b * g.cap[k + 1], alt_b + (long long)b * g.cap[k + 1], rn, cols,
+                 r1, kMaxN, cols, cols};
+      gw.desc[2 * b] = x;
+      gw.desc[2 * b + 1] = y;
+      rk[k + 1] = rn;
+    } else {
+      // new core 1 = V_r^T W  (r x N1 r_2); core 0 was written by the Jacobi kernel
+      const int r2 = rk[2];
+      const int cols = N1 * r2;
+      const int N0 = g.n[0];
+      GemmDesc y{p2, W + (long long)b * W_cap, alt_b + (long long)b * g.cap[1], rn, cols, N0, kMaxN,
+                 cols, cols};
+      gw.desc[b] = y;
+      rk[1] = rn;
+    }
+  }
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- launchers
+void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
+                       const float* core_k, const float* W, long long W_cap, int N0, int N1,
+                       TsqrWork w, float* stack0, float* stack1, long long stack_cap) {
+  k_plan_stage<<<1, 1024, 0, st>>>(w, B, mode, k, g, ranks, core_k, W, W_cap, N0, N1, stack0, stack1,
+                                   stack_cap);
+}
+
+void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid) {
+  for (int L = 0; L < levels; ++L)
+    k_tsqr_level<<<grid, 512, kSmemFloats * sizeof(float), st>>>(w, B, L);
+}
+
+void launch_jacobi(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
+                   int first, RoundState rs, float* P1, float* P2, float* core0_out,
+                   long long core0_cap) {
+  k_jacobi<<<B, 512, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs,
+                                                                P1, P2, core0_out, core0_cap);
+}
+
+void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
+                            const int* newrank, const float* cur_a, float* alt_a,
+                            const float* cur_b, float* alt_b, const float* P1, const float* P2,
+                            const float* W, long long W_cap, int N1, GemmWork gw) {
+  k_plan_gemm_stage<<<1, 1024, 0, st>>>(B, mode, k, g, ranks, newrank, cur_a, alt_a, cur_b, alt_b, P1,
+                                        P2, W, W_cap, N1, gw);
+  k_scan_tiles<<<1, 1024, 0, st>>>(gw);
+}
+
+void launch_gemm(cudaStream_t st, GemmWork gw, int grid) {
+  k_gemm_grouped<<<grid, 256, 0, st>>>(gw);
+}
+
+void launch_scan_tiles(cudaStream_t st, GemmWork gw) { k_scan_tiles<<<1, 1024, 0, st>>>(gw); }
+
+void set_kernel_attributes() {
+  cudaFuncSetAttribute(k_tsqr_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kSmemFloats * (int)sizeof(float));
+  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kJacobiSmemFloats * (int)sizeof(float));
+}
+
+}  // namespace ttgbf

@@ -1,0 +1,452 @@
+// ttops.cu -- tensor-train operations of one filter step on a batch of filters:
+// rank-1 prior (Alg. 2 step 1), re-gridding shear expansion (the hat-weight
+// shear x_m += a x_n as an operator of TT rank S), per-mode dense operators
+// (cloud-in-cell scaling and the Gaussian transition kernel of Eq.
+// tpmconvFFT applied over each core's grid index), the likelihood of Eqs.
+// pmf_filtrace_a/b, and moments / normalisation by TT contraction ("sum",
+// "dot", "power", Sec. 4.1).
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace ttgbf {
+namespace {
+
+struct CorePtrs {
+  float* p[kMaxD];
+};
+
+// --------------------------------------------------------------- prior
+__global__ void k_prior(int B, TTGeom g, CorePtrs cores, int* ranks, const double* axes,
+                        const double* mean, const double* var) {
+  const int b = blockIdx.x, k = blockIdx.y;
+  if (b >= B || k >= g.d) return;
+  int off = 0;
+  for (int j = 0; j < k; ++j) off += g.n[j];
+  float* G = cores.p[k] + (long long)b * g.cap[k];
+  for (int i = threadIdx.x; i < g.n[k]; i += blockDim.x) {
+    const double x = axes[off + i] - mean[k];
+    G[i] = (float)exp(-0.5 * x * x / var[k]);
+  }
+  if (k == 0 && threadIdx.x == 0) {
+    int* rk = ranks + (long long)b * (g.d + 1);
+    for (int j = 0; j <= g.d; ++j) rk[j] = 1;
+  }
+}
+
+// ------------------------------------------------------- shear expansion
+// Shear x_m += a x_n (m != n).  With s(i) = a xi_{n,i} / D_m and integer
+// shifts t = tmin + u, u < S, the operator is sum_u Shift_t (mode m) x
+// diag(hat(t - s)) (mode n) x identity between them: a TT operator of rank S
+// on the links between modes lo = min(m,n) and hi = max(m,n).
+//   core lo : (r_lo,     N, r_lo+1 S)
+//   middle  : (r_l S,    N, r_l+1 S)   = G_l (x) I_S
+//   core hi : (r_hi S,   N, r_hi+1)
+// The shifted side is mode m, the weighted side mode n.
+__global__ void k_shear_expand(int B, TTGeom g, int m, int n, int S, int tmin, const float* wts,
+                               CorePtrs cur, CorePtrs alt, const int* ranks) {
+  const int b = blockIdx.z;
+  const int lo = m < n ? m : n, hi = m < n ? n : m;
+  const int l = lo + blockIdx.y;
+  if (b >= B || l > hi) return;
+  const int* rk = ranks + (long long)b * (g.d + 1);
+  const int a0 = rk[l], a1 = rk[l + 1];
+  const int N = g.n[l];
+  const int o0 = (l == lo) ? a0 : a0 * S;
+  const int o1 = (l == hi) ? a1 : a1 * S;
+  const long long total = (long long)o0 * N * o1;
+  const float* in = cur.p[l] + (long long)b * g.cap[l];
+  float* out = alt.p[l] + (long long)b * g.cap[l];
+  const bool shift_side = (l == m);
+  const int Nn = g.n[n];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(e / ((long long)N * o1));
+    const long long rem = e - (long long)x * N * o1;
+    const int i = (int)(rem / o1);
+    const int y = (int)(rem - (long long)i * o1);
+    float v = 0.f;
+    if (l == lo && l == hi) {
+      v = 0.f;  // not reachable: m != n
+    } else if (l == lo) {
+      const int beta = y / S, u = y - beta * S;
+      if (shift_side) {
+        const int src = i - (tmin + u);
+        if (src >= 0 && src < N) v = in[((long long)x * N + src) * a1 + beta];
+      } else {
+        v = wts[u * Nn + i] * in[((long long)x * N + i) * a1 + beta];
+      }
+    } else if (l == hi) {
+      const int beta = x / S, u = x - beta * S;
+      if (shift_side) {
+        const int src = i - (tmin + u);
+        if (src >= 0 && src < N) v = in[((long long)beta * N + src) * a1 + y];
+      } else {
+        v = wts[u * Nn + i] * in[((long long)beta * N + i) * a1 + y];
+      }
+    } else {
+      const int alpha = x / S, s = x - alpha * S;
+      const int beta = y / S, t = y - beta * S;
+      if (s == t) v = in[((long long)alpha * N + i) * a1 + beta];
+    }
+    out[e] = v;
+  }
+}
+
+__global__ void k_rank_scale(int B, int d, int* ranks, int lo, int hi, int S) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    int* rk = ranks + (long long)b * (d + 1);
+    for (int l = lo + 1; l <= hi; ++l) rk[l] *= S;
+  }
+}
+
+// ------------------------------------------------------- per-mode apply
+// G'(a, j, b) = sum_i M(j, i) G(a, i, b): one GEMM (N x N) x (N x r_{k+1}) per
+// (filter, left index a).
+__global__ void k_plan_mode_apply(int B, int k, TTGeom g, const int* ranks, const float* M,
+                                  const float* cur, float* alt, GemmWork gw, int cap_in) {
+  const int N = g.n[k];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < B * cap_in; q += gridDim.x * blockDim.x) {
+    const int b = q / cap_in, a = q - b * cap_in;
+    const int* rk = ranks + (long long)b * (g.d + 1);
+    const int r0 = rk[k], r1 = rk[k + 1];
+    GemmDesc x{M, nullptr, nullptr, 0, 0, 0, N, r1, r1};
+    if (a < r0) {
+      const long long off = (long long)b * g.cap[k] + (long long)a * N * r1;
+      x.B = cur + off;
+      x.C = alt + off;
+      x.m = N;
+      x.n = r1;
+      x.k = N;
+    }
+    gw.desc[q] = x;
+  }
+}
+
+// W_b = core0 (N0 x r1) * core1 (r1 x N1 r2): the 2-site supercore of modes 0, 1.
+__global__ void k_plan_supercore(int B, TTGeom g, const int* ranks, const float* c0, const float* c1,
+                                 float* W, long long W_cap, GemmWork gw) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int* rk = ranks + (long long)b * (g.d + 1);
+    const int r1 = rk[1], r2 = rk[2];
+    const int cols = g.n[1] * r2;
+    GemmDesc x{c0 + (long long)b * g.cap[0], c1 + (long long)b * g.cap[1], W + (long long)b * W_cap,
+               g.n[0], cols, r1, r1, cols, cols};
+    gw.desc[b] = x;
+  }
+}
+
+// ----------------------------------------------------------- likelihood
+// Per filter b: off_b = min_i (z_b - h(i))^2 over the component's table, so that
+// the scaled likelihood exp(-((z-h)^2 - off)/(2R)) is <= 1 with maximum 1.
+// logoff_b accumulates the dropped factor log(exp(-off/(2R)) / sqrt(2 pi R)).
+__global__ void k_lik_offset(int B, const float* htab, int ntab, const float* z, int zstride, int zc,
+                             double R, float* off, double* logoff) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const float zb = z[(long long)b * zstride + zc];
+  float mn = INFINITY;
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) {
+    const float e = zb - htab[i];
+    mn = fminf(mn, e * e);
+  }
+  __shared__ float s_m[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = s_m[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fminf(v, s_m[w]);
+    off[b] = v;
+    logoff[b] += -(double)v / (2.0 * R) - 0.5 * log(2.0 * 3.14159265358979323846 * R);
+  }
+}
+
+// W(i0, i1, c) *= exp(-((z - h(i0,i1))^2 - off) / (2R)): Hadamard product of the
+// supercore with the (exact, merged-mode) likelihood of a two-mode component.
+__global__ void k_lik_apply_2d(int B, float* W, long long W_cap, int N0, int N1, int d, const int* ranks,
+                               const float* htab, const float* z, int zstride, int zc, double R,
+                               const float* off) {
+  const int b = blockIdx.y;
+  if (b >= B) return;
+  const int r2 = ranks[(long long)b * (d + 1) + 2];
+  const long long total = (long long)N0 * N1 * r2;
+  const float zb = z[(long long)b * zstride + zc];
+  const float ob = off[b];
+  const float inv2r = (float)(0.5 / R);
+  float* Wb = W + (long long)b * W_cap;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long t = e / r2;  // i0 * N1 + i1
+    const float df = zb - htab[t];
+    Wb[e] *= expf(-(df * df - ob) * inv2r);
+  }
+}
+
+// G_k(a, i, b) *= exp(-((z - h(i))^2 - off) / (2R)): one-mode component.
+__global__ void k_lik_apply_1d(int B, float* core, long long cap, int N, int k, int d, const int* ranks,
+                               const float* htab, const float* z, int zstride, int zc, double R,
+                               const float* off) {
+  const int b = blockIdx.y;
+  if (b >= B) return;
+  const int* rk = ranks + (long long)b * (d + 1);
+  const int r0 = rk[k], r1 = rk[k + 1];
+  const long long total = (long long)r0 * N * r1;
+  const float zb = z[(long long)b * zstride + zc];
+  const float ob = off[b];
+  const float inv2r = (float)(0.5 / R);
+  float* G = core + (long long)b * cap;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)((e / r1) % N);
+    const float df = zb - htab[i];
+    G[e] *= expf(-(df * df - ob) * inv2r);
+  }
+}
+
+// -------------------------------------------------------------- moments
+// One CTA per filter.  A_kk^(p)(a, b) = sum_i w_p(i) G_kk(a, i, b) with
+// w_p(i) = (xi_i - c)^p, p <= 2, accumulated in float64; then vector chains:
+//   f_kk = A_kk^(0) f_kk+1 (right sums), mass = f_0 * delta,
+//   mean_k  ~ e_k A_k^(1) f_k+1,  E[x_k^2] ~ e_k A_k^(2) f_k+1,
+//   E[x_m x_k] ~ u_m A_k^(1) f_k+1 with u_m = e_m A_m^(1) A_m+1^(0) ... A_k-1^(0).
+__global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, double* Awork,
+                          long long awork_stride, double* mass_out, double* mean_out, double* cov_out) {
+  extern __shared__ double smd[];
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const int nc = a.ncores;
+  const int P = a.with_moments ? 3 : 1;
+  double* f = smd;                              // (nc + 1) x kMaxN
+  double* u = f + (kMaxD + 2) * kMaxN;          // nc x kMaxN
+  double* e = u + (kMaxD + 1) * kMaxN;          // kMaxN
+  double* tmp = e + kMaxN;                      // kMaxN
+  double* acc = tmp + kMaxN;                    // 3 x 1024
+  double* red = acc + 3 * 1024;                 // 32
+  __shared__ double s_mean[kMaxD + 1];
+  __shared__ double s_S[(kMaxD + 1) * (kMaxD + 1)];
+  const int* rk = ranks + (long long)b * rstride;
+  const long long Astride = (long long)kMaxN * kMaxN;
+  double* Ab = Awork + (long long)b * awork_stride;
+
+  // ---- per-core weighted sums over the grid index
+  for (int kk = 0; kk < nc; ++kk) {
+    const int r0 = rk[a.ridx[kk]], r1 = rk[a.ridx[kk + 1]];
+    const int N = a.n[kk];
+    const float* G = a.core[kk] + (long long)b * a.cap[kk];
+    const double* ax = a.axes[kk];
+    const double c = a.centre[kk];
+    const int npairs = r0 * r1;
+    for (int pb = 0; pb < npairs; pb += 1024) {
+      const int nb = min(1024, npairs - pb);
+      for (int t = threadIdx.x; t < 3 * 1024; t += blockDim.x) acc[t] = 0.0;
+      __syncthreads();
+      const int groups = max(1, (int)blockDim.x / nb);
+      if ((int)threadIdx.x < nb * groups) {
+        const int q = pb + (threadIdx.x % nb);
+        const int grp = threadIdx.x / nb;
+        const int al = q / r1, be = q - al * r1;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int i = grp; i < N; i += groups) {
+          const double v = (double)G[((long long)al * N + i) * r1 + be];
+          s0 += v;
+          if (P > 1) {
+            const double x = ax[i] - c;
+            s1 += x * v;
+            s2 += x * x * v;
+          }
+        }
+        atomicAdd(&acc[q - pb], s0);
+        if (P > 1) {
+          atomicAdd(&acc[1024 + q - pb], s1);
+          atomicAdd(&acc[2048 + q - pb], s2);
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        for (int p = 0; p < P; ++p) Ab[((long long)kk * 3 + p) * Astride + pb + t] = acc[p * 1024 + t];
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+
+  auto block_dot = [&](const double* x, const double* y, int len) -> double {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) s += x[t] * y[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    __syncthreads();
+    return tot;
+  };
+  // y (len r1) = x (len r0) * A (r0 x r1)
+  auto vecmat = [&](const double* x, const double* A, int r0, int r1, double* y) {
+    for (int be = threadIdx.x; be < r1; be += blockDim.x) {
+      double s = 0.0;
+      for (int al = 0; al < r0; ++al) s += x[al] * A[(long long)al * r1 + be];
+      y[be] = s;
+    }
+    __syncthreads();
+  };
+
+  // ---- right sums
+  if (threadIdx.x == 0) f[nc * kMaxN] = 1.0;
+  __syncthreads();
+  for (int kk = nc - 1; kk >= 0; --kk) {
+    const int r0 = rk[a.ridx[kk]], r1 = rk[a.ridx[kk + 1]];
+    const double* A0 = Ab + ((long long)kk * 3 + 0) * Astride;
+    for (int al = threadIdx.x; al < r0; al += blockDim.x) {
+      double s = 0.0;
+      for (int be = 0; be < r1; ++be) s += A0[(long long)al * r1 + be] * f[(kk + 1) * kMaxN + be];
+      f[kk * kMaxN + al] = s;
+    }
+    __syncthreads();
+  }
+  const double mraw = f[0];
+  if (a.with_moments) {
+    if (threadIdx.x == 0) e[0] = 1.0;
+    __syncthreads();
+    for (int kk = 0; kk < nc; ++kk) {
+      const int r0 = rk[a.ridx[kk]], r1 = rk[a.ridx[kk + 1]];
+      const double* A0 = Ab + ((long long)kk * 3 + 0) * Astride;
+      const double* A1 = Ab + ((long long)kk * 3 + 1) * Astride;
+      const double* A2 = Ab + ((long long)kk * 3 + 2) * Astride;
+      const double* fr = f + (kk + 1) * kMaxN;
+      vecmat(e, A2, r0, r1, tmp);
+      const double s2 = block_dot(tmp, fr, r1);
+      for (int mm = 0; mm < kk; ++mm) {
+        vecmat(u + mm * kMaxN, A1, r0, r1, tmp);
+        const double sc = block_dot(tmp, fr, r1);
+        if (threadIdx.x == 0) s_S[mm * (kMaxD + 1) + kk] = sc;
+        vecmat(u + mm * kMaxN, A0, r0, r1, tmp);
+        for (int t = threadIdx.x; t < r1; t += blockDim.x) u[mm * kMaxN + t] = tmp[t];
+        __syncthreads();
+      }
+      vecmat(e, A1, r0, r1, tmp);
+      const double s1 = block_dot(tmp, fr, r1);
+      for (int t = threadIdx.x; t < r1; t += blockDim.x) u[kk * kMaxN + t] = tmp[t];
+      __syncthreads();
+      vecmat(e, A0, r0, r1, tmp);
+      for (int t = threadIdx.x; t < r1; t += blockDim.x) e[t] = tmp[t];
+      if (threadIdx.x == 0) {
+        s_mean[kk] = s1;
+        s_S[kk * (kMaxD + 1) + kk] = s2;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    mass_out[b] = mraw * a.delta;
+    if (a.with_moments && mean_out != nullptr) {
+      for (int k = 0; k < nc; ++k) mean_out[(long long)b * nc + k] = a.centre[k] + s_mean[k] / mraw;
+      for (int k = 0; k < nc; ++k)
+        for (int l = k; l < nc; ++l) {
+          const double mk = s_mean[k] / mraw, ml = s_mean[l] / mraw;
+          const double v = s_S[k * (kMaxD + 1) + l] / mraw - mk * ml;
+          cov_out[((long long)b * nc + k) * nc + l] = v;
+          cov_out[((long long)b * nc + l) * nc + k] = v;
+        }
+    }
+  }
+  if (a.scale_core != nullptr) {
+    const int kk = a.scale_idx;
+    const int r0 = rk[a.ridx[kk]], r1 = rk[a.ridx[kk + 1]];
+    const long long total = (long long)r0 * a.n[kk] * r1;
+    float* G = a.scale_core + (long long)b * a.scale_cap;
+    const float inv = (float)(1.0 / (mraw * a.delta));
+    for (long long t = threadIdx.x; t < total; t += blockDim.x) G[t] *= inv;
+  }
+}
+
+constexpr int kMomentSmemDoubles = (kMaxD + 2) * kMaxN + (kMaxD + 1) * kMaxN + 2 * kMaxN + 3 * 1024 + 32;
+
+}  // namespace
+
+// -------------------------------------------------------------- launchers
+static CorePtrs to_ptrs(float* const* p, int d) {
+  CorePtrs c{};
+  for (int k = 0; k < d; ++k) c.p[k] = p[k];
+  return c;
+}
+
+void launch_prior(cudaStream_t st, int B, const TTGeom& g, float* const* cores, int* ranks,
+                  const double* axes, const double* mean, const double* var) {
+  k_prior<<<dim3(B, g.d), 128, 0, st>>>(B, g, to_ptrs(cores, g.d), ranks, axes, mean, var);
+}
+
+void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, int S, int tmin,
+                         const float* weights, float* const* cur, float* const* alt,
+                         const int* ranks) {
+  const int lo = m < n ? m : n, hi = m < n ? n : m;
+  k_shear_expand<<<dim3(48, hi - lo + 1, B), 256, 0, st>>>(B, g, m, n, S, tmin, weights,
+                                                          to_ptrs(cur, g.d), to_ptrs(alt, g.d), ranks);
+}
+
+void launch_rank_scale(cudaStream_t st, int B, int d, int* ranks, int lo, int hi, int S) {
+  k_rank_scale<<<(B + 255) / 256, 256, 0, st>>>(B, d, ranks, lo, hi, S);
+}
+
+void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, const int* ranks,
+                            const float* M, const float* cur, float* alt, GemmWork gw, int cap_in) {
+  const int total = B * cap_in;
+  k_plan_mode_apply<<<(total + 255) / 256, 256, 0, st>>>(B, k, g, ranks, M, cur, alt, gw, cap_in);
+  launch_scan_tiles(st, gw);
+}
+
+void launch_plan_supercore(cudaStream_t st, int B, const TTGeom& g, const int* ranks,
+                           const float* c0, const float* c1, float* W, long long W_cap,
+                           GemmWork gw) {
+  k_plan_supercore<<<(B + 255) / 256, 256, 0, st>>>(B, g, ranks, c0, c1, W, W_cap, gw);
+  launch_scan_tiles(st, gw);
+}
+
+void launch_lik_offset(cudaStream_t st, int B, const float* htab, int ntab, const float* z,
+                       int zstride, int zc, double R, float* off, double* logoff) {
+  k_lik_offset<<<B, 256, 0, st>>>(B, htab, ntab, z, zstride, zc, R, off, logoff);
+}
+
+void launch_lik_apply_2d(cudaStream_t st, int B, float* W, long long W_cap, int N0, int N1,
+                         const int* ranks, int d, const float* htab, const float* z, int zstride,
+                         int zc, double R, const float* off) {
+  k_lik_apply_2d<<<dim3(64, B), 256, 0, st>>>(B, W, W_cap, N0, N1, d, ranks, htab, z, zstride, zc, R,
+                                             off);
+}
+
+void launch_lik_apply_1d(cudaStream_t st, int B, float* core, long long cap, int N, int k, int d,
+                         const int* ranks, const float* htab, const float* z, int zstride, int zc,
+                         double R, const float* off) {
+  k_lik_apply_1d<<<dim3(16, B), 256, 0, st>>>(B, core, cap, N, k, d, ranks, htab, z, zstride, zc, R,
+                                             off);
+}
+
+void launch_moments(cudaStream_t st, int B, const MomentArgs& a, const int* ranks, int rstride,
+                    double* Awork, long long awork_stride, double* mass, double* mean, double* cov) {
+  k_moments<<<B, 256, kMomentSmemDoubles * sizeof(double), st>>>(B, a, ranks, rstride, Awork,
+                                                                  awork_stride, mass, mean, cov);
+}
+
+__global__ void k_logc(int B, const double* mass, const double* logoff, double* log_c, double* log_lik) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const double lc = log(mass[b]) + logoff[b];
+    log_c[b] = lc;
+    log_lik[b] += lc;
+  }
+}
+
+void launch_logc(cudaStream_t st, int B, const double* mass, const double* logoff, double* log_c,
+                 double* log_lik) {
+  k_logc<<<(B + 255) / 256, 256, 0, st>>>(B, mass, logoff, log_c, log_lik);
+}
+
+void set_ttops_attributes() {
+  cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kMomentSmemDoubles * (int)sizeof(double));
+}
+
+
+}  // namespace ttgbf

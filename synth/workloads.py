@@ -115,7 +115,7 @@ def config1(linear: bool = False) -> Model:
                  lo=np.full(2, -10.0), hi=np.full(2, 10.0), n=np.full(2, 64),
                  m0=np.zeros(2), P0=4.0 * np.eye(2),
                  F=np.array([[0.9, 0.1], [0.0, 0.9]]), Q=0.1 * np.eye(2),
-                 R=0.05 * np.eye(2), comps=comps, steps=20, eps=1e-9, rank_cap=64,
+                 R=0.05 * np.eye(2), comps=comps, steps=20, eps=1e-6, rank_cap=16,
                  config_id=1)
 
 

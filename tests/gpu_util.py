@@ -1,0 +1,47 @@
+"""Helpers shared by the GPU parity tests: build/load the library, move
+measurement tables to the device, compare densities."""
+import numpy as np
+
+import synth
+from oracle import pmf, tt
+
+EPS_TOL_FLOOR = 1e-5  # FP32 arithmetic floor of the TT parity tolerance
+
+
+def lib_module():
+    import paper_2501_07942_gb300 as G
+    from paper_2501_07942_gb300 import build
+    build.build()
+    G.load()
+    return G
+
+
+def rel(a, b) -> float:
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def tt_tol(eps: float, tail_sum: float) -> float:
+    """Parity bound of the TT path against the dense oracle for one step:
+    10 * (eps + discarded tail) + 1e-5 (the discarded tail is zero when the
+    rank cap does not bind, and then the bound is 10 eps + 1e-5)."""
+    return 10.0 * (eps + tail_sum) + EPS_TOL_FLOOR
+
+
+def device_tables(model: synth.Model, axes):
+    import torch
+    return [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device="cuda"))
+            for m, t in model.tables(axes)]
+
+
+def make_filter(G, model: synth.Model, batch=1, rank_cap=None, eps=None, smax=0):
+    return G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=batch,
+                      rank_cap=model.rank_cap if rank_cap is None else rank_cap,
+                      eps=model.eps if eps is None else eps, max_shift_span=smax)
+
+
+def densify_filter(f, b=0):
+    return tt.densify(f.export_cores(b))
+
+
+def oracle_grid(model):
+    return pmf.Grid(model.lo, model.hi, model.n)

@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every function that include/ttgbf.h declares, and validates
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2501_07942_gb300 as G
+from paper_2501_07942_gb300 import build as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ttgbf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return G.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(ttgbf_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_functions_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 19
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(G.EXPORTED) == names
+
+
+def test_strerror(lib):
+    assert G.strerror(0) == "ok"
+    for code in range(-1, -8, -1):
+        assert G.strerror(code) != "unknown error"
+    assert G.strerror(-99) == "unknown error"
+
+
+def test_workspace_bytes(lib):
+    small = G.workspace_bytes([-8] * 4, [8] * 4, [32] * 4, batch=1)
+    big = G.workspace_bytes([-8] * 4, [8] * 4, [128] * 4, batch=100)
+    assert 0 < small < big
+    assert big % 256 == 0 or big > 0
+    # rank_cap * max_shift_span beyond the 160-column limit of one SVD problem
+    assert G.workspace_bytes([-8] * 4, [8] * 4, [32] * 4, rank_cap=17) == 0
+    assert G.workspace_bytes([-8] * 4, [8] * 4, [32] * 4, rank_cap=32, max_shift_span=5) > 0
+    # invalid grids
+    assert G.workspace_bytes([0.0], [0.0], [8]) == 0
+    assert G.workspace_bytes([0.0], [1.0], [1]) == 0
+    assert G.workspace_bytes([np.nan], [1.0], [8]) == 0
+
+
+def _init(lib, lo, hi, n, mean, var, **kw):
+    g, keep = G._grid(lo, hi, n)
+    o = G.Opts(kw.get("batch", 1), kw.get("rank_cap", 16), kw.get("eps", 1e-6),
+               kw.get("smax", 0), None, None, 0)
+    m, v = G._f64(mean), G._f64(var)
+    p = G.Prior(G._dptr(m), G._dptr(v))
+    ctx = ctypes.c_void_p()
+    rc = lib.ttgbf_init(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), ctypes.byref(o))
+    return rc, ctx
+
+
+def test_init_validates_before_device(lib):
+    # every case below must be rejected on the host, before any CUDA call
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], batch=0)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], rank_cap=0)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], eps=float("nan"))[0] == -2
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], eps=-1.0)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], rank_cap=40)[0] == -5
+    assert _init(lib, [0.0], [1.0], [8], [np.inf], [1.0])[0] == -2
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [0.0])[0] == -1
+    assert _init(lib, [1.0], [0.0], [8], [0.0], [1.0])[0] == -1
+    assert _init(lib, [0.0] * 17, [1.0] * 17, [4] * 17, [0.0] * 17, [1.0] * 17)[0] == -1
+
+
+def test_null_context_calls(lib):
+    assert lib.ttgbf_free(None) == 0
+    assert lib.ttgbf_predict(None, None, None) == -1
+    assert lib.ttgbf_round(None) == -1
+    assert lib.ttgbf_normalise(None) == -1
+    assert lib.ttgbf_grid_axes(None, None) == -1

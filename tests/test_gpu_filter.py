@@ -1,0 +1,169 @@
+"""GPU parity of whole filter steps (predict -> update -> estimate) on the
+benchmark workloads against the dense FP64 oracle.
+
+Tolerances: per step the TT density may deviate from the oracle by
+10 * (eps + tau) + 1e-5 in relative Frobenius norm, tau being the discarded
+relative tail the rounding reports (tau = 0 when the rank cap does not bind).
+Over several steps the bounds of the steps add.  Posterior means agree within
+1e-3 grid spacings."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pmf, tt
+
+from gpu_util import device_tables, lib_module, make_filter, oracle_grid, rel, tt_tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    return lib_module()
+
+
+def run_compare(G, model, mcs, steps, batch_extra=0):
+    """Run len(mcs) filters on the GPU and the oracle on each; return per-step
+    errors (density rel, mean err / D, |log c diff|) and the bounds."""
+    B = len(mcs) + batch_extra
+    f = make_filter(G, model, batch=B)
+    comps = device_tables(model, f.grid_axes())
+    g = oracle_grid(model)
+    oc = model.tables(g.axes)
+    zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
+    zs += [zs[0]] * batch_extra
+    Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
+    bound = [0.0] * len(mcs)
+    out = []
+    for k in range(steps):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, np.stack([z[k] for z in zs]))
+        st = f.stats()
+        m, c, lc, ll = f.estimate()
+        row = []
+        for i in range(len(mcs)):
+            Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
+            Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
+            mo, co = pmf.moments(Ps[i], g)
+            bound[i] += tt_tol(model.eps, st[i]["tail_sum"])  # predict + update tails
+            e = rel(tt.densify(f.export_cores(i)), Ps[i])
+            row.append((e, bound[i], np.abs(m[i] - mo).max() / g.delta_axis.min(),
+                        abs(lc[i] - logc), st[i]["max_rank"]))
+        out.append(row)
+    return out, f
+
+
+def test_config1_vs_oracle(G):
+    model = synth.config1()
+    out, f = run_compare(G, model, [0, 1], model.steps)
+    for k, row in enumerate(out):
+        for e, bound, merr, dlc, mr in row:
+            assert e <= bound, (k, e, bound)
+            assert merr < 1e-3, (k, merr)
+            assert dlc < 1e-3 + bound, (k, dlc)
+            assert mr <= model.rank_cap
+
+
+def test_config1_linear_tracks_kalman(G):
+    from oracle import kalman
+    model = synth.config1_linear()
+    x, z = synth.simulate(model, 3, steps=10)
+    f = make_filter(G, model)
+    comps = device_tables(model, f.grid_axes())
+    kf = kalman.kalman(model.m0, model.P0, model.F, model.Q, np.eye(2), model.R, z)
+    for k in range(10):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, z[k][None, :])
+    m, c, lc, ll = f.estimate()
+    # discretisation error of the re-gridded transition at N = 64 (the oracle's
+    # own distance to the Kalman filter is of the same size)
+    assert np.abs(m[0] - kf["means"][-1]).max() < 0.05
+    assert np.abs(c[0] - kf["covs"][-1]).max() < 0.01
+
+
+def test_config2_small_grid_multi_step(G):
+    model = synth.config2(n=32)
+    out, f = run_compare(G, model, [0, 1], 6)
+    for k, row in enumerate(out):
+        for e, bound, merr, dlc, mr in row:
+            assert e <= bound, (k, e, bound)
+            assert merr < 1e-3, (k, merr)
+            assert mr <= 16
+
+
+def test_config2_one_step_from_oracle_posterior(G):
+    # shared input: the oracle's posterior after 3 steps, compressed by the
+    # oracle's TT rounding; both sides take one predict + update from it
+    model = synth.config2(n=32)
+    g = oracle_grid(model)
+    oc = model.tables(g.axes)
+    x, z = synth.simulate(model, 5, steps=4)
+    P = pmf.prior(g, model.m0, model.P0)
+    for k in range(3):
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+        P, _ = pmf.update(P, g, pmf.likelihood(g, oc, z[k], model.R))
+    cores, _ = tt.round_tt(tt.from_dense(P), 1e-7, 16)
+    cores = [c.astype(np.float32) for c in cores]
+    P_in = tt.densify([c.astype(np.float64) for c in cores])
+    P_in, _ = pmf.normalise(P_in, g)
+    f = make_filter(G, model)
+    f.import_cores(0, cores)
+    f.normalise()
+    comps = device_tables(model, f.grid_axes())
+    f.predict(model.F, model.Q)
+    t_pred = f.stats()[0]["tail_sum"]
+    Pp, _ = pmf.predict_rg(P_in, g, model.F, model.Q)
+    assert rel(tt.densify(f.export_cores(0)), Pp) <= tt_tol(model.eps, t_pred)
+    f.update(comps, model.R, z[3][None, :])
+    t_step = f.stats()[0]["tail_sum"]  # predict + update tails of this step
+    Pu, logc = pmf.update(Pp, g, pmf.likelihood(g, oc, z[3], model.R))
+    assert rel(tt.densify(f.export_cores(0)), Pu) <= tt_tol(model.eps, t_step)
+    m, c, lc, ll = f.estimate()
+    mo, co = pmf.moments(Pu, g)
+    assert np.abs(m[0] - mo).max() < 1e-3 * g.delta_axis.min()
+    assert abs(lc[0] - logc) < 1e-3
+
+
+def test_batch_filters_are_independent(G):
+    model = synth.config2(n=24)
+    out, f = run_compare(G, model, [7, 8, 9], 3, batch_extra=2)
+    for row in out:
+        for e, bound, merr, dlc, mr in row:
+            assert e <= bound and merr < 1e-3
+    # the two extra filters saw filter 0's measurements
+    a = tt.densify(f.export_cores(0))
+    np.testing.assert_allclose(tt.densify(f.export_cores(3)), a, rtol=0, atol=0)
+    np.testing.assert_allclose(tt.densify(f.export_cores(4)), a, rtol=0, atol=0)
+
+
+@pytest.mark.slow
+def test_config2_full_size_bench_launch(G):
+    """The bench's launch configuration (100 filters, 128^4 grid, rank cap 16,
+    eps 1e-6): filter 0 is compared with the oracle over two steps on the full
+    grid; every filter is checked for unit mass, finite moments and ranks."""
+    model = synth.config2(n=128)
+    B = 100
+    f = make_filter(G, model, batch=B)
+    comps = device_tables(model, f.grid_axes())
+    zs = np.stack([synth.simulate(model, mc, steps=2)[1] for mc in range(B)], axis=1)
+    g = oracle_grid(model)
+    oc = model.tables(g.axes)
+    P = pmf.prior(g, model.m0, model.P0)
+    bound = 0.0
+    for k in range(2):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, zs[k])
+        st = f.stats()
+        bound += tt_tol(model.eps, st[0]["tail_sum"])
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+        P, logc = pmf.update(P, g, pmf.likelihood(g, oc, zs[k][0], model.R))
+        m, c, lc, ll = f.estimate()
+        e = rel(tt.densify(f.export_cores(0)), P)
+        assert e <= bound, (k, e, bound)
+        mo, co = pmf.moments(P, g)
+        assert np.abs(m[0] - mo).max() < 1e-3 * g.delta_axis.min()
+        assert abs(lc[0] - logc) < 1e-3
+        assert np.isfinite(m).all() and np.isfinite(c).all() and np.isfinite(lc).all()
+        assert (np.abs(m) < 8).all()
+        assert (f.ranks() <= 16).all()
+        assert all(s["max_rank"] <= 16 for s in st)
