@@ -80,10 +80,11 @@ typedef struct {
 /* One measurement component z_c = h_c(x_m [, x_n]) + v_c that depends on one
  * mode or on two adjacent modes (Sec. 4, fourth bullet: the likelihood
  * tensor).  htab is a caller-owned DEVICE array with h_c evaluated at the grid
- * points: n[m] floats, or n[m]*n[n] floats row-major [i_m][i_n].  Two-mode
- * components need n == m + 1 and m == 0 or n == d-1 (one side of the pair
- * carries TT rank 1), and n[m] (m == 0) or n[n] (n == d-1) <= rank_cap *
- * max_shift_span. */
+ * points: n[m] floats, or n[m]*n[n] floats row-major [i_m][i_n].  A two-mode
+ * component must be on modes (0, 1) (its Hadamard product is taken on the
+ * merged first two cores, whose left TT rank is 1), at most one per update,
+ * with n[0] <= 160.  The library cannot check the size of a device array:
+ * a shorter table is read out of bounds. */
 typedef struct {
   int32_t nmodes;
   int32_t modes[2];
@@ -188,6 +189,28 @@ int ttgbf_round(ttgbf_ctx* ctx);
 
 /* Normalise every filter to unit mass (sum(P) * cell volume = 1). */
 int ttgbf_normalise(ttgbf_ctx* ctx);
+
+/* ---- profiling ------------------------------------------------------------ */
+
+/* Per kernel class: launches, device time between CUDA events recorded on the
+ * context's stream around each launch group, and the algorithmic floating-point
+ * work the kernels counted on the device (0 for classes that do not count). */
+typedef struct {
+  char name[24];
+  int64_t launches;
+  double ms;
+  double flops;
+} ttgbf_kernel_prof;
+
+/* enable != 0: reset the counters and record events from now on; 0: stop. */
+int ttgbf_profile(ttgbf_ctx* ctx, int32_t enable);
+
+/* Copy up to cap class records to out; *count receives the number of classes.
+ * Synchronises the stream. */
+int ttgbf_profile_read(ttgbf_ctx* ctx, ttgbf_kernel_prof* out, int32_t cap, int32_t* count);
+
+/* Kernel launches made by the library in this process so far. */
+uint64_t ttgbf_launch_count(void);
 
 #ifdef __cplusplus
 }

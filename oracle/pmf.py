@@ -78,6 +78,14 @@ def gaussian_on_grid(grid: Grid, mean, cov) -> np.ndarray:
     """Point evaluation of N(x; mean, cov) at every grid point."""
     mean = np.asarray(mean, dtype=np.float64)
     cov = np.asarray(cov, dtype=np.float64)
+    if np.all(cov == np.diag(np.diag(cov))):
+        # diagonal covariance: the density is the product of its 1-D marginals
+        out = np.ones(())
+        for m in range(grid.d):
+            v = cov[m, m]
+            f = np.exp(-0.5 * (grid.axes[m] - mean[m]) ** 2 / v) / math.sqrt(2 * math.pi * v)
+            out = np.multiply.outer(out, f)
+        return out
     X = grid.points() - mean
     icov = np.linalg.inv(cov)
     quad = np.einsum("pi,ij,pj->p", X, icov, X)

@@ -32,7 +32,8 @@ EXPORTED = [
     "ttgbf_workspace_bytes", "ttgbf_init", "ttgbf_predict", "ttgbf_update", "ttgbf_update_dev",
     "ttgbf_estimate", "ttgbf_estimate_dev", "ttgbf_free", "ttgbf_strerror", "ttgbf_ranks",
     "ttgbf_stats", "ttgbf_grid_axes", "ttgbf_export_cores", "ttgbf_import_cores", "ttgbf_shear",
-    "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise",
+    "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise", "ttgbf_profile",
+    "ttgbf_profile_read", "ttgbf_launch_count",
 ]
 
 
@@ -73,6 +74,11 @@ class StepStats(ctypes.Structure):
                 ("cap_hits", ctypes.c_int32)]
 
 
+class KernelProf(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -108,12 +114,21 @@ def load() -> ctypes.CDLL:
     lib.ttgbf_convolve.argtypes = [VP, dp]
     lib.ttgbf_round.argtypes = [VP]
     lib.ttgbf_normalise.argtypes = [VP]
+    lib.ttgbf_profile.argtypes = [VP, ctypes.c_int32]
+    lib.ttgbf_profile_read.argtypes = [VP, P(KernelProf), ctypes.c_int32, P(ctypes.c_int32)]
+    lib.ttgbf_launch_count.restype = ctypes.c_uint64
+    lib.ttgbf_launch_count.argtypes = []
     _lib = lib
     return lib
 
 
 def strerror(code: int) -> str:
     return load().ttgbf_strerror(int(code)).decode()
+
+
+def launch_count() -> int:
+    """Kernel launches the library made in this process (ttgbf_launch_count)."""
+    return int(load().ttgbf_launch_count())
 
 
 def _dptr(a: np.ndarray):
@@ -273,6 +288,16 @@ class TTFilter:
 
     def normalise(self):
         _check(self._lib.ttgbf_normalise(self._ctx), "ttgbf_normalise")
+
+    def profile(self, enable=True):
+        _check(self._lib.ttgbf_profile(self._ctx, int(bool(enable))), "ttgbf_profile")
+
+    def profile_read(self):
+        arr = (KernelProf * 16)()
+        cnt = ctypes.c_int32()
+        _check(self._lib.ttgbf_profile_read(self._ctx, arr, 16, ctypes.byref(cnt)), "ttgbf_profile_read")
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops}
+                for i in range(cnt.value)}
 
     def free(self):
         if getattr(self, "_ctx", None) is not None and self._ctx.value:

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -29,6 +30,12 @@ using namespace ttgbf;
 namespace {
 
 constexpr int kMaxComps = 16;
+
+enum ProfClass : int { kPTsqr = 0, kPJacobi, kPGemm, kPShear, kPMoments, kPLik, kPPlan, kPOther, kPClasses };
+const char* const kProfNames[kPClasses] = {"tsqr", "jacobi", "gemm", "shear_expand", "moments",
+                                           "likelihood", "plan", "other"};
+
+std::atomic<unsigned long long> g_launches{0};
 
 struct Arena {
   size_t off = 0;
@@ -47,7 +54,7 @@ struct Layout {
   size_t normA, tail_sum, tail_max, mass, mass_pred, log_c, log_lik, logoff, mean, cov;
   size_t cap_hits, newrank, lik_off;
   size_t tsqr_prob, tsqr_off, stack[2];
-  size_t P1, P2, gdesc, gtiles, awork, W, opmats, zbuf;
+  size_t P1, P2, gdesc, gtiles, awork, W, opmats, zbuf, prof_flops;
   size_t total;
   long long core_cap[kMaxD];
   long long stack_cap, W_cap, opmats_floats, awork_stride;
@@ -163,6 +170,7 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   L.opmats_floats = 2 * nn + (long long)d * d * (smax + 2) * nmax;
   L.opmats = a.take<float>(L.opmats_floats);
   L.zbuf = a.take<float>((size_t)B * kMaxComps);
+  L.prof_flops = a.take<double>(kPClasses);
   L.total = a.off + 256;
   return L;
 }
@@ -219,6 +227,16 @@ struct ttgbf_ctx {
   bool fuse = true;
   bool poisoned = false;
   bool expanded = false;  // ranks may exceed rank_cap (after an unrounded shear or import)
+  // Mixed canonical form: when canon is true, cores < center are left-
+  // orthonormal and cores > center right-orthonormal (the center holds the norm).
+  bool canon = false;
+  int center = 0;
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool[kPClasses];
+  size_t ev_used[kPClasses] = {};
+  long long prof_launches[kPClasses] = {};
+  double* prof_flops = nullptr;
   int sms = 148;
 };
 
@@ -238,6 +256,31 @@ int check(ttgbf_ctx* c) {
   return TTGBF_OK;
 }
 
+// Records CUDA events around a group of launches of one kernel class while
+// profiling is enabled.
+struct Prof {
+  ttgbf_ctx* c;
+  int cls;
+  Prof(ttgbf_ctx* cc, int k, int nlaunch) : c(cc), cls(k) {
+    c->prof_launches[k] += nlaunch;
+    if (c->prof) record();
+  }
+  ~Prof() {
+    if (c->prof) record();
+  }
+  void record() {
+    auto& pool = c->ev_pool[cls];
+    if (c->ev_used[cls] == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    cudaEventRecord(pool[c->ev_used[cls]++], c->st);
+  }
+};
+
+double* flops_of(ttgbf_ctx* c, int cls) { return c->prof_flops + cls; }
+
 float* curp(ttgbf_ctx* c, int k) { return c->buf[c->cur[k]][k]; }
 float* altp(ttgbf_ctx* c, int k) { return c->buf[c->cur[k] ^ 1][k]; }
 
@@ -251,12 +294,21 @@ GemmWork gemm_work(ttgbf_ctx* c, int ndesc) { return GemmWork{c->gdesc, c->gtile
 void stage(ttgbf_ctx* c, int mode, int k, int first) {
   const int B = c->B;
   const float* src = (mode == kStageSplit) ? c->W : curp(c, k);
-  launch_plan_stage(c->st, B, mode, k, c->geom, c->ranks, src, c->W, c->L.W_cap, c->n[0],
-                    c->d > 1 ? c->n[1] : 1, c->tw, c->stack[0], c->stack[1], c->L.stack_cap);
-  launch_tsqr(c->st, c->tw, B, c->L.levels, c->sms);
+  {
+    Prof p(c, kPPlan, 1);
+    launch_plan_stage(c->st, B, mode, k, c->geom, c->ranks, src, c->W, c->L.W_cap, c->n[0],
+                      c->d > 1 ? c->n[1] : 1, c->tw, c->stack[0], c->stack[1], c->L.stack_cap);
+  }
+  {
+    Prof p(c, kPTsqr, c->L.levels);
+    launch_tsqr(c->st, c->tw, B, c->L.levels, c->sms, flops_of(c, kPTsqr));
+  }
   float* core0_alt = (mode == kStageSplit) ? altp(c, 0) : nullptr;
-  launch_jacobi(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1, c->P2,
-                core0_alt, c->L.core_cap[0]);
+  {
+    Prof p(c, kPJacobi, 1);
+    launch_jacobi(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1, c->P2,
+                  core0_alt, c->L.core_cap[0], flops_of(c, kPJacobi));
+  }
   int ka, kb, ndesc = 2 * B;
   if (mode == kStageRight) {
     ka = k;
@@ -270,10 +322,16 @@ void stage(ttgbf_ctx* c, int mode, int k, int first) {
     ndesc = B;
   }
   GemmWork gw = gemm_work(c, ndesc);
-  launch_plan_gemm_stage(c->st, B, mode, k, c->geom, c->ranks, c->newrank, curp(c, ka), altp(c, ka),
-                         curp(c, kb), altp(c, kb), c->P1, c->P2, c->W, c->L.W_cap,
-                         c->d > 1 ? c->n[1] : 1, gw);
-  launch_gemm(c->st, gw, c->sms * 8);
+  {
+    Prof p(c, kPPlan, 2);
+    launch_plan_gemm_stage(c->st, B, mode, k, c->geom, c->ranks, c->newrank, curp(c, ka), altp(c, ka),
+                           curp(c, kb), altp(c, kb), c->P1, c->P2, c->W, c->L.W_cap,
+                           c->d > 1 ? c->n[1] : 1, gw);
+  }
+  {
+    Prof p(c, kPGemm, 1);
+    launch_gemm(c->st, gw, c->sms * 8, flops_of(c, kPGemm));
+  }
   c->cur[ka] ^= 1;
   c->cur[kb] ^= 1;
 }
@@ -284,6 +342,28 @@ void enqueue_round(ttgbf_ctx* c) {
   for (int k = c->d - 1; k >= 1; --k) stage(c, kStageRight, k, 0);
   for (int k = 0; k <= c->d - 2; ++k) stage(c, kStageLeft, k, k == 0);
   c->expanded = false;
+  c->canon = true;
+  c->center = c->d - 1;
+}
+
+// Bring the TT into mixed canonical form with its center inside [lo, hi]:
+// cores < lo left-orthonormal, cores > hi right-orthonormal.
+void enqueue_center_into(ttgbf_ctx* c, int lo, int hi) {
+  if (!c->canon) {
+    for (int k = c->d - 1; k >= 1; --k) stage(c, kStageRight, k, 0);
+    c->canon = true;
+    c->center = 0;
+  }
+  while (c->center > hi) {
+    stage(c, kStageRight, c->center, 0);
+    --c->center;
+  }
+  bool first = true;
+  while (c->center < lo) {
+    stage(c, kStageLeft, c->center, first);
+    first = false;
+    ++c->center;
+  }
 }
 
 MomentArgs tt_moment_args(ttgbf_ctx* c, int with_moments, int scale) {
@@ -307,17 +387,31 @@ MomentArgs tt_moment_args(ttgbf_ctx* c, int with_moments, int scale) {
   return a;
 }
 
+// Normalise to unit mass by scaling one core: the center of the canonical
+// form when there is one (scaling it keeps the other cores orthonormal).
 void enqueue_normalise(ttgbf_ctx* c, double* mass_out) {
   MomentArgs a = tt_moment_args(c, 0, 1);
+  const int k = c->canon ? c->center : c->d - 1;
+  a.scale_core = curp(c, k);
+  a.scale_cap = c->L.core_cap[k];
+  a.scale_idx = k;
+  Prof p(c, kPMoments, 1);
   launch_moments(c->st, c->B, a, c->ranks, c->d + 1, c->awork, c->L.awork_stride, mass_out, nullptr,
                  nullptr);
 }
 
 void mode_apply(ttgbf_ctx* c, int k, const float* M) {
   GemmWork gw = gemm_work(c, c->B * c->capr);
-  launch_plan_mode_apply(c->st, c->B, k, c->geom, c->ranks, M, curp(c, k), altp(c, k), gw, c->capr);
-  launch_gemm(c->st, gw, c->sms * 8);
+  {
+    Prof p(c, kPPlan, 2);
+    launch_plan_mode_apply(c->st, c->B, k, c->geom, c->ranks, M, curp(c, k), altp(c, k), gw, c->capr);
+  }
+  {
+    Prof p(c, kPGemm, 1);
+    launch_gemm(c->st, gw, c->sms * 8, flops_of(c, kPGemm));
+  }
   c->cur[k] ^= 1;
+  if (!(c->canon && c->center == k)) c->canon = false;
 }
 
 double hatf(double t) { return std::max(0.0, 1.0 - std::fabs(t)); }
@@ -478,19 +572,38 @@ int prepare_predict(ttgbf_ctx* c, const double* F, const double* Q) {
   return TTGBF_OK;
 }
 
+// Shear x_m += a x_n as a rank-S TT operator on the links between lo and hi,
+// followed (do_round) by a rounding restricted to that block: the TT is first
+// put in canonical form with its center inside [lo, hi], so the cores outside
+// the block are orthonormal and the block's truncations are the ones the full
+// TT rounding would make on these links.
 void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts, bool do_round) {
+  const int lo = std::min(m, n), hi = std::max(m, n);
+  if (do_round) enqueue_center_into(c, lo, hi);
   float* curv[kMaxD];
   float* altv[kMaxD];
   for (int k = 0; k < c->d; ++k) {
     curv[k] = curp(c, k);
     altv[k] = altp(c, k);
   }
-  launch_shear_expand(c->st, c->B, c->geom, m, n, S, tmin, wts, curv, altv, c->ranks);
-  const int lo = std::min(m, n), hi = std::max(m, n);
-  launch_rank_scale(c->st, c->B, c->d, c->ranks, lo, hi, S);
+  {
+    Prof p(c, kPShear, 1);
+    launch_shear_expand(c->st, c->B, c->geom, m, n, S, tmin, wts, curv, altv, c->ranks);
+  }
+  {
+    Prof p(c, kPOther, 1);
+    launch_rank_scale(c->st, c->B, c->d, c->ranks, lo, hi, S);
+  }
   for (int k = lo; k <= hi; ++k) c->cur[k] ^= 1;
-  c->expanded = true;
-  if (do_round) enqueue_round(c);
+  if (!do_round) {
+    c->expanded = true;
+    c->canon = false;
+    return;
+  }
+  for (int k = hi; k >= lo + 1; --k) stage(c, kStageRight, k, 0);
+  for (int k = lo; k <= hi - 1; ++k) stage(c, kStageLeft, k, k == lo);
+  c->canon = true;
+  c->center = hi;
 }
 
 int guard(ttgbf_ctx* c) {
@@ -533,21 +646,32 @@ int enqueue_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const flo
     if (cp.nmodes != 1) continue;
     const int k = cp.modes[0];
     const double r = R[(size_t)i * h->b + i];
+    Prof p(c, kPLik, 2);
     launch_lik_offset(c->st, B, cp.htab, c->n[k], z, zstride, i, r, c->lik_off, c->logoff);
     launch_lik_apply_1d(c->st, B, curp(c, k), c->L.core_cap[k], c->n[k], k, d, c->ranks, cp.htab, z,
                         zstride, i, r, c->lik_off);
+    if (!(c->canon && c->center == k)) c->canon = false;
   }
   if (two_mode >= 0) {
     const ttgbf_meas_comp& cp = h->comp[two_mode];
     const double r = R[(size_t)two_mode * h->b + two_mode];
     for (int k = d - 1; k >= 2; --k) stage(c, kStageRight, k, 0);
     GemmWork gw = gemm_work(c, B);
-    launch_plan_supercore(c->st, B, c->geom, c->ranks, curp(c, 0), curp(c, 1), c->W, c->L.W_cap, gw);
-    launch_gemm(c->st, gw, c->sms * 8);
-    launch_lik_offset(c->st, B, cp.htab, c->n[0] * c->n[1], z, zstride, two_mode, r, c->lik_off,
-                      c->logoff);
-    launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, cp.htab, z, zstride,
-                        two_mode, r, c->lik_off);
+    {
+      Prof p(c, kPPlan, 2);
+      launch_plan_supercore(c->st, B, c->geom, c->ranks, curp(c, 0), curp(c, 1), c->W, c->L.W_cap, gw);
+    }
+    {
+      Prof p(c, kPGemm, 1);
+      launch_gemm(c->st, gw, c->sms * 8, flops_of(c, kPGemm));
+    }
+    {
+      Prof p(c, kPLik, 2);
+      launch_lik_offset(c->st, B, cp.htab, c->n[0] * c->n[1], z, zstride, two_mode, r, c->lik_off,
+                        c->logoff);
+      launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, cp.htab, z, zstride,
+                          two_mode, r, c->lik_off);
+    }
     // log c before rounding: mass of the TT [W (modes 0,1 merged), core 2, ...]
     MomentArgs a{};
     a.ncores = d - 1;
@@ -562,14 +686,28 @@ int enqueue_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const flo
     }
     for (int kk = 1; kk <= d - 1; ++kk) a.ridx[kk] = kk + 1;
     a.delta = c->delta;
-    launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
-    launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+    {
+      Prof p(c, kPMoments, 1);
+      launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
+    }
+    {
+      Prof p(c, kPOther, 1);
+      launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+    }
     stage(c, kStageSplit, 0, 1);
     for (int k = 1; k <= d - 2; ++k) stage(c, kStageLeft, k, 0);
+    c->canon = true;
+    c->center = d - 1;
   } else {
     MomentArgs a = tt_moment_args(c, 0, 0);
-    launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
-    launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+    {
+      Prof p(c, kPMoments, 1);
+      launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
+    }
+    {
+      Prof p(c, kPOther, 1);
+      launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+    }
   }
   enqueue_normalise(c, c->mass);
   return check(c);
@@ -694,6 +832,7 @@ int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior
   c->W = (float*)(b + L.W);
   c->opmats = (float*)(b + L.opmats);
   c->zbuf = (float*)(b + L.zbuf);
+  c->prof_flops = (double*)(b + L.prof_flops);
   if (cudaMallocHost(&c->stage_ops, sizeof(float) * L.opmats_floats) != cudaSuccess ||
       cudaMallocHost(&c->stage_z, sizeof(float) * (size_t)c->B * kMaxComps) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_ops, cudaEventDisableTiming) != cudaSuccess ||
@@ -712,6 +851,7 @@ int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior
   cudaMemsetAsync(c->tail_max, 0, sizeof(double) * c->B, c->st);
   cudaMemsetAsync(c->cap_hits, 0, sizeof(int) * c->B, c->st);
   cudaMemsetAsync(c->mass_pred, 0, sizeof(double) * c->B, c->st);
+  cudaMemsetAsync(c->prof_flops, 0, sizeof(double) * kPClasses, c->st);
   launch_prior(c->st, c->B, c->geom, c->buf[0], c->ranks, c->axes_d, c->pmean, c->pvar);
   enqueue_normalise(c, c->mass);
   // synchronous: prior values come from host memory the caller may free
@@ -787,6 +927,7 @@ int ttgbf_update_dev(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const f
 
 static int estimate_common(ttgbf_ctx* c) {
   MomentArgs a = tt_moment_args(c, 1, 0);
+  Prof p(c, kPMoments, 1);
   launch_moments(c->st, c->B, a, c->ranks, c->d + 1, c->awork, c->L.awork_stride, c->mass, c->mean,
                  c->cov);
   return check(c);
@@ -827,6 +968,8 @@ int ttgbf_free(ttgbf_ctx* c) {
   if (c->stage_z) cudaFreeHost(c->stage_z);
   if (c->ev_ops) cudaEventDestroy(c->ev_ops);
   if (c->ev_z) cudaEventDestroy(c->ev_z);
+  for (int k = 0; k < kPClasses; ++k)
+    for (cudaEvent_t e : c->ev_pool[k]) cudaEventDestroy(e);
   cudaGetLastError();
   delete c;
   return TTGBF_OK;
@@ -921,6 +1064,7 @@ int ttgbf_import_cores(ttgbf_ctx* c, int32_t f, const float* buf, const int32_t*
   cudaMemcpy(c->ranks + (size_t)f * (d + 1), ranks, sizeof(int) * (d + 1), cudaMemcpyHostToDevice);
   cudaMemcpy(c->log_lik + f, &log_lik, sizeof(double), cudaMemcpyHostToDevice);
   if (over) c->expanded = true;
+  c->canon = false;
   return check(c);
 }
 
@@ -1006,4 +1150,49 @@ int ttgbf_normalise(ttgbf_ctx* c) {
   return check(c);
 }
 
+int ttgbf_profile(ttgbf_ctx* c, int32_t enable) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (enable) {
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+    for (int k = 0; k < kPClasses; ++k) {
+      c->ev_used[k] = 0;
+      c->prof_launches[k] = 0;
+    }
+    cudaMemsetAsync(c->prof_flops, 0, sizeof(double) * kPClasses, c->st);
+  }
+  c->prof = enable != 0;
+  return check(c);
+}
+
+int ttgbf_profile_read(ttgbf_ctx* c, ttgbf_kernel_prof* out, int32_t cap, int32_t* count) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!out || !count || cap < 0) return TTGBF_EINVAL;
+  double fl[kPClasses];
+  cudaMemcpyAsync(fl, c->prof_flops, sizeof(fl), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  *count = kPClasses;
+  for (int k = 0; k < kPClasses && k < cap; ++k) {
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < c->ev_used[k]; i += 2) {
+      float e = 0.f;
+      if (cudaEventElapsedTime(&e, c->ev_pool[k][i], c->ev_pool[k][i + 1]) == cudaSuccess) ms += e;
+    }
+    ttgbf_kernel_prof& o = out[k];
+    std::memset(&o, 0, sizeof(o));
+    std::strncpy(o.name, kProfNames[k], sizeof(o.name) - 1);
+    o.launches = c->prof_launches[k];
+    o.ms = ms;
+    o.flops = fl[k];
+  }
+  return check(c);
+}
+
+uint64_t ttgbf_launch_count(void) { return g_launches.load(); }
+
 }  // extern "C"
+
+namespace ttgbf {
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
+}  // namespace ttgbf

@@ -86,15 +86,15 @@ struct TTGeom {
 void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
                        TsqrWork w, float* stack0, float* stack1, long long stack_cap);
-void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid);
+void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid, double* flops);
 void launch_jacobi(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
-                   long long core0_cap);
+                   long long core0_cap, double* flops);
 void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
                             const int* newrank, const float* cur_a, float* alt_a,
                             const float* cur_b, float* alt_b, const float* P1, const float* P2,
                             const float* W, long long W_cap, int N1, GemmWork gw);
-void launch_gemm(cudaStream_t st, GemmWork gw, int grid);
+void launch_gemm(cudaStream_t st, GemmWork gw, int grid, double* flops);
 // Tile prefix for descriptors already written to gw.desc (ndesc entries).
 void launch_scan_tiles(cudaStream_t st, GemmWork gw);
 
@@ -138,6 +138,8 @@ struct MomentArgs {
 };
 void launch_moments(cudaStream_t st, int B, const MomentArgs& a, const int* ranks, int rstride,
                     double* Awork, long long awork_stride, double* mass, double* mean, double* cov);
+// Process-wide count of kernel launches made by the library (capi.cu).
+void count_launches(int n);
 // Function attributes (large dynamic shared memory); call once per process.
 void set_kernel_attributes();
 void set_ttops_attributes();

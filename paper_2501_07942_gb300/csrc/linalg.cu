@@ -140,7 +140,7 @@ __device__ void householder_chunk(float* sm, int rows, int n, float* out) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(512) k_tsqr_level(TsqrWork w, int B, int L) {
+__global__ void __launch_bounds__(512) k_tsqr_level(TsqrWork w, int B, int L, double* flops) {
   extern __shared__ float sm[];
   const int* off = w.offset + (long long)L * (B + 1);
   const int total = off[B];
@@ -184,6 +184,14 @@ __global__ void __launch_bounds__(512) k_tsqr_level(TsqrWork w, int B, int L) {
     }
     __syncthreads();
     householder_chunk(sm, rows, n, out);
+    if (threadIdx.x == 0 && flops != nullptr) {
+      // Householder R factor: per column j a norm (2 (rows-j)) and a rank-1
+      // update of the n-j-1 trailing columns (4 (rows-j) each)
+      double f = 0.0;
+      const int kmax = rows < n ? rows : n;
+      for (int j = 0; j < kmax; ++j) f += (double)(rows - j) * (2.0 + 4.0 * (n - j - 1));
+      atomicAdd(flops, f);
+    }
   }
 }
 
@@ -202,9 +210,9 @@ __device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int*
 
 // One-sided (Hestenes) Jacobi SVD of the n x n R factor of problem b, then the
 // stage's rank choice and factor output.  One CTA per filter.
-__global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int rank_cap, double eps,
+__global__ void __launch_bounds__(1024) k_jacobi(TsqrWork w, int B, int mode, int rank_cap, double eps,
                                                 int d, int first, RoundState rs, float* P1, float* P2,
-                                                float* core0_out, long long core0_cap) {
+                                                float* core0_out, long long core0_cap, double* flops) {
   extern __shared__ float sm[];
   const int b = blockIdx.x;
   if (b >= B) return;
@@ -218,6 +226,8 @@ __global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int
   int* perm = (int*)(sig + kMaxN);            // [kMaxN]
   __shared__ int s_rot;
   __shared__ int s_rank;
+  __shared__ double s_flops;
+  if (threadIdx.x == 0) s_flops = 0.0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, c = t - i * n;
@@ -227,6 +237,7 @@ __global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int
   __syncthreads();
   const int npad = (n + 1) & ~1;
   const float tol = 5e-7f * sqrtf((float)n);
+  __shared__ float s_floor;
   for (int sweep = 0; sweep < 40 && npad >= 2; ++sweep) {
     for (int c = warp; c < n; c += nwarps) {
       float s = 0.f;
@@ -236,6 +247,16 @@ __global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int
     }
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
+    if (threadIdx.x == 0) {
+      // columns below 1e-7 ||R||_F are rounding noise: rotating them against
+      // each other never converges and changes the matrix by less than fp32
+      // resolution, so they are left alone
+      float tot = 0.f;
+      for (int c = 0; c < n; ++c) tot += nrm[c];
+      s_floor = 1e-14f * tot;
+    }
+    __syncthreads();
+    const float floor2 = s_floor;
     for (int r = 0; r < npad - 1; ++r) {
       for (int k = warp; k < npad / 2; k += nwarps) {
         int pp, qq;
@@ -247,7 +268,7 @@ __global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int
         for (int i = lane; i < n; i += 32) g += ap[i] * aq[i];
         g = warp_sum(g);
         const float al = nrm[pp], be = nrm[qq];
-        if (g == 0.f || !(fabsf(g) > tol * sqrtf(al * be))) continue;
+        if (g == 0.f || fminf(al, be) <= floor2 || !(fabsf(g) > tol * sqrtf(al * be))) continue;
         const float zeta = (be - al) / (2.f * g);
         const float az = fabsf(zeta);
         const float t = (az > 1e15f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta))) *
@@ -275,9 +296,15 @@ __global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int
       }
       __syncthreads();
     }
+    if (threadIdx.x == 0) {
+      // pair dot products 2n each, rotations 12n (A and V), norm refresh 2n^2
+      const double nn = (double)n;
+      s_flops += 0.5 * nn * (nn - 1.0) * 2.0 * nn + (double)s_rot * 12.0 * nn + 2.0 * nn * nn;
+    }
     if (s_rot == 0) break;
     __syncthreads();
   }
+  if (threadIdx.x == 0 && flops != nullptr) atomicAdd(flops, s_flops + 2.0 * (double)n * n);
   // exact column norms, then sort descending
   for (int c = warp; c < n; c += nwarps) {
     double s = 0.0;
@@ -362,7 +389,7 @@ __global__ void __launch_bounds__(512) k_jacobi(TsqrWork w, int B, int mode, int
 }
 
 // ------------------------------------------------------------------ GEMM
-__global__ void __launch_bounds__(256) k_gemm_grouped(GemmWork w) {
+__global__ void __launch_bounds__(256) k_gemm_grouped(GemmWork w, double* flops) {
   __shared__ float As[16][kTile + 4];
   __shared__ float Bs[16][kTile + 4];
   const int total = w.tiles[w.ndesc];
@@ -408,6 +435,10 @@ __global__ void __launch_bounds__(256) k_gemm_grouped(GemmWork w) {
           for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
       }
       __syncthreads();
+    }
+    if (threadIdx.x == 0 && flops != nullptr) {
+      const int tm_rows = min(kTile, g.m - row0), tn_cols = min(kTile, g.n - col0);
+      atomicAdd(flops, 2.0 * tm_rows * tn_cols * (double)g.k);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -542,36 +573,44 @@ __global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, 
 void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
                        TsqrWork w, float* stack0, float* stack1, long long stack_cap) {
+  count_launches(1);
   k_plan_stage<<<1, 1024, 0, st>>>(w, B, mode, k, g, ranks, core_k, W, W_cap, N0, N1, stack0, stack1,
                                    stack_cap);
 }
 
-void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid) {
+void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid, double* flops) {
+  count_launches(levels);
   for (int L = 0; L < levels; ++L)
-    k_tsqr_level<<<grid, 512, kSmemFloats * sizeof(float), st>>>(w, B, L);
+    k_tsqr_level<<<grid, 512, kSmemFloats * sizeof(float), st>>>(w, B, L, flops);
 }
 
 void launch_jacobi(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
-                   long long core0_cap) {
-  k_jacobi<<<B, 512, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs,
-                                                                P1, P2, core0_out, core0_cap);
+                   long long core0_cap, double* flops) {
+  count_launches(1);
+  k_jacobi<<<B, 1024, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs,
+                                                                P1, P2, core0_out, core0_cap, flops);
 }
 
 void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
                             const int* newrank, const float* cur_a, float* alt_a,
                             const float* cur_b, float* alt_b, const float* P1, const float* P2,
                             const float* W, long long W_cap, int N1, GemmWork gw) {
+  count_launches(2);
   k_plan_gemm_stage<<<1, 1024, 0, st>>>(B, mode, k, g, ranks, newrank, cur_a, alt_a, cur_b, alt_b, P1,
                                         P2, W, W_cap, N1, gw);
   k_scan_tiles<<<1, 1024, 0, st>>>(gw);
 }
 
-void launch_gemm(cudaStream_t st, GemmWork gw, int grid) {
-  k_gemm_grouped<<<grid, 256, 0, st>>>(gw);
+void launch_gemm(cudaStream_t st, GemmWork gw, int grid, double* flops) {
+  count_launches(1);
+  k_gemm_grouped<<<grid, 256, 0, st>>>(gw, flops);
 }
 
-void launch_scan_tiles(cudaStream_t st, GemmWork gw) { k_scan_tiles<<<1, 1024, 0, st>>>(gw); }
+void launch_scan_tiles(cudaStream_t st, GemmWork gw) {
+  count_launches(1);
+  k_scan_tiles<<<1, 1024, 0, st>>>(gw);
+}
 
 void set_kernel_attributes() {
   cudaFuncSetAttribute(k_tsqr_level, cudaFuncAttributeMaxDynamicSharedMemorySize,

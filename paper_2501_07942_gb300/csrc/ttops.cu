@@ -376,23 +376,27 @@ static CorePtrs to_ptrs(float* const* p, int d) {
 
 void launch_prior(cudaStream_t st, int B, const TTGeom& g, float* const* cores, int* ranks,
                   const double* axes, const double* mean, const double* var) {
+  count_launches(1);
   k_prior<<<dim3(B, g.d), 128, 0, st>>>(B, g, to_ptrs(cores, g.d), ranks, axes, mean, var);
 }
 
 void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, int S, int tmin,
                          const float* weights, float* const* cur, float* const* alt,
                          const int* ranks) {
+  count_launches(1);
   const int lo = m < n ? m : n, hi = m < n ? n : m;
   k_shear_expand<<<dim3(48, hi - lo + 1, B), 256, 0, st>>>(B, g, m, n, S, tmin, weights,
                                                           to_ptrs(cur, g.d), to_ptrs(alt, g.d), ranks);
 }
 
 void launch_rank_scale(cudaStream_t st, int B, int d, int* ranks, int lo, int hi, int S) {
+  count_launches(1);
   k_rank_scale<<<(B + 255) / 256, 256, 0, st>>>(B, d, ranks, lo, hi, S);
 }
 
 void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, const int* ranks,
                             const float* M, const float* cur, float* alt, GemmWork gw, int cap_in) {
+  count_launches(1);
   const int total = B * cap_in;
   k_plan_mode_apply<<<(total + 255) / 256, 256, 0, st>>>(B, k, g, ranks, M, cur, alt, gw, cap_in);
   launch_scan_tiles(st, gw);
@@ -401,18 +405,21 @@ void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, cons
 void launch_plan_supercore(cudaStream_t st, int B, const TTGeom& g, const int* ranks,
                            const float* c0, const float* c1, float* W, long long W_cap,
                            GemmWork gw) {
+  count_launches(1);
   k_plan_supercore<<<(B + 255) / 256, 256, 0, st>>>(B, g, ranks, c0, c1, W, W_cap, gw);
   launch_scan_tiles(st, gw);
 }
 
 void launch_lik_offset(cudaStream_t st, int B, const float* htab, int ntab, const float* z,
                        int zstride, int zc, double R, float* off, double* logoff) {
+  count_launches(1);
   k_lik_offset<<<B, 256, 0, st>>>(B, htab, ntab, z, zstride, zc, R, off, logoff);
 }
 
 void launch_lik_apply_2d(cudaStream_t st, int B, float* W, long long W_cap, int N0, int N1,
                          const int* ranks, int d, const float* htab, const float* z, int zstride,
                          int zc, double R, const float* off) {
+  count_launches(1);
   k_lik_apply_2d<<<dim3(64, B), 256, 0, st>>>(B, W, W_cap, N0, N1, d, ranks, htab, z, zstride, zc, R,
                                              off);
 }
@@ -420,12 +427,14 @@ void launch_lik_apply_2d(cudaStream_t st, int B, float* W, long long W_cap, int 
 void launch_lik_apply_1d(cudaStream_t st, int B, float* core, long long cap, int N, int k, int d,
                          const int* ranks, const float* htab, const float* z, int zstride, int zc,
                          double R, const float* off) {
+  count_launches(1);
   k_lik_apply_1d<<<dim3(16, B), 256, 0, st>>>(B, core, cap, N, k, d, ranks, htab, z, zstride, zc, R,
                                              off);
 }
 
 void launch_moments(cudaStream_t st, int B, const MomentArgs& a, const int* ranks, int rstride,
                     double* Awork, long long awork_stride, double* mass, double* mean, double* cov) {
+  count_launches(1);
   k_moments<<<B, 256, kMomentSmemDoubles * sizeof(double), st>>>(B, a, ranks, rstride, Awork,
                                                                   awork_stride, mass, mean, cov);
 }
@@ -440,6 +449,7 @@ __global__ void k_logc(int B, const double* mass, const double* logoff, double* 
 
 void launch_logc(cudaStream_t st, int B, const double* mass, const double* logoff, double* log_c,
                  double* log_lik) {
+  count_launches(1);
   k_logc<<<(B + 255) / 256, 256, 0, st>>>(B, mass, logoff, log_c, log_lik);
 }
 
