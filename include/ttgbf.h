@@ -212,6 +212,42 @@ int ttgbf_profile_read(ttgbf_ctx* ctx, ttgbf_kernel_prof* out, int32_t cap, int3
 /* Kernel launches made by the library in this process so far. */
 uint64_t ttgbf_launch_count(void);
 
+/* ---- allocation-free moments ---------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc (code recorded into a CUDA graph by a framework
+ * that forbids allocation while capturing, serving loops with a fixed memory
+ * budget, plugins living inside another framework's memory pool).
+ *
+ * Mass, mean and covariance of `batch` TT densities already in device memory,
+ * computed exactly like ttgbf_estimate but without a context: no memory is
+ * allocated.  Its float64 scratch is one static device array of
+ * TTGBF_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
+ * the process exits.
+ *   grid        host; the cell-centred grid the cores live on
+ *   cores       host array of d DEVICE pointers; core k of filter b is at
+ *               cores[k] + b * core_stride[k], row-major [r_k][n_k][r_{k+1}]
+ *   core_stride host array of d element strides between filters
+ *   ranks       DEVICE int32 [batch][d+1] with r_0 = r_d = 1
+ *   rank_max    bound on every rank, 1..TTGBF_NOALLOC_MAX_RANK; a filter whose
+ *               ranks break it gets NaN outputs
+ *   mass, mean, cov   DEVICE float64 outputs [batch], [batch][d], [batch][d][d]
+ *   stream      cudaStream_t or NULL
+ * Returns TTGBF_ECAPACITY when batch * d * 3 * rank_max^2 doubles exceed the
+ * scratch array (or rank_max > TTGBF_NOALLOC_MAX_RANK), TTGBF_EINVAL /
+ * TTGBF_ENONFINITE on bad arguments, TTGBF_ECUDA if the launch fails.
+ * The first call on a device (with that device current) looks the array's
+ * device address up with cudaGetSymbolAddress; make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU (different streams, no ordering) race.  Nothing in the array needs to
+ * start at zero: every entry a call reads, that call has written first.
+ * Asynchronous on `stream`. */
+#define TTGBF_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define TTGBF_NOALLOC_MAX_RANK 64
+int ttgbf_moments_noalloc(int32_t batch, const ttgbf_grid* grid, const float* const* cores,
+                          const int64_t* core_stride, const int32_t* ranks, int32_t rank_max,
+                          double* mass, double* mean, double* cov, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

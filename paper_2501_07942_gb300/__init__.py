@@ -33,7 +33,7 @@ EXPORTED = [
     "ttgbf_estimate", "ttgbf_estimate_dev", "ttgbf_free", "ttgbf_strerror", "ttgbf_ranks",
     "ttgbf_stats", "ttgbf_grid_axes", "ttgbf_export_cores", "ttgbf_import_cores", "ttgbf_shear",
     "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise", "ttgbf_profile",
-    "ttgbf_profile_read", "ttgbf_launch_count",
+    "ttgbf_profile_read", "ttgbf_launch_count", "ttgbf_moments_noalloc",
 ]
 
 
