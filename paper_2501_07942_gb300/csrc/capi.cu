@@ -18,6 +18,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -237,6 +238,7 @@ struct ttgbf_ctx {
   size_t ev_used[kPClasses] = {};
   long long prof_launches[kPClasses] = {};
   double* prof_flops = nullptr;
+  bool debug_stages = false;
   int sms = 148;
 };
 
@@ -290,6 +292,29 @@ RoundState round_state(ttgbf_ctx* c) {
 
 GemmWork gemm_work(ttgbf_ctx* c, int ndesc) { return GemmWork{c->gdesc, c->gtiles, ndesc}; }
 
+// Diagnostic (environment TTGBF_DEBUG_STAGES=1): after each rounding stage,
+// synchronise and report filter 0's ranks and whether the two cores the
+// stage wrote are finite.  Off by default; it serialises the step.
+void debug_stage_report(ttgbf_ctx* c, int mode, int k, int ka, int kb) {
+  std::vector<int> rk(c->d + 1);
+  cudaStreamSynchronize(c->st);
+  cudaMemcpy(rk.data(), c->ranks, sizeof(int) * (c->d + 1), cudaMemcpyDeviceToHost);
+  bool fin = true;
+  float amax = 0.f;
+  for (int kk : {ka, kb}) {
+    const size_t cnt = (size_t)rk[kk] * c->n[kk] * rk[kk + 1];
+    std::vector<float> h(cnt);
+    cudaMemcpy(h.data(), curp(c, kk), sizeof(float) * cnt, cudaMemcpyDeviceToHost);
+    for (float v : h) {
+      if (!std::isfinite(v)) fin = false;
+      else amax = std::max(amax, std::fabs(v));
+    }
+  }
+  std::fprintf(stderr, "[ttgbf stage] mode=%d k=%d ranks=", mode, k);
+  for (int v : rk) std::fprintf(stderr, "%d ", v);
+  std::fprintf(stderr, "finite=%d absmax=%.3e\n", (int)fin, amax);
+}
+
 // One stage of the rounding sweep: R factor, SVD, rank choice, factor application.
 void stage(ttgbf_ctx* c, int mode, int k, int first) {
   const int B = c->B;
@@ -334,6 +359,7 @@ void stage(ttgbf_ctx* c, int mode, int k, int first) {
   }
   c->cur[ka] ^= 1;
   c->cur[kb] ^= 1;
+  if (c->debug_stages) debug_stage_report(c, mode, k, ka, kb);
 }
 
 // TT rounding: right-to-left orthogonalisation, left-to-right truncation.
@@ -763,6 +789,10 @@ int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior
   c->capr = c->rank_cap * c->smax;
   c->eps = opts->eps;
   c->st = (cudaStream_t)opts->stream;
+  {
+    const char* dbg = std::getenv("TTGBF_DEBUG_STAGES");
+    c->debug_stages = dbg != nullptr && dbg[0] == '1';
+  }
   c->n.assign(grid->n, grid->n + d);
   c->lo.assign(grid->lo, grid->lo + d);
   c->hi.assign(grid->hi, grid->hi + d);

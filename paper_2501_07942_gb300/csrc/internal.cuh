@@ -21,7 +21,7 @@ namespace ttgbf {
 
 constexpr int kSmemFloats = 51200;  // 200 KiB dynamic shared memory per TSQR CTA
 constexpr int kMaxN = 160;          // largest column count of a TSQR / SVD problem
-constexpr int kJacobiSmemFloats = 2 * kMaxN * kMaxN + 4 * kMaxN;
+constexpr int kJacobiSmemFloats = 2 * kMaxN * kMaxN + 8 * kMaxN;  // SVD kernel
 constexpr int kMaxLevels = 20;      // TSQR reduction levels
 constexpr int kMaxD = 16;           // largest state dimension
 constexpr int kTile = 64;           // GEMM tile edge

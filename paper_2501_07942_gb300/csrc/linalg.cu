@@ -5,7 +5,8 @@
 // or one link of the left-to-right truncation sweep) is:
 //   plan    -> per filter, the tall matrix whose R factor is needed
 //   TSQR    -> R (n x n) by a tree of in-shared-memory Householder QRs
-//   Jacobi  -> R = U S V^T, rank choice, small factors P1, P2
+//   SVD     -> R = U S V^T (pivoted QR, then one-sided Jacobi on the
+//              numerically significant rows), rank choice, factors P1, P2
 //   plan2   -> GEMM descriptors for "new core = unfolding * P" and
 //              "neighbour core = P * neighbour"
 //   GEMM    -> grouped SIMT FP32 GEMM over all filters
@@ -16,6 +17,10 @@
 
 namespace ttgbf {
 namespace {
+
+// Smallest magnitude treated as non-zero by the factorisations (above the
+// FP32 denormal range, so that 1/x cannot overflow).
+constexpr float kTiny = 1e-30f;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -89,8 +94,10 @@ __device__ void householder_chunk(float* sm, int rows, int n, float* out) {
       for (int i = j + 1 + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(colj[i]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      // entries below kTiny (FP32 denormals) count as zero: dividing by them
+      // would overflow
       float s = 0.f;
-      if (mx > 0.f) {
+      if (mx >= kTiny) {
         const float inv = 1.f / mx;
         for (int i = j + 1 + lane; i < rows; i += 32) {
           const float x = colj[i] * inv;
@@ -99,7 +106,7 @@ __device__ void householder_chunk(float* sm, int rows, int n, float* out) {
       }
       s = warp_sum(s);
       const float alpha = colj[j];
-      const float tail = mx * sqrtf(s);  // ||x_{j+1:}||
+      const float tail = mx >= kTiny ? mx * sqrtf(s) : 0.f;  // ||x_{j+1:}||
       float tau = 0.f, beta = alpha, scl = 0.f;
       if (tail > 0.f) {
         const float big = fmaxf(fabsf(alpha), tail);
@@ -208,62 +215,230 @@ __device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int*
   }
 }
 
-// One-sided (Hestenes) Jacobi SVD of the n x n R factor of problem b, then the
-// stage's rank choice and factor output.  One CTA per filter.
-__global__ void __launch_bounds__(1024) k_jacobi(TsqrWork w, int B, int mode, int rank_cap, double eps,
-                                                int d, int first, RoundState rs, float* P1, float* P2,
-                                                float* core0_out, long long core0_cap, double* flops) {
+// Block reductions for the SVD kernel (blockDim a multiple of 32, <= 1024).
+__device__ double block_sum_d(double v, double* red) {
+  v = warp_sum_d(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// SVD of the n x n R factor of problem b, in three steps:
+//  1. Householder QR with column pivoting, R P = Q' R', stopped once the
+//     columns left over have Frobenius norm below the stage's drop level (or
+//     after rank_cap + 16 steps when truncating); their norm is added to the
+//     discarded tail.  Pivoting also preconditions step 2.
+//  2. One-sided Jacobi on the k' x n leading rows of R' (their transposes as
+//     k' columns of length n): only k' - 1 rounds per sweep.
+//  3. The right singular vectors (normalised columns, in the order of
+//     decreasing singular value) are re-orthonormalised by classical
+//     Gram-Schmidt applied twice and un-permuted, so that the factor pair the
+//     stage applies (V S^-1 with S V^T, or S^-1 V^T with V S) multiplies to an
+//     exact projector.
+// Then the stage's rank choice and factor output.  One CTA per filter.
+__global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int rank_cap, double eps,
+                                             int d, int first, RoundState rs, float* P1, float* P2,
+                                             float* core0_out, long long core0_cap, double* flops) {
   extern __shared__ float sm[];
   const int b = blockIdx.x;
   if (b >= B) return;
   const TsqrProblem p = w.prob[b];
   const int n = p.src.n;
   const float* R = ((p.nlev - 1) & 1) ? p.stack1 : p.stack0;
-  float* A = sm;                              // column-major n x n: A[c * n + i]
-  float* V = sm + kMaxN * kMaxN;              // column-major n x n
-  float* nrm = sm + 2 * kMaxN * kMaxN;        // [kMaxN]
-  float* sig = nrm + kMaxN;                   // [kMaxN] sorted singular values
-  int* perm = (int*)(sig + kMaxN);            // [kMaxN]
-  __shared__ int s_rot;
-  __shared__ int s_rank;
+  float* A = sm;                        // QRCP work, column-major n x n (ld n); later Q of step 3
+  float* M = sm + kMaxN * kMaxN;        // Jacobi matrix, column-major n x k' (ld n)
+  float* nrm = M + kMaxN * kMaxN;       // [kMaxN] squared column norms
+  float* sig = nrm + kMaxN;             // [kMaxN] sorted singular values
+  float* rdiag = sig + kMaxN;           // [kMaxN] diagonal of R'
+  float* coef = rdiag + kMaxN;          // [kMaxN] Gram-Schmidt coefficients
+  int* perm = (int*)(coef + kMaxN);     // [kMaxN] column permutation of the QRCP
+  int* pinv = perm + kMaxN;             // [kMaxN] its inverse
+  int* ord = pinv + kMaxN;              // [kMaxN] Jacobi columns by decreasing norm
+  __shared__ double s_red[32];
+  __shared__ float s_redf[32];
+  __shared__ int s_redi[32];
+  __shared__ float s_tau;
+  __shared__ int s_piv, s_rot, s_rank, s_stop;
   __shared__ double s_flops;
-  if (threadIdx.x == 0) s_flops = 0.0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+
+  for (int t = tid; t < n * n; t += blockDim.x) {
     const int i = t / n, c = t - i * n;
     A[c * n + i] = R[t];
-    V[c * n + i] = (i == c) ? 1.f : 0.f;
+  }
+  for (int c = tid; c < n; c += blockDim.x) perm[c] = c;
+  if (tid == 0) s_flops = 0.0;
+  __syncthreads();
+  for (int c = warp; c < n; c += nwarps) {
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += (double)A[c * n + i] * (double)A[c * n + i];
+    s = warp_sum_d(s);
+    if (lane == 0) nrm[c] = (float)s;
   }
   __syncthreads();
-  const int npad = (n + 1) & ~1;
+  double tot = 0.0;
+  {
+    double s = 0.0;
+    for (int c = tid; c < n; c += blockDim.x) s += (double)nrm[c];
+    tot = block_sum_d(s, s_red);
+  }
+  double normA = 0.0;
+  if (mode != kStageRight) normA = first ? sqrt(tot) : rs.normA[b];
+  const double delta = (mode == kStageRight || d <= 1) ? 0.0 : eps * normA / sqrt((double)(d - 1));
+  // orthogonalisation drops what is left once it is at the FP32 noise level of
+  // R (1e-7 sqrt(n) ||R||_F); truncation stops once the rest is below 0.3 delta
+  const double stop2 = (mode == kStageRight) ? 1e-14 * n * tot : 0.09 * delta * delta;
+  const int kcap = (mode == kStageRight) ? n : min(n, rank_cap + 16);
+
+  // ---- 1. QR with column pivoting
+  int k = 0;
+  for (; k < kcap; ++k) {
+    double rem = 0.0;
+    float best = -1.f;
+    int bi = n;
+    for (int c = k + tid; c < n; c += blockDim.x) {
+      const float v = nrm[c];
+      rem += (double)v;
+      if (v > best || (v == best && c < bi)) {
+        best = v;
+        bi = c;
+      }
+    }
+    rem = block_sum_d(rem, s_red);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_redf[warp] = best;
+      s_redi[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float bv = s_redf[0];
+      int bx = s_redi[0];
+      for (int q = 1; q < nwarps; ++q)
+        if (s_redf[q] > bv || (s_redf[q] == bv && s_redi[q] < bx)) {
+          bv = s_redf[q];
+          bx = s_redi[q];
+        }
+      s_piv = bx;
+      s_stop = (k > 0 && rem <= stop2) || bx >= n;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int pv = s_piv;
+    if (pv != k) {
+      for (int i = tid; i < n; i += blockDim.x) {
+        const float x = A[k * n + i];
+        A[k * n + i] = A[pv * n + i];
+        A[pv * n + i] = x;
+      }
+      if (tid == 0) {
+        const int tp = perm[k];
+        perm[k] = perm[pv];
+        perm[pv] = tp;
+        const float tn = nrm[k];
+        nrm[k] = nrm[pv];
+        nrm[pv] = tn;
+      }
+    }
+    __syncthreads();
+    float* colk = A + k * n;
+    if (warp == 0) {
+      float mx = 0.f;
+      for (int i = k + 1 + lane; i < n; i += 32) mx = fmaxf(mx, fabsf(colk[i]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      float sq = 0.f;
+      if (mx >= kTiny) {
+        const float inv = 1.f / mx;
+        for (int i = k + 1 + lane; i < n; i += 32) {
+          const float x = colk[i] * inv;
+          sq += x * x;
+        }
+      }
+      sq = warp_sum(sq);
+      const float alpha = colk[k];
+      const float tail = mx >= kTiny ? mx * sqrtf(sq) : 0.f;
+      float tau = 0.f, beta = alpha, scl = 0.f;
+      if (tail > 0.f) {
+        const float big = fmaxf(fabsf(alpha), tail);
+        const float ra = alpha / big, rt = tail / big;
+        const float nm = big * sqrtf(ra * ra + rt * rt);
+        beta = alpha >= 0.f ? -nm : nm;
+        tau = (beta - alpha) / beta;
+        scl = 1.f / (alpha - beta);
+      }
+      if (tau != 0.f)
+        for (int i = k + 1 + lane; i < n; i += 32) colk[i] *= scl;
+      __syncwarp();
+      if (lane == 0) {
+        s_tau = tau;
+        rdiag[k] = beta;
+        colk[k] = 1.f;
+      }
+    }
+    __syncthreads();
+    const float tau = s_tau;
+    for (int c = k + 1 + warp; c < n; c += nwarps) {
+      float* colc = A + c * n;
+      if (tau != 0.f) {
+        float dot = 0.f;
+        for (int i = k + lane; i < n; i += 32) dot += colk[i] * colc[i];
+        dot = warp_sum(dot) * tau;
+        for (int i = k + lane; i < n; i += 32) colc[i] -= dot * colk[i];
+      }
+      float sq = 0.f;
+      for (int i = k + 1 + lane; i < n; i += 32) sq += colc[i] * colc[i];
+      sq = warp_sum(sq);
+      if (lane == 0) nrm[c] = sq;
+    }
+    __syncthreads();
+  }
+  const int kp = k;  // >= 1
+  double dropped2 = 0.0;
+  {
+    double s = 0.0;
+    for (int c = kp + tid; c < n; c += blockDim.x) s += (double)nrm[c];
+    dropped2 = block_sum_d(s, s_red);
+  }
+  // ---- 2. Jacobi on the k' leading rows of R' as columns of length n
+  for (int t = tid; t < kp * n; t += blockDim.x) {
+    const int r = t / n, c = t - r * n;
+    M[r * n + c] = (c < r) ? 0.f : (c == r ? rdiag[r] : A[c * n + r]);
+  }
+  for (int c = tid; c < n; c += blockDim.x) pinv[perm[c]] = c;
+  __syncthreads();
+  const int npad = (kp + 1) & ~1;
   const float tol = 5e-7f * sqrtf((float)n);
-  __shared__ float s_floor;
   for (int sweep = 0; sweep < 40 && npad >= 2; ++sweep) {
-    for (int c = warp; c < n; c += nwarps) {
+    for (int c = warp; c < kp; c += nwarps) {
       float s = 0.f;
-      for (int i = lane; i < n; i += 32) s += A[c * n + i] * A[c * n + i];
+      for (int i = lane; i < n; i += 32) s += M[c * n + i] * M[c * n + i];
       s = warp_sum(s);
       if (lane == 0) nrm[c] = s;
     }
-    if (threadIdx.x == 0) s_rot = 0;
+    if (tid == 0) s_rot = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      // columns below 1e-7 ||R||_F are rounding noise: rotating them against
-      // each other never converges and changes the matrix by less than fp32
-      // resolution, so they are left alone
-      float tot = 0.f;
-      for (int c = 0; c < n; ++c) tot += nrm[c];
-      s_floor = 1e-14f * tot;
-    }
-    __syncthreads();
-    const float floor2 = s_floor;
+    float tnorm = 0.f;
+    for (int c = 0; c < kp; ++c) tnorm += nrm[c];
+    const float floor2 = 1e-14f * tnorm;
     for (int r = 0; r < npad - 1; ++r) {
-      for (int k = warp; k < npad / 2; k += nwarps) {
+      for (int q = warp; q < npad / 2; q += nwarps) {
         int pp, qq;
-        jacobi_pair(k, r, npad, &pp, &qq);
-        if (pp >= n || qq >= n) continue;
-        float* ap = A + pp * n;
-        float* aq = A + qq * n;
+        jacobi_pair(q, r, npad, &pp, &qq);
+        if (pp >= kp || qq >= kp) continue;
+        float* ap = M + pp * n;
+        float* aq = M + qq * n;
         float g = 0.f;
         for (int i = lane; i < n; i += 32) g += ap[i] * aq[i];
         g = warp_sum(g);
@@ -271,93 +446,112 @@ __global__ void __launch_bounds__(1024) k_jacobi(TsqrWork w, int B, int mode, in
         if (g == 0.f || fminf(al, be) <= floor2 || !(fabsf(g) > tol * sqrtf(al * be))) continue;
         const float zeta = (be - al) / (2.f * g);
         const float az = fabsf(zeta);
-        const float t = (az > 1e15f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta))) *
-                        (zeta >= 0.f ? 1.f : -1.f);
-        const float cth = rsqrtf(1.f + t * t);
-        const float sth = cth * t;
+        const float tt = (az > 1e15f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta))) *
+                         (zeta >= 0.f ? 1.f : -1.f);
+        const float cth = rsqrtf(1.f + tt * tt);
+        const float sth = cth * tt;
         for (int i = lane; i < n; i += 32) {
           const float x = ap[i], y = aq[i];
           ap[i] = cth * x - sth * y;
           aq[i] = sth * x + cth * y;
         }
-        float* vp = V + pp * n;
-        float* vq = V + qq * n;
-        for (int i = lane; i < n; i += 32) {
-          const float x = vp[i], y = vq[i];
-          vp[i] = cth * x - sth * y;
-          vq[i] = sth * x + cth * y;
-        }
         __syncwarp();
         if (lane == 0) {
-          nrm[pp] = al - t * g;
-          nrm[qq] = be + t * g;
+          nrm[pp] = al - tt * g;
+          nrm[qq] = be + tt * g;
           atomicAdd(&s_rot, 1);
         }
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      // pair dot products 2n each, rotations 12n (A and V), norm refresh 2n^2
+    if (tid == 0) {
       const double nn = (double)n;
-      s_flops += 0.5 * nn * (nn - 1.0) * 2.0 * nn + (double)s_rot * 12.0 * nn + 2.0 * nn * nn;
+      s_flops += 0.5 * kp * (kp - 1.0) * 2.0 * nn + (double)s_rot * 6.0 * nn + 2.0 * nn * kp;
     }
-    if (s_rot == 0) break;
+    const int rot = s_rot;
     __syncthreads();
+    if (rot == 0) break;
   }
-  if (threadIdx.x == 0 && flops != nullptr) atomicAdd(flops, s_flops + 2.0 * (double)n * n);
-  // exact column norms, then sort descending
-  for (int c = warp; c < n; c += nwarps) {
+  // singular values and their order
+  for (int c = warp; c < kp; c += nwarps) {
     double s = 0.0;
-    for (int i = lane; i < n; i += 32) s += (double)A[c * n + i] * (double)A[c * n + i];
+    for (int i = lane; i < n; i += 32) s += (double)M[c * n + i] * (double)M[c * n + i];
     s = warp_sum_d(s);
     if (lane == 0) nrm[c] = (float)sqrt(s);
   }
   __syncthreads();
-  // non-finite norms (only from non-finite input) sort last as zeros, so every
-  // position 0..n-1 receives exactly one column
-  for (int c = threadIdx.x; c < n; c += blockDim.x)
+  for (int c = tid; c < kp; c += blockDim.x)
     if (!(nrm[c] >= 0.f) || isinf(nrm[c])) nrm[c] = -1.f;
   __syncthreads();
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+  for (int c = tid; c < kp; c += blockDim.x) {
     const float v = nrm[c];
     int pos = 0;
-    for (int e = 0; e < n; ++e) {
+    for (int e = 0; e < kp; ++e) {
       const float u = nrm[e];
       pos += (u > v) || (u == v && e < c);
     }
     sig[pos] = v < 0.f ? 0.f : v;
-    perm[pos] = c;
+    ord[pos] = c;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // ---- 3. orthonormal right singular vectors: Q[t] (column t of A, length n)
+  for (int t = 0; t < kp; ++t) {
+    float* qt = A + t * n;
+    const float* src = M + ord[t] * n;
+    const float st = sig[t];
+    const float inv = st >= kTiny ? 1.f / st : 0.f;
+    for (int i = tid; i < n; i += blockDim.x) qt[i] = src[i] * inv;
+    __syncthreads();
+    if (st >= kTiny) {
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int s = warp; s < t; s += nwarps) {
+          const float* qs = A + s * n;
+          float dot = 0.f;
+          for (int i = lane; i < n; i += 32) dot += qs[i] * qt[i];
+          dot = warp_sum(dot);
+          if (lane == 0) coef[s] = dot;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += blockDim.x) {
+          float v = qt[i];
+          for (int s = 0; s < t; ++s) v -= coef[s] * A[s * n + i];
+          qt[i] = v;
+        }
+        __syncthreads();
+      }
+      double nq = 0.0;
+      for (int i = tid; i < n; i += blockDim.x) nq += (double)qt[i] * (double)qt[i];
+      nq = block_sum_d(nq, s_red);
+      const float sc = nq > 1e-20 ? (float)(1.0 / sqrt(nq)) : 0.f;  // a vector that cancelled is dropped
+      for (int i = tid; i < n; i += blockDim.x) qt[i] *= sc;
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    const double nn = (double)n;
+    s_flops += 2.0 * nn * nn * kp + (double)kp * kp * 4.0 * nn * 2.0;
+  }
+  // ---- rank choice
+  if (tid == 0) {
     int r;
     if (mode == kStageRight) {
       const float s0 = sig[0];
       r = 0;
-      while (r < n && sig[r] > 1e-7f * s0) ++r;
+      while (r < kp && sig[r] > 1e-7f * s0) ++r;
       if (r < 1) r = 1;
     } else {
-      double tot = 0.0;
-      for (int j = 0; j < n; ++j) tot += (double)sig[j] * (double)sig[j];
-      double normA;
-      if (first) {
-        normA = sqrt(tot);
-        rs.normA[b] = normA;
-      } else {
-        normA = rs.normA[b];
-      }
-      const double delta = (d > 1) ? eps * normA / sqrt((double)(d - 1)) : 0.0;
-      // tail[r] = sqrt(sum_{j >= r} sig_j^2); smallest r >= 1 with tail[r] <= delta
-      double acc = 0.0;
-      int reps = n;
-      for (int j = n - 1; j >= 1; --j) {
+      if (first) rs.normA[b] = normA;
+      // tail2[r] = sum_{t >= r} sig_t^2 + dropped2; smallest r >= 1 with tail <= delta
+      double acc = dropped2;
+      int reps = kp + ((sqrt(acc) <= delta) ? 0 : 1);
+      for (int j = kp - 1; j >= 1; --j) {
         acc += (double)sig[j] * (double)sig[j];
         if (sqrt(acc) <= delta) reps = j; else break;
       }
-      r = reps < rank_cap ? reps : rank_cap;
+      r = min(min(reps, rank_cap), kp);
       if (r < 1) r = 1;
-      double tail = 0.0;
-      for (int j = r; j < n; ++j) tail += (double)sig[j] * (double)sig[j];
+      double tail = dropped2;
+      for (int j = r; j < kp; ++j) tail += (double)sig[j] * (double)sig[j];
       const double rel = normA > 0.0 ? sqrt(tail) / normA : 0.0;
       rs.tail_sum[b] += rel;
       if (rel > rs.tail_max[b]) rs.tail_max[b] = rel;
@@ -365,16 +559,21 @@ __global__ void __launch_bounds__(1024) k_jacobi(TsqrWork w, int B, int mode, in
     }
     s_rank = r;
     rs.newrank[b] = r;
+    if (flops != nullptr) {
+      double f = s_flops;
+      for (int j = 0; j < kp; ++j) f += (double)(n - j) * (2.0 + 6.0 * (n - j - 1));
+      atomicAdd(flops, f);
+    }
   }
   __syncthreads();
   const int r = s_rank;
   float* p1 = P1 + (long long)b * kMaxN * kMaxN;
   float* p2 = P2 + (long long)b * kMaxN * kMaxN;
-  for (int t = threadIdx.x; t < n * r; t += blockDim.x) {
-    const int i = t / r, j = t - i * r;  // i < n (row of V), j < r (singular index)
-    const float v = V[perm[j] * n + i];
+  for (int t = tid; t < n * r; t += blockDim.x) {
+    const int i = t / r, j = t - i * r;  // i < n (row of V, original order), j < r
+    const float v = A[j * n + pinv[i]];
     const float s = sig[j];
-    const float inv = s > 1e-30f ? 1.f / s : 0.f;
+    const float inv = s >= kTiny ? 1.f / s : 0.f;
     if (mode == kStageRight) {
       p1[j * kMaxN + i] = v * inv;  // P1 = S^-1 V^T  (r x n)
       p2[i * kMaxN + j] = v * s;    // P2 = V S       (n x r)
@@ -588,8 +787,8 @@ void launch_jacobi(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, d
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
                    long long core0_cap, double* flops) {
   count_launches(1);
-  k_jacobi<<<B, 1024, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs,
-                                                                P1, P2, core0_out, core0_cap, flops);
+  k_svd<<<B, 1024, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs, P1,
+                                                             P2, core0_out, core0_cap, flops);
 }
 
 void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
@@ -615,7 +814,7 @@ void launch_scan_tiles(cudaStream_t st, GemmWork gw) {
 void set_kernel_attributes() {
   cudaFuncSetAttribute(k_tsqr_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kSmemFloats * (int)sizeof(float));
-  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kJacobiSmemFloats * (int)sizeof(float));
 }
 
