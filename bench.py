@@ -132,6 +132,63 @@ def cpu_oracle_step(model, mc: int):
                 "FP64 numpy oracle")
 
 
+def fullgrid_bytes_per_step(model) -> int:
+    """Algorithmic HBM bytes of one dense float32 step: every pass reads and
+    writes the density once (shears, per-axis operators, normalise, likelihood,
+    normalise) or reads it (sums, moments)."""
+    from oracle import pmf
+    n_shear = sum(1 for op in pmf.elementary_ops(model.F) if op[0] == "shear")
+    cells = int(np.prod(model.n))
+    passes_rw = n_shear + model.d + 1 + 1 + 1   # shears, axis operators, scale, likelihood, scale
+    passes_r = 1 + 1                            # mass sum, moments
+    return cells * 4 * (2 * passes_rw + passes_r)
+
+
+def run_fullgrid(args, model, mc, zs, W, K, dev, ttf):
+    """The plain full-grid float32 filter on the same workload (one Monte Carlo
+    run, the batch's first): steps/s, achieved HBM bandwidth, and the density
+    error of the TT filter of that run against it after the same steps."""
+    import torch
+    import paper_2501_07942_gb300 as G
+    from oracle import tt
+    fg = G.FullGridFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), precision=32,
+                          device=dev)
+    comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+             for m, t in model.tables(ttf.grid_axes())]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for k in range(W):
+        fg.predict(model.F, model.Q)
+        fg.update(comps, model.R, zs[k][0])
+        fg.estimate()
+    ms = 0.0
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fg.predict(model.F, model.Q)
+        fg.update(comps, model.R, zs[W + i][0])
+        fg.estimate()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += a.elapsed_time(b)
+    out = {"value": K / (ms * 1e-3), "unit": "filter-steps/s (one filter)", "dtype": "f32",
+           "ms_per_step": ms / K}
+    pk, src = peaks()
+    bytes_step = fullgrid_bytes_per_step(model)
+    gbs = bytes_step / (ms / K * 1e-3) / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                       "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": src,
+                       "bytes_per_step": bytes_step}
+    # the TT filter of the same run after the same W + K steps
+    if args.tt_error:
+        P = fg.density()
+        T = tt.densify(ttf.export_cores(0))
+        out["tt_density_rel_fro_err"] = float(np.linalg.norm(T - P) / np.linalg.norm(P))
+    fg.free()
+    return out
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -215,6 +272,9 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         ms = float(t.item())
         dist.barrier()
 
+    # the full-grid filter on the same run, compared at the same step count
+    fullgrid = None if args.no_fullgrid else run_fullgrid(args, model, mc_ids[0], zs, W, K, dev, f)
+
     # end to end through the host-buffer C calls: z from host memory every
     # step, mean / cov / log normaliser read back to the host every step
     e2e_s = 0.0
@@ -264,7 +324,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "kernels": {k: {"ms_share": (v["ms"] / tot_ms if tot_ms else 0.0), "launches": v["launches"],
                         "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 else 0.0)}
                     for k, v in prof.items() if v["launches"] > 0},
-        "fullgrid": None,
+        "fullgrid": fullgrid,
     }
     if world == 1 and not args.no_cpu_baseline:
         dt, desc = cpu_oracle_step(model, mc_ids[0])
@@ -281,6 +341,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fullgrid", action="store_true")
+    ap.add_argument("--tt-error", action="store_true",
+                    help="also report the TT density error against the full-grid filter")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")

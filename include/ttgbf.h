@@ -212,6 +212,46 @@ int ttgbf_profile_read(ttgbf_ctx* ctx, ttgbf_kernel_prof* out, int32_t cap, int3
 /* Kernel launches made by the library in this process so far. */
 uint64_t ttgbf_launch_count(void);
 
+/* ---- plain full-grid point-mass filter ------------------------------------ */
+
+/* The dense filter of Sec. 2 (Eqs. pdf_pm, pdf_predII, tpmconvFFT,
+ * pmf_filtrace_a/b) for ONE filter on the same grid and with the same
+ * re-gridded transition as the TT path: the comparison the TT filter is
+ * measured against, and the GPU form of the oracle's arithmetic.  The density
+ * is held densely (n[0]*...*n[d-1] values, d <= 6) in float32 (precision 32)
+ * or float64 (precision 64).  Same conventions as above. */
+typedef struct ttgbf_fg ttgbf_fg;
+
+/* Bytes of device workspace for a full-grid filter; 0 on invalid input. */
+size_t ttgbf_fg_workspace_bytes(const ttgbf_grid* grid, int32_t precision);
+
+/* Create a full-grid filter initialised to the (diagonal Gaussian) prior.
+ * workspace: caller-owned device memory or NULL (the library allocates). */
+int ttgbf_fg_init(ttgbf_fg** out, const ttgbf_grid* grid, const ttgbf_prior* prior, int32_t precision,
+                  void* stream, void* workspace, size_t workspace_bytes);
+
+/* Predictive step with the re-gridded transition (diagonal Q), as ttgbf_predict. */
+int ttgbf_fg_predict(ttgbf_fg* fg, const double* F, const double* Q);
+
+/* Predictive step by the textbook direct sum of Eqs. pdf_predII / TPMmat:
+ * P'(j) = sum_i N(xi_j; F xi_i, Q) P(i) delta, normalised; any positive
+ * definite Q.  O(N^2) work: at most 2^22 grid points (TTGBF_ECAPACITY). */
+int ttgbf_fg_predict_direct(ttgbf_fg* fg, const double* F, const double* Q);
+
+/* Bayes update with one measurement vector z (HOST, b doubles).  The htab
+ * pointers of h are DEVICE arrays of float (precision 32) or double
+ * (precision 64); components may use any one or two modes. */
+int ttgbf_fg_update(ttgbf_fg* fg, const ttgbf_meas* h, const double* R, const double* z);
+
+/* Mean [d], covariance [d][d], this step's log c and the cumulative log
+ * likelihood (HOST outputs, any may be NULL).  Synchronises. */
+int ttgbf_fg_estimate(ttgbf_fg* fg, double* mean, double* cov, double* log_c, double* log_lik);
+
+/* Copy the density (converted to float64) to host memory of cap doubles. */
+int ttgbf_fg_density(ttgbf_fg* fg, double* out, size_t cap);
+
+int ttgbf_fg_free(ttgbf_fg* fg);
+
 /* ---- allocation-free moments ---------------------------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -33,7 +33,9 @@ EXPORTED = [
     "ttgbf_estimate", "ttgbf_estimate_dev", "ttgbf_free", "ttgbf_strerror", "ttgbf_ranks",
     "ttgbf_stats", "ttgbf_grid_axes", "ttgbf_export_cores", "ttgbf_import_cores", "ttgbf_shear",
     "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise", "ttgbf_profile",
-    "ttgbf_profile_read", "ttgbf_launch_count", "ttgbf_moments_noalloc",
+    "ttgbf_profile_read", "ttgbf_launch_count", "ttgbf_moments_noalloc", "ttgbf_fg_workspace_bytes",
+    "ttgbf_fg_init", "ttgbf_fg_predict", "ttgbf_fg_predict_direct", "ttgbf_fg_update",
+    "ttgbf_fg_estimate", "ttgbf_fg_density", "ttgbf_fg_free",
 ]
 
 
@@ -118,6 +120,15 @@ def load() -> ctypes.CDLL:
     lib.ttgbf_profile_read.argtypes = [VP, P(KernelProf), ctypes.c_int32, P(ctypes.c_int32)]
     lib.ttgbf_launch_count.restype = ctypes.c_uint64
     lib.ttgbf_launch_count.argtypes = []
+    lib.ttgbf_fg_workspace_bytes.restype = ctypes.c_size_t
+    lib.ttgbf_fg_workspace_bytes.argtypes = [P(Grid), ctypes.c_int32]
+    lib.ttgbf_fg_init.argtypes = [P(VP), P(Grid), P(Prior), ctypes.c_int32, VP, VP, ctypes.c_size_t]
+    lib.ttgbf_fg_predict.argtypes = [VP, dp, dp]
+    lib.ttgbf_fg_predict_direct.argtypes = [VP, dp, dp]
+    lib.ttgbf_fg_update.argtypes = [VP, P(Meas), dp, dp]
+    lib.ttgbf_fg_estimate.argtypes = [VP, dp, dp, dp, dp]
+    lib.ttgbf_fg_density.argtypes = [VP, dp, ctypes.c_size_t]
+    lib.ttgbf_fg_free.argtypes = [VP]
     _lib = lib
     return lib
 
@@ -155,6 +166,72 @@ def workspace_bytes(lo, hi, n, batch=1, rank_cap=16, eps=1e-6, max_shift_span=0)
     g, keep = _grid(lo, hi, n)
     o = Opts(batch, rank_cap, eps, max_shift_span, None, None, 0)
     return int(load().ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o)))
+
+
+class FullGridFilter:
+    """The plain full-grid point-mass filter on the GPU (``ttgbf_fg_*``): one
+    filter, dense float32 (precision=32) or float64 (precision=64) density."""
+
+    def __init__(self, lo, hi, n, prior_mean, prior_var, precision=32, stream=None, device="cuda"):
+        import torch
+        self._lib = load()
+        self.d = len(n)
+        self.n = [int(v) for v in n]
+        self.precision = int(precision)
+        g, self._gkeep = _grid(lo, hi, n)
+        self._stream = torch.cuda.current_stream(device) if stream is None else stream
+        nbytes = self._lib.ttgbf_fg_workspace_bytes(ctypes.byref(g), self.precision)
+        if nbytes == 0:
+            raise TTGBFError(-1, "ttgbf_fg_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        pm, pv = _f64(prior_mean), _f64(prior_var)
+        pr = Prior(_dptr(pm), _dptr(pv))
+        self._ctx = ctypes.c_void_p()
+        _check(self._lib.ttgbf_fg_init(ctypes.byref(self._ctx), ctypes.byref(g), ctypes.byref(pr),
+                                       self.precision, ctypes.c_void_p(self._stream.cuda_stream),
+                                       ctypes.c_void_p(self.workspace.data_ptr()), int(nbytes)),
+               "ttgbf_fg_init")
+
+    def predict(self, F, Q):
+        F, Q = _f64(F), _f64(Q)
+        _check(self._lib.ttgbf_fg_predict(self._ctx, _dptr(F), _dptr(Q)), "ttgbf_fg_predict")
+
+    def predict_direct(self, F, Q):
+        F, Q = _f64(F), _f64(Q)
+        _check(self._lib.ttgbf_fg_predict_direct(self._ctx, _dptr(F), _dptr(Q)),
+               "ttgbf_fg_predict_direct")
+
+    def update(self, comps, R, z):
+        """comps: [(modes, device table of float32 / float64 matching precision)]."""
+        m, keep = TTFilter._meas(comps)
+        R, z = _f64(R), _f64(z)
+        _check(self._lib.ttgbf_fg_update(self._ctx, ctypes.byref(m), _dptr(R), _dptr(z)),
+               "ttgbf_fg_update")
+
+    def estimate(self):
+        mean = np.zeros(self.d)
+        cov = np.zeros((self.d, self.d))
+        lc = np.zeros(1)
+        ll = np.zeros(1)
+        _check(self._lib.ttgbf_fg_estimate(self._ctx, _dptr(mean), _dptr(cov), _dptr(lc), _dptr(ll)),
+               "ttgbf_fg_estimate")
+        return mean, cov, float(lc[0]), float(ll[0])
+
+    def density(self):
+        out = np.zeros(int(np.prod(self.n)))
+        _check(self._lib.ttgbf_fg_density(self._ctx, _dptr(out), out.size), "ttgbf_fg_density")
+        return out.reshape(self.n)
+
+    def free(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.ttgbf_fg_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class TTFilter:
