@@ -81,6 +81,20 @@ __device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 
+// Compensated (Kahan) running sum in the density's own precision: per-thread
+// partial sums stay accurate without float64 arithmetic per element (float64
+// runs at 1/61 of the float32 rate on this GPU).
+template <typename T>
+struct Kahan {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
 template <typename T>
 __global__ void k_fg_prior(T* P, FgGeom g, const double* mean, const double* var) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.total;
@@ -115,28 +129,155 @@ __global__ void k_fg_shear(const T* __restrict__ in, T* __restrict__ out, FgGeom
   }
 }
 
-// out(.., j, ..) = sum_{i in band(j)} M(j, i) in(.., i, ..) along axis m.  A CTA
-// holds 32 fibres of the axis in shared memory (tile[i][f]).
+// out(.., j, ..) = sum_{i in band(j)} M(j, i) in(.., i, ..) along axis m, as a
+// register-blocked product of the banded N x N operator with a tile of 64
+// fibres of the axis.  Shared memory: the operator transposed (Mt[i][j]) and
+// the tile (tile[i][f]).  Thread (tj, tf) computes rows 4 tj .. 4 tj + 3 for
+// fibres 8 tf .. 8 tf + 7 over the union of the four rows' bands.  N must be
+// a multiple of 4 and at most 128 (256 threads x 4 rows).
+constexpr int kAxFib = 64;
+constexpr int kAxPad = kAxFib + 4;
+
+// Column of fibre f in a tile row: fibres 32..63 are shifted by 4 words so that
+// the eight 8-fibre groups of a warp hit distinct shared-memory banks.
+__device__ __forceinline__ int axcol(int f) { return f + ((f >> 5) << 2); }
+
+// Four consecutive values from shared memory (16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* v);
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float* v) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = q.z;
+  v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fg_axis(const T* __restrict__ in, T* __restrict__ out,
                                                  long long nfib, int N, long long post,
                                                  const T* __restrict__ M, const int* __restrict__ blo,
                                                  const int* __restrict__ bhi) {
   extern __shared__ unsigned char smraw[];
-  T* tile = reinterpret_cast<T*>(smraw);  // [N][33]
-  const int f = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  for (long long g0 = (long long)blockIdx.x * 32; g0 < nfib; g0 += (long long)gridDim.x * 32) {
-    const long long gf = g0 + f;
-    const bool ok = gf < nfib;
-    const long long p = ok ? gf / post : 0, q = ok ? gf - p * post : 0;
-    const long long base = p * N * post + q;
-    for (int i = grp; i < N; i += 8) tile[i * 33 + f] = ok ? in[base + (long long)i * post] : (T)0;
+  T* Mt = reinterpret_cast<T*>(smraw);  // [N][N]
+  T* tile = Mt + N * N;                 // [N][kAxPad]
+  __shared__ long long fbase[kAxFib];   // element offset of each fibre's first entry
+  const int tid = threadIdx.x;
+  for (int t = tid; t < N * N; t += blockDim.x) {
+    const int j = t / N, i = t - j * N;
+    Mt[i * N + j] = M[t];
+  }
+  const int tf = tid & 7, tj = tid >> 3;  // 8 fibre groups x 32 row groups
+  const int j0 = tj * 4;
+  const bool rows_ok = j0 < N;
+  int lo = N, hi = -1;
+  if (rows_ok) {
+    for (int q = 0; q < 4; ++q) {
+      if (blo[j0 + q] <= bhi[j0 + q]) {
+        lo = min(lo, blo[j0 + q]);
+        hi = max(hi, bhi[j0 + q]);
+      }
+    }
+  }
+  __syncthreads();
+  for (long long g0 = (long long)blockIdx.x * kAxFib; g0 < nfib; g0 += (long long)gridDim.x * kAxFib) {
+    // ---- load the tile
+    if (tid < kAxFib) {
+      const long long gf = g0 + tid;
+      const long long p = gf / post, q = gf - p * post;
+      fbase[tid] = gf < nfib ? p * N * post + q : -1;
+    }
     __syncthreads();
-    for (int j = grp; j < N; j += 8) {
-      T acc = 0;
-      const int lo = blo[j], hi = bhi[j];
-      for (int i = lo; i <= hi; ++i) acc += M[(long long)j * N + i] * tile[i * 33 + f];
-      if (ok) out[base + (long long)j * post] = acc;
+    // 8 loads in flight per thread before the shared-memory stores
+    const int tot = kAxFib * N;
+    if (post == 1) {
+      // fibres are contiguous rows of N: consecutive threads read consecutive i
+      for (int t0 = tid; t0 < tot; t0 += 8 * 256) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * 256;
+          const int f = t / N, i = t - f * N;
+          const long long gf = g0 + f;
+          v[u] = (t < tot && gf < nfib) ? in[gf * N + i] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * 256;
+          if (t < tot) {
+            const int f = t / N, i = t - f * N;
+            tile[i * kAxPad + axcol(f)] = v[u];
+          }
+        }
+      }
+    } else {
+      for (int t0 = tid; t0 < tot; t0 += 8 * 256) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * 256;
+          const int i = t / kAxFib, f = t - i * kAxFib;
+          const long long b = t < tot ? fbase[f] : -1;
+          v[u] = b >= 0 ? in[b + (long long)i * post] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * 256;
+          if (t < tot) {
+            const int i = t / kAxFib, f = t - i * kAxFib;
+            tile[i * kAxPad + axcol(f)] = v[u];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    T acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0;
+    const int c0 = axcol(tf * 8);
+    for (int i = lo; i <= hi; ++i) {
+      T m4[4], t8[8];
+      ld4<T>(Mt + i * N + j0, m4);
+      ld4<T>(tile + i * kAxPad + c0, t8);
+      ld4<T>(tile + i * kAxPad + c0 + 4, t8 + 4);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] += m4[a] * t8[b];
+    }
+    __syncthreads();
+    // ---- results back into the tile, then out with the load's access pattern
+    if (rows_ok) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) tile[(j0 + a) * kAxPad + c0 + b] = acc[a][b];
+    }
+    __syncthreads();
+    if (post == 1) {
+      for (int t = tid; t < kAxFib * N; t += blockDim.x) {
+        const int f = t / N, j = t - f * N;
+        const long long gf = g0 + f;
+        if (gf < nfib) out[gf * N + j] = tile[j * kAxPad + axcol(f)];
+      }
+    } else {
+      for (int t = tid; t < kAxFib * N; t += blockDim.x) {
+        const int j = t / kAxFib, f = t - j * kAxFib;
+        const long long b = fbase[f];
+        if (b >= 0) out[b + (long long)j * post] = tile[j * kAxPad + axcol(f)];
+      }
     }
     __syncthreads();
   }
@@ -146,10 +287,11 @@ __global__ void __launch_bounds__(256) k_fg_axis(const T* __restrict__ in, T* __
 template <typename T>
 __global__ void k_fg_sum(const T* __restrict__ P, long long total, double* acc) {
   __shared__ double red[32];
-  double s = 0.0;
+  Kahan<T> k;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
-    s += (double)P[e];
+    k.add(P[e]);
+  double s = (double)k.s - (double)k.c;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -191,28 +333,55 @@ __global__ void k_fg_lik_off(const H* htab, int ntab, double z, double* off) {
 }
 
 // P <- P * prod_c exp(-((z_c - h_c)^2 - off_c) / (2 R_c)); acc += sum of the result.
+// One warp per row of the last axis: factors of components that do not use
+// the last axis are evaluated once per row.
+template <typename T>
+__device__ __forceinline__ T lik_factor(const FgLik& lk, int c, int i0, int i1, const double* off) {
+  long long t = i0;
+  if (lk.nmodes[c] == 2) t = (long long)i0 * lk.ld[c] + i1;
+  const T h = (T)static_cast<const T*>(lk.htab[c])[t];
+  const T df = (T)lk.z[c] - h;
+  return exp_t<T>(-(df * df - (T)off[c]) * (T)lk.inv2r[c]);
+}
+
 template <typename T>
 __global__ void k_fg_lik(T* P, FgGeom g, FgLik lk, const double* off, double* acc) {
   __shared__ double red[32];
-  double s = 0.0;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.total;
-       e += (long long)gridDim.x * blockDim.x) {
-    T L = 1;
+  const int d = g.d, last = d - 1;
+  const int NL = g.n[last];
+  const long long rows = g.total / NL;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  Kahan<T> k;
+  for (long long r = warp0; r < rows; r += nwarps) {
+    const long long e0 = r * NL;
+    T Lrow = 1;
     for (int c = 0; c < lk.b; ++c) {
-      const int i0 = axis_index(e, g, lk.modes[c][0]);
-      long long t = i0;
-      if (lk.nmodes[c] == 2) t = (long long)i0 * lk.ld[c] + axis_index(e, g, lk.modes[c][1]);
-      const T h = (T)static_cast<const T*>(lk.htab[c])[t];
-      const T df = (T)lk.z[c] - h;
-      L *= exp_t<T>(-(df * df - (T)off[c]) * (T)lk.inv2r[c]);
+      const bool uses_last = lk.modes[c][0] == last || (lk.nmodes[c] == 2 && lk.modes[c][1] == last);
+      if (uses_last) continue;
+      const int i0 = axis_index(e0, g, lk.modes[c][0]);
+      const int i1 = lk.nmodes[c] == 2 ? axis_index(e0, g, lk.modes[c][1]) : 0;
+      Lrow *= lik_factor<T>(lk, c, i0, i1, off);
     }
-    const T v = P[e] * L;
-    P[e] = v;
-    s += (double)v;
+    for (int il = lane; il < NL; il += 32) {
+      T L = Lrow;
+      for (int c = 0; c < lk.b; ++c) {
+        const bool uses_last = lk.modes[c][0] == last || (lk.nmodes[c] == 2 && lk.modes[c][1] == last);
+        if (!uses_last) continue;
+        const int i0 = lk.modes[c][0] == last ? il : axis_index(e0, g, lk.modes[c][0]);
+        const int i1 = lk.nmodes[c] == 2 ? (lk.modes[c][1] == last ? il : axis_index(e0, g, lk.modes[c][1])) : 0;
+        L *= lik_factor<T>(lk, c, i0, i1, off);
+      }
+      const T v = P[e0 + il] * L;
+      P[e0 + il] = v;
+      k.add(v);
+    }
   }
+  double s = (double)k.s - (double)k.c;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  if (lane == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -223,32 +392,58 @@ __global__ void k_fg_lik(T* P, FgGeom g, FgLik lk, const double* off, double* ac
 
 // acc[0] = sum P, acc[1+m] = sum x_m P, acc[1+D+m*D+l] = sum x_m x_l P (centred
 // x, l >= m).  D is the state dimension (compile time, so the sums stay in
-// registers).
+// registers).  One warp per row of the last axis: per row only sum v, sum x v
+// and sum x^2 v over the last axis are formed, then combined with the row's
+// other coordinates.
 template <typename T, int D>
 __global__ void k_fg_moments(const T* __restrict__ P, FgGeom g, double* acc) {
   constexpr int NA = 1 + D + D * D;
+  constexpr int LAST = D - 1;
   __shared__ double red[NA][8];
-  double s[NA];
+  Kahan<T> s[NA];
+  const int NL = g.n[LAST];
+  const long long rows = g.total / NL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const T lol = (T)(g.lo[LAST] - g.centre[LAST]), dxl = (T)g.dx[LAST];
+  for (long long r = warp0; r < rows; r += nwarps) {
+    const long long e0 = r * NL;
+    Kahan<T> a0, a1, a2;
+    for (int il = lane; il < NL; il += 32) {
+      const T v = P[e0 + il];
+      const T xl = lol + ((T)il + (T)0.5) * dxl;
+      a0.add(v);
+      a1.add(xl * v);
+      a2.add(xl * xl * v);
+    }
+    T r0 = a0.s - a0.c, r1 = a1.s - a1.c, r2 = a2.s - a2.c;
 #pragma unroll
-  for (int a = 0; a < NA; ++a) s[a] = 0.0;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const double v = (double)P[e];
-    double x[D];
+    for (int o = 16; o > 0; o >>= 1) {
+      r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+      r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    }
+    if (lane == 0) {
+      T x[D];
 #pragma unroll
-    for (int m = 0; m < D; ++m) x[m] = g.lo[m] + (axis_index(e, g, m) + 0.5) * g.dx[m] - g.centre[m];
-    s[0] += v;
+      for (int m = 0; m < LAST; ++m)
+        x[m] = (T)(g.lo[m] - g.centre[m]) + ((T)axis_index(e0, g, m) + (T)0.5) * (T)g.dx[m];
+      s[0].add(r0);
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
-      s[1 + m] += x[m] * v;
+      for (int m = 0; m < LAST; ++m) {
+        s[1 + m].add(x[m] * r0);
 #pragma unroll
-      for (int l = m; l < D; ++l) s[1 + D + m * D + l] += x[m] * x[l] * v;
+        for (int l = m; l < LAST; ++l) s[1 + D + m * D + l].add(x[m] * x[l] * r0);
+        s[1 + D + m * D + LAST].add(x[m] * r1);
+      }
+      s[1 + LAST].add(r1);
+      s[1 + D + LAST * D + LAST].add(r2);
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int a = 0; a < NA; ++a) {
-    double t = s[a];
+    double t = (double)s[a].s - (double)s[a].c;  // non-zero on lane 0 of each warp only
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) red[a][warp] = t;
@@ -464,6 +659,9 @@ int fg_prepare(ttgbf_fg* c, const double* F, const double* Q) {
     for (int n = 0; n < m; ++n)
       if (Lm[m * d + n] != 0.0) add_shear(m, n, Lm[m * d + n], &c->shears_l);
   // per-axis operators and their bands
+  // entries below this fraction of the largest are below the density's
+  // rounding resolution and are skipped
+  const double band_tol = sizeof(T) == 4 ? 1e-12 : 1e-20;
   auto add_band = [&](const std::vector<double>& M, int N) {
     const long long at = (long long)ints.size();
     double mx = 0.0;
@@ -472,7 +670,7 @@ int fg_prepare(ttgbf_fg* c, const double* F, const double* Q) {
     for (int j = 0; j < N; ++j) {
       int lo = N, hi = -1;
       for (int i = 0; i < N; ++i)
-        if (std::fabs(M[(size_t)j * N + i]) > 1e-30 * mx) {
+        if (std::fabs(M[(size_t)j * N + i]) > band_tol * mx) {
           lo = std::min(lo, i);
           hi = std::max(hi, i);
         }
@@ -544,9 +742,9 @@ void fg_axis(ttgbf_fg* c, int m, long long moff, long long boff) {
   long long post = 1;
   for (int k = m + 1; k < c->d; ++k) post *= c->n[k];
   const long long nfib = c->g.total / N;
-  const size_t sm = sizeof(T) * (size_t)N * 33;
+  const size_t sm = sizeof(T) * ((size_t)N * N + (size_t)N * kAxPad);
   ttgbf::count_launches(1);
-  k_fg_axis<T><<<c->sms * 8, 256, sm, c->st>>>((const T*)c->buf[c->cur], (T*)c->buf[c->cur ^ 1], nfib, N,
+  k_fg_axis<T><<<c->sms * 2, 256, sm, c->st>>>((const T*)c->buf[c->cur], (T*)c->buf[c->cur ^ 1], nfib, N,
                                               post, (const T*)c->mats + moff, c->ints + boff,
                                               c->ints + boff + N);
   c->cur ^= 1;
@@ -677,7 +875,7 @@ size_t ttgbf_fg_workspace_bytes(const ttgbf_grid* grid, int32_t precision) {
   if (precision != 32 && precision != 64) return 0;
   long long total = 1;
   for (int k = 0; k < grid->d; ++k) {
-    if (grid->n[k] < 2 || !(grid->hi[k] > grid->lo[k])) return 0;
+    if (grid->n[k] < 4 || grid->n[k] > 128 || grid->n[k] % 4 || !(grid->hi[k] > grid->lo[k])) return 0;
     total *= grid->n[k];
     if (total >= (1ll << 31)) return 0;  // 32-bit element indices
   }

@@ -84,7 +84,7 @@ def test_general_F_and_two_mode_any_order(G):
     # non-triangular F (L shears after the scalings) and a two-mode component
     # on modes (2, 0) in float64
     import torch
-    lo, hi, n = [-4.0, -3.0, -3.5], [4.0, 3.0, 3.5], [20, 16, 18]
+    lo, hi, n = [-4.0, -3.0, -3.5], [4.0, 3.0, 3.5], [20, 16, 24]
     F = np.array([[0.95, 0.04, 0.0], [-0.05, 0.97, 0.02], [0.03, 0.0, 0.92]])
     Q = np.diag([0.05, 0.08, 0.03])
     f = G.FullGridFilter(lo, hi, n, [0.2, -0.1, 0.0], [1.0, 0.8, 0.6], precision=64)
