@@ -32,8 +32,8 @@ namespace {
 
 constexpr int kMaxComps = 16;
 
-enum ProfClass : int { kPTsqr = 0, kPJacobi, kPGemm, kPShear, kPMoments, kPLik, kPPlan, kPOther, kPClasses };
-const char* const kProfNames[kPClasses] = {"tsqr", "jacobi", "gemm", "shear_expand", "moments",
+enum ProfClass : int { kPTsqr = 0, kPSvd, kPGemm, kPShear, kPMoments, kPLik, kPPlan, kPOther, kPClasses };
+const char* const kProfNames[kPClasses] = {"tsqr", "svd", "gemm", "shear_expand", "moments",
                                            "likelihood", "plan", "other"};
 
 std::atomic<unsigned long long> g_launches{0};
@@ -330,9 +330,9 @@ void stage(ttgbf_ctx* c, int mode, int k, int first) {
   }
   float* core0_alt = (mode == kStageSplit) ? altp(c, 0) : nullptr;
   {
-    Prof p(c, kPJacobi, 1);
-    launch_jacobi(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1, c->P2,
-                  core0_alt, c->L.core_cap[0], flops_of(c, kPJacobi));
+    Prof p(c, kPSvd, 1);
+    launch_svd(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1, c->P2,
+                  core0_alt, c->L.core_cap[0], flops_of(c, kPSvd));
   }
   int ka, kb, ndesc = 2 * B;
   if (mode == kStageRight) {

@@ -87,7 +87,7 @@ void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
                        TsqrWork w, float* stack0, float* stack1, long long stack_cap);
 void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid, double* flops);
-void launch_jacobi(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
+void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
                    long long core0_cap, double* flops);
 void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,

@@ -28,12 +28,6 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // Rows of the source of problem p at level L, and the chunk size used there.
 __device__ __forceinline__ void tsqr_level_shape(const TsqrProblem& p, int L, int* rows, int* chunk) {
   const int n = p.src.n;
@@ -215,13 +209,15 @@ __device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int*
   }
 }
 
-// Block reductions for the SVD kernel (blockDim a multiple of 32, <= 1024).
-__device__ double block_sum_d(double v, double* red) {
-  v = warp_sum_d(v);
+// Block sum for the SVD kernel (blockDim a multiple of 32, <= 1024).  Every
+// value summed here is non-negative, so FP32 keeps a relative accuracy of
+// about n u; FP64 would cost ~60x the issue slots on this part.
+__device__ float block_sum_f(float v, float* red) {
+  v = warp_sum(v);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double t = 0.0;
+  float t = 0.f;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
   return t;
 }
@@ -257,7 +253,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   int* perm = (int*)(coef + kMaxN);     // [kMaxN] column permutation of the QRCP
   int* pinv = perm + kMaxN;             // [kMaxN] its inverse
   int* ord = pinv + kMaxN;              // [kMaxN] Jacobi columns by decreasing norm
-  __shared__ double s_red[32];
+  __shared__ float s_red[32];
   __shared__ float s_redf[32];
   __shared__ int s_redi[32];
   __shared__ float s_tau;
@@ -273,17 +269,17 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   if (tid == 0) s_flops = 0.0;
   __syncthreads();
   for (int c = warp; c < n; c += nwarps) {
-    double s = 0.0;
-    for (int i = lane; i < n; i += 32) s += (double)A[c * n + i] * (double)A[c * n + i];
-    s = warp_sum_d(s);
-    if (lane == 0) nrm[c] = (float)s;
+    float s = 0.f;
+    for (int i = lane; i < n; i += 32) s += A[c * n + i] * A[c * n + i];
+    s = warp_sum(s);
+    if (lane == 0) nrm[c] = s;
   }
   __syncthreads();
   double tot = 0.0;
   {
-    double s = 0.0;
-    for (int c = tid; c < n; c += blockDim.x) s += (double)nrm[c];
-    tot = block_sum_d(s, s_red);
+    float s = 0.f;
+    for (int c = tid; c < n; c += blockDim.x) s += nrm[c];
+    tot = (double)block_sum_f(s, s_red);
   }
   double normA = 0.0;
   if (mode != kStageRight) normA = first ? sqrt(tot) : rs.normA[b];
@@ -296,18 +292,18 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   // ---- 1. QR with column pivoting
   int k = 0;
   for (; k < kcap; ++k) {
-    double rem = 0.0;
+    float rem = 0.f;
     float best = -1.f;
     int bi = n;
     for (int c = k + tid; c < n; c += blockDim.x) {
       const float v = nrm[c];
-      rem += (double)v;
+      rem += v;
       if (v > best || (v == best && c < bi)) {
         best = v;
         bi = c;
       }
     }
-    rem = block_sum_d(rem, s_red);
+    rem = block_sum_f(rem, s_red);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float ov = __shfl_xor_sync(0xffffffffu, best, o);
@@ -331,7 +327,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
           bx = s_redi[q];
         }
       s_piv = bx;
-      s_stop = (k > 0 && rem <= stop2) || bx >= n;
+      s_stop = (k > 0 && (double)rem <= stop2) || bx >= n;
     }
     __syncthreads();
     if (s_stop) break;
@@ -407,9 +403,9 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   const int kp = k;  // >= 1
   double dropped2 = 0.0;
   {
-    double s = 0.0;
-    for (int c = kp + tid; c < n; c += blockDim.x) s += (double)nrm[c];
-    dropped2 = block_sum_d(s, s_red);
+    float s = 0.f;
+    for (int c = kp + tid; c < n; c += blockDim.x) s += nrm[c];
+    dropped2 = (double)block_sum_f(s, s_red);
   }
   // ---- 2. Jacobi on the k' leading rows of R' as columns of length n
   for (int t = tid; t < kp * n; t += blockDim.x) {
@@ -474,10 +470,10 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   }
   // singular values and their order
   for (int c = warp; c < kp; c += nwarps) {
-    double s = 0.0;
-    for (int i = lane; i < n; i += 32) s += (double)M[c * n + i] * (double)M[c * n + i];
-    s = warp_sum_d(s);
-    if (lane == 0) nrm[c] = (float)sqrt(s);
+    float s = 0.f;
+    for (int i = lane; i < n; i += 32) s += M[c * n + i] * M[c * n + i];
+    s = warp_sum(s);
+    if (lane == 0) nrm[c] = sqrtf(s);
   }
   __syncthreads();
   for (int c = tid; c < kp; c += blockDim.x)
@@ -519,10 +515,10 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
         }
         __syncthreads();
       }
-      double nq = 0.0;
-      for (int i = tid; i < n; i += blockDim.x) nq += (double)qt[i] * (double)qt[i];
-      nq = block_sum_d(nq, s_red);
-      const float sc = nq > 1e-20 ? (float)(1.0 / sqrt(nq)) : 0.f;  // a vector that cancelled is dropped
+      float nq = 0.f;
+      for (int i = tid; i < n; i += blockDim.x) nq += qt[i] * qt[i];
+      nq = block_sum_f(nq, s_red);
+      const float sc = nq > 1e-20f ? rsqrtf(nq) : 0.f;  // a vector that cancelled is dropped
       for (int i = tid; i < n; i += blockDim.x) qt[i] *= sc;
       __syncthreads();
     }
@@ -783,7 +779,7 @@ void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid, doubl
     k_tsqr_level<<<grid, 512, kSmemFloats * sizeof(float), st>>>(w, B, L, flops);
 }
 
-void launch_jacobi(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
+void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
                    long long core0_cap, double* flops) {
   count_launches(1);
