@@ -54,12 +54,12 @@ struct Layout {
   size_t ranks, axes, pmean, pvar;
   size_t normA, tail_sum, tail_max, mass, mass_pred, log_c, log_lik, logoff, mean, cov;
   size_t cap_hits, newrank, lik_off;
-  size_t tsqr_prob, tsqr_off, stack[2];
+  size_t tsqr_prob, tsqr_off, tsqr_cnt, stack[2];
   size_t P1, P2, gdesc, gtiles, awork, W, opmats, zbuf, prof_flops;
   size_t total;
   long long core_cap[kMaxD];
   long long stack_cap, W_cap, opmats_floats, awork_stride;
-  int gdesc_cap, levels, capr;
+  int gdesc_cap, capr;
 };
 
 bool finite_all(const double* p, size_t n) {
@@ -68,25 +68,12 @@ bool finite_all(const double* p, size_t n) {
   return true;
 }
 
-int tsqr_levels_for(long long M, int n) {
-  long long C = kSmemFloats / n;
-  if (C > M) C = M;
-  long long rows = M, Cl = C;
-  int L = 0;
-  for (;; ++L) {
-    const long long nch = (rows + Cl - 1) / Cl;
-    if (nch <= 1) break;
-    rows = nch * n;
-    Cl = (C / n) * n;
-  }
-  return L + 1;
-}
-
+// Floats of the per-filter TSQR stack for an M x n problem: one n x n R
+// factor per row slice.
 long long tsqr_stack_for(long long M, int n) {
-  long long C = kSmemFloats / n;
-  if (C > M) C = M;
-  const long long nch = (M + C - 1) / C;
-  return nch * (long long)n * n;
+  long long nsl = (M + tsqr_slice_rows(n) - 1) / tsqr_slice_rows(n);
+  nsl = std::max<long long>(1, std::min<long long>(nsl, kTsqrMaxSlices));
+  return nsl * (long long)n * n;
 }
 
 int validate_grid(const ttgbf_grid* g) {
@@ -143,18 +130,14 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   L.newrank = a.take<int>(B);
   L.lik_off = a.take<float>(B);
   L.tsqr_prob = a.take<TsqrProblem>(B);
-  L.tsqr_off = a.take<int>((size_t)kMaxLevels * (B + 1));
+  L.tsqr_off = a.take<int>((size_t)B + 1);
+  L.tsqr_cnt = a.take<int>((size_t)B);
   // tall matrices: rows <= capr * nmax, columns <= max(capr, n0)
   const long long Mmax = (long long)capr * nmax;
   const int nsplit = (d >= 2) ? std::min<int>(g->n[0], kMaxN) : 1;
   long long stack = 0;
-  int levels = 1;
-  for (int n = 1; n <= std::max(capr, nsplit); ++n) {
-    stack = std::max(stack, tsqr_stack_for(Mmax, n));
-    levels = std::max(levels, tsqr_levels_for(Mmax, n));
-  }
+  for (int n = 1; n <= std::max(capr, nsplit); ++n) stack = std::max(stack, tsqr_stack_for(Mmax, n));
   L.stack_cap = stack;
-  L.levels = levels;
   L.stack[0] = a.take<float>((size_t)B * stack);
   L.stack[1] = a.take<float>((size_t)B * stack);
   L.P1 = a.take<float>((size_t)B * kMaxN * kMaxN);
@@ -325,8 +308,8 @@ void stage(ttgbf_ctx* c, int mode, int k, int first) {
                       c->d > 1 ? c->n[1] : 1, c->tw, c->stack[0], c->stack[1], c->L.stack_cap);
   }
   {
-    Prof p(c, kPTsqr, c->L.levels);
-    launch_tsqr(c->st, c->tw, B, c->L.levels, c->sms, flops_of(c, kPTsqr));
+    Prof p(c, kPTsqr, 1);
+    launch_tsqr(c->st, c->tw, B, c->sms, flops_of(c, kPTsqr));
   }
   float* core0_alt = (mode == kStageSplit) ? altp(c, 0) : nullptr;
   {
@@ -852,6 +835,7 @@ int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior
   c->lik_off = (float*)(b + L.lik_off);
   c->tw.prob = (TsqrProblem*)(b + L.tsqr_prob);
   c->tw.offset = (int*)(b + L.tsqr_off);
+  c->tw.counter = (int*)(b + L.tsqr_cnt);
   c->stack[0] = (float*)(b + L.stack[0]);
   c->stack[1] = (float*)(b + L.stack[1]);
   c->P1 = (float*)(b + L.P1);

@@ -19,10 +19,10 @@
 
 namespace ttgbf {
 
-constexpr int kSmemFloats = 51200;  // 200 KiB dynamic shared memory per TSQR CTA
 constexpr int kMaxN = 160;          // largest column count of a TSQR / SVD problem
+constexpr int kTsqrTileRows = 256;  // rows of the register-resident QR tile
+constexpr int kTsqrMaxSlices = 64;  // row slices (CTAs) per TSQR problem
 constexpr int kJacobiSmemFloats = 2 * kMaxN * kMaxN + 8 * kMaxN;  // SVD kernel
-constexpr int kMaxLevels = 20;      // TSQR reduction levels
 constexpr int kMaxD = 16;           // largest state dimension
 constexpr int kTile = 64;           // GEMM tile edge
 
@@ -33,21 +33,31 @@ struct MatView {
   int M, n;
 };
 
-// One TSQR problem: the R factor of a tall matrix by a tree of Householder
-// QRs of row chunks.  Level 0 reads `src`; level L >= 1 reads the stack of
-// n x n R blocks written by level L-1 (stack0 at odd L-1 ... see tsqr_rows).
+// One TSQR problem: the R factor of a tall matrix.  Its rows are cut into
+// nslice slices of `slice` rows, one CTA each; with one slice the R factor is
+// written to stack0, otherwise the slice factors are stacked in stack0 and
+// their R factor is written to stack1 (nlev = 1 or 2: R ends in
+// stack[(nlev-1)&1]).
 struct TsqrProblem {
   MatView src;
-  int chunk;  // rows per level-0 chunk; level >= 1 chunks hold floor(chunk/n) blocks
-  int nlev;   // levels this problem needs (>= 1); the R factor ends in stack[(nlev-1)&1]
+  int slice;
+  int nslice;
+  int nlev;
   float* stack0;
   float* stack1;
 };
 
 struct TsqrWork {
   TsqrProblem* prob;  // [B]
-  int* offset;        // [kMaxLevels][B+1] exclusive prefix of chunk counts per level
+  int* offset;        // [B+1] exclusive prefix of slice counts
+  int* counter;       // [B] slices finished (reset by the plan kernel)
 };
+
+// Rows per slice for an n-column problem: the first pass of a slice takes a
+// full tile and each later pass kTsqrTileRows - n new rows; eight later passes.
+__host__ __device__ inline long long tsqr_slice_rows(int n) {
+  return kTsqrTileRows + 8LL * (kTsqrTileRows - n);
+}
 
 // Row-major GEMM C (m x n) = A (m x k) * B (k x n).
 struct GemmDesc {
@@ -86,7 +96,8 @@ struct TTGeom {
 void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
                        TsqrWork w, float* stack0, float* stack1, long long stack_cap);
-void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid, double* flops);
+// tsqr.cu
+void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int grid, double* flops);
 void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
                    long long core0_cap, double* flops);

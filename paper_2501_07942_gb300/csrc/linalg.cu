@@ -1,10 +1,10 @@
-// linalg.cu -- batched tall-skinny QR (R factor only), one-sided Jacobi SVD and
-// grouped GEMM used by TT rounding (Sec. 4.1 "round"; Alg. 2 steps 2 and 4).
+// linalg.cu -- stage plans, the SVD of the R factors and the grouped GEMM
+// used by TT rounding (Sec. 4.1 "round"; Alg. 2 steps 2 and 4).
 //
 // One rounding stage (one core of the right-to-left orthogonalisation sweep,
 // or one link of the left-to-right truncation sweep) is:
 //   plan    -> per filter, the tall matrix whose R factor is needed
-//   TSQR    -> R (n x n) by a tree of in-shared-memory Householder QRs
+//   TSQR    -> R (n x n) by register-resident Householder QR (tsqr.cu)
 //   SVD     -> R = U S V^T (pivoted QR, then one-sided Jacobi on the
 //              numerically significant rows), rank choice, factors P1, P2
 //   plan2   -> GEMM descriptors for "new core = unfolding * P" and
@@ -26,20 +26,6 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-// Rows of the source of problem p at level L, and the chunk size used there.
-__device__ __forceinline__ void tsqr_level_shape(const TsqrProblem& p, int L, int* rows, int* chunk) {
-  const int n = p.src.n;
-  int r = p.src.M;
-  int C = p.chunk;
-  for (int l = 0; l < L; ++l) {
-    const int nch = (r + C - 1) / C;
-    r = nch * n;
-    C = (p.chunk / n) * n;
-  }
-  *rows = r;
-  *chunk = C;
 }
 
 // In-place exclusive scan of o[0..n) by one CTA of at most 1024 threads;
@@ -67,133 +53,6 @@ __device__ void block_scan_inplace(int* o, int n) {
   }
   if (threadIdx.x == 0) o[n] = s_carry;
   __syncthreads();
-}
-
-// ------------------------------------------------------------------ TSQR
-// Householder QR of a rows x n chunk held column-major in shared memory
-// (sm[j * rows + i]); writes the n x n R factor (zeros below the diagonal and
-// below row min(rows, n)) row-major to `out`.  Reflectors use the scaled form
-// H = I - tau v v^T with v_j = 1, tau = (beta - alpha) / beta and norms
-// computed after scaling by the column maximum, so tiny or huge columns
-// neither underflow nor overflow.
-__device__ void householder_chunk(float* sm, int rows, int n, float* out) {
-  __shared__ float s_beta[kMaxN];
-  __shared__ float s_tau;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int kmax = rows < n ? rows : n;
-  for (int j = 0; j < kmax; ++j) {
-    float* colj = sm + (long long)j * rows;
-    if (warp == 0) {
-      float mx = 0.f;
-      for (int i = j + 1 + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(colj[i]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      // entries below kTiny (FP32 denormals) count as zero: dividing by them
-      // would overflow
-      float s = 0.f;
-      if (mx >= kTiny) {
-        const float inv = 1.f / mx;
-        for (int i = j + 1 + lane; i < rows; i += 32) {
-          const float x = colj[i] * inv;
-          s += x * x;
-        }
-      }
-      s = warp_sum(s);
-      const float alpha = colj[j];
-      const float tail = mx >= kTiny ? mx * sqrtf(s) : 0.f;  // ||x_{j+1:}||
-      float tau = 0.f, beta = alpha, scl = 0.f;
-      if (tail > 0.f) {
-        const float big = fmaxf(fabsf(alpha), tail);
-        const float ra = alpha / big, rt = tail / big;
-        const float norm = big * sqrtf(ra * ra + rt * rt);
-        beta = alpha >= 0.f ? -norm : norm;
-        tau = (beta - alpha) / beta;
-        scl = 1.f / (alpha - beta);
-      }
-      if (tau != 0.f)
-        for (int i = j + 1 + lane; i < rows; i += 32) colj[i] *= scl;
-      __syncwarp();
-      if (lane == 0) {
-        s_tau = tau;
-        s_beta[j] = beta;
-        colj[j] = 1.f;
-      }
-    }
-    __syncthreads();
-    const float tau = s_tau;
-    if (tau != 0.f) {
-      for (int c = j + 1 + warp; c < n; c += nwarps) {
-        float* colc = sm + (long long)c * rows;
-        float dot = 0.f;
-        for (int i = j + lane; i < rows; i += 32) dot += colj[i] * colc[i];
-        dot = warp_sum(dot) * tau;
-        for (int i = j + lane; i < rows; i += 32) colc[i] -= dot * colj[i];
-      }
-    }
-    __syncthreads();
-  }
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int i = t / n, c = t - i * n;
-    float v = 0.f;
-    if (i < kmax && c >= i) v = (c == i) ? s_beta[i] : sm[(long long)c * rows + i];
-    out[t] = v;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(512) k_tsqr_level(TsqrWork w, int B, int L, double* flops) {
-  extern __shared__ float sm[];
-  const int* off = w.offset + (long long)L * (B + 1);
-  const int total = off[B];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    int lo = 0, hi = B;  // off[lo] <= item < off[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (off[mid] <= item) lo = mid; else hi = mid;
-    }
-    const int b = lo;
-    const int c = item - off[b];
-    const TsqrProblem p = w.prob[b];
-    const int n = p.src.n;
-    int rowsL, C;
-    tsqr_level_shape(p, L, &rowsL, &C);
-    const int r0 = c * C;
-    const int rows = min(C, rowsL - r0);
-    const float* base;
-    long long rs, cs;
-    if (L == 0) {
-      base = p.src.p;
-      rs = p.src.rs;
-      cs = p.src.cs;
-    } else {
-      base = ((L - 1) & 1) ? p.stack1 : p.stack0;
-      rs = n;
-      cs = 1;
-    }
-    float* out = ((L & 1) ? p.stack1 : p.stack0) + (long long)c * n * n;
-    const long long cnt = (long long)rows * n;
-    if (cs == 1) {
-      for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int i = (int)(t / n), j = (int)(t - (long long)i * n);
-        sm[(long long)j * rows + i] = base[(r0 + i) * rs + j];
-      }
-    } else {
-      for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int j = (int)(t / rows), i = (int)(t - (long long)j * rows);
-        sm[(long long)j * rows + i] = base[(r0 + i) * rs + j * cs];
-      }
-    }
-    __syncthreads();
-    householder_chunk(sm, rows, n, out);
-    if (threadIdx.x == 0 && flops != nullptr) {
-      // Householder R factor: per column j a norm (2 (rows-j)) and a rank-1
-      // update of the n-j-1 trailing columns (4 (rows-j) each)
-      double f = 0.0;
-      const int kmax = rows < n ? rows : n;
-      for (int j = 0; j < kmax; ++j) f += (double)(rows - j) * (2.0 + 4.0 * (n - j - 1));
-      atomicAdd(flops, f);
-    }
-  }
 }
 
 // ------------------------------------------------------------ Jacobi SVD
@@ -693,26 +552,23 @@ __global__ void k_plan_stage(TsqrWork w, int B, int mode, int k, TTGeom g, const
       p.src.n = N0;
     }
     const int n = p.src.n;
-    int C = kSmemFloats / n;
-    if (C > p.src.M) C = p.src.M;
-    if (C < 1) C = 1;
-    p.chunk = C;
+    const long long M = p.src.M;
+    long long nsl = (M + tsqr_slice_rows(n) - 1) / tsqr_slice_rows(n);
+    const long long fit = stack_cap / ((long long)n * n);
+    if (nsl > fit) nsl = fit;
+    if (nsl > kTsqrMaxSlices) nsl = kTsqrMaxSlices;
+    if (nsl < 1) nsl = 1;
+    p.slice = (int)((M + nsl - 1) / nsl);
+    p.nslice = (int)((M + p.slice - 1) / p.slice);
+    p.nlev = p.nslice > 1 ? 2 : 1;
     p.stack0 = stack0 + (long long)b * stack_cap;
     p.stack1 = stack1 + (long long)b * stack_cap;
-    int rows = p.src.M, Cl = C, L = 0;
-    for (;; ++L) {
-      const int nch = (rows + Cl - 1) / Cl;
-      w.offset[(long long)L * (B + 1) + b] = nch;  // counts, scanned below
-      if (nch == 1 || L == kMaxLevels - 1) break;
-      rows = nch * n;
-      Cl = (C / n) * n;
-    }
-    p.nlev = L + 1;
-    for (int l = L + 1; l < kMaxLevels; ++l) w.offset[(long long)l * (B + 1) + b] = 0;
+    w.offset[b] = p.nslice;  // counts, scanned below
+    w.counter[b] = 0;
     w.prob[b] = p;
   }
   __syncthreads();
-  for (int L = 0; L < kMaxLevels; ++L) block_scan_inplace(w.offset + (long long)L * (B + 1), B);
+  block_scan_inplace(w.offset, B);
 }
 
 // Per filter: GEMM descriptors that apply the stage's small factors, then
@@ -773,12 +629,6 @@ void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g,
                                    stack_cap);
 }
 
-void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int levels, int grid, double* flops) {
-  count_launches(levels);
-  for (int L = 0; L < levels; ++L)
-    k_tsqr_level<<<grid, 512, kSmemFloats * sizeof(float), st>>>(w, B, L, flops);
-}
-
 void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
                    long long core0_cap, double* flops) {
@@ -808,8 +658,6 @@ void launch_scan_tiles(cudaStream_t st, GemmWork gw) {
 }
 
 void set_kernel_attributes() {
-  cudaFuncSetAttribute(k_tsqr_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kSmemFloats * (int)sizeof(float));
   cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kJacobiSmemFloats * (int)sizeof(float));
 }
