@@ -69,58 +69,67 @@ __device__ __forceinline__ void qr_load(float (&A)[kQrRPL][CPL], const float* p,
 }
 
 // Reflector H = I - tau v v^T (v_j = 1) that zeroes column j (register
-// column Q) below row j.  Executed by the whole owner warp; half `own` holds
-// the column.  Writes v and tau for the next step and leaves beta on the
+// column Q, so j >= 32 Q) below row j.  Executed by the whole owner warp;
+// half `own` holds the column.  Writes v (rows >= 32 Q; the rows above are
+// never read for this column group) and tau, and leaves beta on the
 // diagonal and zeros below it.
 template <int CPL, int Q>
 __device__ __forceinline__ void qr_reflector(float (&A)[kQrRPL][CPL], int j, int rl, bool own,
                                              float* v, float* tau_out) {
-  float ss = 0.f, mx = 0.f, alpha = 0.f;
+  constexpr int A0 = 2 * Q;
+  float s0 = 0.f, s1 = 0.f, alpha = 0.f;
 #pragma unroll
-  for (int a = 0; a < kQrRPL; ++a) {
+  for (int a = A0; a < kQrRPL; ++a) {
     const int i = rl + kQrRL * a;
     const float x = A[a][Q];
-    if (i > j) {
-      ss = fmaf(x, x, ss);
-      mx = fmaxf(mx, fabsf(x));
-    }
+    const float x2 = (i > j) ? x * x : 0.f;
+    if (a & 1) s1 += x2; else s0 += x2;
     if (i == j) alpha = x;
   }
+  float ss = s0 + s1;
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) {
-    ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
-  }
-  // squares of entries outside [1e-15, 1e15] could underflow or overflow:
-  // those columns take a second pass scaled by the column maximum
-  const bool rescale = mx >= kQrTiny && (mx < 1e-15f || mx > 1e15f);
-  float tail = (mx >= kQrTiny) ? sqrtf(ss) : 0.f;
+  for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  alpha = __shfl_sync(0xffffffffu, alpha, (threadIdx.x & 16) | (j & 15));
+  // |x|^2 sums are exact enough unless they leave [1e-30, 1e30]; such columns
+  // take a second pass scaled by the column maximum
+  const float tot = fmaf(alpha, alpha, ss);
+  const bool rescale = tot != 0.f && !(tot >= 1e-30f && tot <= 1e30f);
+  float nm = sqrtf(tot), tail2 = ss;
   if (__any_sync(0xffffffffu, rescale)) {
-    const float inv = rescale ? 1.f / mx : 0.f;
+    float mx = 0.f;
+#pragma unroll
+    for (int a = A0; a < kQrRPL; ++a) {
+      const int i = rl + kQrRL * a;
+      if (i >= j) mx = fmaxf(mx, fabsf(A[a][Q]));
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float inv = (rescale && mx >= kQrTiny) ? 1.f / mx : 0.f;
     float s2 = 0.f;
 #pragma unroll
-    for (int a = 0; a < kQrRPL; ++a) {
+    for (int a = A0; a < kQrRPL; ++a) {
       const int i = rl + kQrRL * a;
       const float x = A[a][Q] * inv;
       if (i > j) s2 = fmaf(x, x, s2);
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    if (rescale) tail = mx * sqrtf(s2);
+    if (rescale) {
+      const float al = alpha * inv;
+      nm = mx * sqrtf(fmaf(al, al, s2));
+      tail2 = s2;  // only its sign (zero or not) is used below
+    }
   }
   float tau = 0.f, beta = alpha, scl = 0.f;
-  if (tail > 0.f) {
-    const float big = fmaxf(fabsf(alpha), tail);
-    const float ra = alpha / big, rt = tail / big;
-    const float nm = big * sqrtf(ra * ra + rt * rt);
+  if (tail2 > 0.f) {
     beta = alpha >= 0.f ? -nm : nm;
-    tau = (beta - alpha) / beta;
-    scl = 1.f / (alpha - beta);
+    const float am = alpha - beta;  // sign(alpha) (|alpha| + nm): no cancellation
+    tau = -am / beta;                // (beta - alpha) / beta, in [1, 2]
+    scl = 1.f / am;
   }
   if (own) {
 #pragma unroll
-    for (int a = 0; a < kQrRPL; ++a) {
+    for (int a = A0; a < kQrRPL; ++a) {
       const int i = rl + kQrRL * a;
       const float x = A[a][Q];
       v[i] = (i > j) ? x * scl : (i == j ? 1.f : 0.f);
@@ -130,78 +139,108 @@ __device__ __forceinline__ void qr_reflector(float (&A)[kQrRPL][CPL], int j, int
   }
 }
 
-// Apply the reflector of column j (j in [32 Q0, 32 Q0 + 32)) to every
-// column after j.  Rows above 32 Q0 are zero in v and are skipped
-// statically; with R on top (`skipR`), so are the 16-row blocks strictly
-// between the current column group and row n, where R is known zero.
-template <int CPL, int Q0>
-__device__ __forceinline__ void qr_apply(float (&A)[kQrRPL][CPL], int j, int n, bool skipR, int rl,
-                                         int slot, const float* v, float tau) {
-  constexpr int A0 = 2 * Q0;
-  float vr[kQrRPL];
+// Row block a of the tile is skipped by every reflector of column group
+// Q0: rows above 32 Q0 are zero in v; with R on top of the tile (HASR), so
+// are the blocks strictly between the group and row 32 (CPL - 1) < n, where
+// R is known zero; blocks at or past NA hold no rows of this pass.
+template <int CPL, bool HASR, int NA, int Q0>
+__device__ __forceinline__ constexpr bool qr_skip(int a) {
+  return a < 2 * Q0 || a >= NA || (HASR && a >= 2 * Q0 + 2 && a < 2 * (CPL - 1));
+}
+
+// Reflector entries of this lane's rows for column group Q0.
+template <int CPL, bool HASR, int NA, int Q0>
+__device__ __forceinline__ void qr_vload(float (&vr)[kQrRPL], int rl, const float* v) {
 #pragma unroll
-  for (int a = A0; a < kQrRPL; ++a) vr[a] = v[rl + kQrRL * a];
-  float dot[CPL];
+  for (int a = 0; a < kQrRPL; ++a)
+    if (!qr_skip<CPL, HASR, NA, Q0>(a)) vr[a] = v[rl + kQrRL * a];
+}
+
+// Apply the reflector of column j (j in [32 Q0, 32 Q0 + 32)) to the
+// columns after j among register columns [QA, QB).
+template <int CPL, bool HASR, int NA, int Q0, int QA, int QB>
+__device__ __forceinline__ void qr_apply(float (&A)[kQrRPL][CPL], const float* v, int j, int rl,
+                                         int slot, float tau) {
+  if constexpr (QA < QB) {
+    float vr[kQrRPL];
+    qr_vload<CPL, HASR, NA, Q0>(vr, rl, v);
+    float dot[CPL];
 #pragma unroll
-  for (int q = Q0; q < CPL; ++q) dot[q] = 0.f;
+    for (int q = QA; q < QB; ++q) dot[q] = 0.f;
 #pragma unroll
-  for (int a = A0; a < kQrRPL; ++a) {
-    if (skipR && a >= A0 + 2 && kQrRL * a + kQrRL <= n) continue;
+    for (int a = 0; a < kQrRPL; ++a) {
+      if (qr_skip<CPL, HASR, NA, Q0>(a)) continue;
 #pragma unroll
-    for (int q = Q0; q < CPL; ++q) dot[q] = fmaf(vr[a], A[a][q], dot[q]);
-  }
+      for (int q = QA; q < QB; ++q) dot[q] = fmaf(vr[a], A[a][q], dot[q]);
+    }
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1)
+    for (int o = 8; o > 0; o >>= 1)
 #pragma unroll
-    for (int q = Q0; q < CPL; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+      for (int q = QA; q < QB; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
 #pragma unroll
-  for (int q = Q0; q < CPL; ++q) {
-    const int c = kQrSlots * q + slot;
-    dot[q] = (c > j) ? tau * dot[q] : 0.f;
-  }
+    for (int q = QA; q < QB; ++q) {
+      const int c = kQrSlots * q + slot;
+      dot[q] = (c > j) ? tau * dot[q] : 0.f;
+    }
 #pragma unroll
-  for (int a = A0; a < kQrRPL; ++a) {
-    if (skipR && a >= A0 + 2 && kQrRL * a + kQrRL <= n) continue;
+    for (int a = 0; a < kQrRPL; ++a) {
+      if (qr_skip<CPL, HASR, NA, Q0>(a)) continue;
 #pragma unroll
-    for (int q = Q0; q < CPL; ++q) A[a][q] = fmaf(-dot[q], vr[a], A[a][q]);
+      for (int q = QA; q < QB; ++q) A[a][q] = fmaf(-dot[q], vr[a], A[a][q]);
+    }
   }
 }
 
 // Steps j in [32 Q0, 32 Q0 + 32) of a pass (register column group Q0 is
-// static, so every register index below is static).
-template <int CPL, int Q0>
-__device__ __forceinline__ void qr_group(float (&A)[kQrRPL][CPL], int n, bool hasR, QrShared& sh,
-                                         int rl, int half, int warp, int slot) {
+// static, so every register index below is static).  The owner warp of
+// column j + 1 updates that register column first, forms the next
+// reflector, then updates its other columns, so the reflector's latency
+// overlaps the other warps' updates.
+template <int CPL, bool HASR, int NA, int Q0>
+__device__ __forceinline__ void qr_group(float (&A)[kQrRPL][CPL], int n, QrShared& sh, int rl,
+                                         int half, int warp, int slot) {
   for (int s = 0; s < kQrSlots; ++s) {
     const int j = kQrSlots * Q0 + s;
     if (j >= n) break;
     const int buf = j & 1;
     const float tau = sh.tau[buf];
-    if (tau != 0.f) qr_apply<CPL, Q0>(A, j, n, hasR, rl, slot, sh.v[buf], tau);
     const int jn = j + 1;
-    if (jn < n && warp == ((jn & 31) >> 1)) {
-      const bool own = half == (jn & 1);
+    const bool owner = jn < n && warp == ((jn & 31) >> 1);
+    const bool own = half == (jn & 1);
+    const float* v = sh.v[buf];
+    if (owner) {
       if (s + 1 < kQrSlots) {
+        if (tau != 0.f) qr_apply<CPL, HASR, NA, Q0, Q0, Q0 + 1>(A, v, j, rl, slot, tau);
         qr_reflector<CPL, Q0>(A, jn, rl, own, sh.v[buf ^ 1], &sh.tau[buf ^ 1]);
+        if (tau != 0.f) qr_apply<CPL, HASR, NA, Q0, Q0 + 1, CPL>(A, v, j, rl, slot, tau);
       } else if constexpr (Q0 + 1 < CPL) {
+        if (tau != 0.f) qr_apply<CPL, HASR, NA, Q0, Q0 + 1, Q0 + 2>(A, v, j, rl, slot, tau);
         qr_reflector<CPL, Q0 + 1>(A, jn, rl, own, sh.v[buf ^ 1], &sh.tau[buf ^ 1]);
+        if (tau != 0.f) {
+          qr_apply<CPL, HASR, NA, Q0, Q0, Q0 + 1>(A, v, j, rl, slot, tau);
+          qr_apply<CPL, HASR, NA, Q0, Q0 + 2, CPL>(A, v, j, rl, slot, tau);
+        }
       }
+    } else if (tau != 0.f) {
+      qr_apply<CPL, HASR, NA, Q0, Q0, CPL>(A, v, j, rl, slot, tau);
     }
     __syncthreads();
   }
   if constexpr (Q0 + 1 < CPL) {
-    if (kQrSlots * (Q0 + 1) < n) qr_group<CPL, Q0 + 1>(A, n, hasR, sh, rl, half, warp, slot);
+    if (kQrSlots * (Q0 + 1) < n) qr_group<CPL, HASR, NA, Q0 + 1>(A, n, sh, rl, half, warp, slot);
   }
 }
 
-// Householder QR of the tile's n columns; R ends in rows < n.
-template <int CPL>
-__device__ __forceinline__ void qr_pass(float (&A)[kQrRPL][CPL], int n, bool hasR, QrShared& sh) {
+// Householder QR of the tile's n columns; R ends in rows < n.  HASR: rows
+// < n already hold an upper triangular R.
+// NA: row blocks that hold rows of this pass (the rest are zero).
+template <int CPL, bool HASR, int NA>
+__device__ __forceinline__ void qr_pass(float (&A)[kQrRPL][CPL], int n, QrShared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rl = lane & 15, half = lane >> 4, slot = 2 * warp + half;
   if (warp == 0) qr_reflector<CPL, 0>(A, 0, rl, half == 0, sh.v[0], &sh.tau[0]);
   __syncthreads();
-  qr_group<CPL, 0>(A, n, hasR, sh, rl, half, warp, slot);
+  qr_group<CPL, HASR, NA, 0>(A, n, sh, rl, half, warp, slot);
 }
 
 // R factor of rows [row0, row0 + M) of (p, rs, cs), n columns, by passes;
@@ -214,13 +253,15 @@ __device__ __noinline__ void qr_rows(const float* p, long long rs, long long cs,
   float A[kQrRPL][CPL];
   qr_load<CPL>(A, p, rs, cs, row0, M, 0, n, rl, slot, coherent);
   long long done = M < kQrRows ? M : kQrRows;
-  bool hasR = false;
-  for (;;) {
-    qr_pass<CPL>(A, n, hasR, sh);
-    if (done >= M) break;
+  if (M <= kQrRows / 2) {
+    qr_pass<CPL, false, kQrRPL / 2>(A, n, sh);  // rows 128.. are zero
+  } else {
+    qr_pass<CPL, false, kQrRPL>(A, n, sh);
+  }
+  while (done < M) {
     qr_load<CPL>(A, p, rs, cs, row0 + done, M - done, n, n, rl, slot, coherent);
     done += kQrRows - n;
-    hasR = true;
+    qr_pass<CPL, true, kQrRPL>(A, n, sh);
   }
 #pragma unroll
   for (int a = 0; a < kQrRPL; ++a) {
