@@ -162,6 +162,8 @@ def run_fullgrid(args, model, mc, zs, W, K, dev, ttf):
         fg.update(comps, model.R, zs[k][0])
         fg.estimate()
     ms = 0.0
+    if args.profile_fullgrid:
+        torch.cuda.profiler.start()
     for i in range(K):
         flush.fill_(i & 0xFF)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -172,6 +174,8 @@ def run_fullgrid(args, model, mc, zs, W, K, dev, ttf):
         b.record(stream)
         torch.cuda.synchronize(dev)
         ms += a.elapsed_time(b)
+    if args.profile_fullgrid:
+        torch.cuda.profiler.stop()
     out = {"value": K / (ms * 1e-3), "unit": "filter-steps/s (one filter)", "dtype": "f32",
            "ms_per_step": ms / K}
     pk, src = peaks()
@@ -181,7 +185,7 @@ def run_fullgrid(args, model, mc, zs, W, K, dev, ttf):
                        "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": src,
                        "bytes_per_step": bytes_step}
     # the TT filter of the same run after the same W + K steps
-    if args.tt_error:
+    if not args.no_tt_error:
         P = fg.density()
         T = tt.densify(ttf.export_cores(0))
         out["tt_density_rel_fro_err"] = float(np.linalg.norm(T - P) / np.linalg.norm(P))
@@ -342,11 +346,13 @@ def main():
     ap.add_argument("--batch", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fullgrid", action="store_true")
-    ap.add_argument("--tt-error", action="store_true",
-                    help="also report the TT density error against the full-grid filter")
+    ap.add_argument("--no-tt-error", action="store_true",
+                    help="skip the TT density error against the full-grid filter")
     ap.add_argument("--profile-region", action="store_true",
-                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
-                         "--profile-from-start off)")
+                    help="bracket the timed TT steps with cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off; the run's own timings are then invalid)")
+    ap.add_argument("--profile-fullgrid", action="store_true",
+                    help="bracket the timed full-grid steps instead")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

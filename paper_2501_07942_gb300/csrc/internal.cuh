@@ -7,12 +7,13 @@
 //   * ranks: int32 [batch][d+1] on the device.  Every kernel reads the ranks
 //     it needs from there, so a filter step needs no host synchronisation and
 //     can be captured in a CUDA graph.
-//   * Small dense factors (Jacobi output P1/P2) use leading dimension kMaxN.
+//   * Small dense factors (SVD output P1/P2) use leading dimension kMaxN.
 //
 // The rounding of Sec. 4.1 ("round") is built from three generic pieces
-// driven by device-side work lists: a tree QR (TSQR) that returns only the R
-// factor of a tall matrix, a one-sided Jacobi SVD of that R, and a grouped
-// GEMM that applies the resulting small factors to the cores.
+// driven by device-side work lists: a tall-skinny QR (TSQR) that returns only
+// the R factor of a tall matrix, an SVD of that R (pivoted QR, then one-sided
+// Jacobi), and a grouped GEMM that applies the resulting small factors to the
+// cores.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
