@@ -761,6 +761,7 @@ int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior
   if (!attrs) {
     set_kernel_attributes();
     set_ttops_attributes();
+    set_tsqr_attributes();
     attrs = true;
   }
   ttgbf_ctx* c = new (std::nothrow) ttgbf_ctx();

@@ -21,7 +21,7 @@
 namespace ttgbf {
 
 constexpr int kMaxN = 160;          // largest column count of a TSQR / SVD problem
-constexpr int kTsqrTileRows = 256;  // rows of the register-resident QR tile
+constexpr int kTsqrTileRows = 128;  // rows per register block of the TSQR kernel
 constexpr int kTsqrMaxSlices = 64;  // row slices (CTAs) per TSQR problem
 constexpr int kJacobiSmemFloats = 2 * kMaxN * kMaxN + 8 * kMaxN;  // SVD kernel
 constexpr int kMaxD = 16;           // largest state dimension
@@ -54,10 +54,10 @@ struct TsqrWork {
   int* counter;       // [B] slices finished (reset by the plan kernel)
 };
 
-// Rows per slice for an n-column problem: the first pass of a slice takes a
-// full tile and each later pass kTsqrTileRows - n new rows; eight later passes.
+// Rows per slice of an n-column problem: eight register blocks.
 __host__ __device__ inline long long tsqr_slice_rows(int n) {
-  return kTsqrTileRows + 8LL * (kTsqrTileRows - n);
+  (void)n;
+  return 8LL * kTsqrTileRows;
 }
 
 // Row-major GEMM C (m x n) = A (m x k) * B (k x n).
@@ -155,5 +155,6 @@ void count_launches(int n);
 // Function attributes (large dynamic shared memory); call once per process.
 void set_kernel_attributes();
 void set_ttops_attributes();
+void set_tsqr_attributes();
 
 }  // namespace ttgbf
