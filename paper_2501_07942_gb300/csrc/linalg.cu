@@ -56,15 +56,18 @@ __device__ void block_scan_inplace(int* o, int n) {
 }
 
 // ------------------------------------------------------------ Jacobi SVD
-// Pair k of round r of the circle method on npad (even) columns.
+// Pair k of round r (k < npad / 2, r < npad - 1) of the circle method on
+// npad (even) columns; the sums below stay under 2 m, so one conditional
+// subtraction replaces the modulo.
 __device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int* q) {
   const int m = npad - 1;
   if (k == 0) {
     *p = 0;
-    *q = 1 + (r % m);
+    *q = 1 + r;
   } else {
-    *p = 1 + ((k + r) % m);
-    *q = 1 + ((m - k + r) % m);
+    const int a = k + r, b = m - k + r;
+    *p = 1 + (a >= m ? a - m : a);
+    *q = 1 + (b >= m ? b - m : b);
   }
 }
 
@@ -74,11 +77,12 @@ __device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int*
 __device__ float block_sum_f(float v, float* red) {
   v = warp_sum(v);
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  float t = 0.f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-  return t;
+  // every warp reduces the per-warp partials itself (same order in every
+  // warp, so every thread gets the same value)
+  return warp_sum(lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f);
 }
 
 // SVD of the n x n R factor of problem b, in three steps:
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   __shared__ float s_redf[32];
   __shared__ int s_redi[32];
   __shared__ float s_tau;
-  __shared__ int s_piv, s_rot, s_rank, s_stop;
+  __shared__ int s_rot, s_rank;
   __shared__ double s_flops;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
         bi = c;
       }
     }
-    rem = block_sum_f(rem, s_red);
+    rem = warp_sum(rem);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float ov = __shfl_xor_sync(0xffffffffu, best, o);
@@ -173,24 +177,27 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
       }
     }
     if (lane == 0) {
+      s_red[warp] = rem;
       s_redf[warp] = best;
       s_redi[warp] = bi;
     }
     __syncthreads();
-    if (tid == 0) {
-      float bv = s_redf[0];
-      int bx = s_redi[0];
-      for (int q = 1; q < nwarps; ++q)
-        if (s_redf[q] > bv || (s_redf[q] == bv && s_redi[q] < bx)) {
-          bv = s_redf[q];
-          bx = s_redi[q];
-        }
-      s_piv = bx;
-      s_stop = (k > 0 && (double)rem <= stop2) || bx >= n;
+    // every warp reduces the per-warp partials (same result everywhere); the
+    // next writes of these arrays come after later barriers of this step
+    rem = warp_sum(lane < nwarps ? s_red[lane] : 0.f);
+    best = lane < nwarps ? s_redf[lane] : -1.f;
+    bi = lane < nwarps ? s_redi[lane] : n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
     }
-    __syncthreads();
-    if (s_stop) break;
-    const int pv = s_piv;
+    if ((k > 0 && (double)rem <= stop2) || bi >= n) break;
+    const int pv = bi;
     if (pv != k) {
       for (int i = tid; i < n; i += blockDim.x) {
         const float x = A[k * n + i];
@@ -285,8 +292,10 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
     if (tid == 0) s_rot = 0;
     __syncthreads();
     float tnorm = 0.f;
-    for (int c = 0; c < kp; ++c) tnorm += nrm[c];
+    for (int c = lane; c < kp; c += 32) tnorm += nrm[c];
+    tnorm = warp_sum(tnorm);
     const float floor2 = 1e-14f * tnorm;
+    int myrot = 0;
     for (int r = 0; r < npad - 1; ++r) {
       for (int q = warp; q < npad / 2; q += nwarps) {
         int pp, qq;
@@ -299,9 +308,12 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
         g = warp_sum(g);
         const float al = nrm[pp], be = nrm[qq];
         if (g == 0.f || fminf(al, be) <= floor2 || !(fabsf(g) > tol * sqrtf(al * be))) continue;
-        const float zeta = (be - al) / (2.f * g);
+        // rotation parameters need not be correctly rounded: (cth, sth)
+        // below is orthogonal for any tt
+        const float zeta = __fdividef(be - al, 2.f * g);
         const float az = fabsf(zeta);
-        const float tt = (az > 1e15f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta))) *
+        const float tt = (az > 1e15f ? __fdividef(0.5f, az)
+                                     : __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f)))) *
                          (zeta >= 0.f ? 1.f : -1.f);
         const float cth = rsqrtf(1.f + tt * tt);
         const float sth = cth * tt;
@@ -314,18 +326,19 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
         if (lane == 0) {
           nrm[pp] = al - tt * g;
           nrm[qq] = be + tt * g;
-          atomicAdd(&s_rot, 1);
         }
+        ++myrot;
       }
       __syncthreads();
     }
+    if (lane == 0 && myrot > 0) atomicAdd(&s_rot, myrot);
+    const int any = __syncthreads_or(myrot > 0);
     if (tid == 0) {
       const double nn = (double)n;
       s_flops += 0.5 * kp * (kp - 1.0) * 2.0 * nn + (double)s_rot * 6.0 * nn + 2.0 * nn * kp;
     }
-    const int rot = s_rot;
     __syncthreads();
-    if (rot == 0) break;
+    if (!any) break;
   }
   // singular values and their order
   for (int c = warp; c < kp; c += nwarps) {
