@@ -25,7 +25,7 @@ constexpr int kTsqrTileRows = 128;  // rows per register block of the TSQR kerne
 constexpr int kTsqrMaxSlices = 64;  // row slices (CTAs) per TSQR problem
 constexpr int kJacobiSmemFloats = 2 * kMaxN * kMaxN + 8 * kMaxN;  // SVD kernel
 constexpr int kMaxD = 16;           // largest state dimension
-constexpr int kTile = 64;           // GEMM tile edge
+constexpr int kTile = 64;           // GEMM square tile edge
 
 // A strided matrix view: element (i, j) at p[i * rs + j * cs], i < M, j < n.
 struct MatView {
@@ -60,12 +60,14 @@ __host__ __device__ inline long long tsqr_slice_rows(int n) {
   return 8LL * kTsqrTileRows;
 }
 
-// Row-major GEMM C (m x n) = A (m x k) * B (k x n).
+// Row-major GEMM C (m x n) = A (m x k) * B (k x n).  `shape` (the tile
+// shape) is chosen by the tile scan from m and n.
 struct GemmDesc {
   const float* A;
   const float* B;
   float* C;
   int m, n, k, lda, ldb, ldc;
+  int shape;
 };
 
 struct GemmWork {

@@ -456,11 +456,92 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
 }
 
 // ------------------------------------------------------------------ GEMM
-__global__ void __launch_bounds__(256) k_gemm_grouped(GemmWork w, double* flops) {
-  __shared__ float As[16][kTile + 4];
-  __shared__ float Bs[16][kTile + 4];
+// Tile shapes (rows x columns) of the grouped GEMM.  The rounding's products
+// are tall-skinny or short-wide (one side is a rank <= 160, often 16), so a
+// descriptor with n <= 32 takes 128 x 32 tiles and one with m <= 32 takes
+// 32 x 128 tiles; the rest take 64 x 64.  256 threads, 4 x 4 outputs each.
+__host__ __device__ constexpr int gemm_bm(int shape) { return shape == 1 ? 128 : (shape == 2 ? 32 : 64); }
+__host__ __device__ constexpr int gemm_bn(int shape) { return shape == 1 ? 32 : (shape == 2 ? 128 : 64); }
+__device__ __forceinline__ int gemm_shape(int m, int n) { return n <= 32 ? 1 : (m <= 32 ? 2 : 0); }
+
+constexpr int kGemmK = 16;          // k per shared-memory stage
+constexpr int kGemmPitch = 128 + 4;  // floats per k-row of a tile (16-byte aligned rows)
+
+// One BM x BN tile of C = A B, k in chunks of 16 through shared memory with
+// the next chunk's global loads issued before the current chunk's FMAs.
+template <int BM, int BN>
+__device__ __forceinline__ void gemm_tile(const GemmDesc& g, int row0, int col0, float (*As)[kGemmPitch],
+                                          float (*Bs)[kGemmPitch]) {
+  constexpr int TX = BN / 4;           // threads along n
+  constexpr int LA = BM * kGemmK / 256;  // A elements per thread per chunk
+  constexpr int LB = BN * kGemmK / 256;  // B elements per thread per chunk
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  float ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      const int ar = e / kGemmK, ak = e % kGemmK;
+      const int gr = row0 + ar, gk = k0 + ak;
+      ra[q] = (gr < g.m && gk < g.k) ? __ldg(g.A + (long long)gr * g.lda + gk) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      const int bk = e / BN, bc = e % BN;
+      const int hk = k0 + bk, hc = col0 + bc;
+      rb[q] = (hk < g.k && hc < g.n) ? __ldg(g.B + (long long)hk * g.ldb + hc) : 0.f;
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < g.k; k0 += kGemmK) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      As[e % kGemmK][e / kGemmK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      Bs[e / BN][e % BN] = rb[q];
+    }
+    __syncthreads();
+    if (k0 + kGemmK < g.k) fetch(k0 + kGemmK);
+#pragma unroll
+    for (int kk = 0; kk < kGemmK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 bq = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty * 4 + i;
+    if (r >= g.m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx * 4 + j;
+      if (c < g.n) g.C[(long long)r * g.ldc + c] = acc[i][j];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_gemm_grouped(GemmWork w, double* flops) {
+  __shared__ __align__(16) float As[kGemmK][kGemmPitch];
+  __shared__ __align__(16) float Bs[kGemmK][kGemmPitch];
   const int total = w.tiles[w.ndesc];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int lo = 0, hi = w.ndesc;
     while (hi - lo > 1) {
@@ -468,62 +549,28 @@ __global__ void __launch_bounds__(256) k_gemm_grouped(GemmWork w, double* flops)
       if (w.tiles[mid] <= t) lo = mid; else hi = mid;
     }
     const GemmDesc g = w.desc[lo];
-    const int tn_count = (g.n + kTile - 1) / kTile;
+    const int bm = gemm_bm(g.shape), bn = gemm_bn(g.shape);
+    const int tn_count = (g.n + bn - 1) / bn;
     const int local = t - w.tiles[lo];
     const int tm = local / tn_count, tn = local - tm * tn_count;
-    const int row0 = tm * kTile, col0 = tn * kTile;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < g.k; k0 += 16) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = threadIdx.x + 256 * q;
-        const int ar = e >> 4, ak = e & 15;
-        const int gr = row0 + ar, gk = k0 + ak;
-        As[ak][ar] = (gr < g.m && gk < g.k) ? g.A[(long long)gr * g.lda + gk] : 0.f;
-        const int bk = e >> 6, bc = e & 63;
-        const int hk = k0 + bk, hc = col0 + bc;
-        Bs[bk][bc] = (hk < g.k && hc < g.n) ? g.B[(long long)hk * g.ldb + hc] : 0.f;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        float a[4], bv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
-      }
-      __syncthreads();
-    }
+    const int row0 = tm * bm, col0 = tn * bn;
+    if (g.shape == 1) gemm_tile<128, 32>(g, row0, col0, As, Bs);
+    else if (g.shape == 2) gemm_tile<32, 128>(g, row0, col0, As, Bs);
+    else gemm_tile<64, 64>(g, row0, col0, As, Bs);
     if (threadIdx.x == 0 && flops != nullptr) {
-      const int tm_rows = min(kTile, g.m - row0), tn_cols = min(kTile, g.n - col0);
+      const int tm_rows = min(bm, g.m - row0), tn_cols = min(bn, g.n - col0);
       atomicAdd(flops, 2.0 * tm_rows * tn_cols * (double)g.k);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = row0 + ty * 4 + i;
-      if (r >= g.m) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = col0 + tx * 4 + j;
-        if (c < g.n) g.C[(long long)r * g.ldc + c] = acc[i][j];
-      }
     }
   }
 }
 
 __global__ void k_scan_tiles(GemmWork w) {
   for (int i = threadIdx.x; i < w.ndesc; i += blockDim.x) {
-    const GemmDesc g = w.desc[i];
-    w.tiles[i] = (g.m > 0 && g.n > 0) ? ((g.m + kTile - 1) / kTile) * ((g.n + kTile - 1) / kTile) : 0;
+    GemmDesc& g = w.desc[i];
+    const int sh = gemm_shape(g.m, g.n);
+    g.shape = sh;
+    const int bm = gemm_bm(sh), bn = gemm_bn(sh);
+    w.tiles[i] = (g.m > 0 && g.n > 0) ? ((g.m + bm - 1) / bm) * ((g.n + bn - 1) / bn) : 0;
   }
   __syncthreads();
   block_scan_inplace(w.tiles, w.ndesc);
