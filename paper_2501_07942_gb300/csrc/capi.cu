@@ -142,7 +142,7 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   L.stack[1] = a.take<float>((size_t)B * stack);
   L.P1 = a.take<float>((size_t)B * kMaxN * kMaxN);
   L.P2 = a.take<float>((size_t)B * kMaxN * kMaxN);
-  L.gdesc_cap = std::max(2 * B, B * capr);
+  L.gdesc_cap = std::max(2 * B, B * (capr + 1));
   L.gdesc = a.take<GemmDesc>(L.gdesc_cap);
   L.gtiles = a.take<int>(L.gdesc_cap + 1);
   L.awork_stride = (long long)(d + 1) * 3 * kMaxN * kMaxN;
@@ -211,6 +211,9 @@ struct ttgbf_ctx {
   bool fuse = true;
   bool poisoned = false;
   bool expanded = false;  // ranks may exceed rank_cap (after an unrounded shear or import)
+  // virt_S[k] > 0: core k is a middle core of the shear block being rounded
+  // and still holds its unexpanded data (its expanded form is G (x) I_S)
+  int virt_S[kMaxD] = {};
   // Mixed canonical form: when canon is true, cores < center are left-
   // orthonormal and cores > center right-orthonormal (the center holds the norm).
   bool canon = false;
@@ -317,10 +320,12 @@ void stage(ttgbf_ctx* c, int mode, int k, int first) {
     launch_svd(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1, c->P2,
                   core0_alt, c->L.core_cap[0], flops_of(c, kPSvd));
   }
-  int ka, kb, ndesc = 2 * B;
+  int ka, kb, ndesc = 2 * B, vS = 0;
   if (mode == kStageRight) {
     ka = k;
     kb = k - 1;
+    vS = c->virt_S[kb];
+    if (vS > 0) ndesc = B * (c->capr + 1);
   } else if (mode == kStageLeft) {
     ka = k;
     kb = k + 1;
@@ -334,8 +339,9 @@ void stage(ttgbf_ctx* c, int mode, int k, int first) {
     Prof p(c, kPPlan, 2);
     launch_plan_gemm_stage(c->st, B, mode, k, c->geom, c->ranks, c->newrank, curp(c, ka), altp(c, ka),
                            curp(c, kb), altp(c, kb), c->P1, c->P2, c->W, c->L.W_cap,
-                           c->d > 1 ? c->n[1] : 1, gw);
+                           c->d > 1 ? c->n[1] : 1, gw, vS, c->capr + 1);
   }
+  c->virt_S[kb] = 0;  // written densely by this stage's second product
   {
     Prof p(c, kPGemm, 1);
     launch_gemm(c->st, gw, c->sms * 8, flops_of(c, kPGemm));
@@ -595,15 +601,24 @@ void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts
     curv[k] = curp(c, k);
     altv[k] = altp(c, k);
   }
+  // With rounding, the middle cores (G (x) I_S) are never written out: the
+  // right-to-left sweep's products with them use their structure.
+  const int virt = do_round ? 1 : 0;
   {
     Prof p(c, kPShear, 1);
-    launch_shear_expand(c->st, c->B, c->geom, m, n, S, tmin, wts, curv, altv, c->ranks);
+    launch_shear_expand(c->st, c->B, c->geom, m, n, S, tmin, wts, curv, altv, c->ranks, virt);
   }
   {
     Prof p(c, kPOther, 1);
     launch_rank_scale(c->st, c->B, c->d, c->ranks, lo, hi, S);
   }
-  for (int k = lo; k <= hi; ++k) c->cur[k] ^= 1;
+  for (int k = lo; k <= hi; ++k) {
+    if (virt && k > lo && k < hi) {
+      c->virt_S[k] = S;
+    } else {
+      c->cur[k] ^= 1;
+    }
+  }
   if (!do_round) {
     c->expanded = true;
     c->canon = false;

@@ -107,7 +107,8 @@ void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, doub
 void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
                             const int* newrank, const float* cur_a, float* alt_a,
                             const float* cur_b, float* alt_b, const float* P1, const float* P2,
-                            const float* W, long long W_cap, int N1, GemmWork gw);
+                            const float* W, long long W_cap, int N1, GemmWork gw, int vS,
+                            int dstride);
 void launch_gemm(cudaStream_t st, GemmWork gw, int grid, double* flops);
 // Tile prefix for descriptors already written to gw.desc (ndesc entries).
 void launch_scan_tiles(cudaStream_t st, GemmWork gw);
@@ -117,7 +118,7 @@ void launch_prior(cudaStream_t st, int B, const TTGeom& g, float* const* cores, 
                   const double* axes, const double* mean, const double* var);
 void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, int S, int tmin,
                          const float* weights, float* const* cur, float* const* alt,
-                         const int* ranks);
+                         const int* ranks, int virt);
 void launch_rank_scale(cudaStream_t st, int B, int d, int* ranks, int lo, int hi, int S);
 void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, const int* ranks,
                             const float* M, const float* cur, float* alt, GemmWork gw, int cap_in);

@@ -633,10 +633,15 @@ __global__ void k_plan_stage(TsqrWork w, int B, int mode, int k, TTGeom g, const
 
 // Per filter: GEMM descriptors that apply the stage's small factors, then
 // the rank update.
+// vS > 0 (RIGHT only): core k-1 is the middle core of a shear block kept in
+// its unexpanded form G (r x n x r'); its expanded form is G (x) I_vS on both
+// links (index a vS + u), so core k-1 x P2 splits into one (n x r') x
+// (r' x rn) product per (a, u) with the rows b vS + u of P2.  Filter b's
+// descriptors then start at b * dstride.
 __global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, const int* newrank,
                                   const float* cur_a, float* alt_a, const float* cur_b, float* alt_b,
                                   const float* P1, const float* P2, const float* W, long long W_cap,
-                                  int N1, GemmWork gw) {
+                                  int N1, GemmWork gw, int vS, int dstride) {
   const int d = g.d;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     int* rk = ranks + (long long)b * (d + 1);
@@ -649,10 +654,26 @@ __global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, 
       const int cols = g.n[k] * r1;
       GemmDesc x{p1, cur_a + (long long)b * g.cap[k], alt_a + (long long)b * g.cap[k], rn, cols, rkk,
                  kMaxN, cols, cols};
-      GemmDesc y{cur_b + (long long)b * g.cap[k - 1], p2, alt_b + (long long)b * g.cap[k - 1],
-                 rm * g.n[k - 1], rn, rkk, rkk, kMaxN, rn};
-      gw.desc[2 * b] = x;
-      gw.desc[2 * b + 1] = y;
+      if (vS > 0) {
+        const int Nm = g.n[k - 1], rmt = rm / vS, rkt = rkk / vS;
+        GemmDesc* dd = gw.desc + (long long)b * dstride;
+        dd[0] = x;
+        for (int q = 0; q + 1 < dstride; ++q) {
+          GemmDesc y{nullptr, nullptr, nullptr, 0, 0, 0, 1, 1, 1};
+          if (q < rm) {
+            const int a = q / vS, u = q - a * vS;
+            y = GemmDesc{cur_b + (long long)b * g.cap[k - 1] + (long long)a * Nm * rkt, p2 + u * kMaxN,
+                         alt_b + (long long)b * g.cap[k - 1] + (long long)q * Nm * rn, Nm, rn, rkt,
+                         rkt, vS * kMaxN, rn};
+          }
+          dd[1 + q] = y;
+        }
+      } else {
+        GemmDesc y{cur_b + (long long)b * g.cap[k - 1], p2, alt_b + (long long)b * g.cap[k - 1],
+                   rm * g.n[k - 1], rn, rkk, rkk, kMaxN, rn};
+        gw.desc[2 * b] = x;
+        gw.desc[2 * b + 1] = y;
+      }
       rk[k] = rn;
     } else if (mode == kStageLeft) {
       // a = core k ((r_k n_k) x r_{k+1}), b = core k+1 (r_{k+1} x n_{k+1} r_{k+2})
@@ -700,10 +721,11 @@ void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, doub
 void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
                             const int* newrank, const float* cur_a, float* alt_a,
                             const float* cur_b, float* alt_b, const float* P1, const float* P2,
-                            const float* W, long long W_cap, int N1, GemmWork gw) {
+                            const float* W, long long W_cap, int N1, GemmWork gw, int vS,
+                            int dstride) {
   count_launches(2);
   k_plan_gemm_stage<<<1, 1024, 0, st>>>(B, mode, k, g, ranks, newrank, cur_a, alt_a, cur_b, alt_b, P1,
-                                        P2, W, W_cap, N1, gw);
+                                        P2, W, W_cap, N1, gw, vS, dstride);
   k_scan_tiles<<<1, 1024, 0, st>>>(gw);
 }
 

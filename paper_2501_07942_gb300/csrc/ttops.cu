@@ -44,52 +44,56 @@ __global__ void k_prior(int B, TTGeom g, CorePtrs cores, int* ranks, const doubl
 //   core hi : (r_hi S,   N, r_hi+1)
 // The shifted side is mode m, the weighted side mode n.
 __global__ void k_shear_expand(int B, TTGeom g, int m, int n, int S, int tmin, const float* wts,
-                               CorePtrs cur, CorePtrs alt, const int* ranks) {
+                               CorePtrs cur, CorePtrs alt, const int* ranks, int virt) {
   const int b = blockIdx.z;
   const int lo = m < n ? m : n, hi = m < n ? n : m;
-  const int l = lo + blockIdx.y;
+  // virt: the middle cores keep their unexpanded data (G (x) I_S implied)
+  const int l = virt ? (blockIdx.y == 0 ? lo : hi) : lo + blockIdx.y;
   if (b >= B || l > hi) return;
   const int* rk = ranks + (long long)b * (g.d + 1);
   const int a0 = rk[l], a1 = rk[l + 1];
   const int N = g.n[l];
   const int o0 = (l == lo) ? a0 : a0 * S;
   const int o1 = (l == hi) ? a1 : a1 * S;
-  const long long total = (long long)o0 * N * o1;
+  const int rows = o0 * N;  // < 2^31: at most 160 x 4096 (x 160 columns)
   const float* in = cur.p[l] + (long long)b * g.cap[l];
   float* out = alt.p[l] + (long long)b * g.cap[l];
   const bool shift_side = (l == m);
   const int Nn = g.n[n];
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(e / ((long long)N * o1));
-    const long long rem = e - (long long)x * N * o1;
-    const int i = (int)(rem / o1);
-    const int y = (int)(rem - (long long)i * o1);
-    float v = 0.f;
-    if (l == lo && l == hi) {
-      v = 0.f;  // not reachable: m != n
-    } else if (l == lo) {
-      const int beta = y / S, u = y - beta * S;
-      if (shift_side) {
-        const int src = i - (tmin + u);
-        if (src >= 0 && src < N) v = in[((long long)x * N + src) * a1 + beta];
-      } else {
-        v = wts[u * Nn + i] * in[((long long)x * N + i) * a1 + beta];
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  // one warp per output row (x, i); lanes along the row's o1 entries
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += gridDim.x * wpb) {
+    const int x = r / N, i = r - x * N;
+    float* orow = out + (long long)r * o1;
+    if (l == lo) {
+      // row x, entries (beta, u): beta < a1, u < S
+      for (int y = lane; y < o1; y += 32) {
+        const int beta = y / S, u = y - beta * S;
+        float v = 0.f;
+        if (shift_side) {
+          const int src = i - (tmin + u);
+          if (src >= 0 && src < N) v = in[((long long)x * N + src) * a1 + beta];
+        } else {
+          v = wts[u * Nn + i] * in[((long long)x * N + i) * a1 + beta];
+        }
+        orow[y] = v;
       }
     } else if (l == hi) {
       const int beta = x / S, u = x - beta * S;
-      if (shift_side) {
-        const int src = i - (tmin + u);
-        if (src >= 0 && src < N) v = in[((long long)beta * N + src) * a1 + y];
-      } else {
-        v = wts[u * Nn + i] * in[((long long)beta * N + i) * a1 + y];
-      }
+      const int src = shift_side ? i - (tmin + u) : i;
+      const bool ok = src >= 0 && src < N;
+      const float wv = shift_side ? 1.f : wts[u * Nn + i];
+      const float* irow = in + ((long long)beta * N + (ok ? src : 0)) * a1;
+      for (int y = lane; y < o1; y += 32) orow[y] = ok ? wv * irow[y] : 0.f;
     } else {
-      const int alpha = x / S, s = x - alpha * S;
-      const int beta = y / S, t = y - beta * S;
-      if (s == t) v = in[((long long)alpha * N + i) * a1 + beta];
+      const int alpha = x / S, s0 = x - alpha * S;
+      const float* irow = in + ((long long)alpha * N + i) * a1;
+      for (int y = lane; y < o1; y += 32) {
+        const int beta = y / S, t = y - beta * S;
+        orow[y] = (s0 == t) ? irow[beta] : 0.f;
+      }
     }
-    out[e] = v;
   }
 }
 
@@ -382,11 +386,12 @@ void launch_prior(cudaStream_t st, int B, const TTGeom& g, float* const* cores, 
 
 void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, int S, int tmin,
                          const float* weights, float* const* cur, float* const* alt,
-                         const int* ranks) {
+                         const int* ranks, int virt) {
   count_launches(1);
   const int lo = m < n ? m : n, hi = m < n ? n : m;
-  k_shear_expand<<<dim3(48, hi - lo + 1, B), 256, 0, st>>>(B, g, m, n, S, tmin, weights,
-                                                          to_ptrs(cur, g.d), to_ptrs(alt, g.d), ranks);
+  const int ny = virt ? 2 : hi - lo + 1;
+  k_shear_expand<<<dim3(16, ny, B), 256, 0, st>>>(B, g, m, n, S, tmin, weights, to_ptrs(cur, g.d),
+                                                 to_ptrs(alt, g.d), ranks, virt);
 }
 
 void launch_rank_scale(cudaStream_t st, int B, int d, int* ranks, int lo, int hi, int S) {
