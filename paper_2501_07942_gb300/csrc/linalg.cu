@@ -273,20 +273,31 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
     for (int c = kp + tid; c < n; c += blockDim.x) s += nrm[c];
     dropped2 = (double)block_sum_f(s, s_red);
   }
-  // ---- 2. Jacobi on the k' leading rows of R' as columns of length n
-  for (int t = tid; t < kp * n; t += blockDim.x) {
-    const int r = t / n, c = t - r * n;
-    M[r * n + c] = (c < r) ? 0.f : (c == r ? rdiag[r] : A[c * n + r]);
+  // ---- 2. Jacobi on the k' leading rows of R' as columns of length n,
+  // stored with stride ldm (128 or 160, zero padded) so that a lane holds
+  // 4 consecutive entries (16-byte shared loads and stores)
+  const int ldm = n <= 128 ? 128 : kMaxN;
+  const bool ext = ldm > 128;  // lanes 0..7 hold a second group of 4 (entries 128..159)
+  for (int t = tid; t < kp * ldm; t += blockDim.x) {
+    const int r = t / ldm, c = t - r * ldm;
+    M[t] = (c >= n || c < r) ? 0.f : (c == r ? rdiag[r] : A[c * n + r]);
   }
   for (int c = tid; c < n; c += blockDim.x) pinv[perm[c]] = c;
   __syncthreads();
+  auto col4 = [&](int c, int part) -> float4* {
+    return reinterpret_cast<float4*>(M + c * ldm) + (part ? 32 + lane : lane);
+  };
+  auto sq4 = [](const float4& x) { return x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w; };
+  auto col_norm2 = [&](int c) {
+    float s = sq4(*col4(c, 0));
+    if (ext && lane < 8) s += sq4(*col4(c, 1));
+    return warp_sum(s);
+  };
   const int npad = (kp + 1) & ~1;
   const float tol = 5e-7f * sqrtf((float)n);
   for (int sweep = 0; sweep < 40 && npad >= 2; ++sweep) {
     for (int c = warp; c < kp; c += nwarps) {
-      float s = 0.f;
-      for (int i = lane; i < n; i += 32) s += M[c * n + i] * M[c * n + i];
-      s = warp_sum(s);
+      const float s = col_norm2(c);
       if (lane == 0) nrm[c] = s;
     }
     if (tid == 0) s_rot = 0;
@@ -301,10 +312,14 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
         int pp, qq;
         jacobi_pair(q, r, npad, &pp, &qq);
         if (pp >= kp || qq >= kp) continue;
-        float* ap = M + pp * n;
-        float* aq = M + qq * n;
-        float g = 0.f;
-        for (int i = lane; i < n; i += 32) g += ap[i] * aq[i];
+        const float4 x0 = *col4(pp, 0), y0 = *col4(qq, 0);
+        float4 x1 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = x1;
+        if (ext && lane < 8) {
+          x1 = *col4(pp, 1);
+          y1 = *col4(qq, 1);
+        }
+        float g = x0.x * y0.x + x0.y * y0.y + x0.z * y0.z + x0.w * y0.w +
+                  (x1.x * y1.x + x1.y * y1.y + x1.z * y1.z + x1.w * y1.w);
         g = warp_sum(g);
         const float al = nrm[pp], be = nrm[qq];
         if (g == 0.f || fminf(al, be) <= floor2 || !(fabsf(g) > tol * sqrtf(al * be))) continue;
@@ -317,12 +332,14 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
                          (zeta >= 0.f ? 1.f : -1.f);
         const float cth = rsqrtf(1.f + tt * tt);
         const float sth = cth * tt;
-        for (int i = lane; i < n; i += 32) {
-          const float x = ap[i], y = aq[i];
-          ap[i] = cth * x - sth * y;
-          aq[i] = sth * x + cth * y;
-        }
-        __syncwarp();
+        auto rot = [&](const float4& x, const float4& y, float4* px, float4* py) {
+          *px = make_float4(cth * x.x - sth * y.x, cth * x.y - sth * y.y, cth * x.z - sth * y.z,
+                            cth * x.w - sth * y.w);
+          *py = make_float4(sth * x.x + cth * y.x, sth * x.y + cth * y.y, sth * x.z + cth * y.z,
+                            sth * x.w + cth * y.w);
+        };
+        rot(x0, y0, col4(pp, 0), col4(qq, 0));
+        if (ext && lane < 8) rot(x1, y1, col4(pp, 1), col4(qq, 1));
         if (lane == 0) {
           nrm[pp] = al - tt * g;
           nrm[qq] = be + tt * g;
@@ -342,9 +359,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   }
   // singular values and their order
   for (int c = warp; c < kp; c += nwarps) {
-    float s = 0.f;
-    for (int i = lane; i < n; i += 32) s += M[c * n + i] * M[c * n + i];
-    s = warp_sum(s);
+    const float s = col_norm2(c);
     if (lane == 0) nrm[c] = sqrtf(s);
   }
   __syncthreads();
@@ -365,7 +380,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   // ---- 3. orthonormal right singular vectors: Q[t] (column t of A, length n)
   for (int t = 0; t < kp; ++t) {
     float* qt = A + t * n;
-    const float* src = M + ord[t] * n;
+    const float* src = M + ord[t] * ldm;
     const float st = sig[t];
     const float inv = st >= kTiny ? 1.f / st : 0.f;
     for (int i = tid; i < n; i += blockDim.x) qt[i] = src[i] * inv;
