@@ -377,39 +377,6 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
     ord[pos] = c;
   }
   __syncthreads();
-  // ---- 3. orthonormal right singular vectors: Q[t] (column t of A, length n)
-  for (int t = 0; t < kp; ++t) {
-    float* qt = A + t * n;
-    const float* src = M + ord[t] * ldm;
-    const float st = sig[t];
-    const float inv = st >= kTiny ? 1.f / st : 0.f;
-    for (int i = tid; i < n; i += blockDim.x) qt[i] = src[i] * inv;
-    __syncthreads();
-    if (st >= kTiny) {
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int s = warp; s < t; s += nwarps) {
-          const float* qs = A + s * n;
-          float dot = 0.f;
-          for (int i = lane; i < n; i += 32) dot += qs[i] * qt[i];
-          dot = warp_sum(dot);
-          if (lane == 0) coef[s] = dot;
-        }
-        __syncthreads();
-        for (int i = tid; i < n; i += blockDim.x) {
-          float v = qt[i];
-          for (int s = 0; s < t; ++s) v -= coef[s] * A[s * n + i];
-          qt[i] = v;
-        }
-        __syncthreads();
-      }
-      float nq = 0.f;
-      for (int i = tid; i < n; i += blockDim.x) nq += qt[i] * qt[i];
-      nq = block_sum_f(nq, s_red);
-      const float sc = nq > 1e-20f ? rsqrtf(nq) : 0.f;  // a vector that cancelled is dropped
-      for (int i = tid; i < n; i += blockDim.x) qt[i] *= sc;
-      __syncthreads();
-    }
-  }
   if (tid == 0) {
     const double nn = (double)n;
     s_flops += 2.0 * nn * nn * kp + (double)kp * kp * 4.0 * nn * 2.0;
@@ -450,6 +417,87 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   }
   __syncthreads();
   const int r = s_rank;
+  // ---- 3. orthonormal right singular vectors of the kept rank:
+  // Q[t] = M[ord[t]] / sig[t] (column t of A, t < r), then one symmetric
+  // (Loewdin) correction Q <- Q (3 I - Q^T Q) / 2, which leaves Q^T Q = I to
+  // second order in the Jacobi residual; classical Gram-Schmidt applied
+  // twice if that residual is not small.  The factor pair the stage applies
+  // then multiplies to an exact projector.
+  for (int t = warp; t < r; t += nwarps) {
+    const float st = sig[t];
+    const float inv = st >= kTiny ? 1.f / st : 0.f;
+    const float* src = M + ord[t] * ldm;
+    for (int i = lane; i < n; i += 32) A[t * n + i] = src[i] * inv;
+  }
+  __syncthreads();
+  float* E = M;  // r x r Gram (ld r); M is free now
+  float dev = 0.f;
+  for (int q = warp; q < r * r; q += nwarps) {
+    const int s0 = q / r, t0 = q - s0 * r;
+    if (t0 < s0) continue;
+    float dt = 0.f;
+    for (int i = lane; i < n; i += 32) dt = fmaf(A[s0 * n + i], A[t0 * n + i], dt);
+    dt = warp_sum(dt);
+    if (lane == 0) {
+      E[s0 * r + t0] = dt;
+      E[t0 * r + s0] = dt;
+    }
+    const float dd = fabsf(dt - (s0 == t0 && sig[s0] >= kTiny ? 1.f : 0.f));
+    dev = (dd > dev || dd != dd) ? dd : dev;  // NaN propagates
+  }
+  // largest deviation from the identity, NaN counted as large
+  const int bad = __syncthreads_or(!(dev <= 1e-3f));
+  if (!bad) {
+    // rows of Q (r values each) times (3 I - E) / 2, one warp per row
+    for (int i = warp; i < n; i += nwarps) {
+      float acc[(kMaxN + 31) / 32];
+#pragma unroll
+      for (int m = 0; m < (kMaxN + 31) / 32; ++m) acc[m] = 0.f;
+      for (int s1 = 0; s1 < r; ++s1) {
+        const float v = A[s1 * n + i];
+#pragma unroll
+        for (int m = 0; m < (kMaxN + 31) / 32; ++m) {
+          const int t = lane + 32 * m;
+          if (t < r) acc[m] = fmaf(v, (s1 == t ? 1.5f : 0.f) - 0.5f * E[s1 * r + t], acc[m]);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < (kMaxN + 31) / 32; ++m) {
+        const int t = lane + 32 * m;
+        if (t < r) A[t * n + i] = acc[m];
+      }
+    }
+    __syncthreads();
+  } else {
+    for (int t = 0; t < r; ++t) {
+      float* qt = A + t * n;
+      if (sig[t] >= kTiny) {
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int s1 = warp; s1 < t; s1 += nwarps) {
+            const float* qs = A + s1 * n;
+            float dot = 0.f;
+            for (int i = lane; i < n; i += 32) dot += qs[i] * qt[i];
+            dot = warp_sum(dot);
+            if (lane == 0) coef[s1] = dot;
+          }
+          __syncthreads();
+          for (int i = tid; i < n; i += blockDim.x) {
+            float v = qt[i];
+            for (int s1 = 0; s1 < t; ++s1) v -= coef[s1] * A[s1 * n + i];
+            qt[i] = v;
+          }
+          __syncthreads();
+        }
+        float nq = 0.f;
+        for (int i = tid; i < n; i += blockDim.x) nq += qt[i] * qt[i];
+        nq = block_sum_f(nq, s_red);
+        const float sc = nq > 1e-20f ? rsqrtf(nq) : 0.f;  // a vector that cancelled is dropped
+        for (int i = tid; i < n; i += blockDim.x) qt[i] *= sc;
+        __syncthreads();
+      }
+    }
+  }
   float* p1 = P1 + (long long)b * kMaxN * kMaxN;
   float* p2 = P2 + (long long)b * kMaxN * kMaxN;
   for (int t = tid; t < n * r; t += blockDim.x) {
