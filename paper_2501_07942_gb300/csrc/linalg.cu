@@ -22,6 +22,12 @@ namespace {
 // FP32 denormal range, so that 1/x cannot overflow).
 constexpr float kTiny = 1e-30f;
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -152,41 +158,39 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   const double stop2 = (mode == kStageRight) ? 1e-14 * n * tot : 0.09 * delta * delta;
   const int kcap = (mode == kStageRight) ? n : min(n, rank_cap + 16);
 
-  // ---- 1. QR with column pivoting
-  int k = 0;
-  for (; k < kcap; ++k) {
-    float rem = 0.f;
-    float best = -1.f;
-    int bi = n;
-    for (int c = k + tid; c < n; c += blockDim.x) {
+  // ---- 1. QR with column pivoting.  Columns never move: perm[pos] is the
+  // physical column at pivot position pos, and R'(r, pos) = A[perm[pos] n + r].
+  // Two barriers per step: warp 0 picks the pivot and forms its reflector;
+  // then every warp updates its trailing columns, downdates their norms
+  // (recomputed when more than 99.9 % has cancelled) and leaves its part of
+  // the next pivot search.
+  float* nref = reinterpret_cast<float*>(ord + kMaxN);  // norm at the last recomputation
+  for (int c = tid; c < n; c += blockDim.x) nref[c] = nrm[c];
+  {
+    float rl = 0.f, bv = -1.f;
+    int bx = n;
+    for (int c = warp; c < n; c += nwarps) {  // same column split as the updates below
       const float v = nrm[c];
-      rem += v;
-      if (v > best || (v == best && c < bi)) {
-        best = v;
-        bi = c;
-      }
-    }
-    rem = warp_sum(rem);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
+      rl += v;
+      if (v > bv) {
+        bv = v;
+        bx = c;
       }
     }
     if (lane == 0) {
-      s_red[warp] = rem;
-      s_redf[warp] = best;
-      s_redi[warp] = bi;
+      s_red[warp] = rl;
+      s_redf[warp] = bv;
+      s_redi[warp] = bx;
     }
-    __syncthreads();
-    // every warp reduces the per-warp partials (same result everywhere); the
-    // next writes of these arrays come after later barriers of this step
-    rem = warp_sum(lane < nwarps ? s_red[lane] : 0.f);
-    best = lane < nwarps ? s_redf[lane] : -1.f;
-    bi = lane < nwarps ? s_redi[lane] : n;
+  }
+  __syncthreads();
+  int k = 0;
+  double dropped2 = 0.0;
+  for (;; ++k) {
+    // every warp reduces the per-warp partials (same result everywhere)
+    const float rem = warp_sum(lane < nwarps ? s_red[lane] : 0.f);
+    float best = lane < nwarps ? s_redf[lane] : -1.f;
+    int bi = lane < nwarps ? s_redi[lane] : n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float ov = __shfl_xor_sync(0xffffffffu, best, o);
@@ -196,52 +200,51 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
         bi = oi;
       }
     }
-    if ((k > 0 && (double)rem <= stop2) || bi >= n) break;
-    const int pv = bi;
-    if (pv != k) {
-      for (int i = tid; i < n; i += blockDim.x) {
-        const float x = A[k * n + i];
-        A[k * n + i] = A[pv * n + i];
-        A[pv * n + i] = x;
-      }
-      if (tid == 0) {
-        const int tp = perm[k];
-        perm[k] = perm[pv];
-        perm[pv] = tp;
-        const float tn = nrm[k];
-        nrm[k] = nrm[pv];
-        nrm[pv] = tn;
-      }
-    }
-    __syncthreads();
-    float* colk = A + k * n;
+    dropped2 = (double)rem;
+    if (k >= kcap || (k > 0 && (double)rem <= stop2) || bi >= n) break;
     if (warp == 0) {
-      float mx = 0.f;
-      for (int i = k + 1 + lane; i < n; i += 32) mx = fmaxf(mx, fabsf(colk[i]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      float sq = 0.f;
-      if (mx >= kTiny) {
-        const float inv = 1.f / mx;
+      const int pv = perm[bi];
+      __syncwarp();
+      if (lane == 0) {
+        perm[bi] = perm[k];
+        perm[k] = pv;
+      }
+      float* colk = A + pv * n;
+      float ss = 0.f;
+      for (int i = k + 1 + lane; i < n; i += 32) ss = fmaf(colk[i], colk[i], ss);
+      ss = warp_sum(ss);
+      const float alpha = colk[k];
+      float tot = fmaf(alpha, alpha, ss), tail2 = ss, scale = 1.f;
+      // squares are exact enough unless the sum leaves [1e-30, 1e30]; such
+      // columns take a second pass scaled by the column maximum
+      const bool rescale = tot != 0.f && !(tot >= 1e-30f && tot <= 1e30f);
+      if (rescale) {
+        float mx = 0.f;
+        for (int i = k + 1 + lane; i < n; i += 32) mx = fmaxf(mx, fabsf(colk[i]));
+        mx = fmaxf(warp_max(mx), fabsf(alpha));
+        const float inv = mx > 0.f ? 1.f / mx : 0.f;
+        float s2 = 0.f;
         for (int i = k + 1 + lane; i < n; i += 32) {
           const float x = colk[i] * inv;
-          sq += x * x;
+          s2 = fmaf(x, x, s2);
         }
+        s2 = warp_sum(s2);
+        const float al = alpha * inv;
+        tot = fmaf(al, al, s2);
+        tail2 = s2;
+        scale = mx;
       }
-      sq = warp_sum(sq);
-      const float alpha = colk[k];
-      const float tail = mx >= kTiny ? mx * sqrtf(sq) : 0.f;
       float tau = 0.f, beta = alpha, scl = 0.f;
-      if (tail > 0.f) {
-        const float big = fmaxf(fabsf(alpha), tail);
-        const float ra = alpha / big, rt = tail / big;
-        const float nm = big * sqrtf(ra * ra + rt * rt);
+      if (tail2 > 0.f && tot > 0.f) {
+        const float rs = rsqrtf(tot);
+        const float nm = tot * rs * scale;
+        const float aa = fabsf(alpha);
         beta = alpha >= 0.f ? -nm : nm;
-        tau = (beta - alpha) / beta;
-        scl = 1.f / (alpha - beta);
-      }
-      if (tau != 0.f)
+        tau = fmaf(aa / scale, rs, 1.f);  // (|alpha| + nm) / nm
+        const float am = aa + nm;
+        scl = alpha >= 0.f ? __frcp_rn(am) : -__frcp_rn(am);
         for (int i = k + 1 + lane; i < n; i += 32) colk[i] *= scl;
+      }
       __syncwarp();
       if (lane == 0) {
         s_tau = tau;
@@ -251,28 +254,43 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
     }
     __syncthreads();
     const float tau = s_tau;
+    const float* colk = A + perm[k] * n;
+    float rl = 0.f, bv = -1.f;
+    int bx = n;
     for (int c = k + 1 + warp; c < n; c += nwarps) {
-      float* colc = A + c * n;
+      const int pc = perm[c];
+      float* colc = A + pc * n;
       if (tau != 0.f) {
         float dot = 0.f;
-        for (int i = k + lane; i < n; i += 32) dot += colk[i] * colc[i];
+        for (int i = k + lane; i < n; i += 32) dot = fmaf(colk[i], colc[i], dot);
         dot = warp_sum(dot) * tau;
-        for (int i = k + lane; i < n; i += 32) colc[i] -= dot * colk[i];
+        for (int i = k + lane; i < n; i += 32) colc[i] = fmaf(-dot, colk[i], colc[i]);
+        __syncwarp();
       }
-      float sq = 0.f;
-      for (int i = k + 1 + lane; i < n; i += 32) sq += colc[i] * colc[i];
-      sq = warp_sum(sq);
-      if (lane == 0) nrm[c] = sq;
+      const float rk = colc[k];
+      float nr = nrm[pc] - rk * rk;
+      if (!(nr >= 1e-3f * nref[pc])) {  // cancelled (or NaN): recompute
+        float sq = 0.f;
+        for (int i = k + 1 + lane; i < n; i += 32) sq = fmaf(colc[i], colc[i], sq);
+        nr = warp_sum(sq);
+        if (lane == 0) nref[pc] = nr;
+      }
+      if (lane == 0) nrm[pc] = nr;
+      rl += nr;
+      if (nr > bv || (nr == bv && c < bx)) {
+        bv = nr;
+        bx = c;
+      }
+    }
+    if (lane == 0) {
+      s_red[warp] = rl;
+      s_redf[warp] = bv;
+      s_redi[warp] = bx;
     }
     __syncthreads();
   }
+  // dropped2: squared norm of the columns left over
   const int kp = k;  // >= 1
-  double dropped2 = 0.0;
-  {
-    float s = 0.f;
-    for (int c = kp + tid; c < n; c += blockDim.x) s += nrm[c];
-    dropped2 = (double)block_sum_f(s, s_red);
-  }
   // ---- 2. Jacobi on the k' leading rows of R' as columns of length n,
   // stored with stride ldm (128 or 160, zero padded) so that a lane holds
   // 4 consecutive entries (16-byte shared loads and stores)
@@ -280,7 +298,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   const bool ext = ldm > 128;  // lanes 0..7 hold a second group of 4 (entries 128..159)
   for (int t = tid; t < kp * ldm; t += blockDim.x) {
     const int r = t / ldm, c = t - r * ldm;
-    M[t] = (c >= n || c < r) ? 0.f : (c == r ? rdiag[r] : A[c * n + r]);
+    M[t] = (c >= n || c < r) ? 0.f : (c == r ? rdiag[r] : A[perm[c] * n + r]);
   }
   for (int c = tid; c < n; c += blockDim.x) pinv[perm[c]] = c;
   __syncthreads();
