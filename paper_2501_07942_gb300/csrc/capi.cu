@@ -308,7 +308,7 @@ void stage(ttgbf_ctx* c, int mode, int k, int first) {
   {
     Prof p(c, kPPlan, 1);
     launch_plan_stage(c->st, B, mode, k, c->geom, c->ranks, src, c->W, c->L.W_cap, c->n[0],
-                      c->d > 1 ? c->n[1] : 1, c->tw, c->stack[0], c->stack[1], c->L.stack_cap);
+                      c->d > 1 ? c->n[1] : 1, c->tw, c->stack[0], c->stack[1], c->L.stack_cap, 2 * c->sms);
   }
   {
     Prof p(c, kPTsqr, 1);

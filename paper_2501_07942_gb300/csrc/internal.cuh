@@ -98,7 +98,7 @@ struct TTGeom {
 // linalg.cu
 void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
-                       TsqrWork w, float* stack0, float* stack1, long long stack_cap);
+                       TsqrWork w, float* stack0, float* stack1, long long stack_cap, int slots);
 // tsqr.cu
 void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int grid, double* flops);
 void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,

@@ -661,7 +661,7 @@ __global__ void k_scan_tiles(GemmWork w) {
 // Per filter: the tall matrix of this stage and its TSQR schedule.
 __global__ void k_plan_stage(TsqrWork w, int B, int mode, int k, TTGeom g, const int* ranks,
                              const float* core_k, const float* W, long long W_cap, int N0, int N1,
-                             float* stack0, float* stack1, long long stack_cap) {
+                             float* stack0, float* stack1, long long stack_cap, int slots) {
   const int d = g.d;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const int* rk = ranks + (long long)b * (d + 1);
@@ -694,7 +694,12 @@ __global__ void k_plan_stage(TsqrWork w, int B, int mode, int k, TTGeom g, const
     }
     const int n = p.src.n;
     const long long M = p.src.M;
+    // slices of at least eight blocks, and no more per filter than the
+    // resident CTAs can run at once across the batch (fewer slice R
+    // factors to combine at the end)
     long long nsl = (M + tsqr_slice_rows(n) - 1) / tsqr_slice_rows(n);
+    const long long per = slots / B > 1 ? slots / B : 1;
+    if (nsl > per) nsl = per;
     const long long fit = stack_cap / ((long long)n * n);
     if (nsl > fit) nsl = fit;
     if (nsl > kTsqrMaxSlices) nsl = kTsqrMaxSlices;
@@ -785,10 +790,10 @@ __global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, 
 // -------------------------------------------------------------- launchers
 void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
-                       TsqrWork w, float* stack0, float* stack1, long long stack_cap) {
+                       TsqrWork w, float* stack0, float* stack1, long long stack_cap, int slots) {
   count_launches(1);
   k_plan_stage<<<1, 1024, 0, st>>>(w, B, mode, k, g, ranks, core_k, W, W_cap, N0, N1, stack0, stack1,
-                                   stack_cap);
+                                   stack_cap, slots);
 }
 
 void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
