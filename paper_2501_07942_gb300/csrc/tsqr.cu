@@ -4,7 +4,7 @@
 //
 // A CTA of 8 warps keeps the n x n upper-triangular R of the rows it has
 // consumed in shared memory (zero at the start) and takes the rows in blocks
-// of 128: lane (warp w, half h, row lane l) holds rows l + 16 a (a < 8) of
+// of 128: lane (warp w, half h, row lane l) holds rows 8 l + a (a < 8) of
 // the block for the columns 16 q + 2 w + h (q < ceil(n / 16)).  Column j of
 // [R; block] is reduced by one reflector that touches only row j of R and
 // the block (R is triangular), so a block costs n steps of
@@ -40,7 +40,7 @@ constexpr int kQrMaxCPL = (kMaxN + kQrSlots - 1) / kQrSlots;
 static_assert(kQrMaxCPL <= 10, "register budget");
 constexpr int kQrLd = kMaxN;  // row stride of R in shared memory
 
-struct QrShared {
+struct __align__(16) QrShared {
   float v[2][kQrRows];
   float tau[2];
   int last;
@@ -56,7 +56,7 @@ __device__ __forceinline__ void qr_load(float (&A)[kQrRPL][CPL], const float* p,
   const long long qstep = (long long)kQrSlots * cs;
 #pragma unroll
   for (int a = 0; a < kQrRPL; ++a) {
-    const int i = rl + kQrRL * a;
+    const int i = rl * kQrRPL + a;
     const float* rowp = base + (long long)i * rs;
     const bool rok = i < nrows;
 #pragma unroll
@@ -126,11 +126,11 @@ __device__ __forceinline__ void qr_reflector(float (&A)[kQrRPL][CPL], int j, int
     scl = alpha >= 0.f ? __frcp_rn(am) : -__frcp_rn(am);
   }
   if (own) {
+    float4* v4 = reinterpret_cast<float4*>(v + rl * kQrRPL);
+    v4[0] = make_float4(A[0][Q] * scl, A[1][Q] * scl, A[2][Q] * scl, A[3][Q] * scl);
+    v4[1] = make_float4(A[4][Q] * scl, A[5][Q] * scl, A[6][Q] * scl, A[7][Q] * scl);
 #pragma unroll
-    for (int a = 0; a < kQrRPL; ++a) {
-      v[rl + kQrRL * a] = A[a][Q] * scl;
-      A[a][Q] = 0.f;
-    }
+    for (int a = 0; a < kQrRPL; ++a) A[a][Q] = 0.f;
     if (rl == 0) {
       *tau_out = tau;
       Rs[j * kQrLd + j] = beta;
@@ -145,19 +145,30 @@ __device__ __forceinline__ void qr_apply(float (&A)[kQrRPL][CPL], float* Rs, con
                                          int rl, int slot, float tau) {
   if constexpr (QA < QB) {
     float vr[kQrRPL];
-#pragma unroll
-    for (int a = 0; a < kQrRPL; ++a) vr[a] = v[rl + kQrRL * a];
-    float dot[CPL];
+    {
+      const float4* v4 = reinterpret_cast<const float4*>(v + rl * kQrRPL);
+      const float4 v0 = v4[0], v1 = v4[1];
+      vr[0] = v0.x; vr[1] = v0.y; vr[2] = v0.z; vr[3] = v0.w;
+      vr[4] = v1.x; vr[5] = v1.y; vr[6] = v1.z; vr[7] = v1.w;
+    }
+    // R(j, c) enters through row lane 0; columns of groups after Q0 all lie
+    // after j
+    float rj[CPL], dot[CPL];
 #pragma unroll
     for (int q = QA; q < QB; ++q) {
-      float d0 = 0.f, d1 = 0.f;
+      const int c = kQrSlots * q + slot;
+      const bool live = q > Q0 || c > j;
+      rj[q] = (rl == 0 && live) ? Rs[j * kQrLd + c] : 0.f;
+    }
+#pragma unroll
+    for (int q = QA; q < QB; ++q) {
+      float d0 = rj[q], d1 = 0.f;
 #pragma unroll
       for (int a = 0; a < kQrRPL; a += 2) {
         d0 = fmaf(vr[a], A[a][q], d0);
         d1 = fmaf(vr[a + 1], A[a + 1][q], d1);
       }
-      const int c = kQrSlots * q + slot;
-      dot[q] = d0 + d1 + ((rl == 0 && c > j) ? Rs[j * kQrLd + c] : 0.f);
+      dot[q] = d0 + d1;
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1)
@@ -166,8 +177,9 @@ __device__ __forceinline__ void qr_apply(float (&A)[kQrRPL][CPL], float* Rs, con
 #pragma unroll
     for (int q = QA; q < QB; ++q) {
       const int c = kQrSlots * q + slot;
-      const float f = (c > j) ? tau * dot[q] : 0.f;
-      if (c > j && rl == 0) Rs[j * kQrLd + c] -= f;
+      const bool live = q > Q0 || c > j;
+      const float f = live ? tau * dot[q] : 0.f;
+      if (live && rl == 0) Rs[j * kQrLd + c] = rj[q] - f;
 #pragma unroll
       for (int a = 0; a < kQrRPL; ++a) A[a][q] = fmaf(-f, vr[a], A[a][q]);
     }
