@@ -40,11 +40,30 @@ constexpr int kQrMaxCPL = (kMaxN + kQrSlots - 1) / kQrSlots;
 static_assert(kQrMaxCPL <= 10, "register budget");
 constexpr int kQrLd = kMaxN;  // row stride of R in shared memory
 
+// Reflectors rotate through four buffers: the owner of a column publishes
+// the next reflector and finishes its own other columns after the barrier,
+// so a reflector can still be read two steps later.
 struct __align__(16) QrShared {
-  float v[2][kQrRows];
-  float tau[2];
+  float v[4][kQrRows];
+  float tau[4];
   int last;
 };
+
+// Named barriers 1..3 (step j uses 1 + j % 3).  A warp that only arrives at
+// one step's barrier (the owner, which does not wait) is an owner for at
+// most two steps in a row, then waits at the next one, so no warp reaches
+// the same barrier id again before that barrier's previous use completed.
+__device__ __forceinline__ void qr_bar_sync(int id) {
+  static_assert(kQrThreads == 256, "barrier thread count");
+  if (id == 1) asm volatile("bar.sync 1, 256;" ::: "memory");
+  else if (id == 2) asm volatile("bar.sync 2, 256;" ::: "memory");
+  else asm volatile("bar.sync 3, 256;" ::: "memory");
+}
+__device__ __forceinline__ void qr_bar_arrive(int id) {
+  if (id == 1) asm volatile("bar.arrive 1, 256;" ::: "memory");
+  else if (id == 2) asm volatile("bar.arrive 2, 256;" ::: "memory");
+  else asm volatile("bar.arrive 3, 256;" ::: "memory");
+}
 
 // Rows [row0, row0 + 128) of (p, rs, cs) into the block, zero past nrows.
 // `coherent` loads bypass L1 (data written by other CTAs of this kernel).
@@ -194,29 +213,35 @@ __device__ __forceinline__ void qr_group(float (&A)[kQrRPL][CPL], int n, float* 
   for (int s = 0; s < kQrSlots; ++s) {
     const int j = kQrSlots * Q0 + s;
     if (j >= n) break;
-    const int buf = j & 1;
+    const int buf = j & 3, nbuf = (j + 1) & 3, bar = 1 + j % 3;
     const float tau = sh.tau[buf];
     const int jn = j + 1;
     const bool owner = jn < n && warp == ((jn & (kQrSlots - 1)) >> 1);
     const bool own = half == (jn & 1);
     const float* v = sh.v[buf];
     if (owner) {
+      // the owner's chain: update of column jn, its reflector, publish;
+      // its other columns are updated after it has arrived
       if (s + 1 < kQrSlots) {
         if (tau != 0.f) qr_apply<CPL, Q0, Q0, Q0 + 1>(A, Rs, v, j, rl, slot, tau);
-        qr_reflector<CPL, Q0>(A, jn, rl, own, Rs, sh.v[buf ^ 1], &sh.tau[buf ^ 1]);
+        qr_reflector<CPL, Q0>(A, jn, rl, own, Rs, sh.v[nbuf], &sh.tau[nbuf]);
+        qr_bar_arrive(bar);
         if (tau != 0.f) qr_apply<CPL, Q0, Q0 + 1, CPL>(A, Rs, v, j, rl, slot, tau);
       } else if constexpr (Q0 + 1 < CPL) {
         if (tau != 0.f) qr_apply<CPL, Q0, Q0 + 1, Q0 + 2>(A, Rs, v, j, rl, slot, tau);
-        qr_reflector<CPL, Q0 + 1>(A, jn, rl, own, Rs, sh.v[buf ^ 1], &sh.tau[buf ^ 1]);
+        qr_reflector<CPL, Q0 + 1>(A, jn, rl, own, Rs, sh.v[nbuf], &sh.tau[nbuf]);
+        qr_bar_arrive(bar);
         if (tau != 0.f) {
           qr_apply<CPL, Q0, Q0, Q0 + 1>(A, Rs, v, j, rl, slot, tau);
           qr_apply<CPL, Q0, Q0 + 2, CPL>(A, Rs, v, j, rl, slot, tau);
         }
+      } else {
+        qr_bar_sync(bar);  // not reached: jn < n <= 16 CPL
       }
-    } else if (tau != 0.f) {
-      qr_apply<CPL, Q0, Q0, CPL>(A, Rs, v, j, rl, slot, tau);
+    } else {
+      if (tau != 0.f) qr_apply<CPL, Q0, Q0, CPL>(A, Rs, v, j, rl, slot, tau);
+      qr_bar_sync(bar);
     }
-    __syncthreads();
   }
   if constexpr (Q0 + 1 < CPL) {
     if (kQrSlots * (Q0 + 1) < n) qr_group<CPL, Q0 + 1>(A, n, Rs, sh, rl, half, warp, slot);
