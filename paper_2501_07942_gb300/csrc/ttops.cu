@@ -226,8 +226,8 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
   double* u = f + (kMaxD + 2) * kMaxN;          // nc x kMaxN
   double* e = u + (kMaxD + 1) * kMaxN;          // kMaxN
   double* tmp = e + kMaxN;                      // kMaxN
-  double* acc = tmp + kMaxN;                    // 3 x 1024
-  double* red = acc + 3 * 1024;                 // 32
+  double* acc = tmp + kMaxN;                    // 9 x 1024 (group partials)
+  double* red = acc + 9 * 1024;                 // 32
   __shared__ double s_mean[kMaxD + 1];
   __shared__ double s_S[(kMaxD + 1) * (kMaxD + 1)];
   const int* rk = ranks + (long long)b * rstride;
@@ -244,27 +244,45 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
     const int npairs = r0 * r1;
     for (int pb = 0; pb < npairs; pb += 1024) {
       const int nb = min(1024, npairs - pb);
-      for (int t = threadIdx.x; t < 3 * 1024; t += blockDim.x) acc[t] = 0.0;
       __syncthreads();
-      const int groups = max(1, (int)blockDim.x / nb);
+      // groups of threads split the grid index of each (alpha, beta); FP32
+      // partial sums of at most ceil(N / groups) terms, combined in FP64
+      const int groups = max(1, min(3, (int)blockDim.x / nb));
       if ((int)threadIdx.x < nb * groups) {
         const int q = pb + (threadIdx.x % nb);
         const int grp = threadIdx.x / nb;
         const int al = q / r1, be = q - al * r1;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int i = grp; i < N; i += groups) {
-          const double v = (double)G[((long long)al * N + i) * r1 + be];
-          s0 += v;
+        // four interleaved FP32 partial sums each (a few dozen terms apiece)
+        float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* gp = G + (long long)al * N * r1 + be;
+        auto term = [&](int i, float& a0, float& a1, float& a2) {
+          const float v = gp[(long long)i * r1];
+          a0 += v;
           if (P > 1) {
-            const double x = ax[i] - c;
-            s1 += x * v;
-            s2 += x * x * v;
+            const float x = (float)(ax[i] - c);
+            a1 = fmaf(x, v, a1);
+            a2 = fmaf(x * x, v, a2);
           }
+        };
+        int i = grp;
+        for (; i + 3 * groups < N; i += 4 * groups) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) term(i + m * groups, s0[m], s1[m], s2[m]);
         }
-        atomicAdd(&acc[q - pb], s0);
+        for (; i < N; i += groups) term(i, s0[0], s1[0], s2[0]);
+        // one slot per (group, pair): no atomics
+        acc[grp * 1024 + (q - pb)] = ((double)s0[0] + s0[1]) + ((double)s0[2] + s0[3]);
         if (P > 1) {
-          atomicAdd(&acc[1024 + q - pb], s1);
-          atomicAdd(&acc[2048 + q - pb], s2);
+          acc[(3 + grp) * 1024 + (q - pb)] = ((double)s1[0] + s1[1]) + ((double)s1[2] + s1[3]);
+          acc[(6 + grp) * 1024 + (q - pb)] = ((double)s2[0] + s2[1]) + ((double)s2[2] + s2[3]);
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        for (int p = 0; p < P; ++p) {
+          double v = 0.0;
+          for (int g = 0; g < groups; ++g) v += acc[(3 * p + g) * 1024 + t];
+          acc[p * 1024 + t] = v;  // slot (3 p) * 1024 + t is only read by this thread
         }
       }
       __syncthreads();
@@ -276,17 +294,14 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
   }
   __syncthreads();
 
+  // every warp computes the (short, len <= kMaxN) dot product itself: same
+  // order everywhere, no barrier, no per-thread loop over warp partials
   auto block_dot = [&](const double* x, const double* y, int len) -> double {
     double s = 0.0;
-    for (int t = threadIdx.x; t < len; t += blockDim.x) s += x[t] * y[t];
+    for (int t = (int)(threadIdx.x & 31); t < len; t += 32) s += x[t] * y[t];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    __syncthreads();
-    return tot;
+    return s;
   };
   // y (len r1) = x (len r0) * A (r0 x r1)
   auto vecmat = [&](const double* x, const double* A, int r0, int r1, double* y) {
@@ -367,7 +382,7 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
   }
 }
 
-constexpr int kMomentSmemDoubles = (kMaxD + 2) * kMaxN + (kMaxD + 1) * kMaxN + 2 * kMaxN + 3 * 1024 + 32;
+constexpr int kMomentSmemDoubles = (kMaxD + 2) * kMaxN + (kMaxD + 1) * kMaxN + 2 * kMaxN + 9 * 1024 + 32;
 
 }  // namespace
 
