@@ -62,14 +62,16 @@ __global__ void k_shear_expand(int B, TTGeom g, int m, int n, int S, int tmin, c
   const int Nn = g.n[n];
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
+  const float invS = 1.f / (float)S;
   // one warp per output row (x, i); lanes along the row's o1 entries
   for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += gridDim.x * wpb) {
     const int x = r / N, i = r - x * N;
     float* orow = out + (long long)r * o1;
     if (l == lo) {
-      // row x, entries (beta, u): beta < a1, u < S
+      // row x, entries (beta, u): beta < a1, u < S (y < 2^12: the float
+      // quotient is exact after truncation)
       for (int y = lane; y < o1; y += 32) {
-        const int beta = y / S, u = y - beta * S;
+        const int beta = (int)(((float)y + 0.5f) * invS), u = y - beta * S;
         float v = 0.f;
         if (shift_side) {
           const int src = i - (tmin + u);
@@ -90,7 +92,7 @@ __global__ void k_shear_expand(int B, TTGeom g, int m, int n, int S, int tmin, c
       const int alpha = x / S, s0 = x - alpha * S;
       const float* irow = in + ((long long)alpha * N + i) * a1;
       for (int y = lane; y < o1; y += 32) {
-        const int beta = y / S, t = y - beta * S;
+        const int beta = (int)(((float)y + 0.5f) * invS), t = y - beta * S;
         orow[y] = (s0 == t) ? irow[beta] : 0.f;
       }
     }
@@ -405,7 +407,7 @@ void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, 
   count_launches(1);
   const int lo = m < n ? m : n, hi = m < n ? n : m;
   const int ny = virt ? 2 : hi - lo + 1;
-  k_shear_expand<<<dim3(16, ny, B), 256, 0, st>>>(B, g, m, n, S, tmin, weights, to_ptrs(cur, g.d),
+  k_shear_expand<<<dim3(32, ny, B), 256, 0, st>>>(B, g, m, n, S, tmin, weights, to_ptrs(cur, g.d),
                                                  to_ptrs(alt, g.d), ranks, virt);
 }
 
