@@ -800,7 +800,9 @@ void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, doub
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
                    long long core0_cap, double* flops) {
   count_launches(1);
-  k_svd<<<B, 1024, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs, P1,
+  // truncation stages have at most rank_cap + 16 Jacobi columns: half the warps suffice
+  const int threads = mode == kStageRight ? 1024 : 512;
+  k_svd<<<B, threads, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs, P1,
                                                              P2, core0_out, core0_cap, flops);
 }
 
