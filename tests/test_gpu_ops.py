@@ -105,6 +105,27 @@ def test_round_recovers_rank_and_bound(G):
     assert abs(err - rel(tt.densify(ref_cores), A)) < 2e-4
 
 
+@pytest.mark.parametrize("scale", [1e-16, 1e-8, 1e8, 1e16])
+def test_round_scale_invariant_at_extreme_magnitudes(G, scale):
+    """Rounding commutes with scaling: a core of magnitude 1e-16 or 1e16
+    (sums of squares outside [1e-30, 1e30], so the QR reflectors take their
+    rescaled path) gives the scaled result of the unit-scale rounding."""
+    f, g, P = bumps_filter(G, terms=3)
+    f.shear(0, 1, 0.0, do_round=False)
+    f.round()
+    ref = tt.densify(f.export_cores(0))
+    f2, _, _ = bumps_filter(G, terms=3)
+    cores = f2.export_cores(0)
+    cores[1] = cores[1] * np.float32(scale)
+    f2.import_cores(0, cores)
+    f2.shear(0, 1, 0.0, do_round=False)
+    f2.round()
+    out = f2.export_cores(0)
+    assert all(np.isfinite(c).all() for c in out)
+    assert f2.ranks()[0].tolist() == f.ranks()[0].tolist()
+    assert rel(tt.densify([c.astype(np.float64) for c in out]) / scale, ref) < 1e-5
+
+
 def test_predict_one_step(G):
     F = np.array([[0.95, 0.04, -0.03], [0.0, 0.97, 0.05], [0.0, 0.0, 0.92]])
     Q = np.diag([0.05, 0.08, 0.03])
