@@ -645,7 +645,9 @@ __global__ void __launch_bounds__(256, 4) k_gemm_grouped(GemmWork w, double* flo
   }
 }
 
-__global__ void k_scan_tiles(GemmWork w) {
+// Tile shapes and the exclusive prefix of tile counts of descriptors already
+// written (one CTA).
+__device__ void scan_tiles_block(GemmWork w) {
   for (int i = threadIdx.x; i < w.ndesc; i += blockDim.x) {
     GemmDesc& g = w.desc[i];
     const int sh = gemm_shape(g.m, g.n);
@@ -656,6 +658,8 @@ __global__ void k_scan_tiles(GemmWork w) {
   __syncthreads();
   block_scan_inplace(w.tiles, w.ndesc);
 }
+
+__global__ void k_scan_tiles(GemmWork w) { scan_tiles_block(w); }
 
 // ----------------------------------------------------------------- plans
 // Per filter: the tall matrix of this stage and its TSQR schedule.
@@ -783,6 +787,11 @@ __global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, 
       rk[1] = rn;
     }
   }
+  // descriptors of this CTA are in global memory: make them visible to the
+  // whole block before the tile scan reads them
+  __threadfence_block();
+  __syncthreads();
+  scan_tiles_block(gw);
 }
 
 }  // namespace
@@ -811,10 +820,9 @@ void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeo
                             const float* cur_b, float* alt_b, const float* P1, const float* P2,
                             const float* W, long long W_cap, int N1, GemmWork gw, int vS,
                             int dstride) {
-  count_launches(2);
+  count_launches(1);
   k_plan_gemm_stage<<<1, 1024, 0, st>>>(B, mode, k, g, ranks, newrank, cur_a, alt_a, cur_b, alt_b, P1,
                                         P2, W, W_cap, N1, gw, vS, dstride);
-  k_scan_tiles<<<1, 1024, 0, st>>>(gw);
 }
 
 void launch_gemm(cudaStream_t st, GemmWork gw, int grid, double* flops) {
