@@ -167,3 +167,33 @@ def test_config2_full_size_bench_launch(G):
         assert (np.abs(m) < 8).all()
         assert (f.ranks() <= 16).all()
         assert all(s["max_rank"] <= 16 for s in st)
+
+
+def test_batch_split_into_concurrent_parts(G, monkeypatch):
+    """A batch split into parts on their own streams (the library's default
+    for large batches) gives each filter what the unsplit batch gives it:
+    same ranks, densities and moments up to FP32 rounding (the QR's row
+    slicing depends on the batch size)."""
+    model = synth.config2(n=24)
+    B = 8
+    zs = np.stack([synth.simulate(model, mc, steps=3)[1] for mc in range(B)], axis=1)
+    outs = []
+    for parts in ("1", "3"):
+        monkeypatch.setenv("TTGBF_PARTS", parts)
+        f = make_filter(G, model, batch=B)
+        comps = device_tables(model, f.grid_axes())
+        for k in range(3):
+            f.predict(model.F, model.Q)
+            f.update(comps, model.R, zs[k])
+        m, c, lc, ll = f.estimate()
+        outs.append((f.ranks(), [tt.densify(f.export_cores(b)) for b in range(B)], m, lc, ll,
+                     [s["tail_sum"] for s in f.stats()]))
+        f.free()
+    (r1, d1, m1, lc1, ll1, t1), (r3, d3, m3, lc3, ll3, t3) = outs
+    np.testing.assert_array_equal(r1, r3)
+    for b in range(B):
+        assert rel(d3[b], d1[b]) < 1e-4
+    np.testing.assert_allclose(m3, m1, rtol=0, atol=1e-5)
+    np.testing.assert_allclose(lc3, lc1, rtol=0, atol=1e-5)
+    np.testing.assert_allclose(ll3, ll1, rtol=0, atol=1e-4)
+    np.testing.assert_allclose(t3, t1, rtol=1e-3, atol=1e-6)
