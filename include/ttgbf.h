@@ -111,7 +111,20 @@ typedef struct {
 size_t ttgbf_workspace_bytes(const ttgbf_grid* grid, const ttgbf_opts* opts);
 
 /* Create a context holding `opts->batch` filters, each initialised to the
- * prior.  Copies grid, prior and options.  *out is set on success only. */
+ * prior.  Copies grid, prior and options.  *out is set on success only.
+ *
+ * A batch of 24 filters or more runs as up to 8 sub-batches ("parts", one
+ * per 12 filters; environment TTGBF_PARTS=1..8 overrides), each on a stream
+ * the library creates; the workspace then holds the parts' arenas back to
+ * back (ttgbf_workspace_bytes accounts for this).  Every call keeps the
+ * stream contract below for caller memory: the parts start after the work
+ * already on `opts->stream` when a call reads caller device memory, and
+ * `opts->stream` waits for them when a call reads or writes caller memory.
+ * Calls that touch only the filters' own state (predict, shear, scale,
+ * convolve, round, normalise) let the parts run on without a join, so an
+ * event recorded on `opts->stream` right after them does not cover their
+ * work; the next call that returns results (estimate, estimate_dev, ranks,
+ * stats, export) does. */
 int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior,
                const ttgbf_opts* opts);
 
