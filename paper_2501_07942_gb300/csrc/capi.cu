@@ -1042,8 +1042,14 @@ int part_of(const ttgbf_ctx* c, int f, int* local) {
 
 extern "C" {
 
-int ttgbf_predict(ttgbf_ctx* c, const double* F, const double* Q) {
-  if (split(c)) return fan_out(c, [&](ttgbf_ctx* q, int) { return ttgbf_predict(q, F, Q); }, false, false);
+}  // extern "C"
+
+namespace {
+
+// The predict step in three parts (validation and setup; elementary
+// operation i of the re-gridding; per-mode kernels and normalisation), so
+// that a split batch can enqueue its parts operation by operation.
+int predict_begin(ttgbf_ctx* c, const double* F, const double* Q) {
   int rc = guard(c);
   if (rc) return rc;
   if (!F || !Q) return TTGBF_EINVAL;
@@ -1065,17 +1071,54 @@ int ttgbf_predict(ttgbf_ctx* c, const double* F, const double* Q) {
   cudaMemsetAsync(c->tail_sum, 0, sizeof(double) * c->B, c->st);
   cudaMemsetAsync(c->tail_max, 0, sizeof(double) * c->B, c->st);
   cudaMemsetAsync(c->cap_hits, 0, sizeof(int) * c->B, c->st);
-  for (size_t i = 0; i < c->ops.size(); ++i) {
-    const Op& op = c->ops[i];
-    if (op.kind == 0) {
-      enqueue_shear(c, op.m, op.n, c->op_S[i], c->op_tmin[i], c->opmats + c->op_woff[i], true);
-    } else if (!c->fuse) {
-      mode_apply(c, op.m, c->opmats + c->scale_off[op.m]);
-    }
+  return TTGBF_OK;
+}
+
+void predict_op(ttgbf_ctx* c, size_t i) {
+  const Op& op = c->ops[i];
+  if (op.kind == 0) {
+    enqueue_shear(c, op.m, op.n, c->op_S[i], c->op_tmin[i], c->opmats + c->op_woff[i], true);
+  } else if (!c->fuse) {
+    mode_apply(c, op.m, c->opmats + c->scale_off[op.m]);
   }
-  for (int k = 0; k < d; ++k) mode_apply(c, k, c->opmats + c->mat_off[k]);
+}
+
+void predict_mode(ttgbf_ctx* c, int k) { mode_apply(c, k, c->opmats + c->mat_off[k]); }
+
+int predict_end(ttgbf_ctx* c) {
   enqueue_normalise(c, c->mass_pred);
   return check(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ttgbf_predict(ttgbf_ctx* c, const double* F, const double* Q) {
+  if (split(c)) {
+    // every part validates the same arguments: a failure can only come
+    // from the first part, before anything is enqueued
+    for (ttgbf_ctx* q : c->parts) {
+      const int rc = predict_begin(q, F, Q);
+      if (rc) return rc;
+    }
+    const size_t nops = c->parts[0]->ops.size();
+    for (size_t i = 0; i < nops; ++i)
+      for (ttgbf_ctx* q : c->parts) predict_op(q, i);
+    for (int k = 0; k < c->d; ++k)
+      for (ttgbf_ctx* q : c->parts) predict_mode(q, k);
+    int rc = TTGBF_OK;
+    for (ttgbf_ctx* q : c->parts) {
+      const int r = predict_end(q);
+      if (r && !rc) rc = r;
+    }
+    return rc;
+  }
+  const int rc = predict_begin(c, F, Q);
+  if (rc) return rc;
+  for (size_t i = 0; i < c->ops.size(); ++i) predict_op(c, i);
+  for (int k = 0; k < c->d; ++k) predict_mode(c, k);
+  return predict_end(c);
 }
 
 int ttgbf_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z) {
