@@ -250,14 +250,21 @@ class TTFilter:
         o = Opts(self.batch, int(rank_cap), float(eps), int(max_shift_span),
                  ctypes.c_void_p(self._stream.cuda_stream), None, 0)
         nbytes = self._lib.ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
-        if nbytes == 0:
-            raise TTGBFError(-1, "ttgbf_workspace_bytes")
-        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
-        o.workspace = ctypes.c_void_p(self.workspace.data_ptr())
-        o.workspace_bytes = int(nbytes)
         pm, pv = _f64(prior_mean), _f64(prior_var)
         pr = Prior(_dptr(pm), _dptr(pv))
         self._ctx = ctypes.c_void_p()
+        if nbytes == 0:
+            # ttgbf_init validates every argument on the host before it
+            # allocates or launches anything: it names the reason
+            rc = self._lib.ttgbf_init(ctypes.byref(self._ctx), ctypes.byref(g), ctypes.byref(pr),
+                                      ctypes.byref(o))
+            if rc == 0:
+                self._lib.ttgbf_free(self._ctx)
+                self._ctx = ctypes.c_void_p()
+            raise TTGBFError(rc if rc != 0 else -1, "ttgbf_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        o.workspace = ctypes.c_void_p(self.workspace.data_ptr())
+        o.workspace_bytes = int(nbytes)
         _check(self._lib.ttgbf_init(ctypes.byref(self._ctx), ctypes.byref(g), ctypes.byref(pr),
                                     ctypes.byref(o)), "ttgbf_init")
 

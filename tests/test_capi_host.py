@@ -84,3 +84,17 @@ def test_null_context_calls(lib):
     assert lib.ttgbf_round(None) == -1
     assert lib.ttgbf_normalise(None) == -1
     assert lib.ttgbf_grid_axes(None, None) == -1
+
+
+def test_filter_reports_capacity_before_device(lib):
+    # the size query fails; the binding names the reason from ttgbf_init's
+    # host-side validation (no workspace is allocated, nothing is launched)
+    import types
+    null_stream = types.SimpleNamespace(cuda_stream=0)
+    with pytest.raises(G.TTGBFError) as ei:
+        G.TTFilter([-40.0, -10.0], [40.0, 10.0], [256, 256], [0.0, 0.0], [4.0, 1.0],
+                   rank_cap=32, eps=1e-5, stream=null_stream)
+    assert ei.value.code == -5
+    with pytest.raises(G.TTGBFError) as ei:
+        G.TTFilter([0.0], [0.0], [8], [0.0], [1.0], stream=null_stream)
+    assert ei.value.code == -1

@@ -1,0 +1,135 @@
+"""GPU parity on the higher-dimensional workload: d = 6 and d = 8 constant-
+velocity blocks x_{2i} += 0.1 x_{2i+1}, diagonal Q, one-mode measurements
+z_i = x_{2i}^2 / 20 + v_i, rank cap 32, eps 1e-5.
+
+* d = 6 at N = 16 and d = 8 at N = 8: the whole density against the dense
+  FP64 oracle (a 256^d grid is out of any dense filter's reach).
+* d = 8 at N = 128: the model is block diagonal (F, Q, prior and likelihood
+  all factor over the pairs (x_{2i}, x_{2i+1})) and so is the re-gridded
+  transition, whose shears act inside one pair each.  The exact density is
+  then the tensor product of four 2-D oracle densities, each computed densely
+  on its 128 x 128 grid; the TT density is compared with that product through
+  TT inner products, so no 128^8 tensor is formed.
+
+Tolerances as for the other workloads: per step 10 (eps + tau) + 1e-5 in
+relative Frobenius norm, summed over the steps; means within 1e-3 grid
+spacings; log c within 1e-3.  The shear span of this workload is at most 5 up
+to N = 128 (|0.1 xi_vel / Delta_pos| <= 1.59), so the rank expansion stays at
+32 x 5 = 160 columns."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pmf, tt
+
+from gpu_util import device_tables, lib_module, make_filter, oracle_grid, rel, tt_tol
+
+pytestmark = pytest.mark.gpu
+
+SPAN = 5
+
+
+@pytest.fixture(scope="module")
+def G():
+    return lib_module()
+
+
+def block_model(model: synth.Model, i: int) -> synth.Model:
+    """The 2-D model of the pair (x_{2i}, x_{2i+1}) of a config-3 model."""
+    s = slice(2 * i, 2 * i + 2)
+    return synth.Model(name=f"{model.name}-pair{i}", lo=model.lo[s], hi=model.hi[s],
+                       n=model.n[s], m0=model.m0[s], P0=model.P0[s, s], F=model.F[s, s],
+                       Q=model.Q[s, s], R=model.R[i:i + 1, i:i + 1],
+                       comps=[((0,), synth.workloads.h_square20)], eps=model.eps,
+                       rank_cap=model.rank_cap)
+
+
+@pytest.mark.parametrize("d,n,steps", [(6, 16, 4), (8, 8, 3)])
+def test_config3_small_grid_vs_dense_oracle(G, d, n, steps):
+    model = synth.config3(d=d, n=n)
+    mcs = [0, 1]
+    f = make_filter(G, model, batch=len(mcs), smax=SPAN)
+    comps = device_tables(model, f.grid_axes())
+    g = oracle_grid(model)
+    oc = model.tables(g.axes)
+    zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
+    Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
+    bound = [0.0] * len(mcs)
+    for k in range(steps):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, np.stack([z[k] for z in zs]))
+        st = f.stats()
+        m, c, lc, ll = f.estimate()
+        for i in range(len(mcs)):
+            Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
+            Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
+            mo, co = pmf.moments(Ps[i], g)
+            bound[i] += tt_tol(model.eps, st[i]["tail_sum"])
+            e = rel(tt.densify(f.export_cores(i)), Ps[i])
+            assert e <= bound[i], (k, i, e, bound[i])
+            assert np.abs(m[i] - mo).max() < 1e-3 * g.delta_axis.min(), (k, i)
+            assert np.abs(c[i] - co).max() < 1e-3 * g.delta_axis.min(), (k, i)
+            assert abs(lc[i] - logc) < 1e-3, (k, i)
+            assert st[i]["max_rank"] <= model.rank_cap
+
+
+def test_config3_d8_n128_vs_blockwise_oracle(G):
+    model = synth.config3(d=8, n=128)
+    mcs = [0, 1]
+    steps = 4
+    f = make_filter(G, model, batch=len(mcs), smax=SPAN)
+    comps = device_tables(model, f.grid_axes())
+    zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
+    pairs = [block_model(model, i) for i in range(model.d // 2)]
+    grids = [oracle_grid(bm) for bm in pairs]
+    tabs = [bm.tables(gb.axes) for bm, gb in zip(pairs, grids)]
+    P = [[pmf.prior(gb, bm.m0, bm.P0) for bm, gb in zip(pairs, grids)] for _ in mcs]
+    bound = [0.0] * len(mcs)
+    for k in range(steps):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, np.stack([z[k] for z in zs]))
+        st = f.stats()
+        m, c, lc, ll = f.estimate()
+        for b in range(len(mcs)):
+            logc = 0.0
+            mean = np.zeros(model.d)
+            cov = np.zeros((model.d, model.d))
+            exact = []
+            for i, (bm, gb, tb) in enumerate(zip(pairs, grids, tabs)):
+                Pi, _ = pmf.predict_rg(P[b][i], gb, bm.F, bm.Q)
+                Pi, lci = pmf.update(Pi, gb, pmf.likelihood(gb, tb, zs[b][k][i:i + 1], bm.R))
+                P[b][i] = Pi
+                logc += lci
+                mo, co = pmf.moments(Pi, gb)
+                mean[2 * i:2 * i + 2] = mo
+                cov[2 * i:2 * i + 2, 2 * i:2 * i + 2] = co
+                # exact 2-core TT of the pair's density (1e-12 truncation)
+                exact += tt.from_dense(Pi, eps=1e-12)
+            cores = [np.asarray(x, dtype=np.float64) for x in f.export_cores(b)]
+            nn = tt.inner(exact, exact)
+            diff2 = tt.inner(cores, cores) - 2.0 * tt.inner(cores, exact) + nn
+            e = float(np.sqrt(max(diff2, 0.0) / nn))
+            bound[b] += tt_tol(model.eps, st[b]["tail_sum"])
+            assert e <= bound[b], (k, b, e, bound[b])
+            dmin = min(gb.delta_axis.min() for gb in grids)
+            assert np.abs(m[b] - mean).max() < 1e-3 * dmin, (k, b, m[b], mean)
+            assert np.abs(c[b] - cov).max() < 1e-3 * dmin, (k, b)
+            assert abs(lc[b] - logc) < 1e-3, (k, b, lc[b], logc)
+            r = f.ranks()[b]
+            assert r.max() <= model.rank_cap
+            # the pairs are independent: rank 1 between them
+            assert all(r[2 * i] == 1 for i in range(1, model.d // 2)), r
+
+
+def test_config3_full_span_needs_wider_expansion(G):
+    """At N = 256 a shear of this workload spans 9 shifts: 32 x 9 columns
+    exceed the 160-column factorisations, which the library reports as a
+    capacity error rather than truncating the operator."""
+    model = synth.config3(d=6, n=256)
+    with pytest.raises(G.TTGBFError) as ei:
+        make_filter(G, model, batch=1)
+    assert ei.value.code == -5
+    f = make_filter(G, model, batch=1, smax=SPAN)
+    with pytest.raises(G.TTGBFError) as ei:
+        f.predict(model.F, model.Q)
+    assert ei.value.code == -5
