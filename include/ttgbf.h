@@ -42,7 +42,8 @@ extern "C" {
 #define TTGBF_ENONFINITE (-2) /* NaN or Inf in F, Q, R, z, grid or prior   */
 #define TTGBF_ENOMEM (-3)     /* device allocation failed or workspace too small */
 #define TTGBF_ECUDA (-4)      /* a CUDA call failed; the context is poisoned */
-#define TTGBF_ECAPACITY (-5)  /* a shear needs a larger rank expansion than max_shift_span */
+#define TTGBF_ECAPACITY (-5)  /* rank_cap * max_shift_span > 160, or a shear spans more than
+                                 max_shift_span^2 shifts (more than max_shift_span pieces) */
 #define TTGBF_ESINGULAR (-6)  /* F has no LDU factorisation without pivoting */
 #define TTGBF_EPOISONED (-7)  /* an earlier CUDA error poisoned the context */
 
@@ -70,7 +71,9 @@ typedef struct {
   int32_t batch;          /* number of independent filters (>= 1) */
   int32_t rank_cap;       /* maximal TT rank R^max after rounding (Sec. 3.2); >= 1 */
   double eps;             /* rounding tolerance: ||A - round(A)||_F <= eps ||A||_F when the cap does not bind */
-  int32_t max_shift_span; /* largest rank expansion S one re-gridding shear may need; 0 = 10 */
+  int32_t max_shift_span; /* widest rank expansion S applied at once (0 = 10); rank_cap * S must
+                             not exceed 160.  A shear spanning more shifts is applied in pieces
+                             (see ttgbf_predict), up to max_shift_span^2 shifts */
   void* stream;           /* cudaStream_t for all work; NULL = legacy default stream */
   void* workspace;        /* caller-owned device memory of ttgbf_workspace_bytes() bytes, 256-byte
                              aligned, or NULL to let the library cudaMalloc it (freed by ttgbf_free) */
@@ -135,7 +138,12 @@ int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior
  * shears and axis scalings with hat weights, each shear followed by TT
  * rounding, then the per-mode Gaussian convolution with
  * kappa_m(t) = D_m N(D_m t; 0, Q_mm) over each core's grid index, then
- * normalisation (Alg. 2 step 4).  Same F and Q for every filter. */
+ * normalisation (Alg. 2 step 4).  Same F and Q for every filter.
+ * A shear whose hat weights span S > max_shift_span integer shifts is
+ * applied as the TT sum of ceil(S / max_shift_span) pieces of consecutive
+ * shifts, each expanded and rounded on its own, and the sum rounded again
+ * (its discarded tails are reported like any rounding's); TTGBF_ECAPACITY
+ * when that takes more than max_shift_span pieces. */
 int ttgbf_predict(ttgbf_ctx* ctx, const double* F, const double* Q);
 
 /* Bayes update (Eqs. pmf_filtrace_a/b; Alg. 2 step 2): P <- L P / c with the
@@ -186,7 +194,9 @@ int ttgbf_import_cores(ttgbf_ctx* ctx, int32_t f, const float* buf, const int32_
 
 /* Apply one elementary re-gridding shear x_m += a x_n (m != n) with hat
  * weights to every filter, then round if do_round != 0.  Without rounding the
- * ranks of links between m and n grow by the shift span S. */
+ * ranks of links between m and n grow by the shift span S (TTGBF_ECAPACITY
+ * when S > max_shift_span); with rounding a wider shear is applied in pieces
+ * as in ttgbf_predict. */
 int ttgbf_shear(ttgbf_ctx* ctx, int32_t m, int32_t n, double a, int32_t do_round);
 
 /* Apply x_m <- lam x_m (cloud-in-cell) to every filter; ranks unchanged. */

@@ -51,6 +51,8 @@ struct Arena {
 // Offsets of every device buffer inside the workspace.
 struct Layout {
   size_t core[2][kMaxD];
+  size_t piece_core[2][kMaxD];  // saved block, accumulated pieces (wide shears)
+  size_t saved_ranks, acc_rank, piece_off;
   size_t ranks, axes, pmean, pvar;
   size_t normA, tail_sum, tail_max, mass, mass_pred, log_c, log_lik, logoff, mean, cov;
   size_t cap_hits, newrank, lik_off;
@@ -112,6 +114,11 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   }
   for (int s = 0; s < 2; ++s)
     for (int k = 0; k < d; ++k) L.core[s][k] = a.take<float>((size_t)B * L.core_cap[k]);
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < d; ++k) L.piece_core[s][k] = a.take<float>((size_t)B * L.core_cap[k]);
+  L.saved_ranks = a.take<int>((size_t)B * (d + 1));
+  L.acc_rank = a.take<int>((size_t)B * (d + 1));
+  L.piece_off = a.take<int>((size_t)B * smax * (d + 1));
   L.ranks = a.take<int>((size_t)B * (d + 1));
   L.axes = a.take<double>(nsum);
   L.pmean = a.take<double>(d);
@@ -151,7 +158,7 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   L.W = a.take<float>((size_t)B * L.W_cap);
   long long nn = 0;
   for (int k = 0; k < d; ++k) nn += (long long)g->n[k] * g->n[k];
-  L.opmats_floats = 2 * nn + (long long)d * d * (smax + 2) * nmax;
+  L.opmats_floats = 2 * nn + (long long)d * d * (smax * smax + 2) * nmax;
   L.opmats = a.take<float>(L.opmats_floats);
   L.zbuf = a.take<float>((size_t)B * kMaxComps);
   L.prof_flops = a.take<double>(kPClasses);
@@ -182,6 +189,10 @@ struct ttgbf_ctx {
   TTGeom geom{};
   float* buf[2][kMaxD] = {};
   int cur[kMaxD] = {};
+  // a shear wider than smax shifts: saved block cores, accumulated pieces
+  float* save[kMaxD] = {};
+  float* acc[kMaxD] = {};
+  int *saved_ranks = nullptr, *acc_rank = nullptr, *piece_off = nullptr;
   int* ranks = nullptr;
   double *axes_d = nullptr, *pmean = nullptr, *pvar = nullptr;
   double *normA, *tail_sum, *tail_max, *mass, *mass_pred, *log_c, *log_lik, *logoff, *mean, *cov;
@@ -549,7 +560,7 @@ int prepare_predict(ttgbf_ctx* c, const double* F, const double* Q) {
     int S, tmin;
     std::vector<float> w;
     shear_table(c, op.m, op.n, op.a, &S, &tmin, &w);
-    if (S > c->smax) return TTGBF_ECAPACITY;
+    if (S > c->smax * c->smax) return TTGBF_ECAPACITY;  // more pieces than the sum's rank room
     if (at + (long long)w.size() > c->L.opmats_floats) return TTGBF_ECAPACITY;
     std::copy(w.begin(), w.end(), host.begin() + at);
     S_list.push_back(S);
@@ -600,12 +611,80 @@ int prepare_predict(ttgbf_ctx* c, const double* F, const double* Q) {
   return TTGBF_OK;
 }
 
+void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts, bool do_round);
+
+// A shear whose operator spans S > smax shifts: the sum over shifts is cut
+// into np <= smax pieces of consecutive shifts (at most smax each).  Every
+// piece is expanded from a saved copy of the block and rounded on the block;
+// the rounded pieces (ranks <= rank_cap each) are added as tensor trains and
+// the sum (ranks <= np * rank_cap <= capr) is rounded on the block again.  The
+// result differs from the rounding of the whole expansion only by the pieces'
+// own truncations, which the discarded tails report.
+void enqueue_shear_pieces(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts) {
+  const int lo = std::min(m, n), hi = std::max(m, n);
+  const int np = (S + c->smax - 1) / c->smax;
+  const int Nn = c->n[n];
+  enqueue_center_into(c, lo, hi);
+  float* curv[kMaxD];
+  float* altv[kMaxD];
+  for (int k = 0; k < c->d; ++k) curv[k] = curp(c, k);
+  {
+    Prof p(c, kPShear, 1);
+    launch_block_copy(c->st, c->B, c->geom, lo, hi, curv, c->save, c->ranks);
+  }
+  cudaMemcpyAsync(c->saved_ranks, c->ranks, sizeof(int) * (size_t)c->B * (c->d + 1),
+                  cudaMemcpyDeviceToDevice, c->st);
+  int u0 = 0;
+  for (int p = 0; p < np; ++p) {
+    const int Sp = (int)((long long)S * (p + 1) / np - (long long)S * p / np);
+    if (p > 0)
+      cudaMemcpyAsync(c->ranks, c->saved_ranks, sizeof(int) * (size_t)c->B * (c->d + 1),
+                      cudaMemcpyDeviceToDevice, c->st);
+    for (int k = 0; k < c->d; ++k) altv[k] = altp(c, k);
+    {
+      Prof pr(c, kPShear, 1);
+      launch_shear_expand(c->st, c->B, c->geom, m, n, Sp, tmin + u0, wts + (size_t)u0 * Nn, c->save,
+                          altv, c->ranks, 0);
+    }
+    {
+      Prof pr(c, kPOther, 1);
+      launch_rank_scale(c->st, c->B, c->d, c->ranks, lo, hi, Sp);
+    }
+    for (int k = lo; k <= hi; ++k) c->cur[k] ^= 1;
+    for (int k = hi; k >= lo + 1; --k) stage(c, kStageRight, k, 0);
+    for (int k = lo; k <= hi - 1; ++k) stage(c, kStageLeft, k, k == lo);
+    for (int k = 0; k < c->d; ++k) curv[k] = curp(c, k);
+    {
+      Prof pr(c, kPShear, 1);
+      launch_acc_piece(c->st, c->B, c->geom, lo, hi, p, c->smax, c->capr, curv, c->acc, c->ranks,
+                       c->acc_rank, c->piece_off);
+    }
+    u0 += Sp;
+  }
+  for (int k = 0; k < c->d; ++k) altv[k] = altp(c, k);
+  {
+    Prof pr(c, kPShear, 1);
+    launch_acc_sum(c->st, c->B, c->geom, lo, hi, np, c->smax, c->capr, c->acc, altv, c->ranks,
+                   c->acc_rank, c->piece_off);
+  }
+  for (int k = lo; k <= hi; ++k) c->cur[k] ^= 1;
+  // cores outside [lo, hi] are still orthonormal: round the sum on the block
+  for (int k = hi; k >= lo + 1; --k) stage(c, kStageRight, k, 0);
+  for (int k = lo; k <= hi - 1; ++k) stage(c, kStageLeft, k, k == lo);
+  c->canon = true;
+  c->center = hi;
+}
+
 // Shear x_m += a x_n as a rank-S TT operator on the links between lo and hi,
 // followed (do_round) by a rounding restricted to that block: the TT is first
 // put in canonical form with its center inside [lo, hi], so the cores outside
 // the block are orthonormal and the block's truncations are the ones the full
 // TT rounding would make on these links.
 void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts, bool do_round) {
+  if (do_round && S > c->smax) {
+    enqueue_shear_pieces(c, m, n, S, tmin, wts);
+    return;
+  }
   const int lo = std::min(m, n), hi = std::max(m, n);
   if (do_round) enqueue_center_into(c, lo, hi);
   float* curv[kMaxD];
@@ -762,7 +841,7 @@ const char* ttgbf_strerror(int code) {
     case TTGBF_ENONFINITE: return "non-finite input";
     case TTGBF_ENOMEM: return "out of device memory or workspace too small";
     case TTGBF_ECUDA: return "CUDA error (context poisoned)";
-    case TTGBF_ECAPACITY: return "rank expansion exceeds rank_cap * max_shift_span";
+    case TTGBF_ECAPACITY: return "rank expansion beyond capacity (rank_cap * max_shift_span > 160, or a shear wider than max_shift_span^2 shifts)";
     case TTGBF_ESINGULAR: return "F has no LDU factorisation without pivoting";
     case TTGBF_EPOISONED: return "context poisoned by an earlier CUDA error";
     default: return "unknown error";
@@ -863,6 +942,13 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   char* b = c->base;
   for (int s = 0; s < 2; ++s)
     for (int k = 0; k < d; ++k) c->buf[s][k] = (float*)(b + L.core[s][k]);
+  for (int k = 0; k < d; ++k) {
+    c->save[k] = (float*)(b + L.piece_core[0][k]);
+    c->acc[k] = (float*)(b + L.piece_core[1][k]);
+  }
+  c->saved_ranks = (int*)(b + L.saved_ranks);
+  c->acc_rank = (int*)(b + L.acc_rank);
+  c->piece_off = (int*)(b + L.piece_off);
   c->geom.d = d;
   for (int k = 0; k < d; ++k) {
     c->geom.n[k] = c->n[k];
@@ -1363,7 +1449,7 @@ int ttgbf_shear(ttgbf_ctx* c, int32_t m, int32_t n, double a, int32_t do_round) 
   int S, tmin;
   std::vector<float> w;
   shear_table(c, m, n, a, &S, &tmin, &w);
-  if (S > c->smax) return TTGBF_ECAPACITY;
+  if (S > (do_round ? c->smax * c->smax : c->smax)) return TTGBF_ECAPACITY;
   if (c->expanded) enqueue_round(c);
   wait_stage(c->ev_ops, &c->ev_ops_used);
   std::copy(w.begin(), w.end(), c->stage_ops);

@@ -120,6 +120,16 @@ void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, 
                          const float* weights, float* const* cur, float* const* alt,
                          const int* ranks, int virt);
 void launch_rank_scale(cudaStream_t st, int B, int d, int* ranks, int lo, int hi, int S);
+// A shear applied in pieces of its shift range: save the block, accumulate
+// each rounded piece (offsets on the inner links), pack the TT sum.
+void launch_block_copy(cudaStream_t st, int B, const TTGeom& g, int lo, int hi,
+                       float* const* src, float* const* dst, const int* ranks);
+void launch_acc_piece(cudaStream_t st, int B, const TTGeom& g, int lo, int hi, int p, int maxp,
+                      int capr, float* const* cur, float* const* acc, const int* ranks,
+                      int* acc_rank, int* piece_off);
+void launch_acc_sum(cudaStream_t st, int B, const TTGeom& g, int lo, int hi, int np, int maxp,
+                    int capr, float* const* acc, float* const* alt, int* ranks,
+                    const int* acc_rank, const int* piece_off);
 void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, const int* ranks,
                             const float* M, const float* cur, float* alt, GemmWork gw, int cap_in);
 void launch_plan_supercore(cudaStream_t st, int B, const TTGeom& g, const int* ranks,

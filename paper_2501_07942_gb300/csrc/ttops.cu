@@ -106,6 +106,121 @@ __global__ void k_rank_scale(int B, int d, int* ranks, int lo, int hi, int S) {
   }
 }
 
+// ------------------------------------------- a wide shear applied in pieces
+// A shear's TT operator is a sum over its integer shifts t of E_t (x) H_t
+// (shift of mode m, hat weights on mode n).  When that sum is wider than the
+// expansion capacity it is split into pieces of consecutive shifts; each
+// piece is expanded from a saved copy of the block's cores and rounded, and
+// the rounded pieces are added as tensor trains (Sec. 4.1: the TT sum, whose
+// end cores concatenate along the inner rank and whose middle cores are
+// block diagonal) before a final rounding of the sum.  The accumulator keeps
+// every block core at fixed strides [cl][N][cr] (cl = 1 for core 0, else
+// capr; cr = 1 for core d-1, else capr), the capacity layout of that core.
+
+// Used part of cores lo..hi copied between two buffer sets of the same layout.
+__global__ void k_block_copy(int B, TTGeom g, int lo, CorePtrs src, CorePtrs dst,
+                             const int* ranks) {
+  const int b = blockIdx.z, l = lo + blockIdx.y;
+  if (b >= B) return;
+  const int* rk = ranks + (long long)b * (g.d + 1);
+  const long long cnt = (long long)rk[l] * g.n[l] * rk[l + 1];
+  const float* s = src.p[l] + (long long)b * g.cap[l];
+  float* t = dst.p[l] + (long long)b * g.cap[l];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt;
+       e += (long long)gridDim.x * blockDim.x)
+    t[e] = s[e];
+}
+
+// Offsets of piece p on the block's inner links lo+1..hi: the accumulated
+// ranks of the pieces before it, the sum's rank held to the accumulator's
+// capacity capr (never reached: the host allows at most capr / rank_cap
+// pieces of rank <= rank_cap).  One thread per filter.
+__global__ void k_acc_begin(int B, int d, int lo, int hi, int p, int maxp, int capr,
+                            const int* ranks, int* acc_rank, int* piece_off) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int* rk = ranks + (long long)b * (d + 1);
+    int* ar = acc_rank + (long long)b * (d + 1);
+    int* po = piece_off + ((long long)b * maxp + p) * (d + 1);
+    for (int l = lo + 1; l <= hi; ++l) {
+      const int o = (p == 0) ? 0 : ar[l];
+      po[l] = o;
+      ar[l] = min(o + rk[l], capr);
+    }
+  }
+}
+
+__device__ __forceinline__ int acc_stride_left(int l, int capr) { return l == 0 ? 1 : capr; }
+__device__ __forceinline__ int acc_stride_right(const TTGeom& g, int l, int capr) {
+  return l == g.d - 1 ? 1 : capr;
+}
+
+// Piece p's rounded cores (current buffers, current ranks) into the
+// accumulator at the piece's offsets.
+__global__ void k_acc_scatter(int B, TTGeom g, int lo, int hi, int p, int maxp, int capr,
+                              CorePtrs cur, CorePtrs acc, const int* ranks, const int* piece_off) {
+  const int b = blockIdx.z, l = lo + blockIdx.y;
+  if (b >= B) return;
+  const int* rk = ranks + (long long)b * (g.d + 1);
+  const int* po = piece_off + ((long long)b * maxp + p) * (g.d + 1);
+  const int r0 = rk[l], r1 = rk[l + 1], N = g.n[l];
+  const int ro = (l > lo) ? po[l] : 0, co = (l < hi) ? po[l + 1] : 0;
+  const int cl = acc_stride_left(l, capr), cr = acc_stride_right(g, l, capr);
+  const float* s = cur.p[l] + (long long)b * g.cap[l];
+  float* t = acc.p[l] + (long long)b * g.cap[l];
+  const long long cnt = (long long)r0 * N * r1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(e % r1);
+    const long long ai = e / r1;
+    const int i = (int)(ai % N), a = (int)(ai / N);
+    if (ro + a < cl && co + x < cr) t[((long long)(ro + a) * N + i) * cr + co + x] = s[e];
+  }
+}
+
+// The piece whose rows (columns) of link l hold index idx.
+__device__ __forceinline__ int piece_of(const int* po0, int np, int d, int l, int idx) {
+  int p = 0;
+  for (int q = 1; q < np; ++q)
+    if (po0[(long long)q * (d + 1) + l] <= idx) p = q;
+  return p;
+}
+
+// The TT sum of the pieces, packed at its ranks into the other buffer set:
+// end cores as accumulated, middle cores block diagonal (zero between pieces).
+__global__ void k_acc_gather(int B, TTGeom g, int lo, int hi, int np, int maxp, int capr,
+                             CorePtrs acc, CorePtrs alt, const int* ranks, const int* acc_rank,
+                             const int* piece_off) {
+  const int b = blockIdx.z, l = lo + blockIdx.y;
+  if (b >= B) return;
+  const int* rk = ranks + (long long)b * (g.d + 1);
+  const int* ar = acc_rank + (long long)b * (g.d + 1);
+  const int* po0 = piece_off + (long long)b * maxp * (g.d + 1);
+  const int N = g.n[l];
+  const int Rl = (l > lo) ? ar[l] : rk[l], Rr = (l < hi) ? ar[l + 1] : rk[l + 1];
+  const int cl = acc_stride_left(l, capr), cr = acc_stride_right(g, l, capr);
+  const bool middle = (l > lo && l < hi);
+  const float* s = acc.p[l] + (long long)b * g.cap[l];
+  float* t = alt.p[l] + (long long)b * g.cap[l];
+  const long long cnt = (long long)Rl * N * Rr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(e % Rr);
+    const long long ai = e / Rr;
+    const int i = (int)(ai % N), a = (int)(ai / N);
+    float v = 0.f;
+    if (a < cl && x < cr &&
+        (!middle || piece_of(po0, np, g.d, l, a) == piece_of(po0, np, g.d, l + 1, x)))
+      v = s[((long long)a * N + i) * cr + x];
+    t[e] = v;
+  }
+}
+
+// The sum's ranks on the inner links (after the gather has read them).
+__global__ void k_acc_ranks(int B, int d, int lo, int hi, int* ranks, const int* acc_rank) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    for (int l = lo + 1; l <= hi; ++l) ranks[(long long)b * (d + 1) + l] = acc_rank[(long long)b * (d + 1) + l];
+}
+
 // ------------------------------------------------------- per-mode apply
 // G'(a, j, b) = sum_i M(j, i) G(a, i, b): one GEMM (N x N) x (N x r_{k+1}) per
 // (filter, left index a).
@@ -414,6 +529,34 @@ void launch_shear_expand(cudaStream_t st, int B, const TTGeom& g, int m, int n, 
 void launch_rank_scale(cudaStream_t st, int B, int d, int* ranks, int lo, int hi, int S) {
   count_launches(1);
   k_rank_scale<<<(B + 255) / 256, 256, 0, st>>>(B, d, ranks, lo, hi, S);
+}
+
+void launch_block_copy(cudaStream_t st, int B, const TTGeom& g, int lo, int hi,
+                       float* const* src, float* const* dst, const int* ranks) {
+  count_launches(1);
+  k_block_copy<<<dim3(64, hi - lo + 1, B), 256, 0, st>>>(B, g, lo, to_ptrs(src, g.d),
+                                                        to_ptrs(dst, g.d), ranks);
+}
+
+void launch_acc_piece(cudaStream_t st, int B, const TTGeom& g, int lo, int hi, int p, int maxp,
+                      int capr, float* const* cur, float* const* acc, const int* ranks,
+                      int* acc_rank, int* piece_off) {
+  count_launches(2);
+  k_acc_begin<<<(B + 127) / 128, 128, 0, st>>>(B, g.d, lo, hi, p, maxp, capr, ranks, acc_rank,
+                                               piece_off);
+  k_acc_scatter<<<dim3(64, hi - lo + 1, B), 256, 0, st>>>(B, g, lo, hi, p, maxp, capr,
+                                                         to_ptrs(cur, g.d), to_ptrs(acc, g.d),
+                                                         ranks, piece_off);
+}
+
+void launch_acc_sum(cudaStream_t st, int B, const TTGeom& g, int lo, int hi, int np, int maxp,
+                    int capr, float* const* acc, float* const* alt, int* ranks,
+                    const int* acc_rank, const int* piece_off) {
+  count_launches(2);
+  k_acc_gather<<<dim3(64, hi - lo + 1, B), 256, 0, st>>>(B, g, lo, hi, np, maxp, capr,
+                                                        to_ptrs(acc, g.d), to_ptrs(alt, g.d),
+                                                        ranks, acc_rank, piece_off);
+  k_acc_ranks<<<(B + 127) / 128, 128, 0, st>>>(B, g.d, lo, hi, ranks, acc_rank);
 }
 
 void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, const int* ranks,

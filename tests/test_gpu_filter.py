@@ -12,7 +12,7 @@ import pytest
 import synth
 from oracle import pmf, tt
 
-from gpu_util import device_tables, lib_module, make_filter, oracle_grid, rel, tt_tol
+from gpu_util import cov_tol, device_tables, lib_module, make_filter, oracle_grid, rel, tt_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -197,3 +197,37 @@ def test_batch_split_into_concurrent_parts(G, monkeypatch):
     np.testing.assert_allclose(lc3, lc1, rtol=0, atol=1e-5)
     np.testing.assert_allclose(ll3, ll1, rtol=0, atol=1e-4)
     np.testing.assert_allclose(t3, t1, rtol=1e-3, atol=1e-6)
+
+
+def test_shears_in_pieces_small_grid(G):
+    """Every shear of the 32^4 workload spans 3 shifts; with a span of 2 each
+    runs as two rounded pieces (both triangles' couplings, including the
+    non-adjacent ones with block-diagonal middle cores) whose TT sum is
+    rounded again.  Same tolerance against the oracle as the whole
+    expansion."""
+    model = synth.config2(n=32)
+    mcs = [3, 4]
+    steps = 3
+    f = make_filter(G, model, batch=len(mcs), smax=2)
+    comps = device_tables(model, f.grid_axes())
+    g = oracle_grid(model)
+    oc = model.tables(g.axes)
+    zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
+    Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
+    bound = [0.0] * len(mcs)
+    for k in range(steps):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, np.stack([z[k] for z in zs]))
+        st = f.stats()
+        m, c, lc, ll = f.estimate()
+        for i in range(len(mcs)):
+            Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
+            Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
+            mo, co = pmf.moments(Ps[i], g)
+            bound[i] += tt_tol(model.eps, st[i]["tail_sum"])
+            e = rel(tt.densify(f.export_cores(i)), Ps[i])
+            assert e <= bound[i], (k, i, e, bound[i])
+            assert np.abs(m[i] - mo).max() < 1e-3 * g.delta_axis.min(), (k, i)
+            assert (np.abs(c[i] - co) <= cov_tol(g.delta_axis, co)).all(), (k, i)
+            assert abs(lc[i] - logc) < 1e-3, (k, i)
+            assert st[i]["max_rank"] <= model.rank_cap

@@ -70,6 +70,20 @@ def test_shear_rounded_within_eps(G, m, n, a):
     assert f.ranks()[0].max() <= 16
 
 
+@pytest.mark.parametrize("m,n,a,smax", [(0, 1, 0.3, 3), (0, 2, -0.45, 3), (2, 0, 0.3, 4),
+                                         (1, 2, 1.2, 4), (2, 1, -0.2, 3)])
+def test_wide_shear_in_pieces_within_eps(G, m, n, a, smax):
+    """Shears spanning 5-15 shifts with an expansion capacity of 3-4 shifts:
+    2-4 rounded pieces (adjacent and non-adjacent couplings, both triangles)
+    whose TT sum is rounded again."""
+    f, g, P = bumps_filter(G, smax=smax)
+    f.shear(m, n, a, do_round=True)
+    st = f.stats()[0]
+    ref = pmf.shear(P, g, m, n, a)
+    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, st["tail_sum"])
+    assert f.ranks()[0].max() <= 16
+
+
 def test_scale_and_convolve_are_exact(G):
     f, g, P = bumps_filter(G)
     f.scale(1, 0.93)
@@ -205,7 +219,10 @@ def test_invalid_arguments_leave_state(G):
         f.predict(np.full((3, 3), np.nan), np.eye(3))
     assert e.value.code == -2
     with pytest.raises(G.TTGBFError) as e:
-        f.shear(0, 1, 5.0)        # shift span far beyond max_shift_span
+        f.shear(0, 1, 10.0)       # 152 shifts: beyond max_shift_span^2 even in pieces
+    assert e.value.code == -5
+    with pytest.raises(G.TTGBFError) as e:
+        f.shear(0, 1, 5.0, do_round=False)  # 77 shifts unrounded: beyond max_shift_span
     assert e.value.code == -5
     with pytest.raises(G.TTGBFError) as e:
         f.shear(1, 1, 0.1)
