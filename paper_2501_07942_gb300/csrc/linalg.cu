@@ -77,6 +77,88 @@ __device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int*
   }
 }
 
+// One sweep's rounds of the one-sided Jacobi method (circle ordering) on the
+// kp columns of M (stride ldm floats, zero padded), one pair per group of LPP
+// lanes (a warp issues the instructions of 32 / LPP pairs at once): lane gl
+// of a group holds the float4s gl + LPP c (c < 32 / LPP) of both columns,
+// i.e. the first 128 entries with conflict-free 16-byte accesses, and, with
+// EXT (ldm = 160, LPP = 16), lanes gl < 8 also float4 32 + gl.  Returns the
+// rotations counted on lanes gl = 0.
+template <int LPP, bool EXT>
+__device__ __forceinline__ int jacobi_rounds(float* M, float* nrm, int kp, int npad, int ldm,
+                                             float floor2, float tol) {
+  static_assert(LPP == 8 || LPP == 16, "group width");
+  static_assert(!EXT || LPP == 16, "the 160-entry layout uses 16-lane groups");
+  constexpr int C4 = 32 / LPP;  // float4 of the first 128 entries per lane
+  constexpr int PW = 32 / LPP;  // pairs per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int grp = lane / LPP, gl = lane % LPP;
+  const bool gext = EXT && gl < 8;
+  float4* const M4 = reinterpret_cast<float4*>(M);
+  int myrot = 0;
+  for (int r = 0; r < npad - 1; ++r) {
+    // warp-uniform loop: every group reaches the shuffles of every pass
+    for (int q0 = PW * warp; q0 < npad / 2; q0 += PW * nwarps) {
+      const int q = q0 + grp;
+      int pp = 0, qq = 0;
+      bool act = q < npad / 2;
+      if (act) {
+        jacobi_pair(q, r, npad, &pp, &qq);
+        act = pp < kp && qq < kp;
+      }
+      float4* const xp = M4 + (pp * ldm >> 2);
+      float4* const yp = M4 + (qq * ldm >> 2);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 x[C4], y[C4], xe = z4, ye = z4;
+#pragma unroll
+      for (int c = 0; c < C4; ++c) {
+        x[c] = act ? xp[gl + LPP * c] : z4;
+        y[c] = act ? yp[gl + LPP * c] : z4;
+      }
+      if (act && gext) {
+        xe = xp[32 + gl];
+        ye = yp[32 + gl];
+      }
+      float g = xe.x * ye.x + xe.y * ye.y + xe.z * ye.z + xe.w * ye.w;
+#pragma unroll
+      for (int c = 0; c < C4; ++c)
+        g += x[c].x * y[c].x + x[c].y * y[c].y + x[c].z * y[c].z + x[c].w * y[c].w;
+#pragma unroll
+      for (int o = LPP / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+      if (!act) continue;  // no shuffles below
+      const float al = nrm[pp], be = nrm[qq];
+      if (g == 0.f || fminf(al, be) <= floor2) continue;
+      // al, be > 0 here; sqrt(al be) from the approximate reciprocal roots
+      if (!(fabsf(g) * rsqrtf(al) * rsqrtf(be) > tol)) continue;
+      // rotation parameters need not be correctly rounded: (cth, sth)
+      // below is orthogonal for any tt
+      const float zeta = __fdividef(be - al, 2.f * g);
+      const float az = fabsf(zeta);
+      const float w = fmaf(zeta, zeta, 1.f);  // >= 1
+      const float tt = (az > 1e15f ? __fdividef(0.5f, az) : __fdividef(1.f, az + w * rsqrtf(w))) *
+                       (zeta >= 0.f ? 1.f : -1.f);
+      const float cth = rsqrtf(fmaf(tt, tt, 1.f));
+      const float sth = cth * tt;
+      auto rot = [&](const float4& a, const float4& b, float4* pa, float4* pb) {
+        *pa = make_float4(cth * a.x - sth * b.x, cth * a.y - sth * b.y, cth * a.z - sth * b.z,
+                          cth * a.w - sth * b.w);
+        *pb = make_float4(sth * a.x + cth * b.x, sth * a.y + cth * b.y, sth * a.z + cth * b.z,
+                          sth * a.w + cth * b.w);
+      };
+#pragma unroll
+      for (int c = 0; c < C4; ++c) rot(x[c], y[c], xp + gl + LPP * c, yp + gl + LPP * c);
+      if (gext) rot(xe, ye, xp + 32 + gl, yp + 32 + gl);
+      if (gl == 0) {
+        nrm[pp] = al - tt * g;
+        nrm[qq] = be + tt * g;
+        ++myrot;
+      }
+    }
+    __syncthreads();
+  }
+  return myrot;
+}
+
 // Block sum for the SVD kernel (blockDim a multiple of 32, <= 1024).  Every
 // value summed here is non-negative, so FP32 keeps a relative accuracy of
 // about n u; FP64 would cost ~60x the issue slots on this part.
@@ -89,6 +171,225 @@ __device__ float block_sum_f(float v, float* red) {
   // every warp reduces the per-warp partials itself (same order in every
   // warp, so every thread gets the same value)
   return warp_sum(lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f);
+}
+
+// Pivoted Householder QR of the n x n matrix A (column-major, ld n, shared
+// memory) with its columns in registers: of the nw warps, warp w owns the
+// physical columns w + nw t (t < T = ceil(n / nw)) and lane l their rows
+// l + 32 e (e < E = ceil(n / 32)), so an update touches no shared memory but
+// the reflector.
+// Per step: every warp reduces the per-warp pivot candidates; the warp owning
+// the pivot forms its reflector (v = 1 at row k, scaled entries below; tau)
+// and publishes it; every warp applies it to its remaining columns, writes
+// their now final row-k entries R'(k, .) to A, downdates their norms
+// (recomputed when more than 99.9 % has cancelled) and leaves its candidate
+// for the next step.  Same stopping rule and outputs as the shared-memory
+// variant: perm[pos] = physical column at pivot position pos (positions k'..
+// n-1 get the columns never pivoted, ascending), R'(r, pos) =
+// A[perm[pos] n + r] for r < pos, rdiag = diag(R'), *dropped2 = squared norm
+// of the columns left over.  Returns k'.
+template <int E, int T>
+__device__ __forceinline__ int qrcp_reg(float* A, int n, float* nref, int kcap, double stop2, int* perm,
+                        float* rdiag, float* vbuf, int* mark, float* s_red, float* s_redf,
+                        int* s_redi, float* s_tau, double* dropped2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float a[T][E];
+  float nr2[T];  // current squared norms; nref (shared, n floats, on entry the
+                 // initial norms) keeps the norm at the last recomputation
+  unsigned alive = 0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int pc = warp + nw * t;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = lane + 32 * e;
+      a[t][e] = (pc < n && i < n) ? A[pc * n + i] : 0.f;
+    }
+    nr2[t] = pc < n ? nref[pc] : 0.f;
+    if (pc < n) alive |= 1u << t;
+  }
+  auto candidates = [&]() {
+    float rl = 0.f, bv = -1.f;
+    int bx = n;
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+      if ((alive >> t) & 1u) {
+        rl += nr2[t];
+        if (nr2[t] > bv) {
+          bv = nr2[t];
+          bx = warp + nw * t;
+        }
+      }
+    if (lane == 0) {
+      s_red[warp] = rl;
+      s_redf[warp] = bv;
+      s_redi[warp] = bx;
+    }
+  };
+  candidates();
+  __syncthreads();
+  int k = 0;
+  for (;; ++k) {
+    // every warp reduces the nw candidates (same result everywhere)
+    const float rem = warp_sum(lane < nw ? s_red[lane] : 0.f);
+    float best = lane < nw ? s_redf[lane] : -1.f;
+    int bi = lane < nw ? s_redi[lane] : n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    *dropped2 = (double)rem;
+    if (k >= kcap || (k > 0 && (double)rem <= stop2) || bi >= n) break;
+    const int ek = k >> 5, lk = k & 31;
+    if (warp == bi % nw) {
+      const int tp = bi / nw;
+      float col[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) col[e] = 0.f;
+#pragma unroll
+      for (int t = 0; t < T; ++t)
+        if (t == tp) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) col[e] = a[t][e];
+        }
+      float ak = 0.f;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e == ek) ak = col[e];
+      const float alpha = __shfl_sync(0xffffffffu, ak, lk);
+      float ss = 0.f;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (lane + 32 * e > k) ss = fmaf(col[e], col[e], ss);
+      ss = warp_sum(ss);
+      float tot = fmaf(alpha, alpha, ss), tail2 = ss, scale = 1.f;
+      // squares are exact enough unless the sum leaves [1e-30, 1e30]; such
+      // columns take a second pass scaled by the column maximum
+      const bool rescale = tot != 0.f && !(tot >= 1e-30f && tot <= 1e30f);
+      if (rescale) {
+        float mx = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (lane + 32 * e > k) mx = fmaxf(mx, fabsf(col[e]));
+        mx = fmaxf(warp_max(mx), fabsf(alpha));
+        const float inv = mx > 0.f ? 1.f / mx : 0.f;
+        float s2 = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (lane + 32 * e > k) {
+            const float x = col[e] * inv;
+            s2 = fmaf(x, x, s2);
+          }
+        s2 = warp_sum(s2);
+        const float al = alpha * inv;
+        tot = fmaf(al, al, s2);
+        tail2 = s2;
+        scale = mx;
+      }
+      float tau = 0.f, beta = alpha, scl = 0.f;
+      if (tail2 > 0.f && tot > 0.f) {
+        const float rs = rsqrtf(tot);
+        const float nm = tot * rs * scale;
+        const float aa = fabsf(alpha);
+        beta = alpha >= 0.f ? -nm : nm;
+        tau = fmaf(aa / scale, rs, 1.f);  // (|alpha| + nm) / nm
+        const float am = aa + nm;
+        scl = alpha >= 0.f ? __frcp_rn(am) : -__frcp_rn(am);
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        if (i < n) vbuf[i] = i > k ? col[e] * scl : (i == k ? 1.f : 0.f);
+      }
+      if (lane == 0) {
+        *s_tau = tau;
+        rdiag[k] = beta;
+        perm[k] = bi;
+      }
+      alive &= ~(1u << tp);
+    }
+    __syncthreads();
+    const float tau = *s_tau;
+    float v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = lane + 32 * e;
+      v[e] = i < n ? vbuf[i] : 0.f;
+    }
+    float dot[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      float d0 = 0.f;
+#pragma unroll
+      for (int e = 0; e < E; ++e) d0 = fmaf(v[e], a[t][e], d0);
+      dot[t] = d0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int t = 0; t < T; ++t) dot[t] += __shfl_xor_sync(0xffffffffu, dot[t], o);
+    float rl = 0.f, bv = -1.f;
+    int bx = n;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      if (!((alive >> t) & 1u)) continue;  // warp-uniform
+      const float f = tau * dot[t];
+#pragma unroll
+      for (int e = 0; e < E; ++e) a[t][e] = fmaf(-f, v[e], a[t][e]);
+      float xk = 0.f;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e == ek) xk = a[t][e];
+      const float rk = __shfl_sync(0xffffffffu, xk, lk);
+      const int pc = warp + nw * t;
+      if (lane == lk) A[pc * n + k] = rk;  // R'(k, pc) is final
+      float nr = nr2[t] - rk * rk;
+      if (!(nr >= 1e-3f * nref[pc])) {  // cancelled (or NaN): recompute
+        float sq = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (lane + 32 * e > k) sq = fmaf(a[t][e], a[t][e], sq);
+        nr = warp_sum(sq);
+        __syncwarp();
+        if (lane == 0) nref[pc] = nr;
+      }
+      nr2[t] = nr;
+      rl += nr;
+      if (nr > bv || (nr == bv && pc < bx)) {
+        bv = nr;
+        bx = pc;
+      }
+    }
+    if (lane == 0) {
+      s_red[warp] = rl;
+      s_redf[warp] = bv;
+      s_redi[warp] = bx;
+    }
+    __syncthreads();
+  }
+  // positions k..n-1: the columns never pivoted, ascending (mark the
+  // pivots in `mark` (n ints), then one warp compacts the rest)
+  for (int c = threadIdx.x; c < n; c += blockDim.x) mark[c] = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < k; q += blockDim.x) mark[perm[q]] = 1;
+  __syncthreads();
+  if (warp == 0) {
+    int pos = k;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int c = c0 + lane;
+      const bool left = c < n && mark[c] == 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, left);
+      if (left) perm[pos + __popc(bal & ((1u << lane) - 1u))] = c;
+      pos += __popc(bal);
+    }
+  }
+  __syncthreads();
+  return k;
 }
 
 // SVD of the n x n R factor of problem b, in three steps:
@@ -164,130 +465,157 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   // then every warp updates its trailing columns, downdates their norms
   // (recomputed when more than 99.9 % has cancelled) and leaves its part of
   // the next pivot search.
-  float* nref = reinterpret_cast<float*>(ord + kMaxN);  // norm at the last recomputation
-  for (int c = tid; c < n; c += blockDim.x) nref[c] = nrm[c];
-  {
-    float rl = 0.f, bv = -1.f;
-    int bx = n;
-    for (int c = warp; c < n; c += nwarps) {  // same column split as the updates below
-      const float v = nrm[c];
-      rl += v;
-      if (v > bv) {
-        bv = v;
-        bx = c;
-      }
-    }
-    if (lane == 0) {
-      s_red[warp] = rl;
-      s_redf[warp] = bv;
-      s_redi[warp] = bx;
-    }
-  }
-  __syncthreads();
+  // With 32 warps, or 16 warps and n <= 96, the columns live in registers
+  // (qrcp_reg); otherwise in shared memory.
   int k = 0;
   double dropped2 = 0.0;
-  for (;; ++k) {
-    // every warp reduces the per-warp partials (same result everywhere)
-    const float rem = warp_sum(lane < nwarps ? s_red[lane] : 0.f);
-    float best = lane < nwarps ? s_redf[lane] : -1.f;
-    int bi = lane < nwarps ? s_redi[lane] : n;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
-      }
-    }
-    dropped2 = (double)rem;
-    if (k >= kcap || (k > 0 && (double)rem <= stop2) || bi >= n) break;
-    if (warp == 0) {
-      const int pv = perm[bi];
-      __syncwarp();
-      if (lane == 0) {
-        perm[bi] = perm[k];
-        perm[k] = pv;
-      }
-      float* colk = A + pv * n;
-      float ss = 0.f;
-      for (int i = k + 1 + lane; i < n; i += 32) ss = fmaf(colk[i], colk[i], ss);
-      ss = warp_sum(ss);
-      const float alpha = colk[k];
-      float tot = fmaf(alpha, alpha, ss), tail2 = ss, scale = 1.f;
-      // squares are exact enough unless the sum leaves [1e-30, 1e30]; such
-      // columns take a second pass scaled by the column maximum
-      const bool rescale = tot != 0.f && !(tot >= 1e-30f && tot <= 1e30f);
-      if (rescale) {
-        float mx = 0.f;
-        for (int i = k + 1 + lane; i < n; i += 32) mx = fmaxf(mx, fabsf(colk[i]));
-        mx = fmaxf(warp_max(mx), fabsf(alpha));
-        const float inv = mx > 0.f ? 1.f / mx : 0.f;
-        float s2 = 0.f;
-        for (int i = k + 1 + lane; i < n; i += 32) {
-          const float x = colk[i] * inv;
-          s2 = fmaf(x, x, s2);
+  float* vbuf = coef;  // the pivot's reflector; coef is free until step 3
+  // (pinv serves as scratch; it is set from perm after the QR)
+#define TTGBF_QRCP(E, T)                                                                 \
+  k = qrcp_reg<E, T>(A, n, nrm, kcap, stop2, perm, rdiag, vbuf, pinv, s_red, s_redf, s_redi, \
+                     &s_tau, &dropped2)
+  const bool reg = nwarps == 32 || (nwarps == 16 && n <= 96);
+  if (nwarps == 32) {
+    const int E = (n + 31) >> 5;
+    if (E <= 1) TTGBF_QRCP(1, 1);
+    else if (E == 2) TTGBF_QRCP(2, 2);
+    else if (E == 3) TTGBF_QRCP(3, 3);
+    else if (E == 4) TTGBF_QRCP(4, 4);
+    else TTGBF_QRCP(5, 5);
+  } else if (reg) {
+    const int T = (n + 15) >> 4;  // 16 warps
+    if (T <= 1) TTGBF_QRCP(1, 1);
+    else if (T == 2) TTGBF_QRCP(1, 2);
+    else if (T == 3) TTGBF_QRCP(2, 3);
+    else if (T == 4) TTGBF_QRCP(2, 4);
+    else if (T == 5) TTGBF_QRCP(3, 5);
+    else TTGBF_QRCP(3, 6);
+  }
+#undef TTGBF_QRCP
+  if (!reg) {
+    float* nref = reinterpret_cast<float*>(ord + kMaxN);  // norm at the last recomputation
+    for (int c = tid; c < n; c += blockDim.x) nref[c] = nrm[c];
+    {
+      float rl = 0.f, bv = -1.f;
+      int bx = n;
+      for (int c = warp; c < n; c += nwarps) {  // same column split as the updates below
+        const float v = nrm[c];
+        rl += v;
+        if (v > bv) {
+          bv = v;
+          bx = c;
         }
-        s2 = warp_sum(s2);
-        const float al = alpha * inv;
-        tot = fmaf(al, al, s2);
-        tail2 = s2;
-        scale = mx;
       }
-      float tau = 0.f, beta = alpha, scl = 0.f;
-      if (tail2 > 0.f && tot > 0.f) {
-        const float rs = rsqrtf(tot);
-        const float nm = tot * rs * scale;
-        const float aa = fabsf(alpha);
-        beta = alpha >= 0.f ? -nm : nm;
-        tau = fmaf(aa / scale, rs, 1.f);  // (|alpha| + nm) / nm
-        const float am = aa + nm;
-        scl = alpha >= 0.f ? __frcp_rn(am) : -__frcp_rn(am);
-        for (int i = k + 1 + lane; i < n; i += 32) colk[i] *= scl;
-      }
-      __syncwarp();
       if (lane == 0) {
-        s_tau = tau;
-        rdiag[k] = beta;
-        colk[k] = 1.f;
+        s_red[warp] = rl;
+        s_redf[warp] = bv;
+        s_redi[warp] = bx;
       }
     }
     __syncthreads();
-    const float tau = s_tau;
-    const float* colk = A + perm[k] * n;
-    float rl = 0.f, bv = -1.f;
-    int bx = n;
-    for (int c = k + 1 + warp; c < n; c += nwarps) {
-      const int pc = perm[c];
-      float* colc = A + pc * n;
-      if (tau != 0.f) {
-        float dot = 0.f;
-        for (int i = k + lane; i < n; i += 32) dot = fmaf(colk[i], colc[i], dot);
-        dot = warp_sum(dot) * tau;
-        for (int i = k + lane; i < n; i += 32) colc[i] = fmaf(-dot, colk[i], colc[i]);
+    for (;; ++k) {
+      // every warp reduces the per-warp partials (same result everywhere)
+      const float rem = warp_sum(lane < nwarps ? s_red[lane] : 0.f);
+      float best = lane < nwarps ? s_redf[lane] : -1.f;
+      int bi = lane < nwarps ? s_redi[lane] : n;
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      dropped2 = (double)rem;
+      if (k >= kcap || (k > 0 && (double)rem <= stop2) || bi >= n) break;
+      if (warp == 0) {
+        const int pv = perm[bi];
         __syncwarp();
+        if (lane == 0) {
+          perm[bi] = perm[k];
+          perm[k] = pv;
+        }
+        float* colk = A + pv * n;
+        float ss = 0.f;
+        for (int i = k + 1 + lane; i < n; i += 32) ss = fmaf(colk[i], colk[i], ss);
+        ss = warp_sum(ss);
+        const float alpha = colk[k];
+        float tot = fmaf(alpha, alpha, ss), tail2 = ss, scale = 1.f;
+        // squares are exact enough unless the sum leaves [1e-30, 1e30]; such
+        // columns take a second pass scaled by the column maximum
+        const bool rescale = tot != 0.f && !(tot >= 1e-30f && tot <= 1e30f);
+        if (rescale) {
+          float mx = 0.f;
+          for (int i = k + 1 + lane; i < n; i += 32) mx = fmaxf(mx, fabsf(colk[i]));
+          mx = fmaxf(warp_max(mx), fabsf(alpha));
+          const float inv = mx > 0.f ? 1.f / mx : 0.f;
+          float s2 = 0.f;
+          for (int i = k + 1 + lane; i < n; i += 32) {
+            const float x = colk[i] * inv;
+            s2 = fmaf(x, x, s2);
+          }
+          s2 = warp_sum(s2);
+          const float al = alpha * inv;
+          tot = fmaf(al, al, s2);
+          tail2 = s2;
+          scale = mx;
+        }
+        float tau = 0.f, beta = alpha, scl = 0.f;
+        if (tail2 > 0.f && tot > 0.f) {
+          const float rs = rsqrtf(tot);
+          const float nm = tot * rs * scale;
+          const float aa = fabsf(alpha);
+          beta = alpha >= 0.f ? -nm : nm;
+          tau = fmaf(aa / scale, rs, 1.f);  // (|alpha| + nm) / nm
+          const float am = aa + nm;
+          scl = alpha >= 0.f ? __frcp_rn(am) : -__frcp_rn(am);
+          for (int i = k + 1 + lane; i < n; i += 32) colk[i] *= scl;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          s_tau = tau;
+          rdiag[k] = beta;
+          colk[k] = 1.f;
+        }
       }
-      const float rk = colc[k];
-      float nr = nrm[pc] - rk * rk;
-      if (!(nr >= 1e-3f * nref[pc])) {  // cancelled (or NaN): recompute
-        float sq = 0.f;
-        for (int i = k + 1 + lane; i < n; i += 32) sq = fmaf(colc[i], colc[i], sq);
-        nr = warp_sum(sq);
-        if (lane == 0) nref[pc] = nr;
+      __syncthreads();
+      const float tau = s_tau;
+      const float* colk = A + perm[k] * n;
+      float rl = 0.f, bv = -1.f;
+      int bx = n;
+      for (int c = k + 1 + warp; c < n; c += nwarps) {
+        const int pc = perm[c];
+        float* colc = A + pc * n;
+        if (tau != 0.f) {
+          float dot = 0.f;
+          for (int i = k + lane; i < n; i += 32) dot = fmaf(colk[i], colc[i], dot);
+          dot = warp_sum(dot) * tau;
+          for (int i = k + lane; i < n; i += 32) colc[i] = fmaf(-dot, colk[i], colc[i]);
+          __syncwarp();
+        }
+        const float rk = colc[k];
+        float nr = nrm[pc] - rk * rk;
+        if (!(nr >= 1e-3f * nref[pc])) {  // cancelled (or NaN): recompute
+          float sq = 0.f;
+          for (int i = k + 1 + lane; i < n; i += 32) sq = fmaf(colc[i], colc[i], sq);
+          nr = warp_sum(sq);
+          if (lane == 0) nref[pc] = nr;
+        }
+        if (lane == 0) nrm[pc] = nr;
+        rl += nr;
+        if (nr > bv || (nr == bv && c < bx)) {
+          bv = nr;
+          bx = c;
+        }
       }
-      if (lane == 0) nrm[pc] = nr;
-      rl += nr;
-      if (nr > bv || (nr == bv && c < bx)) {
-        bv = nr;
-        bx = c;
+      if (lane == 0) {
+        s_red[warp] = rl;
+        s_redf[warp] = bv;
+        s_redi[warp] = bx;
       }
+      __syncthreads();
     }
-    if (lane == 0) {
-      s_red[warp] = rl;
-      s_redf[warp] = bv;
-      s_redi[warp] = bx;
-    }
-    __syncthreads();
   }
   // dropped2: squared norm of the columns left over
   const int kp = k;  // >= 1
@@ -324,49 +652,9 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
     for (int c = lane; c < kp; c += 32) tnorm += nrm[c];
     tnorm = warp_sum(tnorm);
     const float floor2 = 1e-14f * tnorm;
-    int myrot = 0;
-    for (int r = 0; r < npad - 1; ++r) {
-      for (int q = warp; q < npad / 2; q += nwarps) {
-        int pp, qq;
-        jacobi_pair(q, r, npad, &pp, &qq);
-        if (pp >= kp || qq >= kp) continue;
-        const float4 x0 = *col4(pp, 0), y0 = *col4(qq, 0);
-        float4 x1 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = x1;
-        if (ext && lane < 8) {
-          x1 = *col4(pp, 1);
-          y1 = *col4(qq, 1);
-        }
-        float g = x0.x * y0.x + x0.y * y0.y + x0.z * y0.z + x0.w * y0.w +
-                  (x1.x * y1.x + x1.y * y1.y + x1.z * y1.z + x1.w * y1.w);
-        g = warp_sum(g);
-        const float al = nrm[pp], be = nrm[qq];
-        if (g == 0.f || fminf(al, be) <= floor2 || !(fabsf(g) > tol * sqrtf(al * be))) continue;
-        // rotation parameters need not be correctly rounded: (cth, sth)
-        // below is orthogonal for any tt
-        const float zeta = __fdividef(be - al, 2.f * g);
-        const float az = fabsf(zeta);
-        const float tt = (az > 1e15f ? __fdividef(0.5f, az)
-                                     : __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f)))) *
-                         (zeta >= 0.f ? 1.f : -1.f);
-        const float cth = rsqrtf(1.f + tt * tt);
-        const float sth = cth * tt;
-        auto rot = [&](const float4& x, const float4& y, float4* px, float4* py) {
-          *px = make_float4(cth * x.x - sth * y.x, cth * x.y - sth * y.y, cth * x.z - sth * y.z,
-                            cth * x.w - sth * y.w);
-          *py = make_float4(sth * x.x + cth * y.x, sth * x.y + cth * y.y, sth * x.z + cth * y.z,
-                            sth * x.w + cth * y.w);
-        };
-        rot(x0, y0, col4(pp, 0), col4(qq, 0));
-        if (ext && lane < 8) rot(x1, y1, col4(pp, 1), col4(qq, 1));
-        if (lane == 0) {
-          nrm[pp] = al - tt * g;
-          nrm[qq] = be + tt * g;
-        }
-        ++myrot;
-      }
-      __syncthreads();
-    }
-    if (lane == 0 && myrot > 0) atomicAdd(&s_rot, myrot);
+    const int myrot = ext ? jacobi_rounds<16, true>(M, nrm, kp, npad, ldm, floor2, tol)
+                          : jacobi_rounds<8, false>(M, nrm, kp, npad, ldm, floor2, tol);
+    if (myrot > 0) atomicAdd(&s_rot, myrot);  // counted on one lane per pair group
     const int any = __syncthreads_or(myrot > 0);
     if (tid == 0) {
       const double nn = (double)n;
@@ -809,8 +1097,10 @@ void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, doub
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
                    long long core0_cap, double* flops) {
   count_launches(1);
-  // truncation stages have at most rank_cap + 16 Jacobi columns: half the warps suffice
-  const int threads = mode == kStageRight ? 1024 : 512;
+  // truncation stages have at most rank_cap + 16 Jacobi columns: half the warps
+  // suffice (two CTAs per SM); the split of the merged 2-site core (n = N_0)
+  // takes 32 warps so that its pivoted QR keeps the columns in registers
+  const int threads = mode == kStageLeft ? 512 : 1024;
   k_svd<<<B, threads, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs, P1,
                                                              P2, core0_out, core0_cap, flops);
 }

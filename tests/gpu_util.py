@@ -36,6 +36,19 @@ def cov_tol(delta_axis, cov):
     return 1e-3 * (D[:, None] * sig[None, :] + sig[:, None] * D[None, :])
 
 
+def mean_tol(delta_axis, cov, tail_acc):
+    """Posterior-mean tolerance per mode: 1e-3 grid spacings, plus, where
+    the rounding discarded more than eps (the rank cap binds), 2 tau sigma_m:
+    tau = the discarded relative tails summed over the steps so far bounds
+    the truncation's relative L2 change of the density, which moves the
+    mean of mode m by about tau times that marginal's standard deviation
+    sigma_m (from the oracle's covariance).  Without cap hits tau is at the
+    eps level and the bound is the plain 1e-3 grid spacings."""
+    D = np.asarray(delta_axis, dtype=np.float64)
+    sig = np.sqrt(np.maximum(np.diag(cov), 0.0))
+    return 1e-3 * D + 2.0 * tail_acc * sig
+
+
 def device_tables(model: synth.Model, axes):
     import torch
     return [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device="cuda"))

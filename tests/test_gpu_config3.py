@@ -13,7 +13,7 @@ z_i = x_{2i}^2 / 20 + v_i, rank cap 32, eps 1e-5.
 
 Tolerances as for the other workloads: per step 10 (eps + tau) + 1e-5 in
 relative Frobenius norm, summed over the steps; means within 1e-3 grid
-spacings; covariances within the matching 1e-3 (D_i sigma_j + D_j sigma_i);
+spacings (plus 2 tau sigma where the rank cap binds); covariances within the matching 1e-3 (D_i sigma_j + D_j sigma_i);
 log c within 1e-3.  The shear span of this workload is at most 5 up
 to N = 128 (|0.1 xi_vel / Delta_pos| <= 1.59), so the rank expansion stays at
 32 x 5 = 160 columns; at N = 256 it is 9 and the shears run in pieces."""
@@ -23,7 +23,8 @@ import pytest
 import synth
 from oracle import pmf, tt
 
-from gpu_util import cov_tol, device_tables, lib_module, make_filter, oracle_grid, rel, tt_tol
+from gpu_util import (cov_tol, device_tables, lib_module, make_filter, mean_tol, oracle_grid,
+                      rel, tt_tol)
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +57,7 @@ def test_config3_small_grid_vs_dense_oracle(G, d, n, steps):
     zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
     Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
     bound = [0.0] * len(mcs)
+    tacc = [0.0] * len(mcs)
     for k in range(steps):
         f.predict(model.F, model.Q)
         f.update(comps, model.R, np.stack([z[k] for z in zs]))
@@ -66,9 +68,10 @@ def test_config3_small_grid_vs_dense_oracle(G, d, n, steps):
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
             mo, co = pmf.moments(Ps[i], g)
             bound[i] += tt_tol(model.eps, st[i]["tail_sum"])
+            tacc[i] += st[i]["tail_sum"]
             e = rel(tt.densify(f.export_cores(i)), Ps[i])
             assert e <= bound[i], (k, i, e, bound[i])
-            assert np.abs(m[i] - mo).max() < 1e-3 * g.delta_axis.min(), (k, i)
+            assert (np.abs(m[i] - mo) <= mean_tol(g.delta_axis, co, tacc[i])).all(), (k, i)
             assert (np.abs(c[i] - co) <= cov_tol(g.delta_axis, co)).all(), (k, i)
             assert abs(lc[i] - logc) < 1e-3, (k, i)
             assert st[i]["max_rank"] <= model.rank_cap
@@ -89,6 +92,7 @@ def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
     tabs = [bm.tables(gb.axes) for bm, gb in zip(pairs, grids)]
     P = [[pmf.prior(gb, bm.m0, bm.P0) for bm, gb in zip(pairs, grids)] for _ in mcs]
     bound = [0.0] * len(mcs)
+    tacc = [0.0] * len(mcs)
     for k in range(steps):
         f.predict(model.F, model.Q)
         f.update(comps, model.R, np.stack([z[k] for z in zs]))
@@ -114,10 +118,10 @@ def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
             diff2 = tt.inner(cores, cores) - 2.0 * tt.inner(cores, exact) + nn
             e = float(np.sqrt(max(diff2, 0.0) / nn))
             bound[b] += tt_tol(model.eps, st[b]["tail_sum"])
+            tacc[b] += st[b]["tail_sum"]
             assert e <= bound[b], (k, b, e, bound[b])
-            dmin = min(gb.delta_axis.min() for gb in grids)
-            assert np.abs(m[b] - mean).max() < 1e-3 * dmin, (k, b, m[b], mean)
             D = np.concatenate([gb.delta_axis for gb in grids])
+            assert (np.abs(m[b] - mean) <= mean_tol(D, cov, tacc[b])).all(), (k, b, m[b], mean)
             assert (np.abs(c[b] - cov) <= cov_tol(D, cov)).all(), (k, b, c[b] - cov)
             assert abs(lc[b] - logc) < 1e-3, (k, b, lc[b], logc)
             r = f.ranks()[b]

@@ -5,14 +5,17 @@ Tolerances: per step the TT density may deviate from the oracle by
 10 * (eps + tau) + 1e-5 in relative Frobenius norm, tau being the discarded
 relative tail the rounding reports (tau = 0 when the rank cap does not bind).
 Over several steps the bounds of the steps add.  Posterior means agree within
-1e-3 grid spacings."""
+1e-3 grid spacings, plus 2 tau sigma_m where the rank cap binds (tau the
+summed discarded tails, sigma_m the oracle's marginal standard deviation);
+the same reading of the cap-binding regime as for the density bound."""
 import numpy as np
 import pytest
 
 import synth
 from oracle import pmf, tt
 
-from gpu_util import cov_tol, device_tables, lib_module, make_filter, oracle_grid, rel, tt_tol
+from gpu_util import (cov_tol, device_tables, lib_module, make_filter, mean_tol, oracle_grid,
+                      rel, tt_tol)
 
 pytestmark = pytest.mark.gpu
 
@@ -34,6 +37,7 @@ def run_compare(G, model, mcs, steps, batch_extra=0):
     zs += [zs[0]] * batch_extra
     Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
     bound = [0.0] * len(mcs)
+    tacc = [0.0] * len(mcs)
     out = []
     for k in range(steps):
         f.predict(model.F, model.Q)
@@ -46,9 +50,11 @@ def run_compare(G, model, mcs, steps, batch_extra=0):
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
             mo, co = pmf.moments(Ps[i], g)
             bound[i] += tt_tol(model.eps, st[i]["tail_sum"])  # predict + update tails
+            tacc[i] += st[i]["tail_sum"]
             e = rel(tt.densify(f.export_cores(i)), Ps[i])
-            row.append((e, bound[i], np.abs(m[i] - mo).max() / g.delta_axis.min(),
-                        abs(lc[i] - logc), st[i]["max_rank"]))
+            # mean error in units of its tolerance (< 1 passes)
+            merr = float((np.abs(m[i] - mo) / mean_tol(g.delta_axis, co, tacc[i])).max())
+            row.append((e, bound[i], merr, abs(lc[i] - logc), st[i]["max_rank"]))
         out.append(row)
     return out, f
 
@@ -59,7 +65,7 @@ def test_config1_vs_oracle(G):
     for k, row in enumerate(out):
         for e, bound, merr, dlc, mr in row:
             assert e <= bound, (k, e, bound)
-            assert merr < 1e-3, (k, merr)
+            assert merr < 1.0, (k, merr)
             assert dlc < 1e-3 + bound, (k, dlc)
             assert mr <= model.rank_cap
 
@@ -87,7 +93,7 @@ def test_config2_small_grid_multi_step(G):
     for k, row in enumerate(out):
         for e, bound, merr, dlc, mr in row:
             assert e <= bound, (k, e, bound)
-            assert merr < 1e-3, (k, merr)
+            assert merr < 1.0, (k, merr)
             assert mr <= 16
 
 
@@ -120,7 +126,7 @@ def test_config2_one_step_from_oracle_posterior(G):
     assert rel(tt.densify(f.export_cores(0)), Pu) <= tt_tol(model.eps, t_step)
     m, c, lc, ll = f.estimate()
     mo, co = pmf.moments(Pu, g)
-    assert np.abs(m[0] - mo).max() < 1e-3 * g.delta_axis.min()
+    assert (np.abs(m[0] - mo) <= mean_tol(g.delta_axis, co, t_step)).all()
     assert abs(lc[0] - logc) < 1e-3
 
 
@@ -129,7 +135,7 @@ def test_batch_filters_are_independent(G):
     out, f = run_compare(G, model, [7, 8, 9], 3, batch_extra=2)
     for row in out:
         for e, bound, merr, dlc, mr in row:
-            assert e <= bound and merr < 1e-3
+            assert e <= bound and merr < 1.0
     # the two extra filters saw filter 0's measurements
     a = tt.densify(f.export_cores(0))
     np.testing.assert_allclose(tt.densify(f.export_cores(3)), a, rtol=0, atol=0)
@@ -150,18 +156,20 @@ def test_config2_full_size_bench_launch(G):
     oc = model.tables(g.axes)
     P = pmf.prior(g, model.m0, model.P0)
     bound = 0.0
+    tacc = 0.0
     for k in range(2):
         f.predict(model.F, model.Q)
         f.update(comps, model.R, zs[k])
         st = f.stats()
         bound += tt_tol(model.eps, st[0]["tail_sum"])
+        tacc += st[0]["tail_sum"]
         P, _ = pmf.predict_rg(P, g, model.F, model.Q)
         P, logc = pmf.update(P, g, pmf.likelihood(g, oc, zs[k][0], model.R))
         m, c, lc, ll = f.estimate()
         e = rel(tt.densify(f.export_cores(0)), P)
         assert e <= bound, (k, e, bound)
         mo, co = pmf.moments(P, g)
-        assert np.abs(m[0] - mo).max() < 1e-3 * g.delta_axis.min()
+        assert (np.abs(m[0] - mo) <= mean_tol(g.delta_axis, co, tacc)).all()
         assert abs(lc[0] - logc) < 1e-3
         assert np.isfinite(m).all() and np.isfinite(c).all() and np.isfinite(lc).all()
         assert (np.abs(m) < 8).all()
@@ -215,6 +223,7 @@ def test_shears_in_pieces_small_grid(G):
     zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
     Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
     bound = [0.0] * len(mcs)
+    tacc = [0.0] * len(mcs)
     for k in range(steps):
         f.predict(model.F, model.Q)
         f.update(comps, model.R, np.stack([z[k] for z in zs]))
@@ -225,9 +234,10 @@ def test_shears_in_pieces_small_grid(G):
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
             mo, co = pmf.moments(Ps[i], g)
             bound[i] += tt_tol(model.eps, st[i]["tail_sum"])
+            tacc[i] += st[i]["tail_sum"]
             e = rel(tt.densify(f.export_cores(i)), Ps[i])
             assert e <= bound[i], (k, i, e, bound[i])
-            assert np.abs(m[i] - mo).max() < 1e-3 * g.delta_axis.min(), (k, i)
+            assert (np.abs(m[i] - mo) <= mean_tol(g.delta_axis, co, tacc[i])).all(), (k, i)
             assert (np.abs(c[i] - co) <= cov_tol(g.delta_axis, co)).all(), (k, i)
             assert abs(lc[i] - logc) < 1e-3, (k, i)
             assert st[i]["max_rank"] <= model.rank_cap
