@@ -189,7 +189,7 @@ __device__ float block_sum_f(float v, float* red) {
 // A[perm[pos] n + r] for r < pos, rdiag = diag(R'), *dropped2 = squared norm
 // of the columns left over.  Returns k'.
 template <int E, int T>
-__device__ __forceinline__ int qrcp_reg(float* A, int n, float* nref, int kcap, double stop2, int* perm,
+__device__ __forceinline__ int qrcp_reg(float* A, int n, float* nref, int kcap, float stop2, int* perm,
                         float* rdiag, float* vbuf, int* mark, float* s_red, float* s_redf,
                         int* s_redi, float* s_tau, double* dropped2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -243,8 +243,10 @@ __device__ __forceinline__ int qrcp_reg(float* A, int n, float* nref, int kcap, 
         bi = oi;
       }
     }
-    *dropped2 = (double)rem;
-    if (k >= kcap || (k > 0 && (double)rem <= stop2) || bi >= n) break;
+    if (k >= kcap || (k > 0 && rem <= stop2) || bi >= n) {
+      *dropped2 = (double)rem;
+      break;
+    }
     const int ek = k >> 5, lk = k & 31;
     if (warp == bi % nw) {
       const int tp = bi / nw;
@@ -445,18 +447,30 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
     if (lane == 0) nrm[c] = s;
   }
   __syncthreads();
-  double tot = 0.0;
+  float totf;
   {
     float s = 0.f;
     for (int c = tid; c < n; c += blockDim.x) s += nrm[c];
-    tot = (double)block_sum_f(s, s_red);
+    totf = block_sum_f(s, s_red);
   }
-  double normA = 0.0;
-  if (mode != kStageRight) normA = first ? sqrt(tot) : rs.normA[b];
-  const double delta = (mode == kStageRight || d <= 1) ? 0.0 : eps * normA / sqrt((double)(d - 1));
-  // orthogonalisation drops what is left once it is at the FP32 noise level of
-  // R (1e-7 sqrt(n) ||R||_F); truncation stops once the rest is below 0.3 delta
-  const double stop2 = (mode == kStageRight) ? 1e-14 * n * tot : 0.09 * delta * delta;
+  // The FP64 scalars (norm, truncation threshold) are formed by thread 0
+  // alone: FP64 instructions issue at a small fraction of the FP32 rate on
+  // this part, so a few of them per thread would cost more than the FP32
+  // work around them.  The per-step tests use the FP32 threshold stop2f.
+  __shared__ float s_stop2f;
+  double normA = 0.0, delta = 0.0;
+  if (tid == 0) {
+    const double tot = (double)totf;
+    if (mode != kStageRight) normA = first ? sqrt(tot) : rs.normA[b];
+    delta = (mode == kStageRight || d <= 1) ? 0.0 : eps * normA / sqrt((double)(d - 1));
+    // orthogonalisation drops what is left once it is at the FP32 noise level
+    // of R (1e-7 sqrt(n) ||R||_F); truncation stops once the rest is below
+    // 0.3 delta
+    const double stop2 = (mode == kStageRight) ? 1e-14 * n * tot : 0.09 * delta * delta;
+    s_stop2f = (float)stop2;
+  }
+  __syncthreads();
+  const float stop2f = s_stop2f;
   const int kcap = (mode == kStageRight) ? n : min(n, rank_cap + 16);
 
   // ---- 1. QR with column pivoting.  Columns never move: perm[pos] is the
@@ -472,7 +486,7 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   float* vbuf = coef;  // the pivot's reflector; coef is free until step 3
   // (pinv serves as scratch; it is set from perm after the QR)
 #define TTGBF_QRCP(E, T)                                                                 \
-  k = qrcp_reg<E, T>(A, n, nrm, kcap, stop2, perm, rdiag, vbuf, pinv, s_red, s_redf, s_redi, \
+  k = qrcp_reg<E, T>(A, n, nrm, kcap, stop2f, perm, rdiag, vbuf, pinv, s_red, s_redf, s_redi, \
                      &s_tau, &dropped2)
   const bool reg = nwarps == 32 || (nwarps == 16 && n <= 96);
   if (nwarps == 32) {
@@ -527,8 +541,10 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
           bi = oi;
         }
       }
-      dropped2 = (double)rem;
-      if (k >= kcap || (k > 0 && (double)rem <= stop2) || bi >= n) break;
+      if (k >= kcap || (k > 0 && rem <= stop2f) || bi >= n) {
+        dropped2 = (double)rem;
+        break;
+      }
       if (warp == 0) {
         const int pv = perm[bi];
         __syncwarp();
@@ -1033,7 +1049,7 @@ __global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, 
       GemmDesc x{p1, cur_a + (long long)b * g.cap[k], alt_a + (long long)b * g.cap[k], rn, cols, rkk,
                  kMaxN, cols, cols};
       if (vS > 0) {
-        const int Nm = g.n[k - 1], rmt = rm / vS, rkt = rkk / vS;
+        const int Nm = g.n[k - 1], rkt = rkk / vS;
         GemmDesc* dd = gw.desc + (long long)b * dstride;
         dd[0] = x;
         for (int q = 0; q + 1 < dstride; ++q) {
