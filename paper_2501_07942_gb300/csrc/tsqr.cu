@@ -5,7 +5,7 @@
 // A CTA of 8 warps keeps the n x n upper-triangular R of the rows it has
 // consumed in shared memory (zero at the start) and takes the rows in blocks
 // of 128: lane (warp w, half h, row lane l) holds rows 8 l + a (a < 8) of
-// the block for the columns 16 q + 2 w + h (q < ceil(n / 16)).  Column j of
+// the block for the columns 16 q + w + 8 h (q < ceil(n / 16)).  Column j of
 // [R; block] is reduced by one reflector that touches only row j of R and
 // the block (R is triangular), so a block costs n steps of
 //   reflector: norm of the block's column j (16-lane shuffle sum) with
@@ -50,9 +50,10 @@ struct __align__(16) QrShared {
 };
 
 // Named barriers 1..3 (step j uses 1 + j % 3).  A warp that only arrives at
-// one step's barrier (the owner, which does not wait) is an owner for at
-// most two steps in a row, then waits at the next one, so no warp reaches
-// the same barrier id again before that barrier's previous use completed.
+// one step's barrier (the owner, which does not wait) is never the owner of
+// two consecutive steps (consecutive columns belong to different warps), so
+// it waits at the next barrier and no warp reaches the same barrier id again
+// before that barrier's previous use completed.
 __device__ __forceinline__ void qr_bar_sync(int id) {
   static_assert(kQrThreads == 256, "barrier thread count");
   if (id == 1) asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -216,8 +217,8 @@ __device__ __forceinline__ void qr_group(float (&A)[kQrRPL][CPL], int n, float* 
     const int buf = j & 3, nbuf = (j + 1) & 3, bar = 1 + j % 3;
     const float tau = sh.tau[buf];
     const int jn = j + 1;
-    const bool owner = jn < n && warp == ((jn & (kQrSlots - 1)) >> 1);
-    const bool own = half == (jn & 1);
+    const bool owner = jn < n && warp == (jn & 7);
+    const bool own = half == ((jn >> 3) & 1);
     const float* v = sh.v[buf];
     if (owner) {
       // the owner's chain: update of column jn, its reflector, publish;
@@ -256,7 +257,9 @@ __device__ __noinline__ void qr_rows(const float* p, long long rs, long long cs,
                                      long long M, int n, bool coherent, float* out, float* Rs,
                                      QrShared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rl = lane & 15, half = lane >> 4, slot = 2 * warp + half;
+  // consecutive columns belong to different warps, so the owner of the next
+  // column has finished the previous step's updates when its reflector is due
+  const int rl = lane & 15, half = lane >> 4, slot = warp + 8 * half;
   for (int t = threadIdx.x; t < n * kQrLd; t += kQrThreads) Rs[t] = 0.f;
   float A[kQrRPL][CPL];
   for (long long done = 0; done < M; done += kQrRows) {
