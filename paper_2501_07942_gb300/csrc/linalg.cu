@@ -83,10 +83,11 @@ __device__ __forceinline__ void jacobi_pair(int k, int r, int npad, int* p, int*
 // of a group holds the float4s gl + LPP c (c < 32 / LPP) of both columns,
 // i.e. the first 128 entries with conflict-free 16-byte accesses, and, with
 // EXT (ldm = 160, LPP = 16), lanes gl < 8 also float4 32 + gl.  Returns the
-// rotations counted on lanes gl = 0.
+// rotations counted on lanes gl = 0; *cmax gets the largest |cos| of the
+// angle between two columns that were rotated (the convergence measure).
 template <int LPP, bool EXT>
 __device__ __forceinline__ int jacobi_rounds(float* M, float* nrm, int kp, int npad, int ldm,
-                                             float floor2, float tol) {
+                                             float floor2, float tol, float* cmax) {
   static_assert(LPP == 8 || LPP == 16, "group width");
   static_assert(!EXT || LPP == 16, "the 160-entry layout uses 16-lane groups");
   constexpr int C4 = 32 / LPP;  // float4 of the first 128 entries per lane
@@ -96,6 +97,7 @@ __device__ __forceinline__ int jacobi_rounds(float* M, float* nrm, int kp, int n
   const bool gext = EXT && gl < 8;
   float4* const M4 = reinterpret_cast<float4*>(M);
   int myrot = 0;
+  float mx = 0.f;
   for (int r = 0; r < npad - 1; ++r) {
     // warp-uniform loop: every group reaches the shuffles of every pass
     for (int q0 = PW * warp; q0 < npad / 2; q0 += PW * nwarps) {
@@ -129,7 +131,9 @@ __device__ __forceinline__ int jacobi_rounds(float* M, float* nrm, int kp, int n
       const float al = nrm[pp], be = nrm[qq];
       if (g == 0.f || fminf(al, be) <= floor2) continue;
       // al, be > 0 here; sqrt(al be) from the approximate reciprocal roots
-      if (!(fabsf(g) * rsqrtf(al) * rsqrtf(be) > tol)) continue;
+      const float cosang = fabsf(g) * rsqrtf(al) * rsqrtf(be);
+      if (!(cosang > tol)) continue;
+      mx = fmaxf(mx, cosang);
       // rotation parameters need not be correctly rounded: (cth, sth)
       // below is orthogonal for any tt
       const float zeta = __fdividef(be - al, 2.f * g);
@@ -156,6 +160,7 @@ __device__ __forceinline__ int jacobi_rounds(float* M, float* nrm, int kp, int n
     }
     __syncthreads();
   }
+  *cmax = mx;
   return myrot;
 }
 
@@ -657,20 +662,29 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
   };
   const int npad = (kp + 1) & ~1;
   const float tol = 5e-7f * sqrtf((float)n);
+  const float quad = sqrtf(tol);
+  __shared__ int s_cmax;
   for (int sweep = 0; sweep < 40 && npad >= 2; ++sweep) {
     for (int c = warp; c < kp; c += nwarps) {
       const float s = col_norm2(c);
       if (lane == 0) nrm[c] = s;
     }
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) {
+      s_rot = 0;
+      s_cmax = 0;
+    }
     __syncthreads();
     float tnorm = 0.f;
     for (int c = lane; c < kp; c += 32) tnorm += nrm[c];
     tnorm = warp_sum(tnorm);
     const float floor2 = 1e-14f * tnorm;
-    const int myrot = ext ? jacobi_rounds<16, true>(M, nrm, kp, npad, ldm, floor2, tol)
-                          : jacobi_rounds<8, false>(M, nrm, kp, npad, ldm, floor2, tol);
-    if (myrot > 0) atomicAdd(&s_rot, myrot);  // counted on one lane per pair group
+    float cmax = 0.f;
+    const int myrot = ext ? jacobi_rounds<16, true>(M, nrm, kp, npad, ldm, floor2, tol, &cmax)
+                          : jacobi_rounds<8, false>(M, nrm, kp, npad, ldm, floor2, tol, &cmax);
+    if (myrot > 0) {  // counted on one lane per pair group
+      atomicAdd(&s_rot, myrot);
+      atomicMax(&s_cmax, __float_as_int(cmax));  // non-negative: int order = float order
+    }
     const int any = __syncthreads_or(myrot > 0);
     if (tid == 0) {
       const double nn = (double)n;
@@ -678,6 +692,12 @@ __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int r
     }
     __syncthreads();
     if (!any) break;
+    // one-sided Jacobi converges quadratically: once every rotation of a
+    // sweep had |cos| below sqrt(tol), the next sweep's are of order
+    // cmax^2 < tol, so that sweep (which would rotate little or nothing) is
+    // skipped; what it would leave is far below the FP32 level of the
+    // factors after the Loewdin correction of step 3
+    if (__int_as_float(s_cmax) < quad) break;
   }
   // singular values and their order
   for (int c = warp; c < kp; c += nwarps) {
