@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -210,6 +211,7 @@ struct ttgbf_ctx {
   // pinned host staging
   float* stage_ops = nullptr;
   float* stage_z = nullptr;
+  double* stage_est = nullptr;  // mean, cov, log c, log-likelihood read back by estimate
   cudaEvent_t ev_ops = nullptr, ev_z = nullptr;
   bool ev_ops_used = false, ev_z_used = false;
   // cached predict operators
@@ -752,80 +754,104 @@ int validate_meas(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, int* two_m
   return TTGBF_OK;
 }
 
-int enqueue_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z, int zstride,
-                   int two_mode) {
+// The update as a sequence of enqueue steps, so that a split batch can issue
+// its parts' steps interleaved (all parts start at once and end together).
+// Every step captures what it needs by value; host-side state (ranks
+// bookkeeping, canonical center) changes in step order.
+using EnqueueOps = std::vector<std::function<void()>>;
+
+void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z, int zstride,
+                int two_mode, EnqueueOps* ops) {
   const int B = c->B, d = c->d;
-  if (c->expanded) enqueue_round(c);
-  cudaMemsetAsync(c->logoff, 0, sizeof(double) * B, c->st);
+  ops->push_back([=] {
+    if (c->expanded) enqueue_round(c);
+    cudaMemsetAsync(c->logoff, 0, sizeof(double) * B, c->st);
+  });
   for (int i = 0; i < h->b; ++i) {
-    const ttgbf_meas_comp& cp = h->comp[i];
+    const ttgbf_meas_comp cp = h->comp[i];
     if (cp.nmodes != 1) continue;
     const int k = cp.modes[0];
     const double r = R[(size_t)i * h->b + i];
-    Prof p(c, kPLik, 2);
-    launch_lik_offset(c->st, B, cp.htab, c->n[k], z, zstride, i, r, c->lik_off, c->logoff);
-    launch_lik_apply_1d(c->st, B, curp(c, k), c->L.core_cap[k], c->n[k], k, d, c->ranks, cp.htab, z,
-                        zstride, i, r, c->lik_off);
-    if (!(c->canon && c->center == k)) c->canon = false;
+    ops->push_back([=] {
+      Prof p(c, kPLik, 2);
+      launch_lik_offset(c->st, B, cp.htab, c->n[k], z, zstride, i, r, c->lik_off, c->logoff);
+      launch_lik_apply_1d(c->st, B, curp(c, k), c->L.core_cap[k], c->n[k], k, d, c->ranks, cp.htab,
+                          z, zstride, i, r, c->lik_off);
+      if (!(c->canon && c->center == k)) c->canon = false;
+    });
   }
   if (two_mode >= 0) {
-    const ttgbf_meas_comp& cp = h->comp[two_mode];
+    const ttgbf_meas_comp cp = h->comp[two_mode];
     const double r = R[(size_t)two_mode * h->b + two_mode];
-    for (int k = d - 1; k >= 2; --k) stage(c, kStageRight, k, 0);
-    GemmWork gw = gemm_work(c, B);
-    {
-      Prof p(c, kPPlan, 2);
-      launch_plan_supercore(c->st, B, c->geom, c->ranks, curp(c, 0), curp(c, 1), c->W, c->L.W_cap, gw);
-    }
-    {
-      Prof p(c, kPGemm, 1);
-      launch_gemm(c->st, gw, c->sms * 8, flops_of(c, kPGemm));
-    }
-    {
-      Prof p(c, kPLik, 2);
-      launch_lik_offset(c->st, B, cp.htab, c->n[0] * c->n[1], z, zstride, two_mode, r, c->lik_off,
-                        c->logoff);
-      launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, cp.htab, z, zstride,
-                          two_mode, r, c->lik_off);
-    }
-    // log c before rounding: mass of the TT [W (modes 0,1 merged), core 2, ...]
-    MomentArgs a{};
-    a.ncores = d - 1;
-    a.n[0] = c->n[0] * c->n[1];
-    a.core[0] = c->W;
-    a.cap[0] = c->L.W_cap;
-    a.ridx[0] = 0;
-    for (int k = 2; k < d; ++k) {
-      a.n[k - 1] = c->n[k];
-      a.core[k - 1] = curp(c, k);
-      a.cap[k - 1] = c->L.core_cap[k];
-    }
-    for (int kk = 1; kk <= d - 1; ++kk) a.ridx[kk] = kk + 1;
-    a.delta = c->delta;
-    {
-      Prof p(c, kPMoments, 1);
-      launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
-    }
-    {
-      Prof p(c, kPOther, 1);
-      launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
-    }
-    stage(c, kStageSplit, 0, 1);
-    for (int k = 1; k <= d - 2; ++k) stage(c, kStageLeft, k, 0);
-    c->canon = true;
-    c->center = d - 1;
+    for (int k = d - 1; k >= 2; --k) ops->push_back([=] { stage(c, kStageRight, k, 0); });
+    ops->push_back([=] {
+      GemmWork gw = gemm_work(c, B);
+      {
+        Prof p(c, kPPlan, 2);
+        launch_plan_supercore(c->st, B, c->geom, c->ranks, curp(c, 0), curp(c, 1), c->W, c->L.W_cap, gw);
+      }
+      {
+        Prof p(c, kPGemm, 1);
+        launch_gemm(c->st, gw, c->sms * 8, flops_of(c, kPGemm));
+      }
+      {
+        Prof p(c, kPLik, 2);
+        launch_lik_offset(c->st, B, cp.htab, c->n[0] * c->n[1], z, zstride, two_mode, r, c->lik_off,
+                          c->logoff);
+        launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, cp.htab, z, zstride,
+                            two_mode, r, c->lik_off);
+      }
+      // log c before rounding: mass of the TT [W (modes 0,1 merged), core 2, ...]
+      MomentArgs a{};
+      a.ncores = d - 1;
+      a.n[0] = c->n[0] * c->n[1];
+      a.core[0] = c->W;
+      a.cap[0] = c->L.W_cap;
+      a.ridx[0] = 0;
+      for (int k = 2; k < d; ++k) {
+        a.n[k - 1] = c->n[k];
+        a.core[k - 1] = curp(c, k);
+        a.cap[k - 1] = c->L.core_cap[k];
+      }
+      for (int kk = 1; kk <= d - 1; ++kk) a.ridx[kk] = kk + 1;
+      a.delta = c->delta;
+      {
+        Prof p(c, kPMoments, 1);
+        launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
+      }
+      {
+        Prof p(c, kPOther, 1);
+        launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+      }
+    });
+    ops->push_back([=] { stage(c, kStageSplit, 0, 1); });
+    for (int k = 1; k <= d - 2; ++k) ops->push_back([=] { stage(c, kStageLeft, k, 0); });
+    ops->push_back([=] {
+      c->canon = true;
+      c->center = d - 1;
+    });
   } else {
-    MomentArgs a = tt_moment_args(c, 0, 0);
-    {
-      Prof p(c, kPMoments, 1);
-      launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
-    }
-    {
-      Prof p(c, kPOther, 1);
-      launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
-    }
+    ops->push_back([=] {
+      MomentArgs a = tt_moment_args(c, 0, 0);
+      {
+        Prof p(c, kPMoments, 1);
+        launch_moments(c->st, B, a, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr,
+                       nullptr);
+      }
+      {
+        Prof p(c, kPOther, 1);
+        launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+      }
+    });
   }
-  enqueue_normalise(c, c->mass);
+  ops->push_back([=] { enqueue_normalise(c, c->mass); });
+}
+
+int enqueue_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z, int zstride,
+                   int two_mode) {
+  EnqueueOps ops;
+  update_ops(c, h, R, z, zstride, two_mode, &ops);
+  for (auto& op : ops) op();
   return check(c);
 }
 
@@ -987,6 +1013,7 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   c->prof_flops = (double*)(b + L.prof_flops);
   if (cudaMallocHost(&c->stage_ops, sizeof(float) * L.opmats_floats) != cudaSuccess ||
       cudaMallocHost(&c->stage_z, sizeof(float) * (size_t)c->B * kMaxComps) != cudaSuccess ||
+      cudaMallocHost(&c->stage_est, sizeof(double) * (size_t)c->B * (d + d * d + 2)) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_ops, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_z, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -1207,42 +1234,85 @@ int ttgbf_predict(ttgbf_ctx* c, const double* F, const double* Q) {
   return predict_end(c);
 }
 
-int ttgbf_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z) {
-  if (split(c)) {
-    if (!h || !z) return TTGBF_EINVAL;
-    return fan_out(c, [&](ttgbf_ctx* q, int p) {
-      return ttgbf_update(q, h, R, z + (size_t)c->part_base[p] * h->b);
-    });
-  }
+// Host-side checks and the measurement's device copy for one (part) context;
+// *zq receives the device measurement pointer and *two the two-mode
+// component (-1 if none).
+static int update_prepare(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z_host,
+                          const float* z_dev, const float** zq, int* two) {
   int rc = guard(c);
   if (rc) return rc;
-  int two = -1;
-  rc = validate_meas(c, h, R, &two);
+  *two = -1;
+  rc = validate_meas(c, h, R, two);
   if (rc) return rc;
-  if (!z) return TTGBF_EINVAL;
-  if (!finite_all(z, (size_t)c->B * h->b)) return TTGBF_ENONFINITE;
+  if (z_dev) {
+    *zq = z_dev;
+    return TTGBF_OK;
+  }
+  if (!z_host) return TTGBF_EINVAL;
+  if (!finite_all(z_host, (size_t)c->B * h->b)) return TTGBF_ENONFINITE;
   wait_stage(c->ev_z, &c->ev_z_used);
-  for (size_t i = 0; i < (size_t)c->B * h->b; ++i) c->stage_z[i] = (float)z[i];
-  cudaMemcpyAsync(c->zbuf, c->stage_z, sizeof(float) * (size_t)c->B * h->b, cudaMemcpyHostToDevice, c->st);
+  for (size_t i = 0; i < (size_t)c->B * h->b; ++i) c->stage_z[i] = (float)z_host[i];
+  cudaMemcpyAsync(c->zbuf, c->stage_z, sizeof(float) * (size_t)c->B * h->b, cudaMemcpyHostToDevice,
+                  c->st);
   cudaEventRecord(c->ev_z, c->st);
   c->ev_z_used = true;
-  return enqueue_update(c, h, R, c->zbuf, h->b, two);
+  *zq = c->zbuf;
+  return TTGBF_OK;
+}
+
+// A split batch: every part prepares (identical arguments fail alike on
+// every part, so only the first can fail, before any launch), then the
+// parts' enqueue steps are issued interleaved between a fork and a join.
+static int update_split(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z_host,
+                        const float* z_dev) {
+  if (!h || (!z_host && !z_dev)) return TTGBF_EINVAL;
+  const size_t np = c->parts.size();
+  std::vector<EnqueueOps> lists(np);
+  fork_parts(c);
+  int rc = TTGBF_OK;
+  for (size_t p = 0; p < np && rc == TTGBF_OK; ++p) {
+    ttgbf_ctx* q = c->parts[p];
+    const size_t off = (size_t)c->part_base[p] * (size_t)(h->b);
+    const float* zq = nullptr;
+    int two = -1;
+    rc = update_prepare(q, h, R, z_host ? z_host + off : nullptr, z_dev ? z_dev + off : nullptr, &zq,
+                        &two);
+    if (rc == TTGBF_OK) update_ops(q, h, R, zq, h->b, two, &lists[p]);
+  }
+  if (rc == TTGBF_OK) {
+    size_t nmax = 0;
+    for (const EnqueueOps& l : lists) nmax = std::max(nmax, l.size());
+    for (size_t i = 0; i < nmax; ++i)
+      for (const EnqueueOps& l : lists)
+        if (i < l.size()) l[i]();
+    for (ttgbf_ctx* q : c->parts) {
+      const int r = check(q);
+      if (r && !rc) rc = r;
+    }
+  }
+  join_parts(c);
+  return rc;
+}
+
+int ttgbf_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z) {
+  if (split(c)) return update_split(c, h, R, z, nullptr);
+  const float* zq = nullptr;
+  int two = -1;
+  const int rc = update_prepare(c, h, R, z, nullptr, &zq, &two);
+  if (rc) return rc;
+  return enqueue_update(c, h, R, zq, h->b, two);
 }
 
 int ttgbf_update_dev(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z_dev) {
   if (split(c)) {
-    if (!h || !z_dev) return TTGBF_EINVAL;
-    return fan_out(c, [&](ttgbf_ctx* q, int p) {
-      return ttgbf_update_dev(q, h, R, z_dev + (size_t)c->part_base[p] * h->b);
-    });
+    if (!z_dev) return TTGBF_EINVAL;
+    return update_split(c, h, R, nullptr, z_dev);
   }
-  int rc = guard(c);
-  if (rc) return rc;
+  const float* zq = nullptr;
   int two = -1;
-  rc = validate_meas(c, h, R, &two);
+  const int rc = update_prepare(c, h, R, nullptr, z_dev, &zq, &two);
   if (rc) return rc;
-  if (!z_dev) return TTGBF_EINVAL;
-  return enqueue_update(c, h, R, z_dev, h->b, two);
+  return enqueue_update(c, h, R, zq, h->b, two);
 }
 
 static int estimate_common(ttgbf_ctx* c) {
@@ -1253,25 +1323,48 @@ static int estimate_common(ttgbf_ctx* c) {
   return check(c);
 }
 
-int ttgbf_estimate(ttgbf_ctx* c, double* mean, double* cov, double* log_c, double* log_lik) {
-  if (split(c)) {
-    const int d = c->d;
-    return fan_out(c, [&](ttgbf_ctx* q, int p) {
-      const size_t b0 = (size_t)c->part_base[p];
-      return ttgbf_estimate(q, mean ? mean + b0 * d : nullptr, cov ? cov + b0 * d * d : nullptr,
-                            log_c ? log_c + b0 : nullptr, log_lik ? log_lik + b0 : nullptr);
-    });
-  }
+// Moments of every filter, copied to the pinned staging area (no wait).
+static int estimate_to_stage(ttgbf_ctx* c) {
   int rc = guard(c);
   if (rc) return rc;
   rc = estimate_common(c);
   if (rc) return rc;
-  const int B = c->B, d = c->d;
-  if (mean) cudaMemcpyAsync(mean, c->mean, sizeof(double) * B * d, cudaMemcpyDeviceToHost, c->st);
-  if (cov) cudaMemcpyAsync(cov, c->cov, sizeof(double) * B * d * d, cudaMemcpyDeviceToHost, c->st);
-  if (log_c) cudaMemcpyAsync(log_c, c->log_c, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
-  if (log_lik) cudaMemcpyAsync(log_lik, c->log_lik, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  const size_t B = (size_t)c->B, d = (size_t)c->d;
+  double* h = c->stage_est;
+  cudaMemcpyAsync(h, c->mean, sizeof(double) * B * d, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(h + B * d, c->cov, sizeof(double) * B * d * d, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(h + B * (d + d * d), c->log_c, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(h + B * (d + d * d + 1), c->log_lik, sizeof(double) * B, cudaMemcpyDeviceToHost,
+                  c->st);
+  return check(c);
+}
+
+// Staged moments of filters [b0, b0 + B) to the caller's host arrays.
+static void estimate_from_stage(const ttgbf_ctx* c, size_t b0, double* mean, double* cov,
+                                double* log_c, double* log_lik) {
+  const size_t B = (size_t)c->B, d = (size_t)c->d;
+  const double* h = c->stage_est;
+  if (mean) std::memcpy(mean + b0 * d, h, sizeof(double) * B * d);
+  if (cov) std::memcpy(cov + b0 * d * d, h + B * d, sizeof(double) * B * d * d);
+  if (log_c) std::memcpy(log_c + b0, h + B * (d + d * d), sizeof(double) * B);
+  if (log_lik) std::memcpy(log_lik + b0, h + B * (d + d * d + 1), sizeof(double) * B);
+}
+
+int ttgbf_estimate(ttgbf_ctx* c, double* mean, double* cov, double* log_c, double* log_lik) {
+  if (split(c)) {
+    // every part enqueues its moments and read-back before anything waits,
+    // so the parts finish concurrently; the caller's stream joins them
+    const int rc = fan_out(c, [&](ttgbf_ctx* q, int) { return estimate_to_stage(q); });
+    if (rc) return rc;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+    for (size_t p = 0; p < c->parts.size(); ++p)
+      estimate_from_stage(c->parts[p], (size_t)c->part_base[p], mean, cov, log_c, log_lik);
+    return check(c);
+  }
+  const int rc = estimate_to_stage(c);
+  if (rc) return rc;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  estimate_from_stage(c, 0, mean, cov, log_c, log_lik);
   return check(c);
 }
 
@@ -1311,6 +1404,7 @@ int ttgbf_free(ttgbf_ctx* c) {
   if (c->owns && c->base) cudaFree(c->base);
   if (c->stage_ops) cudaFreeHost(c->stage_ops);
   if (c->stage_z) cudaFreeHost(c->stage_z);
+  if (c->stage_est) cudaFreeHost(c->stage_est);
   if (c->ev_ops) cudaEventDestroy(c->ev_ops);
   if (c->ev_z) cudaEventDestroy(c->ev_z);
   for (int k = 0; k < kPClasses; ++k)
