@@ -345,6 +345,7 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
   double* tmp = e + kMaxN;                      // kMaxN
   double* acc = tmp + kMaxN;                    // 9 x 1024 (group partials)
   double* red = acc + 9 * 1024;                 // 32
+  float* xs = reinterpret_cast<float*>(red + 32);  // N: centred coordinates of the current core
   __shared__ double s_mean[kMaxD + 1];
   __shared__ double s_S[(kMaxD + 1) * (kMaxD + 1)];
   const int* rk = ranks + (long long)b * rstride;
@@ -359,6 +360,12 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
     const double* ax = a.axes[kk];
     const double c = a.centre[kk];
     const int npairs = r0 * r1;
+    // the centred coordinates in FP32, formed once per core (an FP64
+    // subtraction per term and thread would cost more issue time than the
+    // whole FP32 sum on this part)
+    __syncthreads();
+    if (P > 1)
+      for (int i = threadIdx.x; i < N; i += blockDim.x) xs[i] = (float)(ax[i] - c);
     for (int pb = 0; pb < npairs; pb += 1024) {
       const int nb = min(1024, npairs - pb);
       __syncthreads();
@@ -376,7 +383,7 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
           const float v = gp[(long long)i * r1];
           a0 += v;
           if (P > 1) {
-            const float x = (float)(ax[i] - c);
+            const float x = xs[i];
             a1 = fmaf(x, v, a1);
             a2 = fmaf(x * x, v, a2);
           }
@@ -499,7 +506,9 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
   }
 }
 
-constexpr int kMomentSmemDoubles = (kMaxD + 2) * kMaxN + (kMaxD + 1) * kMaxN + 2 * kMaxN + 9 * 1024 + 32;
+constexpr int kMomentMaxN = 4096;  // grid points per mode (the library's limit)
+constexpr int kMomentSmemDoubles =
+    (kMaxD + 2) * kMaxN + (kMaxD + 1) * kMaxN + 2 * kMaxN + 9 * 1024 + 32 + kMomentMaxN / 2;
 
 }  // namespace
 
