@@ -17,7 +17,13 @@
  *    TTGBF_EINVAL / TTGBF_ENONFINITE / TTGBF_ECAPACITY / TTGBF_ESINGULAR the
  *    filter state is unchanged.
  *  - After a CUDA error the context is poisoned: every later call except
- *    ttgbf_free returns TTGBF_EPOISONED.
+ *    ttgbf_free returns TTGBF_EPOISONED (for a batch split into parts: once
+ *    any part is poisoned).
+ *  - Fault injection for tests of these paths (no GPU fault is made): the
+ *    environment variable TTGBF_FAULT, read by ttgbf_init, set to "cuda:N"
+ *    makes the N-th status check after init report a CUDA error (the call
+ *    returns TTGBF_ECUDA and poisons the context), set to "alloc" makes
+ *    ttgbf_init fail with TTGBF_ENOMEM after validating its arguments.
  *  - Host arrays passed in are owned by the caller and are read (or copied)
  *    before the call returns.  Device pointers passed in are owned by the
  *    caller and must stay valid until the work enqueued on the context's

@@ -13,6 +13,7 @@
 // All data-dependent sizes (TT ranks) stay on the device; the host enqueues a
 // fixed sequence of kernels per call.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -63,6 +64,13 @@ struct Layout {
   long long core_cap[kMaxD];
   long long stack_cap, W_cap, opmats_floats, awork_stride;
   int gdesc_cap, capr;
+};
+
+// An NVTX range over one API call (host time; tools such as ncu can filter
+// kernels by it, e.g. --nvtx --nvtx-include "ttgbf_update/").
+struct ApiRange {
+  explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
 };
 
 bool finite_all(const double* p, size_t n) {
@@ -238,6 +246,9 @@ struct ttgbf_ctx {
   long long prof_launches[kPClasses] = {};
   double* prof_flops = nullptr;
   bool debug_stages = false;
+  // Host-side fault injection (TTGBF_FAULT=cuda:N): the N-th status check
+  // after init reports a CUDA error, as a failed call would; 0 = off.
+  long long fault_after = 0;
   int sms = 148;
   // A batch split into independent sub-batches ("parts"), each a full
   // context on its own stream: the parts' kernels overlap on the GPU (one
@@ -261,6 +272,7 @@ int cuda_fail(ttgbf_ctx* c) {
 }
 
 int check(ttgbf_ctx* c) {
+  if (c->fault_after > 0 && --c->fault_after == 0) return cuda_fail(c);  // injected
   const cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -933,6 +945,12 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
     const char* dbg = std::getenv("TTGBF_DEBUG_STAGES");
     c->debug_stages = dbg != nullptr && dbg[0] == '1';
   }
+  // TTGBF_FAULT=alloc: the device allocation "fails" (after validation)
+  const char* fault = std::getenv("TTGBF_FAULT");
+  if (fault != nullptr && std::strcmp(fault, "alloc") == 0) {
+    delete c;
+    return TTGBF_ENOMEM;
+  }
   c->n.assign(grid->n, grid->n + d);
   c->lo.assign(grid->lo, grid->lo + d);
   c->hi.assign(grid->hi, grid->hi + d);
@@ -1040,6 +1058,8 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
     return TTGBF_ECUDA;
   }
   *out = c;
+  if (fault != nullptr && std::strncmp(fault, "cuda:", 5) == 0)
+    c->fault_after = std::max(0L, std::strtol(fault + 5, nullptr, 10));
   return TTGBF_OK;
 }
 
@@ -1134,8 +1154,16 @@ void join_parts(ttgbf_ctx* c) {
 // normalise) do neither, so the parts drift apart and different parts' QR,
 // SVD and GEMM phases overlap; the next joining call (or free) waits for
 // them.
+// A poisoned part poisons the whole batch: only ttgbf_free is valid then.
+int parts_guard(const ttgbf_ctx* c) {
+  for (const ttgbf_ctx* q : c->parts)
+    if (q->poisoned) return TTGBF_EPOISONED;
+  return TTGBF_OK;
+}
+
 template <typename Fn>
 int fan_out(ttgbf_ctx* c, Fn fn, bool join = true, bool fork = true) {
+  if (const int rc = parts_guard(c)) return rc;
   if (fork) fork_parts(c);
   int rc = TTGBF_OK;
   for (size_t p = 0; p < c->parts.size() && rc == TTGBF_OK; ++p) rc = fn(c->parts[p], (int)p);
@@ -1208,7 +1236,9 @@ int predict_end(ttgbf_ctx* c) {
 extern "C" {
 
 int ttgbf_predict(ttgbf_ctx* c, const double* F, const double* Q) {
+  ApiRange range("ttgbf_predict");
   if (split(c)) {
+    if (const int rc = parts_guard(c)) return rc;
     // every part validates the same arguments: a failure can only come
     // from the first part, before anything is enqueued
     for (ttgbf_ctx* q : c->parts) {
@@ -1265,6 +1295,7 @@ static int update_prepare(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, co
 // parts' enqueue steps are issued interleaved between a fork and a join.
 static int update_split(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z_host,
                         const float* z_dev) {
+  if (const int rc = parts_guard(c)) return rc;
   if (!h || (!z_host && !z_dev)) return TTGBF_EINVAL;
   const size_t np = c->parts.size();
   std::vector<EnqueueOps> lists(np);
@@ -1295,6 +1326,7 @@ static int update_split(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, cons
 }
 
 int ttgbf_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const double* z) {
+  ApiRange range("ttgbf_update");
   if (split(c)) return update_split(c, h, R, z, nullptr);
   const float* zq = nullptr;
   int two = -1;
@@ -1304,6 +1336,7 @@ int ttgbf_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const doubl
 }
 
 int ttgbf_update_dev(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z_dev) {
+  ApiRange range("ttgbf_update");
   if (split(c)) {
     if (!z_dev) return TTGBF_EINVAL;
     return update_split(c, h, R, nullptr, z_dev);
@@ -1351,6 +1384,7 @@ static void estimate_from_stage(const ttgbf_ctx* c, size_t b0, double* mean, dou
 }
 
 int ttgbf_estimate(ttgbf_ctx* c, double* mean, double* cov, double* log_c, double* log_lik) {
+  ApiRange range("ttgbf_estimate");
   if (split(c)) {
     // every part enqueues its moments and read-back before anything waits,
     // so the parts finish concurrently; the caller's stream joins them
@@ -1369,6 +1403,7 @@ int ttgbf_estimate(ttgbf_ctx* c, double* mean, double* cov, double* log_c, doubl
 }
 
 int ttgbf_estimate_dev(ttgbf_ctx* c, double* mean, double* cov, double* log_c, double* log_lik) {
+  ApiRange range("ttgbf_estimate");
   if (split(c)) {
     const int d = c->d;
     return fan_out(c, [&](ttgbf_ctx* q, int p) {

@@ -98,3 +98,12 @@ def test_filter_reports_capacity_before_device(lib):
     with pytest.raises(G.TTGBFError) as ei:
         G.TTFilter([0.0], [0.0], [8], [0.0], [1.0], stream=null_stream)
     assert ei.value.code == -1
+
+
+def test_injected_alloc_failure(lib, monkeypatch):
+    # TTGBF_FAULT=alloc: init validates, then reports the allocation failure
+    monkeypatch.setenv("TTGBF_FAULT", "alloc")
+    rc, ctx = _init(lib, [0.0], [1.0], [8], [0.0], [1.0])
+    assert rc == -3 and not ctx.value
+    # invalid arguments are still reported as such
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], batch=0)[0] == -1

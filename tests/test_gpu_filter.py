@@ -241,3 +241,33 @@ def test_shears_in_pieces_small_grid(G):
             assert (np.abs(c[i] - co) <= cov_tol(g.delta_axis, co)).all(), (k, i)
             assert abs(lc[i] - logc) < 1e-3, (k, i)
             assert st[i]["max_rank"] <= model.rank_cap
+
+
+@pytest.mark.parametrize("batch", [2, 24])
+def test_injected_cuda_error_poisons_context(G, monkeypatch, batch):
+    """Failure detection without a GPU fault: TTGBF_FAULT=cuda:2 makes the
+    second status check after init report a CUDA error.  That call returns
+    TTGBF_ECUDA, every later call TTGBF_EPOISONED (for a batch split into
+    parts as well), and the context is still freed cleanly."""
+    monkeypatch.setenv("TTGBF_FAULT", "cuda:2")
+    model = synth.config2(n=16)
+    f = make_filter(G, model, batch=batch)
+    monkeypatch.delenv("TTGBF_FAULT")
+    comps = device_tables(model, f.grid_axes())
+    z = np.stack([synth.simulate(model, mc, steps=1)[1][0] for mc in range(batch)])
+    f.predict(model.F, model.Q)  # first check: fine
+    with pytest.raises(G.TTGBFError) as ei:
+        f.update(comps, model.R, z)  # second check: the injected error
+    assert ei.value.code == -4
+    for call in (lambda: f.estimate(), lambda: f.predict(model.F, model.Q),
+                 lambda: f.update(comps, model.R, z)):
+        with pytest.raises(G.TTGBFError) as ei:
+            call()
+        assert ei.value.code == -7
+    f.free()
+    # a fresh context is unaffected
+    g = make_filter(G, model, batch=batch)
+    g.predict(model.F, model.Q)
+    g.update(comps, model.R, z)
+    m, c, lc, ll = g.estimate()
+    assert np.isfinite(m).all() and np.isfinite(lc).all()
