@@ -403,15 +403,20 @@ __device__ __forceinline__ int qrcp_reg(float* A, int n, float* nref, int kcap, 
 //  1. Householder QR with column pivoting, R P = Q' R', stopped once the
 //     columns left over have Frobenius norm below the stage's drop level (or
 //     after rank_cap + 16 steps when truncating); their norm is added to the
-//     discarded tail.  Pivoting also preconditions step 2.
+//     discarded tail.  Pivoting also preconditions step 2.  The columns stay
+//     in registers (qrcp_reg) for 32 warps, and for 16 warps up to 96
+//     columns; otherwise in shared memory.
 //  2. One-sided Jacobi on the k' x n leading rows of R' (their transposes as
-//     k' columns of length n): only k' - 1 rounds per sweep.
+//     k' columns of length n): only k' - 1 rounds per sweep, one pair per
+//     8- or 16-lane group (jacobi_rounds), stopped once a sweep's rotations
+//     are in the quadratic regime.
 //  3. The right singular vectors (normalised columns, in the order of
-//     decreasing singular value) are re-orthonormalised by classical
-//     Gram-Schmidt applied twice and un-permuted, so that the factor pair the
-//     stage applies (V S^-1 with S V^T, or S^-1 V^T with V S) multiplies to an
-//     exact projector.
-// Then the stage's rank choice and factor output.  One CTA per filter.
+//     decreasing singular value) get one Loewdin correction (classical
+//     Gram-Schmidt applied twice when they are further from orthonormal) and
+//     are un-permuted, so that the factor pair the stage applies (V S^-1 with
+//     S V^T, or S^-1 V^T with V S) multiplies to an exact projector.
+// Then the stage's rank choice and factor output.  One CTA per filter; the
+// FP64 scalars (norm, threshold, tails, rank choice) are formed by thread 0.
 __global__ void __launch_bounds__(1024) k_svd(TsqrWork w, int B, int mode, int rank_cap, double eps,
                                              int d, int first, RoundState rs, float* P1, float* P2,
                                              float* core0_out, long long core0_cap, double* flops) {
