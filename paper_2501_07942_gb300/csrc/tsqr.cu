@@ -146,9 +146,11 @@ __device__ __forceinline__ void qr_reflector(float (&A)[kQrRPL][CPL], int j, int
     scl = alpha >= 0.f ? __frcp_rn(am) : -__frcp_rn(am);
   }
   if (own) {
-    float4* v4 = reinterpret_cast<float4*>(v + rl * kQrRPL);
-    v4[0] = make_float4(A[0][Q] * scl, A[1][Q] * scl, A[2][Q] * scl, A[3][Q] * scl);
-    v4[1] = make_float4(A[4][Q] * scl, A[5][Q] * scl, A[6][Q] * scl, A[7][Q] * scl);
+    // v of rows 8 rl + (0..3) at float4 rl, rows 8 rl + (4..7) at float4
+    // 16 + rl: a half's 16-byte accesses cover contiguous 256 bytes
+    float4* v4 = reinterpret_cast<float4*>(v);
+    v4[rl] = make_float4(A[0][Q] * scl, A[1][Q] * scl, A[2][Q] * scl, A[3][Q] * scl);
+    v4[kQrRL + rl] = make_float4(A[4][Q] * scl, A[5][Q] * scl, A[6][Q] * scl, A[7][Q] * scl);
 #pragma unroll
     for (int a = 0; a < kQrRPL; ++a) A[a][Q] = 0.f;
     if (rl == 0) {
@@ -166,8 +168,8 @@ __device__ __forceinline__ void qr_apply(float (&A)[kQrRPL][CPL], float* Rs, con
   if constexpr (QA < QB) {
     float vr[kQrRPL];
     {
-      const float4* v4 = reinterpret_cast<const float4*>(v + rl * kQrRPL);
-      const float4 v0 = v4[0], v1 = v4[1];
+      const float4* v4 = reinterpret_cast<const float4*>(v);
+      const float4 v0 = v4[rl], v1 = v4[kQrRL + rl];
       vr[0] = v0.x; vr[1] = v0.y; vr[2] = v0.z; vr[3] = v0.w;
       vr[4] = v1.x; vr[5] = v1.y; vr[6] = v1.z; vr[7] = v1.w;
     }
