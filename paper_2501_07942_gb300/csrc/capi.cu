@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -925,13 +926,14 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   if (!finite_all(prior->mean, d) || !finite_all(prior->var, d)) return TTGBF_ENONFINITE;
   for (int k = 0; k < d; ++k)
     if (!(prior->var[k] > 0.0)) return TTGBF_EINVAL;
-  static bool attrs = false;
-  if (!attrs) {
+  // kernel attributes (large dynamic shared memory), once per process even
+  // when several threads create contexts at the same time
+  static std::once_flag attrs;
+  std::call_once(attrs, [] {
     set_kernel_attributes();
     set_ttops_attributes();
     set_tsqr_attributes();
-    attrs = true;
-  }
+  });
   ttgbf_ctx* c = new (std::nothrow) ttgbf_ctx();
   if (!c) return TTGBF_ENOMEM;
   c->B = opts->batch;
