@@ -77,3 +77,59 @@ def test_round_error_bound(eps):
 def test_from_dense_roundtrip():
     A = np.random.default_rng(7).random((3, 4, 5))
     np.testing.assert_allclose(tt.densify(tt.from_dense(A)), A, atol=1e-13)
+
+
+def test_add_is_elementwise_sum():
+    rng = np.random.default_rng(41)
+    a = [rng.standard_normal(s) for s in [(1, 5, 2), (2, 4, 3), (3, 6, 1)]]
+    b = [rng.standard_normal(s) for s in [(1, 5, 3), (3, 4, 2), (2, 6, 1)]]
+    np.testing.assert_allclose(tt.densify(tt.add(a, b)), tt.densify(a) + tt.densify(b),
+                               rtol=0, atol=1e-12)
+    assert tt.ranks(tt.add(a, b)) == [1, 5, 5, 1]
+
+
+SHEAR_CASES = [(0, 1, 0.3), (0, 2, -0.45), (2, 0, 0.3), (1, 2, 1.2), (2, 1, -0.2)]
+
+
+@pytest.mark.parametrize("m,n,a", SHEAR_CASES)
+def test_shear_operator_equals_dense_shear(m, n, a):
+    """The TT form of the hat shear reproduces the dense push-forward
+    (an independent implementation, slice by slice) exactly."""
+    from oracle import pmf
+    g = pmf.Grid([-5.0, -4.0, -3.0], [5.0, 4.0, 3.0], [20, 16, 12])
+    rng = np.random.default_rng(7)
+    cores = [rng.random(sh) for sh in [(1, 20, 2), (2, 16, 3), (3, 12, 1)]]
+    s = a * g.axes[n] / g.delta_axis[m]
+    ref = pmf.shear(tt.densify(cores), g, m, n, a)
+    got = tt.densify(tt.shear_operator(cores, m, n, s))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m,n,a", SHEAR_CASES)
+def test_shear_in_pieces_is_the_sum_of_pieces(m, n, a):
+    """The shear as a TT sum of pieces of consecutive shifts is exactly the
+    whole operator; rounding every piece and then the sum stays within
+    eps (sum of the pieces' norms + the norm of the result)."""
+    from oracle import pmf
+    g = pmf.Grid([-5.0, -4.0, -3.0], [5.0, 4.0, 3.0], [20, 16, 12])
+    rng = np.random.default_rng(8)
+    cores = [rng.random(sh) for sh in [(1, 20, 2), (2, 16, 3), (3, 12, 1)]]
+    s = a * g.axes[n] / g.delta_axis[m]
+    ts = list(range(int(np.floor(s.min())), int(np.floor(s.max())) + 2))
+    cuts = [0, len(ts) // 3, 2 * len(ts) // 3, len(ts)]
+    pieces = [tt.shear_operator(cores, m, n, s, ts[c0:c1])
+              for c0, c1 in zip(cuts[:-1], cuts[1:]) if c1 > c0]
+    whole = tt.densify(tt.shear_operator(cores, m, n, s))
+    total = pieces[0]
+    for p in pieces[1:]:
+        total = tt.add(total, p)
+    np.testing.assert_allclose(tt.densify(total), whole, rtol=0, atol=1e-12 * np.abs(whole).max())
+    eps = 1e-3
+    rounded = [tt.round_tt(p, eps)[0] for p in pieces]
+    acc = rounded[0]
+    for p in rounded[1:]:
+        acc = tt.add(acc, p)
+    out = tt.densify(tt.round_tt(acc, eps)[0])
+    nw = np.linalg.norm(whole)
+    bound = eps * (sum(np.linalg.norm(tt.densify(p)) for p in pieces) + nw) / nw
+    assert np.linalg.norm(out - whole) / nw <= bound * (1 + 1e-9) + 1e-12
