@@ -397,3 +397,38 @@ def test_config1_golden_regression():
                        transition="rg")
     np.testing.assert_allclose(r["means"], gold["rg"]["means"], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(r["log_c"], gold["rg"]["log_c"], rtol=1e-12, atol=1e-12)
+
+
+def test_block_diagonal_model_factors_over_pairs():
+    """For a block-diagonal F, diagonal Q, a separable prior and one-mode
+    measurements (the d = 6, 8 constant-velocity workload), the re-gridded
+    filter's density stays the tensor product of the pairs' 2-D densities:
+    every shear couples modes inside one pair, the kernel and the likelihood
+    are separable.  This is what the GPU tests at N = 128 and 256 compare the
+    TT density against."""
+    import synth
+    model = synth.config3(d=4, n=12)
+    g = pmf.Grid(model.lo, model.hi, model.n)
+    oc = model.tables(g.axes)
+    z = synth.simulate(model, 0, steps=2)[1]
+    P = pmf.prior(g, model.m0, model.P0)
+    pairs = []
+    for i in range(2):
+        s = slice(2 * i, 2 * i + 2)
+        gi = pmf.Grid(model.lo[s], model.hi[s], model.n[s])
+        pairs.append((gi, model.F[s, s], model.Q[s, s], model.R[i:i + 1, i:i + 1],
+                      pmf.prior(gi, model.m0[s], model.P0[s, s])))
+    for k in range(2):
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+        P, logc = pmf.update(P, g, pmf.likelihood(g, oc, z[k], model.R))
+        logc_pairs = 0.0
+        dens = []
+        for i, (gi, Fi, Qi, Ri, Pi) in enumerate(pairs):
+            Pi, _ = pmf.predict_rg(Pi, gi, Fi, Qi)
+            Pi, lci = pmf.update(Pi, gi, pmf.likelihood(gi, [((0,), oc[i][1])], z[k][i:i + 1], Ri))
+            pairs[i] = (gi, Fi, Qi, Ri, Pi)
+            dens.append(Pi)
+            logc_pairs += lci
+        prod = np.einsum("ab,cd->abcd", dens[0], dens[1])
+        assert np.abs(P - prod).max() <= 1e-12 * np.abs(P).max()
+        assert abs(logc - logc_pairs) < 1e-10
