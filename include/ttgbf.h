@@ -288,8 +288,10 @@ int ttgbf_fg_free(ttgbf_fg* fg);
  * that forbids allocation while capturing, serving loops with a fixed memory
  * budget, plugins living inside another framework's memory pool).
  *
- * Mass, mean and covariance of `batch` TT densities already in device memory,
- * computed exactly like ttgbf_estimate but without a context: no memory is
+ * Mass, mean and covariance of `batch` TT densities already in device memory:
+ * the same point-mass moments as ttgbf_estimate (its own kernel, float64
+ * per-term sums; equal to the oracle's moments of the densified TT within
+ * the moment tolerance of the GPU tests), without a context: no memory is
  * allocated.  Its float64 scratch is one static device array of
  * TTGBF_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
  * the process exits.
@@ -305,9 +307,11 @@ int ttgbf_fg_free(ttgbf_fg* fg);
  * Returns TTGBF_ECAPACITY when batch * d * 3 * rank_max^2 doubles exceed the
  * scratch array (or rank_max > TTGBF_NOALLOC_MAX_RANK), TTGBF_EINVAL /
  * TTGBF_ENONFINITE on bad arguments, TTGBF_ECUDA if the launch fails.
- * The first call on a device (with that device current) looks the array's
- * device address up with cudaGetSymbolAddress; make that first call before
- * any stream capture.  All calls share the array: calls that overlap on the
+ * Every call looks the array's device address up with cudaGetSymbolAddress
+ * (with the caller's device current), so the address stays right after a
+ * context reset; the first call on a device also loads the library's device
+ * code there, so make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the
  * GPU (different streams, no ordering) race.  Nothing in the array needs to
  * start at zero: every entry a call reads, that call has written first.
  * Asynchronous on `stream`. */

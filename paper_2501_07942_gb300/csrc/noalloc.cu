@@ -11,7 +11,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "internal.cuh"
 #include "ttgbf.h"
@@ -160,10 +159,6 @@ __global__ void k_moments_noalloc(int B, NoAllocArgs a, const int* ranks, double
   }
 }
 
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
 }  // namespace
 
 extern "C" {
@@ -192,24 +187,17 @@ int ttgbf_moments_noalloc(int32_t batch, const ttgbf_grid* grid, const float* co
   }
   const long long need = (long long)batch * d * 3 * (long long)rank_max * rank_max;
   if (need > kNoAllocScratchDoubles) return TTGBF_ECAPACITY;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  // The array's device address is looked up on every call, with the
+  // caller's device current: it is cheap, allocates nothing, and stays right
+  // after the primary context was reset (the module is then loaded again,
+  // possibly at another address).  In host code the array's name is only a
+  // host-side stand-in and must never be passed to a kernel.
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_moment_scratch) != cudaSuccess || p == nullptr) {
     cudaGetLastError();
     return TTGBF_ECUDA;
   }
-  double* scratch;
-  {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch_ptr[dev] == nullptr) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_moment_scratch) != cudaSuccess || p == nullptr) {
-        cudaGetLastError();
-        return TTGBF_ECUDA;
-      }
-      g_scratch_ptr[dev] = (double*)p;
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  double* scratch = static_cast<double*>(p);
   ttgbf::count_launches(1);
   k_moments_noalloc<<<batch, 128, 0, (cudaStream_t)stream>>>(batch, a, ranks, scratch, mass, mean, cov);
   if (cudaPeekAtLastError() != cudaSuccess) {

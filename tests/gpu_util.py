@@ -22,8 +22,10 @@ def rel(a, b) -> float:
 
 def tt_tol(eps: float, tail_sum: float) -> float:
     """Parity bound of the TT path against the dense oracle for one step:
-    10 * (eps + discarded tail) + 1e-5 (the discarded tail is zero when the
-    rank cap does not bind, and then the bound is 10 eps + 1e-5)."""
+    10 * (eps + tau) + 1e-5, tau the discarded relative tails of the ORACLE's
+    TT filter (oracle/ttfilter.py) on the same input, never a tail the GPU
+    reports about itself.  Where the rank cap does not bind, tau is at the
+    eps level."""
     return 10.0 * (eps + tail_sum) + EPS_TOL_FLOOR
 
 
@@ -37,16 +39,27 @@ def cov_tol(delta_axis, cov):
 
 
 def mean_tol(delta_axis, cov, tail_acc):
-    """Posterior-mean tolerance per mode: 1e-3 grid spacings, plus, where
-    the rounding discarded more than eps (the rank cap binds), 2 tau sigma_m:
-    tau = the discarded relative tails summed over the steps so far bounds
-    the truncation's relative L2 change of the density, which moves the
-    mean of mode m by about tau times that marginal's standard deviation
-    sigma_m (from the oracle's covariance).  Without cap hits tau is at the
-    eps level and the bound is the plain 1e-3 grid spacings."""
+    """Posterior-mean tolerance per mode against the DENSE oracle: 1e-3 grid
+    spacings, plus 2 tau sigma_m for the truncation a TT of capped rank must
+    make: tau = the ORACLE TT filter's discarded relative tails summed over
+    the steps so far (a relative L2 change tau of the density moves the mean
+    of mode m by about tau sigma_m, sigma_m the oracle's marginal standard
+    deviation).  Against the oracle's own TT filter the bound is the flat
+    1e-3 grid spacings."""
     D = np.asarray(delta_axis, dtype=np.float64)
     sig = np.sqrt(np.maximum(np.diag(cov), 0.0))
     return 1e-3 * D + 2.0 * tail_acc * sig
+
+
+def oracle_tt_prior(model):
+    """The model's diagonal Gaussian prior as rank-1 float64 cores (the
+    oracle TT filter's starting point), normalised."""
+    g = pmf.Grid(model.lo, model.hi, model.n)
+    var = np.diag(model.P0)
+    cores = [np.exp(-0.5 * (g.axes[m] - model.m0[m]) ** 2 / var[m]).reshape(1, -1, 1)
+             for m in range(g.d)]
+    cores[-1] = cores[-1] / (tt.full_sum(cores) * g.delta)
+    return cores
 
 
 def device_tables(model: synth.Model, axes):

@@ -12,9 +12,11 @@ z_i = x_{2i}^2 / 20 + v_i, rank cap 32, eps 1e-5.
   TT inner products, so no 128^8 tensor is formed.
 
 Tolerances as for the other workloads: per step 10 (eps + tau) + 1e-5 in
-relative Frobenius norm, summed over the steps; means within 1e-3 grid
-spacings (plus 2 tau sigma where the rank cap binds); covariances within the matching 1e-3 (D_i sigma_j + D_j sigma_i);
-log c within 1e-3.  The shear span of this workload is at most 5 up
+relative Frobenius norm, summed over the steps, tau the discarded tails of
+the float64 TT filter of oracle/ttfilter.py on the same measurements (its
+ranks must equal the GPU's); means within 1e-3 grid spacings (plus 2 tau
+sigma where the rank cap binds); covariances within the matching 1e-3
+(D_i sigma_j + D_j sigma_i); log c within 1e-3.  The shear span of this workload is at most 5 up
 to N = 128 (|0.1 xi_vel / Delta_pos| <= 1.59), so the rank expansion stays at
 32 x 5 = 160 columns; at N = 256 it is 9 and the shears run in pieces."""
 import numpy as np
@@ -22,9 +24,10 @@ import pytest
 
 import synth
 from oracle import pmf, tt
+from oracle import ttfilter as T
 
 from gpu_util import (cov_tol, device_tables, lib_module, make_filter, mean_tol, oracle_grid,
-                      rel, tt_tol)
+                      oracle_tt_prior, rel, tt_tol)
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +59,7 @@ def test_config3_small_grid_vs_dense_oracle(G, d, n, steps):
     oc = model.tables(g.axes)
     zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
     Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
+    X = [oracle_tt_prior(model) for _ in mcs]
     bound = [0.0] * len(mcs)
     tacc = [0.0] * len(mcs)
     for k in range(steps):
@@ -67,8 +71,11 @@ def test_config3_small_grid_vs_dense_oracle(G, d, n, steps):
             Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
             mo, co = pmf.moments(Ps[i], g)
-            bound[i] += tt_tol(model.eps, st[i]["tail_sum"])
-            tacc[i] += st[i]["tail_sum"]
+            X[i], info = T.step(X[i], g, model.F, model.Q, oc, zs[i][k], model.R, model.eps,
+                                model.rank_cap, SPAN)
+            assert f.ranks()[i].tolist() == tt.ranks(X[i]), (k, i)
+            bound[i] += tt_tol(model.eps, info["tail_sum"])
+            tacc[i] += info["tail_sum"]
             e = rel(tt.densify(f.export_cores(i)), Ps[i])
             assert e <= bound[i], (k, i, e, bound[i])
             assert (np.abs(m[i] - mo) <= mean_tol(g.delta_axis, co, tacc[i])).all(), (k, i)
@@ -91,6 +98,9 @@ def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
     grids = [oracle_grid(bm) for bm in pairs]
     tabs = [bm.tables(gb.axes) for bm, gb in zip(pairs, grids)]
     P = [[pmf.prior(gb, bm.m0, bm.P0) for bm, gb in zip(pairs, grids)] for _ in mcs]
+    g = oracle_grid(model)
+    oc = model.tables(g.axes)
+    X = [oracle_tt_prior(model) for _ in mcs]
     bound = [0.0] * len(mcs)
     tacc = [0.0] * len(mcs)
     for k in range(steps):
@@ -117,8 +127,11 @@ def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
             nn = tt.inner(exact, exact)
             diff2 = tt.inner(cores, cores) - 2.0 * tt.inner(cores, exact) + nn
             e = float(np.sqrt(max(diff2, 0.0) / nn))
-            bound[b] += tt_tol(model.eps, st[b]["tail_sum"])
-            tacc[b] += st[b]["tail_sum"]
+            X[b], info = T.step(X[b], g, model.F, model.Q, oc, zs[b][k], model.R, model.eps,
+                                model.rank_cap, smax)
+            assert f.ranks()[b].tolist() == tt.ranks(X[b]), (k, b)
+            bound[b] += tt_tol(model.eps, info["tail_sum"])
+            tacc[b] += info["tail_sum"]
             assert e <= bound[b], (k, b, e, bound[b])
             D = np.concatenate([gb.delta_axis for gb in grids])
             assert (np.abs(m[b] - mean) <= mean_tol(D, cov, tacc[b])).all(), (k, b, m[b], mean)

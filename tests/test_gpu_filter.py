@@ -3,19 +3,21 @@ benchmark workloads against the dense FP64 oracle.
 
 Tolerances: per step the TT density may deviate from the oracle by
 10 * (eps + tau) + 1e-5 in relative Frobenius norm, tau being the discarded
-relative tail the rounding reports (tau = 0 when the rank cap does not bind).
-Over several steps the bounds of the steps add.  Posterior means agree within
-1e-3 grid spacings, plus 2 tau sigma_m where the rank cap binds (tau the
-summed discarded tails, sigma_m the oracle's marginal standard deviation);
-the same reading of the cap-binding regime as for the density bound."""
+relative tails of the float64 TT filter of oracle/ttfilter.py run on the same
+measurements with the same rank cap (tau is at the eps level when the cap
+does not bind; no bound uses a tail the GPU reports).  Over several steps the
+bounds of the steps add.  Posterior means agree within 1e-3 grid spacings,
+plus 2 tau sigma_m where the rank cap binds (tau the oracle's summed tails,
+sigma_m the oracle's marginal standard deviation)."""
 import numpy as np
 import pytest
 
 import synth
 from oracle import pmf, tt
+from oracle import ttfilter as T
 
 from gpu_util import (cov_tol, device_tables, lib_module, make_filter, mean_tol, oracle_grid,
-                      rel, tt_tol)
+                      oracle_tt_prior, rel, tt_tol)
 
 pytestmark = pytest.mark.gpu
 
@@ -26,10 +28,12 @@ def G():
 
 
 def run_compare(G, model, mcs, steps, batch_extra=0):
-    """Run len(mcs) filters on the GPU and the oracle on each; return per-step
-    errors (density rel, mean err / D, |log c diff|) and the bounds."""
+    """Run len(mcs) filters on the GPU, and the dense oracle and the oracle TT
+    filter (for the tails) on each; return per-step errors (density rel,
+    mean err / tolerance, |log c diff|) and the bounds."""
     B = len(mcs) + batch_extra
     f = make_filter(G, model, batch=B)
+    X = [oracle_tt_prior(model) for _ in mcs]
     comps = device_tables(model, f.grid_axes())
     g = oracle_grid(model)
     oc = model.tables(g.axes)
@@ -49,8 +53,10 @@ def run_compare(G, model, mcs, steps, batch_extra=0):
             Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
             mo, co = pmf.moments(Ps[i], g)
-            bound[i] += tt_tol(model.eps, st[i]["tail_sum"])  # predict + update tails
-            tacc[i] += st[i]["tail_sum"]
+            X[i], info = T.step(X[i], g, model.F, model.Q, oc, zs[i][k], model.R, model.eps,
+                                model.rank_cap)
+            bound[i] += tt_tol(model.eps, info["tail_sum"])  # the oracle's predict + update tails
+            tacc[i] += info["tail_sum"]
             e = rel(tt.densify(f.export_cores(i)), Ps[i])
             # mean error in units of its tolerance (< 1 passes)
             merr = float((np.abs(m[i] - mo) / mean_tol(g.delta_axis, co, tacc[i])).max())
@@ -117,11 +123,13 @@ def test_config2_one_step_from_oracle_posterior(G):
     f.normalise()
     comps = device_tables(model, f.grid_axes())
     f.predict(model.F, model.Q)
-    t_pred = f.stats()[0]["tail_sum"]
+    Xp, tp, _ = T.predict([c.astype(np.float64) for c in cores], g, model.F, model.Q, model.eps, 16)
+    t_pred = sum(tp)
     Pp, _ = pmf.predict_rg(P_in, g, model.F, model.Q)
     assert rel(tt.densify(f.export_cores(0)), Pp) <= tt_tol(model.eps, t_pred)
     f.update(comps, model.R, z[3][None, :])
-    t_step = f.stats()[0]["tail_sum"]  # predict + update tails of this step
+    _, tu, _ = T.update(Xp, g, oc, z[3], model.R, model.eps, 16)
+    t_step = t_pred + sum(tu)  # the oracle's predict + update tails of this step
     Pu, logc = pmf.update(Pp, g, pmf.likelihood(g, oc, z[3], model.R))
     assert rel(tt.densify(f.export_cores(0)), Pu) <= tt_tol(model.eps, t_step)
     m, c, lc, ll = f.estimate()
@@ -155,14 +163,16 @@ def test_config2_full_size_bench_launch(G):
     g = oracle_grid(model)
     oc = model.tables(g.axes)
     P = pmf.prior(g, model.m0, model.P0)
+    X = oracle_tt_prior(model)
     bound = 0.0
     tacc = 0.0
     for k in range(2):
         f.predict(model.F, model.Q)
         f.update(comps, model.R, zs[k])
         st = f.stats()
-        bound += tt_tol(model.eps, st[0]["tail_sum"])
-        tacc += st[0]["tail_sum"]
+        X, info = T.step(X, g, model.F, model.Q, oc, zs[k][0], model.R, model.eps, model.rank_cap)
+        bound += tt_tol(model.eps, info["tail_sum"])
+        tacc += info["tail_sum"]
         P, _ = pmf.predict_rg(P, g, model.F, model.Q)
         P, logc = pmf.update(P, g, pmf.likelihood(g, oc, zs[k][0], model.R))
         m, c, lc, ll = f.estimate()
@@ -222,6 +232,7 @@ def test_shears_in_pieces_small_grid(G):
     oc = model.tables(g.axes)
     zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
     Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
+    X = [oracle_tt_prior(model) for _ in mcs]
     bound = [0.0] * len(mcs)
     tacc = [0.0] * len(mcs)
     for k in range(steps):
@@ -233,8 +244,10 @@ def test_shears_in_pieces_small_grid(G):
             Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
             mo, co = pmf.moments(Ps[i], g)
-            bound[i] += tt_tol(model.eps, st[i]["tail_sum"])
-            tacc[i] += st[i]["tail_sum"]
+            X[i], info = T.step(X[i], g, model.F, model.Q, oc, zs[i][k], model.R, model.eps,
+                                model.rank_cap, 2)
+            bound[i] += tt_tol(model.eps, info["tail_sum"])
+            tacc[i] += info["tail_sum"]
             e = rel(tt.densify(f.export_cores(i)), Ps[i])
             assert e <= bound[i], (k, i, e, bound[i])
             assert (np.abs(m[i] - mo) <= mean_tol(g.delta_axis, co, tacc[i])).all(), (k, i)

@@ -2,12 +2,16 @@
 element by element on the densified TT (C ABI through the Python binding).
 
 Inputs are seeded: random positive index-space bump TTs (synth) or oracle
-densities; no input or expected value comes from the CUDA path."""
+densities; no input or expected value comes from the CUDA path.  Where an
+operation rounds, the bound 10 (eps + tau) + 1e-5 takes tau from the float64
+TT filter of oracle/ttfilter.py on the same cores, and the GPU's ranks must
+equal that oracle's."""
 import numpy as np
 import pytest
 
 import synth
 from oracle import pmf, tt
+from oracle import ttfilter as T
 
 from gpu_util import lib_module, rel, tt_tol
 
@@ -33,6 +37,13 @@ def bumps_filter(G, d=3, terms=3, seed=0, cap=16, smax=10, batch=1, n=None):
         f.import_cores(b, cores)
     g = pmf.Grid(LO[:d], HI[:d], n)
     return f, g, tt.densify([c.astype(np.float64) for c in cores])
+
+
+def bumps_cores(d=3, terms=3, seed=0, n=None):
+    """The float32 input cores of bumps_filter, as the oracle sees them."""
+    n = N[:d] if n is None else n
+    return [c.astype(np.float32).astype(np.float64)
+            for c in synth.random_index_bumps_tt(n, terms, seed)]
 
 
 def test_prior_matches_oracle(G):
@@ -64,10 +75,10 @@ def test_shear_unrounded_is_exact(G, m, n, a):
 def test_shear_rounded_within_eps(G, m, n, a):
     f, g, P = bumps_filter(G)
     f.shear(m, n, a, do_round=True)
-    st = f.stats()[0]
+    X, tails = T.shear_round(bumps_cores(), g, m, n, a, EPS, 16)
     ref = pmf.shear(P, g, m, n, a)
-    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, st["tail_sum"])
-    assert f.ranks()[0].max() <= 16
+    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, sum(tails))
+    assert f.ranks()[0].tolist() == tt.ranks(X)
 
 
 @pytest.mark.parametrize("m,n,a,smax", [(0, 1, 0.3, 3), (0, 2, -0.45, 3), (2, 0, 0.3, 4),
@@ -78,10 +89,10 @@ def test_wide_shear_in_pieces_within_eps(G, m, n, a, smax):
     whose TT sum is rounded again."""
     f, g, P = bumps_filter(G, smax=smax)
     f.shear(m, n, a, do_round=True)
-    st = f.stats()[0]
+    X, tails = T.shear_round(bumps_cores(), g, m, n, a, EPS, 16, smax)
     ref = pmf.shear(P, g, m, n, a)
-    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, st["tail_sum"])
-    assert f.ranks()[0].max() <= 16
+    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, sum(tails))
+    assert f.ranks()[0].tolist() == tt.ranks(X)
 
 
 def test_scale_and_convolve_are_exact(G):
@@ -145,16 +156,18 @@ def test_predict_one_step(G):
     Q = np.diag([0.05, 0.08, 0.03])
     f, g, P = bumps_filter(G)
     f.predict(F, Q)
-    st = f.stats()[0]
+    X, tails, _ = T.predict(bumps_cores(), g, F, Q, EPS, 16)
     ref, mass = pmf.predict_rg(P / (P.sum() * g.delta), g, F, Q)
-    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, st["tail_sum"])
+    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, sum(tails))
+    assert f.ranks()[0].tolist() == tt.ranks(X)
     # non-triangular F: L shears follow the scalings
     F2 = np.array([[0.95, 0.04, 0.0], [-0.05, 0.97, 0.02], [0.03, 0.0, 0.92]])
     f, g, P = bumps_filter(G)
     f.predict(F2, Q)
-    st = f.stats()[0]
+    X, tails, _ = T.predict(bumps_cores(), g, F2, Q, EPS, 16)
     ref, _ = pmf.predict_rg(P / (P.sum() * g.delta), g, F2, Q)
-    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, st["tail_sum"])
+    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(EPS, sum(tails))
+    assert f.ranks()[0].tolist() == tt.ranks(X)
 
 
 def test_update_one_and_two_mode_components(G):
@@ -171,12 +184,15 @@ def test_update_one_and_two_mode_components(G):
     z = np.array([[1.5, 0.3], [2.0, -0.5]])
     f.update(comps, R, z)
     m, c, lc, ll = f.estimate()
-    stats = f.stats()
     ocomps = [((0, 1), np.sqrt(g.axes[0][:, None] ** 2 + g.axes[1][None, :] ** 2)),
               ((2,), np.sin(g.axes[2]))]
+    X0 = bumps_cores()
+    X0[-1] = X0[-1] / (tt.full_sum(X0) * g.delta)
     for b in range(2):
         ref, logc = pmf.update(Pn, g, pmf.likelihood(g, ocomps, z[b], R))
-        assert rel(tt.densify(f.export_cores(b)), ref) <= tt_tol(EPS, stats[b]["tail_sum"])
+        X, tails, _ = T.update(X0, g, ocomps, z[b], R, EPS, 16)
+        assert rel(tt.densify(f.export_cores(b)), ref) <= tt_tol(EPS, sum(tails))
+        assert f.ranks()[b].tolist() == tt.ranks(X)
         assert abs(lc[b] - logc) < 1e-5
         assert abs(ll[b] - logc) < 1e-5
         mo, co = pmf.moments(ref, g)
@@ -240,5 +256,9 @@ def test_one_dimensional_and_tiny_grid(G):
     F = np.array([[0.9, 0.2], [0.0, 0.8]])
     f.predict(F, 0.1 * np.eye(2))
     g = pmf.Grid([-3.0, -2.0], [3.0, 2.0], [5, 3])
-    ref, _ = pmf.predict_rg(pmf.prior(g, [0.1, 0.0], np.diag([1.0, 0.5])), g, F, 0.1 * np.eye(2))
-    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(1e-6, f.stats()[0]["tail_sum"])
+    P0 = pmf.prior(g, [0.1, 0.0], np.diag([1.0, 0.5]))
+    ref, _ = pmf.predict_rg(P0, g, F, 0.1 * np.eye(2))
+    X0 = [np.exp(-0.5 * (g.axes[m] - [0.1, 0.0][m]) ** 2 / [1.0, 0.5][m]).reshape(1, -1, 1)
+          for m in range(2)]
+    X, tails, _ = T.predict(X0, g, F, 0.1 * np.eye(2), 1e-6, 8)
+    assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(1e-6, sum(tails))
