@@ -40,6 +40,9 @@ WORKLOAD = ("config2: d=4, 128^4 grid on [-8,8]^4, F=0.95I+0.05U, Q=0.05I, range
             "R=0.01, rank cap 16, eps 1e-6")
 UNIT = "filter-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 126 MiB L2 of GB300
+# TT configurations of the accuracy sweep: (rank cap, max shift span, rounding
+# precision); rank cap x span <= 160 (wider shears run in pieces)
+SWEEP = [(16, 10, "fp32"), (32, 5, "fp32"), (48, 3, "fp32"), (16, 10, "fp64")]
 
 
 def shard_mc_ids(rank: int, world: int, batch: int) -> list[int]:
@@ -134,29 +137,86 @@ def cpu_oracle_step(model, mc: int):
                 "FP64 numpy oracle")
 
 
+def ldu_ops(F):
+    """The elementary re-gridding operations the library applies for x -> F x
+    (F = L D U without pivoting): ("shear", m, n, a) for x_m += a x_n and
+    ("scale", m, lam), in the library's order (U's shears, D, L's shears).
+    Bookkeeping for the algorithmic work counts below."""
+    A = np.asarray(F, dtype=np.float64)
+    d = A.shape[0]
+    L, U, D = np.eye(d), np.eye(d), np.zeros(d)
+    for k in range(d):
+        D[k] = A[k, k] - sum(L[k, j] * D[j] * U[j, k] for j in range(k))
+        for i in range(k + 1, d):
+            L[i, k] = (A[i, k] - sum(L[i, j] * D[j] * U[j, k] for j in range(k))) / D[k]
+            U[k, i] = (A[k, i] - sum(L[k, j] * D[j] * U[j, i] for j in range(k))) / D[k]
+    ops = [("shear", m, n, U[m, n]) for m in range(d) for n in range(m + 1, d) if U[m, n] != 0.0]
+    ops += [("scale", m, D[m]) for m in range(d) if D[m] != 1.0]
+    ops += [("shear", m, n, L[m, n]) for m in range(d - 1, -1, -1) for n in range(m) if L[m, n] != 0.0]
+    return ops
+
+
+def shear_span(model, m, n, a) -> int:
+    """Integer shifts carrying hat weight in the shear x_m += a x_n."""
+    D = (model.hi - model.lo) / model.n
+    xi = model.lo[n] + (np.arange(model.n[n]) + 0.5) * D[n]
+    s = a * xi / D[m]
+    return int(np.floor(s).max() - np.floor(s).min()) + 2
+
+
 def fullgrid_bytes_per_step(model) -> int:
     """Algorithmic HBM bytes of one dense float32 step: every pass reads and
     writes the density once (shears, per-axis operators, normalise, likelihood,
     normalise) or reads it (sums, moments)."""
-    from oracle import pmf
-    n_shear = sum(1 for op in pmf.elementary_ops(model.F) if op[0] == "shear")
+    n_shear = sum(1 for op in ldu_ops(model.F) if op[0] == "shear")
     cells = int(np.prod(model.n))
     passes_rw = n_shear + model.d + 1 + 1 + 1   # shears, axis operators, scale, likelihood, scale
     passes_r = 1 + 1                            # mass sum, moments
     return cells * 4 * (2 * passes_rw + passes_r)
 
 
-def run_fullgrid(args, model, mc, zs, W, K, dev, ttf):
+def tsqr_algorithmic_flops(model, rank_cap) -> float:
+    """Algorithmic flops of the R factors of one filter step's roundings (the
+    rank-expanded links): per elementary shear of span S, every link it
+    expands carries an (r N) x (r S) unfolding whose R factor costs
+    2 (r N) (r S)^2 flops (r the rank cap, N the points per axis)."""
+    r = rank_cap
+    tot = 0.0
+    for op in ldu_ops(model.F):
+        if op[0] != "shear":
+            continue
+        _, m, n, a = op
+        S = shear_span(model, m, n, a)
+        N = int(model.n[min(m, n)])
+        tot += abs(m - n) * 2.0 * (r * N) * (r * S) ** 2
+    return tot
+
+
+def tt_dense_rel_err(cores, P) -> float:
+    """||T - P||_F / ||P||_F of a TT (cores [r_{k-1}][N_k][r_k]) and a dense
+    float64 density P, from <T, T>, <T, P> and <P, P>: T is never formed."""
+    cores = [np.asarray(c, dtype=np.float64) for c in cores]
+    E = np.ones((1, 1))
+    for C in cores:
+        E = np.einsum("ab,aic,bid->cd", E, C, C)
+    tt2 = float(E[0, 0])
+    X = np.tensordot(P, cores[-1][:, :, 0], axes=([P.ndim - 1], [1]))
+    for C in reversed(cores[:-1]):
+        X = np.tensordot(X, C, axes=([X.ndim - 2, X.ndim - 1], [1, 2]))
+    tp = float(np.asarray(X).reshape(-1)[0])
+    pp = float(np.vdot(P, P))
+    return math.sqrt(max(tt2 - 2.0 * tp + pp, 0.0) / pp)
+
+
+def run_fullgrid(args, model, zs, W, K, dev, axes):
     """The plain full-grid float32 filter on the same workload (one Monte Carlo
-    run, the batch's first): steps/s, achieved HBM bandwidth, and the density
-    error of the TT filter of that run against it after the same steps."""
+    run, the batch's first): steps/s and achieved HBM bandwidth."""
     import torch
     import paper_2501_07942_gb300 as G
-    from oracle import tt
     fg = G.FullGridFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), precision=32,
                           device=dev)
     comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
-             for m, t in model.tables(ttf.grid_axes())]
+             for m, t in model.tables(axes)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     for k in range(W):
@@ -186,13 +246,27 @@ def run_fullgrid(args, model, mc, zs, W, K, dev, ttf):
     out["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                        "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": src,
                        "bytes_per_step": bytes_step}
-    # the TT filter of the same run after the same W + K steps
-    if not args.no_tt_error:
-        P = fg.density()
-        T = tt.densify(ttf.export_cores(0))
-        out["tt_density_rel_fro_err"] = float(np.linalg.norm(T - P) / np.linalg.norm(P))
     fg.free()
     return out
+
+
+def fp64_reference_densities(model, zs, S, dev, axes):
+    """The float64 full-grid GPU filter (parity-tested against the oracle to
+    1e-12) on Monte Carlo run 0 for S steps: its density after every step,
+    as host float64 arrays (a generator, one step at a time)."""
+    import torch
+    import paper_2501_07942_gb300 as G
+    fg = G.FullGridFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), precision=64,
+                          device=dev)
+    comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float64, device=dev))
+             for m, t in model.tables(axes)]
+    try:
+        for k in range(S):
+            fg.predict(model.F, model.Q)
+            fg.update(comps, model.R, zs[k][0])
+            yield fg.density()
+    finally:
+        fg.free()
 
 
 def run_reference(args, rank: int, world: int):
@@ -225,6 +299,24 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def make_tt(G, model, dev, batch, rank_cap, smax, precision, parts=None):
+    """A TT filter context; parts (TTGBF_PARTS) overrides the library's batch
+    split for this context only."""
+    old = os.environ.get("TTGBF_PARTS")
+    if parts is not None:
+        os.environ["TTGBF_PARTS"] = str(parts)
+    try:
+        return G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=batch,
+                          rank_cap=rank_cap, eps=model.eps, max_shift_span=smax, device=dev,
+                          precision=precision)
+    finally:
+        if parts is not None:
+            if old is None:
+                del os.environ["TTGBF_PARTS"]
+            else:
+                os.environ["TTGBF_PARTS"] = old
+
+
 def run_ours(args, rank: int, world: int, local_rank: int, dist):
     import torch
     import paper_2501_07942_gb300 as G
@@ -233,12 +325,13 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     model = synth.config2()
     B = args.batch
     W, K = args.warmup, args.steps
+    cap, smax, prec = args.rank_cap, args.max_shift_span, args.precision
     mc_ids = shard_mc_ids(rank, world, B)
     zs = measurement_batches(model, mc_ids, W + 3 * K)
-    f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=B,
-                   rank_cap=model.rank_cap, eps=model.eps, device=dev)
+    f = make_tt(G, model, dev, B, cap, smax, prec)
+    axes = f.grid_axes()
     comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
-             for m, t in model.tables(f.grid_axes())]
+             for m, t in model.tables(axes)]
     z_dev = torch.tensor(zs, dtype=torch.float32, device=dev)
     d = model.d
     mean = torch.zeros(B, d, dtype=torch.float64, device=dev)
@@ -248,50 +341,53 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(k):
-        f.predict(model.F, model.Q)
-        f.update_dev(comps, model.R, z_dev[k])
-        f.estimate_dev(mean, cov, lc, ll)
+    def step(flt, k):
+        flt.predict(model.F, model.Q)
+        flt.update_dev(comps, model.R, z_dev[k])
+        flt.estimate_dev(mean, cov, lc, ll)
+
+    def timed(flt, k0, n):
+        """n steps from measurement k0, L2 flushed before each, CUDA events on
+        the caller's stream; returns the summed milliseconds."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        for i in range(n):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            step(flt, k0 + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in ev)
 
     for k in range(W):
-        step(k)
+        step(f, k)
     torch.cuda.synchronize(dev)
     if dist is not None:
         dist.barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
     l0 = G.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     if args.profile_region:
         torch.cuda.profiler.start()
-    for i in range(K):
-        flush.fill_(i & 0xFF)
-        ev[i][0].record(stream)
-        step(W + i)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize(dev)
+    ms = timed(f, W, K)
     if args.profile_region:
         torch.cuda.profiler.stop()
     launches = G.launch_count() - l0
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
 
-    # the full-grid filter on the same run, compared at the same step count
-    fullgrid = None if args.no_fullgrid else run_fullgrid(args, model, mc_ids[0], zs, W, K, dev, f)
-
-    # per-kernel-class times and device-counted flops: K more steps with the
-    # library's event profiling on (kept out of the timed steps above, whose
-    # value it would lower by the cost of its event records)
+    # per-kernel-class shares of the timed configuration: K more steps with
+    # the library's event profiling on (kept out of the timed steps above,
+    # whose value it would lower by the cost of its event records)
     torch.cuda.synchronize(dev)
     f.profile(True)
     for i in range(K):
         flush.fill_(i & 0xFF)
-        step(W + K + i)
+        step(f, W + K + i)
     torch.cuda.synchronize(dev)
     prof = f.profile_read()
     f.profile(False)
@@ -311,29 +407,97 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+    f.free()
+    del f
+    torch.cuda.empty_cache()
     if rank != 0:
         return
+
+    # the dominant kernel's roofline: the same workload as ONE part on one
+    # stream, so every event interval of the library's profiling brackets
+    # that kernel alone (no concurrent parts sharing the SMs)
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA lanes at max clock
-    tot_ms = sum(v["ms"] for v in prof.values())
-    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    name, rec = top
-    roofline = None
-    if rec["flops"] > 0 and rec["ms"] > 0:
-        achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                    "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                   f"(clock from {pk_src} peaks)"}
+    f1 = make_tt(G, model, dev, B, cap, smax, prec, parts=1)
+    for k in range(W):
+        step(f1, k)
+    torch.cuda.synchronize(dev)
+    f1.profile(True)
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        step(f1, W + i)
+    torch.cuda.synchronize(dev)
+    prof1 = f1.profile_read()
+    f1.free()
+    del f1
+    torch.cuda.empty_cache()
+    tsqr = prof1["tsqr"]
+    alg = tsqr_algorithmic_flops(model, cap) * B * K  # over the K profiled steps
+    achieved = alg / (tsqr["ms"] * 1e-3) / 1e12 if tsqr["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_tsqr", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "algorithmic_flops_per_filter_step": tsqr_algorithmic_flops(model, cap),
+                "launches": tsqr["launches"], "ms_per_launch": tsqr["ms"] / max(tsqr["launches"], 1),
+                "measured": f"{B} filters as one part on one stream, CUDA events around every "
+                            "k_tsqr launch (library profiling), K steps",
+                "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                               f"(clock from {pk_src} peaks); of derived peak"}
+
+    # the full-grid filter on the same workload (the metric's comparison)
+    fullgrid = None if args.no_fullgrid else run_fullgrid(args, model, zs, W, K, dev, axes)
+
+    # accuracy at the bench configuration and a rank-cap sweep: every TT
+    # configuration runs W + K steps from the prior on the batch's
+    # measurements; filter 0 (Monte Carlo run 0) is compared with the float64
+    # full-grid GPU filter of that run after every step
+    accuracy, sweep = None, []
+    if not args.no_accuracy:
+        S = W + K
+        bound = 10.0 * model.eps + 1e-5
+        configs = [(cap, smax, prec)] + [c for c in SWEEP if c != (cap, smax, prec)]
+        runs = []
+        for (rc, sp, pr) in configs:
+            g = make_tt(G, model, dev, B, rc, sp, pr)
+            runs.append({"cfg": (rc, sp, pr), "f": g, "ms": 0.0, "err": []})
+        for k, P in enumerate(fp64_reference_densities(model, zs, S, dev, axes)):
+            for r in runs:
+                g = r["f"]
+                if k >= W:
+                    r["ms"] += timed(g, k, 1)
+                else:
+                    step(g, k)
+                torch.cuda.synchronize(dev)
+                if k == S - 1 or r is runs[0]:
+                    r["err"].append(tt_dense_rel_err(g.export_cores(0), P))
+        main_errs = list(runs[0]["err"])
+        for r in runs:
+            rc, sp, pr = r["cfg"]
+            r["f"].free()
+            ent = {"rank_cap": rc, "max_shift_span": sp, "precision": pr,
+                   "value": B * K / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / K,
+                   "tt_density_rel_fro_err": r["err"][-1], "bound": bound,
+                   "matched": r["err"][-1] <= bound}
+            if fullgrid is not None:
+                ent["vs_fullgrid"] = ent["value"] / fullgrid["value"]
+            sweep.append(ent)
+        runs.clear()
+        torch.cuda.empty_cache()
+        accuracy = {"reference": "float64 full-grid GPU filter (ttgbf_fg, precision 64), Monte "
+                                 "Carlo run 0, same measurements",
+                    "steps": S, "per_step_rel_fro_err": main_errs, "bound": bound,
+                    "tt_density_rel_fro_err": sweep[0]["tt_density_rel_fro_err"],
+                    "matched": sweep[0]["matched"]}
     value = B * world * K / (ms * 1e-3)
     b = model.b
+    tot_ms = sum(v["ms"] for v in prof.values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD,
+        "config": {"workload": WORKLOAD.replace("rank cap 16", f"rank cap {cap}"),
+                   "rounding_precision": prec, "max_shift_span": smax,
                    "filters_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (independent filters, no collective)"},
         "roofline": roofline,
@@ -341,11 +505,20 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
                 "h2d_bytes_per_step": B * b * 4, "d2h_bytes_per_step": B * (d + d * d + 2) * 8},
         "gpu_launches": launches,
         "clocks": clk,
-        "kernels": {k: {"ms_share": (v["ms"] / tot_ms if tot_ms else 0.0), "launches": v["launches"],
-                        "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 else 0.0)}
+        "kernels": {k: {"ms_share": (v["ms"] / tot_ms if tot_ms else 0.0), "launches": v["launches"]}
                     for k, v in prof.items() if v["launches"] > 0},
         "fullgrid": fullgrid,
+        "accuracy": accuracy,
+        "rank_cap_sweep": sweep,
     }
+    if accuracy is not None:
+        ok = [e for e in sweep if e["matched"]]
+        best = min(ok, key=lambda e: e["ms_per_step"]) if ok else min(
+            sweep, key=lambda e: e["tt_density_rel_fro_err"])
+        line["matched_error"] = {
+            "met": bool(ok), "config": {k: best[k] for k in ("rank_cap", "max_shift_span", "precision")},
+            "value": best["value"], "tt_density_rel_fro_err": best["tt_density_rel_fro_err"],
+            "bound": best["bound"], "vs_fullgrid": best.get("vs_fullgrid")}
     if world == 1 and not args.no_cpu_baseline:
         dt, desc = cpu_oracle_step(model, mc_ids[0])
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(),
@@ -360,10 +533,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=100)
+    ap.add_argument("--rank-cap", type=int, default=16)
+    ap.add_argument("--max-shift-span", type=int, default=10)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="arithmetic of the truncating R factors and SVDs (ttgbf_opts.precision)")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy comparison and the rank-cap sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fullgrid", action="store_true")
-    ap.add_argument("--no-tt-error", action="store_true",
-                    help="skip the TT density error against the full-grid filter")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed TT steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off; the run's own timings are then invalid)")

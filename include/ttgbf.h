@@ -84,7 +84,50 @@ typedef struct {
   void* workspace;        /* caller-owned device memory of ttgbf_workspace_bytes() bytes, 256-byte
                              aligned, or NULL to let the library cudaMalloc it (freed by ttgbf_free) */
   size_t workspace_bytes; /* size of `workspace` when it is given */
+  int32_t precision;      /* TTGBF_PRECISION_FP32 (0, default) or TTGBF_PRECISION_FP64; see below */
+  int32_t conv;           /* TTGBF_CONV_AUTO (0, default), TTGBF_CONV_DENSE or TTGBF_CONV_FFT */
+  /* Launch configuration (0 = default; ttgbf_autotune chooses them from measured step times):
+   * parts: sub-batches on their own streams, 1..8 (default one per 12 filters, at most 8; the
+   *        environment variable TTGBF_PARTS overrides the default);
+   * tsqr_slice_blocks: 128-row blocks per CTA slice of a tall R factor, 2, 4, 8 (default) or 16;
+   * svd_threads: CTA width of the truncating SVD stages, 512 (default) or 1024. */
+  int32_t parts;
+  int32_t tsqr_slice_blocks;
+  int32_t svd_threads;
 } ttgbf_opts;
+
+/* How the Gaussian kernel of the predictive step (Eq. tpmconvFFT, applied to
+ * the grid index of every core) is computed:
+ *  DENSE: the N x N Toeplitz matrix (fused with the mode's cloud-in-cell
+ *         scaling when one precedes it) as a GEMM over the core's fibres.
+ *  FFT:   the linear convolution of every fibre through zero-padded cyclic
+ *         FFTs of length M = 2^m >= 2N - 1 (float32; the kernel's spectrum is
+ *         computed in float64 on the host); a preceding scaling is applied as
+ *         its cloud-in-cell gather while the fibres are loaded.  Taken for
+ *         modes with N <= 512 whose scaling has at most 3 source cells per
+ *         target cell; other modes use DENSE.
+ *  AUTO:  FFT for modes with N >= 256, DENSE below (the faster of the two on
+ *         GB300 at those sizes). */
+#define TTGBF_CONV_AUTO 0
+#define TTGBF_CONV_DENSE 1
+#define TTGBF_CONV_FFT 2
+
+/* Arithmetic of the TT rounding (Sec. 4.1 "round").  The cores, the shears,
+ * the per-mode operators and the likelihood are float32 in both modes, and
+ * the log normaliser and the moments are accumulated in float64.
+ *  FP32: every stage forms the R factor of its tall unfolding (Householder)
+ *        and the SVD of R (pivoted QR, then one-sided Jacobi) in float32.
+ *  FP64: the stages that decide a truncation (the left-to-right sweep and the
+ *        split of the merged 2-site core) form R and its SVD in float64, so
+ *        the singular values compared with eps ||A|| / sqrt(d - 1) are those
+ *        of the float32 cores to float64 accuracy; the orthogonalisation
+ *        sweep, which truncates nothing, stays float32.  GB300 issues float64
+ *        at a small fraction of its float32 rate: this mode is slower.
+ *        The float64 SVD keeps at most min(rank_cap + 16, 80) leading rows of
+ *        the pivoted QR for its Jacobi sweeps; what the pivoted QR leaves is
+ *        counted in the discarded tail. */
+#define TTGBF_PRECISION_FP32 0
+#define TTGBF_PRECISION_FP64 1
 
 /* One measurement component z_c = h_c(x_m [, x_n]) + v_c that depends on one
  * mode or on two adjacent modes (Sec. 4, fourth bullet: the likelihood
@@ -240,6 +283,85 @@ int ttgbf_profile_read(ttgbf_ctx* ctx, ttgbf_kernel_prof* out, int32_t cap, int3
 
 /* Kernel launches made by the library in this process so far. */
 uint64_t ttgbf_launch_count(void);
+
+/* ---- groups of uneven batches, CUDA graphs, autotuning -------------------- */
+
+/* A group steps several contexts together: batches of filters of different
+ * d, N, rank cap or model (Alg. 3 for each), one context per shape.  A step
+ * enqueues predict -> update -> estimate of every context with their
+ * operations interleaved (every context's, and every part's, stream starts
+ * after the work already on the group's stream and the group's stream waits
+ * for all of them at the end), so the contexts' kernels overlap on the GPU.
+ * Because one step touches only these streams and synchronises nothing on the
+ * host, a horizon of steps can be recorded once into a CUDA graph and
+ * launched as a whole.  Contexts used by a group should have distinct streams
+ * (contexts sharing a stream run one after another).  The group does not own
+ * the contexts; free it before them. */
+typedef struct ttgbf_group ttgbf_group;
+
+/* Per context, one step's inputs and outputs (same meaning as ttgbf_predict,
+ * ttgbf_update_dev and ttgbf_estimate_dev): F, Q host d*d; h, R as
+ * ttgbf_update; z_dev DEVICE float32 [batch][b]; mean [batch][d], cov
+ * [batch][d][d], log_c [batch], log_lik [batch] DEVICE float64 (any may be
+ * NULL).  For ttgbf_group_capture the device arrays hold a whole horizon:
+ * step t reads z_dev + t batch b and writes mean + t batch d, cov +
+ * t batch d^2, log_c + t batch, log_lik + t batch. */
+typedef struct {
+  const double* F;
+  const double* Q;
+  const ttgbf_meas* h;
+  const double* R;
+  const float* z_dev;
+  double* mean;
+  double* cov;
+  double* log_c;
+  double* log_lik;
+} ttgbf_group_step_args;
+
+/* ctxs: host array of n distinct contexts (n >= 1); stream: the group's
+ * cudaStream_t (NULL = legacy default stream). */
+int ttgbf_group_create(ttgbf_group** out, ttgbf_ctx* const* ctxs, int32_t n, void* stream);
+
+/* One step of every context (args: host array of n).  On TTGBF_EINVAL /
+ * TTGBF_ENONFINITE nothing was enqueued.  Asynchronous on the group's stream. */
+int ttgbf_group_step(ttgbf_group* g, const ttgbf_group_step_args* args);
+
+/* Record `steps` consecutive steps of every context into a CUDA graph
+ * (replacing any earlier one) without running them; ttgbf_group_launch runs
+ * it.  The transition operators of each context's F, Q are prepared on the
+ * host first (outside the recording).  Every pointer in args is baked into
+ * the graph: a launch reads the measurements and writes the estimates at
+ * those addresses, so a caller replays a horizon by refilling z_dev. */
+int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32_t steps);
+
+/* Launch the recorded graph on the group's stream (asynchronous). */
+int ttgbf_group_launch(ttgbf_group* g);
+
+/* Kernel launches one launch of the recorded graph makes. */
+uint64_t ttgbf_group_graph_kernels(const ttgbf_group* g);
+
+/* Per context (host array of n floats): milliseconds from the start of the
+ * last ttgbf_group_step to the end of that context's work in it, every filter
+ * of the context finishing then (the per-filter step latency of a batch step).
+ * Synchronises; TTGBF_EINVAL when no step was timed (graph launches are not). */
+int ttgbf_group_times(ttgbf_group* g, float* ms);
+
+int ttgbf_group_free(ttgbf_group* g);
+
+/* Launch-configuration autotuner.  For the batch shape of *base (grid,
+ * batch, rank cap, span, precision, conv) and the model F, Q, times `steps`
+ * predictive steps (after one untimed step) of every candidate launch
+ * configuration: parts 1, 2, 4, 8 (at most the batch), tsqr_slice_blocks 4,
+ * 8, 16 and svd_threads 512, 1024; the predictive step is where the
+ * rounding's QR and SVD kernels run.  Writes base with the fastest
+ * configuration to *best and its time per step (ms) to *best_ms.  Each
+ * candidate allocates its own device workspace (cudaMalloc) for the timing.
+ * cache_path (may be NULL): a text file of earlier results, one line per
+ * shape and GPU; a shape found there is returned without timing (*best_ms
+ * then holds the recorded time), a new result is appended. */
+int ttgbf_autotune(const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf_opts* base,
+                   const double* F, const double* Q, int32_t steps, const char* cache_path,
+                   ttgbf_opts* best, double* best_ms);
 
 /* ---- plain full-grid point-mass filter ------------------------------------ */
 

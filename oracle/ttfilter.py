@@ -83,22 +83,27 @@ def _rank_and_tail(s, thr, rmax):
     return r, float(tail[r])
 
 
-def left_sweep(G, k0, k1, thr, rmax, normA):
+def left_sweep(G, k0, k1, thr, rmax, normA, trace=None):
     """Truncated SVD of the links k0..k1-1 (between cores k and k+1), left to
     right, for a TT whose cores left of k0 are left-orthonormal and right of
-    k0 right-orthonormal.  Returns the relative tails."""
+    k0 right-orthonormal.  Returns the relative tails.  trace (a list, when
+    given) receives one record per link: link index, singular values,
+    threshold, norm and the rank kept."""
     tails = []
     for k in range(k0, k1):
         r0, n, r1 = G[k].shape
         U, s, Vt = np.linalg.svd(G[k].reshape(r0 * n, r1), full_matrices=False)
         r, tail = _rank_and_tail(s, thr, rmax)
+        if trace is not None:
+            trace.append({"link": k, "s": s.copy(), "thr": thr, "normA": normA, "rank": r,
+                          "rmax": rmax})
         tails.append(tail / normA if normA > 0 else 0.0)
         G[k] = U[:, :r].reshape(r0, n, r)
         G[k + 1] = np.einsum("ab,bic->aic", s[:r, None] * Vt[:r], G[k + 1])
     return tails
 
 
-def round_block(G, lo, hi, eps, rmax):
+def round_block(G, lo, hi, eps, rmax, trace=None):
     """Rounding of the links inside [lo, hi] of a TT whose cores outside the
     block are orthonormal (left of lo left-, right of hi right-orthonormal):
     right-to-left orthogonalisation of cores hi..lo+1, then left-to-right
@@ -111,13 +116,13 @@ def round_block(G, lo, hi, eps, rmax):
     if d < 2 or normA == 0.0:
         return [0.0] * (hi - lo)
     thr = eps * normA / math.sqrt(d - 1)
-    return left_sweep(G, lo, hi, thr, rmax, normA)
+    return left_sweep(G, lo, hi, thr, rmax, normA, trace)
 
 
-def round_full(cores, eps, rmax):
+def round_full(cores, eps, rmax, trace=None):
     """Full TT rounding (every link): round_block over [0, d-1]."""
     G = _cores(cores)
-    tails = round_block(G, 0, len(G) - 1, eps, rmax) if len(G) > 1 else []
+    tails = round_block(G, 0, len(G) - 1, eps, rmax, trace) if len(G) > 1 else []
     return G, tails
 
 
@@ -160,7 +165,7 @@ def shear_shifts(grid: pmf.Grid, m: int, n: int, a: float):
     return s, ts
 
 
-def shear_round(G, grid, m, n, a, eps, rmax, smax=10):
+def shear_round(G, grid, m, n, a, eps, rmax, smax=10, trace=None):
     """Shear x_m += a x_n as a TT operator followed by rounding of its block
     (pieces of at most smax shifts when it spans more).  Returns (cores,
     tails)."""
@@ -170,16 +175,16 @@ def shear_round(G, grid, m, n, a, eps, rmax, smax=10):
     S = len(ts)
     if S <= smax:
         G = tt.shear_operator(G, m, n, s, ts)
-        return G, round_block(G, lo, hi, eps, rmax)
+        return G, round_block(G, lo, hi, eps, rmax, trace)
     npieces = -(-S // smax)
     tails, pieces = [], []
     for p in range(npieces):
         u0, u1 = S * p // npieces, S * (p + 1) // npieces
         P = tt.shear_operator(G, m, n, s, ts[u0:u1])
-        tails += round_block(P, lo, hi, eps, rmax)
+        tails += round_block(P, lo, hi, eps, rmax, trace)
         pieces.append(P)
     G = add_block(pieces, lo, hi)
-    tails += round_block(G, lo, hi, eps, rmax)
+    tails += round_block(G, lo, hi, eps, rmax, trace)
     return G, tails
 
 
@@ -196,7 +201,7 @@ def normalise(G, grid):
     return c
 
 
-def predict(cores, grid: pmf.Grid, F, Q, eps, rmax, smax=10):
+def predict(cores, grid: pmf.Grid, F, Q, eps, rmax, smax=10, trace=None):
     """TT predictive step with the re-gridded transition.  Returns (cores,
     tails of every rounding in order, mass before normalisation)."""
     Q = np.asarray(Q, dtype=np.float64)
@@ -204,7 +209,7 @@ def predict(cores, grid: pmf.Grid, F, Q, eps, rmax, smax=10):
     tails = []
     for op in pmf.elementary_ops(F):
         if op[0] == "shear":
-            G, t = shear_round(G, grid, op[1], op[2], op[3], eps, rmax, smax)
+            G, t = shear_round(G, grid, op[1], op[2], op[3], eps, rmax, smax, trace)
             tails += t
         else:
             apply_mode(G, op[1], pmf.cic_matrix(grid, op[1], op[2]))
@@ -222,7 +227,7 @@ def _lik_factor(table, z, r):
     return np.exp(-0.5 * (z - h) ** 2 / r) / math.sqrt(2 * math.pi * r)
 
 
-def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax):
+def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None):
     """TT Bayes update.  comps = [(modes, table)] as for pmf.likelihood; at most
     one two-mode component, on modes (0, 1).  Returns (cores, tails, log c)."""
     R = np.atleast_2d(np.asarray(R, dtype=np.float64))
@@ -254,10 +259,13 @@ def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax):
         thr = eps * normA / math.sqrt(d - 1) if d > 1 else 0.0
         U, s, Vt = np.linalg.svd(W.reshape(N0, N1 * r2), full_matrices=False)
         rk, tail = _rank_and_tail(s, thr, rmax)
+        if trace is not None:
+            trace.append({"link": 0, "s": s.copy(), "thr": thr, "normA": normA, "rank": rk,
+                          "rmax": rmax})
         tails.append(tail / normA)
         G[0] = U[:, :rk].reshape(1, N0, rk)
         G[1] = (s[:rk, None] * Vt[:rk]).reshape(rk, N1, r2)
-        tails += left_sweep(G, 1, d - 1, thr, rmax, normA)
+        tails += left_sweep(G, 1, d - 1, thr, rmax, normA, trace)
     normalise(G, grid)
     return G, tails, logc
 
@@ -271,6 +279,23 @@ def step(cores, grid, F, Q, comps, z, R, eps, rmax, smax=10):
 
 
 # --------------------------------------------------------------- moments ----
+def rank_is_borderline(rec, rank, eta):
+    """Whether a rank other than the oracle's on a link is a decision at the
+    threshold: data whose singular values are perturbed by up to eta thr could
+    take it.  Keeping more (rank > r): the tail of rank - 1 is within eta thr
+    below the threshold; keeping fewer: the tail of `rank` is within eta thr
+    above it.  A rank above the cap never is."""
+    s, thr, r = rec["s"], rec["thr"], rec["rank"]
+    if rank == r:
+        return True
+    tail = np.sqrt(np.concatenate([np.cumsum((s ** 2)[::-1])[::-1], [0.0]]))
+    if rank < 1 or rank >= len(tail) or (rec["rmax"] is not None and rank > rec["rmax"]):
+        return False
+    if rank > r:
+        return bool(tail[rank - 1] >= (1.0 - eta) * thr)
+    return bool(tail[rank] <= (1.0 + eta) * thr)
+
+
 def moments(cores, grid: pmf.Grid):
     """Point-mass mean and covariance of a TT density (unit mass assumed, as
     pmf.moments) by TT contractions: A_k^(p) = sum_i xi_{k,i}^p G_k(:, i, :),

@@ -35,7 +35,9 @@ EXPORTED = [
     "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise", "ttgbf_profile",
     "ttgbf_profile_read", "ttgbf_launch_count", "ttgbf_moments_noalloc", "ttgbf_fg_workspace_bytes",
     "ttgbf_fg_init", "ttgbf_fg_predict", "ttgbf_fg_predict_direct", "ttgbf_fg_update",
-    "ttgbf_fg_estimate", "ttgbf_fg_density", "ttgbf_fg_free",
+    "ttgbf_fg_estimate", "ttgbf_fg_density", "ttgbf_fg_free", "ttgbf_group_create",
+    "ttgbf_group_step", "ttgbf_group_capture", "ttgbf_group_launch", "ttgbf_group_graph_kernels",
+    "ttgbf_group_times", "ttgbf_group_free", "ttgbf_autotune",
 ]
 
 
@@ -57,7 +59,13 @@ class Prior(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("max_shift_span", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("precision", ctypes.c_int32), ("conv", ctypes.c_int32), ("parts", ctypes.c_int32),
+                ("tsqr_slice_blocks", ctypes.c_int32), ("svd_threads", ctypes.c_int32)]
+
+
+PRECISION = {"fp32": 0, "fp64": 1}  # TTGBF_PRECISION_FP32 / TTGBF_PRECISION_FP64
+CONV = {"auto": 0, "dense": 1, "fft": 2}  # TTGBF_CONV_AUTO / _DENSE / _FFT
 
 
 class MeasComp(ctypes.Structure):
@@ -67,6 +75,13 @@ class MeasComp(ctypes.Structure):
 
 class Meas(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int32), ("comp", ctypes.POINTER(MeasComp))]
+
+
+class GroupStepArgs(ctypes.Structure):
+    _fields_ = [("F", ctypes.POINTER(ctypes.c_double)), ("Q", ctypes.POINTER(ctypes.c_double)),
+                ("h", ctypes.POINTER(Meas)), ("R", ctypes.POINTER(ctypes.c_double)),
+                ("z_dev", ctypes.c_void_p), ("mean", ctypes.c_void_p), ("cov", ctypes.c_void_p),
+                ("log_c", ctypes.c_void_p), ("log_lik", ctypes.c_void_p)]
 
 
 class StepStats(ctypes.Structure):
@@ -129,6 +144,16 @@ def load() -> ctypes.CDLL:
     lib.ttgbf_fg_estimate.argtypes = [VP, dp, dp, dp, dp]
     lib.ttgbf_fg_density.argtypes = [VP, dp, ctypes.c_size_t]
     lib.ttgbf_fg_free.argtypes = [VP]
+    lib.ttgbf_group_create.argtypes = [P(VP), P(VP), ctypes.c_int32, VP]
+    lib.ttgbf_group_step.argtypes = [VP, P(GroupStepArgs)]
+    lib.ttgbf_group_capture.argtypes = [VP, P(GroupStepArgs), ctypes.c_int32]
+    lib.ttgbf_group_launch.argtypes = [VP]
+    lib.ttgbf_group_graph_kernels.restype = ctypes.c_uint64
+    lib.ttgbf_group_graph_kernels.argtypes = [VP]
+    lib.ttgbf_group_times.argtypes = [VP, P(ctypes.c_float)]
+    lib.ttgbf_group_free.argtypes = [VP]
+    lib.ttgbf_autotune.argtypes = [P(Grid), P(Prior), P(Opts), dp, dp, ctypes.c_int32, ctypes.c_char_p,
+                                   P(Opts), dp]
     _lib = lib
     return lib
 
@@ -162,9 +187,10 @@ def _grid(lo, hi, n):
     return g, (n, lo, hi)
 
 
-def workspace_bytes(lo, hi, n, batch=1, rank_cap=16, eps=1e-6, max_shift_span=0) -> int:
+def workspace_bytes(lo, hi, n, batch=1, rank_cap=16, eps=1e-6, max_shift_span=0,
+                    precision="fp32", conv="auto") -> int:
     g, keep = _grid(lo, hi, n)
-    o = Opts(batch, rank_cap, eps, max_shift_span, None, None, 0)
+    o = Opts(batch, rank_cap, eps, max_shift_span, None, None, 0, PRECISION[precision], CONV[conv])
     return int(load().ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o)))
 
 
@@ -239,16 +265,24 @@ class TTFilter:
     (``ttgbf_init``).  Device memory comes from a torch uint8 workspace."""
 
     def __init__(self, lo, hi, n, prior_mean, prior_var, batch=1, rank_cap=16, eps=1e-6,
-                 max_shift_span=0, stream=None, device="cuda"):
+                 max_shift_span=0, stream=None, device="cuda", precision="fp32", conv="auto",
+                 parts=0, tsqr_slice_blocks=0, svd_threads=0):
+        """precision: "fp32" (R factors and SVDs of the rounding in float32) or
+        "fp64" (those of the truncating stages in float64), ttgbf_opts.precision.
+        conv: "auto", "dense" or "fft", how the Gaussian kernel is applied
+        (ttgbf_opts.conv).  parts, tsqr_slice_blocks, svd_threads: the launch
+        configuration (0 = the library's default; see ttgbf_autotune)."""
         import torch
         self._lib = load()
         self.d = len(n)
         self.n = [int(v) for v in n]
         self.batch = int(batch)
+        self.precision = precision
         g, self._gkeep = _grid(lo, hi, n)
         self._stream = torch.cuda.current_stream(device) if stream is None else stream
         o = Opts(self.batch, int(rank_cap), float(eps), int(max_shift_span),
-                 ctypes.c_void_p(self._stream.cuda_stream), None, 0)
+                 ctypes.c_void_p(self._stream.cuda_stream), None, 0, PRECISION[precision],
+                 CONV[conv], int(parts), int(tsqr_slice_blocks), int(svd_threads))
         nbytes = self._lib.ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
         pm, pv = _f64(prior_mean), _f64(prior_var)
         pr = Prior(_dptr(pm), _dptr(pv))
@@ -393,3 +427,89 @@ class TTFilter:
             self.free()
         except Exception:
             pass
+
+
+class TTFilterGroup:
+    """Several TTFilter batches of different shape stepped together
+    (ttgbf_group_*): one call enqueues predict -> update -> estimate of every
+    batch with their operations interleaved; a horizon of steps can be
+    recorded into a CUDA graph (capture) and launched as a whole (launch)."""
+
+    def __init__(self, filters, stream=None, device="cuda"):
+        import torch
+        self._lib = load()
+        self.filters = list(filters)
+        self._stream = torch.cuda.current_stream(device) if stream is None else stream
+        arr = (ctypes.c_void_p * len(self.filters))(*[f._ctx.value for f in self.filters])
+        self._g = ctypes.c_void_p()
+        _check(self._lib.ttgbf_group_create(ctypes.byref(self._g), arr, len(self.filters),
+                                            ctypes.c_void_p(self._stream.cuda_stream)),
+               "ttgbf_group_create")
+
+    def _args(self, models):
+        """models: per filter (F, Q, comps, R, z_dev, mean, cov, log_c, log_lik)
+        with device tensors (or None for outputs)."""
+        keep = []
+        arr = (GroupStepArgs * len(models))()
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        for i, (F, Q, comps, R, z, mean, cov, lc, ll) in enumerate(models):
+            F, Q, R = _f64(F), _f64(Q), _f64(R)
+            m, marr = TTFilter._meas(comps)
+            keep += [F, Q, R, m, marr]
+            arr[i].F, arr[i].Q, arr[i].R = _dptr(F), _dptr(Q), _dptr(R)
+            arr[i].h = ctypes.pointer(m)
+            arr[i].z_dev, arr[i].mean, arr[i].cov = ptr(z), ptr(mean), ptr(cov)
+            arr[i].log_c, arr[i].log_lik = ptr(lc), ptr(ll)
+        return arr, keep
+
+    def step(self, models):
+        arr, keep = self._args(models)
+        _check(self._lib.ttgbf_group_step(self._g, arr), "ttgbf_group_step")
+
+    def capture(self, models, steps):
+        arr, keep = self._args(models)
+        _check(self._lib.ttgbf_group_capture(self._g, arr, int(steps)), "ttgbf_group_capture")
+
+    def launch(self):
+        _check(self._lib.ttgbf_group_launch(self._g), "ttgbf_group_launch")
+
+    def graph_kernels(self) -> int:
+        return int(self._lib.ttgbf_group_graph_kernels(self._g))
+
+    def times(self):
+        """Per filter batch: ms from the last step's start to its end."""
+        ms = (ctypes.c_float * len(self.filters))()
+        _check(self._lib.ttgbf_group_times(self._g, ms), "ttgbf_group_times")
+        return list(ms)
+
+    def free(self):
+        if getattr(self, "_g", None) is not None and self._g.value:
+            self._lib.ttgbf_group_free(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def autotune(lo, hi, n, prior_mean, prior_var, F, Q, batch=1, rank_cap=16, eps=1e-6,
+             max_shift_span=0, precision="fp32", conv="auto", steps=3, cache_path=None):
+    """ttgbf_autotune: the fastest launch configuration (parts,
+    tsqr_slice_blocks, svd_threads) for this batch shape and model, and its
+    time per predictive step in ms."""
+    lib = load()
+    g, gkeep = _grid(lo, hi, n)
+    pm, pv = _f64(prior_mean), _f64(prior_var)
+    pr = Prior(_dptr(pm), _dptr(pv))
+    o = Opts(int(batch), int(rank_cap), float(eps), int(max_shift_span), None, None, 0,
+             PRECISION[precision], CONV[conv], 0, 0, 0)
+    best = Opts()
+    ms = ctypes.c_double()
+    F, Q = _f64(F), _f64(Q)
+    cp = cache_path.encode() if cache_path else None
+    _check(lib.ttgbf_autotune(ctypes.byref(g), ctypes.byref(pr), ctypes.byref(o), _dptr(F), _dptr(Q),
+                              int(steps), cp, ctypes.byref(best), ctypes.byref(ms)), "ttgbf_autotune")
+    return {"parts": best.parts, "tsqr_slice_blocks": best.tsqr_slice_blocks,
+            "svd_threads": best.svd_threads}, ms.value

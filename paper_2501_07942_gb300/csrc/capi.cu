@@ -24,6 +24,7 @@
 #include <functional>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -35,9 +36,18 @@ namespace {
 
 constexpr int kMaxComps = 16;
 
-enum ProfClass : int { kPTsqr = 0, kPSvd, kPGemm, kPShear, kPMoments, kPLik, kPPlan, kPOther, kPClasses };
+enum ProfClass : int { kPTsqr = 0, kPSvd, kPGemm, kPShear, kPMoments, kPLik, kPPlan, kPOther, kPFft,
+                       kPClasses };
 const char* const kProfNames[kPClasses] = {"tsqr", "svd", "gemm", "shear_expand", "moments",
-                                           "likelihood", "plan", "other"};
+                                           "likelihood", "plan", "other", "fft_conv"};
+
+// Smallest power of two >= 2N - 1: the length of the zero-padded cyclic
+// convolution that equals the linear one on the grid.
+int fft_len(int N) {
+  int M = 1;
+  while (M < 2 * N - 1) M <<= 1;
+  return M;
+}
 
 std::atomic<unsigned long long> g_launches{0};
 
@@ -60,7 +70,7 @@ struct Layout {
   size_t normA, tail_sum, tail_max, mass, mass_pred, log_c, log_lik, logoff, mean, cov;
   size_t cap_hits, newrank, lik_off;
   size_t tsqr_prob, tsqr_off, tsqr_cnt, stack[2];
-  size_t P1, P2, gdesc, gtiles, awork, W, opmats, zbuf, prof_flops;
+  size_t P1, P2, gdesc, gtiles, awork, W, opmats, zbuf, prof_flops, fft_off;
   size_t total;
   long long core_cap[kMaxD];
   long long stack_cap, W_cap, opmats_floats, awork_stride;
@@ -82,8 +92,8 @@ bool finite_all(const double* p, size_t n) {
 
 // Floats of the per-filter TSQR stack for an M x n problem: one n x n R
 // factor per row slice.
-long long tsqr_stack_for(long long M, int n) {
-  long long nsl = (M + tsqr_slice_rows(n) - 1) / tsqr_slice_rows(n);
+long long tsqr_stack_for(long long M, int n, int slice_blocks) {
+  long long nsl = (M + tsqr_slice_rows(slice_blocks) - 1) / tsqr_slice_rows(slice_blocks);
   nsl = std::max<long long>(1, std::min<long long>(nsl, kTsqrMaxSlices));
   return nsl * (long long)n * n;
 }
@@ -100,6 +110,13 @@ int validate_grid(const ttgbf_grid* g) {
 
 int validate_opts(const ttgbf_opts* o) {
   if (!o || o->batch < 1 || o->rank_cap < 1) return TTGBF_EINVAL;
+  if (o->precision != TTGBF_PRECISION_FP32 && o->precision != TTGBF_PRECISION_FP64) return TTGBF_EINVAL;
+  if (o->conv < TTGBF_CONV_AUTO || o->conv > TTGBF_CONV_FFT) return TTGBF_EINVAL;
+  if (o->parts < 0 || o->parts > 8) return TTGBF_EINVAL;
+  if (o->tsqr_slice_blocks != 0 && o->tsqr_slice_blocks != 2 && o->tsqr_slice_blocks != 4 &&
+      o->tsqr_slice_blocks != 8 && o->tsqr_slice_blocks != 16)
+    return TTGBF_EINVAL;
+  if (o->svd_threads != 0 && o->svd_threads != 512 && o->svd_threads != 1024) return TTGBF_EINVAL;
   if (!std::isfinite(o->eps)) return TTGBF_ENONFINITE;
   if (o->eps < 0.0) return TTGBF_EINVAL;
   const int smax = o->max_shift_span > 0 ? o->max_shift_span : 10;
@@ -153,7 +170,11 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   const long long Mmax = (long long)capr * nmax;
   const int nsplit = (d >= 2) ? std::min<int>(g->n[0], kMaxN) : 1;
   long long stack = 0;
-  for (int n = 1; n <= std::max(capr, nsplit); ++n) stack = std::max(stack, tsqr_stack_for(Mmax, n));
+  const int sblocks = o->tsqr_slice_blocks > 0 ? o->tsqr_slice_blocks : kTsqrSliceBlocks;
+  for (int n = 1; n <= std::max(capr, nsplit); ++n)
+    stack = std::max(stack, tsqr_stack_for(Mmax, n, sblocks));
+  // float64 slice factors take two words per entry
+  if (o->precision == TTGBF_PRECISION_FP64) stack *= 2;
   L.stack_cap = stack;
   L.stack[0] = a.take<float>((size_t)B * stack);
   L.stack[1] = a.take<float>((size_t)B * stack);
@@ -168,7 +189,11 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   L.W = a.take<float>((size_t)B * L.W_cap);
   long long nn = 0;
   for (int k = 0; k < d; ++k) nn += (long long)g->n[k] * g->n[k];
-  L.opmats_floats = 2 * nn + (long long)d * d * (smax * smax + 2) * nmax;
+  // shear tables, per-mode matrices, and per-mode FFT tables (spectrum,
+  // twiddles, cloud-in-cell gather: 2M + M + 6N words, 8-byte aligned)
+  L.opmats_floats = 2 * nn + (long long)d * d * (smax * smax + 2) * nmax +
+                    (long long)d * (3 * fft_len(nmax) + 6 * nmax + 8);
+  L.fft_off = a.take<int>((size_t)B + 1);
   L.opmats = a.take<float>(L.opmats_floats);
   L.zbuf = a.take<float>((size_t)B * kMaxComps);
   L.prof_flops = a.take<double>(kPClasses);
@@ -191,6 +216,8 @@ struct ttgbf_ctx {
   std::vector<double> lo, hi, dx, axes;
   std::vector<int> axoff;
   int rank_cap = 0, smax = 0, capr = 0;
+  int precision = TTGBF_PRECISION_FP32;
+  int slice_blocks = kTsqrSliceBlocks, svd_threads = 512;
   double eps = 0.0, delta = 1.0;
   cudaStream_t st = nullptr;
   Layout L{};
@@ -231,6 +258,13 @@ struct ttgbf_ctx {
   std::vector<long long> mat_off;  // per mode: fused (or conv) matrix offset
   std::vector<long long> scale_off;  // per mode: CIC matrix (only used when L != I), -1 if none
   bool fuse = true;
+  // the Gaussian kernel of mode k as an FFT convolution (opts.conv): the
+  // mode's tables in the operator area (offsets in words, -1: none)
+  int conv_mode = TTGBF_CONV_AUTO;
+  bool mode_fft[kMaxD] = {};
+  long long fft_khat[kMaxD] = {}, fft_tw[kMaxD] = {}, fft_gsrc[kMaxD] = {}, fft_gw[kMaxD] = {};
+  int fft_M[kMaxD] = {};
+  int* fft_off = nullptr;
   bool poisoned = false;
   bool expanded = false;  // ranks may exceed rank_cap (after an unrounded shear or import)
   // virt_S[k] > 0: core k is a middle core of the shear block being rounded
@@ -340,24 +374,34 @@ void debug_stage_report(ttgbf_ctx* c, int mode, int k, int ka, int kb) {
 }
 
 // One stage of the rounding sweep: R factor, SVD, rank choice, factor application.
+// With float64 precision the truncating stages (left, split) form R and its
+// SVD in float64 (one TSQR CTA per SM: its shared memory holds a float64 R).
 void stage(ttgbf_ctx* c, int mode, int k, int first) {
   const int B = c->B;
   const float* src = (mode == kStageSplit) ? c->W : curp(c, k);
+  const bool fp64 = c->precision == TTGBF_PRECISION_FP64 && mode != kStageRight;
   {
     Prof p(c, kPPlan, 1);
+    const int per_sm = fp64 ? 1 : 2;
     launch_plan_stage(c->st, B, mode, k, c->geom, c->ranks, src, c->W, c->L.W_cap, c->n[0],
                       c->d > 1 ? c->n[1] : 1, c->tw, c->stack[0], c->stack[1], c->L.stack_cap,
-                      std::max(1, (int)(2 * c->sms * c->slot_share)));
+                      std::max(1, (int)(per_sm * c->sms * c->slot_share)), fp64 ? 2 : 1,
+                      c->slice_blocks);
   }
   {
     Prof p(c, kPTsqr, 1);
-    launch_tsqr(c->st, c->tw, B, c->sms, flops_of(c, kPTsqr));
+    if (fp64) launch_tsqr64(c->st, c->tw, B, c->sms, flops_of(c, kPTsqr));
+    else launch_tsqr(c->st, c->tw, B, c->sms, flops_of(c, kPTsqr));
   }
   float* core0_alt = (mode == kStageSplit) ? altp(c, 0) : nullptr;
   {
     Prof p(c, kPSvd, 1);
-    launch_svd(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1, c->P2,
-                  core0_alt, c->L.core_cap[0], flops_of(c, kPSvd));
+    if (fp64)
+      launch_svd64(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1,
+                   c->P2, core0_alt, c->L.core_cap[0], flops_of(c, kPSvd));
+    else
+      launch_svd(c->st, c->tw, B, mode, c->rank_cap, c->eps, c->d, first, round_state(c), c->P1,
+                 c->P2, core0_alt, c->L.core_cap[0], flops_of(c, kPSvd), c->svd_threads);
   }
   int ka, kb, ndesc = 2 * B, vS = 0;
   if (mode == kStageRight) {
@@ -468,6 +512,32 @@ void mode_apply(ttgbf_ctx* c, int k, const float* M) {
   if (!(c->canon && c->center == k)) c->canon = false;
 }
 
+// Mode k's Gaussian kernel as batched FFT convolutions of the core's fibres,
+// from the tables fft_tables put in the operator area.
+void mode_conv_fft(ttgbf_ctx* c, int k) {
+  FftMode md{};
+  md.M = c->fft_M[k];
+  md.khat = reinterpret_cast<const float2*>(c->opmats + c->fft_khat[k]);
+  md.tw = reinterpret_cast<const float2*>(c->opmats + c->fft_tw[k]);
+  md.gsrc = c->fft_gsrc[k] >= 0 ? reinterpret_cast<const int*>(c->opmats + c->fft_gsrc[k]) : nullptr;
+  md.gw = c->fft_gw[k] >= 0 ? c->opmats + c->fft_gw[k] : nullptr;
+  {
+    Prof p(c, kPFft, 2);
+    launch_conv_fft(c->st, c->B, k, c->geom, c->ranks, c->fft_off, curp(c, k), altp(c, k), md,
+                    c->sms * 2, flops_of(c, kPFft));
+  }
+  c->cur[k] ^= 1;
+  if (!(c->canon && c->center == k)) c->canon = false;
+}
+
+bool conv_uses_fft(const ttgbf_ctx* c, int m) {
+  const int N = c->n[m];
+  if (N < 2 || fft_len(N) > kMaxFftM) return false;
+  if (c->conv_mode == TTGBF_CONV_FFT) return true;
+  if (c->conv_mode == TTGBF_CONV_DENSE) return false;
+  return N >= 256;
+}
+
 double hatf(double t) { return std::max(0.0, 1.0 - std::fabs(t)); }
 
 // Shear x_m += a x_n: integer shift range and hat-weight table.
@@ -507,6 +577,79 @@ void conv_matrix(ttgbf_ctx* c, int m, double q, std::vector<double>* K) {
       const double t = (double)(j - i) * D;
       (*K)[(size_t)j * N + i] = norm * std::exp(-0.5 * t * t / q);
     }
+}
+
+// FFT tables of mode m's kernel with variance q, appended to host at *at
+// (4-byte words, 8-byte aligned): the spectrum of kappa zero-padded to M
+// (float64 DFT, divided by M so the inverse transform needs no scaling),
+// the twiddles exp(-2 pi i t / M), and, when lam != 1, the cloud-in-cell
+// gather of the scaling x_m <- lam x_m (kCicTaps sources per target).
+// Returns false (and appends nothing) when the scaling needs more taps.
+bool fft_tables(ttgbf_ctx* c, int m, double q, double lam, std::vector<float>* host, long long* at) {
+  const int N = c->n[m];
+  const int M = fft_len(N);
+  const double D = c->dx[m];
+  std::vector<int> gsrc;
+  std::vector<float> gw;
+  if (lam != 1.0) {
+    gsrc.assign((size_t)N * kCicTaps, -1);
+    gw.assign((size_t)N * kCicTaps, 0.f);
+    std::vector<int> cnt(N, 0);
+    for (int i = 0; i < N; ++i) {
+      const double u = (lam * c->axes[c->axoff[m] + i] - c->lo[m]) / D - 0.5;
+      const int j0 = (int)std::floor(u);
+      for (int j = j0; j <= j0 + 1; ++j) {
+        const double w = hatf(j - u);
+        if (j < 0 || j >= N || w == 0.0) continue;
+        if (cnt[j] == kCicTaps) return false;
+        gsrc[(size_t)j * kCicTaps + cnt[j]] = i;
+        gw[(size_t)j * kCicTaps + cnt[j]] = (float)w;
+        ++cnt[j];
+      }
+    }
+  }
+  long long a = (*at + 1) & ~1LL;
+  const long long need = 2LL * M + M + (lam != 1.0 ? 2LL * N * kCicTaps : 0);
+  if (a + need > (long long)host->size()) return false;
+  // spectrum of kappa(t), t = -(N-1)..N-1, placed at t mod M
+  const double norm = D / std::sqrt(2.0 * M_PI * q);
+  std::vector<double> kap(M, 0.0);
+  for (int t = -(N - 1); t <= N - 1; ++t) {
+    const double x = t * D;
+    kap[(t % M + M) % M] = norm * std::exp(-0.5 * x * x / q);
+  }
+  c->fft_khat[m] = a;
+  for (int u = 0; u < M; ++u) {
+    double re = 0.0, im = 0.0;
+    for (int t = 0; t < M; ++t) {
+      if (kap[t] == 0.0) continue;
+      const double ph = -2.0 * M_PI * (double)(((long long)u * t) % M) / M;
+      re += kap[t] * std::cos(ph);
+      im += kap[t] * std::sin(ph);
+    }
+    (*host)[a + 2 * u] = (float)(re / M);
+    (*host)[a + 2 * u + 1] = (float)(im / M);
+  }
+  a += 2LL * M;
+  c->fft_tw[m] = a;
+  for (int t = 0; t < M / 2; ++t) {
+    const double ph = -2.0 * M_PI * t / M;
+    (*host)[a + 2 * t] = (float)std::cos(ph);
+    (*host)[a + 2 * t + 1] = (float)std::sin(ph);
+  }
+  a += M;
+  c->fft_gsrc[m] = c->fft_gw[m] = -1;
+  if (lam != 1.0) {
+    c->fft_gsrc[m] = a;
+    std::memcpy(host->data() + a, gsrc.data(), sizeof(int) * gsrc.size());
+    a += (long long)gsrc.size();
+    c->fft_gw[m] = a;
+    std::memcpy(host->data() + a, gw.data(), sizeof(float) * gw.size());
+    a += (long long)gw.size();
+  }
+  c->fft_M[m] = M;
+  *at = a;
+  return true;
 }
 
 int ldu(const double* F, int d, std::vector<double>* Lm, std::vector<double>* D, std::vector<double>* U) {
@@ -586,9 +729,27 @@ int prepare_predict(ttgbf_ctx* c, const double* F, const double* Q) {
   std::vector<long long> moff(d), soff(d, -1);
   for (int m = 0; m < d; ++m) {
     std::vector<double> K, Wc;
-    conv_matrix(c, m, Q[(size_t)m * d + m], &K);
     const int N = c->n[m];
     const bool has_scale = D[m] != 1.0;
+    c->mode_fft[m] = false;
+    if (conv_uses_fft(c, m)) {
+      // the kernel by FFT convolution; a scaling that precedes it on this
+      // mode (L = I) is its load-time gather, otherwise its own dense pass
+      long long at2 = at;
+      if (fft_tables(c, m, Q[(size_t)m * d + m], (has_scale && !lower) ? D[m] : 1.0, &host, &at2)) {
+        c->mode_fft[m] = true;
+        at = at2;
+        moff[m] = -1;
+        if (has_scale && lower) {
+          cic_matrix(c, m, D[m], &Wc);
+          soff[m] = at;
+          for (size_t t = 0; t < Wc.size(); ++t) host[at + t] = (float)Wc[t];
+          at += (long long)Wc.size();
+        }
+        continue;
+      }
+    }
+    conv_matrix(c, m, Q[(size_t)m * d + m], &K);
     if (has_scale) cic_matrix(c, m, D[m], &Wc);
     if (has_scale && !lower) {
       // fused operator K_m W_m (the scaling precedes the kernel on this mode)
@@ -887,8 +1048,9 @@ const char* ttgbf_strerror(int code) {
   }
 }
 
-// Number of parts of a batch: one per 12 filters, at most 8 (environment
-// TTGBF_PARTS overrides, 1..8).  Measured on 100 filters of the 128^4
+// Number of parts of a batch: opts.parts when set, else one per 12 filters,
+// at most 8 (environment TTGBF_PARTS overrides the default, 1..8).
+// Measured on 100 filters of the 128^4
 // workload: 1 part 32.8 ms per step, 2 parts 30.9, 4 parts 28.2, 8 parts
 // 27.4.
 static int choose_parts(const ttgbf_opts* opts) {
@@ -897,6 +1059,7 @@ static int choose_parts(const ttgbf_opts* opts) {
     const int v = std::atoi(e);
     if (v >= 1 && v <= 8) np = v;
   }
+  if (opts->parts > 0) np = opts->parts;
   return std::max(1, std::min(np, (int)opts->batch));
 }
 
@@ -933,6 +1096,8 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
     set_kernel_attributes();
     set_ttops_attributes();
     set_tsqr_attributes();
+    set_rsvd64_attributes();
+    set_fft_attributes();
   });
   ttgbf_ctx* c = new (std::nothrow) ttgbf_ctx();
   if (!c) return TTGBF_ENOMEM;
@@ -941,6 +1106,10 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   c->rank_cap = opts->rank_cap;
   c->smax = opts->max_shift_span > 0 ? opts->max_shift_span : 10;
   c->capr = c->rank_cap * c->smax;
+  c->precision = opts->precision;
+  c->conv_mode = opts->conv;
+  c->slice_blocks = opts->tsqr_slice_blocks > 0 ? opts->tsqr_slice_blocks : kTsqrSliceBlocks;
+  c->svd_threads = opts->svd_threads > 0 ? opts->svd_threads : 512;
   c->eps = opts->eps;
   c->st = (cudaStream_t)opts->stream;
   {
@@ -1031,6 +1200,7 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   c->opmats = (float*)(b + L.opmats);
   c->zbuf = (float*)(b + L.zbuf);
   c->prof_flops = (double*)(b + L.prof_flops);
+  c->fft_off = (int*)(b + L.fft_off);
   if (cudaMallocHost(&c->stage_ops, sizeof(float) * L.opmats_floats) != cudaSuccess ||
       cudaMallocHost(&c->stage_z, sizeof(float) * (size_t)c->B * kMaxComps) != cudaSuccess ||
       cudaMallocHost(&c->stage_est, sizeof(double) * (size_t)c->B * (d + d * d + 2)) != cudaSuccess ||
@@ -1226,7 +1396,10 @@ void predict_op(ttgbf_ctx* c, size_t i) {
   }
 }
 
-void predict_mode(ttgbf_ctx* c, int k) { mode_apply(c, k, c->opmats + c->mat_off[k]); }
+void predict_mode(ttgbf_ctx* c, int k) {
+  if (c->mode_fft[k]) mode_conv_fft(c, k);
+  else mode_apply(c, k, c->opmats + c->mat_off[k]);
+}
 
 int predict_end(ttgbf_ctx* c) {
   enqueue_normalise(c, c->mass_pred);
@@ -1627,17 +1800,31 @@ int ttgbf_convolve(ttgbf_ctx* c, const double* q) {
   if (rc) return rc;
   if (!q) return TTGBF_EINVAL;
   if (!finite_all(q, c->d)) return TTGBF_ENONFINITE;
-  std::vector<std::vector<double>> mats(c->d);
-  for (int k = 0; k < c->d; ++k) {
+  for (int k = 0; k < c->d; ++k)
     if (!(q[k] > 0.0)) return TTGBF_EINVAL;
-    conv_matrix(c, k, q[k], &mats[k]);
-  }
-  rc = upload_mats(c, mats);
-  if (rc) return rc;
-  size_t at = 0;
+  // per mode: FFT tables or the dense Toeplitz matrix (opts.conv)
+  std::vector<float> host((size_t)c->L.opmats_floats, 0.f);
+  std::vector<long long> off(c->d, -1);
+  long long at = 0;
   for (int k = 0; k < c->d; ++k) {
-    mode_apply(c, k, c->opmats + at);
-    at += mats[k].size();
+    c->mode_fft[k] = conv_uses_fft(c, k) && fft_tables(c, k, q[k], 1.0, &host, &at);
+    if (c->mode_fft[k]) continue;
+    std::vector<double> K;
+    conv_matrix(c, k, q[k], &K);
+    if (at + (long long)K.size() > c->L.opmats_floats) return TTGBF_ECAPACITY;
+    off[k] = at;
+    for (size_t t = 0; t < K.size(); ++t) host[at + t] = (float)K[t];
+    at += (long long)K.size();
+  }
+  wait_stage(c->ev_ops, &c->ev_ops_used);
+  std::memcpy(c->stage_ops, host.data(), sizeof(float) * at);
+  cudaMemcpyAsync(c->opmats, c->stage_ops, sizeof(float) * at, cudaMemcpyHostToDevice, c->st);
+  cudaEventRecord(c->ev_ops, c->st);
+  c->ev_ops_used = true;
+  c->lastF.clear();  // the operator area no longer holds a predict's operators
+  for (int k = 0; k < c->d; ++k) {
+    if (c->mode_fft[k]) mode_conv_fft(c, k);
+    else mode_apply(c, k, c->opmats + off[k]);
   }
   return check(c);
 }
@@ -1721,6 +1908,487 @@ int ttgbf_profile_read(ttgbf_ctx* c, ttgbf_kernel_prof* out, int32_t cap, int32_
 }
 
 uint64_t ttgbf_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"
+
+// ================================================================ groups
+struct ttgbf_group {
+  cudaStream_t st = nullptr;
+  std::vector<ttgbf_ctx*> ctxs;   // as given
+  std::vector<ttgbf_ctx*> leaves;  // every context's parts (or the context itself)
+  std::vector<int> owner;          // leaf -> index in ctxs
+  std::vector<int> base;           // leaf -> its first filter within the owner
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;  // per leaf
+  // timing of the last ttgbf_group_step: its start on the group's stream and
+  // the end of every leaf's work (not recorded into graphs)
+  cudaEvent_t ev_t0 = nullptr;
+  std::vector<cudaEvent_t> ev_tend;
+  bool timed = false, capturing = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long graph_kernels = 0;
+};
+
+namespace {
+
+int group_fail(ttgbf_group* g) {
+  for (ttgbf_ctx* c : g->leaves) c->poisoned = true;
+  return TTGBF_ECUDA;
+}
+
+// Host-side validation of one context's step arguments (nothing enqueued).
+int group_validate(ttgbf_ctx* c, const ttgbf_group_step_args& a) {
+  if (!a.F || !a.Q || !a.h || !a.R || !a.z_dev) return TTGBF_EINVAL;
+  const int d = c->d;
+  if (!finite_all(a.F, (size_t)d * d) || !finite_all(a.Q, (size_t)d * d)) return TTGBF_ENONFINITE;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      if (i != j && a.Q[(size_t)i * d + j] != 0.0) return TTGBF_EINVAL;
+      if (i == j && !(a.Q[(size_t)i * d + j] > 0.0)) return TTGBF_EINVAL;
+    }
+  ttgbf_ctx* leaf = c->parts.empty() ? c : c->parts[0];
+  int two = -1;
+  return validate_meas(leaf, a.h, a.R, &two);
+}
+
+// Enqueue one step of every leaf, interleaved operation by operation.
+// step_off: offset (in steps) into the horizon arrays of args.
+int group_enqueue(ttgbf_group* g, const ttgbf_group_step_args* args, long long t) {
+  const size_t nl = g->leaves.size();
+  if (!g->capturing) cudaEventRecord(g->ev_t0, g->st);
+  cudaEventRecord(g->ev_fork, g->st);
+  for (ttgbf_ctx* q : g->leaves) cudaStreamWaitEvent(q->st, g->ev_fork, 0);
+  // predict
+  size_t nops = 0;
+  for (size_t l = 0; l < nl; ++l) {
+    const ttgbf_group_step_args& a = args[g->owner[l]];
+    const int rc = predict_begin(g->leaves[l], a.F, a.Q);
+    if (rc) return rc;
+    nops = std::max(nops, g->leaves[l]->ops.size());
+  }
+  for (size_t i = 0; i < nops; ++i)
+    for (ttgbf_ctx* q : g->leaves)
+      if (i < q->ops.size()) predict_op(q, i);
+  int dmax = 0;
+  for (ttgbf_ctx* q : g->leaves) dmax = std::max(dmax, q->d);
+  for (int k = 0; k < dmax; ++k)
+    for (ttgbf_ctx* q : g->leaves)
+      if (k < q->d) predict_mode(q, k);
+  for (ttgbf_ctx* q : g->leaves) predict_end(q);
+  // update (device measurements of the step)
+  std::vector<EnqueueOps> lists(nl);
+  size_t nmax = 0;
+  for (size_t l = 0; l < nl; ++l) {
+    ttgbf_ctx* q = g->leaves[l];
+    const ttgbf_group_step_args& a = args[g->owner[l]];
+    const ttgbf_ctx* own = g->ctxs[g->owner[l]];
+    const long long b = a.h->b;
+    const float* z = a.z_dev + (t * own->B + g->base[l]) * b;
+    const float* zq = nullptr;
+    int two = -1;
+    const int rc = update_prepare(q, a.h, a.R, nullptr, z, &zq, &two);
+    if (rc) return rc;
+    update_ops(q, a.h, a.R, zq, (int)b, two, &lists[l]);
+    nmax = std::max(nmax, lists[l].size());
+  }
+  for (size_t i = 0; i < nmax; ++i)
+    for (size_t l = 0; l < nl; ++l)
+      if (i < lists[l].size()) lists[l][i]();
+  // estimate into the caller's device arrays
+  for (size_t l = 0; l < nl; ++l) {
+    ttgbf_ctx* q = g->leaves[l];
+    const ttgbf_group_step_args& a = args[g->owner[l]];
+    const ttgbf_ctx* own = g->ctxs[g->owner[l]];
+    const long long B = q->B, d = q->d;
+    const long long f0 = t * own->B + g->base[l];
+    const int rc = estimate_common(q);
+    if (rc) return rc;
+    if (a.mean) cudaMemcpyAsync(a.mean + f0 * d, q->mean, sizeof(double) * B * d, cudaMemcpyDeviceToDevice, q->st);
+    if (a.cov)
+      cudaMemcpyAsync(a.cov + f0 * d * d, q->cov, sizeof(double) * B * d * d, cudaMemcpyDeviceToDevice, q->st);
+    if (a.log_c) cudaMemcpyAsync(a.log_c + f0, q->log_c, sizeof(double) * B, cudaMemcpyDeviceToDevice, q->st);
+    if (a.log_lik)
+      cudaMemcpyAsync(a.log_lik + f0, q->log_lik, sizeof(double) * B, cudaMemcpyDeviceToDevice, q->st);
+  }
+  for (size_t l = 0; l < nl; ++l) {
+    if (!g->capturing) cudaEventRecord(g->ev_tend[l], g->leaves[l]->st);
+    cudaEventRecord(g->ev_join[l], g->leaves[l]->st);
+    cudaStreamWaitEvent(g->st, g->ev_join[l], 0);
+  }
+  g->timed = !g->capturing;
+  for (ttgbf_ctx* q : g->leaves) {
+    const int rc = check(q);
+    if (rc) return rc;
+  }
+  return TTGBF_OK;
+}
+
+int group_guard(ttgbf_group* g, const ttgbf_group_step_args* args) {
+  if (!g || !args) return TTGBF_EINVAL;
+  for (ttgbf_ctx* q : g->leaves)
+    if (q->poisoned) return TTGBF_EPOISONED;
+  for (size_t i = 0; i < g->ctxs.size(); ++i) {
+    const int rc = group_validate(g->ctxs[i], args[i]);
+    if (rc) return rc;
+  }
+  return TTGBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ttgbf_group_create(ttgbf_group** out, ttgbf_ctx* const* ctxs, int32_t n, void* stream) {
+  if (!out || !ctxs || n < 1) return TTGBF_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return TTGBF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return TTGBF_EINVAL;
+  }
+  ttgbf_group* g = new (std::nothrow) ttgbf_group();
+  if (!g) return TTGBF_ENOMEM;
+  g->st = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) {
+    ttgbf_ctx* c = ctxs[i];
+    g->ctxs.push_back(c);
+    if (c->parts.empty()) {
+      g->leaves.push_back(c);
+      g->owner.push_back(i);
+      g->base.push_back(0);
+    } else {
+      for (size_t p = 0; p < c->parts.size(); ++p) {
+        g->leaves.push_back(c->parts[p]);
+        g->owner.push_back(i);
+        g->base.push_back(c->part_base[p]);
+      }
+    }
+  }
+  if (cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return TTGBF_ENOMEM;
+  }
+  if (cudaEventCreate(&g->ev_t0) != cudaSuccess) {
+    cudaGetLastError();
+    ttgbf_group_free(g);
+    return TTGBF_ENOMEM;
+  }
+  for (size_t l = 0; l < g->leaves.size(); ++l) {
+    cudaEvent_t e = nullptr, et = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&et) != cudaSuccess) {
+      cudaGetLastError();
+      if (e) cudaEventDestroy(e);
+      ttgbf_group_free(g);
+      return TTGBF_ENOMEM;
+    }
+    g->ev_join.push_back(e);
+    g->ev_tend.push_back(et);
+  }
+  *out = g;
+  return TTGBF_OK;
+}
+
+int ttgbf_group_step(ttgbf_group* g, const ttgbf_group_step_args* args) {
+  ApiRange range("ttgbf_group_step");
+  const int rc = group_guard(g, args);
+  if (rc) return rc;
+  return group_enqueue(g, args, 0);
+}
+
+// The host-side state a recorded step sequence depends on: which ping-pong
+// buffer holds each core, the canonical form, unexpanded middle cores.
+struct LeafState {
+  int cur[kMaxD];
+  int virt_S[kMaxD];
+  bool canon, expanded;
+  int center;
+  bool operator==(const LeafState& o) const {
+    return std::equal(cur, cur + kMaxD, o.cur) && std::equal(virt_S, virt_S + kMaxD, o.virt_S) &&
+           canon == o.canon && expanded == o.expanded && center == o.center;
+  }
+};
+
+static LeafState leaf_state(const ttgbf_ctx* c) {
+  LeafState s{};
+  std::copy(c->cur, c->cur + kMaxD, s.cur);
+  std::copy(c->virt_S, c->virt_S + kMaxD, s.virt_S);
+  s.canon = c->canon;
+  s.expanded = c->expanded;
+  s.center = c->center;
+  return s;
+}
+
+static void group_drop_graph(ttgbf_group* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->exec = nullptr;
+  g->graph = nullptr;
+  g->graph_kernels = 0;
+}
+
+int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32_t steps) {
+  ApiRange range("ttgbf_group_capture");
+  int rc = group_guard(g, args);
+  if (rc) return rc;
+  if (steps < 1) return TTGBF_EINVAL;
+  for (ttgbf_ctx* q : g->leaves)
+    if (q->prof) return TTGBF_EINVAL;  // event timing cannot be replayed
+  // operators of F, Q prepared on the host (and uploaded) before recording
+  for (size_t l = 0; l < g->leaves.size(); ++l) {
+    ttgbf_ctx* q = g->leaves[l];
+    const ttgbf_group_step_args& a = args[g->owner[l]];
+    const int d = q->d;
+    const bool same = q->lastF.size() == (size_t)d * d && std::equal(q->lastF.begin(), q->lastF.end(), a.F) &&
+                      std::equal(q->lastQ.begin(), q->lastQ.end(), a.Q);
+    if (!same) {
+      rc = prepare_predict(q, a.F, a.Q);
+      if (rc) return rc;
+    }
+  }
+  for (ttgbf_ctx* q : g->leaves)
+    if (cudaStreamSynchronize(q->st) != cudaSuccess) return group_fail(g);
+  if (cudaStreamSynchronize(g->st) != cudaSuccess) return group_fail(g);
+  group_drop_graph(g);
+  std::vector<LeafState> before;
+  for (ttgbf_ctx* q : g->leaves) before.push_back(leaf_state(q));
+  const unsigned long long l0 = g_launches.load();
+  if (cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return group_fail(g);
+  }
+  g->capturing = true;
+  for (int t = 0; t < steps && rc == TTGBF_OK; ++t) rc = group_enqueue(g, args, t);
+  g->capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(g->st, &graph);
+  const unsigned long long recorded = g_launches.load() - l0;
+  g_launches.fetch_sub(recorded);  // recorded, not run
+  bool periodic = true;
+  for (size_t l = 0; l < g->leaves.size(); ++l) {
+    periodic = periodic && leaf_state(g->leaves[l]) == before[l];
+    // nothing ran: the contexts are where they were
+    ttgbf_ctx* q = g->leaves[l];
+    std::copy(before[l].cur, before[l].cur + kMaxD, q->cur);
+    std::copy(before[l].virt_S, before[l].virt_S + kMaxD, q->virt_S);
+    q->canon = before[l].canon;
+    q->expanded = before[l].expanded;
+    q->center = before[l].center;
+  }
+  if (e != cudaSuccess || rc != TTGBF_OK) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return rc != TTGBF_OK ? rc : group_fail(g);
+  }
+  if (!periodic) {
+    // a relaunch would start from buffers or a canonical form the recording
+    // did not leave: step once before recording, record an even number
+    cudaGraphDestroy(graph);
+    return TTGBF_EINVAL;
+  }
+  if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return group_fail(g);
+  }
+  g->graph = graph;
+  g->graph_kernels = recorded;
+  return TTGBF_OK;
+}
+
+int ttgbf_group_launch(ttgbf_group* g) {
+  if (!g || !g->exec) return TTGBF_EINVAL;
+  for (ttgbf_ctx* q : g->leaves)
+    if (q->poisoned) return TTGBF_EPOISONED;
+  if (cudaGraphLaunch(g->exec, g->st) != cudaSuccess) {
+    cudaGetLastError();
+    return group_fail(g);
+  }
+  g_launches.fetch_add(g->graph_kernels);
+  return TTGBF_OK;
+}
+
+uint64_t ttgbf_group_graph_kernels(const ttgbf_group* g) { return g ? g->graph_kernels : 0; }
+
+int ttgbf_group_times(ttgbf_group* g, float* ms) {
+  if (!g || !ms) return TTGBF_EINVAL;
+  if (!g->timed) return TTGBF_EINVAL;
+  for (size_t i = 0; i < g->ctxs.size(); ++i) ms[i] = 0.f;
+  for (size_t l = 0; l < g->leaves.size(); ++l) {
+    float e = 0.f;
+    if (cudaEventSynchronize(g->ev_tend[l]) != cudaSuccess ||
+        cudaEventElapsedTime(&e, g->ev_t0, g->ev_tend[l]) != cudaSuccess) {
+      cudaGetLastError();
+      return group_fail(g);
+    }
+    ms[g->owner[l]] = std::max(ms[g->owner[l]], e);
+  }
+  return TTGBF_OK;
+}
+
+int ttgbf_group_free(ttgbf_group* g) {
+  if (!g) return TTGBF_OK;
+  if (g->st) cudaStreamSynchronize(g->st);
+  group_drop_graph(g);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_t0) cudaEventDestroy(g->ev_t0);
+  for (cudaEvent_t e : g->ev_join) cudaEventDestroy(e);
+  for (cudaEvent_t e : g->ev_tend) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete g;
+  return TTGBF_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ autotuning
+namespace {
+
+// Cache key of a batch shape: grid, batch, rank cap, span, precision, conv,
+// the span of every elementary shear of F on this grid (which sets the rank
+// expansions), and the GPU's name.
+std::string tune_key(const ttgbf_grid* g, const ttgbf_opts* o, const double* F) {
+  const int d = g->d;
+  std::string k = "d=" + std::to_string(d) + ";n=";
+  for (int m = 0; m < d; ++m) k += std::to_string(g->n[m]) + (m + 1 < d ? "," : "");
+  k += ";batch=" + std::to_string(o->batch) + ";cap=" + std::to_string(o->rank_cap) +
+       ";span=" + std::to_string(o->max_shift_span > 0 ? o->max_shift_span : 10) +
+       ";prec=" + std::to_string(o->precision) + ";conv=" + std::to_string(o->conv) + ";shears=";
+  std::vector<double> Lm, D, U;
+  if (ldu(F, d, &Lm, &D, &U) == TTGBF_OK) {
+    for (int m = 0; m < d; ++m)
+      for (int n = 0; n < d; ++n) {
+        const double a = m < n ? U[(size_t)m * d + n] : (m > n ? Lm[(size_t)m * d + n] : 0.0);
+        if (a == 0.0) continue;
+        const double dm = (g->hi[m] - g->lo[m]) / g->n[m], dn = (g->hi[n] - g->lo[n]) / g->n[n];
+        int lo = 1 << 30, hi = -(1 << 30);
+        for (int i = 0; i < g->n[n]; ++i) {
+          const int f = (int)std::floor(a * (g->lo[n] + (i + 0.5) * dn) / dm);
+          lo = std::min(lo, f);
+          hi = std::max(hi, f);
+        }
+        k += std::to_string(m) + "." + std::to_string(n) + ":" + std::to_string(hi - lo + 2) + ",";
+      }
+  }
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+    std::string name(prop.name);
+    for (char& ch : name)
+      if (ch == ' ' || ch == '\t') ch = '_';
+    k += ";gpu=" + name;
+  }
+  cudaGetLastError();
+  return k;
+}
+
+// ms per predictive step of one candidate configuration (its own context,
+// stream and workspace); a negative code when it cannot be created.
+int tune_time(const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf_opts* o, const double* F,
+              const double* Q, int steps, double* ms) {
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return TTGBF_ECUDA;
+  }
+  ttgbf_opts oo = *o;
+  oo.stream = st;
+  oo.workspace = nullptr;
+  oo.workspace_bytes = 0;
+  ttgbf_ctx* c = nullptr;
+  int rc = ttgbf_init(&c, grid, prior, &oo);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (rc == TTGBF_OK) rc = ttgbf_predict(c, F, Q);  // untimed: operators, first rounding
+  if (rc == TTGBF_OK) {
+    if (split(c)) join_parts(c);
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    if (split(c)) fork_parts(c);
+    for (int t = 0; t < steps && rc == TTGBF_OK; ++t) rc = ttgbf_predict(c, F, Q);
+    if (split(c)) join_parts(c);
+    cudaEventRecord(b, st);
+    float e = 0.f;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&e, a, b) != cudaSuccess) {
+      cudaGetLastError();
+      if (rc == TTGBF_OK) rc = TTGBF_ECUDA;
+    }
+    *ms = (double)e / steps;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (c) ttgbf_free(c);
+  cudaStreamDestroy(st);
+  cudaGetLastError();
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ttgbf_autotune(const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf_opts* base,
+                   const double* F, const double* Q, int32_t steps, const char* cache_path,
+                   ttgbf_opts* best, double* best_ms) {
+  if (!grid || !prior || !base || !F || !Q || !best || !best_ms || steps < 1) return TTGBF_EINVAL;
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  rc = validate_opts(base);
+  if (rc) return rc;
+  const std::string key = tune_key(grid, base, F);
+  if (cache_path) {
+    if (FILE* fh = std::fopen(cache_path, "r")) {
+      char line[2048];
+      while (std::fgets(line, sizeof(line), fh)) {
+        char* tab = std::strchr(line, '\t');
+        if (!tab || std::string(line, tab - line) != key) continue;
+        int parts = 0, sb = 0, sv = 0;
+        double ms = 0.0;
+        if (std::sscanf(tab + 1, "%d %d %d %lf", &parts, &sb, &sv, &ms) == 4) {
+          *best = *base;
+          best->parts = parts;
+          best->tsqr_slice_blocks = sb;
+          best->svd_threads = sv;
+          *best_ms = ms;
+          std::fclose(fh);
+          return TTGBF_OK;
+        }
+      }
+      std::fclose(fh);
+    }
+  }
+  double bms = 1e300;
+  ttgbf_opts bo = *base;
+  int last = TTGBF_EINVAL;
+  for (int parts : {1, 2, 4, 8}) {
+    if (parts > base->batch) continue;
+    for (int sb : {4, 8, 16})
+      for (int sv : {512, 1024}) {
+        ttgbf_opts o = *base;
+        o.parts = parts;
+        o.tsqr_slice_blocks = sb;
+        o.svd_threads = sv;
+        double ms = 0.0;
+        last = tune_time(grid, prior, &o, F, Q, steps, &ms);
+        if (last == TTGBF_OK && ms < bms) {
+          bms = ms;
+          bo = o;
+        }
+      }
+  }
+  if (bms == 1e300) return last;
+  *best = bo;
+  *best_ms = bms;
+  if (cache_path) {
+    if (FILE* fh = std::fopen(cache_path, "a")) {
+      std::fprintf(fh, "%s\t%d %d %d %.6f\n", key.c_str(), bo.parts, bo.tsqr_slice_blocks, bo.svd_threads,
+                   bms);
+      std::fclose(fh);
+    }
+  }
+  return TTGBF_OK;
+}
 
 }  // extern "C"
 

@@ -54,10 +54,11 @@ struct TsqrWork {
   int* counter;       // [B] slices finished (reset by the plan kernel)
 };
 
-// Rows per slice of an n-column problem: eight register blocks.
-__host__ __device__ inline long long tsqr_slice_rows(int n) {
-  (void)n;
-  return 8LL * kTsqrTileRows;
+// Rows per slice of a TSQR problem: `blocks` register blocks of 128 rows
+// (8 unless a context's options say otherwise).
+constexpr int kTsqrSliceBlocks = 8;
+__host__ __device__ inline long long tsqr_slice_rows(int blocks) {
+  return (long long)blocks * kTsqrTileRows;
 }
 
 // Row-major GEMM C (m x n) = A (m x k) * B (k x n).  `shape` (the tile
@@ -96,14 +97,18 @@ struct TTGeom {
 
 // ------------------------------------------------------------ launchers
 // linalg.cu
+// elem: 4-byte words per stack element (1: float32 slice factors, 2: float64);
+// slice_blocks: 128-row register blocks per TSQR slice
 void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
-                       TsqrWork w, float* stack0, float* stack1, long long stack_cap, int slots);
+                       TsqrWork w, float* stack0, float* stack1, long long stack_cap, int slots,
+                       int elem, int slice_blocks);
 // tsqr.cu
 void launch_tsqr(cudaStream_t st, TsqrWork w, int B, int grid, double* flops);
+// left_threads: CTA width of the truncating left-sweep stages (512 or 1024)
 void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
-                   long long core0_cap, double* flops);
+                   long long core0_cap, double* flops, int left_threads);
 void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, int* ranks,
                             const int* newrank, const float* cur_a, float* alt_a,
                             const float* cur_b, float* alt_b, const float* P1, const float* P2,
@@ -113,6 +118,26 @@ void launch_gemm(cudaStream_t st, GemmWork gw, int grid, double* flops);
 // Tile prefix for descriptors already written to gw.desc (ndesc entries).
 void launch_scan_tiles(cudaStream_t st, GemmWork gw);
 
+// fftconv.cu: the Gaussian kernel of one mode as batched FFT convolutions of
+// the fibres of core k (length N, zero padded to M = 2^m >= 2N - 1), with an
+// optional cloud-in-cell gather (kCicTaps sources per target cell) on load.
+constexpr int kCicTaps = 3;
+constexpr int kMaxFftM = 1024;  // N <= 512
+struct FftMode {
+  int M;
+  const float2* khat;  // [M] FFT of the zero-padded kernel, divided by M
+  const float2* tw;    // [M / 2] exp(-2 pi i t / M)
+  const int* gsrc;     // [N][kCicTaps] source cells (-1: none), or nullptr
+  const float* gw;     // [N][kCicTaps] cloud-in-cell weights
+};
+void launch_conv_fft(cudaStream_t st, int B, int k, const TTGeom& g, const int* ranks, int* off,
+                     const float* cur, float* alt, const FftMode& md, int grid, double* flops);
+void set_fft_attributes();
+// rsvd64.cu: float64 R factor and SVD of the truncating stages (left, split)
+void launch_tsqr64(cudaStream_t st, TsqrWork w, int B, int grid, double* flops);
+void launch_svd64(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
+                  int first, RoundState rs, float* P1, float* P2, float* core0_out,
+                  long long core0_cap, double* flops);
 // ttops.cu
 void launch_prior(cudaStream_t st, int B, const TTGeom& g, float* const* cores, int* ranks,
                   const double* axes, const double* mean, const double* var);
@@ -169,5 +194,6 @@ void count_launches(int n);
 void set_kernel_attributes();
 void set_ttops_attributes();
 void set_tsqr_attributes();
+void set_rsvd64_attributes();
 
 }  // namespace ttgbf

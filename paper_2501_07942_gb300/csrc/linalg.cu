@@ -994,7 +994,8 @@ __global__ void k_scan_tiles(GemmWork w) { scan_tiles_block(w); }
 // Per filter: the tall matrix of this stage and its TSQR schedule.
 __global__ void k_plan_stage(TsqrWork w, int B, int mode, int k, TTGeom g, const int* ranks,
                              const float* core_k, const float* W, long long W_cap, int N0, int N1,
-                             float* stack0, float* stack1, long long stack_cap, int slots) {
+                             float* stack0, float* stack1, long long stack_cap, int slots,
+                             int elem, int slice_blocks) {
   const int d = g.d;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const int* rk = ranks + (long long)b * (d + 1);
@@ -1030,10 +1031,11 @@ __global__ void k_plan_stage(TsqrWork w, int B, int mode, int k, TTGeom g, const
     // slices of at least eight blocks, and no more per filter than the
     // resident CTAs can run at once across the batch (fewer slice R
     // factors to combine at the end)
-    long long nsl = (M + tsqr_slice_rows(n) - 1) / tsqr_slice_rows(n);
+    const long long srows = tsqr_slice_rows(slice_blocks);
+    long long nsl = (M + srows - 1) / srows;
     const long long per = slots / B > 1 ? slots / B : 1;
     if (nsl > per) nsl = per;
-    const long long fit = stack_cap / ((long long)n * n);
+    const long long fit = stack_cap / ((long long)elem * n * n);
     if (nsl > fit) nsl = fit;
     if (nsl > kTsqrMaxSlices) nsl = kTsqrMaxSlices;
     if (nsl < 1) nsl = 1;
@@ -1128,20 +1130,21 @@ __global__ void k_plan_gemm_stage(int B, int mode, int k, TTGeom g, int* ranks, 
 // -------------------------------------------------------------- launchers
 void launch_plan_stage(cudaStream_t st, int B, int mode, int k, const TTGeom& g, const int* ranks,
                        const float* core_k, const float* W, long long W_cap, int N0, int N1,
-                       TsqrWork w, float* stack0, float* stack1, long long stack_cap, int slots) {
+                       TsqrWork w, float* stack0, float* stack1, long long stack_cap, int slots,
+                       int elem, int slice_blocks) {
   count_launches(1);
   k_plan_stage<<<1, 1024, 0, st>>>(w, B, mode, k, g, ranks, core_k, W, W_cap, N0, N1, stack0, stack1,
-                                   stack_cap, slots);
+                                   stack_cap, slots, elem, slice_blocks);
 }
 
 void launch_svd(cudaStream_t st, TsqrWork w, int B, int mode, int rank_cap, double eps, int d,
                    int first, RoundState rs, float* P1, float* P2, float* core0_out,
-                   long long core0_cap, double* flops) {
+                   long long core0_cap, double* flops, int left_threads) {
   count_launches(1);
   // truncation stages have at most rank_cap + 16 Jacobi columns: half the warps
   // suffice (two CTAs per SM); the split of the merged 2-site core (n = N_0)
   // takes 32 warps so that its pivoted QR keeps the columns in registers
-  const int threads = mode == kStageLeft ? 512 : 1024;
+  const int threads = mode == kStageLeft ? left_threads : 1024;
   k_svd<<<B, threads, kJacobiSmemFloats * sizeof(float), st>>>(w, B, mode, rank_cap, eps, d, first, rs, P1,
                                                              P2, core0_out, core0_cap, flops);
 }

@@ -366,8 +366,11 @@ __global__ void k_moments(int B, MomentArgs a, const int* ranks, int rstride, do
     __syncthreads();
     if (P > 1)
       for (int i = threadIdx.x; i < N; i += blockDim.x) xs[i] = (float)(ax[i] - c);
-    for (int pb = 0; pb < npairs; pb += 1024) {
-      const int nb = min(1024, npairs - pb);
+    // passes of at most one (alpha, beta) pair per thread (blockDim.x <= 1024
+    // pairs, the capacity of each partial-sum slot row of acc)
+    const int chunk = (int)blockDim.x;
+    for (int pb = 0; pb < npairs; pb += chunk) {
+      const int nb = min(chunk, npairs - pb);
       __syncthreads();
       // groups of threads split the grid index of each (alpha, beta); FP32
       // partial sums of at most ceil(N / groups) terms, combined in FP64

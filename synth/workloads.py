@@ -176,3 +176,42 @@ def random_index_bumps_tt(n, terms: int, seed: int, dtype=np.float64):
             G[a0, :, a1] += v
         cores.append(G.astype(dtype))
     return cores
+
+
+def config4(n_filters: int = 512, seed: int = 0):
+    """Uneven batch of independent filters: each filter draws its state
+    dimension d in {3..6}, points per axis N in {64, 128, 256} and rank cap in
+    {8, 16, 32}; filters with the same (d, N, cap) form one group with one
+    model, on [-8, 8]^d with prior N(0, 4 I), config 2's range measurement on
+    modes (0, 1), Q_mm ~ U(0.01, 0.1), R ~ U(0.005, 0.02), and a random stable
+    F of spectral radius 0.9 drawn in factored form F = c L D U: L, U unit
+    triangular with off-diagonal entries U(-a, a), D_mm ~ U(0.7, 1),
+    c = 0.9 / rho(L D U) (c rescales D only, so F's LDU factors are c D with
+    the same L and U).  The bound a = (2 S - 3) D_x / (2 x_max), D_x the grid
+    spacing, x_max = 8, S = min(10, 160 / cap), keeps every coupling's shift
+    a x / D_x within 2 S - 3 cells, so no elementary shear of the re-gridding
+    spans more than 2 S integer shifts (two expansions of S at most).
+    Returns [(Model, filter ids)], one entry per group, sorted by shape."""
+    rng = _rng(4, 0, seed)
+    ds = rng.integers(3, 7, size=n_filters)
+    Ns = rng.choice([64, 128, 256], size=n_filters)
+    caps = rng.choice([8, 16, 32], size=n_filters)
+    groups = {}
+    for f in range(n_filters):
+        groups.setdefault((int(ds[f]), int(Ns[f]), int(caps[f])), []).append(f)
+    out = []
+    for (d, N, cap), ids in sorted(groups.items()):
+        g = _rng(4, 1, d * 10000 + N * 10 + cap // 8)
+        S = min(10, 160 // cap)
+        a = (2 * S - 3) * (16.0 / N) / (2 * 8.0)
+        L = np.eye(d) + np.tril(g.uniform(-a, a, size=(d, d)), -1)
+        U = np.eye(d) + np.triu(g.uniform(-a, a, size=(d, d)), 1)
+        D = np.diag(g.uniform(0.7, 1.0, size=d))
+        F0 = L @ D @ U
+        F = 0.9 * F0 / max(abs(np.linalg.eigvals(F0)))
+        model = Model(name=f"config4-d{d}-N{N}-r{cap}", lo=np.full(d, -8.0), hi=np.full(d, 8.0),
+                      n=np.full(d, N), m0=np.zeros(d), P0=4.0 * np.eye(d), F=F,
+                      Q=np.diag(g.uniform(0.01, 0.1, size=d)), R=np.array([[g.uniform(0.005, 0.02)]]),
+                      comps=[((0, 1), h_range)], steps=50, eps=1e-6, rank_cap=cap, config_id=4)
+        out.append((model, ids))
+    return out

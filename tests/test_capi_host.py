@@ -48,6 +48,9 @@ def test_workspace_bytes(lib):
     # rank_cap * max_shift_span beyond the 160-column limit of one SVD problem
     assert G.workspace_bytes([-8] * 4, [8] * 4, [32] * 4, rank_cap=17) == 0
     assert G.workspace_bytes([-8] * 4, [8] * 4, [32] * 4, rank_cap=32, max_shift_span=5) > 0
+    # float64 rounding: the TSQR stacks hold float64 slice factors (twice the words)
+    fp64 = G.workspace_bytes([-8] * 4, [8] * 4, [128] * 4, batch=100, precision="fp64")
+    assert fp64 > big
     # invalid grids
     assert G.workspace_bytes([0.0], [0.0], [8]) == 0
     assert G.workspace_bytes([0.0], [1.0], [1]) == 0
@@ -57,7 +60,7 @@ def test_workspace_bytes(lib):
 def _init(lib, lo, hi, n, mean, var, **kw):
     g, keep = G._grid(lo, hi, n)
     o = G.Opts(kw.get("batch", 1), kw.get("rank_cap", 16), kw.get("eps", 1e-6),
-               kw.get("smax", 0), None, None, 0)
+               kw.get("smax", 0), None, None, 0, kw.get("precision", 0), kw.get("conv", 0))
     m, v = G._f64(mean), G._f64(var)
     p = G.Prior(G._dptr(m), G._dptr(v))
     ctx = ctypes.c_void_p()
@@ -76,6 +79,9 @@ def test_init_validates_before_device(lib):
     assert _init(lib, [0.0], [1.0], [8], [0.0], [0.0])[0] == -1
     assert _init(lib, [1.0], [0.0], [8], [0.0], [1.0])[0] == -1
     assert _init(lib, [0.0] * 17, [1.0] * 17, [4] * 17, [0.0] * 17, [1.0] * 17)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], precision=2)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], precision=-1)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], conv=3)[0] == -1
 
 
 def test_null_context_calls(lib):

@@ -28,10 +28,10 @@ def G():
     return lib_module()
 
 
-def bumps_filter(G, d=3, terms=3, seed=0, cap=16, smax=10, batch=1, n=None):
+def bumps_filter(G, d=3, terms=3, seed=0, cap=16, smax=10, batch=1, n=None, conv="auto"):
     n = N[:d] if n is None else n
     f = G.TTFilter(LO[:d], HI[:d], n, np.zeros(d), np.ones(d), batch=batch, rank_cap=cap, eps=EPS,
-                   max_shift_span=smax)
+                   max_shift_span=smax, conv=conv)
     cores = [c.astype(np.float32) for c in synth.random_index_bumps_tt(n, terms, seed)]
     for b in range(batch):
         f.import_cores(b, cores)
@@ -95,11 +95,14 @@ def test_wide_shear_in_pieces_within_eps(G, m, n, a, smax):
     assert f.ranks()[0].tolist() == tt.ranks(X)
 
 
-def test_scale_and_convolve_are_exact(G):
-    f, g, P = bumps_filter(G)
+@pytest.mark.parametrize("conv", ["dense", "fft"])
+def test_scale_and_convolve_are_exact(G, conv):
+    """The kernel as the dense Toeplitz product or as zero-padded FFT
+    convolutions (float32 transforms: relative error a few u log2 M)."""
+    f, g, P = bumps_filter(G, conv=conv)
     f.scale(1, 0.93)
     assert rel(tt.densify(f.export_cores(0)), pmf.scale_axis(P, g, 1, 0.93)) < 1e-6
-    f, g, P = bumps_filter(G)
+    f, g, P = bumps_filter(G, conv=conv)
     q = [0.05, 0.1, 0.02]
     f.convolve(q)
     ref = P
@@ -151,10 +154,14 @@ def test_round_scale_invariant_at_extreme_magnitudes(G, scale):
     assert rel(tt.densify([c.astype(np.float64) for c in out]) / scale, ref) < 1e-5
 
 
-def test_predict_one_step(G):
+@pytest.mark.parametrize("conv", ["dense", "fft"])
+def test_predict_one_step(G, conv):
+    """Upper-triangular F (scalings fused into the kernel: the FFT path
+    gathers them while loading) and a general F (L shears after the
+    scalings, which then run as their own pass)."""
     F = np.array([[0.95, 0.04, -0.03], [0.0, 0.97, 0.05], [0.0, 0.0, 0.92]])
     Q = np.diag([0.05, 0.08, 0.03])
-    f, g, P = bumps_filter(G)
+    f, g, P = bumps_filter(G, conv=conv)
     f.predict(F, Q)
     X, tails, _ = T.predict(bumps_cores(), g, F, Q, EPS, 16)
     ref, mass = pmf.predict_rg(P / (P.sum() * g.delta), g, F, Q)
@@ -162,7 +169,7 @@ def test_predict_one_step(G):
     assert f.ranks()[0].tolist() == tt.ranks(X)
     # non-triangular F: L shears follow the scalings
     F2 = np.array([[0.95, 0.04, 0.0], [-0.05, 0.97, 0.02], [0.03, 0.0, 0.92]])
-    f, g, P = bumps_filter(G)
+    f, g, P = bumps_filter(G, conv=conv)
     f.predict(F2, Q)
     X, tails, _ = T.predict(bumps_cores(), g, F2, Q, EPS, 16)
     ref, _ = pmf.predict_rg(P / (P.sum() * g.delta), g, F2, Q)
@@ -262,3 +269,25 @@ def test_one_dimensional_and_tiny_grid(G):
           for m in range(2)]
     X, tails, _ = T.predict(X0, g, F, 0.1 * np.eye(2), 1e-6, 8)
     assert rel(tt.densify(f.export_cores(0)), ref) <= tt_tol(1e-6, sum(tails))
+
+
+@pytest.mark.parametrize("terms", [17, 40])
+def test_mass_and_moments_at_ranks_above_16(G, terms):
+    """Ranks 17 and 40 on the inner links (more (alpha, beta) pairs per core
+    than a moments pass takes at once): the normalised TT has unit mass by
+    the oracle's sum, and the moments equal the oracle's of the densified TT."""
+    n = [12, 10, 9]
+    f = G.TTFilter(LO[:3], HI[:3], n, np.zeros(3), np.ones(3), rank_cap=40, eps=EPS,
+                   max_shift_span=4)
+    cores = [c.astype(np.float32) for c in synth.random_index_bumps_tt(n, terms, 7)]
+    f.import_cores(0, cores)
+    assert f.ranks()[0].tolist() == [1, terms, terms, 1]
+    f.normalise()
+    g = pmf.Grid(LO[:3], HI[:3], n)
+    out = f.export_cores(0)
+    assert abs(tt.full_sum([c.astype(np.float64) for c in out]) * g.delta - 1.0) < 1e-5
+    m, c, lc, ll = f.estimate()
+    P = tt.densify([x.astype(np.float64) for x in cores])
+    mo, co = pmf.moments(P / (P.sum() * g.delta), g)
+    np.testing.assert_allclose(m[0], mo, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(c[0], co, rtol=0, atol=1e-5)

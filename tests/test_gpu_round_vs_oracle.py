@@ -10,16 +10,25 @@ discarded tail that the GPU reports about itself.
    float32) of the oracle's, which is the optimal truncation of each link
    given the others; the tails the GPU reports match the oracle's; the cores
    left of the center are orthonormal where it matters (see the test).
+   A link whose rank differs must be one where the oracle's own decision is
+   at the threshold (rank_is_borderline with ETA): the cores are stored in
+   float32, and the orthogonalisation of float32 data perturbs the singular
+   values a truncation compares with eps ||A|| / sqrt(d - 1) by about
+   u sqrt(n) ||A|| (u = 6e-8, n <= 160), a quarter of that threshold at
+   eps = 1e-6; a cap that binds decides alone and must agree.
 2. One predict and one update from a shared input (the oracle's state, in
    float32 on both sides), with the rank cap binding (128^4, cap 16; 32^4, cap
    8) and not binding (32^4, cap 32): equal ranks, matching tails, density
    within 10 (eps + tau) + 1e-5 of the oracle's TT with tau the ORACLE's
    tails, means within 1e-3 grid spacings of the oracle TT's, log c within
-   1e-5.
-3. Flat bounds where the cap does not bind (the oracle's ranks stay below
-   it): config 2 at 32^4 (cap 32) and 64^4 (cap 53, shears in pieces) over 6
-   steps from the prior, every step against the dense oracle at the plain
-   10 eps + 1e-5 (not summed over steps) and means within 1e-3 grid spacings."""
+   LOGC_TOL (below).
+3. Flat bounds where the cap leaves the truncations at the eps level: config
+   2 at 32^4 and 64^4 with rank cap 53 (span 3; shears in pieces at 64^4)
+   over 6 steps from the prior.  The oracle TT filter at the same cap
+   discards less than 1e-5 per step there (the cap binds at most on the split
+   of the merged 2-site core, whose rank can reach N), so every step is held
+   against the dense oracle at the plain 10 eps + 1e-5 (not summed over steps)
+   and means within 1e-3 grid spacings."""
 import math
 
 import numpy as np
@@ -35,6 +44,12 @@ pytestmark = pytest.mark.gpu
 
 TAIL_RTOL = 0.05   # relative agreement of tails / errors with the oracle's
 FP32_FLOOR = 1e-6  # absolute float32 floor of a tail or a relative error
+ETA = 0.25         # relative perturbation of a truncation threshold by float32 data
+# log c: the measurement tables are float32, so h is off by about u h_max and
+# each likelihood exponent (z - h)^2 / 2R by |z - h| u h_max / R; over the
+# points within 3 sigma_R of the measurement that is 3 sqrt(R) u h_max / R
+# = 2e-5 for R = 0.01, h_max = 11.3 (config 2)
+LOGC_TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -64,9 +79,12 @@ def oracle_state(model, mc, steps, cap, smax=10):
     return f32(X), z[steps]
 
 
-def new_filter(G, model, cap, smax=0, batch=1):
+def new_filter(G, model, cap, smax=0, batch=1, precision="fp32"):
     return G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=batch,
-                      rank_cap=cap, eps=model.eps, max_shift_span=smax)
+                      rank_cap=cap, eps=model.eps, max_shift_span=smax, precision=precision)
+
+
+PRECISIONS = ["fp32", "fp64"]  # ttgbf_opts.precision: R factors / SVDs of the truncating stages
 
 
 def gpu_cores(f, b=0):
@@ -88,6 +106,28 @@ def link_singular_values(cores):
     return out
 
 
+def final_decisions(trace):
+    """The oracle's last truncation record of every link."""
+    last = {}
+    for rec in trace:
+        last[rec["link"]] = rec
+    return last
+
+
+def check_ranks(gpu_ranks, orc_ranks, trace, what):
+    """Equal ranks on every link, except where the oracle's own decision is at
+    the threshold; returns the number of such borderline links."""
+    last = final_decisions(trace)
+    border = 0
+    for k in range(len(orc_ranks) - 2):  # link k between cores k and k + 1
+        rg, ro = gpu_ranks[k + 1], orc_ranks[k + 1]
+        if rg == ro:
+            continue
+        assert k in last and T.rank_is_borderline(last[k], rg, ETA), (what, k, gpu_ranks, orc_ranks)
+        border += 1
+    return border
+
+
 def check_left_orthonormal(cores, svals):
     """Cores 0..d-2 (left of the center after a full rounding) against the
     identity: returns (plain max |C^T C - I|, the same weighted by the link's
@@ -99,8 +139,10 @@ def check_left_orthonormal(cores, svals):
     for k in range(len(cores) - 1):
         C = cores[k]
         M = C.reshape(-1, C.shape[2])
-        D = M.T @ M - np.eye(M.shape[1])
-        s = svals[k][:M.shape[1]]
+        q = min(M.shape[1], len(svals[k]))  # ranks may differ on a borderline link
+        M = M[:, :q]
+        D = M.T @ M - np.eye(q)
+        s = svals[k][:q]
         plain = max(plain, float(np.abs(D).max()))
         weighted = max(weighted, float(np.abs(s[:, None] * D * s[None, :]).max() / s[0] ** 2))
     return plain, weighted
@@ -114,14 +156,15 @@ def bench_state():
     return model, X, z
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("m,n,a,S", [(1, 2, 0.055, 9), (0, 2, 0.03, 5), (2, 0, 0.04, 7)])
-def test_round_matches_oracle_at_bench_shapes(G, bench_state, m, n, a, S):
+def test_round_matches_oracle_at_bench_shapes(G, bench_state, m, n, a, S, precision):
     model, X, _ = bench_state
     g = oracle_grid(model)
     s, ts = T.shear_shifts(g, m, n, a)
     assert len(ts) == S
     A = tt.shear_operator(X, m, n, s, ts)
-    f = new_filter(G, model, 16)
+    f = new_filter(G, model, 16, precision=precision)
     f.import_cores(0, [c.astype(np.float32) for c in X])
     f.shear(m, n, a, do_round=False)
     assert T.rel_distance(gpu_cores(f), A) < 1e-6  # the expansion itself is exact
@@ -129,71 +172,82 @@ def test_round_matches_oracle_at_bench_shapes(G, bench_state, m, n, a, S):
     f.round()
     gpu_tail = f.stats()[0]["tail_sum"] - t0
     out = gpu_cores(f)
-    B, tails = T.round_full(A, model.eps, 16)
+    trace = []
+    B, tails = T.round_full(A, model.eps, 16, trace)
     err_orc = math.sqrt(sum(t * t for t in tails))
     assert abs(T.rel_distance(B, A) - err_orc) < 1e-7  # the oracle's error identity
     assert err_orc > 10 * model.eps  # the cap binds
-    assert tt.ranks(out) == tt.ranks(B), (tt.ranks(out), tt.ranks(B))
+    border = check_ranks(tt.ranks(out), tt.ranks(B), trace, "round")
     err_gpu = T.rel_distance(out, A)
     assert err_gpu <= (1 + TAIL_RTOL) * err_orc + FP32_FLOOR, (err_gpu, err_orc)
     assert abs(gpu_tail - sum(tails)) <= TAIL_RTOL * sum(tails) + FP32_FLOOR, (gpu_tail, sum(tails))
     assert T.rel_distance(out, B) <= 2 * err_orc + FP32_FLOOR
     plain, weighted = check_left_orthonormal(out, link_singular_values(B))
-    print(f"shear ({m},{n}) S={S}: ranks {tt.ranks(out)} err gpu {err_gpu:.4e} oracle {err_orc:.4e} "
+    print(f"{precision} shear ({m},{n}) S={S}: ranks {tt.ranks(out)} oracle {tt.ranks(B)} "
+          f"({border} borderline) err gpu {err_gpu:.4e} oracle {err_orc:.4e} "
           f"tail gpu {gpu_tail:.4e} oracle {sum(tails):.4e} |C^T C - I| {plain:.2e} "
           f"weighted {weighted:.2e}")
     assert weighted < 1e-5
 
 
-def _compare_step(G, model, X, z, cap, smax=0):
+def _compare_step(G, model, X, z, cap, smax=0, precision="fp32"):
     """One predict, then one update, each from the oracle's state."""
     g = oracle_grid(model)
-    f = new_filter(G, model, cap, smax)
+    f = new_filter(G, model, cap, smax, precision=precision)
     comps = device_tables(model, f.grid_axes())
     oc = model.tables(g.axes)
     f.import_cores(0, [c.astype(np.float32) for c in X])
     f.predict(model.F, model.Q)
-    Yp, tp, _ = T.predict(X, g, model.F, model.Q, model.eps, cap, smax or 10)
+    trp = []
+    Yp, tp, _ = T.predict(X, g, model.F, model.Q, model.eps, cap, smax or 10, trp)
     out = gpu_cores(f)
     t_gpu = f.stats()[0]["tail_sum"]
-    assert tt.ranks(out) == tt.ranks(Yp), ("predict", tt.ranks(out), tt.ranks(Yp))
+    bp = check_ranks(tt.ranks(out), tt.ranks(Yp), trp, "predict")
     assert abs(t_gpu - sum(tp)) <= TAIL_RTOL * sum(tp) + FP32_FLOOR * len(tp), (t_gpu, sum(tp))
     assert T.rel_distance(out, Yp) <= 10 * (model.eps + sum(tp)) + 1e-5
-    # update from the oracle's predicted state
+    # update from the oracle's predicted state (the step's tail statistics
+    # keep the predict's tails: the update's are the difference)
     Yp = f32(Yp)
     f.import_cores(0, [c.astype(np.float32) for c in Yp])
+    t0 = f.stats()[0]["tail_sum"]
     f.update(comps, model.R, z[None, :])
-    Yu, tu, logc = T.update(Yp, g, oc, z, model.R, model.eps, cap)
+    tru = []
+    Yu, tu, logc = T.update(Yp, g, oc, z, model.R, model.eps, cap, tru)
     out = gpu_cores(f)
     st = f.stats()[0]
-    assert tt.ranks(out) == tt.ranks(Yu), ("update", tt.ranks(out), tt.ranks(Yu))
-    assert abs(st["tail_sum"] - sum(tu)) <= TAIL_RTOL * sum(tu) + FP32_FLOOR * len(tu)
+    bu = check_ranks(tt.ranks(out), tt.ranks(Yu), tru, "update")
+    assert abs(st["tail_sum"] - t0 - sum(tu)) <= TAIL_RTOL * sum(tu) + FP32_FLOOR * len(tu), \
+        (st["tail_sum"] - t0, sum(tu))
     assert T.rel_distance(out, Yu) <= 10 * (model.eps + sum(tu)) + 1e-5
     m, c, lc, ll = f.estimate()
     mo, co = T.moments(Yu, g)
     assert (np.abs(m[0] - mo) <= 1e-3 * g.delta_axis).all(), (m[0], mo)
     assert (np.abs(c[0] - co) <= cov_tol(g.delta_axis, co)).all()
-    assert abs(lc[0] - logc) < 1e-5
+    assert abs(lc[0] - logc) < LOGC_TOL, (lc[0], logc)
+    print(f"{precision} N={model.n[0]} cap {cap}: predict tails gpu {t_gpu:.4e} oracle {sum(tp):.4e}, "
+          f"update tails gpu {st['tail_sum'] - t0:.4e} oracle {sum(tu):.4e}, borderline ranks "
+          f"{bp} + {bu}, |log c diff| {abs(lc[0] - logc):.2e}")
     return sum(tp), sum(tu)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n,cap,mc,k", [(128, 16, 0, 2), (32, 8, 3, 3), (32, 32, 3, 3), (32, 32, 4, 5)])
-def test_one_step_matches_oracle_tt_step(G, n, cap, mc, k):
+def test_one_step_matches_oracle_tt_step(G, n, cap, mc, k, precision):
     model = synth.config2(n=n)
-    X, z = oracle_state(model, mc, k, cap)
-    tp, tu = _compare_step(G, model, X, z, cap)
-    if cap == 32:
-        assert tp + tu < 20 * model.eps  # the cap does not bind: only eps-level tails
+    smax = 5 if cap == 32 else 0  # rank cap x span <= 160 columns
+    X, z = oracle_state(model, mc, k, cap, smax or 10)
+    _compare_step(G, model, X, z, cap, smax, precision=precision)
 
 
-@pytest.mark.parametrize("n,cap,smax", [(32, 32, 5), (64, 53, 3)])
-def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax):
+@pytest.mark.parametrize("n,cap,smax,precision", [(32, 53, 3, "fp32"), (64, 53, 3, "fp32"),
+                                                   (32, 53, 3, "fp64")])
+def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax, precision):
     model = synth.config2(n=n)
     g = oracle_grid(model)
     oc = model.tables(g.axes)
     mcs = [0, 1]
     steps = 6
-    f = new_filter(G, model, cap, smax, batch=len(mcs))
+    f = new_filter(G, model, cap, smax, batch=len(mcs), precision=precision)
     comps = device_tables(model, f.grid_axes())
     zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
     Ps = [pmf.prior(g, model.m0, model.P0) for _ in mcs]
@@ -203,12 +257,11 @@ def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax):
         f.predict(model.F, model.Q)
         f.update(comps, model.R, np.stack([z[k] for z in zs]))
         m, c, lc, ll = f.estimate()
-        st = f.stats()
         for i in range(len(mcs)):
             Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
-            X[i], info = T.step(X[i], g, model.F, model.Q, oc, zs[i][k], model.R, model.eps, None, smax)
-            assert max(tt.ranks(X[i])) <= cap  # the oracle's own ranks stay below the cap
+            X[i], info = T.step(X[i], g, model.F, model.Q, oc, zs[i][k], model.R, model.eps, cap, smax)
+            assert info["tail_sum"] < 1e-5  # the oracle's truncations at this cap: eps level
             e = rel(tt.densify(gpu_cores(f, i)), Ps[i])
             mo, co = pmf.moments(Ps[i], g)
             print(f"N={n} step {k} filter {i}: rel err {e:.3e} (flat bound {flat:.1e}), mean err / D "
@@ -216,5 +269,4 @@ def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax):
             assert e <= flat, (k, i, e)
             assert (np.abs(m[i] - mo) <= 1e-3 * g.delta_axis).all(), (k, i)
             assert (np.abs(c[i] - co) <= cov_tol(g.delta_axis, co)).all(), (k, i)
-            assert abs(lc[i] - logc) < 1e-5, (k, i)
-            assert st[i]["cap_hits"] == 0
+            assert abs(lc[i] - logc) < LOGC_TOL, (k, i, lc[i], logc)

@@ -159,3 +159,18 @@ def test_rel_distance_by_inner_products():
     a = synth.random_index_bumps_tt(g.n, 2, seed=1)
     b = synth.random_index_bumps_tt(g.n, 3, seed=3)
     assert abs(T.rel_distance(a, b) - rel(tt.densify(a), tt.densify(b))) < 1e-7
+
+
+def test_rank_is_borderline():
+    # singular values 1, 0.1, 0.01, 1e-3, 1e-4; threshold 1.02e-3 keeps rank 3
+    # (tail of rank 3 is 1.005e-3 <= thr, tail of rank 2 is 1.0e-2 > thr)
+    s = np.array([1.0, 0.1, 0.01, 1e-3, 1e-4])
+    rec = {"s": s, "thr": 1.02e-3, "rank": 3, "rmax": None}
+    assert T._rank_and_tail(s, rec["thr"], None)[0] == 3
+    assert T.rank_is_borderline(rec, 3, 0.0)
+    assert T.rank_is_borderline(rec, 4, 0.25)       # tail of rank 3 is 0.985 thr: at the threshold
+    assert not T.rank_is_borderline(rec, 4, 0.01)
+    assert not T.rank_is_borderline(rec, 2, 0.25)   # tail of rank 2 is 9.8 thr
+    assert not T.rank_is_borderline(rec, 5, 0.25)   # tail of rank 4 is 0.1 thr
+    capped = dict(rec, rmax=3)
+    assert not T.rank_is_borderline(capped, 4, 0.25)  # above the cap
