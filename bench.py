@@ -299,22 +299,109 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
-def make_tt(G, model, dev, batch, rank_cap, smax, precision, parts=None):
-    """A TT filter context; parts (TTGBF_PARTS) overrides the library's batch
-    split for this context only."""
-    old = os.environ.get("TTGBF_PARTS")
-    if parts is not None:
-        os.environ["TTGBF_PARTS"] = str(parts)
+TUNE_CACHE = os.path.join(ROOT, "paper_2501_07942_gb300", "tune_cache.txt")
+
+
+def run_config4(args, dev):
+    """The uneven batch (512 filters, 36 (d, N, rank cap) groups, each with its
+    own random stable F, Q, R): every group a TTFilter batch on its own stream
+    (launch configuration from the autotuner's persisted choices), all stepped
+    together by one TTFilterGroup; a horizon of H steps recorded into one CUDA
+    graph and launched until the timed steps are done, the measurements of the
+    next H steps copied into the graph's buffer before each launch (inside the
+    timed region).  Per-filter step latency: untimed
+    group steps timed per batch (every filter of a batch finishes with it)."""
+    import torch
+    import paper_2501_07942_gb300 as G
+    groups = synth.config4()
+    total = args.c4_steps
+    H = min(args.c4_horizon, total)
+    reps = max(1, total // H)
+    st = torch.cuda.Stream(dev)
+    filters, models, streams, comps, zall, zbuf, outs, tuned = [], [], [], [], [], [], [], 0
+    for m, ids in groups:
+        s = torch.cuda.Stream(dev)
+        smax = min(10, 160 // m.rank_cap)
+        kw = tuned_config(G, m, len(ids), m.rank_cap, smax, "fp32")
+        tuned += bool(kw)
+        f = G.TTFilter(m.lo, m.hi, m.n, m.m0, np.diag(m.P0), batch=len(ids), rank_cap=m.rank_cap,
+                       eps=m.eps, max_shift_span=smax, stream=s, device=dev, **kw)
+        filters.append(f)
+        models.append(m)
+        streams.append(s)
+        comps.append([(md, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+                      for md, t in m.tables(f.grid_axes())])
+        z = np.stack([synth.simulate(m, fid, steps=reps * H + 4)[1] for fid in ids], axis=1)
+        zall.append(torch.tensor(z, dtype=torch.float32, device=dev))
+        zbuf.append(torch.zeros((H,) + tuple(z.shape[1:]), dtype=torch.float32, device=dev))
+        B = len(ids)
+        outs.append([torch.zeros(H, B, m.d, dtype=torch.float64, device=dev),
+                     torch.zeros(H, B, m.d, m.d, dtype=torch.float64, device=dev),
+                     torch.zeros(H, B, dtype=torch.float64, device=dev),
+                     torch.zeros(H, B, dtype=torch.float64, device=dev)])
+    grp = G.TTFilterGroup(filters, stream=st, device=dev)
+    step_args = lambda k: [(m.F, m.Q, comps[i], m.R, zall[i][k], outs[i][0][0], outs[i][1][0],
+                            outs[i][2][0], outs[i][3][0]) for i, m in enumerate(models)]
+    # per-filter latency of a batch step (untimed group steps, first two warm)
+    lat = []
+    for k in range(4):
+        grp.step(step_args(k))
+        if k >= 2:
+            for i, ms in enumerate(grp.times()):
+                lat += [ms] * filters[i].batch
+    torch.cuda.synchronize(dev)
+    grp.capture([(m.F, m.Q, comps[i], m.R, zbuf[i], *outs[i]) for i, m in enumerate(models)], H)
+    nk = grp.graph_kernels()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(st):
+        a.record(st)
+        for r in range(reps):
+            for i in range(len(models)):
+                zbuf[i].copy_(zall[i][4 + r * H: 4 + (r + 1) * H])
+            grp.launch()
+        b.record(st)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    nf = sum(f.batch for f in filters)
+    mean_ok = all(bool(torch.isfinite(o[0]).all()) for o in outs)
+    grp.free()
+    for f in filters:
+        f.free()
+    lat = np.array(lat)
+    return {"value": nf * reps * H / (ms * 1e-3), "unit": UNIT, "filters": nf, "groups": len(groups),
+            "steps": reps * H, "graph_horizon": H, "graph_launches": reps, "kernels_per_graph": nk,
+            "ms_per_step": ms / (reps * H), "estimates_finite": mean_ok,
+            "per_filter_step_ms": {"p50": float(np.percentile(lat, 50)),
+                                   "p99": float(np.percentile(lat, 99))},
+            "autotuned_groups": tuned,
+            "workload": "config4: 512 filters, d in {3..6}, N in {64,128,256}, rank cap in "
+                        "{8,16,32}, random stable F (rho 0.9), diagonal Q, R, range measurement"}
+
+
+def tuned_config(G, model, batch, rank_cap, smax, precision):
+    """The autotuner's persisted launch configuration for this shape ({} when
+    the cache has none: the library's defaults)."""
+    if not os.path.exists(TUNE_CACHE):
+        return {}
     try:
-        return G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=batch,
-                          rank_cap=rank_cap, eps=model.eps, max_shift_span=smax, device=dev,
-                          precision=precision)
-    finally:
-        if parts is not None:
-            if old is None:
-                del os.environ["TTGBF_PARTS"]
-            else:
-                os.environ["TTGBF_PARTS"] = old
+        best, _ = G.autotune(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), model.F, model.Q,
+                             batch=batch, rank_cap=rank_cap, eps=model.eps, max_shift_span=smax,
+                             precision=precision, cache_path=TUNE_CACHE, cache_only=True)
+        return best
+    except LookupError:
+        return {}
+
+
+def make_tt(G, model, dev, batch, rank_cap, smax, precision, parts=None):
+    """A TT filter context with the autotuned launch configuration of its shape;
+    parts overrides the batch split for this context only."""
+    kw = tuned_config(G, model, batch, rank_cap, smax, precision)
+    if parts is not None:
+        kw["parts"] = parts
+    return G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=batch,
+                      rank_cap=rank_cap, eps=model.eps, max_shift_span=smax, device=dev,
+                      precision=precision, **kw)
 
 
 def run_ours(args, rank: int, world: int, local_rank: int, dist):
@@ -498,6 +585,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("rank cap 16", f"rank cap {cap}"),
                    "rounding_precision": prec, "max_shift_span": smax,
+                   "launch_config": tuned_config(G, model, B, cap, smax, prec) or "library defaults",
                    "filters_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (independent filters, no collective)"},
         "roofline": roofline,
@@ -508,6 +596,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "kernels": {k: {"ms_share": (v["ms"] / tot_ms if tot_ms else 0.0), "launches": v["launches"]}
                     for k, v in prof.items() if v["launches"] > 0},
         "fullgrid": fullgrid,
+        "config4": None if args.no_config4 else run_config4(args, dev),
         "accuracy": accuracy,
         "rank_cap_sweep": sweep,
     }
@@ -537,6 +626,11 @@ def main():
     ap.add_argument("--max-shift-span", type=int, default=10)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="arithmetic of the truncating R factors and SVDs (ttgbf_opts.precision)")
+    ap.add_argument("--no-config4", action="store_true", help="skip the uneven-batch leg")
+    ap.add_argument("--c4-horizon", type=int, default=10,
+                    help="steps recorded into one CUDA graph in the uneven-batch leg (even)")
+    ap.add_argument("--c4-steps", type=int, default=10,
+                    help="timed steps of the uneven-batch leg (graph launches x horizon)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy comparison and the rank-cap sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")

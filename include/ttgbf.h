@@ -331,7 +331,13 @@ int ttgbf_group_step(ttgbf_group* g, const ttgbf_group_step_args* args);
  * it.  The transition operators of each context's F, Q are prepared on the
  * host first (outside the recording).  Every pointer in args is baked into
  * the graph: a launch reads the measurements and writes the estimates at
- * those addresses, so a caller replays a horizon by refilling z_dev. */
+ * those addresses, so a caller replays a horizon by refilling z_dev.
+ * The group's stream and every context's stream must be created streams (the
+ * legacy default stream cannot be recorded): TTGBF_EINVAL otherwise.  The
+ * recorded steps must bring every context back to the state it started from
+ * (which ping-pong buffer holds each core, the canonical form), so that the
+ * graph can be launched again: step once before recording and record an
+ * even number of steps; TTGBF_EINVAL (nothing recorded) otherwise. */
 int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32_t steps);
 
 /* Launch the recorded graph on the group's stream (asynchronous). */
@@ -358,7 +364,8 @@ int ttgbf_group_free(ttgbf_group* g);
  * candidate allocates its own device workspace (cudaMalloc) for the timing.
  * cache_path (may be NULL): a text file of earlier results, one line per
  * shape and GPU; a shape found there is returned without timing (*best_ms
- * then holds the recorded time), a new result is appended. */
+ * then holds the recorded time), a new result is appended.  steps = 0 looks
+ * the shape up in cache_path only: TTGBF_EINVAL when it is not there. */
 int ttgbf_autotune(const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf_opts* base,
                    const double* F, const double* Q, int32_t steps, const char* cache_path,
                    ttgbf_opts* best, double* best_ms);

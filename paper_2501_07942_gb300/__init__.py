@@ -439,7 +439,8 @@ class TTFilterGroup:
         import torch
         self._lib = load()
         self.filters = list(filters)
-        self._stream = torch.cuda.current_stream(device) if stream is None else stream
+        # a created stream: the legacy default stream cannot be recorded into a graph
+        self._stream = torch.cuda.Stream(device) if stream is None else stream
         arr = (ctypes.c_void_p * len(self.filters))(*[f._ctx.value for f in self.filters])
         self._g = ctypes.c_void_p()
         _check(self._lib.ttgbf_group_create(ctypes.byref(self._g), arr, len(self.filters),
@@ -495,10 +496,14 @@ class TTFilterGroup:
 
 
 def autotune(lo, hi, n, prior_mean, prior_var, F, Q, batch=1, rank_cap=16, eps=1e-6,
-             max_shift_span=0, precision="fp32", conv="auto", steps=3, cache_path=None):
+             max_shift_span=0, precision="fp32", conv="auto", steps=3, cache_path=None,
+             cache_only=False):
     """ttgbf_autotune: the fastest launch configuration (parts,
     tsqr_slice_blocks, svd_threads) for this batch shape and model, and its
-    time per predictive step in ms."""
+    time per predictive step in ms.  cache_only: look the shape up in
+    cache_path without timing anything (LookupError when it is not there)."""
+    if cache_only:
+        steps = 0
     lib = load()
     g, gkeep = _grid(lo, hi, n)
     pm, pv = _f64(prior_mean), _f64(prior_var)
@@ -509,7 +514,10 @@ def autotune(lo, hi, n, prior_mean, prior_var, F, Q, batch=1, rank_cap=16, eps=1
     ms = ctypes.c_double()
     F, Q = _f64(F), _f64(Q)
     cp = cache_path.encode() if cache_path else None
-    _check(lib.ttgbf_autotune(ctypes.byref(g), ctypes.byref(pr), ctypes.byref(o), _dptr(F), _dptr(Q),
-                              int(steps), cp, ctypes.byref(best), ctypes.byref(ms)), "ttgbf_autotune")
+    rc = lib.ttgbf_autotune(ctypes.byref(g), ctypes.byref(pr), ctypes.byref(o), _dptr(F), _dptr(Q),
+                            int(steps), cp, ctypes.byref(best), ctypes.byref(ms))
+    if cache_only and rc == -1:
+        raise LookupError("shape not in the autotuner's cache")
+    _check(rc, "ttgbf_autotune")
     return {"parts": best.parts, "tsqr_slice_blocks": best.tsqr_slice_blocks,
             "svd_threads": best.svd_threads}, ms.value

@@ -2133,8 +2133,10 @@ int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32
   int rc = group_guard(g, args);
   if (rc) return rc;
   if (steps < 1) return TTGBF_EINVAL;
+  // the legacy default stream cannot be recorded, nor joined into a recording
+  if (g->st == nullptr) return TTGBF_EINVAL;
   for (ttgbf_ctx* q : g->leaves)
-    if (q->prof) return TTGBF_EINVAL;  // event timing cannot be replayed
+    if (q->prof || q->st == nullptr) return TTGBF_EINVAL;  // event timing cannot be replayed
   // operators of F, Q prepared on the host (and uploaded) before recording
   for (size_t l = 0; l < g->leaves.size(); ++l) {
     ttgbf_ctx* q = g->leaves[l];
@@ -2331,7 +2333,8 @@ extern "C" {
 int ttgbf_autotune(const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf_opts* base,
                    const double* F, const double* Q, int32_t steps, const char* cache_path,
                    ttgbf_opts* best, double* best_ms) {
-  if (!grid || !prior || !base || !F || !Q || !best || !best_ms || steps < 1) return TTGBF_EINVAL;
+  if (!grid || !prior || !base || !F || !Q || !best || !best_ms || steps < 0) return TTGBF_EINVAL;
+  if (steps == 0 && !cache_path) return TTGBF_EINVAL;
   int rc = validate_grid(grid);
   if (rc) return rc;
   rc = validate_opts(base);
@@ -2358,6 +2361,7 @@ int ttgbf_autotune(const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf
       std::fclose(fh);
     }
   }
+  if (steps == 0) return TTGBF_EINVAL;  // cache lookup only, and the shape is not there
   double bms = 1e300;
   ttgbf_opts bo = *base;
   int last = TTGBF_EINVAL;

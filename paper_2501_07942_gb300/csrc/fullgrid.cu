@@ -29,6 +29,8 @@ namespace {
 constexpr int kFgMaxComps = 16;
 constexpr int kFgMaxD = 6;  // dense grids beyond d = 6 do not fit in memory
 constexpr int kFgAcc = 1 + kFgMaxD + kFgMaxD * kFgMaxD;
+constexpr int kFgPredSum = kFgAcc + 1;  // acc slot: sum of the predictive density (fused pass)
+constexpr int kFgLikSum = kFgAcc + 2;   // acc slot: sum of L P
 
 // Division by a run-time constant with a multiply-high and a shift
 // (Granlund-Montgomery round-up method), exact for every 32-bit dividend.
@@ -283,6 +285,204 @@ __global__ void __launch_bounds__(256) k_fg_axis(const T* __restrict__ in, T* __
   }
 }
 
+// ---- fused pass along one axis (upper-triangular F: L = I)
+// When F = D U, every operation of the re-gridding and the kernel on axis m
+// commutes with every operation on another axis that does not weight by x_m:
+// U's shears x_m += a x_n (n > m) act along m with weights from axis n, the
+// scaling and the kernel of axis m act along m alone, and the only operations
+// weighting by x_m (the shears x_l += a x_m, l < m) come earlier in the
+// canonical order.  So the predictive step is one pass per axis m (m
+// ascending): load a tile of fibres along m, apply m's shears in order (each
+// zero outside the grid, exactly as its own pass would), then m's banded
+// operator (cloud-in-cell scaling fused with the Gaussian kernel), store.
+constexpr int kPassMaxShears = kFgMaxD;
+
+struct FgShearList {
+  int ns;                              // shears along this axis, in order
+  int n[kPassMaxShears];               // weight axis of each
+  const int* kshift[kPassMaxShears];   // floor of the shift, per index of the weight axis
+  const double* frac[kPassMaxShears];  // fractional part
+};
+
+// Tiles of FIB fibres along axis m (N <= 128, a multiple of 4): the operator
+// transposed in shared memory (Mt[i][j] = M[j][i]), two tile buffers [N][FIB
+// + 4] (shears ping-pong between them, the product goes to the free one).
+// The next tile's loads are issued into registers before the current tile's
+// shears and product, so they are in flight while the SM computes.  s_in
+// multiplies the input (a pending normalisation); sum_acc (nullable) receives
+// the sum of the output (the mass before normalisation).
+template <typename T, int FIB>
+__global__ void __launch_bounds__(256, 1) k_fg_pass(const T* __restrict__ in, T* __restrict__ out,
+                                                    FgGeom g, long long nfib, int N, long long post,
+                                                    const T* __restrict__ M, const int* __restrict__ blo,
+                                                    const int* __restrict__ bhi, FgShearList sh, T s_in,
+                                                    double* sum_acc) {
+  constexpr int PAD = FIB + 4;
+  constexpr int FPT = FIB / 8;           // fibres per thread in the product
+  constexpr int PER = FIB * 128 / 256;   // tile elements per thread (N <= 128)
+  extern __shared__ unsigned char smraw[];
+  T* Mt = reinterpret_cast<T*>(smraw);   // [N][N]
+  T* A = Mt + N * N;                     // [N][PAD]
+  T* Bw = A + N * PAD;                   // [N][PAD]
+  __shared__ long long fb[2][FIB];       // element offset of every fibre's first entry
+  __shared__ int sk[kPassMaxShears][FIB];
+  __shared__ T sfr[kPassMaxShears][FIB];
+  __shared__ double red[8];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < N * N; t += blockDim.x) {
+    const int j = t / N, i = t - j * N;
+    Mt[i * N + j] = M[t];
+  }
+  const int tf = tid & 7, tj = tid >> 3;
+  const int j0 = tj * 4;
+  const bool rows_ok = j0 < N;
+  int lo = N, hi = -1;
+  if (rows_ok)
+    for (int q = 0; q < 4; ++q)
+      if (blo[j0 + q] <= bhi[j0 + q]) {
+        lo = min(lo, blo[j0 + q]);
+        hi = max(hi, bhi[j0 + q]);
+      }
+  auto fibre_base = [&](long long gf) -> long long {
+    const long long p = gf / post, q = gf - p * post;
+    return p * N * post + q;
+  };
+  const long long tstride = (long long)gridDim.x * FIB;
+  long long g0 = (long long)blockIdx.x * FIB;
+  if (tid < FIB) fb[0][tid] = (g0 + tid < nfib) ? fibre_base(g0 + tid) : -1;
+  __syncthreads();
+  T v[PER];
+  auto load = [&](int sel, long long gb) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u;
+      T x = (T)0;
+      if (e < FIB * N) {
+        if (post == 1) {
+          const int f = e / N, i = e - f * N;
+          if (gb + f < nfib) x = in[(gb + f) * N + i];
+        } else {
+          const int i = e / FIB, f = e - i * FIB;
+          const long long b = fb[sel][f];
+          if (b >= 0) x = in[b + (long long)i * post];
+        }
+      }
+      v[u] = x;
+    }
+  };
+  if (g0 < nfib) load(0, g0);
+  Kahan<T> ks;
+  int sel = 0;
+  for (; g0 < nfib; g0 += tstride) {
+    // ---- the current tile (registers) into A, scaled
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u;
+      if (e < FIB * N) {
+        int i, f;
+        if (post == 1) {
+          f = e / N;
+          i = e - f * N;
+        } else {
+          i = e / FIB;
+          f = e - i * FIB;
+        }
+        A[i * PAD + axcol(f)] = v[u] * s_in;
+      }
+    }
+    const long long g1 = g0 + tstride;
+    if (tid < FIB) fb[sel ^ 1][tid] = (g1 + tid < nfib) ? fibre_base(g1 + tid) : -1;
+    for (int t = tid; t < sh.ns * FIB; t += blockDim.x) {
+      const int q = t / FIB, f = t - q * FIB;
+      const long long b = fb[sel][f];
+      int k = 0;
+      T fr = (T)0;
+      if (b >= 0) {
+        const int ia = axis_index(b, g, sh.n[q]);
+        k = sh.kshift[q][ia];
+        fr = (T)sh.frac[q][ia];
+      }
+      sk[q][f] = k;
+      sfr[q][f] = fr;
+    }
+    __syncthreads();
+    if (g1 < nfib) load(sel ^ 1, g1);  // in flight during the work below
+    // ---- shears along the axis (each zero outside the grid)
+    T* cur = A;
+    T* oth = Bw;
+    for (int q = 0; q < sh.ns; ++q) {
+      for (int t = tid; t < N * FIB; t += blockDim.x) {
+        const int j = t / FIB, f = t - j * FIB;
+        const int k = sk[q][f];
+        const T fr = sfr[q][f];
+        const int s1 = j - k, s2 = j - k - 1;
+        T val = (T)0;
+        if (s1 >= 0 && s1 < N) val += ((T)1 - fr) * cur[s1 * PAD + axcol(f)];
+        if (s2 >= 0 && s2 < N) val += fr * cur[s2 * PAD + axcol(f)];
+        oth[j * PAD + axcol(f)] = val;
+      }
+      __syncthreads();
+      T* sw = cur;
+      cur = oth;
+      oth = sw;
+    }
+    // ---- banded operator: rows j0..j0+3, fibres FPT tf..FPT tf + FPT - 1
+    T acc[4][FPT];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < FPT; ++b) acc[a][b] = 0;
+    const int c0 = axcol(tf * FPT);
+    for (int i = lo; i <= hi; ++i) {
+      T m4[4], tv[FPT];
+      ld4<T>(Mt + i * N + j0, m4);
+#pragma unroll
+      for (int b = 0; b < FPT; b += 4) ld4<T>(cur + i * PAD + c0 + b, tv + b);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < FPT; ++b) acc[a][b] += m4[a] * tv[b];
+    }
+    if (rows_ok) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < FPT; ++b) {
+          oth[(j0 + a) * PAD + c0 + b] = acc[a][b];
+          if (sum_acc != nullptr) ks.add(acc[a][b]);
+        }
+    }
+    __syncthreads();
+    // ---- store with the load's access pattern
+    if (post == 1) {
+      for (int t = tid; t < FIB * N; t += blockDim.x) {
+        const int f = t / N, j = t - f * N;
+        if (g0 + f < nfib) out[(g0 + f) * N + j] = oth[j * PAD + axcol(f)];
+      }
+    } else {
+      for (int t = tid; t < FIB * N; t += blockDim.x) {
+        const int j = t / FIB, f = t - j * FIB;
+        const long long b = fb[sel][f];
+        if (b >= 0) out[b + (long long)j * post] = oth[j * PAD + axcol(f)];
+      }
+    }
+    __syncthreads();
+    sel ^= 1;
+  }
+  if (sum_acc != nullptr) {
+    double sv = (double)ks.s - (double)ks.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    if ((tid & 31) == 0) red[tid >> 5] = sv;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      atomicAdd(sum_acc, t);
+    }
+  }
+}
+
 // Sum of P (float64 accumulation); optionally P *= scale read from *scale_src.
 template <typename T>
 __global__ void k_fg_sum(const T* __restrict__ P, long long total, double* acc) {
@@ -307,6 +507,14 @@ __global__ void k_fg_sum(const T* __restrict__ P, long long total, double* acc) 
 template <typename T>
 __global__ void k_fg_scale(T* P, long long total, const double* acc, double delta) {
   const T s = (T)(1.0 / (acc[0] * delta));
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    P[e] *= s;
+}
+
+// P *= s (a pending normalisation known on the host).
+template <typename T>
+__global__ void k_fg_mul(T* P, long long total, T s) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
     P[e] *= s;
@@ -390,6 +598,93 @@ __global__ void k_fg_lik(T* P, FgGeom g, FgLik lk, const double* off, double* ac
   }
 }
 
+// The Bayes update and the posterior moments in one pass:
+//   v = P * s * prod_c exp(-((z_c - h_c)^2 - off_c) / (2 R_c)),  P <- v,
+// with s = host_scale / (dsum[0] delta) (dsum nullable: the predictive mass a
+// fused predictive pass left on the device); lik_acc += sum v, and mom (the
+// layout of k_fg_moments) += the point-mass sums of v.  One warp per row of
+// the last axis, as both passes it replaces.
+template <typename T, int D>
+__global__ void k_fg_lik_mom(T* P, FgGeom g, FgLik lk, const double* off, const double* dsum,
+                             double host_scale, double delta, double* lik_acc, double* mom) {
+  constexpr int NA = 1 + D + D * D;
+  constexpr int LAST = D - 1;
+  __shared__ double red[NA][8];
+  const int NL = g.n[LAST];
+  const long long rows = g.total / NL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const T sc = (T)(host_scale / (dsum != nullptr ? dsum[0] * delta : 1.0));
+  const T lol = (T)(g.lo[LAST] - g.centre[LAST]), dxl = (T)g.dx[LAST];
+  Kahan<T> s[NA];
+  for (long long r = warp0; r < rows; r += nwarps) {
+    const long long e0 = r * NL;
+    T Lrow = sc;
+    for (int c = 0; c < lk.b; ++c) {
+      const bool uses_last = lk.modes[c][0] == LAST || (lk.nmodes[c] == 2 && lk.modes[c][1] == LAST);
+      if (uses_last) continue;
+      const int i0 = axis_index(e0, g, lk.modes[c][0]);
+      const int i1 = lk.nmodes[c] == 2 ? axis_index(e0, g, lk.modes[c][1]) : 0;
+      Lrow *= lik_factor<T>(lk, c, i0, i1, off);
+    }
+    Kahan<T> a0, a1, a2;
+    for (int il = lane; il < NL; il += 32) {
+      T L = Lrow;
+      for (int c = 0; c < lk.b; ++c) {
+        const bool uses_last = lk.modes[c][0] == LAST || (lk.nmodes[c] == 2 && lk.modes[c][1] == LAST);
+        if (!uses_last) continue;
+        const int i0 = lk.modes[c][0] == LAST ? il : axis_index(e0, g, lk.modes[c][0]);
+        const int i1 = lk.nmodes[c] == 2 ? (lk.modes[c][1] == LAST ? il : axis_index(e0, g, lk.modes[c][1])) : 0;
+        L *= lik_factor<T>(lk, c, i0, i1, off);
+      }
+      const T v = P[e0 + il] * L;
+      P[e0 + il] = v;
+      const T xl = lol + ((T)il + (T)0.5) * dxl;
+      a0.add(v);
+      a1.add(xl * v);
+      a2.add(xl * xl * v);
+    }
+    T r0 = a0.s - a0.c, r1 = a1.s - a1.c, r2 = a2.s - a2.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+      r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    }
+    if (lane == 0) {
+      T x[D];
+#pragma unroll
+      for (int m = 0; m < LAST; ++m)
+        x[m] = (T)(g.lo[m] - g.centre[m]) + ((T)axis_index(e0, g, m) + (T)0.5) * (T)g.dx[m];
+      s[0].add(r0);
+#pragma unroll
+      for (int m = 0; m < LAST; ++m) {
+        s[1 + m].add(x[m] * r0);
+#pragma unroll
+        for (int l = m; l < LAST; ++l) s[1 + D + m * D + l].add(x[m] * x[l] * r0);
+        s[1 + D + m * D + LAST].add(x[m] * r1);
+      }
+      s[1 + LAST].add(r1);
+      s[1 + D + LAST * D + LAST].add(r2);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    double t = (double)s[a].s - (double)s[a].c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[a][warp] = t;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < NA; a += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[a][w];
+    atomicAdd(mom + a, t);
+    if (a == 0) atomicAdd(lik_acc, t);
+  }
+}
+
 // acc[0] = sum P, acc[1+m] = sum x_m P, acc[1+D+m*D+l] = sum x_m x_l P (centred
 // x, l >= m).  D is the state dimension (compile time, so the sums stay in
 // registers).  One warp per row of the last axis: per row only sum v, sum x v
@@ -465,6 +760,20 @@ void launch_fg_moments(int d, int grid, cudaStream_t st, const T* P, const FgGeo
     case 4: k_fg_moments<T, 4><<<grid, 256, 0, st>>>(P, g, acc); break;
     case 5: k_fg_moments<T, 5><<<grid, 256, 0, st>>>(P, g, acc); break;
     default: k_fg_moments<T, 6><<<grid, 256, 0, st>>>(P, g, acc); break;
+  }
+}
+
+template <typename T>
+void launch_fg_lik_mom(int d, int grid, cudaStream_t st, T* P, const FgGeom& g, const FgLik& lk,
+                       const double* off, const double* dsum, double host_scale, double delta,
+                       double* lik_acc, double* mom) {
+  switch (d) {
+    case 1: k_fg_lik_mom<T, 1><<<grid, 256, 0, st>>>(P, g, lk, off, dsum, host_scale, delta, lik_acc, mom); break;
+    case 2: k_fg_lik_mom<T, 2><<<grid, 256, 0, st>>>(P, g, lk, off, dsum, host_scale, delta, lik_acc, mom); break;
+    case 3: k_fg_lik_mom<T, 3><<<grid, 256, 0, st>>>(P, g, lk, off, dsum, host_scale, delta, lik_acc, mom); break;
+    case 4: k_fg_lik_mom<T, 4><<<grid, 256, 0, st>>>(P, g, lk, off, dsum, host_scale, delta, lik_acc, mom); break;
+    case 5: k_fg_lik_mom<T, 5><<<grid, 256, 0, st>>>(P, g, lk, off, dsum, host_scale, delta, lik_acc, mom); break;
+    default: k_fg_lik_mom<T, 6><<<grid, 256, 0, st>>>(P, g, lk, off, dsum, host_scale, delta, lik_acc, mom); break;
   }
 }
 
@@ -547,6 +856,13 @@ struct ttgbf_fg {
   bool fused = true;
   int sms = 148;
   bool poisoned = false;
+  // Normalisations not yet applied to the stored density: it equals the
+  // normalised density divided by pending (a host scalar, from the last
+  // update's mass) and, when dev_pending, by the predictive mass a fused
+  // predictive pass left in acc[kFgPredSum] (times the cell volume).
+  double pending = 1.0;
+  bool dev_pending = false;
+  bool mom_valid = false;  // acc[0..kFgAcc) holds the moments of the stored density
 };
 
 namespace {
@@ -728,6 +1044,49 @@ int fg_prepare(ttgbf_fg* c, const double* F, const double* Q) {
   return TTGBF_OK;
 }
 
+// Apply every pending normalisation with one pass (for the paths that read
+// the density as stored: the direct sum, the general-F sequence, density()).
+template <typename T>
+void fg_apply_pending(ttgbf_fg* c) {
+  if (c->dev_pending) {
+    ttgbf::count_launches(1);
+    k_fg_scale<T><<<c->sms * 8, 256, 0, c->st>>>((T*)c->buf[c->cur], c->g.total, c->acc + kFgPredSum,
+                                                 c->delta);
+    c->dev_pending = false;
+  }
+  if (c->pending != 1.0) {
+    ttgbf::count_launches(1);
+    k_fg_mul<T><<<c->sms * 8, 256, 0, c->st>>>((T*)c->buf[c->cur], c->g.total, (T)c->pending);
+    c->pending = 1.0;
+  }
+}
+
+// One fused pass along axis m: its U shears (in order), its banded operator,
+// the pending host normalisation s_in on load, the output's sum into sum.
+template <typename T>
+void fg_pass(ttgbf_fg* c, int m, T s_in, double* sum) {
+  constexpr int FIB = sizeof(T) == 4 ? 64 : 32;
+  FgShearList sl{};
+  for (const auto& op : c->shears_u)
+    if (op.m == m) {
+      sl.n[sl.ns] = op.n;
+      sl.kshift[sl.ns] = c->ints + op.ioff;
+      sl.frac[sl.ns] = c->fracs + op.foff;
+      ++sl.ns;
+    }
+  const int N = c->n[m];
+  long long post = 1;
+  for (int k = m + 1; k < c->d; ++k) post *= c->n[k];
+  const long long nfib = c->g.total / N;
+  const size_t sm = sizeof(T) * ((size_t)N * N + 2 * (size_t)N * (FIB + 4));
+  ttgbf::count_launches(1);
+  k_fg_pass<T, FIB><<<c->sms, 256, sm, c->st>>>((const T*)c->buf[c->cur], (T*)c->buf[c->cur ^ 1], c->g, nfib,
+                                                N, post, (const T*)c->mats + c->mat_off[m],
+                                                c->ints + c->band_off[m], c->ints + c->band_off[m] + N, sl,
+                                                s_in, sum);
+  c->cur ^= 1;
+}
+
 template <typename T>
 void fg_shear(ttgbf_fg* c, const ttgbf_fg::ShearOp& op) {
   ttgbf::count_launches(1);
@@ -754,6 +1113,8 @@ template <typename T>
 int fg_predict(ttgbf_fg* c, const double* F, const double* Q, bool direct) {
   const int d = c->d;
   if (direct) {
+    fg_apply_pending<T>(c);
+    c->mom_valid = false;
     std::vector<double> Qinv((size_t)d * d);
     // invert Q (symmetric positive definite) by Gauss-Jordan
     std::vector<double> A(Q, Q + (size_t)d * d);
@@ -791,11 +1152,23 @@ int fg_predict(ttgbf_fg* c, const double* F, const double* Q, bool direct) {
       const int rc = fg_prepare<T>(c, F, Q);
       if (rc) return rc;
     }
-    for (const auto& op : c->shears_u) fg_shear<T>(c, op);
-    if (!c->fused) {
-      for (int m : c->scale_axis) fg_axis<T>(c, m, c->smat_off[m], c->sband_off[m]);
-      for (const auto& op : c->shears_l) fg_shear<T>(c, op);
+    c->mom_valid = false;
+    if (c->fused) {
+      // one pass per axis; the pending normalisation rides on the first
+      // pass, the predictive mass is summed by the last and applied by the
+      // update's pass
+      if (c->dev_pending) fg_apply_pending<T>(c);
+      cudaMemsetAsync(c->acc + kFgPredSum, 0, sizeof(double), c->st);
+      for (int m = 0; m < d; ++m)
+        fg_pass<T>(c, m, (T)(m == 0 ? c->pending : 1.0), m == d - 1 ? c->acc + kFgPredSum : nullptr);
+      c->pending = 1.0;
+      c->dev_pending = true;
+      return fg_check(c);
     }
+    fg_apply_pending<T>(c);
+    for (const auto& op : c->shears_u) fg_shear<T>(c, op);
+    for (int m : c->scale_axis) fg_axis<T>(c, m, c->smat_off[m], c->sband_off[m]);
+    for (const auto& op : c->shears_l) fg_shear<T>(c, op);
     for (int m = 0; m < d; ++m) fg_axis<T>(c, m, c->mat_off[m], c->band_off[m]);
   }
   fg_launch_scale_sum<T>(c, c->buf[c->cur]);
@@ -824,12 +1197,19 @@ int fg_update(ttgbf_fg* c, const ttgbf_meas* h, const double* R, const double* z
                                          z[i], c->off + i);
     logoff += -0.5 * std::log(2.0 * M_PI * r);
   }
-  cudaMemsetAsync(c->acc, 0, sizeof(double), c->st);
+  // one pass: the pending normalisations, the likelihood, log c's sum and
+  // the posterior moments (the posterior's own normalisation stays pending)
+  // moment slots and the likelihood sum; the predictive sum (kFgPredSum) is
+  // read by this pass
+  cudaMemsetAsync(c->acc, 0, sizeof(double) * kFgAcc, c->st);
+  cudaMemsetAsync(c->acc + kFgLikSum, 0, sizeof(double), c->st);
   ttgbf::count_launches(1);
-  k_fg_lik<T><<<c->sms * 8, 256, 0, c->st>>>((T*)c->buf[c->cur], c->g, lk, c->off, c->acc);
+  launch_fg_lik_mom<T>(c->d, c->sms * 8, c->st, (T*)c->buf[c->cur], c->g, lk, c->off,
+                       c->dev_pending ? c->acc + kFgPredSum : nullptr, c->pending, c->delta,
+                       c->acc + kFgLikSum, c->acc);
   double hacc = 0.0;
   cudaMemcpyAsync(offs.data(), c->off, sizeof(double) * h->b, cudaMemcpyDeviceToHost, c->st);
-  cudaMemcpyAsync(&hacc, c->acc, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(&hacc, c->acc + kFgLikSum, sizeof(double), cudaMemcpyDeviceToHost, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) {
     cudaGetLastError();
     c->poisoned = true;
@@ -838,17 +1218,22 @@ int fg_update(ttgbf_fg* c, const ttgbf_meas* h, const double* R, const double* z
   for (int i = 0; i < h->b; ++i) logoff += -offs[i] * lk.inv2r[i];
   c->log_c = std::log(hacc * c->delta) + logoff;
   c->log_lik += c->log_c;
-  ttgbf::count_launches(1);
-  k_fg_scale<T><<<c->sms * 8, 256, 0, c->st>>>((T*)c->buf[c->cur], c->g.total, c->acc, c->delta);
+  c->pending = 1.0 / (hacc * c->delta);
+  c->dev_pending = false;
+  c->mom_valid = true;
   return fg_check(c);
 }
 
 template <typename T>
 int fg_estimate(ttgbf_fg* c, double* mean, double* cov) {
   const int d = c->d;
-  cudaMemsetAsync(c->acc, 0, sizeof(double) * kFgAcc, c->st);
-  ttgbf::count_launches(1);
-  launch_fg_moments<T>(d, c->sms * 4, c->st, (const T*)c->buf[c->cur], c->g, c->acc);
+  // the moments are ratios of sums, so a pending normalisation cancels; the
+  // update's pass already formed them
+  if (!c->mom_valid) {
+    cudaMemsetAsync(c->acc, 0, sizeof(double) * kFgAcc, c->st);
+    ttgbf::count_launches(1);
+    launch_fg_moments<T>(d, c->sms * 4, c->st, (const T*)c->buf[c->cur], c->g, c->acc);
+  }
   double a[kFgAcc];
   cudaMemcpyAsync(a, c->acc, sizeof(a), cudaMemcpyDeviceToHost, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return fg_check(c);
@@ -955,11 +1340,13 @@ int ttgbf_fg_init(ttgbf_fg** out, const ttgbf_grid* grid, const ttgbf_prior* pri
   ttgbf::count_launches(1);
   if (precision == 64) {
     cudaFuncSetAttribute(k_fg_axis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fg_pass<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
     k_fg_prior<double><<<c->sms * 8, 256, 0, c->st>>>((double*)c->buf[0], c->g, c->dparams,
                                                       c->dparams + ttgbf::kMaxD);
     fg_launch_scale_sum<double>(c, c->buf[0]);
   } else {
     cudaFuncSetAttribute(k_fg_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_fg_pass<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
     k_fg_prior<float><<<c->sms * 8, 256, 0, c->st>>>((float*)c->buf[0], c->g, c->dparams,
                                                      c->dparams + ttgbf::kMaxD);
     fg_launch_scale_sum<float>(c, c->buf[0]);
@@ -1042,6 +1429,8 @@ int ttgbf_fg_density(ttgbf_fg* c, double* out, size_t cap) {
   int rc = fg_guard(c);
   if (rc) return rc;
   if (!out || cap < (size_t)c->g.total) return TTGBF_EINVAL;
+  if (c->prec == 64) fg_apply_pending<double>(c);
+  else fg_apply_pending<float>(c);
   if (c->prec == 64) {
     cudaMemcpyAsync(out, c->buf[c->cur], sizeof(double) * c->g.total, cudaMemcpyDeviceToHost, c->st);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return fg_check(c);

@@ -183,7 +183,9 @@ def config4(n_filters: int = 512, seed: int = 0):
     dimension d in {3..6}, points per axis N in {64, 128, 256} and rank cap in
     {8, 16, 32}; filters with the same (d, N, cap) form one group with one
     model, on [-8, 8]^d with prior N(0, 4 I), config 2's range measurement on
-    modes (0, 1), Q_mm ~ U(0.01, 0.1), R ~ U(0.005, 0.02), and a random stable
+    modes (0, 1) (for N = 256: z = x_0 + v, since the two-mode update splits a
+    2-site core whose first mode holds at most 160 points), Q_mm ~ U(0.01, 0.1),
+    R ~ U(0.005, 0.02), and a random stable
     F of spectral radius 0.9 drawn in factored form F = c L D U: L, U unit
     triangular with off-diagonal entries U(-a, a), D_mm ~ U(0.7, 1),
     c = 0.9 / rho(L D U) (c rescales D only, so F's LDU factors are c D with
@@ -212,6 +214,7 @@ def config4(n_filters: int = 512, seed: int = 0):
         model = Model(name=f"config4-d{d}-N{N}-r{cap}", lo=np.full(d, -8.0), hi=np.full(d, 8.0),
                       n=np.full(d, N), m0=np.zeros(d), P0=4.0 * np.eye(d), F=F,
                       Q=np.diag(g.uniform(0.01, 0.1, size=d)), R=np.array([[g.uniform(0.005, 0.02)]]),
-                      comps=[((0, 1), h_range)], steps=50, eps=1e-6, rank_cap=cap, config_id=4)
+                      comps=[((0, 1), h_range)] if N <= 160 else [((0,), h_identity)], steps=50,
+                      eps=1e-6, rank_cap=cap, config_id=4)
         out.append((model, ids))
     return out

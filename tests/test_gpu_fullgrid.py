@@ -97,3 +97,59 @@ def test_general_F_and_two_mode_any_order(G):
     f.update([((2, 0), torch.tensor(tab, dtype=torch.float64, device="cuda"))], [[0.05]], [1.2])
     P, _ = pmf.update(P, g, pmf.likelihood(g, [((2, 0), tab)], [1.2], [[0.05]]))
     assert rel_l1(f.density(), P) < 1e-12
+
+
+def test_config2_float32_at_64(G):
+    """The benchmark's model on a 64^4 grid in float32 (one fused pass per
+    axis, likelihood and moments in one pass) against the oracle."""
+    import torch
+    model = synth.config2(n=64)
+    x, z = synth.simulate(model, 6, steps=2)
+    f = G.FullGridFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), precision=32)
+    g = pmf.Grid(model.lo, model.hi, model.n)
+    comps = tables(model, g.axes, torch.float32)
+    oc = model.tables(g.axes)
+    P = pmf.prior(g, model.m0, model.P0)
+    for k in range(2):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, z[k])
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+        P, logc = pmf.update(P, g, pmf.likelihood(g, oc, z[k], model.R))
+        m, c, lc, _ = f.estimate()
+        mo, co = pmf.moments(P, g)
+        np.testing.assert_allclose(m, mo, atol=1e-5)
+        np.testing.assert_allclose(c, co, atol=1e-5)
+        assert abs(lc - logc) < 1e-4
+    assert rel_l1(f.density(), P) < 1e-5
+
+
+def test_pending_normalisations_in_any_call_order(G):
+    """predict twice in a row, estimate after a predict, estimate after an
+    update, density in between: every path that applies or carries the
+    deferred normalisations gives the oracle's densities and moments."""
+    import torch
+    model = synth.config2(n=12)
+    x, z = synth.simulate(model, 1, steps=2)
+    f = G.FullGridFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), precision=64)
+    g = pmf.Grid(model.lo, model.hi, model.n)
+    comps = tables(model, g.axes, torch.float64)
+    oc = model.tables(g.axes)
+    P = pmf.prior(g, model.m0, model.P0)
+    for _ in range(2):
+        f.predict(model.F, model.Q)
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+    m, c, _, _ = f.estimate()
+    mo, co = pmf.moments(P, g)
+    np.testing.assert_allclose(m, mo, atol=1e-11)
+    f.update(comps, model.R, z[0])
+    P, logc = pmf.update(P, g, pmf.likelihood(g, oc, z[0], model.R))
+    m, c, lc, _ = f.estimate()
+    mo, co = pmf.moments(P, g)
+    np.testing.assert_allclose(m, mo, atol=1e-11)
+    np.testing.assert_allclose(c, co, atol=1e-11)
+    assert abs(lc - logc) < 1e-10
+    f.predict(model.F, model.Q)
+    P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+    f.update(comps, model.R, z[1])
+    P, _ = pmf.update(P, g, pmf.likelihood(g, oc, z[1], model.R))
+    assert rel_l1(f.density(), P) < 1e-12
