@@ -352,6 +352,13 @@ uint64_t ttgbf_group_graph_kernels(const ttgbf_group* g);
  * Synchronises; TTGBF_EINVAL when no step was timed (graph launches are not). */
 int ttgbf_group_times(ttgbf_group* g, float* ms);
 
+/* Per step of the recorded horizon and per context (host array of steps x n
+ * floats, step-major): milliseconds from the start of that step in the last
+ * launch of the graph to the end of that context's work in it (event nodes
+ * recorded with the graph).  Synchronises; TTGBF_EINVAL when no graph was
+ * launched. */
+int ttgbf_group_graph_times(ttgbf_group* g, float* ms);
+
 int ttgbf_group_free(ttgbf_group* g);
 
 /* Launch-configuration autotuner.  For the batch shape of *base (grid,

@@ -37,7 +37,7 @@ EXPORTED = [
     "ttgbf_fg_init", "ttgbf_fg_predict", "ttgbf_fg_predict_direct", "ttgbf_fg_update",
     "ttgbf_fg_estimate", "ttgbf_fg_density", "ttgbf_fg_free", "ttgbf_group_create",
     "ttgbf_group_step", "ttgbf_group_capture", "ttgbf_group_launch", "ttgbf_group_graph_kernels",
-    "ttgbf_group_times", "ttgbf_group_free", "ttgbf_autotune",
+    "ttgbf_group_times", "ttgbf_group_graph_times", "ttgbf_group_free", "ttgbf_autotune",
 ]
 
 
@@ -151,6 +151,7 @@ def load() -> ctypes.CDLL:
     lib.ttgbf_group_graph_kernels.restype = ctypes.c_uint64
     lib.ttgbf_group_graph_kernels.argtypes = [VP]
     lib.ttgbf_group_times.argtypes = [VP, P(ctypes.c_float)]
+    lib.ttgbf_group_graph_times.argtypes = [VP, P(ctypes.c_float)]
     lib.ttgbf_group_free.argtypes = [VP]
     lib.ttgbf_autotune.argtypes = [P(Grid), P(Prior), P(Opts), dp, dp, ctypes.c_int32, ctypes.c_char_p,
                                    P(Opts), dp]
@@ -470,6 +471,7 @@ class TTFilterGroup:
     def capture(self, models, steps):
         arr, keep = self._args(models)
         _check(self._lib.ttgbf_group_capture(self._g, arr, int(steps)), "ttgbf_group_capture")
+        self._horizon = int(steps)
 
     def launch(self):
         _check(self._lib.ttgbf_group_launch(self._g), "ttgbf_group_launch")
@@ -482,6 +484,14 @@ class TTFilterGroup:
         ms = (ctypes.c_float * len(self.filters))()
         _check(self._lib.ttgbf_group_times(self._g, ms), "ttgbf_group_times")
         return list(ms)
+
+    def graph_times(self):
+        """Per step of the last graph launch and per filter batch: ms from the
+        step's start to the batch's end of it (steps x batches array)."""
+        H, n = getattr(self, "_horizon", 0), len(self.filters)
+        ms = (ctypes.c_float * max(1, H * n))()
+        _check(self._lib.ttgbf_group_graph_times(self._g, ms), "ttgbf_group_graph_times")
+        return np.array(ms[:H * n], dtype=np.float64).reshape(H, n)
 
     def free(self):
         if getattr(self, "_g", None) is not None and self._g.value:

@@ -1928,6 +1928,12 @@ struct ttgbf_group {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned long long graph_kernels = 0;
+  // timing of a recorded horizon: event nodes at every step's start (group
+  // stream) and at the end of every leaf's step, read after a launch
+  std::vector<cudaEvent_t> gev_t0;   // per step
+  std::vector<cudaEvent_t> gev_end;  // per step x leaf
+  int graph_steps = 0;
+  bool graph_ran = false;
 };
 
 namespace {
@@ -1957,6 +1963,7 @@ int group_validate(ttgbf_ctx* c, const ttgbf_group_step_args& a) {
 int group_enqueue(ttgbf_group* g, const ttgbf_group_step_args* args, long long t) {
   const size_t nl = g->leaves.size();
   if (!g->capturing) cudaEventRecord(g->ev_t0, g->st);
+  else cudaEventRecordWithFlags(g->gev_t0[t], g->st, cudaEventRecordExternal);
   cudaEventRecord(g->ev_fork, g->st);
   for (ttgbf_ctx* q : g->leaves) cudaStreamWaitEvent(q->st, g->ev_fork, 0);
   // predict
@@ -2013,6 +2020,7 @@ int group_enqueue(ttgbf_group* g, const ttgbf_group_step_args* args, long long t
   }
   for (size_t l = 0; l < nl; ++l) {
     if (!g->capturing) cudaEventRecord(g->ev_tend[l], g->leaves[l]->st);
+    else cudaEventRecordWithFlags(g->gev_end[t * nl + l], g->leaves[l]->st, cudaEventRecordExternal);
     cudaEventRecord(g->ev_join[l], g->leaves[l]->st);
     cudaStreamWaitEvent(g->st, g->ev_join[l], 0);
   }
@@ -2126,6 +2134,12 @@ static void group_drop_graph(ttgbf_group* g) {
   g->exec = nullptr;
   g->graph = nullptr;
   g->graph_kernels = 0;
+  for (cudaEvent_t e : g->gev_t0) cudaEventDestroy(e);
+  for (cudaEvent_t e : g->gev_end) cudaEventDestroy(e);
+  g->gev_t0.clear();
+  g->gev_end.clear();
+  g->graph_steps = 0;
+  g->graph_ran = false;
 }
 
 int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32_t steps) {
@@ -2153,6 +2167,12 @@ int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32
     if (cudaStreamSynchronize(q->st) != cudaSuccess) return group_fail(g);
   if (cudaStreamSynchronize(g->st) != cudaSuccess) return group_fail(g);
   group_drop_graph(g);
+  g->gev_t0.assign((size_t)steps, nullptr);
+  g->gev_end.assign((size_t)steps * g->leaves.size(), nullptr);
+  for (cudaEvent_t& e : g->gev_t0)
+    if (cudaEventCreate(&e) != cudaSuccess) return group_fail(g);
+  for (cudaEvent_t& e : g->gev_end)
+    if (cudaEventCreate(&e) != cudaSuccess) return group_fail(g);
   std::vector<LeafState> before;
   for (ttgbf_ctx* q : g->leaves) before.push_back(leaf_state(q));
   const unsigned long long l0 = g_launches.load();
@@ -2196,6 +2216,7 @@ int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32
   }
   g->graph = graph;
   g->graph_kernels = recorded;
+  g->graph_steps = steps;
   return TTGBF_OK;
 }
 
@@ -2208,6 +2229,7 @@ int ttgbf_group_launch(ttgbf_group* g) {
     return group_fail(g);
   }
   g_launches.fetch_add(g->graph_kernels);
+  g->graph_ran = true;
   return TTGBF_OK;
 }
 
@@ -2225,6 +2247,25 @@ int ttgbf_group_times(ttgbf_group* g, float* ms) {
       return group_fail(g);
     }
     ms[g->owner[l]] = std::max(ms[g->owner[l]], e);
+  }
+  return TTGBF_OK;
+}
+
+int ttgbf_group_graph_times(ttgbf_group* g, float* ms) {
+  if (!g || !ms || !g->exec || !g->graph_ran) return TTGBF_EINVAL;
+  const size_t nl = g->leaves.size(), nc = g->ctxs.size();
+  for (int t = 0; t < g->graph_steps; ++t) {
+    for (size_t i = 0; i < nc; ++i) ms[(size_t)t * nc + i] = 0.f;
+    for (size_t l = 0; l < nl; ++l) {
+      float e = 0.f;
+      cudaEvent_t end = g->gev_end[(size_t)t * nl + l];
+      if (cudaEventSynchronize(end) != cudaSuccess || cudaEventElapsedTime(&e, g->gev_t0[t], end) != cudaSuccess) {
+        cudaGetLastError();
+        return group_fail(g);
+      }
+      float& m = ms[(size_t)t * nc + g->owner[l]];
+      m = std::max(m, e);
+    }
   }
   return TTGBF_OK;
 }

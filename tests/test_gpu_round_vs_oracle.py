@@ -239,7 +239,7 @@ def test_one_step_matches_oracle_tt_step(G, n, cap, mc, k, precision):
     _compare_step(G, model, X, z, cap, smax, precision=precision)
 
 
-@pytest.mark.parametrize("n,cap,smax,precision", [(32, 53, 3, "fp32"), (64, 53, 3, "fp32"),
+@pytest.mark.parametrize("n,cap,smax,precision", [(32, 53, 3, "fp32"), (64, 80, 2, "fp32"),
                                                    (32, 53, 3, "fp64")])
 def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax, precision):
     model = synth.config2(n=n)
