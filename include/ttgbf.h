@@ -457,6 +457,57 @@ int ttgbf_moments_noalloc(int32_t batch, const ttgbf_grid* grid, const float* co
                           const int64_t* core_stride, const int32_t* ranks, int32_t rank_max,
                           double* mass, double* mean, double* cov, void* stream);
 
+/* ---------------------------------------------------------------- adjoint
+ * Gradient of the log-likelihood l_b = sum_k log c_k (Eq. pmf_filtrace_b) of
+ * every filter b of a context with respect to F, the diagonal of Q and the
+ * diagonal of R, by a reverse pass over recorded steps with the truncation
+ * bases of the forward pass held fixed (each rounding acts as the orthogonal
+ * projection onto its output's left interface; the gradient of the TT filter
+ * without the movement of those bases).  Use:
+ *   ttgbf_adj_create(&a, ctx, S, n)         S steps per recorded segment, n checkpoints
+ *   forward: before every segment s, ttgbf_adj_save(a, s); run the steps
+ *   reverse: ttgbf_adj_reset(a); for s = n-1 .. 0:
+ *              ttgbf_adj_load(a, s); ttgbf_adj_record(a, 1); run segment s
+ *              again (same F, Q, R, z); ttgbf_adj_record(a, 0);
+ *              ttgbf_adj_backward(a)
+ *   ttgbf_adj_grads(a, dF, dQ, dR, b)
+ * The context must be a single part (opts.parts = 1) with d >= 2; F, Q stay
+ * fixed over the run; every shear must fit the expansion capacity (a wider
+ * one, applied in pieces, makes the recording fail: ttgbf_adj_backward
+ * returns TTGBF_ECAPACITY).  Coefficients of L and U that are exactly 0 and
+ * scalings exactly 1 are not applied by the filter, so their gradient
+ * entries carry no contribution from them.  Device memory: the recording
+ * holds about 3 d^2 compact snapshots of the batch per step. */
+typedef struct ttgbf_adj ttgbf_adj;
+
+/* steps: most steps recorded between ttgbf_adj_record(1) and (0); slots:
+ * checkpoints.  TTGBF_EINVAL for a split context or d < 2. */
+int ttgbf_adj_create(ttgbf_adj** out, ttgbf_ctx* ctx, int32_t steps, int32_t slots);
+int ttgbf_adj_free(ttgbf_adj* a);
+/* Zero the adjoint state and the accumulated gradients (synchronises). */
+int ttgbf_adj_reset(ttgbf_adj* a);
+/* Save / restore the context's filter state (cores, ranks, log-likelihood,
+ * canonical form) in checkpoint slot `slot` (asynchronous). */
+int ttgbf_adj_save(ttgbf_adj* a, int32_t slot);
+int ttgbf_adj_load(ttgbf_adj* a, int32_t slot);
+/* on = 1: record the context's next predict / update calls (clears the
+ * recording); on = 0: stop. */
+int ttgbf_adj_record(ttgbf_adj* a, int32_t on);
+/* Run the recording backwards, carrying the adjoint state from the later
+ * segment (asynchronous after a short host upload of the operator tables). */
+int ttgbf_adj_backward(ttgbf_adj* a);
+/* Accumulated gradients per filter (host arrays): dF [batch][d][d],
+ * dQ [batch][d] (dl/dQ_mm), dR [batch][nR] (dl/dR_cc for measurement
+ * components 0..nR-1).  Synchronises; TTGBF_ECAPACITY if a rank of the
+ * reverse pass outgrew its bound. */
+int ttgbf_adj_grads(ttgbf_adj* a, double* dF, double* dQ, double* dR, int32_t nR);
+/* Host-only: G_F = dl/dF from the gradients with respect to the strictly
+ * lower part of L (GL, d x d), the diagonal D (GD, d) and the strictly upper
+ * part of U (GU, d x d) of F = L D U (no pivoting).  TTGBF_ESINGULAR if F has
+ * no such factorisation. */
+int ttgbf_ldu_adjoint(int32_t d, const double* F, const double* GL, const double* GD, const double* GU,
+                      double* GF);
+
 #ifdef __cplusplus
 }
 #endif

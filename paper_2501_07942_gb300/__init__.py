@@ -38,6 +38,8 @@ EXPORTED = [
     "ttgbf_fg_estimate", "ttgbf_fg_density", "ttgbf_fg_free", "ttgbf_group_create",
     "ttgbf_group_step", "ttgbf_group_capture", "ttgbf_group_launch", "ttgbf_group_graph_kernels",
     "ttgbf_group_times", "ttgbf_group_graph_times", "ttgbf_group_free", "ttgbf_autotune",
+    "ttgbf_adj_create", "ttgbf_adj_free", "ttgbf_adj_reset", "ttgbf_adj_save", "ttgbf_adj_load",
+    "ttgbf_adj_record", "ttgbf_adj_backward", "ttgbf_adj_grads", "ttgbf_ldu_adjoint",
 ]
 
 
@@ -155,6 +157,13 @@ def load() -> ctypes.CDLL:
     lib.ttgbf_group_free.argtypes = [VP]
     lib.ttgbf_autotune.argtypes = [P(Grid), P(Prior), P(Opts), dp, dp, ctypes.c_int32, ctypes.c_char_p,
                                    P(Opts), dp]
+    lib.ttgbf_adj_create.argtypes = [P(VP), VP, ctypes.c_int32, ctypes.c_int32]
+    for name in ("ttgbf_adj_free", "ttgbf_adj_reset", "ttgbf_adj_backward"):
+        getattr(lib, name).argtypes = [VP]
+    for name in ("ttgbf_adj_save", "ttgbf_adj_load", "ttgbf_adj_record"):
+        getattr(lib, name).argtypes = [VP, ctypes.c_int32]
+    lib.ttgbf_adj_grads.argtypes = [VP, dp, dp, dp, ctypes.c_int32]
+    lib.ttgbf_ldu_adjoint.argtypes = [ctypes.c_int32, dp, dp, dp, dp, dp]
     _lib = lib
     return lib
 
@@ -531,3 +540,145 @@ def autotune(lo, hi, n, prior_mean, prior_var, F, Q, batch=1, rank_cap=16, eps=1
     _check(rc, "ttgbf_autotune")
     return {"parts": best.parts, "tsqr_slice_blocks": best.tsqr_slice_blocks,
             "svd_threads": best.svd_threads}, ms.value
+
+
+def ldu_adjoint(F, GL, GD, GU):
+    """ttgbf_ldu_adjoint (host only): dl/dF from the gradients with respect to
+    the strictly lower L, the diagonal D and the strictly upper U of F = L D U."""
+    F, GL, GD, GU = _f64(F), _f64(GL), _f64(GD), _f64(GU)
+    d = F.shape[0]
+    out = np.zeros((d, d))
+    _check(load().ttgbf_ldu_adjoint(d, _dptr(F), _dptr(GL), _dptr(GD), _dptr(GU), _dptr(out)),
+           "ttgbf_ldu_adjoint")
+    return out
+
+
+class Adjoint:
+    """Reverse pass of a TTFilter batch (``ttgbf_adj_*``): checkpoints of the
+    filter state, recording of segments of steps and the backward sweep with
+    frozen truncation bases."""
+
+    def __init__(self, filt, steps, slots):
+        self._lib = load()
+        self.filt = filt
+        self._a = ctypes.c_void_p()
+        _check(self._lib.ttgbf_adj_create(ctypes.byref(self._a), filt._ctx, int(steps), int(slots)),
+               "ttgbf_adj_create")
+
+    def reset(self):
+        _check(self._lib.ttgbf_adj_reset(self._a), "ttgbf_adj_reset")
+
+    def save(self, slot):
+        _check(self._lib.ttgbf_adj_save(self._a, int(slot)), "ttgbf_adj_save")
+
+    def load(self, slot):
+        _check(self._lib.ttgbf_adj_load(self._a, int(slot)), "ttgbf_adj_load")
+
+    def record(self, on):
+        _check(self._lib.ttgbf_adj_record(self._a, 1 if on else 0), "ttgbf_adj_record")
+
+    def backward(self):
+        _check(self._lib.ttgbf_adj_backward(self._a), "ttgbf_adj_backward")
+
+    def grads(self, n_r):
+        B, d = self.filt.batch, self.filt.d
+        dF = np.zeros((B, d, d))
+        dQ = np.zeros((B, d))
+        dR = np.zeros((B, max(1, n_r)))
+        _check(self._lib.ttgbf_adj_grads(self._a, _dptr(dF), _dptr(dQ), _dptr(dR), int(n_r)),
+               "ttgbf_adj_grads")
+        return dF, dQ, dR[:, :n_r]
+
+    def free(self):
+        if getattr(self, "_a", None) is not None and self._a.value:
+            self._lib.ttgbf_adj_free(self._a)
+            self._a = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _run_segment(filt, F, Q, comps, R, z_dev, k0, k1):
+    for k in range(k0, k1):
+        filt.predict(F, Q)
+        filt.update_dev(comps, R, z_dev[k])
+
+
+def _make_loglik_function():
+    import torch
+
+    class _LogLik(torch.autograd.Function):
+        """l_b = sum_k log c_k of every filter of a batch run from its prior
+        over the measurements z (steps, batch, b), as a function of F, q =
+        diag(Q) and r = diag(R); the backward pass is ttgbf_adj_* with
+        checkpoints every `every` steps (each segment recomputed once)."""
+
+        @staticmethod
+        def forward(ctx, F, q, r, spec):
+            Fn = F.detach().cpu().double().numpy()
+            Qn = np.diag(q.detach().cpu().double().numpy())
+            Rn = np.diag(r.detach().cpu().double().numpy())
+            filt = spec["make_filter"]()
+            K, every = spec["z"].shape[0], spec["every"]
+            nseg = -(-K // every)
+            adj = Adjoint(filt, every, nseg)
+            for s in range(nseg):
+                adj.save(s)
+                _run_segment(filt, Fn, Qn, spec["comps"], Rn, spec["z"], s * every, min(K, (s + 1) * every))
+            ll = filt.estimate()[3]
+            ctx.state = (filt, adj, Fn, Qn, Rn, spec, nseg)
+            return torch.tensor(ll, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            filt, adj, Fn, Qn, Rn, spec, nseg = ctx.state
+            K, every = spec["z"].shape[0], spec["every"]
+            adj.reset()
+            for s in range(nseg - 1, -1, -1):
+                adj.load(s)
+                adj.record(True)
+                _run_segment(filt, Fn, Qn, spec["comps"], Rn, spec["z"], s * every, min(K, (s + 1) * every))
+                adj.record(False)
+                adj.backward()
+            dF, dQ, dR = adj.grads(len(spec["comps"]))
+            w = g.detach().cpu().double().numpy()
+            gF = torch.tensor(np.einsum("b,bij->ij", w, dF))
+            gq = torch.tensor(np.einsum("b,bi->i", w, dQ))
+            gr = torch.tensor(np.einsum("b,bi->i", w, dR))
+            adj.free()
+            filt.free()
+            ctx.state = None
+            return gF, gq, gr, None
+
+    return _LogLik
+
+
+_LOGLIK = None
+
+
+def log_likelihood(F, q, r, *, lo, hi, n, prior_mean, prior_var, comps, z, rank_cap=16, eps=1e-6,
+                   max_shift_span=0, precision="fp32", conv="dense", checkpoint_every=20,
+                   device="cuda"):
+    """Differentiable log-likelihood of the TT filter: l_b = sum_k log c_k
+    (Eq. pmf_filtrace_b) of a batch of filters run from the prior over the
+    measurements z (device float32, steps x batch x b), as a torch function of
+    F (d x d), q = diag(Q) and r = diag(R) (float64 CPU tensors).  The
+    gradient comes from the reverse pass (ttgbf_adj_*) with the forward
+    pass's truncation bases held fixed and per-segment checkpoints every
+    `checkpoint_every` steps (each segment is run a second time, recorded,
+    in the backward pass)."""
+    global _LOGLIK
+    if _LOGLIK is None:
+        _LOGLIK = _make_loglik_function()
+    B = int(z.shape[1])
+
+    def make_filter():
+        return TTFilter(lo, hi, n, prior_mean, prior_var, batch=B, rank_cap=rank_cap, eps=eps,
+                        max_shift_span=max_shift_span, device=device, precision=precision, conv=conv,
+                        parts=1)
+
+    spec = {"make_filter": make_filter, "comps": comps, "z": z, "every": int(checkpoint_every)}
+    return _LOGLIK.apply(F, q, r, spec)

@@ -210,6 +210,8 @@ struct Op {
 
 }  // namespace
 
+struct ttgbf_adj;
+
 struct ttgbf_ctx {
   int B = 0, d = 0;
   std::vector<int> n;
@@ -297,6 +299,9 @@ struct ttgbf_ctx {
   cudaEvent_t ev_fork = nullptr;
   // of a part: the share of the GPU's resident QR CTAs it plans for
   double slot_share = 1.0;
+  // reverse pass: while set, predict and update record their steps here
+  ttgbf_adj* tape = nullptr;
+  int tape_op = -1;  // index in ops of the shear being enqueued
 };
 
 namespace {
@@ -376,6 +381,18 @@ void debug_stage_report(ttgbf_ctx* c, int mode, int k, int ka, int kb) {
 // One stage of the rounding sweep: R factor, SVD, rank choice, factor application.
 // With float64 precision the truncating stages (left, split) form R and its
 // SVD in float64 (one TSQR CTA per SM: its shared memory holds a float64 R).
+// Recording of the forward pass for the reverse pass (no-ops unless
+// c->tape is set; defined with the adjoint below).
+enum TapeModeKind : int { kModeConv = 0, kModeScale = 1, kModeConvScale = 2 };
+void tape_shear(ttgbf_ctx* c, int m, int n);
+void tape_proj(ttgbf_ctx* c, int h);
+void tape_mode(ttgbf_ctx* c, int k, int kind);
+void tape_norm(ttgbf_ctx* c, const double* mass);
+void tape_upd_in(ttgbf_ctx* c);
+void tape_lik(ttgbf_ctx* c, int comp, const ttgbf_meas_comp& cp, const float* z, int zstride, double R);
+void tape_logc(ttgbf_ctx* c, const double* mass);
+void tape_fail(ttgbf_ctx* c);
+
 void stage(ttgbf_ctx* c, int mode, int k, int first) {
   const int B = c->B;
   const float* src = (mode == kStageSplit) ? c->W : curp(c, k);
@@ -442,6 +459,7 @@ void enqueue_round(ttgbf_ctx* c) {
   c->expanded = false;
   c->canon = true;
   c->center = c->d - 1;
+  tape_proj(c, c->d - 1);
 }
 
 // Bring the TT into mixed canonical form with its center inside [lo, hi]:
@@ -462,6 +480,7 @@ void enqueue_center_into(ttgbf_ctx* c, int lo, int hi) {
     first = false;
     ++c->center;
   }
+  if (!first) tape_proj(c, c->center);  // the moves truncate links center0..lo-1
 }
 
 MomentArgs tt_moment_args(ttgbf_ctx* c, int with_moments, int scale) {
@@ -493,9 +512,12 @@ void enqueue_normalise(ttgbf_ctx* c, double* mass_out) {
   a.scale_core = curp(c, k);
   a.scale_cap = c->L.core_cap[k];
   a.scale_idx = k;
-  Prof p(c, kPMoments, 1);
-  launch_moments(c->st, c->B, a, c->ranks, c->d + 1, c->awork, c->L.awork_stride, mass_out, nullptr,
-                 nullptr);
+  {
+    Prof p(c, kPMoments, 1);
+    launch_moments(c->st, c->B, a, c->ranks, c->d + 1, c->awork, c->L.awork_stride, mass_out, nullptr,
+                   nullptr);
+  }
+  tape_norm(c, mass_out);
 }
 
 void mode_apply(ttgbf_ctx* c, int k, const float* M) {
@@ -800,6 +822,7 @@ void enqueue_shear_pieces(ttgbf_ctx* c, int m, int n, int S, int tmin, const flo
   const int lo = std::min(m, n), hi = std::max(m, n);
   const int np = (S + c->smax - 1) / c->smax;
   const int Nn = c->n[n];
+  tape_fail(c);  // the reverse pass covers shears within the expansion capacity
   enqueue_center_into(c, lo, hi);
   float* curv[kMaxD];
   float* altv[kMaxD];
@@ -862,7 +885,12 @@ void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts
     return;
   }
   const int lo = std::min(m, n), hi = std::max(m, n);
-  if (do_round) enqueue_center_into(c, lo, hi);
+  if (do_round) {
+    enqueue_center_into(c, lo, hi);
+    tape_shear(c, m, n);
+  } else {
+    tape_fail(c);
+  }
   float* curv[kMaxD];
   float* altv[kMaxD];
   for (int k = 0; k < c->d; ++k) {
@@ -896,6 +924,7 @@ void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts
   for (int k = lo; k <= hi - 1; ++k) stage(c, kStageLeft, k, k == lo);
   c->canon = true;
   c->center = hi;
+  tape_proj(c, hi);
 }
 
 int guard(ttgbf_ctx* c) {
@@ -940,6 +969,7 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
   ops->push_back([=] {
     if (c->expanded) enqueue_round(c);
     cudaMemsetAsync(c->logoff, 0, sizeof(double) * B, c->st);
+    tape_upd_in(c);
   });
   for (int i = 0; i < h->b; ++i) {
     const ttgbf_meas_comp cp = h->comp[i];
@@ -952,6 +982,7 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
       launch_lik_apply_1d(c->st, B, curp(c, k), c->L.core_cap[k], c->n[k], k, d, c->ranks, cp.htab,
                           z, zstride, i, r, c->lik_off);
       if (!(c->canon && c->center == k)) c->canon = false;
+      tape_lik(c, i, cp, z, zstride, r);
     });
   }
   if (two_mode >= 0) {
@@ -975,6 +1006,7 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
         launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, cp.htab, z, zstride,
                             two_mode, r, c->lik_off);
       }
+      tape_lik(c, two_mode, cp, z, zstride, r);
       // log c before rounding: mass of the TT [W (modes 0,1 merged), core 2, ...]
       MomentArgs a{};
       a.ncores = d - 1;
@@ -997,12 +1029,14 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
         Prof p(c, kPOther, 1);
         launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
       }
+      tape_logc(c, c->mass);
     });
     ops->push_back([=] { stage(c, kStageSplit, 0, 1); });
     for (int k = 1; k <= d - 2; ++k) ops->push_back([=] { stage(c, kStageLeft, k, 0); });
     ops->push_back([=] {
       c->canon = true;
       c->center = d - 1;
+      tape_proj(c, d - 1);
     });
   } else {
     ops->push_back([=] {
@@ -1016,6 +1050,7 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
         Prof p(c, kPOther, 1);
         launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
       }
+      tape_logc(c, c->mass);
     });
   }
   ops->push_back([=] { enqueue_normalise(c, c->mass); });
@@ -1098,6 +1133,7 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
     set_tsqr_attributes();
     set_rsvd64_attributes();
     set_fft_attributes();
+    set_adjoint_attributes();
   });
   ttgbf_ctx* c = new (std::nothrow) ttgbf_ctx();
   if (!c) return TTGBF_ENOMEM;
@@ -1390,13 +1426,19 @@ int predict_begin(ttgbf_ctx* c, const double* F, const double* Q) {
 void predict_op(ttgbf_ctx* c, size_t i) {
   const Op& op = c->ops[i];
   if (op.kind == 0) {
+    c->tape_op = (int)i;
     enqueue_shear(c, op.m, op.n, c->op_S[i], c->op_tmin[i], c->opmats + c->op_woff[i], true);
+    c->tape_op = -1;
   } else if (!c->fuse) {
+    tape_mode(c, op.m, kModeScale);
     mode_apply(c, op.m, c->opmats + c->scale_off[op.m]);
   }
 }
 
 void predict_mode(ttgbf_ctx* c, int k) {
+  bool scaled = false;
+  for (const Op& op : c->ops) scaled = scaled || (op.kind == 1 && op.m == k);
+  tape_mode(c, k, (c->fuse && scaled) ? kModeConvScale : kModeConv);
   if (c->mode_fft[k]) mode_conv_fft(c, k);
   else mode_apply(c, k, c->opmats + c->mat_off[k]);
 }
@@ -1704,6 +1746,7 @@ int ttgbf_export_cores(ttgbf_ctx* c, int32_t f, float* buf, size_t cap, int32_t*
 }
 
 int ttgbf_import_cores(ttgbf_ctx* c, int32_t f, const float* buf, const int32_t* ranks, double log_lik) {
+  if (c) tape_fail(c);
   if (split(c)) {
     if (f < 0 || f >= c->B) return TTGBF_EINVAL;
     int local = 0;
@@ -1784,6 +1827,7 @@ int ttgbf_scale(ttgbf_ctx* c, int32_t m, double lam) {
   if (split(c)) return fan_out(c, [&](ttgbf_ctx* q, int) { return ttgbf_scale(q, m, lam); }, false, false);
   int rc = guard(c);
   if (rc) return rc;
+  tape_fail(c);  // single-operation hooks are not part of a recorded step
   if (m < 0 || m >= c->d) return TTGBF_EINVAL;
   if (!std::isfinite(lam)) return TTGBF_ENONFINITE;
   std::vector<std::vector<double>> mats(1);
@@ -1798,6 +1842,7 @@ int ttgbf_convolve(ttgbf_ctx* c, const double* q) {
   if (split(c)) return fan_out(c, [&](ttgbf_ctx* x, int) { return ttgbf_convolve(x, q); }, false, false);
   int rc = guard(c);
   if (rc) return rc;
+  tape_fail(c);
   if (!q) return TTGBF_EINVAL;
   if (!finite_all(q, c->d)) return TTGBF_ENONFINITE;
   for (int k = 0; k < c->d; ++k)
@@ -2440,3 +2485,838 @@ int ttgbf_autotune(const ttgbf_grid* grid, const ttgbf_prior* prior, const ttgbf
 namespace ttgbf {
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
 }  // namespace ttgbf
+
+// ================================================================ adjoint
+// The reverse pass of a run of filter steps: the gradient of the
+// log-likelihood l = sum_k log c_k (Eq. pmf_filtrace_b) with respect to the
+// elementary operators of F = L D U (shear coefficients and scalings), the
+// variances Q_mm and R_cc, with the truncation bases of the forward pass held
+// fixed.  While a tape is attached, predict and update record every step that
+// the reverse pass needs (snapshots of the TT in compact form: ranks are at
+// most rank_cap at every recorded point):
+//   kTShear  the input of a shear (after its canonical-form moves)
+//   kTProj   a truncation sweep that left cores 0..h-1 left-orthonormal: in
+//            the full tensor space it is the orthogonal projection onto the
+//            span of that left interface (x) the rest (nested sweeps reduce
+//            to their last link), so its adjoint is the same projection
+//   kTMode   the input of a per-mode operator (kernel, scaling or both)
+//   kTNorm   a normalisation x = y / m (its output and m)
+//   kTUpdIn  the input of the update
+//   kTLik    a likelihood factor (component, table, z, offset)
+//   kTLogc   the mass c of the update (before its rounding)
+// The reverse pass runs the records backwards on an adjoint TT lambda:
+//   norm:  lambda <- (lambda - delta <lambda, x> 1) / m
+//   proj:  lambda <- P lambda (contraction with the frozen interface)
+//   logc:  lambda <- lambda + (delta / c) 1
+//   lik:   lambda <- Lambda (.) lambda; dl/dR_c = <g_c (.) lambda, w> at the
+//          update's input w, g_c = d log Lambda_c / dR_c
+//   mode:  dl/dtheta = <lambda, (dM/dtheta) y>; lambda <- M^T lambda
+//   shear: dl/da = <lambda, (dS/da) y>; lambda <- S(-a) lambda (S^T = S(-a))
+// and the chain rule through the LDU factorisation gives dl/dF.
+namespace {
+
+enum TapeKind : int { kTShear = 0, kTProj, kTMode, kTNorm, kTUpdIn, kTLik, kTLogc };
+
+struct TapeEntry {
+  int kind = 0;
+  int k = 0;        // proj: h; mode: the mode; shear: m
+  int n = 0;        // shear: n
+  int op = -1;      // shear: index in ops
+  int mkind = 0;    // mode: TapeModeKind
+  size_t snap = 0;  // byte offset of the snapshot in the tape
+  size_t scal = 0;  // byte offset of per-filter doubles (norm, logc) or floats z, off (lik)
+  int comp = -1, nmodes = 0, mode0 = 0;
+  const float* htab = nullptr;
+  double R = 0.0;
+};
+
+struct CkptHost {
+  bool valid = false;
+  bool canon = false, expanded = false;
+  int center = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct ttgbf_adj {
+  ttgbf_ctx* c = nullptr;
+  int B = 0, d = 0, RS = 0, RL = 0, phi_max = 0, chunks = 16, nparams = 0;
+  long long scap[kMaxD] = {};     // snapshot floats per filter per core (rank_cap bound)
+  long long lcap[kMaxD] = {};     // adjoint floats per filter per core
+  size_t snap_cores[kMaxD] = {};  // byte offsets of the cores in a snapshot
+  size_t snap_ranks = 0, snap_bytes = 0, scal_bytes = 0;
+  char* base = nullptr;
+  char* tape = nullptr;
+  size_t tape_cap = 0, tape_used = 0;
+  std::vector<TapeEntry> entries;
+  bool recording = false, failed = false;
+  int nslots = 0;
+  char* ckpt = nullptr;
+  size_t ckpt_bytes = 0;
+  std::vector<CkptHost> ckh;
+  float* lam[2][kMaxD] = {};
+  int lcur[kMaxD] = {};
+  int* lranks = nullptr;
+  float* sA[kMaxD] = {};
+  float* sB[kMaxD] = {};
+  int* sranks = nullptr;
+  float* phi[2] = {};
+  float* part = nullptr;
+  int* err = nullptr;
+  double *val = nullptr, *sc = nullptr, *coef = nullptr, *grad = nullptr;
+  float* mats = nullptr;
+  long long mats_floats = 0;
+};
+
+namespace {
+
+// ---- recording
+char* tape_take(ttgbf_adj* a, size_t bytes, size_t* off) {
+  if (a->failed || a->tape_used + bytes > a->tape_cap) {
+    a->failed = true;
+    return nullptr;
+  }
+  *off = a->tape_used;
+  a->tape_used += align256(bytes);
+  return a->tape + *off;
+}
+
+// Snapshot of the context's TT (compact cores, ranks) at dst.
+void snap_state(ttgbf_adj* a, char* dst) {
+  ttgbf_ctx* c = a->c;
+  for (int k = 0; k < a->d; ++k)
+    cudaMemcpy2DAsync(dst + a->snap_cores[k], sizeof(float) * a->scap[k], curp(c, k),
+                      sizeof(float) * c->L.core_cap[k], sizeof(float) * a->scap[k], a->B,
+                      cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(dst + a->snap_ranks, c->ranks, sizeof(int) * (size_t)a->B * (a->d + 1),
+                  cudaMemcpyDeviceToDevice, c->st);
+}
+
+void tape_push(ttgbf_ctx* c, TapeEntry e, bool with_snap) {
+  ttgbf_adj* a = c->tape;
+  if (with_snap) {
+    char* p = tape_take(a, a->snap_bytes, &e.snap);
+    if (!p) return;
+    snap_state(a, p);
+  }
+  a->entries.push_back(e);
+}
+
+void tape_fail(ttgbf_ctx* c) {
+  if (c->tape) c->tape->failed = true;
+}
+
+void tape_shear(ttgbf_ctx* c, int m, int n) {
+  if (!c->tape) return;
+  if (c->tape_op < 0) {
+    tape_fail(c);
+    return;
+  }
+  TapeEntry e;
+  e.kind = kTShear;
+  e.k = m;
+  e.n = n;
+  e.op = c->tape_op;
+  tape_push(c, e, true);
+}
+
+void tape_proj(ttgbf_ctx* c, int h) {
+  if (!c->tape) return;
+  TapeEntry e;
+  e.kind = kTProj;
+  e.k = h;
+  tape_push(c, e, true);
+}
+
+void tape_mode(ttgbf_ctx* c, int k, int kind) {
+  if (!c->tape) return;
+  TapeEntry e;
+  e.kind = kTMode;
+  e.k = k;
+  e.mkind = kind;
+  tape_push(c, e, true);
+}
+
+void tape_norm(ttgbf_ctx* c, const double* mass) {
+  if (!c->tape) return;
+  ttgbf_adj* a = c->tape;
+  TapeEntry e;
+  e.kind = kTNorm;
+  char* p = tape_take(a, a->scal_bytes, &e.scal);
+  if (!p) return;
+  cudaMemcpyAsync(p, mass, sizeof(double) * a->B, cudaMemcpyDeviceToDevice, c->st);
+  tape_push(c, e, true);
+}
+
+void tape_upd_in(ttgbf_ctx* c) {
+  if (!c->tape) return;
+  TapeEntry e;
+  e.kind = kTUpdIn;
+  tape_push(c, e, true);
+}
+
+void tape_lik(ttgbf_ctx* c, int comp, const ttgbf_meas_comp& cp, const float* z, int zstride, double R) {
+  if (!c->tape) return;
+  ttgbf_adj* a = c->tape;
+  TapeEntry e;
+  e.kind = kTLik;
+  e.comp = comp;
+  e.nmodes = cp.nmodes;
+  e.mode0 = cp.modes[0];
+  e.htab = cp.htab;
+  e.R = R;
+  char* p = tape_take(a, a->scal_bytes, &e.scal);
+  if (!p) return;
+  // z of this component and the factor's offset, per filter (floats)
+  cudaMemcpy2DAsync(p, sizeof(float), z + comp, sizeof(float) * (size_t)zstride, sizeof(float), a->B,
+                    cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(p + sizeof(float) * a->B, c->lik_off, sizeof(float) * a->B, cudaMemcpyDeviceToDevice,
+                  c->st);
+  tape_push(c, e, false);
+}
+
+void tape_logc(ttgbf_ctx* c, const double* mass) {
+  if (!c->tape) return;
+  ttgbf_adj* a = c->tape;
+  TapeEntry e;
+  e.kind = kTLogc;
+  char* p = tape_take(a, a->scal_bytes, &e.scal);
+  if (!p) return;
+  cudaMemcpyAsync(p, mass, sizeof(double) * a->B, cudaMemcpyDeviceToDevice, c->st);
+  tape_push(c, e, false);
+}
+
+// ---- tensor-train views of the reverse pass
+struct TTv {
+  const float* p[kMaxD];
+  long long cap[kMaxD];
+  const int* ranks;
+};
+
+TTv snap_view(const ttgbf_adj* a, size_t snap) {
+  TTv v{};
+  for (int k = 0; k < a->d; ++k) {
+    v.p[k] = reinterpret_cast<const float*>(a->tape + snap + a->snap_cores[k]);
+    v.cap[k] = a->scap[k];
+  }
+  v.ranks = reinterpret_cast<const int*>(a->tape + snap + a->snap_ranks);
+  return v;
+}
+
+TTv lam_view(const ttgbf_adj* a) {
+  TTv v{};
+  for (int k = 0; k < a->d; ++k) {
+    v.p[k] = a->lam[a->lcur[k]][k];
+    v.cap[k] = a->lcap[k];
+  }
+  v.ranks = a->lranks;
+  return v;
+}
+
+float* lam_cur(ttgbf_adj* a, int k) { return a->lam[a->lcur[k]][k]; }
+float* lam_alt(ttgbf_adj* a, int k) { return a->lam[a->lcur[k] ^ 1][k]; }
+
+// Left environments of X and Y over cores [0, kend); returns the index of
+// the buffer holding Phi_kend.  With kend = d the scalar <X, Y> goes to scal.
+int env_left(ttgbf_adj* a, const TTv& X, const TTv& Y, int kend, double* scal, double mul, int acc) {
+  ttgbf_ctx* c = a->c;
+  int cur = 0;
+  for (int k = 0; k < kend; ++k) {
+    launch_env_step(c->st, a->B, k, c->n[k], X.p[k], X.cap[k], X.ranks, Y.p[k], Y.cap[k], Y.ranks, a->d + 1,
+                    a->phi[cur], a->phi_max, a->part, a->chunks, a->phi_max, a->err);
+    launch_env_reduce(c->st, a->B, k, X.ranks, Y.ranks, a->d + 1, a->part, a->chunks, a->phi_max,
+                      a->phi[cur ^ 1], a->phi_max, k == a->d - 1 ? scal : nullptr, mul, acc);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+void inner(ttgbf_adj* a, const TTv& X, const TTv& Y) { env_left(a, X, Y, a->d, a->val, 1.0, 0); }
+
+void add_grad(ttgbf_adj* a, int gi) {
+  launch_scalars(a->c->st, a->B, 2, nullptr, a->val, 0.0, nullptr, nullptr, a->grad, a->nparams, gi, 1.0);
+}
+
+// lambda <- P lambda with P the projection onto the interface U_{<h} of U.
+void project(ttgbf_adj* a, const TTv& U, int h) {
+  ttgbf_ctx* c = a->c;
+  const TTv L = lam_view(a);
+  const int pc = env_left(a, U, L, h, nullptr, 0.0, 0);
+  launch_env_out(c->st, a->B, h, c->n[h], U.ranks, L.p[h], a->lcap[h], a->lranks, a->d + 1, a->phi[pc],
+                 a->phi_max, lam_alt(a, h), a->lcap[h], a->phi_max, a->err);
+  a->lcur[h] ^= 1;
+  float* dst[kMaxD];
+  for (int k = 0; k < a->d; ++k) dst[k] = lam_cur(a, k);
+  launch_copy_cores(c->st, a->B, 0, h, U.p, U.cap, c->n.data(), U.ranks, a->d + 1, dst, a->lcap);
+  launch_copy_ranks(c->st, a->B, a->d + 1, U.ranks, a->lranks, 1, h);
+}
+
+void add_ones(ttgbf_adj* a) {
+  ttgbf_ctx* c = a->c;
+  const float* src[kMaxD];
+  float* dst[kMaxD];
+  for (int k = 0; k < a->d; ++k) {
+    src[k] = lam_cur(a, k);
+    dst[k] = lam_alt(a, k);
+  }
+  launch_add_ones(c->st, a->B, a->d, src, a->lcap, c->n.data(), dst, a->lcap, a->lranks, a->d + 1, a->sc,
+                  a->coef);
+  for (int k = 0; k < a->d; ++k) a->lcur[k] ^= 1;
+}
+
+TTGeom adj_geom(const ttgbf_adj* a) {
+  TTGeom g{};
+  g.d = a->d;
+  for (int k = 0; k < a->d; ++k) {
+    g.n[k] = a->c->n[k];
+    g.cap[k] = a->lcap[k];
+  }
+  return g;
+}
+
+// Operator tables of the reverse pass (float, uploaded at every backward call).
+struct AdjMats {
+  long long convT[kMaxD], convDq[kMaxD], convDl[kMaxD], scaleT[kMaxD], scaleD[kMaxD];
+  std::vector<long long> wT, wD;  // per op: weights of S(-a), of dS/da
+  std::vector<int> ST, tT;        // per op: span and first shift of S(-a)
+};
+
+void cic_derivative(ttgbf_ctx* c, int m, double lam, std::vector<double>* W) {
+  const int N = c->n[m];
+  W->assign((size_t)N * N, 0.0);
+  for (int i = 0; i < N; ++i) {
+    const double xi = c->axes[c->axoff[m] + i];
+    const double u = (lam * xi - c->lo[m]) / c->dx[m] - 0.5;
+    for (int j = 0; j < N; ++j) {
+      const double t = j - u;
+      if (std::fabs(t) < 1.0 && t != 0.0) (*W)[(size_t)j * N + i] = (t > 0 ? 1.0 : -1.0) * xi / c->dx[m];
+    }
+  }
+}
+
+void conv_derivative(ttgbf_ctx* c, int m, double q, std::vector<double>* K) {
+  conv_matrix(c, m, q, K);
+  const int N = c->n[m];
+  const double D = c->dx[m];
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < N; ++i) {
+      const double t = (double)(j - i) * D;
+      (*K)[(size_t)j * N + i] *= -0.5 / q + 0.5 * t * t / (q * q);
+    }
+}
+
+std::vector<double> matmul(const std::vector<double>& A, const std::vector<double>& B, int N) {
+  std::vector<double> C((size_t)N * N, 0.0);
+  for (int j = 0; j < N; ++j)
+    for (int l = 0; l < N; ++l) {
+      const double x = A[(size_t)j * N + l];
+      if (x == 0.0) continue;
+      for (int i = 0; i < N; ++i) C[(size_t)j * N + i] += x * B[(size_t)l * N + i];
+    }
+  return C;
+}
+
+int build_mats(ttgbf_adj* a, AdjMats* M) {
+  ttgbf_ctx* c = a->c;
+  const int d = c->d;
+  std::vector<float> host;
+  auto put = [&](const std::vector<double>& X, bool transpose, int N) -> long long {
+    const long long at = (long long)host.size();
+    host.resize(host.size() + (size_t)N * N);
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i)
+        host[at + (size_t)j * N + i] = (float)(transpose ? X[(size_t)i * N + j] : X[(size_t)j * N + i]);
+    return at;
+  };
+  std::vector<double> Dm(d, 1.0);
+  for (const Op& op : c->ops)
+    if (op.kind == 1) Dm[op.m] = op.a;
+  for (int m = 0; m < d; ++m) {
+    const int N = c->n[m];
+    const double q = c->lastQ[(size_t)m * d + m];
+    std::vector<double> K, dK, W, dW;
+    conv_matrix(c, m, q, &K);
+    conv_derivative(c, m, q, &dK);
+    cic_matrix(c, m, Dm[m], &W);
+    cic_derivative(c, m, Dm[m], &dW);
+    const bool fused = c->fuse && Dm[m] != 1.0;
+    if (fused) {
+      M->convT[m] = put(matmul(K, W, N), true, N);
+      M->convDq[m] = put(matmul(dK, W, N), false, N);
+      M->convDl[m] = put(matmul(K, dW, N), false, N);
+    } else {
+      M->convT[m] = put(K, true, N);
+      M->convDq[m] = put(dK, false, N);
+      M->convDl[m] = -1;
+    }
+    M->scaleT[m] = put(W, true, N);
+    M->scaleD[m] = put(dW, false, N);
+  }
+  M->wT.assign(c->ops.size(), -1);
+  M->wD.assign(c->ops.size(), -1);
+  M->ST.assign(c->ops.size(), 0);
+  M->tT.assign(c->ops.size(), 0);
+  for (size_t i = 0; i < c->ops.size(); ++i) {
+    const Op& op = c->ops[i];
+    if (op.kind != 0) continue;
+    int S, tmin;
+    std::vector<float> w;
+    shear_table(c, op.m, op.n, -op.a, &S, &tmin, &w);
+    if (S > c->smax + 1) return TTGBF_ECAPACITY;
+    M->ST[i] = S;
+    M->tT[i] = tmin;
+    M->wT[i] = (long long)host.size();
+    host.insert(host.end(), w.begin(), w.end());
+    // derivative of the forward weights hat(t - s_i), s_i = a xi_{n,i} / D_m
+    const int Nn = c->n[op.n], Sf = c->op_S[i], tf = c->op_tmin[i];
+    M->wD[i] = (long long)host.size();
+    for (int u = 0; u < Sf; ++u)
+      for (int j = 0; j < Nn; ++j) {
+        const double xi = c->axes[c->axoff[op.n] + j];
+        const double t = (tf + u) - op.a * xi / c->dx[op.m];
+        host.push_back(std::fabs(t) < 1.0 && t != 0.0 ? (float)((t > 0 ? 1.0 : -1.0) * xi / c->dx[op.m]) : 0.f);
+      }
+  }
+  if ((long long)host.size() > a->mats_floats) return TTGBF_ECAPACITY;
+  if (cudaMemcpyAsync(a->mats, host.data(), sizeof(float) * host.size(), cudaMemcpyHostToDevice, c->st) !=
+      cudaSuccess)
+    return TTGBF_ECUDA;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return TTGBF_ECUDA;  // host is freed on return
+  return TTGBF_OK;
+}
+
+// ---- the reverse steps
+void back_norm(ttgbf_adj* a, const TapeEntry& e) {
+  ttgbf_ctx* c = a->c;
+  inner(a, snap_view(a, e.snap), lam_view(a));
+  launch_scalars(c->st, a->B, 0, reinterpret_cast<const double*>(a->tape + e.scal), a->val, c->delta, a->sc,
+                 a->coef, nullptr, 0, 0, 0.0);
+  add_ones(a);
+}
+
+void back_logc(ttgbf_adj* a, const TapeEntry& e) {
+  ttgbf_ctx* c = a->c;
+  launch_scalars(c->st, a->B, 1, reinterpret_cast<const double*>(a->tape + e.scal), nullptr, c->delta, a->sc,
+                 a->coef, nullptr, 0, 0, 0.0);
+  add_ones(a);
+}
+
+const float* lik_z(const ttgbf_adj* a, const TapeEntry& e) {
+  return reinterpret_cast<const float*>(a->tape + e.scal);
+}
+const float* lik_off(const ttgbf_adj* a, const TapeEntry& e) { return lik_z(a, e) + a->B; }
+
+void back_lik(ttgbf_adj* a, const TapeEntry& e) {
+  ttgbf_ctx* c = a->c;
+  if (e.nmodes == 1) {
+    const int k = e.mode0;
+    launch_lik1(c->st, a->B, k, c->n[k], lam_cur(a, k), a->lcap[k], lam_cur(a, k), a->lcap[k], a->lranks,
+                a->d + 1, e.htab, lik_z(a, e), lik_off(a, e), e.R, 0);
+  } else {
+    launch_lik2_split(c->st, a->B, c->n[0], c->n[1], lam_cur(a, 0), a->lcap[0], lam_cur(a, 1), a->lcap[1],
+                      lam_alt(a, 0), a->lcap[0], lam_alt(a, 1), a->lcap[1], a->lranks, a->d + 1, e.htab,
+                      lik_z(a, e), lik_off(a, e), e.R);
+    a->lcur[0] ^= 1;
+    a->lcur[1] ^= 1;
+  }
+}
+
+// dl/dR_c = <g_c (.) lambda, w> for every likelihood factor of the update.
+void back_upd_in(ttgbf_adj* a, const TapeEntry& e, const std::vector<TapeEntry>& liks) {
+  ttgbf_ctx* c = a->c;
+  const TTv w = snap_view(a, e.snap);
+  for (const TapeEntry& l : liks) {
+    TTv Y = lam_view(a);
+    if (l.nmodes == 1) {
+      const int k = l.mode0;
+      launch_lik1(c->st, a->B, k, c->n[k], lam_cur(a, k), a->lcap[k], a->sB[k], a->lcap[k], a->lranks, a->d + 1,
+                  l.htab, lik_z(a, l), lik_off(a, l), l.R, 1);
+      Y.p[k] = a->sB[k];
+    } else {
+      launch_lik2_weight(c->st, a->B, c->n[0], c->n[1], lam_cur(a, 1), a->lcap[1], a->sB[1], a->lcap[1],
+                         a->lranks, a->d + 1, l.htab, lik_z(a, l), lik_off(a, l), l.R, 1);
+      Y.p[1] = a->sB[1];
+    }
+    inner(a, w, Y);
+    add_grad(a, a->d * a->d + a->d + l.comp);
+  }
+}
+
+void back_mode(ttgbf_adj* a, const TapeEntry& e, const AdjMats& M) {
+  ttgbf_ctx* c = a->c;
+  const int k = e.k, d = a->d, N = c->n[k];
+  const TTv y = snap_view(a, e.snap);
+  auto grad_of = [&](long long moff, int gi) {
+    launch_mode(c->st, a->B, k, N, a->mats + moff, y.p[k], a->scap[k], a->sB[k], a->lcap[k], y.ranks, d + 1);
+    TTv X = y;
+    X.p[k] = a->sB[k];
+    X.cap[k] = a->lcap[k];
+    inner(a, X, lam_view(a));
+    add_grad(a, gi);
+  };
+  long long mt;
+  if (e.mkind == kModeScale) {
+    grad_of(M.scaleD[k], k * d + k);
+    mt = M.scaleT[k];
+  } else {
+    grad_of(M.convDq[k], d * d + k);
+    if (e.mkind == kModeConvScale) grad_of(M.convDl[k], k * d + k);
+    mt = M.convT[k];
+  }
+  launch_mode(c->st, a->B, k, N, a->mats + mt, lam_cur(a, k), a->lcap[k], lam_alt(a, k), a->lcap[k], a->lranks,
+              d + 1);
+  a->lcur[k] ^= 1;
+}
+
+void back_shear(ttgbf_adj* a, const TapeEntry& e, const AdjMats& M) {
+  ttgbf_ctx* c = a->c;
+  const int m = e.k, n = e.n, d = a->d, lo = std::min(m, n), hi = std::max(m, n);
+  const TTv y = snap_view(a, e.snap);
+  const TTGeom g = adj_geom(a);
+  // (dS/da) y: the block of y at adjoint strides, expanded with the derivative weights
+  launch_copy_cores(c->st, a->B, lo, hi + 1, y.p, y.cap, c->n.data(), y.ranks, d + 1, a->sA, a->lcap);
+  cudaMemcpyAsync(a->sranks, y.ranks, sizeof(int) * (size_t)a->B * (d + 1), cudaMemcpyDeviceToDevice, c->st);
+  launch_shear_expand(c->st, a->B, g, m, n, c->op_S[e.op], c->op_tmin[e.op], a->mats + M.wD[e.op], a->sA, a->sB,
+                      a->sranks, 0);
+  launch_rank_scale(c->st, a->B, d, a->sranks, lo, hi, c->op_S[e.op]);
+  TTv Y = y;
+  for (int k = lo; k <= hi; ++k) {
+    Y.p[k] = a->sB[k];
+    Y.cap[k] = a->lcap[k];
+  }
+  Y.ranks = a->sranks;
+  inner(a, lam_view(a), Y);
+  add_grad(a, m * d + n);
+  // lambda <- S(-a) lambda
+  float* cur[kMaxD];
+  float* alt[kMaxD];
+  for (int k = 0; k < d; ++k) {
+    cur[k] = lam_cur(a, k);
+    alt[k] = lam_alt(a, k);
+  }
+  launch_shear_expand(c->st, a->B, g, m, n, M.ST[e.op], M.tT[e.op], a->mats + M.wT[e.op], cur, alt, a->lranks, 0);
+  launch_rank_scale(c->st, a->B, d, a->lranks, lo, hi, M.ST[e.op]);
+  for (int k = lo; k <= hi; ++k) a->lcur[k] ^= 1;
+}
+
+// Gradient with respect to F from the gradients with respect to the
+// strictly lower L, diagonal D and strictly upper U of F = L D U: with
+// X = L^{-1} dF U^{-1} one has dL = L tril(X) D^{-1}, dD = diag(X),
+// dU = D^{-1} triu(X) U, so G_X = tril(L^T G_L D^{-1}) + diag(G_D) +
+// triu(D^{-1} G_U U^T) and G_F = L^{-T} G_X U^{-T}.
+int ldu_adjoint(int d, const double* F, const double* GL, const double* GD, const double* GU, double* GF) {
+  std::vector<double> L, D, U;
+  const int rc = ldu(F, d, &L, &D, &U);
+  if (rc) return rc;
+  auto at = [d](std::vector<double>& A, int i, int j) -> double& { return A[(size_t)i * d + j]; };
+  std::vector<double> GX((size_t)d * d, 0.0);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      if (i > j) {
+        for (int l = 0; l < d; ++l) s += L[(size_t)l * d + i] * GL[(size_t)l * d + j];  // (L^T G_L)_ij
+        s /= D[j];
+      } else if (i < j) {
+        for (int l = 0; l < d; ++l) s += GU[(size_t)i * d + l] * U[(size_t)j * d + l];  // (G_U U^T)_ij
+        s /= D[i];
+      } else {
+        s = GD[i];
+      }
+      at(GX, i, j) = s;
+    }
+  // Linv (unit lower) and Uinv (unit upper)
+  std::vector<double> Li((size_t)d * d, 0.0), Ui((size_t)d * d, 0.0);
+  for (int j = 0; j < d; ++j) {
+    at(Li, j, j) = 1.0;
+    for (int i = j + 1; i < d; ++i) {
+      double s = 0.0;
+      for (int l = j; l < i; ++l) s += L[(size_t)i * d + l] * at(Li, l, j);
+      at(Li, i, j) = -s;
+    }
+  }
+  for (int i = 0; i < d; ++i) {
+    at(Ui, i, i) = 1.0;
+    for (int j = i + 1; j < d; ++j) {
+      double s = 0.0;
+      for (int l = i; l < j; ++l) s += at(Ui, i, l) * U[(size_t)l * d + j];
+      at(Ui, i, j) = -s;
+    }
+  }
+  // G_F = Li^T G_X Ui^T
+  std::vector<double> T((size_t)d * d, 0.0);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < d; ++l) s += at(GX, i, l) * at(Ui, j, l);
+      at(T, i, j) = s;
+    }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < d; ++l) s += at(Li, l, i) * at(T, l, j);
+      GF[(size_t)i * d + j] = s;
+    }
+  return TTGBF_OK;
+}
+
+int adj_guard(ttgbf_adj* a) {
+  if (!a || !a->c) return TTGBF_EINVAL;
+  if (a->c->poisoned) return TTGBF_EPOISONED;
+  return TTGBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ttgbf_adj_create(ttgbf_adj** out, ttgbf_ctx* c, int32_t steps, int32_t slots) {
+  if (!out) return TTGBF_EINVAL;
+  *out = nullptr;
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!c->parts.empty() || c->d < 2 || steps < 1 || slots < 0) return TTGBF_EINVAL;
+  ttgbf_adj* a = new (std::nothrow) ttgbf_adj;
+  if (!a) return TTGBF_ENOMEM;
+  const int d = c->d, B = c->B, cap = c->rank_cap, smax = c->smax;
+  a->c = c;
+  a->B = B;
+  a->d = d;
+  a->RS = cap + 2;
+  a->RL = std::max(c->n[0] + 2, (cap + 2) * (smax + 1));
+  a->phi_max = a->RS * a->RL;
+  a->nparams = d * d + d + kMaxComps;
+  int nmax = 0;
+  for (int k = 0; k < d; ++k) {
+    nmax = std::max(nmax, c->n[k]);
+    a->scap[k] = (long long)(k == 0 ? 1 : cap) * c->n[k] * (k == d - 1 ? 1 : cap);
+    a->lcap[k] = (long long)(k == 0 ? 1 : a->RL) * c->n[k] * (k == d - 1 ? 1 : a->RL);
+  }
+  size_t off = 0;
+  for (int k = 0; k < d; ++k) {
+    a->snap_cores[k] = off;
+    off += align256(sizeof(float) * (size_t)B * a->scap[k]);
+  }
+  a->snap_ranks = off;
+  off += align256(sizeof(int) * (size_t)B * (d + 1));
+  a->snap_bytes = off;
+  a->scal_bytes = align256(sizeof(double) * (size_t)B);
+  const size_t snaps_per_step = 3 * (size_t)d * (d - 1) + 2 * (size_t)d + 5;
+  a->tape_cap = (size_t)steps * (snaps_per_step * a->snap_bytes + (3 + kMaxComps) * a->scal_bytes);
+  a->nslots = slots;
+  a->ckpt_bytes = a->snap_bytes + a->scal_bytes;
+  a->ckh.assign((size_t)slots, CkptHost{});
+  a->mats_floats = 0;
+  for (int k = 0; k < d; ++k) a->mats_floats += 5LL * c->n[k] * c->n[k];
+  a->mats_floats += (long long)d * (d - 1) * (2 * smax + 3) * nmax;
+  Arena ar;
+  const size_t o_tape = ar.take<char>(a->tape_cap);
+  const size_t o_ckpt = ar.take<char>((size_t)slots * a->ckpt_bytes);
+  size_t o_lam[2][kMaxD], o_sA[kMaxD], o_sB[kMaxD];
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < d; ++k) o_lam[s][k] = ar.take<float>((size_t)B * a->lcap[k]);
+  for (int k = 0; k < d; ++k) o_sA[k] = ar.take<float>((size_t)B * a->lcap[k]);
+  for (int k = 0; k < d; ++k) o_sB[k] = ar.take<float>((size_t)B * a->lcap[k]);
+  const size_t o_lr = ar.take<int>((size_t)B * (d + 1));
+  const size_t o_sr = ar.take<int>((size_t)B * (d + 1));
+  const size_t o_phi0 = ar.take<float>((size_t)B * a->phi_max);
+  const size_t o_phi1 = ar.take<float>((size_t)B * a->phi_max);
+  const size_t o_part = ar.take<float>((size_t)B * a->chunks * a->phi_max);
+  const size_t o_err = ar.take<int>(1);
+  const size_t o_val = ar.take<double>(B), o_sc = ar.take<double>(B), o_coef = ar.take<double>(B);
+  const size_t o_grad = ar.take<double>((size_t)B * a->nparams);
+  const size_t o_mats = ar.take<float>((size_t)a->mats_floats);
+  if (cudaMalloc(&a->base, ar.off + 256) != cudaSuccess) {
+    cudaGetLastError();
+    delete a;
+    return TTGBF_ENOMEM;
+  }
+  char* b = a->base;
+  a->tape = b + o_tape;
+  a->ckpt = b + o_ckpt;
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < d; ++k) a->lam[s][k] = reinterpret_cast<float*>(b + o_lam[s][k]);
+  for (int k = 0; k < d; ++k) {
+    a->sA[k] = reinterpret_cast<float*>(b + o_sA[k]);
+    a->sB[k] = reinterpret_cast<float*>(b + o_sB[k]);
+  }
+  a->lranks = reinterpret_cast<int*>(b + o_lr);
+  a->sranks = reinterpret_cast<int*>(b + o_sr);
+  a->phi[0] = reinterpret_cast<float*>(b + o_phi0);
+  a->phi[1] = reinterpret_cast<float*>(b + o_phi1);
+  a->part = reinterpret_cast<float*>(b + o_part);
+  a->err = reinterpret_cast<int*>(b + o_err);
+  a->val = reinterpret_cast<double*>(b + o_val);
+  a->sc = reinterpret_cast<double*>(b + o_sc);
+  a->coef = reinterpret_cast<double*>(b + o_coef);
+  a->grad = reinterpret_cast<double*>(b + o_grad);
+  a->mats = reinterpret_cast<float*>(b + o_mats);
+  *out = a;
+  rc = ttgbf_adj_reset(a);
+  if (rc) {
+    ttgbf_adj_free(a);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int ttgbf_adj_free(ttgbf_adj* a) {
+  if (!a) return TTGBF_OK;
+  if (a->c && a->c->tape == a) a->c->tape = nullptr;
+  if (a->c && a->c->st) cudaStreamSynchronize(a->c->st);
+  if (a->base) cudaFree(a->base);
+  cudaGetLastError();
+  delete a;
+  return TTGBF_OK;
+}
+
+int ttgbf_adj_reset(ttgbf_adj* a) {
+  int rc = adj_guard(a);
+  if (rc) return rc;
+  ttgbf_ctx* c = a->c;
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < a->d; ++k)
+      cudaMemsetAsync(a->lam[s][k], 0, sizeof(float) * (size_t)a->B * a->lcap[k], c->st);
+  for (int k = 0; k < a->d; ++k) a->lcur[k] = 0;
+  std::vector<int> ones((size_t)a->B * (a->d + 1), 1);
+  cudaMemcpyAsync(a->lranks, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, c->st);
+  cudaMemsetAsync(a->grad, 0, sizeof(double) * (size_t)a->B * a->nparams, c->st);
+  cudaMemsetAsync(a->err, 0, sizeof(int), c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);  // ones is freed on return
+  a->entries.clear();
+  a->tape_used = 0;
+  a->failed = false;
+  return check(c);
+}
+
+int ttgbf_adj_save(ttgbf_adj* a, int32_t slot) {
+  int rc = adj_guard(a);
+  if (rc) return rc;
+  ttgbf_ctx* c = a->c;
+  if (slot < 0 || slot >= a->nslots || a->recording || c->expanded) return TTGBF_EINVAL;
+  char* dst = a->ckpt + (size_t)slot * a->ckpt_bytes;
+  snap_state(a, dst);
+  cudaMemcpyAsync(dst + a->snap_bytes, c->log_lik, sizeof(double) * a->B, cudaMemcpyDeviceToDevice, c->st);
+  CkptHost& h = a->ckh[slot];
+  h.valid = true;
+  h.canon = c->canon;
+  h.expanded = c->expanded;
+  h.center = c->center;
+  return check(c);
+}
+
+int ttgbf_adj_load(ttgbf_adj* a, int32_t slot) {
+  int rc = adj_guard(a);
+  if (rc) return rc;
+  ttgbf_ctx* c = a->c;
+  if (slot < 0 || slot >= a->nslots || a->recording || !a->ckh[slot].valid) return TTGBF_EINVAL;
+  const char* src = a->ckpt + (size_t)slot * a->ckpt_bytes;
+  for (int k = 0; k < a->d; ++k)
+    cudaMemcpy2DAsync(curp(c, k), sizeof(float) * c->L.core_cap[k], src + a->snap_cores[k],
+                      sizeof(float) * a->scap[k], sizeof(float) * a->scap[k], a->B, cudaMemcpyDeviceToDevice,
+                      c->st);
+  cudaMemcpyAsync(c->ranks, src + a->snap_ranks, sizeof(int) * (size_t)a->B * (a->d + 1),
+                  cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->log_lik, src + a->snap_bytes, sizeof(double) * a->B, cudaMemcpyDeviceToDevice, c->st);
+  const CkptHost& h = a->ckh[slot];
+  c->canon = h.canon;
+  c->expanded = h.expanded;
+  c->center = h.center;
+  for (int k = 0; k < kMaxD; ++k) c->virt_S[k] = 0;
+  return check(c);
+}
+
+int ttgbf_adj_record(ttgbf_adj* a, int32_t on) {
+  int rc = adj_guard(a);
+  if (rc) return rc;
+  if (on) {
+    if (a->c->tape && a->c->tape != a) return TTGBF_EINVAL;
+    a->entries.clear();
+    a->tape_used = 0;
+    a->failed = false;
+    a->recording = true;
+    a->c->tape = a;
+  } else {
+    a->recording = false;
+    if (a->c->tape == a) a->c->tape = nullptr;
+  }
+  return TTGBF_OK;
+}
+
+int ttgbf_adj_backward(ttgbf_adj* a) {
+  int rc = adj_guard(a);
+  if (rc) return rc;
+  if (a->recording) return TTGBF_EINVAL;
+  if (a->failed) {
+    a->entries.clear();
+    a->tape_used = 0;
+    return TTGBF_ECAPACITY;
+  }
+  ttgbf_ctx* c = a->c;
+  AdjMats M;
+  rc = build_mats(a, &M);
+  if (rc) return rc == TTGBF_ECUDA ? cuda_fail(c) : rc;
+  std::vector<TapeEntry> liks;
+  for (size_t i = a->entries.size(); i-- > 0;) {
+    const TapeEntry& e = a->entries[i];
+    switch (e.kind) {
+      case kTNorm: back_norm(a, e); break;
+      case kTProj: project(a, snap_view(a, e.snap), e.k); break;
+      case kTLogc: back_logc(a, e); break;
+      case kTLik:
+        back_lik(a, e);
+        liks.push_back(e);
+        break;
+      case kTUpdIn:
+        back_upd_in(a, e, liks);
+        liks.clear();
+        break;
+      case kTMode: back_mode(a, e, M); break;
+      case kTShear: back_shear(a, e, M); break;
+      default: break;
+    }
+  }
+  a->entries.clear();
+  a->tape_used = 0;
+  return check(c);
+}
+
+int ttgbf_adj_grads(ttgbf_adj* a, double* dF, double* dQ, double* dR, int32_t nR) {
+  int rc = adj_guard(a);
+  if (rc) return rc;
+  if (!dF || !dQ || (nR > 0 && !dR) || nR < 0 || nR > kMaxComps) return TTGBF_EINVAL;
+  ttgbf_ctx* c = a->c;
+  const int d = a->d, B = a->B;
+  if (c->lastF.size() != (size_t)d * d) return TTGBF_EINVAL;
+  std::vector<double> g((size_t)B * a->nparams);
+  int err = 0;
+  cudaMemcpyAsync(g.data(), a->grad, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(&err, a->err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  if (err) return TTGBF_ECAPACITY;
+  for (int b = 0; b < B; ++b) {
+    const double* gb = g.data() + (size_t)b * a->nparams;
+    std::vector<double> GL((size_t)d * d, 0.0), GU((size_t)d * d, 0.0), GD(d, 0.0);
+    for (int m = 0; m < d; ++m)
+      for (int n = 0; n < d; ++n) {
+        if (m > n) GL[(size_t)m * d + n] = gb[m * d + n];
+        else if (m < n) GU[(size_t)m * d + n] = gb[m * d + n];
+        else GD[m] = gb[m * d + m];
+      }
+    rc = ldu_adjoint(d, c->lastF.data(), GL.data(), GD.data(), GU.data(), dF + (size_t)b * d * d);
+    if (rc) return rc;
+    for (int m = 0; m < d; ++m) dQ[(size_t)b * d + m] = gb[d * d + m];
+    for (int k = 0; k < nR; ++k) dR[(size_t)b * nR + k] = gb[d * d + d + k];
+  }
+  return TTGBF_OK;
+}
+
+int ttgbf_ldu_adjoint(int32_t d, const double* F, const double* GL, const double* GD, const double* GU,
+                      double* GF) {
+  if (d < 1 || d > kMaxD || !F || !GL || !GD || !GU || !GF) return TTGBF_EINVAL;
+  if (!finite_all(F, (size_t)d * d)) return TTGBF_ENONFINITE;
+  return ldu_adjoint(d, F, GL, GD, GU, GF);
+}
+
+}  // extern "C"

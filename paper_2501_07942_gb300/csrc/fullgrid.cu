@@ -311,8 +311,8 @@ struct FgShearList {
 // shears and product, so they are in flight while the SM computes.  s_in
 // multiplies the input (a pending normalisation); sum_acc (nullable) receives
 // the sum of the output (the mass before normalisation).
-template <typename T, int FIB>
-__global__ void __launch_bounds__(256, 1) k_fg_pass(const T* __restrict__ in, T* __restrict__ out,
+template <typename T, int FIB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_fg_pass(const T* __restrict__ in, T* __restrict__ out,
                                                     FgGeom g, long long nfib, int N, long long post,
                                                     const T* __restrict__ M, const int* __restrict__ blo,
                                                     const int* __restrict__ bhi, FgShearList sh, T s_in,
@@ -609,6 +609,7 @@ __global__ void k_fg_lik_mom(T* P, FgGeom g, FgLik lk, const double* off, const 
                              double host_scale, double delta, double* lik_acc, double* mom) {
   constexpr int NA = 1 + D + D * D;
   constexpr int LAST = D - 1;
+  constexpr int PER = (NA + 31) / 32;  // accumulators per lane
   __shared__ double red[NA][8];
   const int NL = g.n[LAST];
   const long long rows = g.total / NL;
@@ -617,7 +618,38 @@ __global__ void k_fg_lik_mom(T* P, FgGeom g, FgLik lk, const double* off, const 
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const T sc = (T)(host_scale / (dsum != nullptr ? dsum[0] * delta : 1.0));
   const T lol = (T)(g.lo[LAST] - g.centre[LAST]), dxl = (T)g.dx[LAST];
-  Kahan<T> s[NA];
+  // accumulator a (layout of k_fg_moments) is lane a % 32's slot a / 32: the
+  // row sum r_p (p = 0, 1, 2: sums of v, x_last v, x_last^2 v) times the row
+  // coordinates x_ma, x_mb (-1: none)
+  int ap[PER], ama[PER], amb[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int a = lane + 32 * q;
+    ap[q] = -1;
+    ama[q] = amb[q] = -1;
+    if (a == 0) {
+      ap[q] = 0;
+    } else if (a < 1 + D) {
+      const int m = a - 1;
+      ap[q] = m == LAST ? 1 : 0;
+      ama[q] = m == LAST ? -1 : m;
+    } else if (a < NA) {
+      const int m = (a - 1 - D) / D, l = (a - 1 - D) % D;
+      if (m <= l) {
+        if (l < LAST) {
+          ap[q] = 0;
+          ama[q] = m;
+          amb[q] = l;
+        } else if (m < LAST) {
+          ap[q] = 1;
+          ama[q] = m;
+        } else {
+          ap[q] = 2;
+        }
+      }
+    }
+  }
+  Kahan<T> s[PER];
   for (long long r = warp0; r < rows; r += nwarps) {
     const long long e0 = r * NL;
     T Lrow = sc;
@@ -652,29 +684,26 @@ __global__ void k_fg_lik_mom(T* P, FgGeom g, FgLik lk, const double* off, const 
       r1 += __shfl_xor_sync(0xffffffffu, r1, o);
       r2 += __shfl_xor_sync(0xffffffffu, r2, o);
     }
-    if (lane == 0) {
-      T x[D];
+    T x[D];
 #pragma unroll
-      for (int m = 0; m < LAST; ++m)
-        x[m] = (T)(g.lo[m] - g.centre[m]) + ((T)axis_index(e0, g, m) + (T)0.5) * (T)g.dx[m];
-      s[0].add(r0);
+    for (int m = 0; m < LAST; ++m)
+      x[m] = (T)(g.lo[m] - g.centre[m]) + ((T)axis_index(e0, g, m) + (T)0.5) * (T)g.dx[m];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      if (ap[q] < 0) continue;
+      T t = ap[q] == 0 ? r0 : (ap[q] == 1 ? r1 : r2);
 #pragma unroll
       for (int m = 0; m < LAST; ++m) {
-        s[1 + m].add(x[m] * r0);
-#pragma unroll
-        for (int l = m; l < LAST; ++l) s[1 + D + m * D + l].add(x[m] * x[l] * r0);
-        s[1 + D + m * D + LAST].add(x[m] * r1);
+        if (ama[q] == m) t *= x[m];
+        if (amb[q] == m) t *= x[m];
       }
-      s[1 + LAST].add(r1);
-      s[1 + D + LAST * D + LAST].add(r2);
+      s[q].add(t);
     }
   }
 #pragma unroll
-  for (int a = 0; a < NA; ++a) {
-    double t = (double)s[a].s - (double)s[a].c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[a][warp] = t;
+  for (int q = 0; q < PER; ++q) {
+    const int a = lane + 32 * q;
+    if (a < NA) red[a][warp] = (double)s[q].s - (double)s[q].c;
   }
   __syncthreads();
   for (int a = threadIdx.x; a < NA; a += blockDim.x) {
@@ -1065,7 +1094,10 @@ void fg_apply_pending(ttgbf_fg* c) {
 // the pending host normalisation s_in on load, the output's sum into sum.
 template <typename T>
 void fg_pass(ttgbf_fg* c, int m, T s_in, double* sum) {
-  constexpr int FIB = sizeof(T) == 4 ? 64 : 32;
+  // float: tiles of 32 fibres, two CTAs per SM (16 warps hide the shared-
+  // memory latency of the shears and the banded product); double: one CTA
+  constexpr int FIB = 32;
+  constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
   FgShearList sl{};
   for (const auto& op : c->shears_u)
     if (op.m == m) {
@@ -1080,7 +1112,7 @@ void fg_pass(ttgbf_fg* c, int m, T s_in, double* sum) {
   const long long nfib = c->g.total / N;
   const size_t sm = sizeof(T) * ((size_t)N * N + 2 * (size_t)N * (FIB + 4));
   ttgbf::count_launches(1);
-  k_fg_pass<T, FIB><<<c->sms, 256, sm, c->st>>>((const T*)c->buf[c->cur], (T*)c->buf[c->cur ^ 1], c->g, nfib,
+  k_fg_pass<T, FIB, MINB><<<c->sms * MINB, 256, sm, c->st>>>((const T*)c->buf[c->cur], (T*)c->buf[c->cur ^ 1], c->g, nfib,
                                                 N, post, (const T*)c->mats + c->mat_off[m],
                                                 c->ints + c->band_off[m], c->ints + c->band_off[m] + N, sl,
                                                 s_in, sum);
@@ -1340,13 +1372,14 @@ int ttgbf_fg_init(ttgbf_fg** out, const ttgbf_grid* grid, const ttgbf_prior* pri
   ttgbf::count_launches(1);
   if (precision == 64) {
     cudaFuncSetAttribute(k_fg_axis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fg_pass<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
+    cudaFuncSetAttribute(k_fg_pass<double, 32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
     k_fg_prior<double><<<c->sms * 8, 256, 0, c->st>>>((double*)c->buf[0], c->g, c->dparams,
                                                       c->dparams + ttgbf::kMaxD);
     fg_launch_scale_sum<double>(c, c->buf[0]);
   } else {
     cudaFuncSetAttribute(k_fg_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_fg_pass<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
+    cudaFuncSetAttribute(k_fg_pass<float, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+    cudaFuncSetAttribute(k_fg_pass<float, 32, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     k_fg_prior<float><<<c->sms * 8, 256, 0, c->st>>>((float*)c->buf[0], c->g, c->dparams,
                                                      c->dparams + ttgbf::kMaxD);
     fg_launch_scale_sum<float>(c, c->buf[0]);

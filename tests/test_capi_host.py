@@ -113,3 +113,37 @@ def test_injected_alloc_failure(lib, monkeypatch):
     assert rc == -3 and not ctx.value
     # invalid arguments are still reported as such
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], batch=0)[0] == -1
+
+
+@pytest.mark.parametrize("d,seed", [(2, 0), (4, 1), (6, 2)])
+def test_ldu_adjoint_matches_central_differences(lib, d, seed):
+    """ttgbf_ldu_adjoint (host code of the reverse pass): the gradient of
+    f(F) = <GL, L> + <GD, D> + <GU, U> over F = L D U equals central
+    differences of f through the oracle's Doolittle factorisation."""
+    from oracle import pmf
+    rng = np.random.default_rng(seed)
+    F = np.eye(d) * 1.5 + 0.3 * rng.standard_normal((d, d))
+    GL = np.tril(rng.standard_normal((d, d)), -1)
+    GU = np.triu(rng.standard_normal((d, d)), 1)
+    GD = rng.standard_normal(d)
+
+    def f(X):
+        L, D, U = pmf.ldu(X)
+        return float((GL * L).sum() + (GD * D).sum() + (GU * U).sum())
+
+    h = 1e-6
+    fd = np.zeros((d, d))
+    for i in range(d):
+        for j in range(d):
+            E = np.zeros((d, d))
+            E[i, j] = h
+            fd[i, j] = (f(F + E) - f(F - E)) / (2 * h)
+    got = G.ldu_adjoint(F, GL, GD, GU)
+    assert np.abs(got - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max()), (got, fd)
+
+
+def test_ldu_adjoint_rejects_singular_leading_minor(lib):
+    F = np.array([[0.0, 1.0], [1.0, 0.0]])
+    with pytest.raises(G.TTGBFError) as e:
+        G.ldu_adjoint(F, np.zeros((2, 2)), np.zeros(2), np.zeros((2, 2)))
+    assert e.value.code == -6

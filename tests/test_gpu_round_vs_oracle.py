@@ -24,11 +24,12 @@ discarded tail that the GPU reports about itself.
    LOGC_TOL (below).
 3. Flat bounds where the cap leaves the truncations at the eps level: config
    2 at 32^4 and 64^4 with rank cap 53 (span 3; shears in pieces at 64^4)
-   over 6 steps from the prior.  The oracle TT filter at the same cap
-   discards less than the flat bound per step there (the cap binds at most on
-   the split of the merged 2-site core, whose rank can reach N), so every step is held
-   against the dense oracle at the plain 10 eps + 1e-5 (not summed over steps)
-   and means within 1e-3 grid spacings."""
+   over 6 steps from the prior.  The oracle TT filter at the same cap stays
+   within the flat bound of the dense oracle at every step (checked as the
+   premise: its truncations, though they add up to more than the bound, do
+   not move the density that far), so every GPU step is held against the
+   dense oracle at the plain 10 eps + 1e-5 (not summed over steps) and means
+   within 1e-3 grid spacings."""
 import math
 
 import numpy as np
@@ -239,7 +240,7 @@ def test_one_step_matches_oracle_tt_step(G, n, cap, mc, k, precision):
     _compare_step(G, model, X, z, cap, smax, precision=precision)
 
 
-@pytest.mark.parametrize("n,cap,smax,precision", [(32, 53, 3, "fp32"), (64, 80, 2, "fp32"),
+@pytest.mark.parametrize("n,cap,smax,precision", [(32, 53, 3, "fp32"), (64, 53, 3, "fp32"),
                                                    (32, 53, 3, "fp64")])
 def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax, precision):
     model = synth.config2(n=n)
@@ -261,7 +262,10 @@ def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax, precision):
             Ps[i], _ = pmf.predict_rg(Ps[i], g, model.F, model.Q)
             Ps[i], logc = pmf.update(Ps[i], g, pmf.likelihood(g, oc, zs[i][k], model.R))
             X[i], info = T.step(X[i], g, model.F, model.Q, oc, zs[i][k], model.R, model.eps, cap, smax)
-            assert info["tail_sum"] < flat  # the cap's truncations alone stay within the flat bound
+            # premise: the TT method itself meets the flat bound at this rank cap
+            # (the oracle TT filter's density error), so the GPU path must too
+            e_or = rel(tt.densify(X[i]), Ps[i])
+            assert e_or < flat, (k, i, e_or)
             e = rel(tt.densify(gpu_cores(f, i)), Ps[i])
             mo, co = pmf.moments(Ps[i], g)
             print(f"N={n} step {k} filter {i}: rel err {e:.3e} (flat bound {flat:.1e}), mean err / D "
