@@ -460,10 +460,13 @@ int ttgbf_moments_noalloc(int32_t batch, const ttgbf_grid* grid, const float* co
 /* ---------------------------------------------------------------- adjoint
  * Gradient of the log-likelihood l_b = sum_k log c_k (Eq. pmf_filtrace_b) of
  * every filter b of a context with respect to F, the diagonal of Q and the
- * diagonal of R, by a reverse pass over recorded steps with the truncation
- * bases of the forward pass held fixed (each rounding acts as the orthogonal
- * projection onto its output's left interface; the gradient of the TT filter
- * without the movement of those bases).  Use:
+ * diagonal of R.  A reverse pass over recorded steps runs the adjoint
+ * recursion of the filter equations (transposed shears, scalings, kernels and
+ * likelihood products; the adjoints of the normalisations and of log c) with
+ * the adjoint density held as a tensor train of the same rank cap and eps,
+ * rounded like the forward density, and takes every gradient as an inner
+ * product of the adjoint with a derivative operator applied to the recorded
+ * forward cores.  Use:
  *   ttgbf_adj_create(&a, ctx, S, n)         S steps per recorded segment, n checkpoints
  *   forward: before every segment s, ttgbf_adj_save(a, s); run the steps
  *   reverse: ttgbf_adj_reset(a); for s = n-1 .. 0:
@@ -471,13 +474,15 @@ int ttgbf_moments_noalloc(int32_t batch, const ttgbf_grid* grid, const float* co
  *              again (same F, Q, R, z); ttgbf_adj_record(a, 0);
  *              ttgbf_adj_backward(a)
  *   ttgbf_adj_grads(a, dF, dQ, dR, b)
- * The context must be a single part (opts.parts = 1) with d >= 2; F, Q stay
- * fixed over the run; every shear must fit the expansion capacity (a wider
- * one, applied in pieces, makes the recording fail: ttgbf_adj_backward
- * returns TTGBF_ECAPACITY).  Coefficients of L and U that are exactly 0 and
- * scalings exactly 1 are not applied by the filter, so their gradient
- * entries carry no contribution from them.  Device memory: the recording
- * holds about 3 d^2 compact snapshots of the batch per step. */
+ * The context must be a single part (opts.parts = 1) with d >= 2, F and Q
+ * stay fixed over the run, and the single-operation hooks (ttgbf_scale,
+ * ttgbf_convolve, an unrounded ttgbf_shear, ttgbf_import_cores) are not used
+ * while recording (the recording fails: ttgbf_adj_backward returns
+ * TTGBF_ECAPACITY).  Coefficients of L and U that are exactly 0 and scalings
+ * exactly 1 are not applied by the filter, so their gradient entries carry no
+ * contribution from them.  Device memory: a second context of the same shape
+ * for the adjoint density, and about d^2 + 2 d + 3 compact snapshots of the
+ * batch per recorded step. */
 typedef struct ttgbf_adj ttgbf_adj;
 
 /* steps: most steps recorded between ttgbf_adj_record(1) and (0); slots:

@@ -555,8 +555,9 @@ def ldu_adjoint(F, GL, GD, GU):
 
 class Adjoint:
     """Reverse pass of a TTFilter batch (``ttgbf_adj_*``): checkpoints of the
-    filter state, recording of segments of steps and the backward sweep with
-    frozen truncation bases."""
+    filter state, recording of segments of steps and the backward sweep (the
+    adjoint recursion of the filter equations with the adjoint density as a
+    rounded tensor train)."""
 
     def __init__(self, filt, steps, slots):
         self._lib = load()
@@ -666,8 +667,8 @@ def log_likelihood(F, q, r, *, lo, hi, n, prior_mean, prior_var, comps, z, rank_
     (Eq. pmf_filtrace_b) of a batch of filters run from the prior over the
     measurements z (device float32, steps x batch x b), as a torch function of
     F (d x d), q = diag(Q) and r = diag(R) (float64 CPU tensors).  The
-    gradient comes from the reverse pass (ttgbf_adj_*) with the forward
-    pass's truncation bases held fixed and per-segment checkpoints every
+    gradient comes from the reverse pass (ttgbf_adj_*: the adjoint recursion
+    of the filter equations in TT form) with per-segment checkpoints every
     `checkpoint_every` steps (each segment is run a second time, recorded,
     in the backward pass)."""
     global _LOGLIK

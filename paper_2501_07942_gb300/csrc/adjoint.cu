@@ -1,26 +1,24 @@
-// adjoint.cu -- kernels of the reverse pass of the TT filter step (the
-// gradient of the log-likelihood l = sum_k log c_k, Eq. pmf_filtrace_b, with
-// respect to the model F, Q, R).
+// adjoint.cu -- kernels of the reverse pass of the filter (the gradient of
+// the log-likelihood l = sum_k log c_k, Eq. pmf_filtrace_b, with respect to
+// the model F, Q, R).
 //
-// The reverse pass works in the full tensor space with the truncation bases
-// of the forward pass held fixed: a rounding whose output has left-orthonormal
-// cores 0..h-1 acts as the orthogonal projection onto span(U_{<h}) (x) R^{rest},
-// where U_{<h} is that output's left interface, so its adjoint is the same
-// projection.  The adjoint of the density is carried as a tensor train whose
-// ranks every projection brings back to those of the forward cores.  The
-// pieces here:
+// The reverse pass runs the adjoint recursion of the filter equations
+// (transposed transition operators, transposed likelihood product, the
+// adjoints of the normalisations and of log c) with the adjoint density held
+// as a tensor train and rounded like the forward density; the gradients are
+// inner products of the adjoint with the derivative operators applied to the
+// forward pass's recorded cores.  The pieces here:
 //   * environments: Phi_{k+1} = sum_i X_k(:,i,:)^T Phi_k Y_k(:,i,:), the left
-//     contraction of two tensor trains (a projection's coefficients, an inner
-//     product), split over the grid index into chunks and reduced;
-//   * the projection's new core Z_h = Phi_h Y_h;
-//   * a dense operator on one core's grid index (the transposed Gaussian
-//     kernel and cloud-in-cell scaling, and their derivatives);
+//     contraction of two tensor trains (an inner product), split over the
+//     grid index into chunks and reduced;
+//   * a dense operator on one core's grid index (the derivatives of the
+//     Gaussian kernel and of the cloud-in-cell scaling);
 //   * the TT sum with the all-ones tensor (the adjoints of normalisation and
 //     of log c);
 //   * the likelihood factors (and their derivative in R) on one core or on
 //     the merged cores 0, 1 (written as an exact split with an identity core).
-// The shear's transpose is the shear with the opposite coefficient and uses
-// the forward expansion kernel.
+// The transposed shear is the shear with the opposite coefficient; it and the
+// transposed kernels use the forward kernels.
 #include <math.h>
 
 #include "internal.cuh"
@@ -115,41 +113,7 @@ __global__ void k_env_reduce(int B, int k, const int* __restrict__ xr, const int
   }
 }
 
-// Z(beta, i, alpha') = sum_alpha Phi(beta, alpha) Y_h(alpha, i, alpha'): the
-// new core h of a projection (rx = xr[h] from the frozen interface, ry, ry'
-// from Y).
-__global__ void k_env_out(int B, int h, int n, const int* __restrict__ xr, const float* __restrict__ Y,
-                          long long ycap, const int* __restrict__ yr, int rstride,
-                          const float* __restrict__ Phi, long long phi_stride, float* __restrict__ Z,
-                          long long zcap, int phi_max, int* err) {
-  extern __shared__ float sm[];
-  const int b = blockIdx.y;
-  if (b >= B) return;
-  const int rx = h == 0 ? 1 : xr[(long long)b * rstride + h];
-  const int ry = yr[(long long)b * rstride + h], ry1 = yr[(long long)b * rstride + h + 1];
-  if ((long long)rx * ry > phi_max || (long long)rx * n * ry1 > zcap) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(err, 2);
-    return;
-  }
-  for (int e = threadIdx.x; e < rx * ry; e += blockDim.x)
-    sm[e] = h == 0 ? 1.f : Phi[(long long)b * phi_stride + e];
-  __syncthreads();
-  const float* Yb = Y + (long long)b * ycap;
-  float* Zb = Z + (long long)b * zcap;
-  const long long total = (long long)rx * n * ry1;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long be = e / ((long long)n * ry1);
-    const long long rem = e - be * n * ry1;  // i ry1 + alpha'
-    const float* pr = sm + be * ry;
-    float acc = 0.f;
-    for (int al = 0; al < ry; ++al) acc = fmaf(pr[al], Yb[(long long)al * n * ry1 + rem], acc);
-    Zb[e] = acc;
-  }
-}
-
 // ------------------------------------------------------ core copies, ranks
-// dst core k <- src core k for k in [k0, k1) (the used part, from src's ranks).
 struct PtrSet {
   const float* p[kMaxD];
   long long cap[kMaxD];
@@ -160,6 +124,7 @@ struct MutPtrSet {
   long long cap[kMaxD];
 };
 
+// dst core k <- src core k for k in [k0, k1) (the used part, from src's ranks).
 __global__ void k_copy_cores(int B, int k0, PtrSet src, const int* sr, int rstride, MutPtrSet dst) {
   const int b = blockIdx.z, k = k0 + blockIdx.y;
   if (b >= B) return;
@@ -170,11 +135,6 @@ __global__ void k_copy_cores(int B, int k0, PtrSet src, const int* sr, int rstri
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt;
        e += (long long)gridDim.x * blockDim.x)
     t[e] = s[e];
-}
-
-__global__ void k_copy_ranks(int B, int rstride, const int* src, int* dst, int j0, int j1) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
-    for (int j = j0; j <= j1; ++j) dst[(long long)b * rstride + j] = src[(long long)b * rstride + j];
 }
 
 // ---------------------------------------------------- per-mode operator
@@ -278,14 +238,16 @@ __global__ void k_lik1(int B, int k, int N, const float* src, long long scap, fl
   }
 }
 
-// The two-mode factor on modes (0, 1) applied to the TT (cores 0, 1 of
-// ranks (1, r1), (r1, r2)), written exactly as core 0 = identity (1 x N0 x N0)
-// and core 1 (N0 x N1 x r2) = weight(i0, i1) sum_a G0(i0, a) G1(a, i1, :).
+// The two-mode factor on modes (0, 1) (which as in lik_weight) applied to
+// the TT (cores 0, 1 of ranks (1, r1), (r1, r2)), written exactly as core 0 =
+// identity (1 x N0 x N0) and core 1 (N0 x N1 x r2) = weight(i0, i1) sum_a
+// G0(i0, a) G1(a, i1, :).
 __global__ void k_lik2_split(int B, int N0, int N1, const float* __restrict__ g0, long long g0cap,
                              const float* __restrict__ g1, long long g1cap, float* __restrict__ o0,
                              long long o0cap, float* __restrict__ o1, long long o1cap,
                              const int* __restrict__ ranks, int rstride, const float* __restrict__ htab,
-                             const float* __restrict__ zv, const float* __restrict__ off, double R) {
+                             const float* __restrict__ zv, const float* __restrict__ off, double R,
+                             int which) {
   const int b = blockIdx.y;
   if (b >= B) return;
   const int r1 = ranks[(long long)b * rstride + 1], r2 = ranks[(long long)b * rstride + 2];
@@ -303,7 +265,7 @@ __global__ void k_lik2_split(int B, int N0, int N1, const float* __restrict__ g0
     const int i0 = (int)(t / N1), i1 = (int)(t - (long long)i0 * N1);
     float acc = 0.f;
     for (int a = 0; a < r1; ++a) acc = fmaf(G0[(long long)i0 * r1 + a], G1[((long long)a * N1 + i1) * r2 + c], acc);
-    O1[e] = lik_weight(zb, htab[t], ob, R, 0) * acc;
+    O1[e] = lik_weight(zb, htab[t], ob, R, which) * acc;
   }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N0 * N0;
        e += (long long)gridDim.x * blockDim.x) {
@@ -372,15 +334,6 @@ void launch_env_reduce(cudaStream_t st, int B, int k, const int* xr, const int* 
                                            scal, mul, accumulate);
 }
 
-void launch_env_out(cudaStream_t st, int B, int h, int n, const int* xr, const float* Y, long long ycap,
-                    const int* yr, int rstride, const float* Phi, long long phi_stride, float* Z,
-                    long long zcap, int phi_max, int* err) {
-  count_launches(1);
-  k_env_out<<<dim3(64, B), 256, sizeof(float) * (size_t)phi_max, st>>>(B, h, n, xr, Y, ycap, yr, rstride,
-                                                                       Phi, phi_stride, Z, zcap, phi_max,
-                                                                       err);
-}
-
 void launch_copy_cores(cudaStream_t st, int B, int k0, int k1, const float* const* src, const long long* scap,
                        const int* n, const int* sr, int rstride, float* const* dst, const long long* dcap) {
   if (k1 <= k0) return;
@@ -395,11 +348,6 @@ void launch_copy_cores(cudaStream_t st, int B, int k0, int k1, const float* cons
   }
   count_launches(1);
   k_copy_cores<<<dim3(32, k1 - k0, B), 256, 0, st>>>(B, k0, s, sr, rstride, t);
-}
-
-void launch_copy_ranks(cudaStream_t st, int B, int rstride, const int* src, int* dst, int j0, int j1) {
-  count_launches(1);
-  k_copy_ranks<<<(B + 127) / 128, 128, 0, st>>>(B, rstride, src, dst, j0, j1);
 }
 
 void launch_mode(cudaStream_t st, int B, int k, int N, const float* M, const float* in, long long icap,
@@ -435,10 +383,10 @@ void launch_lik1(cudaStream_t st, int B, int k, int N, const float* src, long lo
 void launch_lik2_split(cudaStream_t st, int B, int N0, int N1, const float* g0, long long g0cap,
                        const float* g1, long long g1cap, float* o0, long long o0cap, float* o1,
                        long long o1cap, int* ranks, int rstride, const float* htab, const float* zv,
-                       const float* off, double R) {
+                       const float* off, double R, int which) {
   count_launches(2);
   k_lik2_split<<<dim3(64, B), 256, 0, st>>>(B, N0, N1, g0, g0cap, g1, g1cap, o0, o0cap, o1, o1cap, ranks,
-                                            rstride, htab, zv, off, R);
+                                            rstride, htab, zv, off, R, which);
   // link 1 now carries the grid index of mode 0
   k_set_link<<<(B + 127) / 128, 128, 0, st>>>(B, ranks, rstride, 1, N0);
 }
@@ -459,7 +407,6 @@ void launch_scalars(cudaStream_t st, int B, int op, const double* m, const doubl
 
 void set_adjoint_attributes() {
   cudaFuncSetAttribute(k_env_step, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_env_out, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace ttgbf

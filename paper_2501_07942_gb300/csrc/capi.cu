@@ -385,7 +385,6 @@ void debug_stage_report(ttgbf_ctx* c, int mode, int k, int ka, int kb) {
 // c->tape is set; defined with the adjoint below).
 enum TapeModeKind : int { kModeConv = 0, kModeScale = 1, kModeConvScale = 2 };
 void tape_shear(ttgbf_ctx* c, int m, int n);
-void tape_proj(ttgbf_ctx* c, int h);
 void tape_mode(ttgbf_ctx* c, int k, int kind);
 void tape_norm(ttgbf_ctx* c, const double* mass);
 void tape_upd_in(ttgbf_ctx* c);
@@ -459,7 +458,6 @@ void enqueue_round(ttgbf_ctx* c) {
   c->expanded = false;
   c->canon = true;
   c->center = c->d - 1;
-  tape_proj(c, c->d - 1);
 }
 
 // Bring the TT into mixed canonical form with its center inside [lo, hi]:
@@ -480,7 +478,6 @@ void enqueue_center_into(ttgbf_ctx* c, int lo, int hi) {
     first = false;
     ++c->center;
   }
-  if (!first) tape_proj(c, c->center);  // the moves truncate links center0..lo-1
 }
 
 MomentArgs tt_moment_args(ttgbf_ctx* c, int with_moments, int scale) {
@@ -822,8 +819,8 @@ void enqueue_shear_pieces(ttgbf_ctx* c, int m, int n, int S, int tmin, const flo
   const int lo = std::min(m, n), hi = std::max(m, n);
   const int np = (S + c->smax - 1) / c->smax;
   const int Nn = c->n[n];
-  tape_fail(c);  // the reverse pass covers shears within the expansion capacity
   enqueue_center_into(c, lo, hi);
+  tape_shear(c, m, n);
   float* curv[kMaxD];
   float* altv[kMaxD];
   for (int k = 0; k < c->d; ++k) curv[k] = curp(c, k);
@@ -924,7 +921,6 @@ void enqueue_shear(ttgbf_ctx* c, int m, int n, int S, int tmin, const float* wts
   for (int k = lo; k <= hi - 1; ++k) stage(c, kStageLeft, k, k == lo);
   c->canon = true;
   c->center = hi;
-  tape_proj(c, hi);
 }
 
 int guard(ttgbf_ctx* c) {
@@ -1036,7 +1032,6 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
     ops->push_back([=] {
       c->canon = true;
       c->center = d - 1;
-      tape_proj(c, d - 1);
     });
   } else {
     ops->push_back([=] {
@@ -2490,23 +2485,28 @@ void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
 // The reverse pass of a run of filter steps: the gradient of the
 // log-likelihood l = sum_k log c_k (Eq. pmf_filtrace_b) with respect to the
 // elementary operators of F = L D U (shear coefficients and scalings), the
-// variances Q_mm and R_cc, with the truncation bases of the forward pass held
-// fixed.  While a tape is attached, predict and update record every step that
-// the reverse pass needs (snapshots of the TT in compact form: ranks are at
-// most rank_cap at every recorded point):
-//   kTShear  the input of a shear (after its canonical-form moves)
-//   kTProj   a truncation sweep that left cores 0..h-1 left-orthonormal: in
-//            the full tensor space it is the orthogonal projection onto the
-//            span of that left interface (x) the rest (nested sweeps reduce
-//            to their last link), so its adjoint is the same projection
+// variances Q_mm and R_cc.  It runs the adjoint recursion of the filter
+// equations (the operators the TT step applies, transposed) with the adjoint
+// density lambda held as a tensor train in a second context of the same grid
+// and rounded there like a forward density, and takes the gradients as inner
+// products of lambda with the derivative operators applied to the forward
+// pass's cores.  The forward pass's roundings do not enter: it is the
+// gradient of the filter equations, evaluated with the TT densities of the
+// forward pass.  (Differentiating the roundings with their bases held fixed
+// would drop the first-order change of a kept subspace that turns to follow
+// its input: a rank-r truncation of A + dA at an A of rank r returns
+// A + dA to first order, not U U^T (A + dA).)
+//
+// While a tape is attached, predict and update record (compact snapshots:
+// ranks are at most rank_cap at every recorded point):
+//   kTShear  the input y of a shear x_m += a x_n
 //   kTMode   the input of a per-mode operator (kernel, scaling or both)
-//   kTNorm   a normalisation x = y / m (its output and m)
-//   kTUpdIn  the input of the update
+//   kTNorm   a normalisation x = y / m: its output and m
+//   kTUpdIn  the input w of the update
 //   kTLik    a likelihood factor (component, table, z, offset)
-//   kTLogc   the mass c of the update (before its rounding)
-// The reverse pass runs the records backwards on an adjoint TT lambda:
+//   kTLogc   the mass c of the update's product (before its rounding)
+// and the reverse pass runs the records backwards:
 //   norm:  lambda <- (lambda - delta <lambda, x> 1) / m
-//   proj:  lambda <- P lambda (contraction with the frozen interface)
 //   logc:  lambda <- lambda + (delta / c) 1
 //   lik:   lambda <- Lambda (.) lambda; dl/dR_c = <g_c (.) lambda, w> at the
 //          update's input w, g_c = d log Lambda_c / dR_c
@@ -2515,11 +2515,11 @@ void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
 // and the chain rule through the LDU factorisation gives dl/dF.
 namespace {
 
-enum TapeKind : int { kTShear = 0, kTProj, kTMode, kTNorm, kTUpdIn, kTLik, kTLogc };
+enum TapeKind : int { kTShear = 0, kTMode, kTNorm, kTUpdIn, kTLik, kTLogc };
 
 struct TapeEntry {
   int kind = 0;
-  int k = 0;        // proj: h; mode: the mode; shear: m
+  int k = 0;        // mode: the mode; shear: m
   int n = 0;        // shear: n
   int op = -1;      // shear: index in ops
   int mkind = 0;    // mode: TapeModeKind
@@ -2541,10 +2541,11 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 struct ttgbf_adj {
-  ttgbf_ctx* c = nullptr;
+  ttgbf_ctx* c = nullptr;   // the filter batch
+  ttgbf_ctx* lc = nullptr;  // holds the adjoint density lambda (same grid and batch)
   int B = 0, d = 0, RS = 0, RL = 0, phi_max = 0, chunks = 16, nparams = 0;
   long long scap[kMaxD] = {};     // snapshot floats per filter per core (rank_cap bound)
-  long long lcap[kMaxD] = {};     // adjoint floats per filter per core
+  long long lcap[kMaxD] = {};     // scratch floats per filter per core
   size_t snap_cores[kMaxD] = {};  // byte offsets of the cores in a snapshot
   size_t snap_ranks = 0, snap_bytes = 0, scal_bytes = 0;
   char* base = nullptr;
@@ -2556,9 +2557,6 @@ struct ttgbf_adj {
   char* ckpt = nullptr;
   size_t ckpt_bytes = 0;
   std::vector<CkptHost> ckh;
-  float* lam[2][kMaxD] = {};
-  int lcur[kMaxD] = {};
-  int* lranks = nullptr;
   float* sA[kMaxD] = {};
   float* sB[kMaxD] = {};
   int* sranks = nullptr;
@@ -2619,14 +2617,6 @@ void tape_shear(ttgbf_ctx* c, int m, int n) {
   e.k = m;
   e.n = n;
   e.op = c->tape_op;
-  tape_push(c, e, true);
-}
-
-void tape_proj(ttgbf_ctx* c, int h) {
-  if (!c->tape) return;
-  TapeEntry e;
-  e.kind = kTProj;
-  e.k = h;
   tape_push(c, e, true);
 }
 
@@ -2705,75 +2695,51 @@ TTv snap_view(const ttgbf_adj* a, size_t snap) {
   return v;
 }
 
-TTv lam_view(const ttgbf_adj* a) {
+TTv lam_view(ttgbf_adj* a) {
   TTv v{};
   for (int k = 0; k < a->d; ++k) {
-    v.p[k] = a->lam[a->lcur[k]][k];
-    v.cap[k] = a->lcap[k];
+    v.p[k] = curp(a->lc, k);
+    v.cap[k] = a->lc->L.core_cap[k];
   }
-  v.ranks = a->lranks;
+  v.ranks = a->lc->ranks;
   return v;
 }
 
-float* lam_cur(ttgbf_adj* a, int k) { return a->lam[a->lcur[k]][k]; }
-float* lam_alt(ttgbf_adj* a, int k) { return a->lam[a->lcur[k] ^ 1][k]; }
-
-// Left environments of X and Y over cores [0, kend); returns the index of
-// the buffer holding Phi_kend.  With kend = d the scalar <X, Y> goes to scal.
-int env_left(ttgbf_adj* a, const TTv& X, const TTv& Y, int kend, double* scal, double mul, int acc) {
+// Left environments of X and Y over all cores: <X, Y> per filter into a->val.
+void inner(ttgbf_adj* a, const TTv& X, const TTv& Y) {
   ttgbf_ctx* c = a->c;
   int cur = 0;
-  for (int k = 0; k < kend; ++k) {
+  for (int k = 0; k < a->d; ++k) {
     launch_env_step(c->st, a->B, k, c->n[k], X.p[k], X.cap[k], X.ranks, Y.p[k], Y.cap[k], Y.ranks, a->d + 1,
                     a->phi[cur], a->phi_max, a->part, a->chunks, a->phi_max, a->err);
     launch_env_reduce(c->st, a->B, k, X.ranks, Y.ranks, a->d + 1, a->part, a->chunks, a->phi_max,
-                      a->phi[cur ^ 1], a->phi_max, k == a->d - 1 ? scal : nullptr, mul, acc);
+                      a->phi[cur ^ 1], a->phi_max, k == a->d - 1 ? a->val : nullptr, 1.0, 0);
     cur ^= 1;
   }
-  return cur;
 }
-
-void inner(ttgbf_adj* a, const TTv& X, const TTv& Y) { env_left(a, X, Y, a->d, a->val, 1.0, 0); }
 
 void add_grad(ttgbf_adj* a, int gi) {
   launch_scalars(a->c->st, a->B, 2, nullptr, a->val, 0.0, nullptr, nullptr, a->grad, a->nparams, gi, 1.0);
 }
 
-// lambda <- P lambda with P the projection onto the interface U_{<h} of U.
-void project(ttgbf_adj* a, const TTv& U, int h) {
-  ttgbf_ctx* c = a->c;
-  const TTv L = lam_view(a);
-  const int pc = env_left(a, U, L, h, nullptr, 0.0, 0);
-  launch_env_out(c->st, a->B, h, c->n[h], U.ranks, L.p[h], a->lcap[h], a->lranks, a->d + 1, a->phi[pc],
-                 a->phi_max, lam_alt(a, h), a->lcap[h], a->phi_max, a->err);
-  a->lcur[h] ^= 1;
-  float* dst[kMaxD];
-  for (int k = 0; k < a->d; ++k) dst[k] = lam_cur(a, k);
-  launch_copy_cores(c->st, a->B, 0, h, U.p, U.cap, c->n.data(), U.ranks, a->d + 1, dst, a->lcap);
-  launch_copy_ranks(c->st, a->B, a->d + 1, U.ranks, a->lranks, 1, h);
-}
-
-void add_ones(ttgbf_adj* a) {
-  ttgbf_ctx* c = a->c;
+// lambda <- sc lambda + coef 1 (per-filter sc, coef in a->sc, a->coef).
+void lam_add_ones(ttgbf_adj* a) {
+  ttgbf_ctx* l = a->lc;
   const float* src[kMaxD];
   float* dst[kMaxD];
   for (int k = 0; k < a->d; ++k) {
-    src[k] = lam_cur(a, k);
-    dst[k] = lam_alt(a, k);
+    src[k] = curp(l, k);
+    dst[k] = altp(l, k);
   }
-  launch_add_ones(c->st, a->B, a->d, src, a->lcap, c->n.data(), dst, a->lcap, a->lranks, a->d + 1, a->sc,
-                  a->coef);
-  for (int k = 0; k < a->d; ++k) a->lcur[k] ^= 1;
+  launch_add_ones(l->st, a->B, a->d, src, l->L.core_cap, l->n.data(), dst, l->L.core_cap, l->ranks, a->d + 1,
+                  a->sc, a->coef);
+  for (int k = 0; k < a->d; ++k) l->cur[k] ^= 1;
+  l->canon = false;
+  l->expanded = true;
 }
 
-TTGeom adj_geom(const ttgbf_adj* a) {
-  TTGeom g{};
-  g.d = a->d;
-  for (int k = 0; k < a->d; ++k) {
-    g.n[k] = a->c->n[k];
-    g.cap[k] = a->lcap[k];
-  }
-  return g;
+void lam_bound(ttgbf_adj* a) {
+  if (a->lc->expanded) enqueue_round(a->lc);
 }
 
 // Operator tables of the reverse pass (float, uploaded at every backward call).
@@ -2841,8 +2807,7 @@ int build_mats(ttgbf_adj* a, AdjMats* M) {
     conv_derivative(c, m, q, &dK);
     cic_matrix(c, m, Dm[m], &W);
     cic_derivative(c, m, Dm[m], &dW);
-    const bool fused = c->fuse && Dm[m] != 1.0;
-    if (fused) {
+    if (c->fuse && Dm[m] != 1.0) {
       M->convT[m] = put(matmul(K, W, N), true, N);
       M->convDq[m] = put(matmul(dK, W, N), false, N);
       M->convDl[m] = put(matmul(K, dW, N), false, N);
@@ -2864,7 +2829,7 @@ int build_mats(ttgbf_adj* a, AdjMats* M) {
     int S, tmin;
     std::vector<float> w;
     shear_table(c, op.m, op.n, -op.a, &S, &tmin, &w);
-    if (S > c->smax + 1) return TTGBF_ECAPACITY;
+    if (S > a->lc->smax * a->lc->smax) return TTGBF_ECAPACITY;
     M->ST[i] = S;
     M->tT[i] = tmin;
     M->wT[i] = (long long)host.size();
@@ -2887,20 +2852,14 @@ int build_mats(ttgbf_adj* a, AdjMats* M) {
   return TTGBF_OK;
 }
 
-// ---- the reverse steps
-void back_norm(ttgbf_adj* a, const TapeEntry& e) {
-  ttgbf_ctx* c = a->c;
-  inner(a, snap_view(a, e.snap), lam_view(a));
-  launch_scalars(c->st, a->B, 0, reinterpret_cast<const double*>(a->tape + e.scal), a->val, c->delta, a->sc,
-                 a->coef, nullptr, 0, 0, 0.0);
-  add_ones(a);
-}
-
-void back_logc(ttgbf_adj* a, const TapeEntry& e) {
-  ttgbf_ctx* c = a->c;
-  launch_scalars(c->st, a->B, 1, reinterpret_cast<const double*>(a->tape + e.scal), nullptr, c->delta, a->sc,
-                 a->coef, nullptr, 0, 0, 0.0);
-  add_ones(a);
+TTGeom scratch_geom(const ttgbf_adj* a) {
+  TTGeom g{};
+  g.d = a->d;
+  for (int k = 0; k < a->d; ++k) {
+    g.n[k] = a->c->n[k];
+    g.cap[k] = a->lcap[k];
+  }
+  return g;
 }
 
 const float* lik_z(const ttgbf_adj* a, const TapeEntry& e) {
@@ -2908,39 +2867,76 @@ const float* lik_z(const ttgbf_adj* a, const TapeEntry& e) {
 }
 const float* lik_off(const ttgbf_adj* a, const TapeEntry& e) { return lik_z(a, e) + a->B; }
 
-void back_lik(ttgbf_adj* a, const TapeEntry& e) {
+// ---- the reverse steps
+void back_norm(ttgbf_adj* a, const TapeEntry& e) {
   ttgbf_ctx* c = a->c;
-  if (e.nmodes == 1) {
-    const int k = e.mode0;
-    launch_lik1(c->st, a->B, k, c->n[k], lam_cur(a, k), a->lcap[k], lam_cur(a, k), a->lcap[k], a->lranks,
-                a->d + 1, e.htab, lik_z(a, e), lik_off(a, e), e.R, 0);
-  } else {
-    launch_lik2_split(c->st, a->B, c->n[0], c->n[1], lam_cur(a, 0), a->lcap[0], lam_cur(a, 1), a->lcap[1],
-                      lam_alt(a, 0), a->lcap[0], lam_alt(a, 1), a->lcap[1], a->lranks, a->d + 1, e.htab,
-                      lik_z(a, e), lik_off(a, e), e.R);
-    a->lcur[0] ^= 1;
-    a->lcur[1] ^= 1;
-  }
+  lam_bound(a);  // ranks back to the cap before they grow again
+  inner(a, snap_view(a, e.snap), lam_view(a));
+  launch_scalars(c->st, a->B, 0, reinterpret_cast<const double*>(a->tape + e.scal), a->val, c->delta, a->sc,
+                 a->coef, nullptr, 0, 0, 0.0);
+  lam_add_ones(a);
 }
 
-// dl/dR_c = <g_c (.) lambda, w> for every likelihood factor of the update.
-void back_upd_in(ttgbf_adj* a, const TapeEntry& e, const std::vector<TapeEntry>& liks) {
+void back_logc(ttgbf_adj* a, const TapeEntry& e) {
   ttgbf_ctx* c = a->c;
+  launch_scalars(c->st, a->B, 1, reinterpret_cast<const double*>(a->tape + e.scal), nullptr, c->delta, a->sc,
+                 a->coef, nullptr, 0, 0, 0.0);
+  lam_add_ones(a);
+}
+
+// lambda <- Lambda (.) lambda with the factor as the forward pass applied it:
+// a one-mode factor scales a core's slices, the two-mode factor multiplies
+// the merged cores 0, 1, which the split of the rounding then separates.
+void back_lik(ttgbf_adj* a, const TapeEntry& e) {
+  ttgbf_ctx* l = a->lc;
+  const int B = a->B, d = a->d;
+  if (e.nmodes == 1) {
+    const int k = e.mode0;
+    launch_lik_apply_1d(l->st, B, curp(l, k), l->L.core_cap[k], l->n[k], k, d, l->ranks, e.htab, lik_z(a, e), 1,
+                        0, e.R, lik_off(a, e));
+    if (!(l->canon && l->center == k)) l->canon = false;
+    return;
+  }
+  for (int k = d - 1; k >= 2; --k) stage(l, kStageRight, k, 0);
+  GemmWork gw = gemm_work(l, B);
+  launch_plan_supercore(l->st, B, l->geom, l->ranks, curp(l, 0), curp(l, 1), l->W, l->L.W_cap, gw);
+  launch_gemm(l->st, gw, l->sms * 8, flops_of(l, kPGemm));
+  launch_lik_apply_2d(l->st, B, l->W, l->L.W_cap, l->n[0], l->n[1], l->ranks, d, e.htab, lik_z(a, e), 1, 0, e.R,
+                      lik_off(a, e));
+  stage(l, kStageSplit, 0, 1);
+  for (int k = 1; k <= d - 2; ++k) stage(l, kStageLeft, k, 0);
+  l->canon = true;
+  l->center = d - 1;
+  l->expanded = false;
+}
+
+// dl/dR_c = <g_c (.) lambda, w> for every likelihood factor of the update
+// (lambda the adjoint of the update's input, w that input).
+void back_upd_in(ttgbf_adj* a, const TapeEntry& e, const std::vector<TapeEntry>& liks) {
+  ttgbf_ctx* l = a->lc;
+  const int B = a->B, d = a->d;
   const TTv w = snap_view(a, e.snap);
-  for (const TapeEntry& l : liks) {
+  for (const TapeEntry& f : liks) {
     TTv Y = lam_view(a);
-    if (l.nmodes == 1) {
-      const int k = l.mode0;
-      launch_lik1(c->st, a->B, k, c->n[k], lam_cur(a, k), a->lcap[k], a->sB[k], a->lcap[k], a->lranks, a->d + 1,
-                  l.htab, lik_z(a, l), lik_off(a, l), l.R, 1);
+    if (f.nmodes == 1) {
+      const int k = f.mode0;
+      launch_lik1(l->st, B, k, l->n[k], curp(l, k), l->L.core_cap[k], a->sB[k], a->lcap[k], l->ranks, d + 1,
+                  f.htab, lik_z(a, f), lik_off(a, f), f.R, 1);
       Y.p[k] = a->sB[k];
+      Y.cap[k] = a->lcap[k];
     } else {
-      launch_lik2_weight(c->st, a->B, c->n[0], c->n[1], lam_cur(a, 1), a->lcap[1], a->sB[1], a->lcap[1],
-                         a->lranks, a->d + 1, l.htab, lik_z(a, l), lik_off(a, l), l.R, 1);
+      cudaMemcpyAsync(a->sranks, l->ranks, sizeof(int) * (size_t)B * (d + 1), cudaMemcpyDeviceToDevice, l->st);
+      launch_lik2_split(l->st, B, l->n[0], l->n[1], curp(l, 0), l->L.core_cap[0], curp(l, 1), l->L.core_cap[1],
+                        a->sA[0], a->lcap[0], a->sB[1], a->lcap[1], a->sranks, d + 1, f.htab, lik_z(a, f),
+                        lik_off(a, f), f.R, 1);
+      Y.p[0] = a->sA[0];
       Y.p[1] = a->sB[1];
+      Y.cap[0] = a->lcap[0];
+      Y.cap[1] = a->lcap[1];
+      Y.ranks = a->sranks;
     }
     inner(a, w, Y);
-    add_grad(a, a->d * a->d + a->d + l.comp);
+    add_grad(a, d * d + d + f.comp);
   }
 }
 
@@ -2965,40 +2961,37 @@ void back_mode(ttgbf_adj* a, const TapeEntry& e, const AdjMats& M) {
     if (e.mkind == kModeConvScale) grad_of(M.convDl[k], k * d + k);
     mt = M.convT[k];
   }
-  launch_mode(c->st, a->B, k, N, a->mats + mt, lam_cur(a, k), a->lcap[k], lam_alt(a, k), a->lcap[k], a->lranks,
-              d + 1);
-  a->lcur[k] ^= 1;
+  mode_apply(a->lc, k, a->mats + mt);
 }
 
 void back_shear(ttgbf_adj* a, const TapeEntry& e, const AdjMats& M) {
   ttgbf_ctx* c = a->c;
   const int m = e.k, n = e.n, d = a->d, lo = std::min(m, n), hi = std::max(m, n);
   const TTv y = snap_view(a, e.snap);
-  const TTGeom g = adj_geom(a);
-  // (dS/da) y: the block of y at adjoint strides, expanded with the derivative weights
+  const TTGeom g = scratch_geom(a);
+  // <lambda, (dS/da) y>, the shifts taken in pieces of at most smax (dS/da is
+  // a sum over the shifts): the block of y at scratch strides, expanded with
+  // the derivative weights of the piece
   launch_copy_cores(c->st, a->B, lo, hi + 1, y.p, y.cap, c->n.data(), y.ranks, d + 1, a->sA, a->lcap);
-  cudaMemcpyAsync(a->sranks, y.ranks, sizeof(int) * (size_t)a->B * (d + 1), cudaMemcpyDeviceToDevice, c->st);
-  launch_shear_expand(c->st, a->B, g, m, n, c->op_S[e.op], c->op_tmin[e.op], a->mats + M.wD[e.op], a->sA, a->sB,
-                      a->sranks, 0);
-  launch_rank_scale(c->st, a->B, d, a->sranks, lo, hi, c->op_S[e.op]);
-  TTv Y = y;
-  for (int k = lo; k <= hi; ++k) {
-    Y.p[k] = a->sB[k];
-    Y.cap[k] = a->lcap[k];
+  const int Sf = c->op_S[e.op], tf = c->op_tmin[e.op], Nn = c->n[n];
+  for (int u0 = 0; u0 < Sf; u0 += c->smax) {
+    const int Sp = std::min(c->smax, Sf - u0);
+    cudaMemcpyAsync(a->sranks, y.ranks, sizeof(int) * (size_t)a->B * (d + 1), cudaMemcpyDeviceToDevice, c->st);
+    launch_shear_expand(c->st, a->B, g, m, n, Sp, tf + u0, a->mats + M.wD[e.op] + (long long)u0 * Nn, a->sA,
+                        a->sB, a->sranks, 0);
+    launch_rank_scale(c->st, a->B, d, a->sranks, lo, hi, Sp);
+    TTv Y = y;
+    for (int k = lo; k <= hi; ++k) {
+      Y.p[k] = a->sB[k];
+      Y.cap[k] = a->lcap[k];
+    }
+    Y.ranks = a->sranks;
+    inner(a, lam_view(a), Y);
+    add_grad(a, m * d + n);
   }
-  Y.ranks = a->sranks;
-  inner(a, lam_view(a), Y);
-  add_grad(a, m * d + n);
-  // lambda <- S(-a) lambda
-  float* cur[kMaxD];
-  float* alt[kMaxD];
-  for (int k = 0; k < d; ++k) {
-    cur[k] = lam_cur(a, k);
-    alt[k] = lam_alt(a, k);
-  }
-  launch_shear_expand(c->st, a->B, g, m, n, M.ST[e.op], M.tT[e.op], a->mats + M.wT[e.op], cur, alt, a->lranks, 0);
-  launch_rank_scale(c->st, a->B, d, a->lranks, lo, hi, M.ST[e.op]);
-  for (int k = lo; k <= hi; ++k) a->lcur[k] ^= 1;
+  // lambda <- S(-a) lambda, rounded on the block as the forward shear is
+  lam_bound(a);
+  enqueue_shear(a->lc, m, n, M.ST[e.op], M.tT[e.op], a->mats + M.wT[e.op], true);
 }
 
 // Gradient with respect to F from the gradients with respect to the
@@ -3026,8 +3019,7 @@ int ldu_adjoint(int d, const double* F, const double* GL, const double* GD, cons
       }
       at(GX, i, j) = s;
     }
-  // Linv (unit lower) and Uinv (unit upper)
-  std::vector<double> Li((size_t)d * d, 0.0), Ui((size_t)d * d, 0.0);
+  std::vector<double> Li((size_t)d * d, 0.0), Ui((size_t)d * d, 0.0);  // L^{-1}, U^{-1}
   for (int j = 0; j < d; ++j) {
     at(Li, j, j) = 1.0;
     for (int i = j + 1; i < d; ++i) {
@@ -3044,8 +3036,7 @@ int ldu_adjoint(int d, const double* F, const double* GL, const double* GD, cons
       at(Ui, i, j) = -s;
     }
   }
-  // G_F = Li^T G_X Ui^T
-  std::vector<double> T((size_t)d * d, 0.0);
+  std::vector<double> T((size_t)d * d, 0.0);  // G_X U^{-T}
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
       double s = 0.0;
@@ -3062,8 +3053,8 @@ int ldu_adjoint(int d, const double* F, const double* GL, const double* GD, cons
 }
 
 int adj_guard(ttgbf_adj* a) {
-  if (!a || !a->c) return TTGBF_EINVAL;
-  if (a->c->poisoned) return TTGBF_EPOISONED;
+  if (!a || !a->c || !a->lc) return TTGBF_EINVAL;
+  if (a->c->poisoned || a->lc->poisoned) return TTGBF_EPOISONED;
   return TTGBF_OK;
 }
 
@@ -3083,8 +3074,31 @@ int ttgbf_adj_create(ttgbf_adj** out, ttgbf_ctx* c, int32_t steps, int32_t slots
   a->c = c;
   a->B = B;
   a->d = d;
+  // the adjoint density: a context of the same grid, batch, rank cap and eps
+  {
+    std::vector<int32_t> n(c->n.begin(), c->n.end());
+    std::vector<double> mean(d, 0.0), var(d, 1.0);
+    ttgbf_grid g{d, n.data(), c->lo.data(), c->hi.data()};
+    ttgbf_prior p{mean.data(), var.data()};
+    ttgbf_opts o{};
+    o.batch = B;
+    o.rank_cap = cap;
+    o.eps = c->eps;
+    o.max_shift_span = smax;
+    o.stream = c->st;
+    o.precision = c->precision;
+    o.conv = TTGBF_CONV_DENSE;
+    o.parts = 1;
+    o.tsqr_slice_blocks = c->slice_blocks;
+    o.svd_threads = c->svd_threads;
+    rc = init_single(&a->lc, &g, &p, &o);
+    if (rc) {
+      delete a;
+      return rc;
+    }
+  }
   a->RS = cap + 2;
-  a->RL = std::max(c->n[0] + 2, (cap + 2) * (smax + 1));
+  a->RL = std::max(c->n[0] + 2, cap * smax + 2);
   a->phi_max = a->RS * a->RL;
   a->nparams = d * d + d + kMaxComps;
   int nmax = 0;
@@ -3102,23 +3116,22 @@ int ttgbf_adj_create(ttgbf_adj** out, ttgbf_ctx* c, int32_t steps, int32_t slots
   off += align256(sizeof(int) * (size_t)B * (d + 1));
   a->snap_bytes = off;
   a->scal_bytes = align256(sizeof(double) * (size_t)B);
-  const size_t snaps_per_step = 3 * (size_t)d * (d - 1) + 2 * (size_t)d + 5;
+  // per step: the shears' inputs, the per-mode operators' inputs (scalings
+  // and kernels), two normalisations and the update's input
+  const size_t snaps_per_step = (size_t)d * (d - 1) + 2 * (size_t)d + 3;
   a->tape_cap = (size_t)steps * (snaps_per_step * a->snap_bytes + (3 + kMaxComps) * a->scal_bytes);
   a->nslots = slots;
   a->ckpt_bytes = a->snap_bytes + a->scal_bytes;
   a->ckh.assign((size_t)slots, CkptHost{});
   a->mats_floats = 0;
   for (int k = 0; k < d; ++k) a->mats_floats += 5LL * c->n[k] * c->n[k];
-  a->mats_floats += (long long)d * (d - 1) * (2 * smax + 3) * nmax;
+  a->mats_floats += (long long)d * (d - 1) * (smax * smax + smax + 2) * nmax;
   Arena ar;
   const size_t o_tape = ar.take<char>(a->tape_cap);
   const size_t o_ckpt = ar.take<char>((size_t)slots * a->ckpt_bytes);
-  size_t o_lam[2][kMaxD], o_sA[kMaxD], o_sB[kMaxD];
-  for (int s = 0; s < 2; ++s)
-    for (int k = 0; k < d; ++k) o_lam[s][k] = ar.take<float>((size_t)B * a->lcap[k]);
+  size_t o_sA[kMaxD], o_sB[kMaxD];
   for (int k = 0; k < d; ++k) o_sA[k] = ar.take<float>((size_t)B * a->lcap[k]);
   for (int k = 0; k < d; ++k) o_sB[k] = ar.take<float>((size_t)B * a->lcap[k]);
-  const size_t o_lr = ar.take<int>((size_t)B * (d + 1));
   const size_t o_sr = ar.take<int>((size_t)B * (d + 1));
   const size_t o_phi0 = ar.take<float>((size_t)B * a->phi_max);
   const size_t o_phi1 = ar.take<float>((size_t)B * a->phi_max);
@@ -3129,19 +3142,17 @@ int ttgbf_adj_create(ttgbf_adj** out, ttgbf_ctx* c, int32_t steps, int32_t slots
   const size_t o_mats = ar.take<float>((size_t)a->mats_floats);
   if (cudaMalloc(&a->base, ar.off + 256) != cudaSuccess) {
     cudaGetLastError();
+    ttgbf_free(a->lc);
     delete a;
     return TTGBF_ENOMEM;
   }
   char* b = a->base;
   a->tape = b + o_tape;
   a->ckpt = b + o_ckpt;
-  for (int s = 0; s < 2; ++s)
-    for (int k = 0; k < d; ++k) a->lam[s][k] = reinterpret_cast<float*>(b + o_lam[s][k]);
   for (int k = 0; k < d; ++k) {
     a->sA[k] = reinterpret_cast<float*>(b + o_sA[k]);
     a->sB[k] = reinterpret_cast<float*>(b + o_sB[k]);
   }
-  a->lranks = reinterpret_cast<int*>(b + o_lr);
   a->sranks = reinterpret_cast<int*>(b + o_sr);
   a->phi[0] = reinterpret_cast<float*>(b + o_phi0);
   a->phi[1] = reinterpret_cast<float*>(b + o_phi1);
@@ -3166,6 +3177,7 @@ int ttgbf_adj_free(ttgbf_adj* a) {
   if (a->c && a->c->tape == a) a->c->tape = nullptr;
   if (a->c && a->c->st) cudaStreamSynchronize(a->c->st);
   if (a->base) cudaFree(a->base);
+  if (a->lc) ttgbf_free(a->lc);
   cudaGetLastError();
   delete a;
   return TTGBF_OK;
@@ -3175,15 +3187,19 @@ int ttgbf_adj_reset(ttgbf_adj* a) {
   int rc = adj_guard(a);
   if (rc) return rc;
   ttgbf_ctx* c = a->c;
-  for (int s = 0; s < 2; ++s)
-    for (int k = 0; k < a->d; ++k)
-      cudaMemsetAsync(a->lam[s][k], 0, sizeof(float) * (size_t)a->B * a->lcap[k], c->st);
-  for (int k = 0; k < a->d; ++k) a->lcur[k] = 0;
+  ttgbf_ctx* l = a->lc;
+  // lambda = 0: rank-1 cores of zeros
+  for (int k = 0; k < a->d; ++k)
+    cudaMemset2DAsync(curp(l, k), sizeof(float) * l->L.core_cap[k], 0, sizeof(float) * l->n[k], a->B, c->st);
   std::vector<int> ones((size_t)a->B * (a->d + 1), 1);
-  cudaMemcpyAsync(a->lranks, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(l->ranks, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, c->st);
   cudaMemsetAsync(a->grad, 0, sizeof(double) * (size_t)a->B * a->nparams, c->st);
   cudaMemsetAsync(a->err, 0, sizeof(int), c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);  // ones is freed on return
+  l->canon = false;
+  l->expanded = false;
+  l->center = 0;
+  for (int k = 0; k < kMaxD; ++k) l->virt_S[k] = 0;
   a->entries.clear();
   a->tape_used = 0;
   a->failed = false;
@@ -3262,7 +3278,6 @@ int ttgbf_adj_backward(ttgbf_adj* a) {
     const TapeEntry& e = a->entries[i];
     switch (e.kind) {
       case kTNorm: back_norm(a, e); break;
-      case kTProj: project(a, snap_view(a, e.snap), e.k); break;
       case kTLogc: back_logc(a, e); break;
       case kTLik:
         back_lik(a, e);
@@ -3279,7 +3294,8 @@ int ttgbf_adj_backward(ttgbf_adj* a) {
   }
   a->entries.clear();
   a->tape_used = 0;
-  return check(c);
+  rc = check(a->lc);
+  return rc ? rc : check(c);
 }
 
 int ttgbf_adj_grads(ttgbf_adj* a, double* dF, double* dQ, double* dR, int32_t nR) {

@@ -188,7 +188,7 @@ struct MomentArgs {
 };
 void launch_moments(cudaStream_t st, int B, const MomentArgs& a, const int* ranks, int rstride,
                     double* Awork, long long awork_stride, double* mass, double* mean, double* cov);
-// adjoint.cu: kernels of the reverse pass (frozen truncation bases).  Tensor
+// adjoint.cu: kernels of the reverse pass (adjoint recursion in TT form).  Tensor
 // trains are given per core as (pointer, per-filter stride) with ranks
 // [B][rstride]; environments are rx x ry float matrices at phi_stride.
 void launch_env_step(cudaStream_t st, int B, int k, int n, const float* X, long long xcap, const int* xr,
@@ -197,12 +197,8 @@ void launch_env_step(cudaStream_t st, int B, int k, int n, const float* X, long 
 void launch_env_reduce(cudaStream_t st, int B, int k, const int* xr, const int* yr, int rstride,
                        const float* part, int chunks, int phi_max, float* Phi_out, long long phi_stride,
                        double* scal, double mul, int accumulate);
-void launch_env_out(cudaStream_t st, int B, int h, int n, const int* xr, const float* Y, long long ycap,
-                    const int* yr, int rstride, const float* Phi, long long phi_stride, float* Z,
-                    long long zcap, int phi_max, int* err);
 void launch_copy_cores(cudaStream_t st, int B, int k0, int k1, const float* const* src, const long long* scap,
                        const int* n, const int* sr, int rstride, float* const* dst, const long long* dcap);
-void launch_copy_ranks(cudaStream_t st, int B, int rstride, const int* src, int* dst, int j0, int j1);
 void launch_mode(cudaStream_t st, int B, int k, int N, const float* M, const float* in, long long icap,
                  float* out, long long ocap, const int* ranks, int rstride);
 void launch_add_ones(cudaStream_t st, int B, int d, const float* const* src, const long long* scap,
@@ -214,7 +210,7 @@ void launch_lik1(cudaStream_t st, int B, int k, int N, const float* src, long lo
 void launch_lik2_split(cudaStream_t st, int B, int N0, int N1, const float* g0, long long g0cap,
                        const float* g1, long long g1cap, float* o0, long long o0cap, float* o1,
                        long long o1cap, int* ranks, int rstride, const float* htab, const float* zv,
-                       const float* off, double R);
+                       const float* off, double R, int which);
 void launch_lik2_weight(cudaStream_t st, int B, int N0, int N1, const float* src, long long scap, float* dst,
                         long long dcap, const int* ranks, int rstride, const float* htab, const float* zv,
                         const float* off, double R, int which);
