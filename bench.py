@@ -165,14 +165,21 @@ def shear_span(model, m, n, a) -> int:
 
 
 def fullgrid_bytes_per_step(model) -> int:
-    """Algorithmic HBM bytes of one dense float32 step: every pass reads and
-    writes the density once (shears, per-axis operators, normalise, likelihood,
-    normalise) or reads it (sums, moments)."""
-    n_shear = sum(1 for op in ldu_ops(model.F) if op[0] == "shear")
+    """Algorithmic HBM bytes of one dense float32 step as the full-grid filter
+    runs it: with F = D U (no L shears) one fused pass per axis (its shears,
+    scaling and kernel) and one pass for the likelihood with the posterior
+    moments, each reading and writing the density once; otherwise a pass per
+    shear, per scaling axis and per kernel axis, a normalising pass, the
+    likelihood pass and a moments read."""
+    ops = ldu_ops(model.F)
     cells = int(np.prod(model.n))
-    passes_rw = n_shear + model.d + 1 + 1 + 1   # shears, axis operators, scale, likelihood, scale
-    passes_r = 1 + 1                            # mass sum, moments
-    return cells * 4 * (2 * passes_rw + passes_r)
+    lower = any(op[0] == "shear" and op[1] > op[2] for op in ops)
+    if not lower:
+        return cells * 4 * 2 * (model.d + 1)
+    n_shear = sum(1 for op in ops if op[0] == "shear")
+    n_scale = sum(1 for op in ops if op[0] == "scale")
+    passes_rw = n_shear + n_scale + model.d + 1 + 1
+    return cells * 4 * (2 * passes_rw + 1)
 
 
 def tsqr_algorithmic_flops(model, rank_cap) -> float:

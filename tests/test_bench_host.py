@@ -41,3 +41,18 @@ def test_tt_dense_rel_err_matches_densified():
     assert abs(bench.tt_dense_rel_err(a, P) - ref) < 1e-9
     assert bench.tt_dense_rel_err(b, P) < 1e-7
     assert math.isfinite(bench.tt_dense_rel_err([c.astype(np.float32) for c in a], P))
+
+
+def test_fullgrid_bytes_count_the_fused_passes():
+    """Config 2's F = 0.95 I + 0.05 U has no L shears: the full-grid filter
+    makes one fused pass per axis and one likelihood-moments pass, each a read
+    and a write of the 2^28-cell float32 density."""
+    m = synth.config2()
+    assert bench.fullgrid_bytes_per_step(m) == 2 ** 28 * 4 * 2 * (4 + 1)
+    # a lower-triangular coupling forces the per-operation sequence
+    m2 = synth.config2()
+    m2.F = np.array(m2.F)
+    m2.F[3, 0] = 0.02
+    n_ops = len(bench.ldu_ops(m2.F))
+    assert bench.fullgrid_bytes_per_step(m2) > 2 ** 28 * 4 * 2 * (4 + 1)
+    assert n_ops > 6
