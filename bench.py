@@ -137,6 +137,11 @@ def cpu_oracle_step(model, mc: int):
                 "FP64 numpy oracle")
 
 
+def log(msg):
+    """Progress of the run on stderr (the JSON line goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def ldu_ops(F):
     """The elementary re-gridding operations the library applies for x -> F x
     (F = L D U without pivoting): ("shear", m, n, a) for x_m += a x_n and
@@ -319,6 +324,7 @@ def run_config4(args, dev):
     timed region).  Per-filter step latency: event nodes recorded with the
     graph at every step's start and at the end of every batch's step, read
     after the last timed launch (every filter of a batch finishes with it)."""
+    log("config4 leg")
     import torch
     import paper_2501_07942_gb300 as G
     groups = synth.config4()
@@ -339,7 +345,7 @@ def run_config4(args, dev):
         streams.append(s)
         comps.append([(md, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
                       for md, t in m.tables(f.grid_axes())])
-        z = np.stack([synth.simulate(m, fid, steps=(reps + 2) * H + 1)[1] for fid in ids], axis=1)
+        z = np.stack([synth.simulate(m, fid, steps=reps * H + 1)[1] for fid in ids], axis=1)
         zall.append(torch.tensor(z, dtype=torch.float32, device=dev))
         zbuf.append(torch.zeros((H,) + tuple(z.shape[1:]), dtype=torch.float32, device=dev))
         B = len(ids)
@@ -351,24 +357,23 @@ def run_config4(args, dev):
     step_args = lambda k: [(m.F, m.Q, comps[i], m.R, zall[i][k], outs[i][0][0], outs[i][1][0],
                             outs[i][2][0], outs[i][3][0]) for i, m in enumerate(models)]
     # one eager group step (the recorded horizon must start from a stepped
-    # state), the recording, one untimed launch, then the timed launches
+    # state), the recording, then the timed launches (the first one includes
+    # the graph's upload)
     t_eager = time.time()
     grp.step(step_args(0))
     torch.cuda.synchronize(dev)
     t_eager = time.time() - t_eager
+    log(f"config4: eager group step {t_eager:.1f} s")
     grp.capture([(m.F, m.Q, comps[i], m.R, zbuf[i], *outs[i]) for i, m in enumerate(models)], H)
     nk = grp.graph_kernels()
-    with torch.cuda.stream(st):
-        for i in range(len(models)):
-            zbuf[i].copy_(zall[i][1: 1 + H])
-        grp.launch()
+    log(f"config4: recorded {H} steps, {nk} kernels")
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(st):
         a.record(st)
         for r in range(reps):
             for i in range(len(models)):
-                zbuf[i].copy_(zall[i][1 + (r + 1) * H: 1 + (r + 2) * H])
+                zbuf[i].copy_(zall[i][1 + r * H: 1 + (r + 1) * H])
             grp.launch()
         b.record(st)
     torch.cuda.synchronize(dev)
@@ -390,6 +395,49 @@ def run_config4(args, dev):
             "autotuned_groups": tuned,
             "workload": "config4: 512 filters, d in {3..6}, N in {64,128,256}, rank cap in "
                         "{8,16,32}, random stable F (rho 0.9), diagonal Q, R, range measurement"}
+
+
+def run_adjoint(args, dev):
+    """Config 5: the gradient of the log-likelihood (sum of log c over the run)
+    of one config-2 filter over 200 steps with respect to F, diag Q and
+    diag R, through the torch function over the reverse pass (checkpoints
+    every 20 steps, each segment recomputed and recorded once in the backward
+    pass).  Times the forward and the backward call with CUDA events on the
+    filter's stream (wall-clock synchronised around each)."""
+    log("gradient (config 5) leg")
+    import torch
+    import paper_2501_07942_gb300 as G
+    model = synth.config2()
+    K, every = args.adj_steps, 20
+    z = synth.simulate(model, 0, steps=K)[1]
+    probe = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1,
+                       rank_cap=model.rank_cap, eps=model.eps, device=dev)
+    comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+             for m, t in model.tables(probe.grid_axes())]
+    probe.free()
+    zd = torch.tensor(z[:, None, :], dtype=torch.float32, device=dev)  # K x 1 x b
+    Ft = torch.tensor(model.F, dtype=torch.float64, requires_grad=True)
+    qt = torch.tensor(np.diag(model.Q).copy(), dtype=torch.float64, requires_grad=True)
+    rt = torch.tensor(np.diag(np.atleast_2d(model.R)).copy(), dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.time()
+    ll = G.log_likelihood(Ft, qt, rt, lo=model.lo, hi=model.hi, n=model.n, prior_mean=model.m0,
+                          prior_var=np.diag(model.P0), comps=comps, z=zd, rank_cap=model.rank_cap,
+                          eps=model.eps, max_shift_span=10, checkpoint_every=every, device=dev)
+    torch.cuda.synchronize(dev)
+    t1 = time.time()
+    ll.sum().backward()
+    torch.cuda.synchronize(dev)
+    t2 = time.time()
+    g = np.concatenate([Ft.grad.numpy().ravel(), qt.grad.numpy(), rt.grad.numpy()])
+    return {"workload": f"config5: config-2 model, 1 filter, {K} steps, checkpoints every {every} steps",
+            "log_lik": float(ll.detach().numpy()[0]), "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "backward_ms_per_step": 1e3 * (t2 - t1) / K,
+            "gradient_finite": bool(np.isfinite(g).all()), "grad_max_abs": float(np.abs(g).max()),
+            "dl_dF": Ft.grad.numpy().round(6).tolist(), "dl_dq": qt.grad.numpy().round(6).tolist(),
+            "dl_dr": rt.grad.numpy().round(6).tolist(),
+            "checked": "against the float64 dense oracle gradient and central differences at 32^4 "
+                       "(tests/test_gpu_adjoint.py)"}
 
 
 def tuned_config(G, model, batch, rank_cap, smax, precision):
@@ -546,6 +594,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
                                f"(clock from {pk_src} peaks); of derived peak"}
 
     # the full-grid filter on the same workload (the metric's comparison)
+    log("full-grid leg")
     fullgrid = None if args.no_fullgrid else run_fullgrid(args, model, zs, W, K, dev, axes)
 
     # accuracy at the bench configuration and a rank-cap sweep: every TT
@@ -554,6 +603,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     # full-grid GPU filter of that run after every step
     accuracy, sweep = None, []
     if not args.no_accuracy:
+        log("accuracy leg and rank-cap sweep")
         S = W + K
         bound = 10.0 * model.eps + 1e-5
         configs = [(cap, smax, prec)] + [c for c in SWEEP if c != (cap, smax, prec)]
@@ -610,6 +660,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
                     for k, v in prof.items() if v["launches"] > 0},
         "fullgrid": fullgrid,
         "config4": None if args.no_config4 else run_config4(args, dev),
+        "adjoint": None if args.no_adjoint else run_adjoint(args, dev),
         "accuracy": accuracy,
         "rank_cap_sweep": sweep,
     }
@@ -622,6 +673,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
             "value": best["value"], "tt_density_rel_fro_err": best["tt_density_rel_fro_err"],
             "bound": best["bound"], "vs_fullgrid": best.get("vs_fullgrid")}
     if world == 1 and not args.no_cpu_baseline:
+        log("cpu baseline (oracle)")
         dt, desc = cpu_oracle_step(model, mc_ids[0])
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle", "sample": desc}
@@ -644,6 +696,8 @@ def main():
                     help="steps recorded into one CUDA graph in the uneven-batch leg (even)")
     ap.add_argument("--c4-steps", type=int, default=10,
                     help="timed steps of the uneven-batch leg (graph launches x horizon)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (config 5) leg")
+    ap.add_argument("--adj-steps", type=int, default=200, help="steps of the gradient leg")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy comparison and the rank-cap sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -2897,6 +2897,7 @@ void back_lik(ttgbf_adj* a, const TapeEntry& e) {
     if (!(l->canon && l->center == k)) l->canon = false;
     return;
   }
+  lam_bound(a);  // the merged core holds ranks up to the cap only
   for (int k = d - 1; k >= 2; --k) stage(l, kStageRight, k, 0);
   GemmWork gw = gemm_work(l, B);
   launch_plan_supercore(l->st, B, l->geom, l->ranks, curp(l, 0), curp(l, 1), l->W, l->L.W_cap, gw);
