@@ -321,9 +321,10 @@ def run_config4(args, dev):
     together by one TTFilterGroup; a horizon of H steps recorded into one CUDA
     graph and launched until the timed steps are done, the measurements of the
     next H steps copied into the graph's buffer before each launch (inside the
-    timed region).  Per-filter step latency: event nodes recorded with the
-    graph at every step's start and at the end of every batch's step, read
-    after the last timed launch (every filter of a batch finishes with it)."""
+    timed region).  Per-filter step latency: the GPU's global timer, written
+    by one-thread kernels recorded with the graph at every step's start and at
+    the end of every batch's step, read after the last timed launch (every
+    filter of a batch finishes with it)."""
     log("config4 leg")
     import torch
     import paper_2501_07942_gb300 as G
@@ -391,7 +392,7 @@ def run_config4(args, dev):
             "eager_group_step_s": t_eager,
             "per_filter_step_ms": {"p50": float(np.percentile(lat, 50)),
                                    "p99": float(np.percentile(lat, 99)),
-                                   "source": "graph event nodes, last timed launch"},
+                                   "source": "global-timer stamps recorded in the graph, last timed launch"},
             "autotuned_groups": tuned,
             "workload": "config4: 512 filters, d in {3..6}, N in {64,128,256}, rank cap in "
                         "{8,16,32}, random stable F (rho 0.9), diagonal Q, R, range measurement"}

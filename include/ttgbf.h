@@ -354,9 +354,10 @@ int ttgbf_group_times(ttgbf_group* g, float* ms);
 
 /* Per step of the recorded horizon and per context (host array of steps x n
  * floats, step-major): milliseconds from the start of that step in the last
- * launch of the graph to the end of that context's work in it (event nodes
- * recorded with the graph).  Synchronises; TTGBF_EINVAL when no graph was
- * launched. */
+ * launch of the graph to the end of that context's work in it (the GPU's
+ * global timer, written by a one-thread kernel recorded with the graph at
+ * every step's start and after every context's step).  Synchronises;
+ * TTGBF_EINVAL when no graph was launched. */
 int ttgbf_group_graph_times(ttgbf_group* g, float* ms);
 
 int ttgbf_group_free(ttgbf_group* g);

@@ -1952,6 +1952,22 @@ uint64_t ttgbf_launch_count(void) { return g_launches.load(); }
 }  // extern "C"
 
 // ================================================================ groups
+namespace {
+
+// The GPU's global timer (nanoseconds) into *p: the clock of recorded horizons.
+__global__ void k_stamp(unsigned long long* p) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *p = t;
+}
+
+void launch_stamp(cudaStream_t st, unsigned long long* p) {
+  ttgbf::count_launches(1);
+  k_stamp<<<1, 1, 0, st>>>(p);
+}
+
+}  // namespace
+
 struct ttgbf_group {
   cudaStream_t st = nullptr;
   std::vector<ttgbf_ctx*> ctxs;   // as given
@@ -1968,10 +1984,10 @@ struct ttgbf_group {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned long long graph_kernels = 0;
-  // timing of a recorded horizon: event nodes at every step's start (group
-  // stream) and at the end of every leaf's step, read after a launch
-  std::vector<cudaEvent_t> gev_t0;   // per step
-  std::vector<cudaEvent_t> gev_end;  // per step x leaf
+  // timing of a recorded horizon: the GPU's global timer written by a one-
+  // thread kernel at every step's start (group stream) and at the end of
+  // every leaf's step, [step][1 + leaf] nanoseconds, read after a launch
+  unsigned long long* stamps = nullptr;
   int graph_steps = 0;
   bool graph_ran = false;
 };
@@ -2003,7 +2019,7 @@ int group_validate(ttgbf_ctx* c, const ttgbf_group_step_args& a) {
 int group_enqueue(ttgbf_group* g, const ttgbf_group_step_args* args, long long t) {
   const size_t nl = g->leaves.size();
   if (!g->capturing) cudaEventRecord(g->ev_t0, g->st);
-  else cudaEventRecordWithFlags(g->gev_t0[t], g->st, cudaEventRecordExternal);
+  else launch_stamp(g->st, g->stamps + (size_t)t * (nl + 1));
   cudaEventRecord(g->ev_fork, g->st);
   for (ttgbf_ctx* q : g->leaves) cudaStreamWaitEvent(q->st, g->ev_fork, 0);
   // predict
@@ -2060,7 +2076,7 @@ int group_enqueue(ttgbf_group* g, const ttgbf_group_step_args* args, long long t
   }
   for (size_t l = 0; l < nl; ++l) {
     if (!g->capturing) cudaEventRecord(g->ev_tend[l], g->leaves[l]->st);
-    else cudaEventRecordWithFlags(g->gev_end[t * nl + l], g->leaves[l]->st, cudaEventRecordExternal);
+    else launch_stamp(g->leaves[l]->st, g->stamps + (size_t)t * (nl + 1) + 1 + l);
     cudaEventRecord(g->ev_join[l], g->leaves[l]->st);
     cudaStreamWaitEvent(g->st, g->ev_join[l], 0);
   }
@@ -2174,10 +2190,8 @@ static void group_drop_graph(ttgbf_group* g) {
   g->exec = nullptr;
   g->graph = nullptr;
   g->graph_kernels = 0;
-  for (cudaEvent_t e : g->gev_t0) cudaEventDestroy(e);
-  for (cudaEvent_t e : g->gev_end) cudaEventDestroy(e);
-  g->gev_t0.clear();
-  g->gev_end.clear();
+  if (g->stamps) cudaFree(g->stamps);
+  g->stamps = nullptr;
   g->graph_steps = 0;
   g->graph_ran = false;
 }
@@ -2207,12 +2221,12 @@ int ttgbf_group_capture(ttgbf_group* g, const ttgbf_group_step_args* args, int32
     if (cudaStreamSynchronize(q->st) != cudaSuccess) return group_fail(g);
   if (cudaStreamSynchronize(g->st) != cudaSuccess) return group_fail(g);
   group_drop_graph(g);
-  g->gev_t0.assign((size_t)steps, nullptr);
-  g->gev_end.assign((size_t)steps * g->leaves.size(), nullptr);
-  for (cudaEvent_t& e : g->gev_t0)
-    if (cudaEventCreate(&e) != cudaSuccess) return group_fail(g);
-  for (cudaEvent_t& e : g->gev_end)
-    if (cudaEventCreate(&e) != cudaSuccess) return group_fail(g);
+  if (cudaMalloc(&g->stamps, sizeof(unsigned long long) * (size_t)steps * (g->leaves.size() + 1)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    g->stamps = nullptr;
+    return TTGBF_ENOMEM;
+  }
   std::vector<LeafState> before;
   for (ttgbf_ctx* q : g->leaves) before.push_back(leaf_state(q));
   const unsigned long long l0 = g_launches.load();
@@ -2292,17 +2306,20 @@ int ttgbf_group_times(ttgbf_group* g, float* ms) {
 }
 
 int ttgbf_group_graph_times(ttgbf_group* g, float* ms) {
-  if (!g || !ms || !g->exec || !g->graph_ran) return TTGBF_EINVAL;
+  if (!g || !ms || !g->exec || !g->graph_ran || !g->stamps) return TTGBF_EINVAL;
   const size_t nl = g->leaves.size(), nc = g->ctxs.size();
+  std::vector<unsigned long long> st((size_t)g->graph_steps * (nl + 1));
+  if (cudaStreamSynchronize(g->st) != cudaSuccess ||
+      cudaMemcpy(st.data(), g->stamps, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return group_fail(g);
+  }
   for (int t = 0; t < g->graph_steps; ++t) {
+    const unsigned long long* row = st.data() + (size_t)t * (nl + 1);
     for (size_t i = 0; i < nc; ++i) ms[(size_t)t * nc + i] = 0.f;
     for (size_t l = 0; l < nl; ++l) {
-      float e = 0.f;
-      cudaEvent_t end = g->gev_end[(size_t)t * nl + l];
-      if (cudaEventSynchronize(end) != cudaSuccess || cudaEventElapsedTime(&e, g->gev_t0[t], end) != cudaSuccess) {
-        cudaGetLastError();
-        return group_fail(g);
-      }
+      const float e = row[1 + l] > row[0] ? (float)((double)(row[1 + l] - row[0]) * 1e-6) : 0.f;
       float& m = ms[(size_t)t * nc + g->owner[l]];
       m = std::max(m, e);
     }

@@ -8,8 +8,8 @@ autotuner, through the C ABI.
   step (tau the oracle TT filter's tails), means within 1e-3 grid spacings
   plus 2 tau sigma.
 * A recorded horizon (CUDA graph) of two steps, launched, gives what two more
-  group steps give, bitwise; per-step, per-batch times come from the graph's
-  event nodes.
+  group steps give, bitwise; per-step, per-batch times come from global-timer
+  stamps recorded in the graph.
 * ttgbf_autotune returns a valid launch configuration and, from its cache file,
   the same one again."""
 import numpy as np
@@ -143,7 +143,7 @@ def test_group_graph_replays_steps(G):
             zbuf[i].copy_(a.zd[i][1 + rep * horizon: 1 + (rep + 1) * horizon])
         ga.launch()
         torch.cuda.synchronize()
-        gt = ga.graph_times()  # per step and batch, from the graph's event nodes
+        gt = ga.graph_times()  # per step and batch, from the timer stamps recorded in the graph
         assert gt.shape == (horizon, len(models)) and (gt > 0).all()
         for i in range(len(models)):
             for o, t in zip(obuf[i], a.out[i]):
