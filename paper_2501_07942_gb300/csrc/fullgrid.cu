@@ -650,20 +650,6 @@ __global__ void k_fg_lik_mom(T* P, FgGeom g, FgLik lk, const double* off, const 
     }
   }
   Kahan<T> s[PER];
-  // fast path (no factor on the last axis, NL a multiple of 32 up to 256):
-  // every lane holds its NL / 32 values of the row, and the next row's loads
-  // are issued before this row's arithmetic
-  constexpr int kVals = 8;
-  bool fast = NL % 32 == 0 && NL <= 32 * kVals;
-  for (int c = 0; c < lk.b; ++c)
-    fast = fast && !(lk.modes[c][0] == LAST || (lk.nmodes[c] == 2 && lk.modes[c][1] == LAST));
-  const int nv = NL / 32;
-  T cur[kVals], nxt[kVals];
-  if (fast && warp0 < rows) {
-#pragma unroll
-    for (int u = 0; u < kVals; ++u)
-      if (u < nv) cur[u] = P[warp0 * NL + lane + 32 * u];
-  }
   for (long long r = warp0; r < rows; r += nwarps) {
     const long long e0 = r * NL;
     T Lrow = sc;
@@ -675,27 +661,7 @@ __global__ void k_fg_lik_mom(T* P, FgGeom g, FgLik lk, const double* off, const 
       Lrow *= lik_factor<T>(lk, c, i0, i1, off);
     }
     Kahan<T> a0, a1, a2;
-    if (fast) {
-      const long long rn = r + nwarps;
-#pragma unroll
-      for (int u = 0; u < kVals; ++u)
-        if (u < nv) nxt[u] = rn < rows ? P[rn * NL + lane + 32 * u] : (T)0;
-#pragma unroll
-      for (int u = 0; u < kVals; ++u) {
-        if (u < nv) {
-          const int il = lane + 32 * u;
-          const T v = cur[u] * Lrow;
-          P[e0 + il] = v;
-          const T xl = lol + ((T)il + (T)0.5) * dxl;
-          a0.add(v);
-          a1.add(xl * v);
-          a2.add(xl * xl * v);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kVals; ++u) cur[u] = nxt[u];
-    }
-    for (int il = fast ? NL : lane; il < NL; il += 32) {
+    for (int il = lane; il < NL; il += 32) {
       T L = Lrow;
       for (int c = 0; c < lk.b; ++c) {
         const bool uses_last = lk.modes[c][0] == LAST || (lk.nmodes[c] == 2 && lk.modes[c][1] == LAST);

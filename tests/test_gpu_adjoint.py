@@ -158,3 +158,45 @@ def test_checkpointed_segments_and_torch_function(G):
     assert np.allclose(Ft.grad.numpy(), g1[0].sum(0), rtol=1e-6, atol=1e-9)
     assert np.allclose(qt.grad.numpy(), g1[1].sum(0), rtol=1e-6, atol=1e-9)
     assert np.allclose(rt.grad.numpy(), g1[2].sum(0), rtol=1e-6, atol=1e-9)
+
+
+def _general_model(d):
+    """The models of the oracle gradient's own pins (tests/test_oracle_grad.py):
+    a full F (lower couplings, so separate scalings and L shears), one-mode
+    components (d = 2) and a two-mode range with a one-mode component (d = 3)."""
+    if d == 2:
+        g = pmf.Grid([-6.0, -5.0], [6.0, 5.0], [20, 18])
+        F = np.array([[0.93, 0.12], [-0.07, 0.88]])
+        Q = np.diag([0.09, 0.12])
+        comps = [((0,), synth.workloads.h_identity), ((1,), synth.workloads.h_sin)]
+        R = np.diag([0.2, 0.1])
+        z = np.array([[0.4, 0.2], [0.1, -0.3], [-0.2, 0.1]])
+    else:
+        g = pmf.Grid([-4.0, -4.0, -3.0], [4.0, 4.0, 3.0], [12, 10, 9])
+        F = np.array([[0.95, 0.05, -0.04], [0.03, 0.9, 0.06], [0.0, -0.05, 0.92]])
+        Q = np.diag([0.1, 0.15, 0.08])
+        comps = [((0, 1), synth.workloads.h_range), ((2,), synth.workloads.h_identity)]
+        R = np.diag([0.3, 0.2])
+        z = np.array([[1.1, 0.2], [0.9, -0.1]])
+    m = synth.Model(name=f"grad-d{d}", lo=np.array(g.lo), hi=np.array(g.hi), n=np.array(g.shape),
+                    m0=np.zeros(d), P0=np.eye(d), F=F, Q=Q, R=R, comps=comps, eps=1e-6, rank_cap=32)
+    return m, g, z
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_gradient_general_models_match_oracle(G, d):
+    """Separate scalings (kernel and scaling not fused), L shears, one-mode
+    likelihood factors (their R-derivative on one core) and, at d = 3, a
+    two-mode range with a one-mode component: against the oracle gradient."""
+    model, g, z = _general_model(d)
+    ll, (dF, dQ, dR) = gpu_run(G, model, [z], cap=32, smax=5)
+    oc = model.tables(g.axes)
+    ll_o, dF_o, dq_o, dr_o = grad.gradient(model.F, model.Q, model.R, g, model.m0, model.P0, oc, list(z))
+    ref = flat(dF_o, dq_o, dr_o)
+    got = flat(dF[0], dQ[0], dR[0])
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"d={d}: l gpu {ll[0]:.6f} oracle {ll_o:.6f}; max |grad err| / max |grad| {err:.2e}")
+    print("  gpu", np.round(got, 5).tolist())
+    print("  oracle", np.round(ref, 5).tolist())
+    assert abs(ll[0] - ll_o) <= LL_TOL * len(z), (ll[0], ll_o)
+    assert err <= GRAD_TOL, err
