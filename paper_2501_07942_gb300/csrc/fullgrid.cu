@@ -311,24 +311,6 @@ struct FgShearList {
 // shears and product, so they are in flight while the SM computes.  s_in
 // multiplies the input (a pending normalisation); sum_acc (nullable) receives
 // the sum of the output (the mass before normalisation).
-// Along the contiguous last axis (post == 1), element e of a tile of FIB
-// fibres as (fibre f, index i).  With N a multiple of 8, every 32 consecutive
-// e cover 4 fibres x 8 consecutive indices: the global accesses are 32-byte
-// segments, and the tile's shared-memory row stride (FIB + 4 = 4 mod 32)
-// then puts the 32 lanes on 32 different banks (4 (i mod 8) + f mod 32),
-// where one fibre per warp would put 4 lanes on each bank.
-__device__ __forceinline__ void last_axis_fi(int e, int N, bool oct, int& f, int& i) {
-  if (oct) {
-    const int c = e >> 5, l = e & 31, octs = N >> 3;
-    const int fq = c / octs, io = c - fq * octs;
-    f = 4 * fq + (l & 3);
-    i = 8 * io + (l >> 2);
-  } else {
-    f = e / N;
-    i = e - f * N;
-  }
-}
-
 template <typename T, int FIB, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_fg_pass(const T* __restrict__ in, T* __restrict__ out,
                                                     FgGeom g, long long nfib, int N, long long post,
@@ -347,7 +329,6 @@ __global__ void __launch_bounds__(256, MINB) k_fg_pass(const T* __restrict__ in,
   __shared__ T sfr[kPassMaxShears][FIB];
   __shared__ double red[8];
   const int tid = threadIdx.x;
-  const bool oct = (N & 7) == 0 && (FIB & 3) == 0;
   for (int t = tid; t < N * N; t += blockDim.x) {
     const int j = t / N, i = t - j * N;
     Mt[i * N + j] = M[t];
@@ -378,8 +359,7 @@ __global__ void __launch_bounds__(256, MINB) k_fg_pass(const T* __restrict__ in,
       T x = (T)0;
       if (e < FIB * N) {
         if (post == 1) {
-          int f, i;
-          last_axis_fi(e, N, oct, f, i);
+          const int f = e / N, i = e - f * N;
           if (gb + f < nfib) x = in[(gb + f) * N + i];
         } else {
           const int i = e / FIB, f = e - i * FIB;
@@ -401,7 +381,8 @@ __global__ void __launch_bounds__(256, MINB) k_fg_pass(const T* __restrict__ in,
       if (e < FIB * N) {
         int i, f;
         if (post == 1) {
-          last_axis_fi(e, N, oct, f, i);
+          f = e / N;
+          i = e - f * N;
         } else {
           i = e / FIB;
           f = e - i * FIB;
@@ -475,8 +456,7 @@ __global__ void __launch_bounds__(256, MINB) k_fg_pass(const T* __restrict__ in,
     // ---- store with the load's access pattern
     if (post == 1) {
       for (int t = tid; t < FIB * N; t += blockDim.x) {
-        int f, j;
-        last_axis_fi(t, N, oct, f, j);
+        const int f = t / N, j = t - f * N;
         if (g0 + f < nfib) out[(g0 + f) * N + j] = oth[j * PAD + axcol(f)];
       }
     } else {
