@@ -458,6 +458,29 @@ int ttgbf_moments_noalloc(int32_t batch, const ttgbf_grid* grid, const float* co
                           const int64_t* core_stride, const int32_t* ranks, int32_t rank_max,
                           double* mass, double* mean, double* cov, void* stream);
 
+/* ------------------------------------------------------- grid re-design
+ * Alg. 4 with linear dynamics, for a batch that shares one grid.
+ * ttgbf_design_grid (host only): from each filter's filtering mean (host
+ * [batch][d]) and covariance ([batch][d][d]), the predictive moments
+ * F m, F C F^T + Q, the corners of the box F m +- kappa sqrt(diag(F C F^T + Q))
+ * and the same corners mapped back by F^{-1}; lo, hi (host [d]) receive the
+ * axis-aligned box around all corners of all filters (the step maps the grid
+ * onto itself, so it must hold the filtering and the predictive density).
+ * TTGBF_ESINGULAR if F is singular, TTGBF_EINVAL if the box is degenerate.
+ * ttgbf_regrid: every filter's density onto the grid [lo, hi] with the same
+ * cell counts: separable piecewise-linear interpolation of the density values
+ * at the new cell centres from the old ones (the density zero at points
+ * beyond the old grid), then renormalisation on the new grid (one N x N
+ * operator per mode on each core; ranks unchanged).  The axes, the cell
+ * volume and the transition operators of the next predict follow the new
+ * grid; measurement tables passed to the next update must be evaluated on the
+ * new axes (ttgbf_grid_axes).  A recording for the reverse pass fails when
+ * it meets a regrid.  Asynchronous after one host synchronisation (the new
+ * axes' upload). */
+int ttgbf_design_grid(int32_t d, int32_t batch, const double* F, const double* Q, const double* mean,
+                      const double* cov, double kappa, double* lo, double* hi);
+int ttgbf_regrid(ttgbf_ctx* ctx, const double* lo, const double* hi);
+
 /* ---------------------------------------------------------------- adjoint
  * Gradient of the log-likelihood l_b = sum_k log c_k (Eq. pmf_filtrace_b) of
  * every filter b of a context with respect to F, the diagonal of Q and the

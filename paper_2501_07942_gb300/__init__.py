@@ -40,6 +40,7 @@ EXPORTED = [
     "ttgbf_group_times", "ttgbf_group_graph_times", "ttgbf_group_free", "ttgbf_autotune",
     "ttgbf_adj_create", "ttgbf_adj_free", "ttgbf_adj_reset", "ttgbf_adj_save", "ttgbf_adj_load",
     "ttgbf_adj_record", "ttgbf_adj_backward", "ttgbf_adj_grads", "ttgbf_ldu_adjoint",
+    "ttgbf_design_grid", "ttgbf_regrid",
 ]
 
 
@@ -164,6 +165,8 @@ def load() -> ctypes.CDLL:
         getattr(lib, name).argtypes = [VP, ctypes.c_int32]
     lib.ttgbf_adj_grads.argtypes = [VP, dp, dp, dp, ctypes.c_int32]
     lib.ttgbf_ldu_adjoint.argtypes = [ctypes.c_int32, dp, dp, dp, dp, dp]
+    lib.ttgbf_design_grid.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp, ctypes.c_double, dp, dp]
+    lib.ttgbf_regrid.argtypes = [VP, dp, dp]
     _lib = lib
     return lib
 
@@ -410,6 +413,12 @@ class TTFilter:
     def convolve(self, q):
         q = _f64(q)
         _check(self._lib.ttgbf_convolve(self._ctx, _dptr(q)), "ttgbf_convolve")
+
+    def regrid(self, lo, hi):
+        """ttgbf_regrid: every filter's density onto the grid [lo, hi] (same cell
+        counts), then renormalised (Alg. 4 step 5)."""
+        lo, hi = _f64(lo), _f64(hi)
+        _check(self._lib.ttgbf_regrid(self._ctx, _dptr(lo), _dptr(hi)), "ttgbf_regrid")
 
     def round(self):
         _check(self._lib.ttgbf_round(self._ctx), "ttgbf_round")
@@ -683,3 +692,17 @@ def log_likelihood(F, q, r, *, lo, hi, n, prior_mean, prior_var, comps, z, rank_
 
     spec = {"make_filter": make_filter, "comps": comps, "z": z, "every": int(checkpoint_every)}
     return _LOGLIK.apply(F, q, r, spec)
+
+
+def design_grid(F, Q, means, covs, kappa=5.0):
+    """ttgbf_design_grid (host only): the grid box of Alg. 4 for a batch from
+    its filtering means (batch, d) and covariances (batch, d, d): returns
+    (lo, hi)."""
+    F, Q = _f64(F), _f64(Q)
+    means = _f64(np.atleast_2d(means))
+    covs = _f64(np.asarray(covs, dtype=np.float64).reshape(means.shape[0], F.shape[0], F.shape[0]))
+    d, B = F.shape[0], means.shape[0]
+    lo, hi = np.zeros(d), np.zeros(d)
+    _check(load().ttgbf_design_grid(d, B, _dptr(F), _dptr(Q), _dptr(means), _dptr(covs), float(kappa),
+                                    _dptr(lo), _dptr(hi)), "ttgbf_design_grid")
+    return lo, hi

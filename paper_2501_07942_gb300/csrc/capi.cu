@@ -1869,6 +1869,135 @@ int ttgbf_convolve(ttgbf_ctx* c, const double* q) {
   return check(c);
 }
 
+// Grid re-design, interpolation step (Alg. 4 step 5): every filter's density
+// values onto a new axis-aligned grid of the same cell counts, by separable
+// piecewise-linear interpolation (the value at a new point from the two old
+// points around it; the density is zero at points beyond the old grid, as
+// in the filter's boundary reading: one N x N matrix per mode with at most
+// two entries per row), then renormalised on the new grid.  The transition
+// operators of the next predict are rebuilt for the new spacing.
+int ttgbf_regrid(ttgbf_ctx* c, const double* lo, const double* hi) {
+  if (split(c)) return fan_out(c, [&](ttgbf_ctx* q, int) { return ttgbf_regrid(q, lo, hi); }, false, false);
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!lo || !hi) return TTGBF_EINVAL;
+  const int d = c->d;
+  if (!finite_all(lo, d) || !finite_all(hi, d)) return TTGBF_ENONFINITE;
+  for (int k = 0; k < d; ++k)
+    if (!(hi[k] > lo[k])) return TTGBF_EINVAL;
+  tape_fail(c);
+  std::vector<std::vector<double>> mats(d);
+  std::vector<double> axes;
+  for (int k = 0; k < d; ++k) {
+    const int N = c->n[k];
+    const double dxn = (hi[k] - lo[k]) / N;
+    mats[k].assign((size_t)N * N, 0.0);
+    for (int j = 0; j < N; ++j) {
+      const double x = lo[k] + (j + 0.5) * dxn;
+      axes.push_back(x);
+      const double u = (x - c->lo[k]) / c->dx[k] - 0.5;  // position among the old points
+      const int i0 = (int)std::floor(u);
+      for (int i = i0; i <= i0 + 1; ++i)
+        if (i >= 0 && i < N) mats[k][(size_t)j * N + i] = hatf(u - i);
+    }
+  }
+  rc = upload_mats(c, mats);
+  if (rc) return rc;
+  size_t at = 0;
+  for (int k = 0; k < d; ++k) {
+    mode_apply(c, k, c->opmats + at);
+    at += mats[k].size();
+  }
+  c->delta = 1.0;
+  for (int k = 0; k < d; ++k) {
+    c->lo[k] = lo[k];
+    c->hi[k] = hi[k];
+    c->dx[k] = (hi[k] - lo[k]) / c->n[k];
+    c->delta *= c->dx[k];
+  }
+  c->axes = axes;
+  cudaMemcpyAsync(c->axes_d, c->axes.data(), sizeof(double) * c->axes.size(), cudaMemcpyHostToDevice, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  enqueue_normalise(c, c->mass);
+  c->lastF.clear();
+  c->lastQ.clear();
+  return check(c);
+}
+
+// Grid re-design, steps 1-4 of Alg. 4, for a batch that shares its grid:
+// per filter, the predictive moments of the linear model (x = F m,
+// P = F C F^T + Q from the filtering mean m and covariance C), the 2^d
+// corners of the box x +- kappa sqrt(diag P), the same corners mapped back by
+// F^{-1} into the filtering space, and the axis-aligned box around all of
+// them; the batch's grid is the box around every filter's.  (The step's
+// transition maps the grid onto itself, so the grid holds both the filtering
+// density and the predictive one.)
+int ttgbf_design_grid(int32_t d, int32_t batch, const double* F, const double* Q, const double* mean,
+                      const double* cov, double kappa, double* lo, double* hi) {
+  if (d < 1 || d > kMaxD || batch < 1 || !F || !Q || !mean || !cov || !lo || !hi) return TTGBF_EINVAL;
+  if (!finite_all(F, (size_t)d * d) || !finite_all(Q, (size_t)d * d) || !finite_all(mean, (size_t)batch * d) ||
+      !finite_all(cov, (size_t)batch * d * d) || !std::isfinite(kappa))
+    return TTGBF_ENONFINITE;
+  if (!(kappa > 0.0)) return TTGBF_EINVAL;
+  // LU of F with partial pivoting, for the corners' F^{-1}
+  std::vector<double> A(F, F + (size_t)d * d);
+  std::vector<int> piv(d);
+  for (int k = 0; k < d; ++k) {
+    int p = k;
+    for (int i = k + 1; i < d; ++i)
+      if (std::fabs(A[(size_t)i * d + k]) > std::fabs(A[(size_t)p * d + k])) p = i;
+    if (A[(size_t)p * d + k] == 0.0) return TTGBF_ESINGULAR;
+    piv[k] = p;
+    if (p != k)
+      for (int j = 0; j < d; ++j) std::swap(A[(size_t)k * d + j], A[(size_t)p * d + j]);
+    for (int i = k + 1; i < d; ++i) {
+      const double f = A[(size_t)i * d + k] / A[(size_t)k * d + k];
+      A[(size_t)i * d + k] = f;
+      for (int j = k + 1; j < d; ++j) A[(size_t)i * d + j] -= f * A[(size_t)k * d + j];
+    }
+  }
+  auto solve = [&](std::vector<double> x) {
+    for (int k = 0; k < d; ++k) std::swap(x[k], x[piv[k]]);
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < i; ++j) x[i] -= A[(size_t)i * d + j] * x[j];
+    for (int i = d - 1; i >= 0; --i) {
+      for (int j = i + 1; j < d; ++j) x[i] -= A[(size_t)i * d + j] * x[j];
+      x[i] /= A[(size_t)i * d + i];
+    }
+    return x;
+  };
+  for (int k = 0; k < d; ++k) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+  }
+  std::vector<double> xp(d), w(d), cpred(d);
+  for (int b = 0; b < batch; ++b) {
+    const double* m = mean + (size_t)b * d;
+    const double* C = cov + (size_t)b * d * d;
+    for (int i = 0; i < d; ++i) {
+      xp[i] = 0.0;
+      for (int j = 0; j < d; ++j) xp[i] += F[(size_t)i * d + j] * m[j];
+    }
+    for (int i = 0; i < d; ++i) {  // (F C F^T + Q)_ii
+      double s = Q[(size_t)i * d + i];
+      for (int j = 0; j < d; ++j)
+        for (int l = 0; l < d; ++l) s += F[(size_t)i * d + j] * C[(size_t)j * d + l] * F[(size_t)i * d + l];
+      w[i] = kappa * std::sqrt(std::max(s, 0.0));
+    }
+    for (long long cidx = 0; cidx < (1LL << d); ++cidx) {
+      for (int i = 0; i < d; ++i) cpred[i] = xp[i] + (((cidx >> i) & 1) ? w[i] : -w[i]);
+      const std::vector<double> cmeas = solve(cpred);
+      for (int i = 0; i < d; ++i) {
+        lo[i] = std::min(lo[i], std::min(cpred[i], cmeas[i]));
+        hi[i] = std::max(hi[i], std::max(cpred[i], cmeas[i]));
+      }
+    }
+  }
+  for (int k = 0; k < d; ++k)
+    if (!(hi[k] > lo[k]) || !std::isfinite(lo[k]) || !std::isfinite(hi[k])) return TTGBF_EINVAL;
+  return TTGBF_OK;
+}
+
 int ttgbf_round(ttgbf_ctx* c) {
   if (split(c)) return fan_out(c, [&](ttgbf_ctx* q, int) { return ttgbf_round(q); }, false, false);
   int rc = guard(c);

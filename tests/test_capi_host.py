@@ -147,3 +147,22 @@ def test_ldu_adjoint_rejects_singular_leading_minor(lib):
     with pytest.raises(G.TTGBFError) as e:
         G.ldu_adjoint(F, np.zeros((2, 2)), np.zeros(2), np.zeros((2, 2)))
     assert e.value.code == -6
+
+
+def test_design_grid_matches_oracle(lib):
+    """ttgbf_design_grid (host code, Alg. 4 steps 1-4) equals the oracle's
+    design rule on random models and batches."""
+    from oracle import grid_design as GD
+    rng = np.random.default_rng(11)
+    for d, B in [(2, 1), (3, 4), (4, 2)]:
+        F = np.eye(d) * 0.9 + 0.2 * rng.standard_normal((d, d))
+        Q = np.diag(rng.uniform(0.01, 0.1, d))
+        means = rng.standard_normal((B, d))
+        covs = np.array([(lambda A: A @ A.T / d + 0.05 * np.eye(d))(rng.standard_normal((d, d)))
+                         for _ in range(B)])
+        lo, hi = G.design_grid(F, Q, means, covs, kappa=4.5)
+        elo, ehi = GD.design_grid(F, Q, means, covs, 4.5)
+        assert np.allclose(lo, elo, rtol=0, atol=1e-12) and np.allclose(hi, ehi, rtol=0, atol=1e-12)
+    with pytest.raises(G.TTGBFError) as e:
+        G.design_grid(np.zeros((2, 2)), np.eye(2), np.zeros((1, 2)), np.eye(2)[None], 3.0)
+    assert e.value.code == -6
