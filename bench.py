@@ -446,6 +446,52 @@ def run_adjoint(args, dev):
                        "(tests/test_gpu_adjoint.py)"}
 
 
+def run_grid_design(args, dev):
+    """Alg. 4 grid re-design against the fixed grid: config 2's model, Monte
+    Carlo run 0 over 100 steps (its trajectory leaves [-8, 8]^4 after about 60
+    steps), one filter each: fixed grid, and the grid re-designed after every
+    update from the posterior moments (kappa = 5).  Reports each filter's
+    log-likelihood, the RMS error of its mean against the true state over the
+    last 50 steps and its time per step (re-design and interpolation
+    included)."""
+    import torch
+    import paper_2501_07942_gb300 as G
+    log("grid re-design leg")
+    model = synth.config2()
+    K = 100
+    x, z = synth.simulate(model, 0, steps=K)
+    out = {}
+    for name in ("fixed", "redesigned"):
+        f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1,
+                       rank_cap=model.rank_cap, eps=model.eps, device=dev)
+        comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+                 for m, t in model.tables(f.grid_axes())]
+        errs = []
+        torch.cuda.synchronize(dev)
+        t0 = time.time()
+        for k in range(K):
+            if name == "redesigned" and k > 0:
+                comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+                         for m, t in model.tables(f.grid_axes())]
+            f.predict(model.F, model.Q)
+            f.update(comps, model.R, z[k][None, :])
+            mean, cov, lc, ll = f.estimate()
+            errs.append(mean[0] - x[k + 1])
+            if name == "redesigned":
+                lo, hi = G.design_grid(model.F, model.Q, mean, cov, kappa=5.0)
+                f.regrid(lo, hi)
+        torch.cuda.synchronize(dev)
+        dt = time.time() - t0
+        e = np.array(errs[K // 2:])
+        out[name] = {"log_lik": float(ll[0]), "rmse_last_50": float(np.sqrt((e ** 2).mean())),
+                     "ms_per_step": 1e3 * dt / K}
+        f.free()
+    out["workload"] = ("config-2 model, Monte Carlo run 0, 100 steps, 1 filter; grid re-designed after "
+                       "every update (Alg. 4, kappa 5) vs the fixed [-8, 8]^4 grid; wall clock per step "
+                       "including the host's moments, design and measurement tables")
+    return out
+
+
 def run_leg(name, args):
     """Run one secondary leg (config4, adjoint) in a child process of its own:
     its device memory (66 GB for config 4) is returned when it exits, and a
@@ -686,6 +732,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "fullgrid": fullgrid,
         "config4": None if args.no_config4 or rank != 0 else run_leg("config4", args),
         "adjoint": None if args.no_adjoint or rank != 0 else run_leg("adjoint", args),
+        "grid_design": None if args.no_grid_design or rank != 0 else run_grid_design(args, dev),
         "accuracy": accuracy,
         "rank_cap_sweep": sweep,
     }
@@ -722,6 +769,7 @@ def main():
     ap.add_argument("--c4-steps", type=int, default=10,
                     help="timed steps of the uneven-batch leg (graph launches x horizon)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (config 5) leg")
+    ap.add_argument("--no-grid-design", action="store_true", help="skip the grid re-design leg")
     ap.add_argument("--leg", choices=["config4", "adjoint"], default=None,
                     help="run only this secondary leg and print its result (used by the main run)")
     ap.add_argument("--adj-steps", type=int, default=200, help="steps of the gradient leg")
