@@ -134,8 +134,9 @@ typedef struct {
  * tensor).  htab is a caller-owned DEVICE array with h_c evaluated at the grid
  * points: n[m] floats, or n[m]*n[n] floats row-major [i_m][i_n].  A two-mode
  * component must be on modes (0, 1) (its Hadamard product is taken on the
- * merged first two cores, whose left TT rank is 1), at most one per update,
- * with n[0] <= 160.  The library cannot check the size of a device array:
+ * merged first two cores, whose left TT rank is 1; several such components
+ * multiply the merged cores one after the other), with n[0] <= 160.  The
+ * library cannot check the size of a device array:
  * a shorter table is read out of bounds. */
 typedef struct {
   int32_t nmodes;

@@ -228,31 +228,33 @@ def _lik_factor(table, z, r):
 
 
 def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None):
-    """TT Bayes update.  comps = [(modes, table)] as for pmf.likelihood; at most
-    one two-mode component, on modes (0, 1).  Returns (cores, tails, log c)."""
+    """TT Bayes update.  comps = [(modes, table)] as for pmf.likelihood; the
+    two-mode components, all on modes (0, 1), multiply the merged 2-site core
+    (the likelihood is the product of the components, Eq. pmf_filtrace_a).
+    Returns (cores, tails, log c)."""
     R = np.atleast_2d(np.asarray(R, dtype=np.float64))
     z = np.atleast_1d(np.asarray(z, dtype=np.float64))
     G = _cores(cores)
     d = len(G)
-    two = None
+    twos = []
     for c, (modes, table) in enumerate(comps):
         r = float(R[c, c])
         if len(modes) == 1:
             m = modes[0]
             G[m] = G[m] * _lik_factor(table, z[c], r)[None, :, None]
         else:
-            if tuple(modes) != (0, 1) or two is not None:
-                raise ValueError("one two-mode component, on modes (0, 1)")
-            two = (c, table, r)
+            if tuple(modes) != (0, 1):
+                raise ValueError("two-mode components on modes (0, 1) only")
+            twos.append((c, table, r))
     tails = []
-    if two is None:
+    if not twos:
         logc = math.log(mass(G, grid))
     else:
-        c, table, r = two
         for k in range(d - 1, 1, -1):
             right_orth(G, k)
         W = np.einsum("ia,ajb->ijb", G[0][0], G[1])
-        W = W * _lik_factor(table, z[c], r)[:, :, None]
+        for c, table, r in twos:
+            W = W * _lik_factor(table, z[c], r)[:, :, None]
         logc = math.log(tt.full_sum([W.reshape(1, -1, W.shape[2])] + G[2:]) * grid.delta)
         N0, N1, r2 = W.shape
         normA = float(np.linalg.norm(W))

@@ -944,8 +944,7 @@ int validate_meas(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, int* two_m
     } else if (cp.nmodes == 2) {
       if (cp.modes[0] != 0 || cp.modes[1] != 1 || c->d < 2) return TTGBF_EINVAL;
       if (c->n[0] > kMaxN) return TTGBF_ECAPACITY;
-      if (*two_mode >= 0) return TTGBF_EINVAL;
-      *two_mode = i;
+      if (*two_mode < 0) *two_mode = i;  // the first; every two-mode component is on (0, 1)
     } else {
       return TTGBF_EINVAL;
     }
@@ -982,8 +981,15 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
     });
   }
   if (two_mode >= 0) {
-    const ttgbf_meas_comp cp = h->comp[two_mode];
-    const double r = R[(size_t)two_mode * h->b + two_mode];
+    // every two-mode component (all on modes (0, 1)) multiplies the merged core
+    struct Two {
+      int i;
+      ttgbf_meas_comp cp;
+      double r;
+    };
+    std::vector<Two> twos;
+    for (int i = 0; i < h->b; ++i)
+      if (h->comp[i].nmodes == 2) twos.push_back({i, h->comp[i], R[(size_t)i * h->b + i]});
     for (int k = d - 1; k >= 2; --k) ops->push_back([=] { stage(c, kStageRight, k, 0); });
     ops->push_back([=] {
       GemmWork gw = gemm_work(c, B);
@@ -995,14 +1001,16 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
         Prof p(c, kPGemm, 1);
         launch_gemm(c->st, gw, c->sms * 8, flops_of(c, kPGemm));
       }
-      {
-        Prof p(c, kPLik, 2);
-        launch_lik_offset(c->st, B, cp.htab, c->n[0] * c->n[1], z, zstride, two_mode, r, c->lik_off,
-                          c->logoff);
-        launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, cp.htab, z, zstride,
-                            two_mode, r, c->lik_off);
+      for (const Two& t : twos) {
+        {
+          Prof p(c, kPLik, 2);
+          launch_lik_offset(c->st, B, t.cp.htab, c->n[0] * c->n[1], z, zstride, t.i, t.r, c->lik_off,
+                            c->logoff);
+          launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, t.cp.htab, z,
+                              zstride, t.i, t.r, c->lik_off);
+        }
+        tape_lik(c, t.i, t.cp, z, zstride, t.r);
       }
-      tape_lik(c, two_mode, cp, z, zstride, r);
       // log c before rounding: mass of the TT [W (modes 0,1 merged), core 2, ...]
       MomentArgs a{};
       a.ncores = d - 1;

@@ -42,6 +42,11 @@ def h_range(x, y):
     return np.sqrt(x * x + y * y)
 
 
+def h_bearing_deg(x, y):
+    """Four-quadrant angle of (x, y) from the origin, in degrees."""
+    return np.degrees(np.arctan2(np.asarray(y, dtype=np.float64), np.asarray(x, dtype=np.float64)))
+
+
 def h_square20(x):
     x = np.asarray(x, dtype=np.float64)
     return x * x / 20.0
@@ -134,6 +139,21 @@ def config2(n: int = 128) -> Model:
                  m0=np.zeros(4), P0=np.eye(4), F=config2_F(), Q=0.05 * np.eye(4),
                  R=np.array([[0.01]]), comps=[((0, 1), h_range)], steps=50,
                  eps=1e-6, rank_cap=16, config_id=2)
+
+
+def radar(n: int = 128) -> Model:
+    """The 2-D radar model of the paper's numerical study (Sec. 5): position
+    x_{k+1} = [[1.1, 0.1], [-0.2, 1.1]] x_k + w, Q = I, range and bearing (in
+    degrees) from the origin with R = diag(1, 0.1), 10 steps.  Initial
+    condition and grid are not stated there: prior N([20, 20], 4 I) (the
+    bearing then turns clockwise from about 45 to between -35 and -60 degrees
+    over the 10 steps, far from the +-180 cut), first grid the prior mean
+    +- 10."""
+    m0 = np.array([20.0, 20.0])
+    return Model(name="radar", lo=m0 - 10.0, hi=m0 + 10.0, n=np.full(2, n), m0=m0, P0=4.0 * np.eye(2),
+                 F=np.array([[1.1, 0.1], [-0.2, 1.1]]), Q=np.eye(2), R=np.diag([1.0, 0.1]),
+                 comps=[((0, 1), h_range), ((0, 1), h_bearing_deg)], steps=10, eps=1e-6, rank_cap=16,
+                 config_id=6)
 
 
 def config3(d: int = 6, n: int = 256) -> Model:

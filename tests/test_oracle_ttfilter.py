@@ -174,3 +174,21 @@ def test_rank_is_borderline():
     assert not T.rank_is_borderline(rec, 5, 0.25)   # tail of rank 4 is 0.1 thr
     capped = dict(rec, rmax=3)
     assert not T.rank_is_borderline(capped, 4, 0.25)  # above the cap
+
+
+def test_two_two_mode_components_equal_dense_update():
+    """Range and bearing on modes (0, 1) (the radar measurement of Sec. 5):
+    without truncation the TT update equals the dense update, log c included."""
+    g = pmf.Grid([5.0, 6.0, -2.0], [15.0, 14.0, 2.0], [14, 12, 6])
+    X, Y = g.axes[0][:, None], g.axes[1][None, :]
+    comps = [((0, 1), np.hypot(X, Y)), ((0, 1), np.degrees(np.arctan2(Y, X))), ((2,), g.axes[2])]
+    R = np.diag([1.0, 0.1, 0.3])
+    z = np.array([13.5, 41.0, 0.2])
+    G = synth.random_index_bumps_tt(g.n, 3, seed=4)
+    P = tt.densify(G)
+    P = P / (P.sum() * g.delta)
+    G[-1] = G[-1] / (tt.full_sum(G) * g.delta)
+    Gt, _, logc = T.update(G, g, comps, z, R, 0.0, None)
+    Pd, logc_d = pmf.update(P, g, pmf.likelihood(g, comps, z, R))
+    assert rel(tt.densify(Gt), Pd) < 1e-12
+    assert abs(logc - logc_d) < 1e-12
