@@ -142,6 +142,12 @@ typedef struct {
   int32_t nmodes;
   int32_t modes[2];
   const float* htab;
+  /* 0 for an ordinary component.  > 0 for an angle-like one (the bearing of
+   * the radar study of Sec. 5, in degrees: 360): the residual z_c - h_c is
+   * taken modulo period into [-period/2, period/2] before it enters the
+   * Gaussian, so that a bearing near the +-180 cut is compared with the
+   * nearer branch.  Negative or non-finite: TTGBF_EINVAL. */
+  double period;
 } ttgbf_meas_comp;
 
 typedef struct {

@@ -95,11 +95,13 @@ def convolve(P: torch.Tensor, grid: pmf.Grid, m: int, q: torch.Tensor) -> torch.
 
 
 def likelihood(grid: pmf.Grid, comps, z, r: torch.Tensor) -> torch.Tensor:
-    """L(i) = prod_c N(z_c; h_c(xi_i), R_cc), r = diag(R)."""
+    """L(i) = prod_c N(z_c; h_c(xi_i), R_cc), r = diag(R); the residuals as
+    pmf.residual takes them."""
     L = torch.ones(grid.shape, dtype=_T)
-    for c, (modes, table) in enumerate(comps):
-        h = torch.as_tensor(np.asarray(table, dtype=np.float64), dtype=_T)
-        lc = torch.exp(-0.5 * (float(z[c]) - h) ** 2 / r[c]) / torch.sqrt(2 * math.pi * r[c])
+    for c, comp in enumerate(comps):
+        modes, table, period = pmf.unpack_comp(comp)
+        res = torch.as_tensor(pmf.residual(float(z[c]), table, period), dtype=_T)
+        lc = torch.exp(-0.5 * res ** 2 / r[c]) / torch.sqrt(2 * math.pi * r[c])
         if len(modes) == 2 and modes[0] > modes[1]:
             lc = lc.T
         shape = [1] * grid.d

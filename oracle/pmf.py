@@ -262,20 +262,39 @@ def predict_textbook(P: np.ndarray, grid: Grid, F, Q):
 
 
 # ------------------------------------------------------------- update ----
+def unpack_comp(comp):
+    """(modes, table) or (modes, table, period) -> (modes, table, period),
+    period 0 for an ordinary component."""
+    modes, table = comp[0], comp[1]
+    return modes, table, float(comp[2]) if len(comp) > 2 else 0.0
+
+
+def residual(z, h, period=0.0) -> np.ndarray:
+    """z - h.  For an angle-like component (period > 0: the four-quadrant
+    bearing of Sec. 5 in degrees has period 360) the residual is the
+    representative of z - h modulo the period nearest to zero, i.e. the
+    angle is compared on its nearer branch."""
+    r = np.asarray(z, dtype=np.float64) - np.asarray(h, dtype=np.float64)
+    if period > 0.0:
+        r = r - period * np.round(r / period)
+    return r
+
+
 def likelihood(grid: Grid, comps, z, R) -> np.ndarray:
     """Likelihood tensor L (Sec. 4, fourth bullet) of a measurement whose
     components each depend on one or two modes:
-    L(i) = prod_c N(z_c; h_c(xi_i), R_cc).  comps[c] = (modes, table) with
-    table[i_m] or table[i_m, i_n] = h_c at the grid points.  R diagonal."""
+    L(i) = prod_c N(z_c; h_c(xi_i), R_cc).  comps[c] = (modes, table) or
+    (modes, table, period) with table[i_m] or table[i_m, i_n] = h_c at the
+    grid points (period: see residual).  R diagonal."""
     R = np.atleast_2d(np.asarray(R, dtype=np.float64))
     z = np.atleast_1d(np.asarray(z, dtype=np.float64))
     if np.any(R != np.diag(np.diag(R))):
         raise ValueError("R must be diagonal")
     L = np.ones(grid.shape)
-    for c, (modes, table) in enumerate(comps):
+    for c, comp in enumerate(comps):
+        modes, table, period = unpack_comp(comp)
         r = float(R[c, c])
-        h = np.asarray(table, dtype=np.float64)
-        lc = np.exp(-0.5 * (z[c] - h) ** 2 / r) / math.sqrt(2 * math.pi * r)
+        lc = np.exp(-0.5 * residual(z[c], table, period) ** 2 / r) / math.sqrt(2 * math.pi * r)
         shape = [1] * grid.d
         for k, m in enumerate(modes):
             shape[m] = grid.shape[m]

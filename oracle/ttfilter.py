@@ -222,13 +222,12 @@ def predict(cores, grid: pmf.Grid, F, Q, eps, rmax, smax=10, trace=None):
 
 
 # ---------------------------------------------------------------- update ----
-def _lik_factor(table, z, r):
-    h = np.asarray(table, dtype=np.float64)
-    return np.exp(-0.5 * (z - h) ** 2 / r) / math.sqrt(2 * math.pi * r)
+def _lik_factor(table, z, r, period):
+    return np.exp(-0.5 * pmf.residual(z, table, period) ** 2 / r) / math.sqrt(2 * math.pi * r)
 
 
 def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None):
-    """TT Bayes update.  comps = [(modes, table)] as for pmf.likelihood; the
+    """TT Bayes update.  comps = [(modes, table[, period])] as for pmf.likelihood; the
     two-mode components, all on modes (0, 1), multiply the merged 2-site core
     (the likelihood is the product of the components, Eq. pmf_filtrace_a).
     Returns (cores, tails, log c)."""
@@ -237,15 +236,16 @@ def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None):
     G = _cores(cores)
     d = len(G)
     twos = []
-    for c, (modes, table) in enumerate(comps):
+    for c, comp in enumerate(comps):
+        modes, table, period = pmf.unpack_comp(comp)
         r = float(R[c, c])
         if len(modes) == 1:
             m = modes[0]
-            G[m] = G[m] * _lik_factor(table, z[c], r)[None, :, None]
+            G[m] = G[m] * _lik_factor(table, z[c], r, period)[None, :, None]
         else:
             if tuple(modes) != (0, 1):
                 raise ValueError("two-mode components on modes (0, 1) only")
-            twos.append((c, table, r))
+            twos.append((c, table, r, period))
     tails = []
     if not twos:
         logc = math.log(mass(G, grid))
@@ -253,8 +253,8 @@ def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None):
         for k in range(d - 1, 1, -1):
             right_orth(G, k)
         W = np.einsum("ia,ajb->ijb", G[0][0], G[1])
-        for c, table, r in twos:
-            W = W * _lik_factor(table, z[c], r)[:, :, None]
+        for c, table, r, period in twos:
+            W = W * _lik_factor(table, z[c], r, period)[:, :, None]
         logc = math.log(tt.full_sum([W.reshape(1, -1, W.shape[2])] + G[2:]) * grid.delta)
         N0, N1, r2 = W.shape
         normA = float(np.linalg.norm(W))

@@ -73,7 +73,7 @@ CONV = {"auto": 0, "dense": 1, "fft": 2}  # TTGBF_CONV_AUTO / _DENSE / _FFT
 
 class MeasComp(ctypes.Structure):
     _fields_ = [("nmodes", ctypes.c_int32), ("modes", ctypes.c_int32 * 2),
-                ("htab", ctypes.c_void_p)]
+                ("htab", ctypes.c_void_p), ("period", ctypes.c_double)]
 
 
 class Meas(ctypes.Structure):
@@ -323,15 +323,18 @@ class TTFilter:
     @staticmethod
     def _meas(comps):
         arr = (MeasComp * len(comps))()
-        for i, (modes, tab) in enumerate(comps):
+        for i, (modes, tab, *period) in enumerate(comps):
             arr[i].nmodes = len(modes)
             arr[i].modes[0] = int(modes[0])
             arr[i].modes[1] = int(modes[1]) if len(modes) > 1 else -1
             arr[i].htab = ctypes.c_void_p(tab.data_ptr())
+            arr[i].period = float(period[0]) if period else 0.0
         return Meas(len(comps), arr), arr
 
     def update(self, comps, R, z):
-        """comps: [(modes, device float32 table)]; R: (b, b); z: host (batch, b)."""
+        """comps: [(modes, device float32 table[, period])], period > 0 for an
+        angle-like component (ttgbf_meas_comp.period); R: (b, b); z: host
+        (batch, b)."""
         m, keep = self._meas(comps)
         R, z = _f64(R), _f64(z)
         _check(self._lib.ttgbf_update(self._ctx, ctypes.byref(m), _dptr(R), _dptr(z)), "ttgbf_update")

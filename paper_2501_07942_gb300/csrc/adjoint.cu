@@ -212,9 +212,10 @@ __global__ void k_ranks_add(int B, int d, int* ranks, int rstride, int delta) {
 // Likelihood factor of one component as the forward pass applies it
 // (exp(-((z - h)^2 - off) / (2R)), off the per-filter offset), or
 // (which = 1) the derivative of the log of the true likelihood in R,
-// -1/(2R) + (z - h)^2 / (2R^2).
-__device__ __forceinline__ float lik_weight(float z, float h, float off, double R, int which) {
-  const float df = z - h;
+// -1/(2R) + (z - h)^2 / (2R^2); the residual wrapped for an angle-like
+// component (period > 0).
+__device__ __forceinline__ float lik_weight(float z, float h, float off, double R, float period, int which) {
+  const float df = wrap_residual(z - h, period);
   if (which == 0) return expf(-(df * df - off) * (float)(0.5 / R));
   return (float)(-0.5 / R + (double)df * df * (0.5 / (R * R)));
 }
@@ -222,7 +223,8 @@ __device__ __forceinline__ float lik_weight(float z, float h, float off, double 
 // dst core k = weight(i) * src core k (in place when dst == src).
 __global__ void k_lik1(int B, int k, int N, const float* src, long long scap, float* dst, long long dcap,
                        const int* __restrict__ ranks, int rstride, const float* __restrict__ htab,
-                       const float* __restrict__ zv, const float* __restrict__ off, double R, int which) {
+                       const float* __restrict__ zv, const float* __restrict__ off, double R, float period,
+                       int which) {
   const int b = blockIdx.y;
   if (b >= B) return;
   const int ra = ranks[(long long)b * rstride + k], rb = ranks[(long long)b * rstride + k + 1];
@@ -234,7 +236,7 @@ __global__ void k_lik1(int B, int k, int N, const float* src, long long scap, fl
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)((e / rb) % N);
-    t[e] = lik_weight(zb, htab[i], ob, R, which) * s[e];
+    t[e] = lik_weight(zb, htab[i], ob, R, period, which) * s[e];
   }
 }
 
@@ -247,7 +249,7 @@ __global__ void k_lik2_split(int B, int N0, int N1, const float* __restrict__ g0
                              long long o0cap, float* __restrict__ o1, long long o1cap,
                              const int* __restrict__ ranks, int rstride, const float* __restrict__ htab,
                              const float* __restrict__ zv, const float* __restrict__ off, double R,
-                             int which) {
+                             float period, int which) {
   const int b = blockIdx.y;
   if (b >= B) return;
   const int r1 = ranks[(long long)b * rstride + 1], r2 = ranks[(long long)b * rstride + 2];
@@ -265,32 +267,13 @@ __global__ void k_lik2_split(int B, int N0, int N1, const float* __restrict__ g0
     const int i0 = (int)(t / N1), i1 = (int)(t - (long long)i0 * N1);
     float acc = 0.f;
     for (int a = 0; a < r1; ++a) acc = fmaf(G0[(long long)i0 * r1 + a], G1[((long long)a * N1 + i1) * r2 + c], acc);
-    O1[e] = lik_weight(zb, htab[t], ob, R, which) * acc;
+    O1[e] = lik_weight(zb, htab[t], ob, R, period, which) * acc;
   }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N0 * N0;
        e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / N0, j = e - i * N0;
     O0[e] = i == j ? 1.f : 0.f;
   }
-}
-
-// dst = weight(i0, i1) src on a core 1 of shape (N0, N1, r2) whose left index
-// is i0 (the split form above).
-__global__ void k_lik2_weight(int B, int N0, int N1, const float* __restrict__ src, long long scap,
-                              float* __restrict__ dst, long long dcap, const int* __restrict__ ranks,
-                              int rstride, const float* __restrict__ htab, const float* __restrict__ zv,
-                              const float* __restrict__ off, double R, int which) {
-  const int b = blockIdx.y;
-  if (b >= B) return;
-  const int r2 = ranks[(long long)b * rstride + 2];
-  const long long total = (long long)N0 * N1 * r2;
-  if (total > dcap) return;
-  const float zb = zv[b], ob = off[b];
-  const float* s = src + (long long)b * scap;
-  float* t = dst + (long long)b * dcap;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x)
-    t[e] = lik_weight(zb, htab[e / r2], ob, R, which) * s[e];
 }
 
 // ------------------------------------------------------------ scalars
@@ -375,28 +358,21 @@ void launch_add_ones(cudaStream_t st, int B, int d, const float* const* src, con
 
 void launch_lik1(cudaStream_t st, int B, int k, int N, const float* src, long long scap, float* dst,
                  long long dcap, const int* ranks, int rstride, const float* htab, const float* zv,
-                 const float* off, double R, int which) {
+                 const float* off, double R, float period, int which) {
   count_launches(1);
-  k_lik1<<<dim3(16, B), 256, 0, st>>>(B, k, N, src, scap, dst, dcap, ranks, rstride, htab, zv, off, R, which);
+  k_lik1<<<dim3(16, B), 256, 0, st>>>(B, k, N, src, scap, dst, dcap, ranks, rstride, htab, zv, off, R, period,
+                                      which);
 }
 
 void launch_lik2_split(cudaStream_t st, int B, int N0, int N1, const float* g0, long long g0cap,
                        const float* g1, long long g1cap, float* o0, long long o0cap, float* o1,
                        long long o1cap, int* ranks, int rstride, const float* htab, const float* zv,
-                       const float* off, double R, int which) {
+                       const float* off, double R, float period, int which) {
   count_launches(2);
   k_lik2_split<<<dim3(64, B), 256, 0, st>>>(B, N0, N1, g0, g0cap, g1, g1cap, o0, o0cap, o1, o1cap, ranks,
-                                            rstride, htab, zv, off, R, which);
+                                            rstride, htab, zv, off, R, period, which);
   // link 1 now carries the grid index of mode 0
   k_set_link<<<(B + 127) / 128, 128, 0, st>>>(B, ranks, rstride, 1, N0);
-}
-
-void launch_lik2_weight(cudaStream_t st, int B, int N0, int N1, const float* src, long long scap, float* dst,
-                        long long dcap, const int* ranks, int rstride, const float* htab, const float* zv,
-                        const float* off, double R, int which) {
-  count_launches(1);
-  k_lik2_weight<<<dim3(64, B), 256, 0, st>>>(B, N0, N1, src, scap, dst, dcap, ranks, rstride, htab, zv, off,
-                                             R, which);
 }
 
 void launch_scalars(cudaStream_t st, int B, int op, const double* m, const double* val, double delta,

@@ -939,6 +939,7 @@ int validate_meas(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, int* two_m
     if (!(R[(size_t)i * h->b + i] > 0.0)) return TTGBF_EINVAL;
     const ttgbf_meas_comp& cp = h->comp[i];
     if (!cp.htab) return TTGBF_EINVAL;
+    if (!(cp.period >= 0.0) || !std::isfinite(cp.period)) return TTGBF_EINVAL;
     if (cp.nmodes == 1) {
       if (cp.modes[0] < 0 || cp.modes[0] >= c->d) return TTGBF_EINVAL;
     } else if (cp.nmodes == 2) {
@@ -973,9 +974,10 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
     const double r = R[(size_t)i * h->b + i];
     ops->push_back([=] {
       Prof p(c, kPLik, 2);
-      launch_lik_offset(c->st, B, cp.htab, c->n[k], z, zstride, i, r, c->lik_off, c->logoff);
+      launch_lik_offset(c->st, B, cp.htab, c->n[k], z, zstride, i, r, (float)cp.period, c->lik_off,
+                        c->logoff);
       launch_lik_apply_1d(c->st, B, curp(c, k), c->L.core_cap[k], c->n[k], k, d, c->ranks, cp.htab,
-                          z, zstride, i, r, c->lik_off);
+                          z, zstride, i, r, (float)cp.period, c->lik_off);
       if (!(c->canon && c->center == k)) c->canon = false;
       tape_lik(c, i, cp, z, zstride, r);
     });
@@ -1004,10 +1006,10 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
       for (const Two& t : twos) {
         {
           Prof p(c, kPLik, 2);
-          launch_lik_offset(c->st, B, t.cp.htab, c->n[0] * c->n[1], z, zstride, t.i, t.r, c->lik_off,
-                            c->logoff);
+          launch_lik_offset(c->st, B, t.cp.htab, c->n[0] * c->n[1], z, zstride, t.i, t.r,
+                            (float)t.cp.period, c->lik_off, c->logoff);
           launch_lik_apply_2d(c->st, B, c->W, c->L.W_cap, c->n[0], c->n[1], c->ranks, d, t.cp.htab, z,
-                              zstride, t.i, t.r, c->lik_off);
+                              zstride, t.i, t.r, (float)t.cp.period, c->lik_off);
         }
         tape_lik(c, t.i, t.cp, z, zstride, t.r);
       }
@@ -2682,6 +2684,7 @@ struct TapeEntry {
   int comp = -1, nmodes = 0, mode0 = 0;
   const float* htab = nullptr;
   double R = 0.0;
+  float period = 0.f;
 };
 
 struct CkptHost {
@@ -2811,6 +2814,7 @@ void tape_lik(ttgbf_ctx* c, int comp, const ttgbf_meas_comp& cp, const float* z,
   e.mode0 = cp.modes[0];
   e.htab = cp.htab;
   e.R = R;
+  e.period = (float)cp.period;
   char* p = tape_take(a, a->scal_bytes, &e.scal);
   if (!p) return;
   // z of this component and the factor's offset, per filter (floats)
@@ -3047,7 +3051,7 @@ void back_lik(ttgbf_adj* a, const TapeEntry& e) {
   if (e.nmodes == 1) {
     const int k = e.mode0;
     launch_lik_apply_1d(l->st, B, curp(l, k), l->L.core_cap[k], l->n[k], k, d, l->ranks, e.htab, lik_z(a, e), 1,
-                        0, e.R, lik_off(a, e));
+                        0, e.R, e.period, lik_off(a, e));
     if (!(l->canon && l->center == k)) l->canon = false;
     return;
   }
@@ -3057,7 +3061,7 @@ void back_lik(ttgbf_adj* a, const TapeEntry& e) {
   launch_plan_supercore(l->st, B, l->geom, l->ranks, curp(l, 0), curp(l, 1), l->W, l->L.W_cap, gw);
   launch_gemm(l->st, gw, l->sms * 8, flops_of(l, kPGemm));
   launch_lik_apply_2d(l->st, B, l->W, l->L.W_cap, l->n[0], l->n[1], l->ranks, d, e.htab, lik_z(a, e), 1, 0, e.R,
-                      lik_off(a, e));
+                      e.period, lik_off(a, e));
   stage(l, kStageSplit, 0, 1);
   for (int k = 1; k <= d - 2; ++k) stage(l, kStageLeft, k, 0);
   l->canon = true;
@@ -3076,14 +3080,14 @@ void back_upd_in(ttgbf_adj* a, const TapeEntry& e, const std::vector<TapeEntry>&
     if (f.nmodes == 1) {
       const int k = f.mode0;
       launch_lik1(l->st, B, k, l->n[k], curp(l, k), l->L.core_cap[k], a->sB[k], a->lcap[k], l->ranks, d + 1,
-                  f.htab, lik_z(a, f), lik_off(a, f), f.R, 1);
+                  f.htab, lik_z(a, f), lik_off(a, f), f.R, f.period, 1);
       Y.p[k] = a->sB[k];
       Y.cap[k] = a->lcap[k];
     } else {
       cudaMemcpyAsync(a->sranks, l->ranks, sizeof(int) * (size_t)B * (d + 1), cudaMemcpyDeviceToDevice, l->st);
       launch_lik2_split(l->st, B, l->n[0], l->n[1], curp(l, 0), l->L.core_cap[0], curp(l, 1), l->L.core_cap[1],
                         a->sA[0], a->lcap[0], a->sB[1], a->lcap[1], a->sranks, d + 1, f.htab, lik_z(a, f),
-                        lik_off(a, f), f.R, 1);
+                        lik_off(a, f), f.R, f.period, 1);
       Y.p[0] = a->sA[0];
       Y.p[1] = a->sB[1];
       Y.cap[0] = a->lcap[0];

@@ -68,6 +68,7 @@ struct FgLik {
   const void* htab[kFgMaxComps];
   double z[kFgMaxComps];
   double inv2r[kFgMaxComps];
+  double period[kFgMaxComps];  // 0, or the period of an angle-like component
   int ld[kFgMaxComps];  // row length of a two-mode table
 };
 
@@ -520,13 +521,14 @@ __global__ void k_fg_mul(T* P, long long total, T s) {
     P[e] *= s;
 }
 
-// Per component: off_c = min over the table of (z_c - h)^2.
+// Per component: off_c = min over the table of (z_c - h)^2 (the residual
+// wrapped for an angle-like component).
 template <typename H>
-__global__ void k_fg_lik_off(const H* htab, int ntab, double z, double* off) {
+__global__ void k_fg_lik_off(const H* htab, int ntab, double z, double period, double* off) {
   __shared__ double red[32];
   double mn = INFINITY;
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) {
-    const double e = z - (double)htab[i];
+    const double e = ttgbf::wrap_residual(z - (double)htab[i], period);
     mn = fmin(mn, e * e);
   }
 #pragma unroll
@@ -548,7 +550,7 @@ __device__ __forceinline__ T lik_factor(const FgLik& lk, int c, int i0, int i1, 
   long long t = i0;
   if (lk.nmodes[c] == 2) t = (long long)i0 * lk.ld[c] + i1;
   const T h = (T)static_cast<const T*>(lk.htab[c])[t];
-  const T df = (T)lk.z[c] - h;
+  const T df = ttgbf::wrap_residual((T)lk.z[c] - h, (T)lk.period[c]);
   return exp_t<T>(-(df * df - (T)off[c]) * (T)lk.inv2r[c]);
 }
 
@@ -1222,11 +1224,12 @@ int fg_update(ttgbf_fg* c, const ttgbf_meas* h, const double* R, const double* z
     lk.z[i] = z[i];
     const double r = R[(size_t)i * h->b + i];
     lk.inv2r[i] = 0.5 / r;
+    lk.period[i] = cp.period;
     lk.ld[i] = cp.nmodes == 2 ? c->n[cp.modes[1]] : 1;
     const int ntab = cp.nmodes == 2 ? c->n[cp.modes[0]] * c->n[cp.modes[1]] : c->n[cp.modes[0]];
     ttgbf::count_launches(1);
     k_fg_lik_off<T><<<1, 256, 0, c->st>>>(static_cast<const T*>(static_cast<const void*>(cp.htab)), ntab,
-                                         z[i], c->off + i);
+                                         z[i], cp.period, c->off + i);
     logoff += -0.5 * std::log(2.0 * M_PI * r);
   }
   // one pass: the pending normalisations, the likelihood, log c's sum and
@@ -1436,6 +1439,7 @@ int ttgbf_fg_update(ttgbf_fg* c, const ttgbf_meas* h, const double* R, const dou
   for (int i = 0; i < h->b; ++i) {
     const ttgbf_meas_comp& cp = h->comp[i];
     if (!cp.htab || cp.nmodes < 1 || cp.nmodes > 2) return TTGBF_EINVAL;
+    if (!(cp.period >= 0.0) || !std::isfinite(cp.period)) return TTGBF_EINVAL;
     for (int k = 0; k < cp.nmodes; ++k)
       if (cp.modes[k] < 0 || cp.modes[k] >= c->d) return TTGBF_EINVAL;
     if (cp.nmodes == 2 && cp.modes[0] == cp.modes[1]) return TTGBF_EINVAL;

@@ -27,6 +27,15 @@ constexpr int kJacobiSmemFloats = 2 * kMaxN * kMaxN + 8 * kMaxN;  // SVD kernel
 constexpr int kMaxD = 16;           // largest state dimension
 constexpr int kTile = 64;           // GEMM square tile edge
 
+// Residual r = z - h of a measurement component.  An angle-like component
+// (period > 0) has its residual taken modulo the period into [-period/2,
+// period/2]: the nearer branch of the angle (the square of the two ends is
+// the same).
+template <typename T>
+__host__ __device__ __forceinline__ T wrap_residual(T r, T period) {
+  return period > T(0) ? r - period * floor(r / period + T(0.5)) : r;
+}
+
 // A strided matrix view: element (i, j) at p[i * rs + j * cs], i < M, j < n.
 struct MatView {
   const float* p;
@@ -160,14 +169,16 @@ void launch_plan_mode_apply(cudaStream_t st, int B, int k, const TTGeom& g, cons
 void launch_plan_supercore(cudaStream_t st, int B, const TTGeom& g, const int* ranks,
                            const float* c0, const float* c1, float* W, long long W_cap,
                            GemmWork gw);
+// Likelihood factors (ttops.cu).  period: 0, or the period of an angle-like
+// component whose residual is wrapped (wrap_residual).
 void launch_lik_offset(cudaStream_t st, int B, const float* htab, int ntab, const float* z,
-                       int zstride, int zc, double R, float* off, double* logoff);
+                       int zstride, int zc, double R, float period, float* off, double* logoff);
 void launch_lik_apply_2d(cudaStream_t st, int B, float* W, long long W_cap, int N0, int N1,
                          const int* ranks, int d, const float* htab, const float* z, int zstride,
-                         int zc, double R, const float* off);
+                         int zc, double R, float period, const float* off);
 void launch_lik_apply_1d(cudaStream_t st, int B, float* core, long long cap, int N, int k, int d,
                          const int* ranks, const float* htab, const float* z, int zstride, int zc,
-                         double R, const float* off);
+                         double R, float period, const float* off);
 void launch_logc(cudaStream_t st, int B, const double* mass, const double* logoff, double* log_c,
                  double* log_lik);
 // Moments of a TT given by per-core base pointers (filter stride cap[kk]) and
@@ -206,14 +217,11 @@ void launch_add_ones(cudaStream_t st, int B, int d, const float* const* src, con
                      const double* sc, const double* coef);
 void launch_lik1(cudaStream_t st, int B, int k, int N, const float* src, long long scap, float* dst,
                  long long dcap, const int* ranks, int rstride, const float* htab, const float* zv,
-                 const float* off, double R, int which);
+                 const float* off, double R, float period, int which);
 void launch_lik2_split(cudaStream_t st, int B, int N0, int N1, const float* g0, long long g0cap,
                        const float* g1, long long g1cap, float* o0, long long o0cap, float* o1,
                        long long o1cap, int* ranks, int rstride, const float* htab, const float* zv,
-                       const float* off, double R, int which);
-void launch_lik2_weight(cudaStream_t st, int B, int N0, int N1, const float* src, long long scap, float* dst,
-                        long long dcap, const int* ranks, int rstride, const float* htab, const float* zv,
-                        const float* off, double R, int which);
+                       const float* off, double R, float period, int which);
 void launch_scalars(cudaStream_t st, int B, int op, const double* m, const double* val, double delta,
                     double* sc, double* coef, double* grad, int gstride, int gi, double mul);
 void set_adjoint_attributes();

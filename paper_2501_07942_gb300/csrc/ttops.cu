@@ -258,17 +258,18 @@ __global__ void k_plan_supercore(int B, TTGeom g, const int* ranks, const float*
 }
 
 // ----------------------------------------------------------- likelihood
-// Per filter b: off_b = min_i (z_b - h(i))^2 over the component's table, so that
+// Per filter b: off_b = min_i (z_b - h(i))^2 over the component's table (the
+// residual wrapped for an angle-like component, as everywhere below), so that
 // the scaled likelihood exp(-((z-h)^2 - off)/(2R)) is <= 1 with maximum 1.
 // logoff_b accumulates the dropped factor log(exp(-off/(2R)) / sqrt(2 pi R)).
 __global__ void k_lik_offset(int B, const float* htab, int ntab, const float* z, int zstride, int zc,
-                             double R, float* off, double* logoff) {
+                             double R, float period, float* off, double* logoff) {
   const int b = blockIdx.x;
   if (b >= B) return;
   const float zb = z[(long long)b * zstride + zc];
   float mn = INFINITY;
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) {
-    const float e = zb - htab[i];
+    const float e = wrap_residual(zb - htab[i], period);
     mn = fminf(mn, e * e);
   }
   __shared__ float s_m[32];
@@ -288,7 +289,7 @@ __global__ void k_lik_offset(int B, const float* htab, int ntab, const float* z,
 // supercore with the (exact, merged-mode) likelihood of a two-mode component.
 __global__ void k_lik_apply_2d(int B, float* W, long long W_cap, int N0, int N1, int d, const int* ranks,
                                const float* htab, const float* z, int zstride, int zc, double R,
-                               const float* off) {
+                               float period, const float* off) {
   const int b = blockIdx.y;
   if (b >= B) return;
   const int r2 = ranks[(long long)b * (d + 1) + 2];
@@ -300,7 +301,7 @@ __global__ void k_lik_apply_2d(int B, float* W, long long W_cap, int N0, int N1,
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long t = e / r2;  // i0 * N1 + i1
-    const float df = zb - htab[t];
+    const float df = wrap_residual(zb - htab[t], period);
     Wb[e] *= expf(-(df * df - ob) * inv2r);
   }
 }
@@ -308,7 +309,7 @@ __global__ void k_lik_apply_2d(int B, float* W, long long W_cap, int N0, int N1,
 // G_k(a, i, b) *= exp(-((z - h(i))^2 - off) / (2R)): one-mode component.
 __global__ void k_lik_apply_1d(int B, float* core, long long cap, int N, int k, int d, const int* ranks,
                                const float* htab, const float* z, int zstride, int zc, double R,
-                               const float* off) {
+                               float period, const float* off) {
   const int b = blockIdx.y;
   if (b >= B) return;
   const int* rk = ranks + (long long)b * (d + 1);
@@ -321,7 +322,7 @@ __global__ void k_lik_apply_1d(int B, float* core, long long cap, int N, int k, 
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)((e / r1) % N);
-    const float df = zb - htab[i];
+    const float df = wrap_residual(zb - htab[i], period);
     G[e] *= expf(-(df * df - ob) * inv2r);
   }
 }
@@ -588,25 +589,25 @@ void launch_plan_supercore(cudaStream_t st, int B, const TTGeom& g, const int* r
 }
 
 void launch_lik_offset(cudaStream_t st, int B, const float* htab, int ntab, const float* z,
-                       int zstride, int zc, double R, float* off, double* logoff) {
+                       int zstride, int zc, double R, float period, float* off, double* logoff) {
   count_launches(1);
-  k_lik_offset<<<B, 256, 0, st>>>(B, htab, ntab, z, zstride, zc, R, off, logoff);
+  k_lik_offset<<<B, 256, 0, st>>>(B, htab, ntab, z, zstride, zc, R, period, off, logoff);
 }
 
 void launch_lik_apply_2d(cudaStream_t st, int B, float* W, long long W_cap, int N0, int N1,
                          const int* ranks, int d, const float* htab, const float* z, int zstride,
-                         int zc, double R, const float* off) {
+                         int zc, double R, float period, const float* off) {
   count_launches(1);
   k_lik_apply_2d<<<dim3(64, B), 256, 0, st>>>(B, W, W_cap, N0, N1, d, ranks, htab, z, zstride, zc, R,
-                                             off);
+                                             period, off);
 }
 
 void launch_lik_apply_1d(cudaStream_t st, int B, float* core, long long cap, int N, int k, int d,
                          const int* ranks, const float* htab, const float* z, int zstride, int zc,
-                         double R, const float* off) {
+                         double R, float period, const float* off) {
   count_launches(1);
   k_lik_apply_1d<<<dim3(16, B), 256, 0, st>>>(B, core, cap, N, k, d, ranks, htab, z, zstride, zc, R,
-                                             off);
+                                             period, off);
 }
 
 void launch_moments(cudaStream_t st, int B, const MomentArgs& a, const int* ranks, int rstride,

@@ -65,7 +65,7 @@ class Model:
     F: np.ndarray
     Q: np.ndarray
     R: np.ndarray
-    comps: list = field(default_factory=list)   # [(modes tuple, function)]
+    comps: list = field(default_factory=list)   # [(modes tuple, function[, period])]
     steps: int = 10
     eps: float = 1e-6
     rank_cap: int = 16
@@ -81,19 +81,22 @@ class Model:
 
     def h(self, x: np.ndarray) -> np.ndarray:
         """Full measurement function h(x) for one state vector."""
-        return np.array([float(fn(*[x[m] for m in modes])) for modes, fn in self.comps])
+        return np.array([float(fn(*[x[m] for m in modes])) for modes, fn, *_ in self.comps])
 
     def tables(self, axes):
         """Measurement components evaluated on grid axes supplied by the
-        caller: [(modes, table)] with table of shape (N_m,) or (N_m, N_n)."""
+        caller: [(modes, table)] with table of shape (N_m,) or (N_m, N_n);
+        a component declared with a period (an angle) keeps it as a third
+        entry, (modes, table, period)."""
         out = []
-        for modes, fn in self.comps:
+        for modes, fn, *period in self.comps:
             if len(modes) == 1:
-                out.append((modes, fn(np.asarray(axes[modes[0]]))))
+                tab = fn(np.asarray(axes[modes[0]]))
             else:
                 a = np.asarray(axes[modes[0]])[:, None]
                 b = np.asarray(axes[modes[1]])[None, :]
-                out.append((modes, fn(a, b)))
+                tab = fn(a, b)
+            out.append((modes, tab, *period))
         return out
 
 
@@ -144,15 +147,15 @@ def config2(n: int = 128) -> Model:
 def radar(n: int = 128) -> Model:
     """The 2-D radar model of the paper's numerical study (Sec. 5): position
     x_{k+1} = [[1.1, 0.1], [-0.2, 1.1]] x_k + w, Q = I, range and bearing (in
-    degrees) from the origin with R = diag(1, 0.1), 10 steps.  Initial
-    condition and grid are not stated there: prior N([20, 20], 4 I) (the
-    bearing then turns clockwise from about 45 to between -35 and -60 degrees
-    over the 10 steps, far from the +-180 cut), first grid the prior mean
-    +- 10."""
+    degrees, an angle of period 360) from the origin with R = diag(1, 0.1),
+    10 steps.  Initial condition and grid are not stated there: prior
+    N([20, 20], 4 I) (the bearing then turns clockwise from about 45 to
+    between -35 and -60 degrees over the 10 steps, far from the +-180 cut),
+    first grid the prior mean +- 10."""
     m0 = np.array([20.0, 20.0])
     return Model(name="radar", lo=m0 - 10.0, hi=m0 + 10.0, n=np.full(2, n), m0=m0, P0=4.0 * np.eye(2),
                  F=np.array([[1.1, 0.1], [-0.2, 1.1]]), Q=np.eye(2), R=np.diag([1.0, 0.1]),
-                 comps=[((0, 1), h_range), ((0, 1), h_bearing_deg)], steps=10, eps=1e-6, rank_cap=16,
+                 comps=[((0, 1), h_range), ((0, 1), h_bearing_deg, 360.0)], steps=10, eps=1e-6, rank_cap=16,
                  config_id=6)
 
 

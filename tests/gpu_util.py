@@ -64,8 +64,8 @@ def oracle_tt_prior(model):
 
 def device_tables(model: synth.Model, axes):
     import torch
-    return [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device="cuda"))
-            for m, t in model.tables(axes)]
+    return [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device="cuda"), *period)
+            for m, t, *period in model.tables(axes)]
 
 
 def make_filter(G, model: synth.Model, batch=1, rank_cap=None, eps=None, smax=0):
@@ -80,3 +80,17 @@ def densify_filter(f, b=0):
 
 def oracle_grid(model):
     return pmf.Grid(model.lo, model.hi, model.n)
+
+
+def bearing_cut_model(n=(20, 18)):
+    """Range and bearing (an angle of period 360) of an object near the
+    negative x axis, on a fixed grid across it, so that the bearing's residual
+    switches branch inside the grid (the same numbers as the oracle gradient's
+    bearing pin).  Returns (model, measurements (3, 2))."""
+    comps = [((0, 1), synth.workloads.h_range), ((0, 1), synth.workloads.h_bearing_deg, 360.0)]
+    m = synth.Model(name="bearing-cut", lo=np.array([-15.0, -5.0]), hi=np.array([-5.0, 5.0]),
+                    n=np.array(n), m0=np.array([-10.0, 0.0]), P0=2.0 * np.eye(2),
+                    F=np.array([[0.96, 0.05], [-0.04, 0.97]]), Q=np.diag([0.3, 0.25]),
+                    R=np.diag([0.5, 9.0]), comps=comps, eps=1e-6, rank_cap=32)
+    z = np.array([[9.6, 178.0], [9.3, -177.0], [9.0, 179.5]])
+    return m, z

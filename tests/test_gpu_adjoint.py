@@ -22,7 +22,7 @@ import pytest
 import synth
 from oracle import grad, pmf
 
-from gpu_util import device_tables, lib_module, oracle_grid
+from gpu_util import bearing_cut_model, device_tables, lib_module, oracle_grid
 
 pytestmark = pytest.mark.gpu
 
@@ -183,12 +183,18 @@ def _general_model(d):
     return m, g, z
 
 
-@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("d", [2, 3, "bearing"])
 def test_gradient_general_models_match_oracle(G, d):
     """Separate scalings (kernel and scaling not fused), L shears, one-mode
-    likelihood factors (their R-derivative on one core) and, at d = 3, a
-    two-mode range with a one-mode component: against the oracle gradient."""
-    model, g, z = _general_model(d)
+    likelihood factors (their R-derivative on one core), at d = 3 a two-mode
+    range with a one-mode component, and two two-mode components (range and
+    a bearing whose residual wraps across the negative x axis): against the
+    oracle gradient."""
+    if d == "bearing":
+        model, z = bearing_cut_model()
+        g = oracle_grid(model)
+    else:
+        model, g, z = _general_model(d)
     ll, (dF, dQ, dR) = gpu_run(G, model, [z], cap=32, smax=5)
     oc = model.tables(g.axes)
     ll_o, dF_o, dq_o, dr_o = grad.gradient(model.F, model.Q, model.R, g, model.m0, model.P0, oc, list(z))

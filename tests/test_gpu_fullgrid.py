@@ -9,7 +9,7 @@ import pytest
 import synth
 from oracle import pmf
 
-from gpu_util import lib_module
+from gpu_util import bearing_cut_model, lib_module
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,7 @@ def rel_l1(a, b):
 
 def tables(model, axes, dtype):
     import torch
-    return [(m, torch.tensor(np.asarray(t), dtype=dtype, device="cuda")) for m, t in model.tables(axes)]
+    return [(m, torch.tensor(np.asarray(t), dtype=dtype, device="cuda"), *p) for m, t, *p in model.tables(axes)]
 
 
 @pytest.mark.parametrize("transition", ["textbook", "rg"])
@@ -153,3 +153,22 @@ def test_pending_normalisations_in_any_call_order(G):
     f.update(comps, model.R, z[1])
     P, _ = pmf.update(P, g, pmf.likelihood(g, oc, z[1], model.R))
     assert rel_l1(f.density(), P) < 1e-12
+
+
+def test_bearing_across_the_cut_float64(G):
+    """Range and a bearing whose residual wraps inside the grid (period 360):
+    float64 full-grid filter against the dense oracle to 1e-12."""
+    import torch
+    model, zs = bearing_cut_model((40, 36))
+    f = G.FullGridFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), precision=64)
+    g = pmf.Grid(model.lo, model.hi, model.n)
+    comps = tables(model, g.axes, torch.float64)
+    oc = model.tables(g.axes)
+    P = pmf.prior(g, model.m0, model.P0)
+    for z in zs:
+        f.predict(model.F, model.Q)
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+        f.update(comps, model.R, z)
+        P, logc = pmf.update(P, g, pmf.likelihood(g, oc, z, model.R))
+        assert rel_l1(f.density(), P) < 1e-12
+        assert abs(f.estimate()[2] - logc) < 1e-10

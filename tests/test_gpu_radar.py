@@ -6,6 +6,10 @@ Model (synth.radar): x_{k+1} = [[1.1, 0.1], [-0.2, 1.1]] x_k + w, Q = I,
 range and bearing in degrees, R = diag(1, 0.1), 10 steps, prior
 N([20, 20], 4 I), 128 x 128 cells, rank cap 16, eps 1e-6, kappa 5.
 
+* A bearing across the +-180 cut (an object near the negative x axis, a
+  fixed grid across it): the GPU filter, whose likelihood kernels take the
+  bearing's residual on its nearer branch, within the same bound of the
+  dense oracle at every step.
 * Every step of every run: the GPU density within the summed parity bound
   10 (eps + tau) + 1e-5 of the dense oracle's (tau the oracle TT filter's
   tails on the same grids), and the GPU's grid rule equal to the oracle's.
@@ -13,7 +17,10 @@ N([20, 20], 4 I), 128 x 128 cells, rank cap 16, eps 1e-6, kappa 5.
   the TT filter's mean against the true state, per coordinate, differs from
   the dense filter's by less than 1 % (the paper reports 0.004-0.04 % for its
   TT filter and 1.8-5.7 % for its TT-FFT filter, with its own initial
-  condition and grid, which it does not state)."""
+  condition and grid, which it does not state).  Both ways of applying the
+  Gaussian kernel run: the dense banded product (the TT filter, Alg. 2) and
+  the linear convolution through zero-padded cyclic FFTs (the TT-FFT
+  filter, Alg. 3)."""
 import numpy as np
 import pytest
 
@@ -22,7 +29,7 @@ from oracle import grid_design as GD
 from oracle import pmf, tt
 from oracle import ttfilter as T
 
-from gpu_util import device_tables, lib_module, rel, tt_tol
+from gpu_util import bearing_cut_model, device_tables, lib_module, oracle_grid, rel, tt_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +51,8 @@ def _regrid_tt(X, g_old, g_new):
     return X
 
 
-def test_radar_study_tt_vs_dense(G):
+@pytest.mark.parametrize("conv", ["dense", "fft"])
+def test_radar_study_tt_vs_dense(G, conv):
     model = synth.radar()
     d = model.d
     se_tt, se_dense = [], []
@@ -52,7 +60,7 @@ def test_radar_study_tt_vs_dense(G):
     for mc in range(RUNS):
         x, zs = synth.simulate(model, mc)
         f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1,
-                       rank_cap=model.rank_cap, eps=model.eps, max_shift_span=10)
+                       rank_cap=model.rank_cap, eps=model.eps, max_shift_span=10, conv=conv)
         g = pmf.Grid(model.lo, model.hi, model.n)
         P = pmf.prior(g, model.m0, model.P0)
         X = [np.exp(-0.5 * (g.axes[m] - model.m0[m]) ** 2 / model.P0[m, m]).reshape(1, -1, 1)
@@ -87,6 +95,49 @@ def test_radar_study_tt_vs_dense(G):
     rmse_tt = np.sqrt(np.mean(se_tt, axis=0))
     rmse_dense = np.sqrt(np.mean(se_dense, axis=0))
     diff = 100.0 * np.abs(rmse_tt - rmse_dense) / rmse_dense
-    print(f"RMSE (x, y): TT {rmse_tt}, dense {rmse_dense}, difference {diff} %; "
+    print(f"{conv}: RMSE (x, y): TT {rmse_tt}, dense {rmse_dense}, difference {diff} %; "
           f"worst density error / bound {worst:.2f}")
     assert (diff < 1.0).all(), diff
+
+
+def test_bearing_across_the_cut_matches_oracle(G):
+    model, zs = bearing_cut_model((64, 60))
+    g = oracle_grid(model)
+    f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1, rank_cap=32,
+                   eps=model.eps, max_shift_span=5)
+    comps = device_tables(model, f.grid_axes())
+    tables = model.tables(g.axes)
+    P = pmf.prior(g, model.m0, model.P0)
+    X = [np.exp(-0.5 * (g.axes[m] - model.m0[m]) ** 2 / model.P0[m, m]).reshape(1, -1, 1) for m in range(2)]
+    T.normalise(X, g)
+    bound = 0.0
+    for k, z in enumerate(zs):
+        f.predict(model.F, model.Q)
+        f.update(comps, model.R, z[None, :])
+        mean, cov, lc, ll = f.estimate()
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+        P, logc = pmf.update(P, g, pmf.likelihood(g, tables, z, model.R))
+        X, info = T.step(X, g, model.F, model.Q, tables, z, model.R, model.eps, 32, 5)
+        bound += tt_tol(model.eps, info["tail_sum"])
+        e = rel(tt.densify(f.export_cores(0)), P)
+        print(f"step {k}: rel L2 {e:.2e} (bound {bound:.1e}), |log c diff| {abs(lc[0] - logc):.1e}")
+        assert e <= bound, (k, e, bound)
+        assert abs(lc[0] - logc) < 1e-4
+        mo, _ = pmf.moments(P, g)
+        assert (np.abs(mean[0] - mo) <= 1e-3 * g.delta_axis).all(), (k, mean[0], mo)
+    f.free()
+
+
+def test_negative_period_is_rejected(G):
+    import torch
+    model, zs = bearing_cut_model()
+    f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1, rank_cap=32,
+                   eps=model.eps, max_shift_span=5)
+    comps = device_tables(model, f.grid_axes())
+    bad = [comps[0], (comps[1][0], comps[1][1], -360.0)]
+    f.predict(model.F, model.Q)
+    with pytest.raises(G.TTGBFError) as ei:
+        f.update(bad, model.R, zs[:1])
+    assert ei.value.code == -1  # TTGBF_EINVAL
+    f.free()
+    torch.cuda.synchronize()

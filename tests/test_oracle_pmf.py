@@ -315,6 +315,34 @@ def test_likelihood_mode_order_and_one_mode():
             np.testing.assert_allclose(L3[i0, :, i2], v, rtol=1e-13)
 
 
+def test_angle_residual_is_the_nearest_branch():
+    """Brute force: the wrapped residual is, among z - h + 360 k, the one of
+    smallest magnitude (either one at a tie, where the squares agree)."""
+    rng = np.random.default_rng([11, 0])
+    z, h = rng.uniform(-400, 400, 500), rng.uniform(-400, 400, 500)
+    r = pmf.residual(z, h, 360.0)
+    cand = (z - h)[:, None] + 360.0 * np.arange(-4, 5)[None, :]
+    best = cand[np.arange(500), np.argmin(np.abs(cand), axis=1)]
+    np.testing.assert_allclose(r * r, best * best, rtol=1e-12, atol=1e-9)
+    k = (r - (z - h)) / 360.0
+    np.testing.assert_allclose(k, np.round(k), atol=1e-12)
+    assert (np.abs(r) <= 180.0 + 1e-9).all()
+    np.testing.assert_array_equal(pmf.residual(z, h), z - h)
+
+
+def test_bearing_likelihood_across_the_cut():
+    """A bearing component on a grid across the negative x axis: every
+    point's factor is the normal density of its angular distance to z."""
+    g = pmf.Grid([-30.0, -10.0], [-10.0, 10.0], [9, 8])
+    b = np.degrees(np.arctan2(g.axes[1][None, :], g.axes[0][:, None]))
+    L = pmf.likelihood(g, [((0, 1), b, 360.0)], [179.0], [[0.5]])
+    for i0 in range(9):
+        for i1 in range(8):
+            dist = min(abs(179.0 - b[i0, i1]), 360.0 - abs(179.0 - b[i0, i1]))
+            assert L[i0, i1] == pytest.approx(stats.norm(0.0, math.sqrt(0.5)).pdf(dist), rel=1e-12)
+    assert (b.max() > 150.0) and (b.min() < -150.0)  # the grid spans the cut
+
+
 # ----------------------------------------------------------- full filter
 def test_filter_matches_kalman_textbook_and_rg():
     # Linear-Gaussian variant of config 1: the point-mass filter converges to

@@ -176,14 +176,21 @@ def test_rank_is_borderline():
     assert not T.rank_is_borderline(capped, 4, 0.25)  # above the cap
 
 
-def test_two_two_mode_components_equal_dense_update():
+@pytest.mark.parametrize("where", ["first quadrant", "across the cut"])
+def test_two_two_mode_components_equal_dense_update(where):
     """Range and bearing on modes (0, 1) (the radar measurement of Sec. 5):
-    without truncation the TT update equals the dense update, log c included."""
-    g = pmf.Grid([5.0, 6.0, -2.0], [15.0, 14.0, 2.0], [14, 12, 6])
+    without truncation the TT update equals the dense update, log c included;
+    on a grid across the negative x axis the bearing's residual is taken on
+    its nearer branch by both."""
+    if where == "first quadrant":
+        g = pmf.Grid([5.0, 6.0, -2.0], [15.0, 14.0, 2.0], [14, 12, 6])
+        z = np.array([13.5, 41.0, 0.2])
+    else:
+        g = pmf.Grid([-15.0, -4.0, -2.0], [-5.0, 4.0, 2.0], [14, 12, 6])
+        z = np.array([10.5, 178.5, 0.2])
     X, Y = g.axes[0][:, None], g.axes[1][None, :]
-    comps = [((0, 1), np.hypot(X, Y)), ((0, 1), np.degrees(np.arctan2(Y, X))), ((2,), g.axes[2])]
+    comps = [((0, 1), np.hypot(X, Y)), ((0, 1), np.degrees(np.arctan2(Y, X)), 360.0), ((2,), g.axes[2])]
     R = np.diag([1.0, 0.1, 0.3])
-    z = np.array([13.5, 41.0, 0.2])
     G = synth.random_index_bumps_tt(g.n, 3, seed=4)
     P = tt.densify(G)
     P = P / (P.sum() * g.delta)
