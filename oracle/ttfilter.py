@@ -24,6 +24,10 @@ the same operator as the dense oracle (oracle/pmf.py), applied to the cores:
   log of the mass of that product times the cell volume, and W is split by a
   truncated SVD that starts the left-to-right truncation sweep of the rounding
   (the remaining links are truncated in the same sweep).  Then normalisation.
+  A factor on any other set of modes (three or more, or two other than
+  (0, 1)) multiplies the block of cores it spans afterwards, one such factor
+  at a time: exactly, or by the deterministic cross of oracle/cross.py, then
+  the block's links are rounded and the TT normalised; its log c adds.
 * Truncation rule on each link (the reading of the rounding tolerance): keep
   the smallest rank whose discarded singular values have norm <= eps ||A||_F /
   sqrt(d - 1), ||A||_F taken when the sweep starts, then cap the rank at rmax.
@@ -226,25 +230,94 @@ def _lik_factor(table, z, r, period):
     return np.exp(-0.5 * pmf.residual(z, table, period) ** 2 / r) / math.sqrt(2 * math.pi * r)
 
 
-def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None):
+def is_block_comp(modes) -> bool:
+    """Whether a component is applied as a block (by the cross or, for the
+    exact reference, a dense block product): every component other than a
+    one-mode one and a two-mode one on modes (0, 1)."""
+    return len(modes) > 2 or (len(modes) == 2 and tuple(modes) != (0, 1))
+
+
+def block_of(modes):
+    """The block of cores lo..hi a component couples."""
+    return min(modes), max(modes)
+
+
+def block_likelihood(grid: pmf.Grid, modes, factor):
+    """A component's likelihood factor (its table's shape, modes in the
+    component's order) as an array over every grid index of its block."""
+    lo, hi = block_of(modes)
+    order = np.argsort(modes)
+    f = np.transpose(factor, order)
+    shape = [1] * (hi - lo + 1)
+    for m in modes:
+        shape[m - lo] = grid.shape[m]
+    return np.broadcast_to(f.reshape(shape), tuple(grid.shape[lo:hi + 1]))
+
+
+def _exact_block_product(G, lo, hi, lik):
+    """Cores lo..hi <- the exact TT (ranks r_lo, full, ..., r_hi+1) of the
+    block (G_lo ... G_hi) times the likelihood, by successive QR splits of
+    the dense product."""
+    W = G[lo]
+    for k in range(lo + 1, hi + 1):
+        W = np.tensordot(W, G[k], axes=([W.ndim - 1], [0]))
+    W = W * lik[None, ..., None]
+    r0 = W.shape[0]
+    rest = W.reshape(r0, -1)
+    for k in range(lo, hi):
+        n = G[k].shape[1]
+        Qm, Rm = np.linalg.qr(rest.reshape(r0 * n, -1))
+        G[k] = Qm.reshape(r0, n, -1)
+        r0 = G[k].shape[2]
+        rest = Rm
+    G[hi] = rest.reshape(r0, G[hi].shape[1], -1)
+
+
+def update_block(G, grid, comp, z, r, eps, rmax, cross=None, trace=None):
+    """Multiply a normalised TT by the likelihood factor of a block
+    component (modes lo..hi) and round the block's links: the TT is put in
+    canonical form with its center in the block, the block times the factor
+    is formed exactly (cross None) or by the deterministic cross of
+    oracle/cross.py (cross = {"s": rank, "sweeps": n}), log c is the log of
+    the product's mass, and the block is rounded (round_block) and the TT
+    normalised.  Returns (cores, tails, log c)."""
+    from . import cross as X
+    modes, table, period = pmf.unpack_comp(comp)
+    lo, hi = block_of(modes)
+    canonical(G, lo, hi)
+    lik = block_likelihood(grid, modes, _lik_factor(table, z, r, period))
+    if cross is None:
+        _exact_block_product(G, lo, hi, lik)
+    else:
+        G[lo:hi + 1], _ = X.block_cross(G[lo:hi + 1], lik, cross["s"], cross.get("sweeps", 1),
+                                        cross.get("delta", 0.05))
+    logc = math.log(mass(G, grid))
+    tails = round_block(G, lo, hi, eps, rmax, trace)
+    normalise(G, grid)
+    return G, tails, logc
+
+
+def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None, cross=None):
     """TT Bayes update.  comps = [(modes, table[, period])] as for pmf.likelihood; the
-    two-mode components, all on modes (0, 1), multiply the merged 2-site core
-    (the likelihood is the product of the components, Eq. pmf_filtrace_a).
-    Returns (cores, tails, log c)."""
+    two-mode components on modes (0, 1) multiply the merged 2-site core (the
+    likelihood is the product of the components, Eq. pmf_filtrace_a); one-
+    and (0, 1)-components are applied first, with log c, rounding and
+    normalisation; then every block component in turn (update_block), its
+    log c added.  Returns (cores, tails, log c)."""
     R = np.atleast_2d(np.asarray(R, dtype=np.float64))
     z = np.atleast_1d(np.asarray(z, dtype=np.float64))
     G = _cores(cores)
     d = len(G)
-    twos = []
+    twos, blocks = [], []
     for c, comp in enumerate(comps):
         modes, table, period = pmf.unpack_comp(comp)
         r = float(R[c, c])
         if len(modes) == 1:
             m = modes[0]
             G[m] = G[m] * _lik_factor(table, z[c], r, period)[None, :, None]
+        elif is_block_comp(modes):
+            blocks.append((c, comp, r))
         else:
-            if tuple(modes) != (0, 1):
-                raise ValueError("two-mode components on modes (0, 1) only")
             twos.append((c, table, r, period))
     tails = []
     if not twos:
@@ -269,13 +342,17 @@ def update(cores, grid: pmf.Grid, comps, z, R, eps, rmax, trace=None):
         G[1] = (s[:rk, None] * Vt[:rk]).reshape(rk, N1, r2)
         tails += left_sweep(G, 1, d - 1, thr, rmax, normA, trace)
     normalise(G, grid)
+    for c, comp, r in blocks:
+        G, tb, lcb = update_block(G, grid, comp, z[c], r, eps, rmax, cross, trace)
+        tails += tb
+        logc += lcb
     return G, tails, logc
 
 
-def step(cores, grid, F, Q, comps, z, R, eps, rmax, smax=10):
+def step(cores, grid, F, Q, comps, z, R, eps, rmax, smax=10, cross=None):
     """predict -> update.  Returns (cores, dict of tails / log c / mass)."""
     G, tp, mp = predict(cores, grid, F, Q, eps, rmax, smax)
-    G, tu, logc = update(G, grid, comps, z, R, eps, rmax)
+    G, tu, logc = update(G, grid, comps, z, R, eps, rmax, cross=cross)
     return G, {"tails_predict": tp, "tails_update": tu, "tail_sum": float(sum(tp) + sum(tu)),
                "log_c": logc, "mass_pred": mp}
 
