@@ -94,6 +94,17 @@ typedef struct {
   int32_t parts;
   int32_t tsqr_slice_blocks;
   int32_t svd_threads;
+  /* Likelihood factors that couple several modes (ttgbf_meas_comp with three
+   * or more modes, or two modes other than (0, 1)) are applied by a
+   * deterministic TT cross of rank cross_rank (see ttgbf_update).  0 (the
+   * default): no workspace for it, and such components are TTGBF_EINVAL.
+   * Otherwise rank_cap <= cross_rank <= min(64, rank_cap * max_shift_span);
+   * the workspace grows by about batch * (2 cross_rank^2 N_max + 2 (d + 1)
+   * cross_rank^2) floats. */
+  int32_t cross_rank;
+  /* (left-to-right, right-to-left) pairs of cross sweeps before the final
+   * left-to-right sweep; 0 = 1. */
+  int32_t cross_sweeps;
 } ttgbf_opts;
 
 /* How the Gaussian kernel of the predictive step (Eq. tpmconvFFT, applied to
@@ -129,15 +140,23 @@ typedef struct {
 #define TTGBF_PRECISION_FP32 0
 #define TTGBF_PRECISION_FP64 1
 
-/* One measurement component z_c = h_c(x_m [, x_n]) + v_c that depends on one
- * mode or on two adjacent modes (Sec. 4, fourth bullet: the likelihood
- * tensor).  htab is a caller-owned DEVICE array with h_c evaluated at the grid
- * points: n[m] floats, or n[m]*n[n] floats row-major [i_m][i_n].  A two-mode
- * component must be on modes (0, 1) (its Hadamard product is taken on the
- * merged first two cores, whose left TT rank is 1; several such components
- * multiply the merged cores one after the other), with n[0] <= 160.  The
- * library cannot check the size of a device array:
- * a shorter table is read out of bounds. */
+/* One measurement component z_c = h_c(x_...) + v_c (Sec. 4, fourth bullet: the
+ * likelihood tensor).  htab is a caller-owned DEVICE array with h_c evaluated
+ * at the grid points, row-major over the component's modes:
+ *  nmodes = 1: modes[0] = m, n[m] floats; the factor scales core m exactly.
+ *  nmodes = 2, modes = (0, 1): n[0]*n[1] floats [i_0][i_1]; the factor
+ *         multiplies the merged first two cores exactly (their left TT rank
+ *         is 1; several such components multiply them one after the other),
+ *         n[0] <= 160.
+ *  nmodes = 2, any other pair modes = (m, n), m != n: n[m]*n[n] floats
+ *         [i_m][i_n]; applied by the TT cross over the block of cores
+ *         min(m, n)..max(m, n) (opts.cross_rank > 0).
+ *  nmodes = k >= 3: the consecutive modes modes[0] .. modes[1], with
+ *         modes[1] = modes[0] + k - 1; n[modes[0]] * ... * n[modes[1]] floats
+ *         [i_modes[0]]...[i_modes[1]], at most 2^31 - 1; applied by the TT
+ *         cross over that block (opts.cross_rank > 0).
+ * The library cannot check the size of a device array: a shorter table is
+ * read out of bounds. */
 typedef struct {
   int32_t nmodes;
   int32_t modes[2];
@@ -206,7 +225,22 @@ int ttgbf_predict(ttgbf_ctx* ctx, const double* F, const double* Q);
  * likelihood L(i) = prod_c N(z_c; h_c(x_i), R_cc), then TT rounding and
  * normalisation; log c is accumulated into the log-likelihood.
  * R: host b*b row-major, diagonal and positive.  z: HOST array [batch][b]
- * (float64), one measurement vector per filter, copied to the device. */
+ * (float64), one measurement vector per filter, copied to the device.
+ * The one-mode and (0, 1) components are applied first (exactly), with log
+ * c, rounding and normalisation.  Then every other component ("block"
+ * component, see ttgbf_meas_comp) in turn, as its own Bayes update: the TT
+ * is put in mixed canonical form with its center in the component's block
+ * of cores lo..hi; the product of the factor with that block is built by a
+ * deterministic TT cross of rank opts.cross_rank (Sec. 3, Eq. matrixDecomp:
+ * skeletons whose rows and columns are chosen by maximum volume -- Gaussian
+ * elimination with partial pivoting, then row exchanges while an entry of
+ * Q Q[rows]^-1 exceeds 1.05 -- on orthonormal bases of fiber matrices; start
+ * index sets from the density block, opts.cross_sweeps refinement pairs,
+ * a final left-to-right sweep), which evaluates the factor only on the
+ * fibers it visits; log c of the product is added; the block's links are
+ * rounded and the TT normalised.  The adjoint (ttgbf_adj_*) does not record
+ * block components: a recorded update with one makes ttgbf_adj_backward
+ * return TTGBF_ECAPACITY, as for any step the tape cannot hold. */
 int ttgbf_update(ttgbf_ctx* ctx, const ttgbf_meas* h, const double* R, const double* z);
 
 /* Same as ttgbf_update with z a DEVICE array [batch][b] of float32. */

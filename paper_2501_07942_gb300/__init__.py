@@ -64,7 +64,8 @@ class Opts(ctypes.Structure):
                 ("max_shift_span", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("precision", ctypes.c_int32), ("conv", ctypes.c_int32), ("parts", ctypes.c_int32),
-                ("tsqr_slice_blocks", ctypes.c_int32), ("svd_threads", ctypes.c_int32)]
+                ("tsqr_slice_blocks", ctypes.c_int32), ("svd_threads", ctypes.c_int32),
+                ("cross_rank", ctypes.c_int32), ("cross_sweeps", ctypes.c_int32)]
 
 
 PRECISION = {"fp32": 0, "fp64": 1}  # TTGBF_PRECISION_FP32 / TTGBF_PRECISION_FP64
@@ -201,9 +202,10 @@ def _grid(lo, hi, n):
 
 
 def workspace_bytes(lo, hi, n, batch=1, rank_cap=16, eps=1e-6, max_shift_span=0,
-                    precision="fp32", conv="auto") -> int:
+                    precision="fp32", conv="auto", cross_rank=0) -> int:
     g, keep = _grid(lo, hi, n)
-    o = Opts(batch, rank_cap, eps, max_shift_span, None, None, 0, PRECISION[precision], CONV[conv])
+    o = Opts(batch, rank_cap, eps, max_shift_span, None, None, 0, PRECISION[precision], CONV[conv],
+             0, 0, 0, int(cross_rank), 0)
     return int(load().ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o)))
 
 
@@ -279,12 +281,14 @@ class TTFilter:
 
     def __init__(self, lo, hi, n, prior_mean, prior_var, batch=1, rank_cap=16, eps=1e-6,
                  max_shift_span=0, stream=None, device="cuda", precision="fp32", conv="auto",
-                 parts=0, tsqr_slice_blocks=0, svd_threads=0):
+                 parts=0, tsqr_slice_blocks=0, svd_threads=0, cross_rank=0, cross_sweeps=0):
         """precision: "fp32" (R factors and SVDs of the rounding in float32) or
         "fp64" (those of the truncating stages in float64), ttgbf_opts.precision.
         conv: "auto", "dense" or "fft", how the Gaussian kernel is applied
         (ttgbf_opts.conv).  parts, tsqr_slice_blocks, svd_threads: the launch
-        configuration (0 = the library's default; see ttgbf_autotune)."""
+        configuration (0 = the library's default; see ttgbf_autotune).
+        cross_rank, cross_sweeps: the TT cross of likelihood factors on several
+        modes (ttgbf_opts.cross_rank; 0 = not available)."""
         import torch
         self._lib = load()
         self.d = len(n)
@@ -295,7 +299,8 @@ class TTFilter:
         self._stream = torch.cuda.current_stream(device) if stream is None else stream
         o = Opts(self.batch, int(rank_cap), float(eps), int(max_shift_span),
                  ctypes.c_void_p(self._stream.cuda_stream), None, 0, PRECISION[precision],
-                 CONV[conv], int(parts), int(tsqr_slice_blocks), int(svd_threads))
+                 CONV[conv], int(parts), int(tsqr_slice_blocks), int(svd_threads), int(cross_rank),
+                 int(cross_sweeps))
         nbytes = self._lib.ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
         pm, pv = _f64(prior_mean), _f64(prior_var)
         pr = Prior(_dptr(pm), _dptr(pv))
@@ -326,7 +331,8 @@ class TTFilter:
         for i, (modes, tab, *period) in enumerate(comps):
             arr[i].nmodes = len(modes)
             arr[i].modes[0] = int(modes[0])
-            arr[i].modes[1] = int(modes[1]) if len(modes) > 1 else -1
+            # one mode: -1; a pair: the second; three or more (consecutive): the last
+            arr[i].modes[1] = int(modes[-1]) if len(modes) > 1 else -1
             arr[i].htab = ctypes.c_void_p(tab.data_ptr())
             arr[i].period = float(period[0]) if period else 0.0
         return Meas(len(comps), arr), arr

@@ -37,9 +37,9 @@ namespace {
 constexpr int kMaxComps = 16;
 
 enum ProfClass : int { kPTsqr = 0, kPSvd, kPGemm, kPShear, kPMoments, kPLik, kPPlan, kPOther, kPFft,
-                       kPClasses };
+                       kPCross, kPClasses };
 const char* const kProfNames[kPClasses] = {"tsqr", "svd", "gemm", "shear_expand", "moments",
-                                           "likelihood", "plan", "other", "fft_conv"};
+                                           "likelihood", "plan", "other", "fft_conv", "cross"};
 
 // Smallest power of two >= 2N - 1: the length of the zero-padded cyclic
 // convolution that equals the linear one on the grid.
@@ -71,6 +71,8 @@ struct Layout {
   size_t cap_hits, newrank, lik_off;
   size_t tsqr_prob, tsqr_off, tsqr_cnt, stack[2];
   size_t P1, P2, gdesc, gtiles, awork, W, opmats, zbuf, prof_flops, fft_off;
+  size_t xF, xQ, xrn, xmask, xoffI, xoffJ, xU, xV, xsz, xstatus;  // the cross (cross_rank > 0)
+  long long x_fcap = 0, x_mcap = 0;
   size_t total;
   long long core_cap[kMaxD];
   long long stack_cap, W_cap, opmats_floats, awork_stride;
@@ -121,6 +123,10 @@ int validate_opts(const ttgbf_opts* o) {
   if (o->eps < 0.0) return TTGBF_EINVAL;
   const int smax = o->max_shift_span > 0 ? o->max_shift_span : 10;
   if ((long long)o->rank_cap * smax > kMaxN || smax < 2) return TTGBF_ECAPACITY;
+  if (o->cross_sweeps < 0 || o->cross_rank < 0) return TTGBF_EINVAL;
+  if (o->cross_rank > 0 && (o->cross_rank < o->rank_cap || o->cross_rank > kCrossMaxS ||
+                            o->cross_rank > o->rank_cap * smax))
+    return TTGBF_EINVAL;
   return TTGBF_OK;
 }
 
@@ -197,6 +203,23 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   L.opmats = a.take<float>(L.opmats_floats);
   L.zbuf = a.take<float>((size_t)B * kMaxComps);
   L.prof_flops = a.take<double>(kPClasses);
+  if (o->cross_rank > 0) {
+    // fiber matrices: rows <= s * N_max (the block's boundary ranks are at
+    // most the rank cap <= s), columns <= s
+    const long long s = o->cross_rank;
+    L.x_mcap = s * nmax;
+    L.x_fcap = L.x_mcap * s;
+    L.xF = a.take<float>((size_t)B * L.x_fcap);
+    L.xQ = a.take<float>((size_t)B * L.x_fcap);
+    L.xrn = a.take<float>((size_t)B * L.x_mcap);
+    L.xmask = a.take<unsigned>((size_t)B * (L.x_mcap / 32 + 1));
+    L.xoffI = a.take<long long>((size_t)B * (d + 1) * s);
+    L.xoffJ = a.take<long long>((size_t)B * (d + 1) * s);
+    L.xU = a.take<float>((size_t)B * (d + 1) * s * s);
+    L.xV = a.take<float>((size_t)B * (d + 1) * s * s);
+    L.xsz = a.take<int>((size_t)B * 2 * (d + 1));
+    L.xstatus = a.take<int>((size_t)B);
+  }
   L.total = a.off + 256;
   return L;
 }
@@ -218,6 +241,10 @@ struct ttgbf_ctx {
   std::vector<double> lo, hi, dx, axes;
   std::vector<int> axoff;
   int rank_cap = 0, smax = 0, capr = 0;
+  // the cross of block likelihood components: rank (0: not available),
+  // refinement sweeps, and its workspace (per-call fields filled in later)
+  int cross_s = 0, cross_sweeps = 1;
+  CrossArgs x{};
   int precision = TTGBF_PRECISION_FP32;
   int slice_blocks = kTsqrSliceBlocks, svd_threads = 512;
   double eps = 0.0, delta = 1.0;
@@ -929,6 +956,23 @@ int guard(ttgbf_ctx* c) {
   return TTGBF_OK;
 }
 
+// A component applied by the cross: three or more modes, or a pair other
+// than (0, 1).
+bool is_block_comp(const ttgbf_meas_comp& cp) {
+  return cp.nmodes >= 3 || (cp.nmodes == 2 && !(cp.modes[0] == 0 && cp.modes[1] == 1));
+}
+
+// The modes of a component in the order of its table's indices.
+std::vector<int> comp_modes(const ttgbf_meas_comp& cp) {
+  std::vector<int> m;
+  if (cp.nmodes <= 2) {
+    for (int t = 0; t < cp.nmodes; ++t) m.push_back(cp.modes[t]);
+  } else {
+    for (int t = 0; t < cp.nmodes; ++t) m.push_back(cp.modes[0] + t);
+  }
+  return m;
+}
+
 int validate_meas(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, int* two_mode) {
   if (!h || h->b < 1 || h->b > kMaxComps || !h->comp || !R) return TTGBF_EINVAL;
   if (!finite_all(R, (size_t)h->b * h->b)) return TTGBF_ENONFINITE;
@@ -940,14 +984,19 @@ int validate_meas(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, int* two_m
     const ttgbf_meas_comp& cp = h->comp[i];
     if (!cp.htab) return TTGBF_EINVAL;
     if (!(cp.period >= 0.0) || !std::isfinite(cp.period)) return TTGBF_EINVAL;
-    if (cp.nmodes == 1) {
-      if (cp.modes[0] < 0 || cp.modes[0] >= c->d) return TTGBF_EINVAL;
+    if (cp.nmodes < 1 || cp.nmodes > c->d) return TTGBF_EINVAL;
+    for (int t = 0; t < std::min(cp.nmodes, 2); ++t)
+      if (cp.modes[t] < 0 || cp.modes[t] >= c->d) return TTGBF_EINVAL;
+    if (cp.nmodes >= 2 && cp.modes[0] == cp.modes[1]) return TTGBF_EINVAL;
+    if (cp.nmodes >= 3 && cp.modes[1] != cp.modes[0] + cp.nmodes - 1) return TTGBF_EINVAL;
+    if (is_block_comp(cp)) {
+      if (c->cross_s <= 0) return TTGBF_EINVAL;
+      long long ntab = 1;
+      for (const int m : comp_modes(cp)) ntab *= c->n[m];
+      if (ntab > 2147483647LL) return TTGBF_EINVAL;
     } else if (cp.nmodes == 2) {
-      if (cp.modes[0] != 0 || cp.modes[1] != 1 || c->d < 2) return TTGBF_EINVAL;
       if (c->n[0] > kMaxN) return TTGBF_ECAPACITY;
-      if (*two_mode < 0) *two_mode = i;  // the first; every two-mode component is on (0, 1)
-    } else {
-      return TTGBF_EINVAL;
+      if (*two_mode < 0) *two_mode = i;  // the first (0, 1) component
     }
   }
   return TTGBF_OK;
@@ -958,6 +1007,82 @@ int validate_meas(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, int* two_m
 // Every step captures what it needs by value; host-side state (ranks
 // bookkeeping, canonical center) changes in step order.
 using EnqueueOps = std::vector<std::function<void()>>;
+
+// One block component as its own Bayes update: canonical form centred in the
+// block, the cross of the factor times the block (cross.cu), log c of the
+// product added, the block's links rounded, normalisation.
+void enqueue_block_update(ttgbf_ctx* c, const ttgbf_meas_comp& cp, int comp, double r, const float* z,
+                          int zstride) {
+  const int B = c->B, d = c->d;
+  const std::vector<int> modes = comp_modes(cp);
+  const int lo = *std::min_element(modes.begin(), modes.end());
+  const int hi = *std::max_element(modes.begin(), modes.end());
+  const int k = hi - lo + 1;
+  tape_fail(c);  // not recordable by the adjoint
+  enqueue_center_into(c, lo, hi);
+  long long ntab = 1;
+  for (const int m : modes) ntab *= c->n[m];
+  CrossArgs a = c->x;
+  a.B = B;
+  a.d = d;
+  a.lo = lo;
+  a.k = k;
+  a.s = c->cross_s;
+  a.ranks = c->ranks;
+  for (int q = 0; q < k; ++q) {
+    a.core[q] = curp(c, lo + q);
+    a.out[q] = altp(c, lo + q);
+    a.cap[q] = c->L.core_cap[lo + q];
+    a.N[q] = c->n[lo + q];
+    a.stride[q] = 0;
+  }
+  // table strides: row-major over the component's modes in their order
+  long long st = 1;
+  for (int t = (int)modes.size() - 1; t >= 0; --t) {
+    a.stride[modes[t] - lo] = st;
+    st *= c->n[modes[t]];
+  }
+  a.htab = cp.htab;
+  a.z = z;
+  a.zstride = zstride;
+  a.zc = comp;
+  a.R = r;
+  a.period = (float)cp.period;
+  a.off = c->lik_off;
+  cudaMemsetAsync(c->logoff, 0, sizeof(double) * B, c->st);
+  {
+    Prof p(c, kPLik, 1);
+    launch_lik_offset(c->st, B, cp.htab, (int)ntab, z, zstride, comp, r, (float)cp.period, c->lik_off,
+                      c->logoff);
+  }
+  {
+    Prof p(c, kPCross, (k - 1) * (2 * c->cross_sweeps + 2) + 1);
+    for (int q = k - 1; q >= 1; --q) launch_cross_step(c->st, a, q, kCrossStart);
+    for (int sw = 0; sw < c->cross_sweeps; ++sw) {
+      for (int q = 0; q <= k - 2; ++q) launch_cross_step(c->st, a, q, kCrossLR);
+      for (int q = k - 1; q >= 1; --q) launch_cross_step(c->st, a, q, kCrossRL);
+    }
+    for (int q = 0; q <= k - 2; ++q) launch_cross_step(c->st, a, q, kCrossFinal);
+    launch_cross_last(c->st, a);
+  }
+  for (int q = lo; q <= hi; ++q) c->cur[q] ^= 1;
+  c->canon = false;
+  {
+    MomentArgs m = tt_moment_args(c, 0, 0);
+    Prof p(c, kPMoments, 1);
+    launch_moments(c->st, B, m, c->ranks, d + 1, c->awork, c->L.awork_stride, c->mass, nullptr, nullptr);
+  }
+  {
+    Prof p(c, kPOther, 1);
+    launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik, 1);
+  }
+  // round the block's links (the cores outside it are still orthonormal)
+  for (int q = hi; q >= lo + 1; --q) stage(c, kStageRight, q, 0);
+  for (int q = lo; q <= hi - 1; ++q) stage(c, kStageLeft, q, q == lo);
+  c->canon = true;
+  c->center = hi;
+  enqueue_normalise(c, c->mass);
+}
 
 void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z, int zstride,
                 int two_mode, EnqueueOps* ops) {
@@ -991,7 +1116,8 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
     };
     std::vector<Two> twos;
     for (int i = 0; i < h->b; ++i)
-      if (h->comp[i].nmodes == 2) twos.push_back({i, h->comp[i], R[(size_t)i * h->b + i]});
+      if (h->comp[i].nmodes == 2 && !is_block_comp(h->comp[i]))
+        twos.push_back({i, h->comp[i], R[(size_t)i * h->b + i]});
     for (int k = d - 1; k >= 2; --k) ops->push_back([=] { stage(c, kStageRight, k, 0); });
     ops->push_back([=] {
       GemmWork gw = gemm_work(c, B);
@@ -1033,7 +1159,7 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
       }
       {
         Prof p(c, kPOther, 1);
-        launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+        launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik, 0);
       }
       tape_logc(c, c->mass);
     });
@@ -1053,12 +1179,18 @@ void update_ops(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float*
       }
       {
         Prof p(c, kPOther, 1);
-        launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik);
+        launch_logc(c->st, B, c->mass, c->logoff, c->log_c, c->log_lik, 0);
       }
       tape_logc(c, c->mass);
     });
   }
   ops->push_back([=] { enqueue_normalise(c, c->mass); });
+  for (int i = 0; i < h->b; ++i) {
+    const ttgbf_meas_comp cp = h->comp[i];
+    if (!is_block_comp(cp)) continue;
+    const double r = R[(size_t)i * h->b + i];
+    ops->push_back([=] { enqueue_block_update(c, cp, i, r, z, zstride); });
+  }
 }
 
 int enqueue_update(ttgbf_ctx* c, const ttgbf_meas* h, const double* R, const float* z, int zstride,
@@ -1152,6 +1284,8 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   c->slice_blocks = opts->tsqr_slice_blocks > 0 ? opts->tsqr_slice_blocks : kTsqrSliceBlocks;
   c->svd_threads = opts->svd_threads > 0 ? opts->svd_threads : 512;
   c->eps = opts->eps;
+  c->cross_s = opts->cross_rank;
+  c->cross_sweeps = opts->cross_sweeps > 0 ? opts->cross_sweeps : 1;
   c->st = (cudaStream_t)opts->stream;
   {
     const char* dbg = std::getenv("TTGBF_DEBUG_STAGES");
@@ -1242,6 +1376,20 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   c->zbuf = (float*)(b + L.zbuf);
   c->prof_flops = (double*)(b + L.prof_flops);
   c->fft_off = (int*)(b + L.fft_off);
+  if (c->cross_s > 0) {
+    c->x.F = (float*)(b + L.xF);
+    c->x.Qb = (float*)(b + L.xQ);
+    c->x.rn = (float*)(b + L.xrn);
+    c->x.mask = (unsigned*)(b + L.xmask);
+    c->x.offI = (long long*)(b + L.xoffI);
+    c->x.offJ = (long long*)(b + L.xoffJ);
+    c->x.U = (float*)(b + L.xU);
+    c->x.V = (float*)(b + L.xV);
+    c->x.sz = (int*)(b + L.xsz);
+    c->x.status = (int*)(b + L.xstatus);
+    c->x.fcap = L.x_fcap;
+    c->x.mcap = L.x_mcap;
+  }
   if (cudaMallocHost(&c->stage_ops, sizeof(float) * L.opmats_floats) != cudaSuccess ||
       cudaMallocHost(&c->stage_z, sizeof(float) * (size_t)c->B * kMaxComps) != cudaSuccess ||
       cudaMallocHost(&c->stage_est, sizeof(double) * (size_t)c->B * (d + d * d + 2)) != cudaSuccess ||

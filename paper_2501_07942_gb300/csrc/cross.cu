@@ -1,0 +1,588 @@
+// cross.cu -- deterministic tensor-train cross (Sec. 3: the black-box
+// approximation from skeletons, Eq. matrixDecomp, with maximum-volume choices
+// of rows and columns) of the product of a likelihood factor with the block of
+// cores lo..hi of every filter's density TT: the update of Alg. 2, step 2, for
+// a factor that couples several modes.
+//
+// The block tensor T(a, i_lo, ..., i_hi, b) = L(i_lo..i_hi) [G_lo ... G_hi](a, b)
+// has k = hi - lo + 1 "virtual" modes: (a, i_lo) first, (i_hi, b) last, the
+// grid index in between.  With the density's cores left of lo left- and right
+// of hi right-orthonormal (the caller's canonical form), approximating T
+// approximates L (.) P with the same relative error.
+//
+// One CTA per filter takes one step of a sweep at block mode q:
+//   * the step's fiber matrix, float32, column-major in the filter's scratch:
+//     left-to-right rows (alpha in I_q, v in mode q), columns beta in J_{q+1};
+//     right-to-left rows (v, beta in J_{q+1}), columns alpha in I_q; entries
+//     T(alpha, v, beta) = L(...) U_q[alpha] G_q(v) V_{q+1}[beta], U and V the
+//     products of the density's cores along each set element (interfaces);
+//   * its Householder QR and the explicit orthonormal basis Q;
+//   * the maximum-volume rows of Q: Gaussian elimination with partial row
+//     pivoting for a start, then single-row exchanges while an entry of
+//     B = Q Q[rows]^-1 exceeds 1 + delta (the largest entry, the first in
+//     row-major order at a tie);
+//   * the new index set (table offsets and interfaces) and, in the final
+//     sweep, the core B in the density's layout.
+// The start steps choose right sets from the density block alone (columns:
+// its rank index) and pad them to the link's size with the rows of largest
+// norm.  The last kernel writes the last core, the fibers T(I_{k-1}, v), and
+// the block's new ranks.
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace ttgbf {
+namespace {
+
+constexpr int kCT = 512;  // threads per CTA
+constexpr int kCW = kCT / 32;
+constexpr int S = kCrossMaxS;
+constexpr float kDelta = 0.05f;
+constexpr int kMaxvolIters = 100;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread gets the same value (same order).
+__device__ float block_sum(float v, float* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < kCW; ++w) t += red[w];
+  return t;
+}
+
+// Elementwise block sum of part[0..len-1] into out[0..len-1] (shared).
+__device__ void block_vec_sum(const float* part, int len, float* red, float* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  for (int e = 0; e < len; ++e) {
+    const float x = warp_sum(part[e]);
+    if (lane == 0) red[w * S + e] = x;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < len; e += kCT) {
+    float t = 0.f;
+    for (int ww = 0; ww < kCW; ++ww) t += red[ww * S + e];
+    out[e] = t;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool better(float v1, long long i1, float v2, long long i2) {
+  return v1 > v2 || (v1 == v2 && i1 < i2);
+}
+
+// Largest value (the smallest index at a tie) over the block; every thread
+// gets the winner's index (-1 when no thread offered one).
+__device__ long long block_argmax(float v, long long i, float* rv, long long* ri, float* best) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const long long i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    if (better(v2, i2, v, i)) {
+      v = v2;
+      i = i2;
+    }
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    rv[threadIdx.x >> 5] = v;
+    ri[threadIdx.x >> 5] = i;
+  }
+  __syncthreads();
+  float bv = -1.f;
+  long long bi = -1;
+  for (int w = 0; w < kCW; ++w)
+    if (ri[w] >= 0 && (bi < 0 || better(rv[w], ri[w], bv, bi))) {
+      bv = rv[w];
+      bi = ri[w];
+    }
+  *best = bv;
+  return bi;
+}
+
+// Per-filter geometry of the block.
+struct Geo {
+  int k;
+  int r[kMaxD + 1];      // density ranks at links lo .. lo + k
+  long long nv[kMaxD];   // virtual mode sizes
+  __device__ int rl(int q) const { return q == 0 ? 1 : r[q]; }
+  __device__ int rr(int q) const { return q == k - 1 ? 1 : r[q + 1]; }
+  __device__ long long grid(const CrossArgs& a, int q, long long v) const {
+    if (q == 0) return v % a.N[0];
+    if (q == k - 1) return v / r[k];
+    return v;
+  }
+};
+
+// Reads the block's ranks; false if one exceeds the cross rank (the caller's
+// rounding keeps them within the rank cap, which is at most s).
+__device__ bool load_geo(const CrossArgs& a, int b, Geo* g) {
+  const int* rk = a.ranks + (long long)b * (a.d + 1);
+  g->k = a.k;
+  for (int t = 0; t <= a.k; ++t) {
+    g->r[t] = rk[a.lo + t];
+    if (g->r[t] < 1 || g->r[t] > a.s) return false;
+  }
+  for (int q = 0; q < a.k; ++q) {
+    long long n = a.N[q];
+    if (q == 0) n *= g->r[0];
+    if (q == a.k - 1) n *= g->r[a.k];
+    g->nv[q] = n;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float lik_at(const CrossArgs& a, long long idx, float zb, float ob, float inv2r) {
+  const float df = wrap_residual(zb - a.htab[idx], a.period);
+  return expf(-(df * df - ob) * inv2r);
+}
+
+__device__ __forceinline__ bool taken(const unsigned* mask, long long i) {
+  return (mask[i >> 5] >> (i & 31)) & 1u;
+}
+
+__global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind) {
+  const int b = blockIdx.x;
+  if (b >= a.B) return;
+  __shared__ float s_red[kCW * S];
+  __shared__ float s_vec[S];
+  __shared__ float s_brow[S];
+  __shared__ float s_taus[S];
+  __shared__ float s_Qp[S * S];
+  __shared__ float s_Inv[S * S];
+  __shared__ float s_rv[kCW];
+  __shared__ long long s_ri[kCW];
+  __shared__ long long s_piv[S];
+  __shared__ int s_prow;
+  const int tid = threadIdx.x;
+  const int k = a.k, s = a.s, ld = a.d + 1;
+  const bool first = (kind == kCrossStart && q == k - 1);
+  if (first) {
+    if (tid == 0) a.status[b] = 0;
+  } else if (a.status[b] != 0) {
+    return;  // an earlier step of this cross was skipped
+  }
+  Geo g;
+  if (!load_geo(a, b, &g)) {
+    if (tid == 0) a.status[b] = 1;
+    return;
+  }
+  int* szI = a.sz + (long long)b * 2 * ld;
+  int* szJ = szI + ld;
+  long long* offI = a.offI + (long long)b * ld * s;
+  long long* offJ = a.offJ + (long long)b * ld * s;
+  float* U = a.U + (long long)b * ld * s * s;
+  float* V = a.V + (long long)b * ld * s * s;
+  if (first) {
+    // the empty sets at both ends: one element, interface [1]
+    if (tid == 0) {
+      szI[0] = 1;
+      offI[0] = 0;
+      U[0] = 1.f;
+      szJ[k] = 1;
+      offJ[(long long)k * s] = 0;
+      V[(long long)k * s * s] = 1.f;
+    }
+    __syncthreads();
+  }
+  const long long nq = g.nv[q];
+  const int rlq = g.rl(q), rrq = g.rr(q);
+  const float* G = a.core[q] + (long long)b * a.cap[q];
+  const bool lr = (kind == kCrossLR || kind == kCrossFinal);
+  const int sL = (kind == kCrossStart) ? 0 : szI[q];
+  const int sR = szJ[q + 1];
+  long long M;
+  int ncol, target;
+  if (lr) {
+    M = (long long)sL * nq;
+    ncol = sR;
+    target = sR;
+  } else if (kind == kCrossRL) {
+    M = nq * sR;
+    ncol = sL;
+    target = sL;
+  } else {
+    M = nq * sR;
+    ncol = rlq;
+    long long left = 1, right = 1;
+    for (int t = 0; t < q; ++t) left = min(left * g.nv[t], 1LL << 30);
+    for (int t = q; t < k; ++t) right = min(right * g.nv[t], 1LL << 30);
+    target = (int)min((long long)s, min(left, right));
+  }
+  if (ncol > M) ncol = (int)M;
+  if (target > M) target = (int)M;
+  if (M * ncol > a.fcap || M > a.mcap || ncol < 1 || target < 1 ||
+      (kind == kCrossFinal && M * target > a.cap[q])) {
+    if (tid == 0) a.status[b] = 2;
+    return;
+  }
+  const long long* oIq = offI + (long long)q * s;
+  const long long* oJn = offJ + (long long)(q + 1) * s;
+  const float* Uq = U + (long long)q * s * s;
+  const float* Vn = V + (long long)(q + 1) * s * s;
+  float* F = a.F + (long long)b * a.fcap;
+  float* Qb = a.Qb + (long long)b * a.fcap;
+  float* rn = a.rn + (long long)b * a.mcap;
+  unsigned* mask = a.mask + (long long)b * (a.mcap / 32 + 1);
+  const float zb = a.z[(long long)b * a.zstride + a.zc];
+  const float ob = a.off[b];
+  const float inv2r = (float)(0.5 / a.R);
+  const long long strq = a.stride[q];
+
+  // ---- fiber matrix F (M x ncol, column-major)
+  for (long long row = tid; row < M; row += kCT) {
+    if (lr) {
+      const int al = (int)(row / nq);
+      const long long v = row - (long long)al * nq;
+      float w[S];
+      for (int cp = 0; cp < rrq; ++cp) {
+        float acc = 0.f;
+        for (int c = 0; c < rlq; ++c) acc = fmaf(Uq[al * s + c], G[((long long)c * nq + v) * rrq + cp], acc);
+        w[cp] = acc;
+      }
+      const long long base = oIq[al] + g.grid(a, q, v) * strq;
+      for (int be = 0; be < sR; ++be) {
+        float acc = 0.f;
+        for (int cp = 0; cp < rrq; ++cp) acc = fmaf(w[cp], Vn[be * s + cp], acc);
+        F[(long long)be * M + row] = acc * lik_at(a, base + oJn[be], zb, ob, inv2r);
+      }
+    } else {
+      const long long v = row / sR;
+      const int be = (int)(row - v * sR);
+      float y[S];
+      for (int c = 0; c < rlq; ++c) {
+        float acc = 0.f;
+        for (int cp = 0; cp < rrq; ++cp) acc = fmaf(G[((long long)c * nq + v) * rrq + cp], Vn[be * s + cp], acc);
+        y[c] = acc;
+      }
+      if (kind == kCrossStart) {
+        float nn = 0.f;
+        for (int c = 0; c < ncol; ++c) {
+          F[(long long)c * M + row] = y[c];
+          nn = fmaf(y[c], y[c], nn);
+        }
+        rn[row] = nn;
+      } else {
+        const long long baseJ = g.grid(a, q, v) * strq + oJn[be];
+        for (int al = 0; al < sL; ++al) {
+          float acc = 0.f;
+          for (int c = 0; c < rlq; ++c) acc = fmaf(Uq[al * s + c], y[c], acc);
+          F[(long long)al * M + row] = acc * lik_at(a, oIq[al] + baseJ, zb, ob, inv2r);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- Householder QR of F: reflectors in place (v_j in rows j.. of column j)
+  const int n = ncol;
+  for (int j = 0; j < n; ++j) {
+    float ps = 0.f;
+    for (long long i = j + tid; i < M; i += kCT) {
+      const float x = F[(long long)j * M + i];
+      ps = fmaf(x, x, ps);
+    }
+    const float nrm2 = block_sum(ps, s_red);
+    const float x0 = F[(long long)j * M + j];
+    const float nrm = sqrtf(nrm2);
+    const float alpha = (x0 >= 0.f) ? -nrm : nrm;
+    const float v0 = x0 - alpha;
+    const float vn2 = nrm2 - x0 * x0 + v0 * v0;
+    const float tau = (nrm2 > 0.f && vn2 > 0.f) ? 2.f / vn2 : 0.f;
+    __syncthreads();
+    if (tid == 0) {
+      F[(long long)j * M + j] = v0;
+      s_taus[j] = tau;
+    }
+    __syncthreads();
+    const int len = n - j - 1;
+    if (tau != 0.f && len > 0) {
+      float part[S];
+      for (int e = 0; e < len; ++e) part[e] = 0.f;
+      for (long long i = j + tid; i < M; i += kCT) {
+        const float vi = F[(long long)j * M + i];
+        for (int e = 0; e < len; ++e) part[e] = fmaf(vi, F[(long long)(j + 1 + e) * M + i], part[e]);
+      }
+      block_vec_sum(part, len, s_red, s_vec);
+      for (long long i = j + tid; i < M; i += kCT) {
+        const float vi = F[(long long)j * M + i];
+        for (int e = 0; e < len; ++e) F[(long long)(j + 1 + e) * M + i] -= tau * vi * s_vec[e];
+      }
+      __syncthreads();
+    }
+  }
+  // explicit Q (M x n): the reflectors applied to the first n unit vectors
+  for (long long e = tid; e < M * n; e += kCT) {
+    const long long col = e / M, row = e - col * M;
+    Qb[e] = (row == col) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    const float tau = s_taus[j];
+    if (tau == 0.f) continue;
+    const int len = n - j;
+    float part[S];
+    for (int e = 0; e < len; ++e) part[e] = 0.f;
+    for (long long i = j + tid; i < M; i += kCT) {
+      const float vi = F[(long long)j * M + i];
+      for (int e = 0; e < len; ++e) part[e] = fmaf(vi, Qb[(long long)(j + e) * M + i], part[e]);
+    }
+    block_vec_sum(part, len, s_red, s_vec);
+    for (long long i = j + tid; i < M; i += kCT) {
+      const float vi = F[(long long)j * M + i];
+      for (int e = 0; e < len; ++e) Qb[(long long)(j + e) * M + i] -= tau * vi * s_vec[e];
+    }
+    __syncthreads();
+  }
+
+  // ---- maxvol on the first nm columns of Q
+  const int nm = min(n, target);
+  const long long mwords = M / 32 + 1;
+  for (long long e = tid; e < M * nm; e += kCT) F[e] = Qb[e];
+  for (long long e = tid; e < mwords; e += kCT) mask[e] = 0u;
+  __syncthreads();
+  float best;
+  for (int j = 0; j < nm; ++j) {
+    float bv = -1.f;
+    long long bi = -1;
+    for (long long i = tid; i < M; i += kCT) {
+      if (taken(mask, i)) continue;
+      const float x = fabsf(F[(long long)j * M + i]);
+      if (bi < 0 || better(x, i, bv, bi)) {
+        bv = x;
+        bi = i;
+      }
+    }
+    const long long p = block_argmax(bv, bi, s_rv, s_ri, &best);
+    if (p < 0) {  // no free row: cannot happen while nm <= M
+      if (tid == 0) a.status[b] = 3;
+      return;
+    }
+    const float pv = F[(long long)j * M + p];
+    if (tid == 0) {
+      s_piv[j] = p;
+      mask[p >> 5] |= 1u << (p & 31);
+    }
+    const int len = nm - j - 1;
+    if (pv != 0.f && len > 0) {
+      for (int e = tid; e < len; e += kCT) s_brow[e] = F[(long long)(j + 1 + e) * M + p] / pv;
+      __syncthreads();
+      for (long long i = tid; i < M; i += kCT) {
+        const float xi = F[(long long)j * M + i];
+        for (int e = 0; e < len; ++e) F[(long long)(j + 1 + e) * M + i] -= xi * s_brow[e];
+      }
+    }
+    __syncthreads();
+  }
+  // Q[rows]^-1 by Gauss-Jordan elimination with partial pivoting
+  for (int e = tid; e < nm * nm; e += kCT) {
+    const int r = e / nm, c = e - r * nm;
+    s_Qp[r * S + c] = Qb[(long long)c * M + s_piv[r]];
+    s_Inv[r * S + c] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int col = 0; col < nm; ++col) {
+    if (tid == 0) {
+      int pr = col;
+      float pvv = fabsf(s_Qp[col * S + col]);
+      for (int r = col + 1; r < nm; ++r)
+        if (fabsf(s_Qp[r * S + col]) > pvv) {
+          pvv = fabsf(s_Qp[r * S + col]);
+          pr = r;
+        }
+      s_prow = pr;
+    }
+    __syncthreads();
+    const int pr = s_prow;
+    if (pr != col)
+      for (int c = tid; c < nm; c += kCT) {
+        float t = s_Qp[col * S + c];
+        s_Qp[col * S + c] = s_Qp[pr * S + c];
+        s_Qp[pr * S + c] = t;
+        t = s_Inv[col * S + c];
+        s_Inv[col * S + c] = s_Inv[pr * S + c];
+        s_Inv[pr * S + c] = t;
+      }
+    __syncthreads();
+    const float d = s_Qp[col * S + col];
+    if (tid < nm) s_vec[tid] = s_Qp[tid * S + col];
+    __syncthreads();
+    for (int c = tid; c < nm; c += kCT) {
+      s_Qp[col * S + c] /= d;
+      s_Inv[col * S + c] /= d;
+    }
+    __syncthreads();
+    for (int e = tid; e < nm * nm; e += kCT) {
+      const int r = e / nm, c = e - r * nm;
+      if (r == col) continue;
+      s_Qp[r * S + c] -= s_vec[r] * s_Qp[col * S + c];
+      s_Inv[r * S + c] -= s_vec[r] * s_Inv[col * S + c];
+    }
+    __syncthreads();
+  }
+  // B = Q Q[rows]^-1 (M x nm) into F
+  for (long long i = tid; i < M; i += kCT) {
+    float qrow[S];
+    for (int t = 0; t < nm; ++t) qrow[t] = Qb[(long long)t * M + i];
+    for (int c = 0; c < nm; ++c) {
+      float acc = 0.f;
+      for (int t = 0; t < nm; ++t) acc = fmaf(qrow[t], s_Inv[t * S + c], acc);
+      F[(long long)c * M + i] = acc;
+    }
+  }
+  __syncthreads();
+  for (int it = 0; it < kMaxvolIters; ++it) {
+    float bv = -1.f;
+    long long bi = -1;
+    for (long long e = tid; e < M * nm; e += kCT) {
+      const long long i = e / nm;
+      const int c = (int)(e - i * nm);
+      const float x = fabsf(F[(long long)c * M + i]);
+      if (bi < 0 || better(x, e, bv, bi)) {
+        bv = x;
+        bi = e;
+      }
+    }
+    const long long e = block_argmax(bv, bi, s_rv, s_ri, &best);
+    if (e < 0 || !(best > 1.f + kDelta)) break;
+    const long long is = e / nm;
+    const int js = (int)(e - is * nm);
+    const float pvv = F[(long long)js * M + is];
+    for (int c = tid; c < nm; c += kCT) s_brow[c] = F[(long long)c * M + is] - (c == js ? 1.f : 0.f);
+    if (tid == 0) s_piv[js] = is;
+    __syncthreads();
+    for (long long i = tid; i < M; i += kCT) {
+      const float f = F[(long long)js * M + i] / pvv;
+      for (int c = 0; c < nm; ++c) F[(long long)c * M + i] -= f * s_brow[c];
+    }
+    __syncthreads();
+  }
+  // start sets: pad with the rows of largest norm
+  if (target > nm) {
+    for (long long e = tid; e < mwords; e += kCT) mask[e] = 0u;
+    __syncthreads();
+    if (tid == 0)
+      for (int j = 0; j < nm; ++j) mask[s_piv[j] >> 5] |= 1u << (s_piv[j] & 31);
+    __syncthreads();
+    for (int j = nm; j < target; ++j) {
+      float bv = -1.f;
+      long long bi = -1;
+      for (long long i = tid; i < M; i += kCT) {
+        if (taken(mask, i)) continue;
+        if (bi < 0 || better(rn[i], i, bv, bi)) {
+          bv = rn[i];
+          bi = i;
+        }
+      }
+      const long long p = block_argmax(bv, bi, s_rv, s_ri, &best);
+      if (p < 0) {  // no free row: cannot happen while target <= M
+        if (tid == 0) a.status[b] = 3;
+        return;
+      }
+      if (tid == 0) {
+        s_piv[j] = p;
+        mask[p >> 5] |= 1u << (p & 31);
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+
+  // ---- the new index set and its interfaces
+  if (lr) {
+    long long* oN = offI + (long long)(q + 1) * s;
+    float* Un = U + (long long)(q + 1) * s * s;
+    for (int e = tid; e < target * rrq; e += kCT) {
+      const int j = e / rrq, cp = e - j * rrq;
+      const long long row = s_piv[j];
+      const int al = (int)(row / nq);
+      const long long v = row - (long long)al * nq;
+      float acc = 0.f;
+      for (int c = 0; c < rlq; ++c) acc = fmaf(Uq[al * s + c], G[((long long)c * nq + v) * rrq + cp], acc);
+      Un[j * s + cp] = acc;
+      if (cp == 0) oN[j] = oIq[al] + g.grid(a, q, v) * strq;
+    }
+    if (tid == 0) szI[q + 1] = target;
+  } else {
+    long long* oN = offJ + (long long)q * s;
+    float* Vq = V + (long long)q * s * s;
+    for (int e = tid; e < target * rlq; e += kCT) {
+      const int j = e / rlq, c = e - j * rlq;
+      const long long row = s_piv[j];
+      const long long v = row / sR;
+      const int be = (int)(row - v * sR);
+      float acc = 0.f;
+      for (int cp = 0; cp < rrq; ++cp) acc = fmaf(G[((long long)c * nq + v) * rrq + cp], Vn[be * s + cp], acc);
+      Vq[j * s + c] = acc;
+      if (c == 0) oN[j] = g.grid(a, q, v) * strq + oJn[be];
+    }
+    if (tid == 0) szJ[q] = target;
+  }
+  if (kind == kCrossFinal) {
+    // core q = B in the density's layout [alpha][v][j]
+    float* O = a.out[q] + (long long)b * a.cap[q];
+    for (long long e = tid; e < M * target; e += kCT) {
+      const long long row = e / target;
+      const int j = (int)(e - row * target);
+      O[e] = F[(long long)j * M + row];
+    }
+  }
+}
+
+// The last core (fibers T(I_{k-1}, v) over the last virtual mode) and the
+// block's new ranks.
+__global__ void __launch_bounds__(kCT) k_cross_last(CrossArgs a) {
+  const int b = blockIdx.x;
+  if (b >= a.B) return;
+  const int tid = threadIdx.x, k = a.k, s = a.s, ld = a.d + 1;
+  Geo g;
+  if (!load_geo(a, b, &g)) return;
+  if (a.status[b] != 0) return;
+  const int* szI = a.sz + (long long)b * 2 * ld;
+  const int q = k - 1;
+  const int sL = szI[q];
+  const long long nq = g.nv[q];
+  const int rlq = g.rl(q);
+  if ((long long)sL * nq > a.cap[q]) return;
+  const long long* oI = a.offI + ((long long)b * ld + q) * s;
+  const float* Uq = a.U + ((long long)b * ld + q) * s * s;
+  const float* G = a.core[q] + (long long)b * a.cap[q];
+  float* O = a.out[q] + (long long)b * a.cap[q];
+  const float zb = a.z[(long long)b * a.zstride + a.zc];
+  const float ob = a.off[b];
+  const float inv2r = (float)(0.5 / a.R);
+  for (long long e = tid; e < (long long)sL * nq; e += kCT) {
+    const int al = (int)(e / nq);
+    const long long v = e - (long long)al * nq;
+    float acc = 0.f;
+    for (int c = 0; c < rlq; ++c) acc = fmaf(Uq[al * s + c], G[(long long)c * nq + v], acc);
+    O[e] = acc * lik_at(a, oI[al] + g.grid(a, q, v) * a.stride[q], zb, ob, inv2r);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int* rk = a.ranks + (long long)b * ld;
+    for (int l = 1; l < k; ++l) rk[a.lo + l] = szI[l];
+  }
+}
+
+}  // namespace
+
+void launch_cross_step(cudaStream_t st, const CrossArgs& a, int q, int kind) {
+  count_launches(1);
+  k_cross_step<<<a.B, kCT, 0, st>>>(a, q, kind);
+}
+
+void launch_cross_last(cudaStream_t st, const CrossArgs& a) {
+  count_launches(1);
+  k_cross_last<<<a.B, kCT, 0, st>>>(a);
+}
+
+}  // namespace ttgbf

@@ -180,7 +180,7 @@ void launch_lik_apply_1d(cudaStream_t st, int B, float* core, long long cap, int
                          const int* ranks, const float* htab, const float* z, int zstride, int zc,
                          double R, float period, const float* off);
 void launch_logc(cudaStream_t st, int B, const double* mass, const double* logoff, double* log_c,
-                 double* log_lik);
+                 double* log_lik, int add);
 // Moments of a TT given by per-core base pointers (filter stride cap[kk]) and
 // rank indices: core kk has ranks (ranks[b][ridx[kk]], ranks[b][ridx[kk+1]]).
 struct MomentArgs {
@@ -225,6 +225,39 @@ void launch_lik2_split(cudaStream_t st, int B, int N0, int N1, const float* g0, 
 void launch_scalars(cudaStream_t st, int B, int op, const double* m, const double* val, double delta,
                     double* sc, double* coef, double* grad, int gstride, int gi, double mul);
 void set_adjoint_attributes();
+
+// cross.cu: deterministic TT cross of the product of a likelihood factor with
+// the block of cores lo..lo+k-1 of every filter (one CTA per filter per step).
+constexpr int kCrossMaxS = 64;  // largest cross rank
+enum CrossKind : int { kCrossStart = 0, kCrossLR = 1, kCrossRL = 2, kCrossFinal = 3 };
+struct CrossArgs {
+  int B, d, lo, k, s;
+  int* ranks;                  // [B][d+1]: read during the cross, the block's links written last
+  const float* core[kMaxD];    // block cores q = 0..k-1 (current buffers), filter stride cap[q]
+  float* out[kMaxD];           // the result's cores (the other buffers)
+  long long cap[kMaxD];
+  int N[kMaxD];                // grid sizes of the block's modes
+  long long stride[kMaxD];     // offset in the table of one step along each block mode (0: not used)
+  const float* htab;           // the component's table
+  const float* z;              // z[b * zstride + zc]
+  int zstride, zc;
+  double R;
+  float period;
+  const float* off;            // [B] likelihood offsets (k_lik_offset)
+  float* F;                    // [B][fcap] fiber matrix / B = Q Q[rows]^-1 (column-major)
+  float* Qb;                   // [B][fcap] orthonormal basis
+  float* rn;                   // [B][mcap] row norms of the start matrices
+  unsigned* mask;              // [B][mcap / 32 + 1] rows taken (elimination)
+  long long fcap, mcap;
+  long long* offI;             // [B][d+1][s] table offsets of the left index sets
+  long long* offJ;             // [B][d+1][s] ... of the right index sets
+  float* U;                    // [B][d+1][s][s] left interfaces (row vectors)
+  float* V;                    // [B][d+1][s][s] right interfaces
+  int* sz;                     // [B][2][d+1] sizes of the left and right sets
+  int* status;                 // [B] nonzero: a rank of the block exceeded s (the step was skipped)
+};
+void launch_cross_step(cudaStream_t st, const CrossArgs& a, int q, int kind);
+void launch_cross_last(cudaStream_t st, const CrossArgs& a);
 // Process-wide count of kernel launches made by the library (capi.cu).
 void count_launches(int n);
 // Function attributes (large dynamic shared memory); call once per process.

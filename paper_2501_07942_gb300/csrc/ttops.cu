@@ -617,18 +617,21 @@ void launch_moments(cudaStream_t st, int B, const MomentArgs& a, const int* rank
                                                                   awork_stride, mass, mean, cov);
 }
 
-__global__ void k_logc(int B, const double* mass, const double* logoff, double* log_c, double* log_lik) {
+// log c = log(mass) + logoff, added to the log-likelihood; add != 0: also
+// added to this step's log c (a further factor of the same update).
+__global__ void k_logc(int B, const double* mass, const double* logoff, double* log_c, double* log_lik,
+                       int add) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
     const double lc = log(mass[b]) + logoff[b];
-    log_c[b] = lc;
+    log_c[b] = add ? log_c[b] + lc : lc;
     log_lik[b] += lc;
   }
 }
 
 void launch_logc(cudaStream_t st, int B, const double* mass, const double* logoff, double* log_c,
-                 double* log_lik) {
+                 double* log_lik, int add) {
   count_launches(1);
-  k_logc<<<(B + 255) / 256, 256, 0, st>>>(B, mass, logoff, log_c, log_lik);
+  k_logc<<<(B + 255) / 256, 256, 0, st>>>(B, mass, logoff, log_c, log_lik, add);
 }
 
 void set_ttops_attributes() {

@@ -51,6 +51,9 @@ def test_workspace_bytes(lib):
     # float64 rounding: the TSQR stacks hold float64 slice factors (twice the words)
     fp64 = G.workspace_bytes([-8] * 4, [8] * 4, [128] * 4, batch=100, precision="fp64")
     assert fp64 > big
+    # the cross's scratch: 2 s^2 N_max fiber floats, row norms, masks, index sets per filter
+    cross = G.workspace_bytes([-8] * 4, [8] * 4, [128] * 4, batch=100, cross_rank=24)
+    assert cross - big >= 100 * (2 * 24 * 24 * 128 + 2 * 5 * 24 * 24) * 4
     # invalid grids
     assert G.workspace_bytes([0.0], [0.0], [8]) == 0
     assert G.workspace_bytes([0.0], [1.0], [1]) == 0
@@ -60,7 +63,8 @@ def test_workspace_bytes(lib):
 def _init(lib, lo, hi, n, mean, var, **kw):
     g, keep = G._grid(lo, hi, n)
     o = G.Opts(kw.get("batch", 1), kw.get("rank_cap", 16), kw.get("eps", 1e-6),
-               kw.get("smax", 0), None, None, 0, kw.get("precision", 0), kw.get("conv", 0))
+               kw.get("smax", 0), None, None, 0, kw.get("precision", 0), kw.get("conv", 0),
+               0, 0, 0, kw.get("cross_rank", 0), kw.get("cross_sweeps", 0))
     m, v = G._f64(mean), G._f64(var)
     p = G.Prior(G._dptr(m), G._dptr(v))
     ctx = ctypes.c_void_p()
@@ -82,6 +86,12 @@ def test_init_validates_before_device(lib):
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], precision=2)[0] == -1
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], precision=-1)[0] == -1
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], conv=3)[0] == -1
+    # the cross rank: at least the rank cap, at most 64 and the rank capacity
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], cross_rank=8)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], cross_rank=65)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], rank_cap=8, smax=2, cross_rank=24)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], cross_rank=-1)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], cross_rank=24, cross_sweeps=-1)[0] == -1
 
 
 def test_null_context_calls(lib):

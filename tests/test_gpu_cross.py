@@ -1,0 +1,211 @@
+"""Likelihood factors on several modes, applied by the deterministic TT cross
+(ttgbf_opts.cross_rank; csrc/cross.cu), against the oracle.
+
+* One update from a shared input (the oracle TT filter's state, loaded into
+  the GPU filter): a 3-D range ||x[0:3]|| on 32^4 and 64^4 grids, a pair of
+  modes other than (0, 1) (adjacent and not, with an angle's period), all
+  four modes of a 4-D grid, and a batch of filters with different
+  measurements; the GPU density within 10 (eps + tau) + 1e-5 of the dense
+  oracle's update (tau: the tails of the oracle TT filter's exact block
+  product and rounding, oracle/ttfilter.update), log c within 1e-4, means
+  within 1e-3 grid spacings.
+* A filter over several steps (config 2's model with a 3-D range instead of
+  the 2-D one) against the dense oracle, per-step bounds summed.
+* The oracle's own cross on the same input (the algorithm the kernels
+  follow) is checked against the same bound first, so a failure points at
+  the GPU path, not at the method.
+* A block component needs cross_rank > 0 (TTGBF_EINVAL otherwise), and the
+  adjoint does not record one (ttgbf_adj_backward: TTGBF_ECAPACITY)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pmf, tt
+from oracle import ttfilter as T
+
+from gpu_util import lib_module, rel, tt_tol
+
+pytestmark = pytest.mark.gpu
+
+S = 24  # cross rank (rank cap 16 + 8)
+
+
+@pytest.fixture(scope="module")
+def G():
+    return lib_module()
+
+
+def range3(g):
+    a = g.axes
+    return np.sqrt(a[0][:, None, None] ** 2 + a[1][None, :, None] ** 2 + a[2][None, None, :] ** 2)
+
+
+def dev(tab):
+    import torch
+    return torch.tensor(np.ascontiguousarray(tab), dtype=torch.float32, device="cuda")
+
+
+def prior_tt(g, m0, var):
+    X = [np.exp(-0.5 * (g.axes[m] - m0[m]) ** 2 / var[m]).reshape(1, -1, 1) for m in range(g.d)]
+    T.normalise(X, g)
+    return X
+
+
+def step_state(g, m0, var, F, Q, eps, cap, steps=1):
+    """An oracle TT filter state after `steps` predictions (a non-trivial
+    density with ranks > 1), and its densified copy."""
+    X = prior_tt(g, m0, var)
+    for _ in range(steps):
+        X, _, _ = T.predict(X, g, F, Q, eps, cap, 10)
+    return X
+
+
+def load(f, b, X):
+    f.import_cores(b, [np.asarray(c, dtype=np.float32) for c in X], 0.0)
+
+
+def check_update(G, g, Xs, comps_host, comps_dev, zs, R, cap=16, eps=1e-6, smax=10):
+    """Every filter b starts from Xs[b]; one GPU update against the oracle."""
+    B = len(Xs)
+    f = G.TTFilter(g.lo, g.hi, g.shape, np.zeros(g.d), np.ones(g.d), batch=B, rank_cap=cap, eps=eps,
+                   max_shift_span=smax, cross_rank=S)
+    for b in range(B):
+        load(f, b, Xs[b])
+    f.update(comps_dev, R, np.array(zs))
+    mean, cov, lc, ll = f.estimate()
+    out = []
+    for b in range(B):
+        P = tt.densify(Xs[b])
+        P = P / (P.sum() * g.delta)
+        Pd, logc_d = pmf.update(P, g, pmf.likelihood(g, comps_host, zs[b], R))
+        Xe, tails, lce = T.update(Xs[b], g, comps_host, zs[b], R, eps, cap)
+        Xc, tails_c, lcc = T.update(Xs[b], g, comps_host, zs[b], R, eps, cap, cross={"s": S, "sweeps": 1})
+        bound = tt_tol(eps, sum(tails))
+        e_oracle_cross = rel(tt.densify(Xc), Pd)
+        e = rel(tt.densify(f.export_cores(b)), Pd)
+        mo, _ = pmf.moments(Pd, g)
+        print(f"filter {b}: GPU {e:.2e}, oracle cross {e_oracle_cross:.2e}, oracle exact "
+              f"{rel(tt.densify(Xe), Pd):.2e}, bound {bound:.1e}; log c diff {abs(lc[b] - logc_d):.1e}; "
+              f"ranks GPU {f.ranks()[b].tolist()} oracle {tt.ranks(Xe)}")
+        assert e_oracle_cross <= bound  # premise: the method itself meets the bound here
+        assert e <= bound, (b, e, bound)
+        assert abs(lc[b] - logc_d) < 1e-4
+        assert (np.abs(mean[b] - mo) <= 1e-3 * g.delta_axis).all(), (b, mean[b], mo)
+        out.append(e)
+    f.free()
+    return out
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_range3_update(G, n):
+    g = pmf.Grid([-4.0] * 4, [4.0] * 4, [n] * 4)
+    F = 0.95 * np.eye(4) + 0.05 * np.triu(np.ones((4, 4)), 1)
+    X = step_state(g, np.array([1.5, 1.0, 0.5, 0.0]), np.ones(4), F, 0.05 * np.eye(4), 1e-6, 16)
+    tab = range3(g)
+    check_update(G, g, [X], [((0, 1, 2), tab)], [((0, 1, 2), dev(tab))], [np.array([2.2])],
+                 np.array([[0.05]]))
+
+
+def test_batch_of_filters_with_different_measurements(G):
+    g = pmf.Grid([-4.0] * 4, [4.0] * 4, [32] * 4)
+    F = 0.95 * np.eye(4) + 0.05 * np.triu(np.ones((4, 4)), 1)
+    Xs = [step_state(g, m0, np.ones(4), F, 0.05 * np.eye(4), 1e-6, 16)
+          for m0 in (np.array([1.5, 1.0, 0.5, 0.0]), np.array([-1.0, 0.5, 1.0, 0.3]),
+                     np.array([0.2, -1.5, 0.0, -0.4]))]
+    tab = range3(g)
+    check_update(G, g, Xs, [((1, 2, 3), tab)], [((1, 2, 3), dev(tab))],
+                 [np.array([1.6]), np.array([2.4]), np.array([1.1])], np.array([[0.08]]))
+
+
+@pytest.mark.parametrize("pair", [(2, 3), (3, 1)])
+def test_pairs_other_than_01(G, pair):
+    """A bearing-like angle (period 360) on an adjacent pair and a product on
+    a non-adjacent pair given in decreasing mode order, together with a (0, 1)
+    range and a one-mode component."""
+    g = pmf.Grid([-4.0, -4.0, -3.0, -3.0], [4.0, 4.0, 3.0, 3.0], [24, 24, 20, 20])
+    F = 0.95 * np.eye(4) + 0.05 * np.triu(np.ones((4, 4)), 1)
+    X = step_state(g, np.array([1.0, 0.5, -0.5, 0.8]), np.ones(4), F, 0.05 * np.eye(4), 1e-6, 16)
+    a = g.axes
+    rng2 = np.hypot(a[0][:, None], a[1][None, :])
+    if pair == (2, 3):
+        tab = np.degrees(np.arctan2(a[3][None, :], a[2][:, None]))
+        c2 = ((2, 3), tab, 360.0)
+        c2d = ((2, 3), dev(tab), 360.0)
+        z2 = 120.0
+    else:
+        tab = a[3][:, None] + 0.5 * np.sin(a[1][None, :])
+        c2, c2d, z2 = ((3, 1), tab), ((3, 1), dev(tab)), 0.6
+    comps = [((0, 1), rng2), ((2,), a[2]), c2]
+    comps_d = [((0, 1), dev(rng2)), ((2,), dev(a[2])), c2d]
+    check_update(G, g, [X], comps, comps_d, [np.array([1.3, -0.4, z2])], np.diag([0.1, 0.3, 4.0 if pair == (2, 3) else 0.2]))
+
+
+def test_all_four_modes(G):
+    """The block is the whole TT (boundary ranks 1)."""
+    g = pmf.Grid([-3.0] * 4, [3.0] * 4, [16] * 4)
+    F = 0.95 * np.eye(4) + 0.05 * np.triu(np.ones((4, 4)), 1)
+    X = step_state(g, np.array([0.8, 0.4, -0.3, 0.2]), np.ones(4), F, 0.05 * np.eye(4), 1e-6, 16)
+    a = g.axes
+    tab = np.sqrt(a[0][:, None, None, None] ** 2 + a[1][None, :, None, None] ** 2
+                  + a[2][None, None, :, None] ** 2 + a[3][None, None, None, :] ** 2)
+    check_update(G, g, [X], [((0, 1, 2, 3), tab)], [((0, 1, 2, 3), dev(tab))], [np.array([1.7])],
+                 np.array([[0.1]]))
+
+
+def test_filter_with_range3_over_steps(G):
+    """Config 2's model with ||x[0:3]|| as its measurement, 32^4, 4 steps."""
+    base = synth.config2(n=32)
+    model = synth.Model(name="config2-range3", lo=base.lo, hi=base.hi, n=base.n, m0=base.m0, P0=base.P0,
+                        F=base.F, Q=base.Q, R=np.array([[0.02]]),
+                        comps=[((0, 1, 2), lambda x, y, z: np.sqrt(x * x + y * y + z * z))],
+                        steps=4, eps=1e-6, rank_cap=16, config_id=2)
+    g = pmf.Grid(model.lo, model.hi, model.n)
+    x, zs = synth.simulate(model, 0, steps=4)
+    a = g.axes
+    tab = range3(g)
+    f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1, rank_cap=16,
+                   eps=model.eps, max_shift_span=10, cross_rank=S)
+    comps_d = [((0, 1, 2), dev(tab))]
+    comps = [((0, 1, 2), tab)]
+    P = pmf.prior(g, model.m0, model.P0)
+    X = prior_tt(g, model.m0, np.diag(model.P0))
+    bound = 0.0
+    for k, z in enumerate(zs):
+        f.predict(model.F, model.Q)
+        f.update(comps_d, model.R, z[None, :])
+        mean, cov, lc, ll = f.estimate()
+        P, _ = pmf.predict_rg(P, g, model.F, model.Q)
+        P, logc = pmf.update(P, g, pmf.likelihood(g, comps, z, model.R))
+        X, info = T.step(X, g, model.F, model.Q, comps, z, model.R, model.eps, 16, 10)
+        bound += tt_tol(model.eps, info["tail_sum"])
+        e = rel(tt.densify(f.export_cores(0)), P)
+        print(f"step {k}: rel L2 {e:.2e} (bound {bound:.1e}), |log c diff| {abs(lc[0] - logc):.1e}, "
+              f"ranks {f.ranks()[0].tolist()}")
+        assert e <= bound, (k, e, bound)
+        assert abs(lc[0] - logc) < 1e-4
+    f.free()
+
+
+def test_block_component_needs_cross_rank_and_is_not_recorded(G):
+    g = pmf.Grid([-3.0] * 3, [3.0] * 3, [12] * 3)
+    a = g.axes
+    tab = dev(np.sqrt(a[0][:, None, None] ** 2 + a[1][None, :, None] ** 2 + a[2][None, None, :] ** 2))
+    f = G.TTFilter(g.lo, g.hi, g.shape, np.zeros(3), np.ones(3), batch=1, rank_cap=16, eps=1e-6,
+                   max_shift_span=5)
+    with pytest.raises(G.TTGBFError) as ei:
+        f.update([((0, 1, 2), tab)], np.array([[0.1]]), np.array([[1.0]]))
+    assert ei.value.code == -1
+    f.free()
+    f = G.TTFilter(g.lo, g.hi, g.shape, np.zeros(3), np.ones(3), batch=1, rank_cap=16, eps=1e-6,
+                   max_shift_span=5, cross_rank=S)
+    adj = G.Adjoint(f, 1, 1)
+    adj.save(0)
+    adj.record(True)
+    f.predict(np.eye(3) * 0.9, np.eye(3) * 0.1)
+    f.update([((0, 1, 2), tab)], np.array([[0.1]]), np.array([[1.0]]))
+    adj.record(False)
+    with pytest.raises(G.TTGBFError) as ei:
+        adj.backward()
+    assert ei.value.code == -5
+    adj.free()
+    f.free()
