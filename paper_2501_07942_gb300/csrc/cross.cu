@@ -58,6 +58,18 @@ __device__ float block_sum(float v, float* red) {
   return t;
 }
 
+// Largest value over the block; every thread gets it.
+__device__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = red[0];
+  for (int w = 1; w < kCW; ++w) t = fmaxf(t, red[w]);
+  return t;
+}
+
 // Elementwise block sum of part[0..len-1] into out[0..len-1] (shared).
 __device__ void block_vec_sum(const float* part, int len, float* red, float* out) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -282,26 +294,35 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   }
   __syncthreads();
 
-  // ---- Householder QR of F: reflectors in place (v_j in rows j.. of column j)
+  // ---- Householder QR of F: reflectors H_j = I - tau_j v_j v_j^T in place,
+  // v_j in rows j.. of column j with v_j(j) = 1 (the scaled form: the fibers
+  // span many decades, and squares of entries near 1e-20 are below float32's
+  // normal range, so the norm is taken of the column divided by its largest
+  // magnitude, and tau = (beta - x0) / beta lies in [1, 2]).  A column whose
+  // largest magnitude is below the smallest normal float counts as zero.
   const int n = ncol;
   for (int j = 0; j < n; ++j) {
-    float ps = 0.f;
-    for (long long i = j + tid; i < M; i += kCT) {
-      const float x = F[(long long)j * M + i];
-      ps = fmaf(x, x, ps);
+    float am = 0.f;
+    for (long long i = j + tid; i < M; i += kCT) am = fmaxf(am, fabsf(F[(long long)j * M + i]));
+    const float amax = block_max(am, s_red);
+    float tau = 0.f;
+    if (amax >= 1.17549435e-38f) {
+      const float inv = 1.f / amax;
+      float ps = 0.f;
+      for (long long i = j + tid; i < M; i += kCT) {
+        const float x = F[(long long)j * M + i] * inv;
+        ps = fmaf(x, x, ps);
+      }
+      const float nrm = sqrtf(block_sum(ps, s_red));  // of the scaled column
+      const float x0 = F[(long long)j * M + j] * inv;
+      const float beta = (x0 >= 0.f) ? -nrm : nrm;
+      tau = (beta - x0) / beta;
+      const float dv = 1.f / (x0 - beta);
+      __syncthreads();
+      for (long long i = j + 1 + tid; i < M; i += kCT) F[(long long)j * M + i] = (F[(long long)j * M + i] * inv) * dv;
+      if (tid == 0) F[(long long)j * M + j] = 1.f;
     }
-    const float nrm2 = block_sum(ps, s_red);
-    const float x0 = F[(long long)j * M + j];
-    const float nrm = sqrtf(nrm2);
-    const float alpha = (x0 >= 0.f) ? -nrm : nrm;
-    const float v0 = x0 - alpha;
-    const float vn2 = nrm2 - x0 * x0 + v0 * v0;
-    const float tau = (nrm2 > 0.f && vn2 > 0.f) ? 2.f / vn2 : 0.f;
-    __syncthreads();
-    if (tid == 0) {
-      F[(long long)j * M + j] = v0;
-      s_taus[j] = tau;
-    }
+    if (tid == 0) s_taus[j] = tau;
     __syncthreads();
     const int len = n - j - 1;
     if (tau != 0.f && len > 0) {
