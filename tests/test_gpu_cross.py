@@ -11,7 +11,8 @@
   within 1e-3 grid spacings plus 2 tau sigma (the rank cap binds on the 3-D
   range: gpu_util.mean_tol).
 * A filter over several steps (config 2's model with a 3-D range instead of
-  the 2-D one) against the dense oracle, per-step bounds summed.
+  the 2-D one) against the dense oracle, per-step bounds summed; log c within
+  1e-3 of the dense filter's and 1e-4 of the oracle TT filter's.
 * The oracle's own cross on the same input (the algorithm the kernels
   follow) is checked against the same bound first, so a failure points at
   the GPU path, not at the method.
@@ -183,7 +184,12 @@ def test_filter_with_range3_over_steps(G):
         print(f"step {k}: rel L2 {e:.2e} (bound {bound:.1e}), |log c diff| {abs(lc[0] - logc):.1e}, "
               f"ranks {f.ranks()[0].tolist()}")
         assert e <= bound, (k, e, bound)
-        assert abs(lc[0] - logc) < 1e-4
+        # against the dense filter as the other horizons are held (1e-3: the
+        # capped TT's predictive density differs from the dense one by ~1e-3
+        # here); against the oracle TT filter, which makes the same
+        # truncations, to the one-step 1e-4
+        assert abs(lc[0] - logc) < 1e-3
+        assert abs(lc[0] - info["log_c"]) < 1e-4, (k, lc[0], info["log_c"])
     f.free()
 
 
