@@ -447,7 +447,9 @@ int ttgbf_fg_predict_direct(ttgbf_fg* fg, const double* F, const double* Q);
 
 /* Bayes update with one measurement vector z (HOST, b doubles).  The htab
  * pointers of h are DEVICE arrays of float (precision 32) or double
- * (precision 64); components may use any one or two modes. */
+ * (precision 64); components may use any one or two modes, or three or more
+ * consecutive ones (the layouts of ttgbf_meas_comp), applied exactly at every
+ * grid point. */
 int ttgbf_fg_update(ttgbf_fg* fg, const ttgbf_meas* h, const double* R, const double* z);
 
 /* Mean [d], covariance [d][d], this step's log c and the cumulative log

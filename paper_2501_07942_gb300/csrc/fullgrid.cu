@@ -63,13 +63,13 @@ struct FgGeom {
 
 struct FgLik {
   int b;
-  int modes[kFgMaxComps][2];
-  int nmodes[kFgMaxComps];
   const void* htab[kFgMaxComps];
   double z[kFgMaxComps];
   double inv2r[kFgMaxComps];
   double period[kFgMaxComps];  // 0, or the period of an angle-like component
-  int ld[kFgMaxComps];  // row length of a two-mode table
+  // offset in the component's table of one step along each axis (0: the
+  // component does not depend on it); the table is row-major over its modes
+  long long tstride[kFgMaxComps][ttgbf::kMaxD];
 };
 
 __device__ __forceinline__ int axis_index(long long e, const FgGeom& g, int m) {
@@ -545,10 +545,18 @@ __global__ void k_fg_lik_off(const H* htab, int ntab, double z, double period, d
 // P <- P * prod_c exp(-((z_c - h_c)^2 - off_c) / (2 R_c)); acc += sum of the result.
 // One warp per row of the last axis: factors of components that do not use
 // the last axis are evaluated once per row.
+// Table offset of component c at the point of the row starting at e0, the
+// last axis left out.
+__device__ __forceinline__ long long lik_row_offset(const FgLik& lk, int c, long long e0, const FgGeom& g,
+                                                     int last) {
+  long long t = 0;
+  for (int m = 0; m < g.d; ++m)
+    if (m != last && lk.tstride[c][m] != 0) t += (long long)axis_index(e0, g, m) * lk.tstride[c][m];
+  return t;
+}
+
 template <typename T>
-__device__ __forceinline__ T lik_factor(const FgLik& lk, int c, int i0, int i1, const double* off) {
-  long long t = i0;
-  if (lk.nmodes[c] == 2) t = (long long)i0 * lk.ld[c] + i1;
+__device__ __forceinline__ T lik_factor(const FgLik& lk, int c, long long t, const double* off) {
   const T h = (T)static_cast<const T*>(lk.htab[c])[t];
   const T df = ttgbf::wrap_residual((T)lk.z[c] - h, (T)lk.period[c]);
   return exp_t<T>(-(df * df - (T)off[c]) * (T)lk.inv2r[c]);
@@ -567,22 +575,15 @@ __global__ void k_fg_lik(T* P, FgGeom g, FgLik lk, const double* off, double* ac
   for (long long r = warp0; r < rows; r += nwarps) {
     const long long e0 = r * NL;
     T Lrow = 1;
+    long long rb[kFgMaxComps];
     for (int c = 0; c < lk.b; ++c) {
-      const bool uses_last = lk.modes[c][0] == last || (lk.nmodes[c] == 2 && lk.modes[c][1] == last);
-      if (uses_last) continue;
-      const int i0 = axis_index(e0, g, lk.modes[c][0]);
-      const int i1 = lk.nmodes[c] == 2 ? axis_index(e0, g, lk.modes[c][1]) : 0;
-      Lrow *= lik_factor<T>(lk, c, i0, i1, off);
+      rb[c] = lik_row_offset(lk, c, e0, g, last);
+      if (lk.tstride[c][last] == 0) Lrow *= lik_factor<T>(lk, c, rb[c], off);
     }
     for (int il = lane; il < NL; il += 32) {
       T L = Lrow;
-      for (int c = 0; c < lk.b; ++c) {
-        const bool uses_last = lk.modes[c][0] == last || (lk.nmodes[c] == 2 && lk.modes[c][1] == last);
-        if (!uses_last) continue;
-        const int i0 = lk.modes[c][0] == last ? il : axis_index(e0, g, lk.modes[c][0]);
-        const int i1 = lk.nmodes[c] == 2 ? (lk.modes[c][1] == last ? il : axis_index(e0, g, lk.modes[c][1])) : 0;
-        L *= lik_factor<T>(lk, c, i0, i1, off);
-      }
+      for (int c = 0; c < lk.b; ++c)
+        if (lk.tstride[c][last] != 0) L *= lik_factor<T>(lk, c, rb[c] + (long long)il * lk.tstride[c][last], off);
       const T v = P[e0 + il] * L;
       P[e0 + il] = v;
       k.add(v);
@@ -655,23 +656,16 @@ __global__ void k_fg_lik_mom(T* P, FgGeom g, FgLik lk, const double* off, const 
   for (long long r = warp0; r < rows; r += nwarps) {
     const long long e0 = r * NL;
     T Lrow = sc;
+    long long rb[kFgMaxComps];
     for (int c = 0; c < lk.b; ++c) {
-      const bool uses_last = lk.modes[c][0] == LAST || (lk.nmodes[c] == 2 && lk.modes[c][1] == LAST);
-      if (uses_last) continue;
-      const int i0 = axis_index(e0, g, lk.modes[c][0]);
-      const int i1 = lk.nmodes[c] == 2 ? axis_index(e0, g, lk.modes[c][1]) : 0;
-      Lrow *= lik_factor<T>(lk, c, i0, i1, off);
+      rb[c] = lik_row_offset(lk, c, e0, g, LAST);
+      if (lk.tstride[c][LAST] == 0) Lrow *= lik_factor<T>(lk, c, rb[c], off);
     }
     Kahan<T> a0, a1, a2;
     for (int il = lane; il < NL; il += 32) {
       T L = Lrow;
-      for (int c = 0; c < lk.b; ++c) {
-        const bool uses_last = lk.modes[c][0] == LAST || (lk.nmodes[c] == 2 && lk.modes[c][1] == LAST);
-        if (!uses_last) continue;
-        const int i0 = lk.modes[c][0] == LAST ? il : axis_index(e0, g, lk.modes[c][0]);
-        const int i1 = lk.nmodes[c] == 2 ? (lk.modes[c][1] == LAST ? il : axis_index(e0, g, lk.modes[c][1])) : 0;
-        L *= lik_factor<T>(lk, c, i0, i1, off);
-      }
+      for (int c = 0; c < lk.b; ++c)
+        if (lk.tstride[c][LAST] != 0) L *= lik_factor<T>(lk, c, rb[c] + (long long)il * lk.tstride[c][LAST], off);
       const T v = P[e0 + il] * L;
       P[e0 + il] = v;
       const T xl = lol + ((T)il + (T)0.5) * dxl;
@@ -1217,16 +1211,20 @@ int fg_update(ttgbf_fg* c, const ttgbf_meas* h, const double* R, const double* z
   std::vector<double> offs(h->b);
   for (int i = 0; i < h->b; ++i) {
     const ttgbf_meas_comp& cp = h->comp[i];
-    lk.nmodes[i] = cp.nmodes;
-    lk.modes[i][0] = cp.modes[0];
-    lk.modes[i][1] = cp.nmodes == 2 ? cp.modes[1] : 0;
+    // the component's modes in its table's order, and their strides
+    int modes[ttgbf::kMaxD];
+    for (int t = 0; t < cp.nmodes; ++t) modes[t] = cp.nmodes <= 2 ? cp.modes[t] : cp.modes[0] + t;
+    long long st = 1;
+    for (int t = cp.nmodes - 1; t >= 0; --t) {
+      lk.tstride[i][modes[t]] = st;
+      st *= c->n[modes[t]];
+    }
+    const int ntab = (int)st;
     lk.htab[i] = cp.htab;
     lk.z[i] = z[i];
     const double r = R[(size_t)i * h->b + i];
     lk.inv2r[i] = 0.5 / r;
     lk.period[i] = cp.period;
-    lk.ld[i] = cp.nmodes == 2 ? c->n[cp.modes[1]] : 1;
-    const int ntab = cp.nmodes == 2 ? c->n[cp.modes[0]] * c->n[cp.modes[1]] : c->n[cp.modes[0]];
     ttgbf::count_launches(1);
     k_fg_lik_off<T><<<1, 256, 0, c->st>>>(static_cast<const T*>(static_cast<const void*>(cp.htab)), ntab,
                                          z[i], cp.period, c->off + i);
@@ -1438,11 +1436,15 @@ int ttgbf_fg_update(ttgbf_fg* c, const ttgbf_meas* h, const double* R, const dou
   if (!h || h->b < 1 || h->b > kFgMaxComps || !h->comp || !R || !z) return TTGBF_EINVAL;
   for (int i = 0; i < h->b; ++i) {
     const ttgbf_meas_comp& cp = h->comp[i];
-    if (!cp.htab || cp.nmodes < 1 || cp.nmodes > 2) return TTGBF_EINVAL;
+    if (!cp.htab || cp.nmodes < 1 || cp.nmodes > c->d) return TTGBF_EINVAL;
     if (!(cp.period >= 0.0) || !std::isfinite(cp.period)) return TTGBF_EINVAL;
-    for (int k = 0; k < cp.nmodes; ++k)
+    for (int k = 0; k < std::min(cp.nmodes, 2); ++k)
       if (cp.modes[k] < 0 || cp.modes[k] >= c->d) return TTGBF_EINVAL;
-    if (cp.nmodes == 2 && cp.modes[0] == cp.modes[1]) return TTGBF_EINVAL;
+    if (cp.nmodes >= 2 && cp.modes[0] == cp.modes[1]) return TTGBF_EINVAL;
+    if (cp.nmodes >= 3 && cp.modes[1] != cp.modes[0] + cp.nmodes - 1) return TTGBF_EINVAL;
+    long long ntab = 1;
+    for (int t = 0; t < cp.nmodes; ++t) ntab *= c->n[cp.nmodes <= 2 ? cp.modes[t] : cp.modes[0] + t];
+    if (ntab > 2147483647LL) return TTGBF_EINVAL;
     if (!std::isfinite(z[i])) return TTGBF_ENONFINITE;
     for (int j = 0; j < h->b; ++j) {
       if (!std::isfinite(R[i * h->b + j])) return TTGBF_ENONFINITE;

@@ -172,3 +172,29 @@ def test_bearing_across_the_cut_float64(G):
         P, logc = pmf.update(P, g, pmf.likelihood(g, oc, z, model.R))
         assert rel_l1(f.density(), P) < 1e-12
         assert abs(f.estimate()[2] - logc) < 1e-10
+
+
+def test_three_mode_and_other_pairs_float64(G):
+    """Components on three consecutive modes, on a non-adjacent pair in
+    decreasing order and on one mode: float64 full-grid filter against the
+    dense oracle to 1e-12."""
+    import torch
+    g = pmf.Grid([-3.0, -3.0, -2.5, -2.0], [3.0, 3.0, 2.5, 2.0], [14, 12, 10, 9])
+    a = g.axes
+    r3 = np.sqrt(a[1][:, None, None] ** 2 + a[2][None, :, None] ** 2 + a[3][None, None, :] ** 2)
+    t31 = a[3][:, None] + 0.5 * np.sin(a[1][None, :])
+    oc = [((1, 2, 3), r3), ((3, 1), t31), ((0,), a[0])]
+    comps = [(m, torch.tensor(t, dtype=torch.float64, device="cuda")) for m, t in oc]
+    F = 0.95 * np.eye(4) + 0.05 * np.triu(np.ones((4, 4)), 1)
+    Q = 0.05 * np.eye(4)
+    R = np.diag([0.1, 0.2, 0.3])
+    m0, P0 = np.array([0.5, -0.3, 0.2, 0.1]), np.eye(4)
+    f = G.FullGridFilter(g.lo, g.hi, g.shape, m0, np.diag(P0), precision=64)
+    P = pmf.prior(g, m0, P0)
+    for z in (np.array([1.2, 0.4, 0.3]), np.array([0.9, -0.2, 0.6])):
+        f.predict(F, Q)
+        P, _ = pmf.predict_rg(P, g, F, Q)
+        f.update(comps, R, z)
+        P, logc = pmf.update(P, g, pmf.likelihood(g, oc, z, R))
+        assert rel_l1(f.density(), P) < 1e-12
+        assert abs(f.estimate()[2] - logc) < 1e-10
