@@ -492,12 +492,93 @@ def run_grid_design(args, dev):
     return out
 
 
+def run_cross(args, dev):
+    """Likelihood factors on three modes by the deterministic TT cross: the
+    range3 workload (config 2's grid, prior, F and Q with z = ||x[0:3]|| + v,
+    R = 0.02), 128^4, 100 filters, rank cap 16, cross rank 24 with one
+    refinement sweep.  Times predict + update + estimate per step (L2 flushed
+    before each timed step, CUDA events on the filter's stream), the share of
+    each kernel class (library profiling, on further steps), the float32
+    full-grid filter on the same measurement (one filter), and the TT
+    density's relative Frobenius error against the float64 full-grid filter
+    on Monte Carlo run 0 after every step."""
+    import torch
+    import paper_2501_07942_gb300 as G
+    log("cross leg (likelihood on three modes)")
+    model = synth.range3()
+    B, W, K = 100, 3, args.cross_steps
+    cap, smax, S = model.rank_cap, 10, 24
+    zs = measurement_batches(model, list(range(B)), W + 2 * K)
+    kw = tuned_config(G, model, B, cap, smax, "fp32")
+    f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=B, rank_cap=cap,
+                   eps=model.eps, max_shift_span=smax, device=dev, cross_rank=S, **kw)
+    axes = f.grid_axes()
+    comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+             for m, t, *_ in model.tables(axes)]
+    z_dev = torch.tensor(zs, dtype=torch.float32, device=dev)
+    d = model.d
+    mean = torch.zeros(B, d, dtype=torch.float64, device=dev)
+    cov = torch.zeros(B, d, d, dtype=torch.float64, device=dev)
+    lc = torch.zeros(B, dtype=torch.float64, device=dev)
+    ll = torch.zeros(B, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(flt, k):
+        flt.predict(model.F, model.Q)
+        flt.update_dev(comps, model.R, z_dev[k])
+        flt.estimate_dev(mean, cov, lc, ll)
+
+    for k in range(W):
+        step(f, k)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step(f, W + i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    f.profile(True)
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        step(f, W + K + i)
+    torch.cuda.synchronize(dev)
+    prof = f.profile_read()
+    f.profile(False)
+    f.free()
+    del f
+    torch.cuda.empty_cache()
+    tot = sum(v["ms"] for v in prof.values()) or 1.0
+    out = {"workload": "range3: config-2 grid, prior, F, Q; z = ||x[0:3]|| + v, R = 0.02; 128^4, "
+                       f"{B} filters, rank cap {cap}, cross rank {S}, 1 refinement sweep",
+           "value": B * K / (ms * 1e-3), "unit": "filter-steps/s", "ms_per_step": ms / K,
+           "kernels": {k: {"ms_share": v["ms"] / tot, "launches": v["launches"]} for k, v in prof.items()
+                       if v["launches"]},
+           "cross_ms_per_step": prof.get("cross", {}).get("ms", 0.0) / K}
+    log("cross leg: full-grid comparison")
+    out["fullgrid"] = run_fullgrid(args, model, zs, W, K, dev, axes)
+    # accuracy: Monte Carlo run 0 against the float64 full-grid filter
+    f0 = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1, rank_cap=cap,
+                    eps=model.eps, max_shift_span=smax, device=dev, cross_rank=S)
+    errs = []
+    for k, P in enumerate(fp64_reference_densities(model, zs, W + K, dev, axes)):
+        f0.predict(model.F, model.Q)
+        f0.update(comps, model.R, zs[k][0][None, :])
+        errs.append(tt_dense_rel_err(f0.export_cores(0), P))
+    f0.free()
+    out["tt_density_rel_fro_err"] = errs
+    return out
+
+
 def run_leg(name, args):
     """Run one secondary leg (config4, adjoint) in a child process of its own:
     its device memory (66 GB for config 4) is returned when it exits, and a
     failure there costs that leg only.  Returns the leg's dict, or the error."""
     cmd = [sys.executable, os.path.abspath(__file__), "--leg", name, "--c4-horizon", str(args.c4_horizon),
-           "--c4-steps", str(args.c4_steps), "--adj-steps", str(args.adj_steps)]
+           "--c4-steps", str(args.c4_steps), "--adj-steps", str(args.adj_steps),
+           "--cross-steps", str(args.cross_steps)]
     env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
     try:
         res = subprocess.run(cmd, capture_output=True, text=True, timeout=1200, env=env)
@@ -732,6 +813,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "fullgrid": fullgrid,
         "config4": None if args.no_config4 or rank != 0 else run_leg("config4", args),
         "adjoint": None if args.no_adjoint or rank != 0 else run_leg("adjoint", args),
+        "cross": None if args.no_cross or rank != 0 else run_leg("cross", args),
         "grid_design": None if args.no_grid_design or rank != 0 else run_grid_design(args, dev),
         "accuracy": accuracy,
         "rank_cap_sweep": sweep,
@@ -770,7 +852,9 @@ def main():
                     help="timed steps of the uneven-batch leg (graph launches x horizon)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (config 5) leg")
     ap.add_argument("--no-grid-design", action="store_true", help="skip the grid re-design leg")
-    ap.add_argument("--leg", choices=["config4", "adjoint"], default=None,
+    ap.add_argument("--no-cross", action="store_true", help="skip the three-mode likelihood (TT cross) leg")
+    ap.add_argument("--cross-steps", type=int, default=10, help="timed steps of the TT cross leg")
+    ap.add_argument("--leg", choices=["config4", "adjoint", "cross"], default=None,
                     help="run only this secondary leg and print its result (used by the main run)")
     ap.add_argument("--adj-steps", type=int, default=200, help="steps of the gradient leg")
     ap.add_argument("--no-accuracy", action="store_true",
@@ -788,7 +872,8 @@ def main():
     if args.leg is not None:
         import torch
         torch.cuda.set_device(0)
-        out = run_config4(args, "cuda:0") if args.leg == "config4" else run_adjoint(args, "cuda:0")
+        legs = {"config4": run_config4, "adjoint": run_adjoint, "cross": run_cross}
+        out = legs[args.leg](args, "cuda:0")
         print(json.dumps(out), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -85,18 +85,16 @@ class Model:
 
     def tables(self, axes):
         """Measurement components evaluated on grid axes supplied by the
-        caller: [(modes, table)] with table of shape (N_m,) or (N_m, N_n);
+        caller: [(modes, table)] with table of shape (N_m,), (N_m, N_n), ...
+        (one axis per mode of the component, in its order);
         a component declared with a period (an angle) keeps it as a third
         entry, (modes, table, period)."""
         out = []
         for modes, fn, *period in self.comps:
-            if len(modes) == 1:
-                tab = fn(np.asarray(axes[modes[0]]))
-            else:
-                a = np.asarray(axes[modes[0]])[:, None]
-                b = np.asarray(axes[modes[1]])[None, :]
-                tab = fn(a, b)
-            out.append((modes, tab, *period))
+            k = len(modes)
+            args = [np.asarray(axes[m], dtype=np.float64).reshape([-1 if t == j else 1 for t in range(k)])
+                    for j, m in enumerate(modes)]
+            out.append((modes, fn(*args), *period))
         return out
 
 
@@ -142,6 +140,21 @@ def config2(n: int = 128) -> Model:
                  m0=np.zeros(4), P0=np.eye(4), F=config2_F(), Q=0.05 * np.eye(4),
                  R=np.array([[0.01]]), comps=[((0, 1), h_range)], steps=50,
                  eps=1e-6, rank_cap=16, config_id=2)
+
+
+def h_range3(x, y, z):
+    return np.sqrt(x * x + y * y + z * z)
+
+
+def range3(n: int = 128) -> Model:
+    """Config 2's model (grid, prior, F, Q) with a likelihood that couples
+    three modes: the range over the first three coordinates,
+    z = ||x[0:3]|| + v, R = 0.02, 50 steps (the workload of the TT cross for
+    factors on three or more modes)."""
+    base = config2(n)
+    return Model(name="range3", lo=base.lo, hi=base.hi, n=base.n, m0=base.m0, P0=base.P0, F=base.F,
+                 Q=base.Q, R=np.array([[0.02]]), comps=[((0, 1, 2), h_range3)], steps=50, eps=1e-6,
+                 rank_cap=16, config_id=7)
 
 
 def radar(n: int = 128) -> Model:

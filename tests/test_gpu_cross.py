@@ -156,11 +156,7 @@ def test_all_four_modes(G):
 
 def test_filter_with_range3_over_steps(G):
     """Config 2's model with ||x[0:3]|| as its measurement, 32^4, 4 steps."""
-    base = synth.config2(n=32)
-    model = synth.Model(name="config2-range3", lo=base.lo, hi=base.hi, n=base.n, m0=base.m0, P0=base.P0,
-                        F=base.F, Q=base.Q, R=np.array([[0.02]]),
-                        comps=[((0, 1, 2), lambda x, y, z: np.sqrt(x * x + y * y + z * z))],
-                        steps=4, eps=1e-6, rank_cap=16, config_id=2)
+    model = synth.range3(n=32)
     g = pmf.Grid(model.lo, model.hi, model.n)
     x, zs = synth.simulate(model, 0, steps=4)
     a = g.axes
