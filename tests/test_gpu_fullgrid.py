@@ -179,7 +179,7 @@ def test_three_mode_and_other_pairs_float64(G):
     decreasing order and on one mode: float64 full-grid filter against the
     dense oracle to 1e-12."""
     import torch
-    g = pmf.Grid([-3.0, -3.0, -2.5, -2.0], [3.0, 3.0, 2.5, 2.0], [14, 12, 10, 9])
+    g = pmf.Grid([-3.0, -3.0, -2.5, -2.0], [3.0, 3.0, 2.5, 2.0], [16, 12, 12, 8])  # multiples of 4
     a = g.axes
     r3 = np.sqrt(a[1][:, None, None] ** 2 + a[2][None, :, None] ** 2 + a[3][None, None, :] ** 2)
     t31 = a[3][:, None] + 0.5 * np.sin(a[1][None, :])
