@@ -506,7 +506,7 @@ def run_cross(args, dev):
     import paper_2501_07942_gb300 as G
     log("cross leg (likelihood on three modes)")
     model = synth.range3()
-    B, W, K = 100, 3, args.cross_steps
+    B, W, K = args.cross_batch, 3, args.cross_steps
     cap, smax, S = model.rank_cap, 10, 24
     zs = measurement_batches(model, list(range(B)), W + 2 * K)
     kw = tuned_config(G, model, B, cap, smax, "fp32")
@@ -558,6 +558,8 @@ def run_cross(args, dev):
                        if v["launches"]},
            "cross_ms_per_step": prof.get("cross", {}).get("ms", 0.0) / K}
     log("cross leg: full-grid comparison")
+    if args.cross_no_compare:
+        return out
     out["fullgrid"] = run_fullgrid(args, model, zs, W, K, dev, axes)
     # accuracy: Monte Carlo run 0 against the float64 full-grid filter
     f0 = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1, rank_cap=cap,
@@ -578,7 +580,7 @@ def run_leg(name, args):
     failure there costs that leg only.  Returns the leg's dict, or the error."""
     cmd = [sys.executable, os.path.abspath(__file__), "--leg", name, "--c4-horizon", str(args.c4_horizon),
            "--c4-steps", str(args.c4_steps), "--adj-steps", str(args.adj_steps),
-           "--cross-steps", str(args.cross_steps)]
+           "--cross-steps", str(args.cross_steps), "--cross-batch", str(args.cross_batch)]
     env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
     try:
         res = subprocess.run(cmd, capture_output=True, text=True, timeout=1200, env=env)
@@ -854,6 +856,9 @@ def main():
     ap.add_argument("--no-grid-design", action="store_true", help="skip the grid re-design leg")
     ap.add_argument("--no-cross", action="store_true", help="skip the three-mode likelihood (TT cross) leg")
     ap.add_argument("--cross-steps", type=int, default=10, help="timed steps of the TT cross leg")
+    ap.add_argument("--cross-batch", type=int, default=100, help="filters of the TT cross leg")
+    ap.add_argument("--cross-no-compare", action="store_true",
+                    help="TT cross leg: skip the full-grid comparison and the accuracy run")
     ap.add_argument("--leg", choices=["config4", "adjoint", "cross"], default=None,
                     help="run only this secondary leg and print its result (used by the main run)")
     ap.add_argument("--adj-steps", type=int, default=200, help="steps of the gradient leg")
