@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   // ---- fiber matrix F (M x ncol, column-major)
   for (long long row = tid; row < M; row += kCT) {
     if (lr) {
-      const int al = (int)(row / nq);
+      const int al = (int)((int)row / (int)nq);  // M < 2^31 (M <= mcap)
       const long long v = row - (long long)al * nq;
       float w[S];
       for (int cp = 0; cp < rrq; ++cp) {
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
         F[(long long)be * M + row] = acc * lik_at(a, base + oJn[be], zb, ob, inv2r);
       }
     } else {
-      const long long v = row / sR;
+      const long long v = (int)row / sR;
       const int be = (int)(row - v * sR);
       float y[S];
       for (int c = 0; c < rlq; ++c) {
@@ -341,10 +341,8 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
     }
   }
   // explicit Q (M x n): the reflectors applied to the first n unit vectors
-  for (long long e = tid; e < M * n; e += kCT) {
-    const long long col = e / M, row = e - col * M;
-    Qb[e] = (row == col) ? 1.f : 0.f;
-  }
+  for (int c = 0; c < n; ++c)
+    for (long long i = tid; i < M; i += kCT) Qb[(long long)c * M + i] = (i == c) ? 1.f : 0.f;
   __syncthreads();
   for (int j = n - 1; j >= 0; --j) {
     const float tau = s_taus[j];
@@ -463,15 +461,15 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   for (int it = 0; it < kMaxvolIters; ++it) {
     float bv = -1.f;
     long long bi = -1;
-    for (long long e = tid; e < M * nm; e += kCT) {
-      const long long i = e / nm;
-      const int c = (int)(e - i * nm);
-      const float x = fabsf(F[(long long)c * M + i]);
-      if (bi < 0 || better(x, e, bv, bi)) {
-        bv = x;
-        bi = e;
+    for (long long i = tid; i < M; i += kCT)
+      for (int c = 0; c < nm; ++c) {
+        const float x = fabsf(F[(long long)c * M + i]);
+        const long long e = i * nm + c;  // row-major position: the tie order
+        if (bi < 0 || better(x, e, bv, bi)) {
+          bv = x;
+          bi = e;
+        }
       }
-    }
     const long long e = block_argmax(bv, bi, s_rv, s_ri, &best);
     if (e < 0 || !(best > 1.f + kDelta)) break;
     const long long is = e / nm;
@@ -550,11 +548,8 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   if (kind == kCrossFinal) {
     // core q = B in the density's layout [alpha][v][j]
     float* O = a.out[q] + (long long)b * a.cap[q];
-    for (long long e = tid; e < M * target; e += kCT) {
-      const long long row = e / target;
-      const int j = (int)(e - row * target);
-      O[e] = F[(long long)j * M + row];
-    }
+    for (long long row = tid; row < M; row += kCT)
+      for (int j = 0; j < target; ++j) O[row * target + j] = F[(long long)j * M + row];
   }
 }
 

@@ -7,6 +7,8 @@
 // "dot", "power", Sec. 4.1).
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace ttgbf {
@@ -283,6 +285,42 @@ __global__ void k_lik_offset(int B, const float* htab, int ntab, const float* z,
     off[b] = v;
     logoff[b] += -(double)v / (2.0 * R) - 0.5 * log(2.0 * 3.14159265358979323846 * R);
   }
+}
+
+// The same offset for a large table (a factor on three or more modes): a
+// grid of chunks per filter, each folding its chunk's minimum into off_b with
+// an atomic minimum on the float's bits (non-negative floats order like their
+// bit patterns); then k_lik_offset_log adds the dropped factor.
+__global__ void k_lik_offset_chunks(int B, const float* htab, long long ntab, const float* z, int zstride,
+                                    int zc, float period, float* off) {
+  const int b = blockIdx.y;
+  if (b >= B) return;
+  const float zb = z[(long long)b * zstride + zc];
+  float mn = INFINITY;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntab;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float e = wrap_residual(zb - htab[i], period);
+    mn = fminf(mn, e * e);
+  }
+  __shared__ float s_m[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = s_m[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fminf(v, s_m[w]);
+    atomicMin(reinterpret_cast<unsigned*>(off) + b, __float_as_uint(v));
+  }
+}
+
+__global__ void k_lik_offset_init(int B, float* off) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) off[b] = INFINITY;
+}
+
+__global__ void k_lik_offset_log(int B, double R, const float* off, double* logoff) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    logoff[b] += -(double)off[b] / (2.0 * R) - 0.5 * log(2.0 * 3.14159265358979323846 * R);
 }
 
 // W(i0, i1, c) *= exp(-((z - h(i0,i1))^2 - off) / (2R)): Hadamard product of the
@@ -590,8 +628,17 @@ void launch_plan_supercore(cudaStream_t st, int B, const TTGeom& g, const int* r
 
 void launch_lik_offset(cudaStream_t st, int B, const float* htab, int ntab, const float* z,
                        int zstride, int zc, double R, float period, float* off, double* logoff) {
-  count_launches(1);
-  k_lik_offset<<<B, 256, 0, st>>>(B, htab, ntab, z, zstride, zc, R, period, off, logoff);
+  if (ntab <= (1 << 16)) {
+    count_launches(1);
+    k_lik_offset<<<B, 256, 0, st>>>(B, htab, ntab, z, zstride, zc, R, period, off, logoff);
+    return;
+  }
+  // about 16 entries per thread, at most 128 chunks of 256 threads per filter
+  const int chunks = (int)std::min<long long>(128, ((long long)ntab + 4095) / 4096);
+  count_launches(3);
+  k_lik_offset_init<<<(B + 255) / 256, 256, 0, st>>>(B, off);
+  k_lik_offset_chunks<<<dim3(chunks, B), 256, 0, st>>>(B, htab, ntab, z, zstride, zc, period, off);
+  k_lik_offset_log<<<(B + 255) / 256, 256, 0, st>>>(B, R, off, logoff);
 }
 
 void launch_lik_apply_2d(cudaStream_t st, int B, float* W, long long W_cap, int N0, int N1,
