@@ -234,13 +234,46 @@ def rl_step(blk, Iq, J_next, q, delta=0.05):
     return [rows[i] for i in sel], Bm.T.reshape(len(sel), blk.n[q], len(J_next))
 
 
+class TransitionBlock(Block):
+    """The 2-site block of cores (m, m+1) after one factor of the textbook
+    transition (Eqs. pdf_predII, TPMmat) whose mode-m Gaussian is shifted by
+    the coupling to mode m+1:
+
+        T(a, j, i', b) = sum_i K(j, i, i') [G_m(i) G_{m+1}(i')](a, b),
+
+    K of shape (N_m, N_m, N_{m+1}).  Virtual modes: (a, j) and (i', b).  The
+    start sets, which look at the density alone, are those of Block."""
+
+    def __init__(self, cores, K):
+        super().__init__(cores, np.ones([c.shape[1] for c in cores]))
+        if self.k != 2:
+            raise ValueError("a transition block spans two modes")
+        self.K = np.asarray(K, dtype=np.float64)
+
+    def value(self, vs):
+        a, j = divmod(vs[0], self.N[0])
+        i1, b = divmod(vs[1], self.r_last)
+        w = self.G[1][:, i1, b]                      # (r,)
+        y = self.G[0][a] @ w                         # (N_m,) over i
+        return float(self.K[j, :, i1] @ y)
+
+    def fiber(self, alpha, q, beta):
+        if q == 0:
+            return np.array([self.value((v, beta[0])) for v in range(self.n[0])])
+        return np.array([self.value((alpha[0], v)) for v in range(self.n[1])])
+
+
 def block_cross(cores, lik, s, sweeps=1, delta=0.05):
     """Cross approximation of the likelihood-weighted block (module
-    docstring): start sets, then `sweeps` pairs of (left-to-right,
-    right-to-left) half sweeps, then the final left-to-right sweep whose
-    cores are returned, in the density's core shapes with ranks
-    (r_lo, s_1, ..., s_{k-1}, r_hi+1).  Returns (cores, index sets)."""
-    blk = Block(cores, lik)
+    docstring): see cross_of_block."""
+    return cross_of_block(Block(cores, lik), s, sweeps, delta)
+
+
+def cross_of_block(blk, s, sweeps=1, delta=0.05):
+    """Start sets, then `sweeps` pairs of (left-to-right, right-to-left) half
+    sweeps, then the final left-to-right sweep whose cores are returned, in
+    the density's core shapes with ranks (r_lo, s_1, ..., s_{k-1}, r_hi+1).
+    Returns (cores, index sets)."""
     k = blk.k
     J = start_sets(blk, s, delta)
     I = [None] * k

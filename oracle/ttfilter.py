@@ -225,6 +225,80 @@ def predict(cores, grid: pmf.Grid, F, Q, eps, rmax, smax=10, trace=None):
     return G, tails, c
 
 
+# ------------------------------------------------- textbook transition ----
+def transition_factor(grid: pmf.Grid, F, Q, m):
+    """The mode-m factor of the textbook transition (Eq. TPMmat,
+    T[j, i] = N(xi_j; F xi_i, Q) delta) for an upper bidiagonal F and a
+    diagonal Q, whose Gaussian factorises over the modes:
+    K_m(j, i, i') = D_m N(xi_{m,j} - F_mm xi_{m,i} - F_{m,m+1} xi_{m+1,i'}; 0, Q_mm),
+    shape (N_m, N_m, N_{m+1}); (N_m, N_m) for the last mode and for a mode
+    without coupling."""
+    F = np.asarray(F, dtype=np.float64)
+    q = float(np.asarray(Q, dtype=np.float64)[m, m])
+    xm = grid.axes[m]
+    coupled = m + 1 < grid.d and F[m, m + 1] != 0.0
+    x = xm[:, None] - F[m, m] * xm[None, :]
+    if coupled:
+        x = x[:, :, None] - F[m, m + 1] * grid.axes[m + 1][None, None, :]
+    return grid.delta_axis[m] * np.exp(-0.5 * x * x / q) / math.sqrt(2 * math.pi * q)
+
+
+def check_bidiagonal(F, Q):
+    F = np.asarray(F, dtype=np.float64)
+    Q = np.asarray(Q, dtype=np.float64)
+    d = F.shape[0]
+    for m in range(d):
+        for n in range(d):
+            if F[m, n] != 0.0 and not (n == m or n == m + 1):
+                raise ValueError("the exact transition needs an upper bidiagonal F")
+    if np.any(Q != np.diag(np.diag(Q))):
+        raise ValueError("the exact transition needs a diagonal Q")
+
+
+def predict_exact(cores, grid: pmf.Grid, F, Q, eps, rmax, cross=None, trace=None):
+    """TT predictive step with the textbook transition (Eqs. pdf_predII,
+    TPMmat) for an upper bidiagonal F and a diagonal Q, without the
+    re-gridding's interpolation: the modes' factors K_m applied in the order
+    m = 0, 1, ..., each summing out i_m while i_{m+1} is still the old index.
+    The TT starts in canonical form with its center at core 0; a coupled
+    factor acts on the 2-site block (m, m+1) (formed exactly, or by the cross
+    of oracle/cross.py when cross = {"s": rank, "sweeps": n}) and the block's
+    link is rounded (round_block, center then at m + 1); an uncoupled factor
+    is a matrix on core m followed by the truncating left step of the
+    rounding; the last mode's factor is a matrix on the last core.  Then
+    normalisation.  Returns (cores, tails, mass before normalisation)."""
+    from . import cross as X
+    check_bidiagonal(F, Q)
+    F = np.asarray(F, dtype=np.float64)
+    G = _cores(cores)
+    d = len(G)
+    canonical(G, 0, 0)
+    tails = []
+    for m in range(d - 1):
+        K = transition_factor(grid, F, Q, m)
+        if K.ndim == 3:
+            if cross is None:
+                W = np.einsum("aic,cjb->aijb", G[m], G[m + 1])
+                W = np.einsum("kij,aijb->akjb", K, W)
+                r0, n0, n1, r1 = W.shape
+                Qm, Rm = np.linalg.qr(W.reshape(r0 * n0, n1 * r1))
+                G[m] = Qm.reshape(r0, n0, -1)
+                G[m + 1] = Rm.reshape(-1, n1, r1)
+            else:
+                blk = X.TransitionBlock([G[m], G[m + 1]], K)
+                (G[m], G[m + 1]), _ = X.cross_of_block(blk, cross["s"], cross.get("sweeps", 1),
+                                                       cross.get("delta", 0.05))
+            tails += round_block(G, m, m + 1, eps, rmax, trace)
+        else:
+            apply_mode(G, m, K)
+            normA = float(np.linalg.norm(G[m]))
+            thr = eps * normA / math.sqrt(d - 1) if d > 1 else 0.0
+            tails += left_sweep(G, m, m + 1, thr, rmax, normA, trace)
+    apply_mode(G, d - 1, transition_factor(grid, F, Q, d - 1))
+    c = normalise(G, grid)
+    return G, tails, c
+
+
 # ---------------------------------------------------------------- update ----
 def _lik_factor(table, z, r, period):
     return np.exp(-0.5 * pmf.residual(z, table, period) ** 2 / r) / math.sqrt(2 * math.pi * r)
