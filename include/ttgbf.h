@@ -221,6 +221,24 @@ int ttgbf_init(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prior* prior
  * when that takes more than max_shift_span pieces. */
 int ttgbf_predict(ttgbf_ctx* ctx, const double* F, const double* Q);
 
+/* Predictive step with the textbook transition (Eq. pdf_predII with the
+ * transition matrix of Eq. TPMmat, T[j, i] = N(x_j; F x_i, Q) delta, then
+ * normalisation), without the re-gridding's hat and cloud-in-cell
+ * interpolation of ttgbf_predict: for an upper bidiagonal F (couplings of
+ * adjacent modes only, F[m][n] = 0 unless n == m or n == m + 1) and a
+ * diagonal positive Q the transition's Gaussian factorises over the modes,
+ * K_m(j, i, i') = D_m N(x_{m,j} - F_mm x_{m,i} - F_{m,m+1} x_{m+1,i'}; 0, Q_mm),
+ * and the factors apply in the order m = 0, 1, ... (each sums out i_m while
+ * i_{m+1} is still the old index).  A coupled factor acts on the 2-site block
+ * of cores (m, m+1): its product with the block is built by the TT cross of
+ * rank opts.cross_rank (see ttgbf_update; the entries it needs are sums over
+ * i_m of K times the block), the block's link rounded; an uncoupled factor
+ * and the last mode's are dense N x N matrices on their core.  Needs
+ * opts.cross_rank > 0.  TTGBF_EINVAL for other F, a non-diagonal Q or
+ * cross_rank 0.  Not recorded by the adjoint (ttgbf_adj_backward then
+ * returns TTGBF_ECAPACITY).  Same F and Q for every filter. */
+int ttgbf_predict_exact(ttgbf_ctx* ctx, const double* F, const double* Q);
+
 /* Bayes update (Eqs. pmf_filtrace_a/b; Alg. 2 step 2): P <- L P / c with the
  * likelihood L(i) = prod_c N(z_c; h_c(x_i), R_cc), then TT rounding and
  * normalisation; log c is accumulated into the log-likelihood.

@@ -29,7 +29,8 @@ ERRORS = {
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = [
-    "ttgbf_workspace_bytes", "ttgbf_init", "ttgbf_predict", "ttgbf_update", "ttgbf_update_dev",
+    "ttgbf_workspace_bytes", "ttgbf_init", "ttgbf_predict", "ttgbf_predict_exact", "ttgbf_update",
+    "ttgbf_update_dev",
     "ttgbf_estimate", "ttgbf_estimate_dev", "ttgbf_free", "ttgbf_strerror", "ttgbf_ranks",
     "ttgbf_stats", "ttgbf_grid_axes", "ttgbf_export_cores", "ttgbf_import_cores", "ttgbf_shear",
     "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise", "ttgbf_profile",
@@ -117,6 +118,7 @@ def load() -> ctypes.CDLL:
     lib.ttgbf_workspace_bytes.argtypes = [P(Grid), P(Opts)]
     lib.ttgbf_init.argtypes = [P(VP), P(Grid), P(Prior), P(Opts)]
     lib.ttgbf_predict.argtypes = [VP, dp, dp]
+    lib.ttgbf_predict_exact.argtypes = [VP, dp, dp]
     lib.ttgbf_update.argtypes = [VP, P(Meas), dp, dp]
     lib.ttgbf_update_dev.argtypes = [VP, P(Meas), dp, VP]
     lib.ttgbf_estimate.argtypes = [VP, dp, dp, dp, dp]
@@ -324,6 +326,12 @@ class TTFilter:
     def predict(self, F, Q):
         F, Q = _f64(F), _f64(Q)
         _check(self._lib.ttgbf_predict(self._ctx, _dptr(F), _dptr(Q)), "ttgbf_predict")
+
+    def predict_exact(self, F, Q):
+        """ttgbf_predict_exact: the textbook transition for an upper
+        bidiagonal F (needs cross_rank > 0)."""
+        F, Q = _f64(F), _f64(Q)
+        _check(self._lib.ttgbf_predict_exact(self._ctx, _dptr(F), _dptr(Q)), "ttgbf_predict_exact")
 
     @staticmethod
     def _meas(comps):

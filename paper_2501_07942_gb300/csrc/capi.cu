@@ -2027,6 +2027,113 @@ int ttgbf_convolve(ttgbf_ctx* c, const double* q) {
   return check(c);
 }
 
+// The predictive step with the textbook transition (Eqs. pdf_predII,
+// TPMmat) for an upper bidiagonal F and a diagonal Q.  The transition's
+// Gaussian then factorises over the modes, K_m(j, i, i') = D_m N(xi_{m,j} -
+// F_mm xi_{m,i} - F_{m,m+1} xi_{m+1,i'}; 0, Q_mm), and the factors apply in
+// the order m = 0, 1, ..., each summing out i_m while i_{m+1} is still the
+// old index.  From the canonical form centred at core 0: a coupled factor
+// acts on the 2-site block (m, m+1), built by the cross of the transition
+// block (cross.cu, no supercore is formed), and the block's link is rounded
+// (the center moves to m + 1); an uncoupled factor is a dense matrix on core
+// m followed by the truncating left step; the last mode's factor is a matrix
+// on the last core; then normalisation.
+int ttgbf_predict_exact(ttgbf_ctx* c, const double* F, const double* Q) {
+  ApiRange range("ttgbf_predict_exact");
+  if (split(c))
+    return fan_out(c, [&](ttgbf_ctx* q, int) { return ttgbf_predict_exact(q, F, Q); }, false, false);
+  int rc = guard(c);
+  if (rc) return rc;
+  const int d = c->d;
+  if (!F || !Q) return TTGBF_EINVAL;
+  if (!finite_all(F, (size_t)d * d) || !finite_all(Q, (size_t)d * d)) return TTGBF_ENONFINITE;
+  for (int m = 0; m < d; ++m)
+    for (int n = 0; n < d; ++n) {
+      const double f = F[(size_t)m * d + n], q = Q[(size_t)m * d + n];
+      if (f != 0.0 && n != m && n != m + 1) return TTGBF_EINVAL;
+      if (m == n ? !(q > 0.0) : q != 0.0) return TTGBF_EINVAL;
+    }
+  if (c->cross_s <= 0) return TTGBF_EINVAL;
+  tape_fail(c);  // not recordable by the adjoint
+  // dense factors of the uncoupled modes and of the last mode
+  std::vector<std::vector<double>> mats;
+  std::vector<long long> off(d, -1);
+  long long at = 0;
+  for (int m = 0; m < d; ++m) {
+    if (m + 1 < d && F[(size_t)m * d + m + 1] != 0.0) continue;
+    const int N = c->n[m];
+    const double D = c->dx[m], q = Q[(size_t)m * d + m], f = F[(size_t)m * d + m];
+    const double norm = D / std::sqrt(2.0 * M_PI * q);
+    std::vector<double> K((size_t)N * N);
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        const double x = (c->lo[m] + (j + 0.5) * D) - f * (c->lo[m] + (i + 0.5) * D);
+        K[(size_t)j * N + i] = norm * std::exp(-0.5 * x * x / q);
+      }
+    off[m] = at;
+    at += (long long)K.size();
+    mats.push_back(std::move(K));
+  }
+  rc = upload_mats(c, mats);
+  if (rc) return rc;
+  if (c->expanded) enqueue_round(c);
+  enqueue_center_into(c, 0, 0);
+  for (int m = 0; m + 1 < d; ++m) {
+    if (F[(size_t)m * d + m + 1] != 0.0) {
+      CrossArgs a = c->x;
+      a.B = c->B;
+      a.d = d;
+      a.lo = m;
+      a.k = 2;
+      a.s = c->cross_s;
+      a.ranks = c->ranks;
+      for (int q = 0; q < 2; ++q) {
+        a.core[q] = curp(c, m + q);
+        a.out[q] = altp(c, m + q);
+        a.cap[q] = c->L.core_cap[m + q];
+        a.N[q] = c->n[m + q];
+        a.stride[q] = 0;
+      }
+      a.htab = nullptr;
+      a.z = nullptr;
+      a.off = nullptr;
+      a.R = 1.0;
+      a.trans = 1;
+      const double q = Q[(size_t)m * d + m];
+      a.tF0 = (float)F[(size_t)m * d + m];
+      a.tF1 = (float)F[(size_t)m * d + m + 1];
+      a.tiq = (float)(1.0 / q);
+      a.tkc = (float)(c->dx[m] / std::sqrt(2.0 * M_PI * q));
+      a.tlo0 = (float)c->lo[m];
+      a.tdx0 = (float)c->dx[m];
+      a.tlo1 = (float)c->lo[m + 1];
+      a.tdx1 = (float)c->dx[m + 1];
+      {
+        Prof p(c, kPCross, 2 * c->cross_sweeps + 3);
+        launch_cross_step(c->st, a, 1, kCrossStart);
+        for (int sw = 0; sw < c->cross_sweeps; ++sw) {
+          launch_cross_step(c->st, a, 0, kCrossLR);
+          launch_cross_step(c->st, a, 1, kCrossRL);
+        }
+        launch_cross_step(c->st, a, 0, kCrossFinal);
+        launch_cross_last(c->st, a);
+      }
+      c->cur[m] ^= 1;
+      c->cur[m + 1] ^= 1;
+      stage(c, kStageRight, m + 1, 0);
+      stage(c, kStageLeft, m, 1);
+    } else {
+      mode_apply(c, m, c->opmats + off[m]);
+      stage(c, kStageLeft, m, 1);
+    }
+    c->canon = true;
+    c->center = m + 1;
+  }
+  mode_apply(c, d - 1, c->opmats + off[d - 1]);
+  enqueue_normalise(c, c->mass_pred);
+  return check(c);
+}
+
 // Grid re-design, interpolation step (Alg. 4 step 5): every filter's density
 // values onto a new axis-aligned grid of the same cell counts, by separable
 // piecewise-linear interpolation (the value at a new point from the two old

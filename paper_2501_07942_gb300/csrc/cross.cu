@@ -157,6 +157,65 @@ __device__ __forceinline__ float lik_at(const CrossArgs& a, long long idx, float
   return expf(-(df * df - ob) * inv2r);
 }
 
+// The textbook transition's mode factor K(j, i, i') of a transition block.
+__device__ __forceinline__ float trans_k(const CrossArgs& a, int j, int i, int i1) {
+  const float x = (a.tlo0 + ((float)j + 0.5f) * a.tdx0) - a.tF0 * (a.tlo0 + ((float)i + 0.5f) * a.tdx0) -
+                  a.tF1 * (a.tlo1 + ((float)i1 + 0.5f) * a.tdx1);
+  return a.tkc * expf(-0.5f * x * x * a.tiq);
+}
+
+// Transition block, left-to-right fibers at mode 0: column be of F is
+// T((a, j), v1_be) = sum_i K(j, i, i'_be) y(a, i), y(a, i) = G_0(a, i, :) . V_1[be]
+// (y staged in the scratch Y, r_a N_0 floats).
+__device__ void trans_fibers_lr(const CrossArgs& a, const float* G0, int rr0, long long M, int sR,
+                                const long long* oJ, const float* V1, int rlast, float* F, float* Y) {
+  const int N0 = a.N[0], s = a.s;
+  for (int be = 0; be < sR; ++be) {
+    const int i1 = (int)(oJ[be] / rlast);
+    for (long long t = threadIdx.x; t < M; t += blockDim.x) {
+      float acc = 0.f;
+      for (int c = 0; c < rr0; ++c) acc = fmaf(G0[t * rr0 + c], V1[be * s + c], acc);
+      Y[t] = acc;
+    }
+    __syncthreads();
+    for (long long row = threadIdx.x; row < M; row += blockDim.x) {
+      const int aa = (int)row / N0, j = (int)row - aa * N0;
+      const float* y = Y + (long long)aa * N0;
+      float acc = 0.f;
+      for (int i = 0; i < N0; ++i) acc = fmaf(trans_k(a, j, i, i1), y[i], acc);
+      F[(long long)be * M + row] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Transition block, fibers along mode 1 for the left elements alpha = (a, j)
+// in oI (raw virtual indices): out(v1, al) = sum_c h(i', c) G_1(c, i', b) with
+// h(i', c) = sum_i K(j, i, i') G_0(a, i, c) (staged in Y, N_1 r_1 floats);
+// column al of F (ld M), or row al of the last core (ld nq) when last.
+__device__ void trans_fibers_rl(const CrossArgs& a, const float* G0, const float* G1, int r1, int rb, int sL,
+                                const long long* oI, float* F, long long M, float* Y, bool last) {
+  const int N0 = a.N[0], N1 = a.N[1];
+  for (int al = 0; al < sL; ++al) {
+    const int aa = (int)(oI[al] / N0), jj = (int)(oI[al] - (long long)aa * N0);
+    for (int e = threadIdx.x; e < N1 * r1; e += blockDim.x) {
+      const int i1 = e / r1, c = e - i1 * r1;
+      float acc = 0.f;
+      for (int i = 0; i < N0; ++i) acc = fmaf(trans_k(a, jj, i, i1), G0[((long long)aa * N0 + i) * r1 + c], acc);
+      Y[e] = acc;
+    }
+    __syncthreads();
+    for (long long row = threadIdx.x; row < (long long)N1 * rb; row += blockDim.x) {
+      const int i1 = (int)row / rb, bb = (int)row - i1 * rb;
+      float acc = 0.f;
+      for (int c = 0; c < r1; ++c) acc = fmaf(Y[i1 * r1 + c], G1[((long long)c * N1 + i1) * rb + bb], acc);
+      if (last) F[(long long)al * M + row] = acc;  // core layout [al][v1]
+      else F[(long long)al * M + row] = acc;      // column al of the fiber matrix
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ bool taken(const unsigned* mask, long long i) {
   return (mask[i >> 5] >> (i & 31)) & 1u;
 }
@@ -244,13 +303,18 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   float* Qb = a.Qb + (long long)b * a.fcap;
   float* rn = a.rn + (long long)b * a.mcap;
   unsigned* mask = a.mask + (long long)b * (a.mcap / 32 + 1);
-  const float zb = a.z[(long long)b * a.zstride + a.zc];
-  const float ob = a.off[b];
+  const float zb = a.trans ? 0.f : a.z[(long long)b * a.zstride + a.zc];
+  const float ob = a.trans ? 0.f : a.off[b];
   const float inv2r = (float)(0.5 / a.R);
   const long long strq = a.stride[q];
 
   // ---- fiber matrix F (M x ncol, column-major)
-  for (long long row = tid; row < M; row += kCT) {
+  if (a.trans && lr) {
+    trans_fibers_lr(a, G, rrq, M, sR, oJn, Vn, g.r[k], F, Qb);
+  } else if (a.trans && kind == kCrossRL) {
+    trans_fibers_rl(a, a.core[0] + (long long)b * a.cap[0], G, g.r[1], g.r[k], sL, oIq, F, M, Qb, false);
+  }
+  for (long long row = tid; row < M && !(a.trans && kind != kCrossStart); row += kCT) {
     if (lr) {
       const int al = (int)((int)row / (int)nq);  // M < 2^31 (M <= mcap)
       const long long v = row - (long long)al * nq;
@@ -527,7 +591,7 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
       float acc = 0.f;
       for (int c = 0; c < rlq; ++c) acc = fmaf(Uq[al * s + c], G[((long long)c * nq + v) * rrq + cp], acc);
       Un[j * s + cp] = acc;
-      if (cp == 0) oN[j] = oIq[al] + g.grid(a, q, v) * strq;
+      if (cp == 0) oN[j] = a.trans ? row : oIq[al] + g.grid(a, q, v) * strq;
     }
     if (tid == 0) szI[q + 1] = target;
   } else {
@@ -541,7 +605,7 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
       float acc = 0.f;
       for (int cp = 0; cp < rrq; ++cp) acc = fmaf(G[((long long)c * nq + v) * rrq + cp], Vn[be * s + cp], acc);
       Vq[j * s + c] = acc;
-      if (c == 0) oN[j] = g.grid(a, q, v) * strq + oJn[be];
+      if (c == 0) oN[j] = a.trans ? row : g.grid(a, q, v) * strq + oJn[be];
     }
     if (tid == 0) szJ[q] = target;
   }
@@ -572,10 +636,14 @@ __global__ void __launch_bounds__(kCT) k_cross_last(CrossArgs a) {
   const float* Uq = a.U + ((long long)b * ld + q) * s * s;
   const float* G = a.core[q] + (long long)b * a.cap[q];
   float* O = a.out[q] + (long long)b * a.cap[q];
-  const float zb = a.z[(long long)b * a.zstride + a.zc];
-  const float ob = a.off[b];
+  if (a.trans) {
+    trans_fibers_rl(a, a.core[0] + (long long)b * a.cap[0], G, g.r[1], g.r[k], sL, oI, O, nq,
+                    a.Qb + (long long)b * a.fcap, true);
+  }
+  const float zb = a.trans ? 0.f : a.z[(long long)b * a.zstride + a.zc];
+  const float ob = a.trans ? 0.f : a.off[b];
   const float inv2r = (float)(0.5 / a.R);
-  for (long long e = tid; e < (long long)sL * nq; e += kCT) {
+  for (long long e = tid; e < (long long)sL * nq && !a.trans; e += kCT) {
     const int al = (int)(e / nq);
     const long long v = e - (long long)al * nq;
     float acc = 0.f;

@@ -255,6 +255,14 @@ struct CrossArgs {
   float* V;                    // [B][d+1][s][s] right interfaces
   int* sz;                     // [B][2][d+1] sizes of the left and right sets
   int* status;                 // [B] nonzero: a rank of the block exceeded s (the step was skipped)
+  // trans != 0: the block is the 2-site block (lo, lo+1) after the mode-lo
+  // factor of the textbook transition, T(a, j, i', b) = sum_i K(j, i, i')
+  // [G_lo(i) G_lo+1(i')](a, b), K(j, i, i') = dx0 N(xi0_j - F0 xi0_i - F1
+  // xi1_i'; 0, q) (no likelihood table); the index sets then hold the raw
+  // virtual indices (a, j) and (i', b) instead of table offsets
+  int trans;
+  float tF0, tF1, tiq, tkc;    // F_lo,lo, F_lo,lo+1, 1 / q, dx0 / sqrt(2 pi q)
+  float tlo0, tdx0, tlo1, tdx1;  // axes: xi = lo + (i + 1/2) dx
 };
 void launch_cross_step(cudaStream_t st, const CrossArgs& a, int q, int kind);
 void launch_cross_last(cudaStream_t st, const CrossArgs& a);
