@@ -11,6 +11,8 @@ on 2-site blocks by the cross of csrc/cross.cu) against the oracle.
 * A filter of predict_exact + update over several steps against the dense
   oracle filter with the textbook transition (pmf.run_filter), per-step
   bounds summed; means within the cap-aware tolerance.
+* Config 3's model at its full size (d = 6, N = 256) against the tensor
+  product of its pairs' exact 2-D densities.
 * Other couplings, a non-diagonal Q and cross_rank 0 are TTGBF_EINVAL."""
 import numpy as np
 import pytest
@@ -123,4 +125,61 @@ def test_exact_step_rejects_other_models(G):
     with pytest.raises(G.TTGBFError) as ei:
         f.predict_exact(np.eye(3), np.eye(3) * 0.1)
     assert ei.value.code == -1
+    f.free()
+
+
+def test_config3_exact_transition_full_size(G):
+    """Config 3's model (d = 6 constant-velocity pairs, N = 256, rank cap 32,
+    eps 1e-5) with the textbook transition: F is upper bidiagonal (each pair's
+    coupling x_{2i} += 0.1 x_{2i+1} is the only one), so every coupled factor
+    is the 2-site block of one pair, between links of rank 1.  The exact
+    density is the tensor product of the three pairs' 2-D densities, each
+    stepped by the oracle's untruncated exact transition and the dense
+    update; the GPU density is compared with that product through TT inner
+    products.  Per-step bounds 10 (eps + tau) + 1e-5 summed, tau the tails of
+    the oracle TT filter with the same transition; its ranks equal the GPU's."""
+    model = synth.config3(d=6, n=256)
+    mcs, steps, cap = [0, 1], 3, model.rank_cap
+    f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=len(mcs), rank_cap=cap,
+                   eps=model.eps, max_shift_span=5, cross_rank=cap + 8)
+    comps = device_tables(model, f.grid_axes())
+    zs = [synth.simulate(model, mc, steps=steps)[1] for mc in mcs]
+    g = pmf.Grid(model.lo, model.hi, model.n)
+    oc = model.tables(g.axes)
+    npair = model.d // 2
+    pg = [pmf.Grid(model.lo[2 * i:2 * i + 2], model.hi[2 * i:2 * i + 2], model.n[2 * i:2 * i + 2])
+          for i in range(npair)]
+    P = [[pmf.prior(pg[i], model.m0[2 * i:2 * i + 2], model.P0[2 * i:2 * i + 2, 2 * i:2 * i + 2])
+          for i in range(npair)] for _ in mcs]
+    X = []
+    for _ in mcs:
+        Xb = [np.exp(-0.5 * (g.axes[m] - model.m0[m]) ** 2 / model.P0[m, m]).reshape(1, -1, 1)
+              for m in range(model.d)]
+        T.normalise(Xb, g)
+        X.append(Xb)
+    bound = [0.0] * len(mcs)
+    for k in range(steps):
+        f.predict_exact(model.F, model.Q)
+        f.update(comps, model.R, np.stack([z[k] for z in zs]))
+        for b in range(len(mcs)):
+            exact = []
+            for i in range(npair):
+                s = slice(2 * i, 2 * i + 2)
+                Xi, _, _ = T.predict_exact(tt.from_dense(P[b][i], eps=1e-14), pg[i], model.F[s, s],
+                                           model.Q[s, s], 0.0, None)
+                Pi = tt.densify(Xi)
+                tab = [((0,), synth.workloads.h_square20(pg[i].axes[0]))]
+                Pi, _ = pmf.update(Pi, pg[i], pmf.likelihood(pg[i], tab, zs[b][k][i:i + 1],
+                                                               model.R[i:i + 1, i:i + 1]))
+                P[b][i] = Pi
+                exact += tt.from_dense(Pi, eps=1e-12)
+            cores = [np.asarray(x, dtype=np.float64) for x in f.export_cores(b)]
+            nn = tt.inner(exact, exact)
+            e = float(np.sqrt(max(tt.inner(cores, cores) - 2.0 * tt.inner(cores, exact) + nn, 0.0) / nn))
+            X[b], tp, _ = T.predict_exact(X[b], g, model.F, model.Q, model.eps, cap)
+            X[b], tu, _ = T.update(X[b], g, oc, zs[b][k], model.R, model.eps, cap)
+            bound[b] += tt_tol(model.eps, sum(tp) + sum(tu))
+            print(f"step {k} filter {b}: rel L2 {e:.2e} (bound {bound[b]:.1e}), ranks {f.ranks()[b].tolist()}")
+            assert f.ranks()[b].tolist() == tt.ranks(X[b]), (k, b)
+            assert e <= bound[b], (k, b, e, bound[b])
     f.free()
