@@ -574,13 +574,145 @@ def run_cross(args, dev):
     return out
 
 
+def tt_pairs_rel_err(cores, pairs) -> float:
+    """||T - P_0 (x) P_1 (x) ...||_F / ||P_0 (x) P_1 (x) ...||_F of a TT over
+    d = 2 len(pairs) modes and dense 2-D densities P_i over the modes
+    (2i, 2i + 1), from inner products (the d-dimensional tensors are never
+    formed)."""
+    cores = [np.asarray(c, dtype=np.float64) for c in cores]
+    E = np.ones((1, 1))
+    for C in cores:
+        E = np.einsum("ab,aic,bid->cd", E, C, C)
+    tt2 = float(E[0, 0])
+    v = np.ones((1,))
+    pp = 1.0
+    for i, P in enumerate(pairs):
+        M = np.einsum("ajc,jk,ckd->ad", cores[2 * i], P, cores[2 * i + 1])
+        v = v @ M
+        pp *= float(np.vdot(P, P))
+    tp = float(v.reshape(-1)[0])
+    return math.sqrt(max(tt2 - 2.0 * tp + pp, 0.0) / pp)
+
+
+def run_config3(args, dev):
+    """Config 3 (d = 6 constant-velocity pairs x_{2i} += 0.1 x_{2i+1}, N = 256,
+    rank cap 32, eps 1e-5, one-mode measurements x_{2i}^2 / 20) with both
+    transitions: the re-gridded one (ttgbf_predict: hat shears in pieces,
+    Gaussian kernel) and the textbook one (ttgbf_predict_exact: each pair's
+    coupled factor on its 2-site block by the cross, rank 40).  Throughput of
+    predict + update + estimate for a batch (L2 flushed before each timed
+    step, CUDA events).  Accuracy at N = 128 (the full-grid filter's largest
+    axis), Monte Carlo run 0: the TT density against the tensor product of
+    the three pairs' float64 full-grid filters with the textbook direct sum
+    (and with the re-gridded transition for the re-gridded TT filter's own
+    operator), per step."""
+    import torch
+    import paper_2501_07942_gb300 as G
+    log("config-3 leg (re-gridded and textbook transitions)")
+    out = {"workload": "config3: d=6, N=256, F block-diagonal [[1, 0.1], [0, 1]], diagonal Q, "
+                       "z_i = x_{2i}^2 / 20 + v_i, R = 0.02 I, rank cap 32, eps 1e-5; "
+                       f"{args.c3_batch} filters"}
+    model = synth.config3(d=6, n=256)
+    B, W, K = args.c3_batch, 2, args.c3_steps
+    zs = measurement_batches(model, list(range(B)), W + K)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for name, exact in (("regridded", False), ("textbook", True)):
+        f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=B,
+                       rank_cap=model.rank_cap, eps=model.eps, max_shift_span=5, device=dev,
+                       cross_rank=model.rank_cap + 8 if exact else 0)
+        comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+                 for m, t, *_ in model.tables(f.grid_axes())]
+        z_dev = torch.tensor(zs, dtype=torch.float32, device=dev)
+
+        def step(k):
+            if exact:
+                f.predict_exact(model.F, model.Q)
+            else:
+                f.predict(model.F, model.Q)
+            f.update_dev(comps, model.R, z_dev[k])
+            f.estimate()
+
+        for k in range(W):
+            step(k)
+        torch.cuda.synchronize(dev)
+        ms = 0.0
+        for i in range(K):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(W + i)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += a.elapsed_time(b)
+        out[name] = {"value": B * K / (ms * 1e-3), "unit": "filter-steps/s", "ms_per_step": ms / K,
+                     "max_rank": int(f.ranks().max())}
+        f.free()
+        del f
+        torch.cuda.empty_cache()
+    # accuracy at N = 128 against the pairs' float64 full-grid filters
+    m128 = synth.config3(d=6, n=128)
+    S = args.c3_acc_steps
+    z0 = synth.simulate(m128, 0, steps=S)[1]
+    npair = m128.d // 2
+    acc = {}
+    refs = {}
+    for ref_name, direct in (("textbook", True), ("regridded", False)):
+        dens = [[None] * npair for _ in range(S)]
+        for i in range(npair):
+            sl = slice(2 * i, 2 * i + 2)
+            fg = G.FullGridFilter(m128.lo[sl], m128.hi[sl], m128.n[sl], m128.m0[sl], np.diag(m128.P0)[sl],
+                                  precision=64, device=dev)
+            ax = [np.asarray(a) for a in fg_axes(m128.lo[sl], m128.hi[sl], m128.n[sl])]
+            tab = [((0,), torch.tensor(synth.workloads.h_square20(ax[0]), dtype=torch.float64, device=dev))]
+            for k in range(S):
+                if direct:
+                    fg.predict_direct(m128.F[sl, sl], m128.Q[sl, sl])
+                else:
+                    fg.predict(m128.F[sl, sl], m128.Q[sl, sl])
+                fg.update(tab, m128.R[i:i + 1, i:i + 1], z0[k][i:i + 1])
+                dens[k][i] = fg.density()
+            fg.free()
+        refs[ref_name] = dens
+    for name, exact in (("regridded", False), ("textbook", True)):
+        f = G.TTFilter(m128.lo, m128.hi, m128.n, m128.m0, np.diag(m128.P0), batch=1, rank_cap=m128.rank_cap,
+                       eps=m128.eps, max_shift_span=5, device=dev, cross_rank=m128.rank_cap + 8 if exact else 0)
+        comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
+                 for m, t, *_ in m128.tables(f.grid_axes())]
+        e_text, e_rg = [], []
+        for k in range(S):
+            if exact:
+                f.predict_exact(m128.F, m128.Q)
+            else:
+                f.predict(m128.F, m128.Q)
+            f.update(comps, m128.R, z0[k][None, :])
+            cores = f.export_cores(0)
+            e_text.append(tt_pairs_rel_err(cores, refs["textbook"][k]))
+            e_rg.append(tt_pairs_rel_err(cores, refs["regridded"][k]))
+        f.free()
+        acc[name] = {"vs_textbook_full_grid": e_text, "vs_regridded_full_grid": e_rg}
+    out["accuracy_n128"] = acc
+    out["accuracy_reference"] = ("Monte Carlo run 0 at N = 128: the tensor product of the three pairs' float64 "
+                                 "full-grid GPU filters, with the textbook direct sum (ttgbf_fg_predict_direct) "
+                                 "or the re-gridded transition (ttgbf_fg_predict); relative Frobenius error per "
+                                 "step")
+    return out
+
+
+def fg_axes(lo, hi, n):
+    """Cell-centred axes of a grid (the library's and the oracle's reading)."""
+    return [lo[m] + (np.arange(n[m]) + 0.5) * (hi[m] - lo[m]) / n[m] for m in range(len(n))]
+
+
 def run_leg(name, args):
     """Run one secondary leg (config4, adjoint) in a child process of its own:
     its device memory (66 GB for config 4) is returned when it exits, and a
     failure there costs that leg only.  Returns the leg's dict, or the error."""
     cmd = [sys.executable, os.path.abspath(__file__), "--leg", name, "--c4-horizon", str(args.c4_horizon),
            "--c4-steps", str(args.c4_steps), "--adj-steps", str(args.adj_steps),
-           "--cross-steps", str(args.cross_steps), "--cross-batch", str(args.cross_batch)]
+           "--cross-steps", str(args.cross_steps), "--cross-batch", str(args.cross_batch),
+           "--c3-batch", str(args.c3_batch), "--c3-steps", str(args.c3_steps),
+           "--c3-acc-steps", str(args.c3_acc_steps)]
     env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
     try:
         res = subprocess.run(cmd, capture_output=True, text=True, timeout=1200, env=env)
@@ -816,6 +948,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "config4": None if args.no_config4 or rank != 0 else run_leg("config4", args),
         "adjoint": None if args.no_adjoint or rank != 0 else run_leg("adjoint", args),
         "cross": None if args.no_cross or rank != 0 else run_leg("cross", args),
+        "config3": None if args.no_config3 or rank != 0 else run_leg("config3", args),
         "grid_design": None if args.no_grid_design or rank != 0 else run_grid_design(args, dev),
         "accuracy": accuracy,
         "rank_cap_sweep": sweep,
@@ -855,11 +988,15 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (config 5) leg")
     ap.add_argument("--no-grid-design", action="store_true", help="skip the grid re-design leg")
     ap.add_argument("--no-cross", action="store_true", help="skip the three-mode likelihood (TT cross) leg")
+    ap.add_argument("--no-config3", action="store_true", help="skip the config-3 (two transitions) leg")
+    ap.add_argument("--c3-batch", type=int, default=32, help="filters of the config-3 leg")
+    ap.add_argument("--c3-steps", type=int, default=3, help="timed steps of the config-3 leg")
+    ap.add_argument("--c3-acc-steps", type=int, default=5, help="accuracy steps of the config-3 leg")
     ap.add_argument("--cross-steps", type=int, default=10, help="timed steps of the TT cross leg")
     ap.add_argument("--cross-batch", type=int, default=100, help="filters of the TT cross leg")
     ap.add_argument("--cross-no-compare", action="store_true",
                     help="TT cross leg: skip the full-grid comparison and the accuracy run")
-    ap.add_argument("--leg", choices=["config4", "adjoint", "cross"], default=None,
+    ap.add_argument("--leg", choices=["config4", "adjoint", "cross", "config3"], default=None,
                     help="run only this secondary leg and print its result (used by the main run)")
     ap.add_argument("--adj-steps", type=int, default=200, help="steps of the gradient leg")
     ap.add_argument("--no-accuracy", action="store_true",
@@ -877,7 +1014,7 @@ def main():
     if args.leg is not None:
         import torch
         torch.cuda.set_device(0)
-        legs = {"config4": run_config4, "adjoint": run_adjoint, "cross": run_cross}
+        legs = {"config4": run_config4, "adjoint": run_adjoint, "cross": run_cross, "config3": run_config3}
         out = legs[args.leg](args, "cuda:0")
         print(json.dumps(out), flush=True)
         return

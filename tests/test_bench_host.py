@@ -56,3 +56,15 @@ def test_fullgrid_bytes_count_the_fused_passes():
     n_ops = len(bench.ldu_ops(m2.F))
     assert bench.fullgrid_bytes_per_step(m2) > 2 ** 28 * 4 * 2 * (4 + 1)
     assert n_ops > 6
+
+
+def test_tt_pairs_rel_err_matches_densified():
+    import bench
+    rng = np.random.default_rng([51])
+    cores = [rng.standard_normal(s) for s in [(1, 5, 3), (3, 4, 1), (1, 6, 2), (2, 3, 1)]]
+    pairs = [rng.standard_normal((5, 4)), rng.standard_normal((6, 3))]
+    from oracle import tt
+    T = tt.densify(cores)
+    P = np.einsum("ab,cd->abcd", pairs[0], pairs[1])
+    ref = np.linalg.norm(T - P) / np.linalg.norm(P)
+    assert abs(bench.tt_pairs_rel_err(cores, pairs) - ref) < 1e-10
