@@ -196,13 +196,27 @@ __device__ void trans_fibers_lr(const CrossArgs& a, const float* G0, int rr0, lo
 __device__ void trans_fibers_rl(const CrossArgs& a, const float* G0, const float* G1, int r1, int rb, int sL,
                                 const long long* oI, float* F, long long M, float* Y, bool last) {
   const int N0 = a.N[0], N1 = a.N[1];
+  constexpr int kC = 16;  // columns of h per pass: K(j, i, i') is evaluated once per kC columns
+  const int npass = (r1 + kC - 1) / kC;
   for (int al = 0; al < sL; ++al) {
     const int aa = (int)(oI[al] / N0), jj = (int)(oI[al] - (long long)aa * N0);
-    for (int e = threadIdx.x; e < N1 * r1; e += blockDim.x) {
-      const int i1 = e / r1, c = e - i1 * r1;
-      float acc = 0.f;
-      for (int i = 0; i < N0; ++i) acc = fmaf(trans_k(a, jj, i, i1), G0[((long long)aa * N0 + i) * r1 + c], acc);
-      Y[e] = acc;
+    for (int e = threadIdx.x; e < N1 * npass; e += blockDim.x) {
+      const int i1 = e / npass, c0 = (e - i1 * npass) * kC;
+      const int nc = min(kC, r1 - c0);
+      float acc[kC];
+#pragma unroll
+      for (int t = 0; t < kC; ++t) acc[t] = 0.f;
+      const float* g = G0 + (long long)aa * N0 * r1 + c0;
+      for (int i = 0; i < N0; ++i) {
+        const float kv = trans_k(a, jj, i, i1);
+        const float* gi = g + (long long)i * r1;
+#pragma unroll
+        for (int t = 0; t < kC; ++t)
+          if (t < nc) acc[t] = fmaf(kv, gi[t], acc[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < kC; ++t)
+        if (t < nc) Y[i1 * r1 + c0 + t] = acc[t];
     }
     __syncthreads();
     for (long long row = threadIdx.x; row < (long long)N1 * rb; row += blockDim.x) {
