@@ -2108,6 +2108,11 @@ int ttgbf_predict_exact(ttgbf_ctx* c, const double* F, const double* Q) {
       a.tdx0 = (float)c->dx[m];
       a.tlo1 = (float)c->lo[m + 1];
       a.tdx1 = (float)c->dx[m + 1];
+      // sums over the old index skip the cells where K < exp(-32) of its
+      // peak (8 standard deviations; below float32's resolution); two cells
+      // of margin for the rounding of the window's centre
+      const double f0 = std::fabs(F[(size_t)m * d + m]);
+      a.twin = f0 > 0.0 ? (float)std::min(8.0 * std::sqrt(q) / (f0 * c->dx[m]) + 2.0, 1e6) : 0.f;
       {
         Prof p(c, kPCross, 2 * c->cross_sweeps + 3);
         launch_cross_step(c->st, a, 1, kCrossStart);

@@ -164,6 +164,20 @@ __device__ __forceinline__ float trans_k(const CrossArgs& a, int j, int i, int i
   return a.tkc * expf(-0.5f * x * x * a.tiq);
 }
 
+// The old indices i where K(j, i, i') is not below exp(-32) of its peak (8
+// standard deviations from x = 0): the window around the i that solves
+// F0 xi0_i = xi0_j - F1 xi1_i', clamped to the axis.
+__device__ __forceinline__ void trans_window(const CrossArgs& a, int j, int i1, int N0, int* ilo, int* ihi) {
+  *ilo = 0;
+  *ihi = N0 - 1;
+  if (!(a.twin > 0.f)) return;
+  const float xj = a.tlo0 + ((float)j + 0.5f) * a.tdx0;
+  const float x1 = a.tlo1 + ((float)i1 + 0.5f) * a.tdx1;
+  const float ic = ((xj - a.tF1 * x1) / a.tF0 - a.tlo0) / a.tdx0 - 0.5f;
+  *ilo = max(0, (int)floorf(ic - a.twin));
+  *ihi = min(N0 - 1, (int)ceilf(ic + a.twin));
+}
+
 // Transition block, left-to-right fibers at mode 0: column be of F is
 // T((a, j), v1_be) = sum_i K(j, i, i'_be) y(a, i), y(a, i) = G_0(a, i, :) . V_1[be]
 // (y staged in the scratch Y, r_a N_0 floats).
@@ -181,8 +195,10 @@ __device__ void trans_fibers_lr(const CrossArgs& a, const float* G0, int rr0, lo
     for (long long row = threadIdx.x; row < M; row += blockDim.x) {
       const int aa = (int)row / N0, j = (int)row - aa * N0;
       const float* y = Y + (long long)aa * N0;
+      int ilo, ihi;
+      trans_window(a, j, i1, N0, &ilo, &ihi);
       float acc = 0.f;
-      for (int i = 0; i < N0; ++i) acc = fmaf(trans_k(a, j, i, i1), y[i], acc);
+      for (int i = ilo; i <= ihi; ++i) acc = fmaf(trans_k(a, j, i, i1), y[i], acc);
       F[(long long)be * M + row] = acc;
     }
     __syncthreads();
@@ -207,7 +223,9 @@ __device__ void trans_fibers_rl(const CrossArgs& a, const float* G0, const float
 #pragma unroll
       for (int t = 0; t < kC; ++t) acc[t] = 0.f;
       const float* g = G0 + (long long)aa * N0 * r1 + c0;
-      for (int i = 0; i < N0; ++i) {
+      int ilo, ihi;
+      trans_window(a, jj, i1, N0, &ilo, &ihi);
+      for (int i = ilo; i <= ihi; ++i) {
         const float kv = trans_k(a, jj, i, i1);
         const float* gi = g + (long long)i * r1;
 #pragma unroll

@@ -263,6 +263,8 @@ struct CrossArgs {
   int trans;
   float tF0, tF1, tiq, tkc;    // F_lo,lo, F_lo,lo+1, 1 / q, dx0 / sqrt(2 pi q)
   float tlo0, tdx0, tlo1, tdx1;  // axes: xi = lo + (i + 1/2) dx
+  float twin;                  // half-width in cells of the old-index window of a sum (beyond it
+                               // K < exp(-32) of its peak); <= 0: the whole axis
 };
 void launch_cross_step(cudaStream_t st, const CrossArgs& a, int q, int kind);
 void launch_cross_last(cudaStream_t st, const CrossArgs& a);
