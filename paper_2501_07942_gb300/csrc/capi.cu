@@ -1271,7 +1271,6 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
     set_rsvd64_attributes();
     set_fft_attributes();
     set_adjoint_attributes();
-    set_cross_attributes();
   });
   ttgbf_ctx* c = new (std::nothrow) ttgbf_ctx();
   if (!c) return TTGBF_ENOMEM;

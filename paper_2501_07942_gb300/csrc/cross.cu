@@ -40,10 +40,6 @@ constexpr int kCW = kCT / 32;
 constexpr int S = kCrossMaxS;
 constexpr float kDelta = 0.05f;
 constexpr int kMaxvolIters = 100;
-// Dynamic shared memory of a step: a filter whose fiber matrix and basis fit
-// in it works there instead of in its global scratch (the CTA's static
-// shared arrays take about 38 KB of the 227 KB).
-constexpr int kDynFloats = 45 * 1024;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -337,17 +333,6 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   const float* Vn = V + (long long)(q + 1) * s * s;
   float* F = a.F + (long long)b * a.fcap;
   float* Qb = a.Qb + (long long)b * a.fcap;
-  {
-    // F (M x ncol) and Qb (M x ncol, or the transition fibers' staging) in
-    // shared memory when both fit: a per-filter choice (sizes are per filter)
-    extern __shared__ float s_dyn[];
-    long long needQ = M * ncol;
-    if (a.trans) needQ = max(needQ, max(M, (long long)a.N[1] * g.r[1]));
-    if (M * ncol + needQ <= kDynFloats) {
-      F = s_dyn;
-      Qb = s_dyn + M * ncol;
-    }
-  }
   float* rn = a.rn + (long long)b * a.mcap;
   unsigned* mask = a.mask + (long long)b * (a.mcap / 32 + 1);
   const float zb = a.trans ? 0.f : a.z[(long long)b * a.zstride + a.zc];
@@ -708,12 +693,7 @@ __global__ void __launch_bounds__(kCT) k_cross_last(CrossArgs a) {
 
 void launch_cross_step(cudaStream_t st, const CrossArgs& a, int q, int kind) {
   count_launches(1);
-  k_cross_step<<<a.B, kCT, kDynFloats * sizeof(float), st>>>(a, q, kind);
-}
-
-void set_cross_attributes() {
-  cudaFuncSetAttribute(k_cross_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kDynFloats * (int)sizeof(float));
+  k_cross_step<<<a.B, kCT, 0, st>>>(a, q, kind);
 }
 
 void launch_cross_last(cudaStream_t st, const CrossArgs& a) {

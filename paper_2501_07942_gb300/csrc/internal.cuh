@@ -268,7 +268,6 @@ struct CrossArgs {
 };
 void launch_cross_step(cudaStream_t st, const CrossArgs& a, int q, int kind);
 void launch_cross_last(cudaStream_t st, const CrossArgs& a);
-void set_cross_attributes();
 // Process-wide count of kernel launches made by the library (capi.cu).
 void count_launches(int n);
 // Function attributes (large dynamic shared memory); call once per process.
