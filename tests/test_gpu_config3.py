@@ -85,10 +85,14 @@ def test_config3_small_grid_vs_dense_oracle(G, d, n, steps):
 
 
 @pytest.mark.parametrize("d,n,steps,smax", [(8, 128, 4, 5), (6, 256, 3, 5), (8, 256, 3, 5),
-                                             (6, 256, 2, 3)])
+                                             (6, 256, 2, 3), (6, 256, 25, 5)])
 def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
     """At N = 256 every shear spans 9 shifts: with a span of 5 (3) it is
-    applied as 2 (3) rounded pieces whose TT sum is rounded again."""
+    applied as 2 (3) rounded pieces whose TT sum is rounded again.  The
+    25-step case is the long horizon: the pieces' extra truncations compound
+    over it, and the summed per-step bound still holds; its ranks may part from
+    the oracle TT filter's at a decision on the threshold (R23), so there it
+    checks them within one of the oracle's."""
     model = synth.config3(d=d, n=n)
     mcs = [0, 1]
     f = make_filter(G, model, batch=len(mcs), smax=smax)
@@ -129,7 +133,10 @@ def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
             e = float(np.sqrt(max(diff2, 0.0) / nn))
             X[b], info = T.step(X[b], g, model.F, model.Q, oc, zs[b][k], model.R, model.eps,
                                 model.rank_cap, smax)
-            assert f.ranks()[b].tolist() == tt.ranks(X[b]), (k, b)
+            if steps <= 4:
+                assert f.ranks()[b].tolist() == tt.ranks(X[b]), (k, b)
+            else:
+                assert np.abs(np.array(f.ranks()[b]) - np.array(tt.ranks(X[b]))).max() <= 1, (k, b)
             bound[b] += tt_tol(model.eps, info["tail_sum"])
             tacc[b] += info["tail_sum"]
             assert e <= bound[b], (k, b, e, bound[b])
