@@ -92,7 +92,9 @@ def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
     25-step case is the long horizon: the pieces' extra truncations compound
     over it, and the summed per-step bound still holds; its ranks may part from
     the oracle TT filter's at a decision on the threshold (R23), so there it
-    checks them within one of the oracle's."""
+    checks them within one of the oracle's, and its covariances, like its
+    means, within the flat bound plus 2 tau sigma_i sigma_j (tau the oracle's
+    summed tails)."""
     model = synth.config3(d=d, n=n)
     mcs = [0, 1]
     f = make_filter(G, model, batch=len(mcs), smax=smax)
@@ -142,7 +144,10 @@ def test_config3_vs_blockwise_oracle(G, d, n, steps, smax):
             assert e <= bound[b], (k, b, e, bound[b])
             D = np.concatenate([gb.delta_axis for gb in grids])
             assert (np.abs(m[b] - mean) <= mean_tol(D, cov, tacc[b])).all(), (k, b, m[b], mean)
-            assert (np.abs(c[b] - cov) <= cov_tol(D, cov)).all(), (k, b, c[b] - cov)
+            # the long horizon's covariances carry its roundings' drift (tau-aware, as the means)
+            ct = cov_tol(D, cov) if steps <= 4 else cov_tol(D, cov, tacc[b])
+            ratio = float((np.abs(c[b] - cov) / ct).max())
+            assert ratio <= 1.0, (k, b, ratio, np.unravel_index(np.argmax(np.abs(c[b] - cov) / ct), ct.shape))
             assert abs(lc[b] - logc) < 1e-3, (k, b, lc[b], logc)
             r = f.ranks()[b]
             assert r.max() <= model.rank_cap
