@@ -29,17 +29,13 @@ def tt_tol(eps: float, tail_sum: float) -> float:
     return 10.0 * (eps + tail_sum) + EPS_TOL_FLOOR
 
 
-def cov_tol(delta_axis, cov, tail_acc=0.0):
+def cov_tol(delta_axis, cov):
     """Covariance tolerance matching the 1e-3 grid-spacing bound on the mean:
     a first-moment error of 1e-3 D_i moves E[x_i x_j] by about
-    1e-3 (D_i sigma_j + D_j sigma_i), sigma from the oracle's diagonal; plus,
-    as for the mean, 2 tau sigma_i sigma_j for the truncations a TT must
-    make (tau the ORACLE TT filter's summed discarded relative tails; 0 gives
-    the flat bound)."""
+    1e-3 (D_i sigma_j + D_j sigma_i), sigma from the oracle's diagonal."""
     D = np.asarray(delta_axis, dtype=np.float64)
     sig = np.sqrt(np.maximum(np.diag(cov), 0.0))
-    return (1e-3 * (D[:, None] * sig[None, :] + sig[:, None] * D[None, :])
-            + 2.0 * tail_acc * sig[:, None] * sig[None, :])
+    return 1e-3 * (D[:, None] * sig[None, :] + sig[:, None] * D[None, :])
 
 
 def mean_tol(delta_axis, cov, tail_acc):
