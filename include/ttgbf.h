@@ -251,11 +251,11 @@ int ttgbf_predict_exact(ttgbf_ctx* ctx, const double* F, const double* Q);
  * of cores lo..hi; the product of the factor with that block is built by a
  * deterministic TT cross of rank opts.cross_rank (Sec. 3, Eq. matrixDecomp:
  * skeletons whose rows and columns are chosen by maximum volume -- Gaussian
- * elimination with partial pivoting, then row exchanges while an entry of
- * Q Q[rows]^-1 exceeds 1.05 -- on orthonormal bases of fiber matrices; start
- * index sets from the density block, opts.cross_sweeps refinement pairs,
- * a final left-to-right sweep), which evaluates the factor only on the
- * fibers it visits; log c of the product is added; the block's links are
+ * elimination with partial pivoting on a fiber matrix (the rows of the same
+ * elimination on an orthonormal basis of its columns), then row exchanges
+ * while an entry of B = Q Q[rows]^-1 exceeds 1.05; start index sets from the
+ * density block, opts.cross_sweeps refinement pairs, a final left-to-right
+ * sweep), which evaluates the factor only on the fibers it visits; log c of the product is added; the block's links are
  * rounded and the TT normalised.  The adjoint (ttgbf_adj_*) does not record
  * block components: a recorded update with one makes ttgbf_adj_backward
  * return TTGBF_ECAPACITY, as for any step the tape cannot hold. */

@@ -16,11 +16,13 @@
 //     right-to-left rows (v, beta in J_{q+1}), columns alpha in I_q; entries
 //     T(alpha, v, beta) = L(...) U_q[alpha] G_q(v) V_{q+1}[beta], U and V the
 //     products of the density's cores along each set element (interfaces);
-//   * its Householder QR and the explicit orthonormal basis Q;
-//   * the maximum-volume rows of Q: Gaussian elimination with partial row
-//     pivoting for a start, then single-row exchanges while an entry of
-//     B = Q Q[rows]^-1 exceeds 1 + delta (the largest entry, the first in
-//     row-major order at a tie);
+//   * the maximum-volume rows of its column space: Gaussian elimination with
+//     partial row pivoting for a start (on the fiber matrix itself: the rows
+//     are those of the same elimination on an orthonormal basis Q of its
+//     columns, the two differing by an upper triangular factor), B =
+//     Q Q[rows]^-1 from the elimination's multipliers (L L1^-1), then
+//     single-row exchanges while an entry of B exceeds 1 + delta (the largest
+//     entry, the first in row-major order at a tie);
 //   * the new index set (table offsets and interfaces) and, in the final
 //     sweep, the core B in the density's layout.
 // The start steps choose right sets from the density block alone (columns:
@@ -40,52 +42,6 @@ constexpr int kCW = kCT / 32;
 constexpr int S = kCrossMaxS;
 constexpr float kDelta = 0.05f;
 constexpr int kMaxvolIters = 100;
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum over the block; every thread gets the same value (same order).
-__device__ float block_sum(float v, float* red) {
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = 0.f;
-  for (int w = 0; w < kCW; ++w) t += red[w];
-  return t;
-}
-
-// Largest value over the block; every thread gets it.
-__device__ float block_max(float v, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = red[0];
-  for (int w = 1; w < kCW; ++w) t = fmaxf(t, red[w]);
-  return t;
-}
-
-// Elementwise block sum of part[0..len-1] into out[0..len-1] (shared).
-__device__ void block_vec_sum(const float* part, int len, float* red, float* out) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  for (int e = 0; e < len; ++e) {
-    const float x = warp_sum(part[e]);
-    if (lane == 0) red[w * S + e] = x;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < len; e += kCT) {
-    float t = 0.f;
-    for (int ww = 0; ww < kCW; ++ww) t += red[ww * S + e];
-    out[e] = t;
-  }
-  __syncthreads();
-}
 
 __device__ __forceinline__ bool better(float v1, long long i1, float v2, long long i2) {
   return v1 > v2 || (v1 == v2 && i1 < i2);
@@ -255,16 +211,11 @@ __device__ __forceinline__ bool taken(const unsigned* mask, long long i) {
 __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind) {
   const int b = blockIdx.x;
   if (b >= a.B) return;
-  __shared__ float s_red[kCW * S];
-  __shared__ float s_vec[S];
   __shared__ float s_brow[S];
-  __shared__ float s_taus[S];
-  __shared__ float s_Qp[S * S];
-  __shared__ float s_Inv[S * S];
+  __shared__ float s_Qp[S * S];  // L1 of the start rows' elimination
   __shared__ float s_rv[kCW];
   __shared__ long long s_ri[kCW];
   __shared__ long long s_piv[S];
-  __shared__ int s_prow;
   const int tid = threadIdx.x;
   const int k = a.k, s = a.s, ld = a.d + 1;
   const bool first = (kind == kCrossStart && q == k - 1);
@@ -390,78 +341,14 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   }
   __syncthreads();
 
-  // ---- Householder QR of F: reflectors H_j = I - tau_j v_j v_j^T in place,
-  // v_j in rows j.. of column j with v_j(j) = 1 (the scaled form: the fibers
-  // span many decades, and squares of entries near 1e-20 are below float32's
-  // normal range, so the norm is taken of the column divided by its largest
-  // magnitude, and tau = (beta - x0) / beta lies in [1, 2]).  A column whose
-  // largest magnitude is below the smallest normal float counts as zero.
+  // ---- maxvol start rows: Gaussian elimination with partial row pivoting on
+  // the fiber matrix itself.  Its rows are those the same elimination picks
+  // on an orthonormal basis Q of the columns (F = Q R, R upper triangular,
+  // leaves every residual column a multiple of Q's), and it needs no basis.
+  // A row not yet pivoted keeps its multipliers L(i, j) in column j.
   const int n = ncol;
-  for (int j = 0; j < n; ++j) {
-    float am = 0.f;
-    for (long long i = j + tid; i < M; i += kCT) am = fmaxf(am, fabsf(F[(long long)j * M + i]));
-    const float amax = block_max(am, s_red);
-    float tau = 0.f;
-    if (amax >= 1.17549435e-38f) {
-      const float inv = 1.f / amax;
-      float ps = 0.f;
-      for (long long i = j + tid; i < M; i += kCT) {
-        const float x = F[(long long)j * M + i] * inv;
-        ps = fmaf(x, x, ps);
-      }
-      const float nrm = sqrtf(block_sum(ps, s_red));  // of the scaled column
-      const float x0 = F[(long long)j * M + j] * inv;
-      const float beta = (x0 >= 0.f) ? -nrm : nrm;
-      tau = (beta - x0) / beta;
-      const float dv = 1.f / (x0 - beta);
-      __syncthreads();
-      for (long long i = j + 1 + tid; i < M; i += kCT) F[(long long)j * M + i] = (F[(long long)j * M + i] * inv) * dv;
-      if (tid == 0) F[(long long)j * M + j] = 1.f;
-    }
-    if (tid == 0) s_taus[j] = tau;
-    __syncthreads();
-    const int len = n - j - 1;
-    if (tau != 0.f && len > 0) {
-      float part[S];
-      for (int e = 0; e < len; ++e) part[e] = 0.f;
-      for (long long i = j + tid; i < M; i += kCT) {
-        const float vi = F[(long long)j * M + i];
-        for (int e = 0; e < len; ++e) part[e] = fmaf(vi, F[(long long)(j + 1 + e) * M + i], part[e]);
-      }
-      block_vec_sum(part, len, s_red, s_vec);
-      for (long long i = j + tid; i < M; i += kCT) {
-        const float vi = F[(long long)j * M + i];
-        for (int e = 0; e < len; ++e) F[(long long)(j + 1 + e) * M + i] -= tau * vi * s_vec[e];
-      }
-      __syncthreads();
-    }
-  }
-  // explicit Q (M x n): the reflectors applied to the first n unit vectors
-  for (int c = 0; c < n; ++c)
-    for (long long i = tid; i < M; i += kCT) Qb[(long long)c * M + i] = (i == c) ? 1.f : 0.f;
-  __syncthreads();
-  for (int j = n - 1; j >= 0; --j) {
-    const float tau = s_taus[j];
-    if (tau == 0.f) continue;
-    const int len = n - j;
-    float part[S];
-    for (int e = 0; e < len; ++e) part[e] = 0.f;
-    for (long long i = j + tid; i < M; i += kCT) {
-      const float vi = F[(long long)j * M + i];
-      for (int e = 0; e < len; ++e) part[e] = fmaf(vi, Qb[(long long)(j + e) * M + i], part[e]);
-    }
-    block_vec_sum(part, len, s_red, s_vec);
-    for (long long i = j + tid; i < M; i += kCT) {
-      const float vi = F[(long long)j * M + i];
-      for (int e = 0; e < len; ++e) Qb[(long long)(j + e) * M + i] -= tau * vi * s_vec[e];
-    }
-    __syncthreads();
-  }
-
-  // ---- maxvol on the first nm columns of Q
   const int nm = min(n, target);
   const long long mwords = M / 32 + 1;
-  for (long long e = tid; e < M * nm; e += kCT) F[e] = Qb[e];
   for (long long e = tid; e < mwords; e += kCT) mask[e] = 0u;
   __syncthreads();
   float best;
@@ -482,76 +369,43 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
       return;
     }
     const float pv = F[(long long)j * M + p];
+    const int len = nm - j - 1;
+    for (int e = tid; e < len; e += kCT) s_brow[e] = F[(long long)(j + 1 + e) * M + p];
+    __syncthreads();  // every thread has read pv and the pivot row before they change
+    for (long long i = tid; i < M; i += kCT) {
+      if (i == p || taken(mask, i)) continue;
+      const float l = pv != 0.f ? F[(long long)j * M + i] / pv : 0.f;
+      F[(long long)j * M + i] = l;
+      for (int e = 0; e < len; ++e) F[(long long)(j + 1 + e) * M + i] -= l * s_brow[e];
+    }
     if (tid == 0) {
       s_piv[j] = p;
       mask[p >> 5] |= 1u << (p & 31);
     }
-    const int len = nm - j - 1;
-    if (pv != 0.f && len > 0) {
-      for (int e = tid; e < len; e += kCT) s_brow[e] = F[(long long)(j + 1 + e) * M + p] / pv;
-      __syncthreads();
-      for (long long i = tid; i < M; i += kCT) {
-        const float xi = F[(long long)j * M + i];
-        for (int e = 0; e < len; ++e) F[(long long)(j + 1 + e) * M + i] -= xi * s_brow[e];
-      }
-    }
     __syncthreads();
   }
-  // Q[rows]^-1 by Gauss-Jordan elimination with partial pivoting
+  // B = F F[rows]^-1 = L L1^-1 (L1 = L[rows], unit lower triangular), in place
+  // of F: a pivot row is the unit row of its place; another row solves
+  // x L1 = L(i, :) from the last column down
   for (int e = tid; e < nm * nm; e += kCT) {
     const int r = e / nm, c = e - r * nm;
-    s_Qp[r * S + c] = Qb[(long long)c * M + s_piv[r]];
-    s_Inv[r * S + c] = (r == c) ? 1.f : 0.f;
+    s_Qp[r * S + c] = c < r ? F[(long long)c * M + s_piv[r]] : (c == r ? 1.f : 0.f);
   }
   __syncthreads();
-  for (int col = 0; col < nm; ++col) {
-    if (tid == 0) {
-      int pr = col;
-      float pvv = fabsf(s_Qp[col * S + col]);
-      for (int r = col + 1; r < nm; ++r)
-        if (fabsf(s_Qp[r * S + col]) > pvv) {
-          pvv = fabsf(s_Qp[r * S + col]);
-          pr = r;
-        }
-      s_prow = pr;
-    }
-    __syncthreads();
-    const int pr = s_prow;
-    if (pr != col)
-      for (int c = tid; c < nm; c += kCT) {
-        float t = s_Qp[col * S + c];
-        s_Qp[col * S + c] = s_Qp[pr * S + c];
-        s_Qp[pr * S + c] = t;
-        t = s_Inv[col * S + c];
-        s_Inv[col * S + c] = s_Inv[pr * S + c];
-        s_Inv[pr * S + c] = t;
-      }
-    __syncthreads();
-    const float d = s_Qp[col * S + col];
-    if (tid < nm) s_vec[tid] = s_Qp[tid * S + col];
-    __syncthreads();
-    for (int c = tid; c < nm; c += kCT) {
-      s_Qp[col * S + c] /= d;
-      s_Inv[col * S + c] /= d;
-    }
-    __syncthreads();
-    for (int e = tid; e < nm * nm; e += kCT) {
-      const int r = e / nm, c = e - r * nm;
-      if (r == col) continue;
-      s_Qp[r * S + c] -= s_vec[r] * s_Qp[col * S + c];
-      s_Inv[r * S + c] -= s_vec[r] * s_Inv[col * S + c];
-    }
-    __syncthreads();
-  }
-  // B = Q Q[rows]^-1 (M x nm) into F
   for (long long i = tid; i < M; i += kCT) {
-    float qrow[S];
-    for (int t = 0; t < nm; ++t) qrow[t] = Qb[(long long)t * M + i];
-    for (int c = 0; c < nm; ++c) {
-      float acc = 0.f;
-      for (int t = 0; t < nm; ++t) acc = fmaf(qrow[t], s_Inv[t * S + c], acc);
-      F[(long long)c * M + i] = acc;
+    if (taken(mask, i)) {
+      int r = 0;
+      while (r < nm && s_piv[r] != i) ++r;
+      for (int c = 0; c < nm; ++c) F[(long long)c * M + i] = (c == r) ? 1.f : 0.f;
+      continue;
     }
+    float x[S];
+    for (int c = nm - 1; c >= 0; --c) {
+      float v = F[(long long)c * M + i];
+      for (int c2 = c + 1; c2 < nm; ++c2) v = fmaf(-x[c2], s_Qp[c2 * S + c], v);
+      x[c] = v;
+    }
+    for (int c = 0; c < nm; ++c) F[(long long)c * M + i] = x[c];
   }
   __syncthreads();
   for (int it = 0; it < kMaxvolIters; ++it) {
