@@ -98,7 +98,7 @@ typedef struct {
    * or more modes, or two modes other than (0, 1)) are applied by a
    * deterministic TT cross of rank cross_rank (see ttgbf_update).  0 (the
    * default): no workspace for it, and such components are TTGBF_EINVAL.
-   * Otherwise rank_cap <= cross_rank <= min(64, rank_cap * max_shift_span);
+   * Otherwise max(rank_cap, 2) <= cross_rank <= min(64, rank_cap * max_shift_span);
    * the workspace grows by about batch * (2 cross_rank^2 N_max + 2 (d + 1)
    * cross_rank^2) floats. */
   int32_t cross_rank;

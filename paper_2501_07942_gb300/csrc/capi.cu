@@ -124,7 +124,7 @@ int validate_opts(const ttgbf_opts* o) {
   const int smax = o->max_shift_span > 0 ? o->max_shift_span : 10;
   if ((long long)o->rank_cap * smax > kMaxN || smax < 2) return TTGBF_ECAPACITY;
   if (o->cross_sweeps < 0 || o->cross_rank < 0) return TTGBF_EINVAL;
-  if (o->cross_rank > 0 && (o->cross_rank < o->rank_cap || o->cross_rank > kCrossMaxS ||
+  if (o->cross_rank > 0 && (o->cross_rank < o->rank_cap || o->cross_rank < 2 || o->cross_rank > kCrossMaxS ||
                             o->cross_rank > o->rank_cap * smax))
     return TTGBF_EINVAL;
   return TTGBF_OK;

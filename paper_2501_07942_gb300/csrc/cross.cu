@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   const int b = blockIdx.x;
   if (b >= a.B) return;
   __shared__ float s_brow[S];
-  __shared__ float s_Qp[S * S];  // L1 of the start rows' elimination
+  __shared__ float s_Qp[S * S];  // the right interfaces while the fibers are built; then L1
+  __shared__ float s_U[S * S];   // the left interfaces while the fibers are built
   __shared__ float s_rv[kCW];
   __shared__ long long s_ri[kCW];
   __shared__ long long s_piv[S];
@@ -292,6 +293,18 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   const long long strq = a.stride[q];
 
   // ---- fiber matrix F (M x ncol, column-major)
+  if (!a.trans) {
+    // the step's interfaces in shared memory (read once per fiber entry)
+    for (int e = tid; e < sL * rlq; e += kCT) {
+      const int al = e / rlq, c = e - al * rlq;
+      s_U[al * S + c] = Uq[al * s + c];
+    }
+    for (int e = tid; e < sR * rrq; e += kCT) {
+      const int be = e / rrq, c = e - be * rrq;
+      s_Qp[be * S + c] = Vn[be * s + c];
+    }
+    __syncthreads();
+  }
   if (a.trans && lr) {
     trans_fibers_lr(a, G, rrq, M, sR, oJn, Vn, g.r[k], F, Qb);
   } else if (a.trans && kind == kCrossRL) {
@@ -304,13 +317,13 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
       float w[S];
       for (int cp = 0; cp < rrq; ++cp) {
         float acc = 0.f;
-        for (int c = 0; c < rlq; ++c) acc = fmaf(Uq[al * s + c], G[((long long)c * nq + v) * rrq + cp], acc);
+        for (int c = 0; c < rlq; ++c) acc = fmaf(s_U[al * S + c], G[((long long)c * nq + v) * rrq + cp], acc);
         w[cp] = acc;
       }
       const long long base = oIq[al] + g.grid(a, q, v) * strq;
       for (int be = 0; be < sR; ++be) {
         float acc = 0.f;
-        for (int cp = 0; cp < rrq; ++cp) acc = fmaf(w[cp], Vn[be * s + cp], acc);
+        for (int cp = 0; cp < rrq; ++cp) acc = fmaf(w[cp], s_Qp[be * S + cp], acc);
         F[(long long)be * M + row] = acc * lik_at(a, base + oJn[be], zb, ob, inv2r);
       }
     } else {
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
       float y[S];
       for (int c = 0; c < rlq; ++c) {
         float acc = 0.f;
-        for (int cp = 0; cp < rrq; ++cp) acc = fmaf(G[((long long)c * nq + v) * rrq + cp], Vn[be * s + cp], acc);
+        for (int cp = 0; cp < rrq; ++cp) acc = fmaf(G[((long long)c * nq + v) * rrq + cp], s_Qp[be * S + cp], acc);
         y[c] = acc;
       }
       if (kind == kCrossStart) {
@@ -333,7 +346,7 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
         const long long baseJ = g.grid(a, q, v) * strq + oJn[be];
         for (int al = 0; al < sL; ++al) {
           float acc = 0.f;
-          for (int c = 0; c < rlq; ++c) acc = fmaf(Uq[al * s + c], y[c], acc);
+          for (int c = 0; c < rlq; ++c) acc = fmaf(s_U[al * S + c], y[c], acc);
           F[(long long)al * M + row] = acc * lik_at(a, oIq[al] + baseJ, zb, ob, inv2r);
         }
       }
@@ -408,18 +421,35 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
     for (int c = 0; c < nm; ++c) F[(long long)c * M + i] = x[c];
   }
   __syncthreads();
+  // each row's largest |B(i, c)| and the first column holding it, kept in
+  // the (now free) scratch Qb by the row's owner and refreshed by each
+  // exchange's update, so an exchange scans M row maxima, not M x nm entries
+  float* rmax = Qb;
+  int* rcol = reinterpret_cast<int*>(Qb + M);
+  for (long long i = tid; i < M; i += kCT) {
+    float mv = -1.f;
+    int mc = 0;
+    for (int c = 0; c < nm; ++c) {
+      const float x = fabsf(F[(long long)c * M + i]);
+      if (x > mv) {
+        mv = x;
+        mc = c;
+      }
+    }
+    rmax[i] = mv;
+    rcol[i] = mc;
+  }
+  __syncthreads();
   for (int it = 0; it < kMaxvolIters; ++it) {
     float bv = -1.f;
     long long bi = -1;
-    for (long long i = tid; i < M; i += kCT)
-      for (int c = 0; c < nm; ++c) {
-        const float x = fabsf(F[(long long)c * M + i]);
-        const long long e = i * nm + c;  // row-major position: the tie order
-        if (bi < 0 || better(x, e, bv, bi)) {
-          bv = x;
-          bi = e;
-        }
+    for (long long i = tid; i < M; i += kCT) {
+      const long long e = i * nm + rcol[i];  // row-major position: the tie order
+      if (bi < 0 || better(rmax[i], e, bv, bi)) {
+        bv = rmax[i];
+        bi = e;
       }
+    }
     const long long e = block_argmax(bv, bi, s_rv, s_ri, &best);
     if (e < 0 || !(best > 1.f + kDelta)) break;
     const long long is = e / nm;
@@ -430,7 +460,18 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
     __syncthreads();
     for (long long i = tid; i < M; i += kCT) {
       const float f = F[(long long)js * M + i] / pvv;
-      for (int c = 0; c < nm; ++c) F[(long long)c * M + i] -= f * s_brow[c];
+      float mv = -1.f;
+      int mc = 0;
+      for (int c = 0; c < nm; ++c) {
+        const float x = F[(long long)c * M + i] - f * s_brow[c];
+        F[(long long)c * M + i] = x;
+        if (fabsf(x) > mv) {
+          mv = fabsf(x);
+          mc = c;
+        }
+      }
+      rmax[i] = mv;
+      rcol[i] = mc;
     }
     __syncthreads();
   }
