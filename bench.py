@@ -762,7 +762,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     cap, smax, prec = args.rank_cap, args.max_shift_span, args.precision
     mc_ids = shard_mc_ids(rank, world, B)
     zs = measurement_batches(model, mc_ids, W + 3 * K)
-    f = make_tt(G, model, dev, B, cap, smax, prec, parts=args.parts)
+    f = make_tt(G, model, dev, B, cap, smax, prec)
     axes = f.grid_axes()
     comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
              for m, t in model.tables(axes)]
@@ -934,9 +934,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("rank cap 16", f"rank cap {cap}"),
                    "rounding_precision": prec, "max_shift_span": smax,
-                   "launch_config": (dict(tuned_config(G, model, B, cap, smax, prec), parts=args.parts)
-                                     if args.parts else
-                                     tuned_config(G, model, B, cap, smax, prec) or "library defaults"),
+                   "launch_config": tuned_config(G, model, B, cap, smax, prec) or "library defaults",
                    "filters_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (independent filters, no collective)"},
         "roofline": roofline,
@@ -991,8 +989,6 @@ def main():
     ap.add_argument("--no-grid-design", action="store_true", help="skip the grid re-design leg")
     ap.add_argument("--no-cross", action="store_true", help="skip the three-mode likelihood (TT cross) leg")
     ap.add_argument("--no-config3", action="store_true", help="skip the config-3 (two transitions) leg")
-    ap.add_argument("--parts", type=int, default=None,
-                    help="concurrent sub-batches of the timed context (default: the autotuned choice)")
     ap.add_argument("--c3-batch", type=int, default=32, help="filters of the config-3 leg")
     ap.add_argument("--c3-steps", type=int, default=3, help="timed steps of the config-3 leg")
     ap.add_argument("--c3-acc-steps", type=int, default=5, help="accuracy steps of the config-3 leg")

@@ -87,7 +87,7 @@ typedef struct {
   int32_t precision;      /* TTGBF_PRECISION_FP32 (0, default) or TTGBF_PRECISION_FP64; see below */
   int32_t conv;           /* TTGBF_CONV_AUTO (0, default), TTGBF_CONV_DENSE or TTGBF_CONV_FFT */
   /* Launch configuration (0 = default; ttgbf_autotune chooses them from measured step times):
-   * parts: sub-batches on their own streams, 1..16 (default one per 12 filters, at most 8; the
+   * parts: sub-batches on their own streams, 1..8 (default one per 12 filters, at most 8; the
    *        environment variable TTGBF_PARTS overrides the default);
    * tsqr_slice_blocks: 128-row blocks per CTA slice of a tall R factor, 2, 4, 8 (default) or 16;
    * svd_threads: CTA width of the truncating SVD stages, 512 (default) or 1024. */

@@ -114,7 +114,7 @@ int validate_opts(const ttgbf_opts* o) {
   if (!o || o->batch < 1 || o->rank_cap < 1) return TTGBF_EINVAL;
   if (o->precision != TTGBF_PRECISION_FP32 && o->precision != TTGBF_PRECISION_FP64) return TTGBF_EINVAL;
   if (o->conv < TTGBF_CONV_AUTO || o->conv > TTGBF_CONV_FFT) return TTGBF_EINVAL;
-  if (o->parts < 0 || o->parts > 16) return TTGBF_EINVAL;
+  if (o->parts < 0 || o->parts > 8) return TTGBF_EINVAL;
   if (o->tsqr_slice_blocks != 0 && o->tsqr_slice_blocks != 2 && o->tsqr_slice_blocks != 4 &&
       o->tsqr_slice_blocks != 8 && o->tsqr_slice_blocks != 16)
     return TTGBF_EINVAL;
@@ -1221,8 +1221,7 @@ const char* ttgbf_strerror(int code) {
 }
 
 // Number of parts of a batch: opts.parts when set, else one per 12 filters,
-// at most 8 (environment TTGBF_PARTS overrides the default, 1..16; opts.parts
-// may ask for up to 16).
+// at most 8 (environment TTGBF_PARTS overrides the default, 1..8).
 // Measured on 100 filters of the 128^4
 // workload: 1 part 32.8 ms per step, 2 parts 30.9, 4 parts 28.2, 8 parts
 // 27.4.
@@ -1230,7 +1229,7 @@ static int choose_parts(const ttgbf_opts* opts) {
   int np = std::min(8, std::max(1, (int)opts->batch / 12));
   if (const char* e = std::getenv("TTGBF_PARTS")) {
     const int v = std::atoi(e);
-    if (v >= 1 && v <= 16) np = v;
+    if (v >= 1 && v <= 8) np = v;
   }
   if (opts->parts > 0) np = opts->parts;
   return std::max(1, std::min(np, (int)opts->batch));
