@@ -212,3 +212,33 @@ def test_block_component_needs_cross_rank_and_is_not_recorded(G):
     assert ei.value.code == -5
     adj.free()
     f.free()
+
+
+def test_split_batch_matches_oracle(G):
+    """26 filters (two concurrent parts, as the bench runs its batches) with
+    different states and measurements of the 3-D range: three of them, one
+    from each end of each part, against the dense update."""
+    g = pmf.Grid([-4.0] * 4, [4.0] * 4, [32] * 4)
+    F = 0.95 * np.eye(4) + 0.05 * np.triu(np.ones((4, 4)), 1)
+    B = 26
+    rng = np.random.default_rng([61])
+    m0s = rng.uniform(-1.5, 1.5, (B, 4))
+    zs = rng.uniform(1.0, 2.6, (B, 1))
+    Xs = [step_state(g, m0s[b], np.ones(4), F, 0.05 * np.eye(4), 1e-6, 16) for b in range(B)]
+    tab = range3(g)
+    f = G.TTFilter(g.lo, g.hi, g.shape, np.zeros(4), np.ones(4), batch=B, rank_cap=16, eps=1e-6,
+                   max_shift_span=10, cross_rank=S)
+    for b in range(B):
+        load(f, b, Xs[b])
+    f.update([((0, 1, 2), dev(tab))], np.array([[0.08]]), zs)
+    mean, cov, lc, ll = f.estimate()
+    for b in (0, 12, 13, B - 1):
+        P = tt.densify(Xs[b])
+        P = P / (P.sum() * g.delta)
+        Pd, logc_d = pmf.update(P, g, pmf.likelihood(g, [((0, 1, 2), tab)], zs[b], np.array([[0.08]])))
+        _, tails, _ = T.update(Xs[b], g, [((0, 1, 2), tab)], zs[b], np.array([[0.08]]), 1e-6, 16)
+        e = rel(tt.densify(f.export_cores(b)), Pd)
+        print(f"filter {b}: GPU {e:.2e}, bound {tt_tol(1e-6, sum(tails)):.1e}, log c diff {abs(lc[b] - logc_d):.1e}")
+        assert e <= tt_tol(1e-6, sum(tails)), (b, e)
+        assert abs(lc[b] - logc_d) < 1e-4
+    f.free()

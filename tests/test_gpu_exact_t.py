@@ -183,3 +183,24 @@ def test_config3_exact_transition_full_size(G):
             assert f.ranks()[b].tolist() == tt.ranks(X[b]), (k, b)
             assert e <= bound[b], (k, b, e, bound[b])
     f.free()
+
+
+def test_split_batch_exact_step(G):
+    """26 filters (two concurrent parts): one textbook step of each from its
+    own state, four of them against the untruncated oracle step."""
+    g = pmf.Grid([-4.0, -2.0, -4.0, -2.0], [4.0, 2.0, 4.0, 2.0], [24, 20, 24, 20])
+    F = np.array([[1.0, 0.4, 0, 0], [0, 1.0, 0, 0], [0, 0, 1.0, 0.4], [0, 0, 0, 1.0]])
+    Q = np.diag([0.02, 0.05, 0.03, 0.04])
+    B = 26
+    Xs = [_state(g, 100 + b) for b in range(B)]
+    f = _filter(G, g, B=B)
+    for b in range(B):
+        f.import_cores(b, [np.asarray(c, dtype=np.float32) for c in Xs[b]], 0.0)
+    f.predict_exact(F, Q)
+    for b in (0, 12, 13, B - 1):
+        ref = tt.densify(T.predict_exact(Xs[b], g, F, Q, 0.0, None)[0])
+        _, tails, _ = T.predict_exact(Xs[b], g, F, Q, 1e-6, 16)
+        e = rel(tt.densify(f.export_cores(b)), ref)
+        print(f"filter {b}: GPU {e:.2e}, bound {tt_tol(1e-6, sum(tails)):.1e}")
+        assert e <= tt_tol(1e-6, sum(tails)), (b, e)
+    f.free()
