@@ -183,3 +183,75 @@ def test_autotune_and_cache(G, tmp_path):
             x.update(comps, m.R, z[k])
     for b in range(4):
         assert rel(tt.densify(f.export_cores(b)), tt.densify(f0.export_cores(b))) < 1e-4
+
+
+def test_group_and_graph_with_a_cross_component(G):
+    """A batch whose likelihood factor couples three modes (applied by the TT
+    cross, cross_rank 16) in a group with an ordinary batch: a group step, and
+    a recorded two-step horizon launched, give bitwise what stepping the batch
+    on its own gives."""
+    import torch
+    m3 = synth.Model(name="range3-small", lo=np.full(3, -4.0), hi=np.full(3, 4.0), n=np.full(3, 16),
+                     m0=np.array([1.0, 0.5, 0.2]), P0=np.eye(3), F=np.eye(3) * 0.95, Q=np.eye(3) * 0.05,
+                     R=np.array([[0.05]]), comps=[((0, 1, 2), synth.workloads.h_range3)], eps=1e-6, rank_cap=8)
+    m2 = small_models()[1]
+    B3, B2, steps = 2, 3, 3
+    z3 = np.stack([synth.simulate(m3, b, steps=steps)[1] for b in range(B3)], axis=1)
+    z2 = np.stack([synth.simulate(m2, b, steps=steps)[1] for b in range(B2)], axis=1)
+
+    def contexts():
+        s3, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        f3 = G.TTFilter(m3.lo, m3.hi, m3.n, m3.m0, np.diag(m3.P0), batch=B3, rank_cap=8, eps=1e-6,
+                        max_shift_span=10, stream=s3, cross_rank=16)
+        f2 = make(G, m2, B2, s2)
+        return f3, f2
+
+    def outs(m, B):
+        return [torch.zeros(B, m.d, dtype=torch.float64, device="cuda"),
+                torch.zeros(B, m.d, m.d, dtype=torch.float64, device="cuda"),
+                torch.zeros(B, dtype=torch.float64, device="cuda"),
+                torch.zeros(B, dtype=torch.float64, device="cuda")]
+
+    fa3, fa2 = contexts()
+    fb3, fb2 = contexts()
+    c3 = device_tables(m3, fa3.grid_axes())
+    c2 = device_tables(m2, fa2.grid_axes())
+    z3d = torch.tensor(z3, dtype=torch.float32, device="cuda")
+    z2d = torch.tensor(z2, dtype=torch.float32, device="cuda")
+    grp = G.TTFilterGroup([fa3, fa2])
+    oa3, oa2, ob3, ob2 = outs(m3, B3), outs(m2, B2), outs(m3, B3), outs(m2, B2)
+    # step 0 as a group step; steps 1, 2 as a recorded horizon of two steps
+    grp.step([(m3.F, m3.Q, c3, m3.R, z3d[0], *oa3), (m2.F, m2.Q, c2, m2.R, z2d[0], *oa2)])
+    zb3 = torch.zeros((2, B3, 1), dtype=torch.float32, device="cuda")
+    zb2 = torch.zeros((2, B2, 1), dtype=torch.float32, device="cuda")
+    ob = [[torch.zeros((2,) + tuple(t.shape), dtype=t.dtype, device="cuda") for t in o] for o in (oa3, oa2)]
+    grp.capture([(m3.F, m3.Q, c3, m3.R, zb3, *ob[0]), (m2.F, m2.Q, c2, m2.R, zb2, *ob[1])], 2)
+    zb3.copy_(z3d[1:3])
+    zb2.copy_(z2d[1:3])
+    grp.launch()
+    for k in range(steps):
+        for f, m, c, zd, o in ((fb3, m3, c3, z3d, ob3), (fb2, m2, c2, z2d, ob2)):
+            f.predict(m.F, m.Q)
+            f.update_dev(c, m.R, zd[k])
+            f.estimate_dev(*o)
+    torch.cuda.synchronize()
+    for fa, fb, B in ((fa3, fb3, B3), (fa2, fb2, B2)):
+        for b in range(B):
+            assert all(np.array_equal(x, y) for x, y in zip(fa.export_cores(b), fb.export_cores(b)))
+    assert torch.equal(ob[0][0][1], ob3[0]) and torch.equal(ob[0][2][1], ob3[2])
+    # and the cross batch against the dense oracle (tails from the oracle TT filter with its cross)
+    g = oracle_grid(m3)
+    oc = m3.tables(g.axes)
+    for b in range(B3):
+        P = pmf.prior(g, m3.m0, m3.P0)
+        X = oracle_tt_prior(m3)
+        bound = 0.0
+        for k in range(steps):
+            P, _ = pmf.predict_rg(P, g, m3.F, m3.Q)
+            P, _ = pmf.update(P, g, pmf.likelihood(g, oc, z3[k][b], m3.R))
+            X, info = T.step(X, g, m3.F, m3.Q, oc, z3[k][b], m3.R, m3.eps, 8, 10)
+            bound += tt_tol(m3.eps, info["tail_sum"])
+        e = rel(tt.densify(fa3.export_cores(b)), P)
+        assert e <= bound, (b, e, bound)
+    for f in (fa3, fa2, fb3, fb2):
+        f.free()
