@@ -29,6 +29,12 @@
 // its rank index) and pad them to the link's size with the rows of largest
 // norm.  The last kernel writes the last core, the fibers T(I_{k-1}, v), and
 // the block's new ranks.
+//
+// With CrossArgs::trans set the block is instead the 2-site block (lo, lo+1)
+// after one factor of the textbook transition (ttgbf_predict_exact): there
+// is no likelihood table, and its fibers are sums over the old grid index of
+// the shifted Gaussian times the block (trans_fibers_lr / trans_fibers_rl);
+// the elimination, exchanges and index sets are the same.
 #include <math.h>
 #include <stdint.h>
 
@@ -163,10 +169,11 @@ __device__ void trans_fibers_lr(const CrossArgs& a, const float* G0, int rr0, lo
 
 // Transition block, fibers along mode 1 for the left elements alpha = (a, j)
 // in oI (raw virtual indices): out(v1, al) = sum_c h(i', c) G_1(c, i', b) with
-// h(i', c) = sum_i K(j, i, i') G_0(a, i, c) (staged in Y, N_1 r_1 floats);
-// column al of F (ld M), or row al of the last core (ld nq) when last.
+// h(i', c) = sum_i K(j, i, i') G_0(a, i, c) (staged in Y, N_1 r_1 floats),
+// written at F + al * M: column al of a fiber matrix (ld M), or row al of the
+// last core (M = its row length).
 __device__ void trans_fibers_rl(const CrossArgs& a, const float* G0, const float* G1, int r1, int rb, int sL,
-                                const long long* oI, float* F, long long M, float* Y, bool last) {
+                                const long long* oI, float* F, long long M, float* Y) {
   const int N0 = a.N[0], N1 = a.N[1];
   constexpr int kC = 16;  // columns of h per pass: K(j, i, i') is evaluated once per kC columns
   const int npass = (r1 + kC - 1) / kC;
@@ -197,8 +204,7 @@ __device__ void trans_fibers_rl(const CrossArgs& a, const float* G0, const float
       const int i1 = (int)row / rb, bb = (int)row - i1 * rb;
       float acc = 0.f;
       for (int c = 0; c < r1; ++c) acc = fmaf(Y[i1 * r1 + c], G1[((long long)c * N1 + i1) * rb + bb], acc);
-      if (last) F[(long long)al * M + row] = acc;  // core layout [al][v1]
-      else F[(long long)al * M + row] = acc;      // column al of the fiber matrix
+      F[(long long)al * M + row] = acc;  // column al of the fiber matrix, or row al of the last core
     }
     __syncthreads();
   }
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(kCT) k_cross_step(CrossArgs a, int q, int kind
   if (a.trans && lr) {
     trans_fibers_lr(a, G, rrq, M, sR, oJn, Vn, g.r[k], F, Qb);
   } else if (a.trans && kind == kCrossRL) {
-    trans_fibers_rl(a, a.core[0] + (long long)b * a.cap[0], G, g.r[1], g.r[k], sL, oIq, F, M, Qb, false);
+    trans_fibers_rl(a, a.core[0] + (long long)b * a.cap[0], G, g.r[1], g.r[k], sL, oIq, F, M, Qb);
   }
   for (long long row = tid; row < M && !(a.trans && kind != kCrossStart); row += kCT) {
     if (lr) {
@@ -565,7 +571,7 @@ __global__ void __launch_bounds__(kCT) k_cross_last(CrossArgs a) {
   float* O = a.out[q] + (long long)b * a.cap[q];
   if (a.trans) {
     trans_fibers_rl(a, a.core[0] + (long long)b * a.cap[0], G, g.r[1], g.r[k], sL, oI, O, nq,
-                    a.Qb + (long long)b * a.fcap, true);
+                    a.Qb + (long long)b * a.fcap);
   }
   const float zb = a.trans ? 0.f : a.z[(long long)b * a.zstride + a.zc];
   const float ob = a.trans ? 0.f : a.off[b];
