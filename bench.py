@@ -561,16 +561,21 @@ def run_cross(args, dev):
     if args.cross_no_compare:
         return out
     out["fullgrid"] = run_fullgrid(args, model, zs, W, K, dev, axes)
-    # accuracy: Monte Carlo run 0 against the float64 full-grid filter
-    f0 = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1, rank_cap=cap,
-                    eps=model.eps, max_shift_span=smax, device=dev, cross_rank=S)
-    errs = []
+    # accuracy: Monte Carlo run 0 against the float64 full-grid filter, at the
+    # leg's rank cap and at rank cap 32 (span 5, cross rank 40)
+    runs = [(cap, smax, S), (32, 5, 40)]
+    tts = [G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=1, rank_cap=c,
+                      eps=model.eps, max_shift_span=sp, device=dev, cross_rank=sr) for c, sp, sr in runs]
+    errs = [[] for _ in runs]
     for k, P in enumerate(fp64_reference_densities(model, zs, W + K, dev, axes)):
-        f0.predict(model.F, model.Q)
-        f0.update(comps, model.R, zs[k][0][None, :])
-        errs.append(tt_dense_rel_err(f0.export_cores(0), P))
-    f0.free()
-    out["tt_density_rel_fro_err"] = errs
+        for f0, e in zip(tts, errs):
+            f0.predict(model.F, model.Q)
+            f0.update(comps, model.R, zs[k][0][None, :])
+            e.append(tt_dense_rel_err(f0.export_cores(0), P))
+    for f0 in tts:
+        f0.free()
+    out["tt_density_rel_fro_err"] = errs[0]
+    out["tt_density_rel_fro_err_rank_cap_32"] = errs[1]
     return out
 
 
