@@ -295,6 +295,16 @@ int ttgbf_grid_axes(const ttgbf_ctx* ctx, double* axes);
  * of buf in floats; TTGBF_ENOMEM if too small.  Synchronises. */
 int ttgbf_export_cores(ttgbf_ctx* ctx, int32_t f, float* buf, size_t cap, int32_t* ranks_out);
 
+/* Filter f's TT contracted into its full tensor on the device, float64
+ * accumulation of the float32 cores: host out[n_0][n_1]...[n_{d-1}] row-major
+ * (the last mode fastest), the density's values at the cell centres (summing
+ * to 1 / cell volume after a step's normalisation).  For small grids only: it
+ * allocates and frees two device buffers of at most max_k n_0...n_k r_{k+1}
+ * doubles.  cap is the size of out in doubles; TTGBF_ENOMEM if n_0...n_{d-1}
+ * exceeds it or 2^32, or if the device buffers cannot be allocated.
+ * Synchronises. */
+int ttgbf_densify(ttgbf_ctx* ctx, int32_t f, double* out, size_t cap);
+
 /* Replace filter f's cores (same layout as export); ranks[k] <= rank_cap for
  * interior links.  Resets f's log-likelihood to log_lik. */
 int ttgbf_import_cores(ttgbf_ctx* ctx, int32_t f, const float* buf, const int32_t* ranks,

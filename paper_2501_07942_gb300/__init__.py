@@ -32,7 +32,8 @@ EXPORTED = [
     "ttgbf_workspace_bytes", "ttgbf_init", "ttgbf_predict", "ttgbf_predict_exact", "ttgbf_update",
     "ttgbf_update_dev",
     "ttgbf_estimate", "ttgbf_estimate_dev", "ttgbf_free", "ttgbf_strerror", "ttgbf_ranks",
-    "ttgbf_stats", "ttgbf_grid_axes", "ttgbf_export_cores", "ttgbf_import_cores", "ttgbf_shear",
+    "ttgbf_stats", "ttgbf_grid_axes", "ttgbf_export_cores", "ttgbf_densify", "ttgbf_import_cores",
+    "ttgbf_shear",
     "ttgbf_scale", "ttgbf_convolve", "ttgbf_round", "ttgbf_normalise", "ttgbf_profile",
     "ttgbf_profile_read", "ttgbf_launch_count", "ttgbf_moments_noalloc", "ttgbf_fg_workspace_bytes",
     "ttgbf_fg_init", "ttgbf_fg_predict", "ttgbf_fg_predict_direct", "ttgbf_fg_update",
@@ -132,6 +133,7 @@ def load() -> ctypes.CDLL:
     lib.ttgbf_export_cores.argtypes = [VP, ctypes.c_int32, P(ctypes.c_float), ctypes.c_size_t,
                                        P(ctypes.c_int32)]
     lib.ttgbf_import_cores.argtypes = [VP, ctypes.c_int32, P(ctypes.c_float), P(ctypes.c_int32), D]
+    lib.ttgbf_densify.argtypes = [VP, ctypes.c_int32, dp, ctypes.c_size_t]
     lib.ttgbf_shear.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, D, ctypes.c_int32]
     lib.ttgbf_scale.argtypes = [VP, ctypes.c_int32, D]
     lib.ttgbf_convolve.argtypes = [VP, dp]
@@ -410,6 +412,15 @@ class TTFilter:
             cores.append(buf[at:at + cnt].reshape(int(r[k]), self.n[k], int(r[k + 1])).copy())
             at += cnt
         return cores
+
+    def densify(self, f=0, cap=None):
+        """Filter f's density on the full grid (float64, shape n), contracted
+        on the device; small grids only."""
+        total = int(np.prod(self.n))
+        out = np.zeros(total if cap is None else int(cap), dtype=np.float64)
+        _check(self._lib.ttgbf_densify(self._ctx, int(f), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       out.size), "ttgbf_densify")
+        return out[:total].reshape(self.n)
 
     def import_cores(self, f, cores, log_lik=0.0):
         r = np.array([1] + [int(c.shape[2]) for c in cores], dtype=np.int32)

@@ -1898,6 +1898,51 @@ int ttgbf_export_cores(ttgbf_ctx* c, int32_t f, float* buf, size_t cap, int32_t*
   return check(c);
 }
 
+int ttgbf_densify(ttgbf_ctx* c, int32_t f, double* out, size_t cap) {
+  if (split(c)) {
+    if (f < 0 || f >= c->B) return TTGBF_EINVAL;
+    int local = 0;
+    const int p = part_of(c, f, &local);
+    return fan_out(c, [&](ttgbf_ctx* q, int pp) { return pp == p ? ttgbf_densify(q, local, out, cap) : TTGBF_OK; });
+  }
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!out || f < 0 || f >= c->B) return TTGBF_EINVAL;
+  const int d = c->d;
+  std::vector<int32_t> r(d + 1);
+  cudaMemcpyAsync(r.data(), c->ranks + (size_t)f * (d + 1), sizeof(int) * (d + 1), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c);
+  // Sizes of the stages' results n_0 ... n_k r_{k+1}; the last is the tensor.
+  const long long kMaxElems = 1LL << 32;
+  long long P = 1, most = 1;
+  for (int k = 0; k < d; ++k) {
+    P *= c->n[k];
+    if (P > kMaxElems) return TTGBF_ENOMEM;
+    most = std::max(most, P * r[k + 1]);
+    if (most > kMaxElems) return TTGBF_ENOMEM;
+  }
+  if ((size_t)P > cap) return TTGBF_ENOMEM;
+  double* buf[2] = {nullptr, nullptr};
+  if (cudaMalloc(&buf[0], sizeof(double) * most) != cudaSuccess ||
+      cudaMalloc(&buf[1], sizeof(double) * most) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(buf[0]);
+    return TTGBF_ENOMEM;
+  }
+  long long rows = 1;
+  for (int k = 0; k < d; ++k) {
+    launch_densify_stage(c->st, k ? buf[(k + 1) & 1] : nullptr, rows, r[k], curp(c, k) + (size_t)f * c->L.core_cap[k],
+                         c->n[k], r[k + 1], buf[k & 1]);
+    rows *= c->n[k];
+  }
+  cudaMemcpyAsync(out, buf[(d - 1) & 1], sizeof(double) * P, cudaMemcpyDeviceToHost, c->st);
+  const bool ok = cudaStreamSynchronize(c->st) == cudaSuccess;
+  cudaFree(buf[0]);
+  cudaFree(buf[1]);
+  if (!ok) return cuda_fail(c);
+  return check(c);
+}
+
 int ttgbf_import_cores(ttgbf_ctx* c, int32_t f, const float* buf, const int32_t* ranks, double log_lik) {
   if (c) tape_fail(c);
   if (split(c)) {

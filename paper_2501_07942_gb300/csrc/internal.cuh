@@ -181,6 +181,8 @@ void launch_lik_apply_1d(cudaStream_t st, int B, float* core, long long cap, int
                          double R, float period, const float* off);
 void launch_logc(cudaStream_t st, int B, const double* mass, const double* logoff, double* log_c,
                  double* log_lik, int add);
+void launch_densify_stage(cudaStream_t st, const double* X, long long P, int ra, const float* G, int n, int rb,
+                          double* Y);
 // Moments of a TT given by per-core base pointers (filter stride cap[kk]) and
 // rank indices: core kk has ranks (ranks[b][ridx[kk]], ranks[b][ridx[kk+1]]).
 struct MomentArgs {

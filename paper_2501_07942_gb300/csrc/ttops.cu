@@ -681,6 +681,35 @@ void launch_logc(cudaStream_t st, int B, const double* mass, const double* logof
   k_logc<<<(B + 255) / 256, 256, 0, st>>>(B, mass, logoff, log_c, log_lik, add);
 }
 
+// One stage of contracting a TT into its full tensor (a diagnostic for small
+// grids): Y[p][i][b] = sum_a X[p][a] G[a][i][b], with X the row vector 1 for
+// the first core (ra = 1); float32 cores, float64 accumulation.
+__global__ void k_densify_stage(const double* X, long long P, int ra, const float* G, int n, int rb, double* Y) {
+  const long long tot = P * n * rb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t % rb);
+    const long long pi = t / rb;
+    const int i = (int)(pi % n);
+    const long long p = pi / n;
+    double s = 0.0;
+    if (!X) {
+      s = (double)G[(long long)i * rb + b];
+    } else {
+      for (int a = 0; a < ra; ++a) s += X[p * ra + a] * (double)G[((long long)a * n + i) * rb + b];
+    }
+    Y[t] = s;
+  }
+}
+
+void launch_densify_stage(cudaStream_t st, const double* X, long long P, int ra, const float* G, int n, int rb,
+                          double* Y) {
+  count_launches(1);
+  const long long tot = P * n * rb;
+  const long long blocks = std::min<long long>((tot + 255) / 256, 152LL * 8);
+  k_densify_stage<<<(int)std::max<long long>(blocks, 1), 256, 0, st>>>(X, P, ra, G, n, rb, Y);
+}
+
 void set_ttops_attributes() {
   cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kMomentSmemDoubles * (int)sizeof(double));

@@ -217,6 +217,45 @@ def test_batch_split_into_concurrent_parts(G, monkeypatch):
     np.testing.assert_allclose(t3, t1, rtol=1e-3, atol=1e-6)
 
 
+@pytest.mark.parametrize("parts", ["1", "3"])
+def test_densify_on_device(G, monkeypatch, parts):
+    """ttgbf_densify contracts a filter's cores into the full grid on the
+    device: the same tensor as the host contraction of the exported cores
+    (both in float64 from the same float32 cores, so equal up to the order of
+    the sums), normalised to 1 / cell volume after a step, and within one
+    step's parity bound of the dense oracle; too small a buffer and a filter
+    index out of range are refused."""
+    monkeypatch.setenv("TTGBF_PARTS", parts)
+    model = synth.config2(n=24)
+    B = 4
+    zs = np.stack([synth.simulate(model, mc, steps=1)[1] for mc in range(B)], axis=1)
+    f = make_filter(G, model, batch=B)
+    comps = device_tables(model, f.grid_axes())
+    f.predict(model.F, model.Q)
+    f.update(comps, model.R, zs[0])
+    g = oracle_grid(model)
+    oc = model.tables(g.axes)
+    X0 = oracle_tt_prior(model)
+    for b in range(B):
+        D = f.densify(b)
+        assert D.shape == tuple(model.n)
+        H = tt.densify(f.export_cores(b))
+        assert float(np.abs(D - H).max()) <= 1e-12 * float(np.abs(H).max())
+        assert abs(D.sum() * g.delta - 1.0) < 1e-5
+        P, _ = pmf.predict_rg(pmf.prior(g, model.m0, model.P0), g, model.F, model.Q)
+        P, _ = pmf.update(P, g, pmf.likelihood(g, oc, zs[0][b], model.R))
+        _, info = T.step(X0, g, model.F, model.Q, oc, zs[0][b], model.R, model.eps, model.rank_cap)
+        assert rel(D, P) <= tt_tol(model.eps, info["tail_sum"])
+    total = int(np.prod(model.n))
+    with pytest.raises(G.TTGBFError) as ei:
+        f.densify(0, cap=total - 1)
+    assert ei.value.code == -3
+    with pytest.raises(G.TTGBFError) as ei:
+        f.densify(B)
+    assert ei.value.code == -1
+    f.free()
+
+
 def test_shears_in_pieces_small_grid(G):
     """Every shear of the 32^4 workload spans 3 shifts; with a span of 2 each
     runs as two rounded pieces (both triangles' couplings, including the
