@@ -105,6 +105,7 @@ typedef struct {
   /* (left-to-right, right-to-left) pairs of cross sweeps before the final
    * left-to-right sweep; 0 = 1. */
   int32_t cross_sweeps;
+  int32_t contraction;    /* TTGBF_CONTRACT_FP32 (0, default), _TF32 or _TF32X3; see below */
 } ttgbf_opts;
 
 /* How the Gaussian kernel of the predictive step (Eq. tpmconvFFT, applied to
@@ -139,6 +140,25 @@ typedef struct {
  *        counted in the discarded tail. */
 #define TTGBF_PRECISION_FP32 0
 #define TTGBF_PRECISION_FP64 1
+
+/* Arithmetic of the core contractions (the grouped products that apply the
+ * rounding's factors to the cores, the per-mode operators of the predictive
+ * step and the 2-site merge of the update):
+ *  FP32:   float32 fused multiply-adds on the CUDA cores.
+ *  TF32:   the tensor cores (tcgen05.mma, kind::tf32): operands rounded to
+ *          TF32 (10-bit mantissa, round to nearest), float32 accumulation.
+ *          A product's relative error is about 2^-11 per term, which can
+ *          exceed eps-level rounding tolerances: the TT's error against the
+ *          float32 path grows accordingly.
+ *  TF32X3: the tensor cores with each operand split into a TF32 part and a
+ *          TF32-rounded remainder, three products (hi*hi + hi*lo + lo*hi):
+ *          float32-level products (about 2^-21 relative) at three times the
+ *          tensor work.
+ * A tensor-core product whose completion wait exceeds one second is written
+ * as NaN and makes the next ttgbf_stats return TTGBF_ECUDA. */
+#define TTGBF_CONTRACT_FP32 0
+#define TTGBF_CONTRACT_TF32 1
+#define TTGBF_CONTRACT_TF32X3 2
 
 /* One measurement component z_c = h_c(x_...) + v_c (Sec. 4, fourth bullet: the
  * likelihood tensor).  htab is a caller-owned DEVICE array with h_c evaluated

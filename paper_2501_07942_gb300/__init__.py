@@ -67,11 +67,13 @@ class Opts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("precision", ctypes.c_int32), ("conv", ctypes.c_int32), ("parts", ctypes.c_int32),
                 ("tsqr_slice_blocks", ctypes.c_int32), ("svd_threads", ctypes.c_int32),
-                ("cross_rank", ctypes.c_int32), ("cross_sweeps", ctypes.c_int32)]
+                ("cross_rank", ctypes.c_int32), ("cross_sweeps", ctypes.c_int32),
+                ("contraction", ctypes.c_int32)]
 
 
 PRECISION = {"fp32": 0, "fp64": 1}  # TTGBF_PRECISION_FP32 / TTGBF_PRECISION_FP64
 CONV = {"auto": 0, "dense": 1, "fft": 2}  # TTGBF_CONV_AUTO / _DENSE / _FFT
+CONTRACT = {"fp32": 0, "tf32": 1, "tf32x3": 2}  # TTGBF_CONTRACT_FP32 / _TF32 / _TF32X3
 
 
 class MeasComp(ctypes.Structure):
@@ -285,14 +287,17 @@ class TTFilter:
 
     def __init__(self, lo, hi, n, prior_mean, prior_var, batch=1, rank_cap=16, eps=1e-6,
                  max_shift_span=0, stream=None, device="cuda", precision="fp32", conv="auto",
-                 parts=0, tsqr_slice_blocks=0, svd_threads=0, cross_rank=0, cross_sweeps=0):
+                 parts=0, tsqr_slice_blocks=0, svd_threads=0, cross_rank=0, cross_sweeps=0,
+                 contraction="fp32"):
         """precision: "fp32" (R factors and SVDs of the rounding in float32) or
         "fp64" (those of the truncating stages in float64), ttgbf_opts.precision.
         conv: "auto", "dense" or "fft", how the Gaussian kernel is applied
         (ttgbf_opts.conv).  parts, tsqr_slice_blocks, svd_threads: the launch
         configuration (0 = the library's default; see ttgbf_autotune).
         cross_rank, cross_sweeps: the TT cross of likelihood factors on several
-        modes (ttgbf_opts.cross_rank; 0 = not available)."""
+        modes (ttgbf_opts.cross_rank; 0 = not available).  contraction: "fp32"
+        (CUDA cores), "tf32" or "tf32x3" (tensor cores), the arithmetic of the
+        core contractions (ttgbf_opts.contraction)."""
         import torch
         self._lib = load()
         self.d = len(n)
@@ -304,7 +309,7 @@ class TTFilter:
         o = Opts(self.batch, int(rank_cap), float(eps), int(max_shift_span),
                  ctypes.c_void_p(self._stream.cuda_stream), None, 0, PRECISION[precision],
                  CONV[conv], int(parts), int(tsqr_slice_blocks), int(svd_threads), int(cross_rank),
-                 int(cross_sweeps))
+                 int(cross_sweeps), CONTRACT[contraction])
         nbytes = self._lib.ttgbf_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
         pm, pv = _f64(prior_mean), _f64(prior_var)
         pr = Prior(_dptr(pm), _dptr(pv))
@@ -553,7 +558,7 @@ class TTFilterGroup:
 
 def autotune(lo, hi, n, prior_mean, prior_var, F, Q, batch=1, rank_cap=16, eps=1e-6,
              max_shift_span=0, precision="fp32", conv="auto", steps=3, cache_path=None,
-             cache_only=False):
+             cache_only=False, contraction="fp32"):
     """ttgbf_autotune: the fastest launch configuration (parts,
     tsqr_slice_blocks, svd_threads) for this batch shape and model, and its
     time per predictive step in ms.  cache_only: look the shape up in
@@ -565,7 +570,7 @@ def autotune(lo, hi, n, prior_mean, prior_var, F, Q, batch=1, rank_cap=16, eps=1
     pm, pv = _f64(prior_mean), _f64(prior_var)
     pr = Prior(_dptr(pm), _dptr(pv))
     o = Opts(int(batch), int(rank_cap), float(eps), int(max_shift_span), None, None, 0,
-             PRECISION[precision], CONV[conv], 0, 0, 0)
+             PRECISION[precision], CONV[conv], 0, 0, 0, 0, 0, CONTRACT[contraction])
     best = Opts()
     ms = ctypes.c_double()
     F, Q = _f64(F), _f64(Q)

@@ -113,6 +113,7 @@ int validate_grid(const ttgbf_grid* g) {
 int validate_opts(const ttgbf_opts* o) {
   if (!o || o->batch < 1 || o->rank_cap < 1) return TTGBF_EINVAL;
   if (o->precision != TTGBF_PRECISION_FP32 && o->precision != TTGBF_PRECISION_FP64) return TTGBF_EINVAL;
+  if (o->contraction < TTGBF_CONTRACT_FP32 || o->contraction > TTGBF_CONTRACT_TF32X3) return TTGBF_EINVAL;
   if (o->conv < TTGBF_CONV_AUTO || o->conv > TTGBF_CONV_FFT) return TTGBF_EINVAL;
   if (o->parts < 0 || o->parts > 8) return TTGBF_EINVAL;
   if (o->tsqr_slice_blocks != 0 && o->tsqr_slice_blocks != 2 && o->tsqr_slice_blocks != 4 &&
@@ -188,7 +189,7 @@ Layout make_layout(const ttgbf_grid* g, const ttgbf_opts* o) {
   L.P2 = a.take<float>((size_t)B * kMaxN * kMaxN);
   L.gdesc_cap = std::max(2 * B, B * (capr + 1));
   L.gdesc = a.take<GemmDesc>(L.gdesc_cap);
-  L.gtiles = a.take<int>(L.gdesc_cap + 1);
+  L.gtiles = a.take<int>(L.gdesc_cap + 2);  // + the tensor-core status word
   L.awork_stride = (long long)(d + 1) * 3 * kMaxN * kMaxN;
   L.awork = a.take<double>((size_t)B * L.awork_stride);
   L.W_cap = (d >= 2) ? (long long)g->n[0] * g->n[1] * o->rank_cap : 1;
@@ -246,6 +247,8 @@ struct ttgbf_ctx {
   int cross_s = 0, cross_sweeps = 1;
   CrossArgs x{};
   int precision = TTGBF_PRECISION_FP32;
+  int contract = kContractFp32;  // arithmetic of the grouped GEMM (opts.contraction)
+  int* tc_status = nullptr;      // set by a tensor-core tile that gave up waiting
   int slice_blocks = kTsqrSliceBlocks, svd_threads = 512;
   double eps = 0.0, delta = 1.0;
   cudaStream_t st = nullptr;
@@ -380,7 +383,9 @@ RoundState round_state(ttgbf_ctx* c) {
   return RoundState{c->normA, c->tail_sum, c->tail_max, c->cap_hits, c->newrank};
 }
 
-GemmWork gemm_work(ttgbf_ctx* c, int ndesc) { return GemmWork{c->gdesc, c->gtiles, ndesc}; }
+GemmWork gemm_work(ttgbf_ctx* c, int ndesc) {
+  return GemmWork{c->gdesc, c->gtiles, ndesc, c->contract, c->tc_status};
+}
 
 // Diagnostic (environment TTGBF_DEBUG_STAGES=1): after each rounding stage,
 // synchronise and report filter 0's ranks and whether the two cores the
@@ -1280,6 +1285,7 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   c->smax = opts->max_shift_span > 0 ? opts->max_shift_span : 10;
   c->capr = c->rank_cap * c->smax;
   c->precision = opts->precision;
+  c->contract = opts->contraction;
   c->conv_mode = opts->conv;
   c->slice_blocks = opts->tsqr_slice_blocks > 0 ? opts->tsqr_slice_blocks : kTsqrSliceBlocks;
   c->svd_threads = opts->svd_threads > 0 ? opts->svd_threads : 512;
@@ -1370,6 +1376,7 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   c->P2 = (float*)(b + L.P2);
   c->gdesc = (GemmDesc*)(b + L.gdesc);
   c->gtiles = (int*)(b + L.gtiles);
+  c->tc_status = c->gtiles + L.gdesc_cap + 1;
   c->awork = (double*)(b + L.awork);
   c->W = (float*)(b + L.W);
   c->opmats = (float*)(b + L.opmats);
@@ -1410,6 +1417,7 @@ static int init_single(ttgbf_ctx** out, const ttgbf_grid* grid, const ttgbf_prio
   cudaMemsetAsync(c->cap_hits, 0, sizeof(int) * c->B, c->st);
   cudaMemsetAsync(c->mass_pred, 0, sizeof(double) * c->B, c->st);
   cudaMemsetAsync(c->prof_flops, 0, sizeof(double) * kPClasses, c->st);
+  cudaMemsetAsync(c->tc_status, 0, sizeof(int), c->st);
   launch_prior(c->st, c->B, c->geom, c->buf[0], c->ranks, c->axes_d, c->pmean, c->pvar);
   enqueue_normalise(c, c->mass);
   // synchronous: prior values come from host memory the caller may free
@@ -1845,6 +1853,8 @@ int ttgbf_stats(ttgbf_ctx* c, ttgbf_step_stats* out) {
   const int B = c->B, d = c->d;
   std::vector<double> ts(B), tm(B), mp(B), lc(B), ll(B);
   std::vector<int> ch(B), rk((size_t)B * (d + 1));
+  int tcs = 0;
+  cudaMemcpyAsync(&tcs, c->tc_status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(ts.data(), c->tail_sum, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(tm.data(), c->tail_max, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(mp.data(), c->mass_pred, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st);
@@ -1858,6 +1868,7 @@ int ttgbf_stats(ttgbf_ctx* c, ttgbf_step_stats* out) {
     for (int k = 0; k <= d; ++k) mr = std::max(mr, rk[(size_t)b * (d + 1) + k]);
     out[b] = ttgbf_step_stats{ts[b], tm[b], mp[b], lc[b], ll[b], mr, ch[b]};
   }
+  if (tcs != 0) return cuda_fail(c);  // a tensor-core product was given up (written as NaN)
   return check(c);
 }
 
@@ -2798,7 +2809,8 @@ std::string tune_key(const ttgbf_grid* g, const ttgbf_opts* o, const double* F) 
   for (int m = 0; m < d; ++m) k += std::to_string(g->n[m]) + (m + 1 < d ? "," : "");
   k += ";batch=" + std::to_string(o->batch) + ";cap=" + std::to_string(o->rank_cap) +
        ";span=" + std::to_string(o->max_shift_span > 0 ? o->max_shift_span : 10) +
-       ";prec=" + std::to_string(o->precision) + ";conv=" + std::to_string(o->conv) + ";shears=";
+       ";prec=" + std::to_string(o->precision) + ";contract=" + std::to_string(o->contraction) +
+       ";conv=" + std::to_string(o->conv) + ";shears=";
   std::vector<double> Lm, D, U;
   if (ldu(F, d, &Lm, &D, &U) == TTGBF_OK) {
     for (int m = 0; m < d; ++m)
@@ -3551,6 +3563,7 @@ int ttgbf_adj_create(ttgbf_adj** out, ttgbf_ctx* c, int32_t steps, int32_t slots
     o.max_shift_span = smax;
     o.stream = c->st;
     o.precision = c->precision;
+    o.contraction = c->contract;
     o.conv = TTGBF_CONV_DENSE;
     o.parts = 1;
     o.tsqr_slice_blocks = c->slice_blocks;

@@ -82,9 +82,20 @@ struct GemmDesc {
 
 struct GemmWork {
   GemmDesc* desc;  // [ndesc]
-  int* tiles;      // [ndesc + 1] exclusive prefix of kTile x kTile tile counts
+  int* tiles;      // [ndesc + 1] exclusive prefix of tile counts
   int ndesc;
+  int tc;          // kContract*: SIMT float32 tiles, or tensor-core tiles
+  int* status;     // set to 1 by a tensor-core tile that gave up waiting
 };
+
+// Contraction arithmetic of the grouped GEMM.
+enum ContractMode : int { kContractFp32 = 0, kContractTf32 = 1, kContractTf32x3 = 2 };
+// Tensor-core tiles: 128 along C's longer side, 32 along the shorter;
+// shape kTcShapeN = rows of C along the 128, kTcShapeT = columns of C.
+constexpr int kTcTileM = 128;
+constexpr int kTcTileN = 32;
+constexpr int kTcShapeN = 3;
+constexpr int kTcShapeT = 4;
 
 enum StageMode : int { kStageRight = 0, kStageLeft = 1, kStageSplit = 2 };
 
@@ -124,6 +135,7 @@ void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeo
                             const float* W, long long W_cap, int N1, GemmWork gw, int vS,
                             int dstride);
 void launch_gemm(cudaStream_t st, GemmWork gw, int grid, double* flops);
+void launch_gemm_tc(cudaStream_t st, GemmWork gw, int grid, double* flops);
 // Tile prefix for descriptors already written to gw.desc (ndesc entries).
 void launch_scan_tiles(cudaStream_t st, GemmWork gw);
 

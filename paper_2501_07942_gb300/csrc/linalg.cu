@@ -13,6 +13,8 @@
 // Every problem size is read from the device rank array.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace ttgbf {
@@ -979,6 +981,13 @@ __global__ void __launch_bounds__(256, 4) k_gemm_grouped(GemmWork w, double* flo
 __device__ void scan_tiles_block(GemmWork w) {
   for (int i = threadIdx.x; i < w.ndesc; i += blockDim.x) {
     GemmDesc& g = w.desc[i];
+    if (w.tc != kContractFp32) {
+      const bool tr = g.n > g.m;
+      g.shape = tr ? kTcShapeT : kTcShapeN;
+      const int lng = tr ? g.n : g.m, sht = tr ? g.m : g.n;
+      w.tiles[i] = (g.m > 0 && g.n > 0) ? ((lng + kTcTileM - 1) / kTcTileM) * ((sht + kTcTileN - 1) / kTcTileN) : 0;
+      continue;
+    }
     const int sh = gemm_shape(g.m, g.n);
     g.shape = sh;
     const int bm = gemm_bm(sh), bn = gemm_bn(sh);
@@ -1160,6 +1169,10 @@ void launch_plan_gemm_stage(cudaStream_t st, int B, int mode, int k, const TTGeo
 }
 
 void launch_gemm(cudaStream_t st, GemmWork gw, int grid, double* flops) {
+  if (gw.tc != kContractFp32) {
+    launch_gemm_tc(st, gw, std::max(1, grid / 2), flops);
+    return;
+  }
   count_launches(1);
   k_gemm_grouped<<<grid, 256, 0, st>>>(gw, flops);
 }

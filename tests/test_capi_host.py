@@ -64,7 +64,7 @@ def _init(lib, lo, hi, n, mean, var, **kw):
     g, keep = G._grid(lo, hi, n)
     o = G.Opts(kw.get("batch", 1), kw.get("rank_cap", 16), kw.get("eps", 1e-6),
                kw.get("smax", 0), None, None, 0, kw.get("precision", 0), kw.get("conv", 0),
-               0, 0, 0, kw.get("cross_rank", 0), kw.get("cross_sweeps", 0))
+               0, 0, 0, kw.get("cross_rank", 0), kw.get("cross_sweeps", 0), kw.get("contraction", 0))
     m, v = G._f64(mean), G._f64(var)
     p = G.Prior(G._dptr(m), G._dptr(v))
     ctx = ctypes.c_void_p()
@@ -86,6 +86,8 @@ def test_init_validates_before_device(lib):
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], precision=2)[0] == -1
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], precision=-1)[0] == -1
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], conv=3)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], contraction=3)[0] == -1
+    assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], contraction=-1)[0] == -1
     # the cross rank: at least the rank cap, at most 64 and the rank capacity
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], cross_rank=8)[0] == -1
     assert _init(lib, [0.0], [1.0], [8], [0.0], [1.0], cross_rank=65)[0] == -1

@@ -81,11 +81,16 @@ def oracle_state(model, mc, steps, cap, smax=10):
 
 
 def new_filter(G, model, cap, smax=0, batch=1, precision="fp32"):
+    """precision: ttgbf_opts.precision, optionally "/" and the contraction."""
+    prec, _, contraction = precision.partition("/")
     return G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=batch,
-                      rank_cap=cap, eps=model.eps, max_shift_span=smax, precision=precision)
+                      rank_cap=cap, eps=model.eps, max_shift_span=smax, precision=prec,
+                      contraction=contraction or "fp32")
 
 
-PRECISIONS = ["fp32", "fp64"]  # ttgbf_opts.precision: R factors / SVDs of the truncating stages
+# ttgbf_opts.precision (R factors / SVDs of the truncating stages), and float32
+# R / SVD with the core contractions on the tensor cores in split TF32
+PRECISIONS = ["fp32", "fp64", "fp32/tf32x3"]
 
 
 def gpu_cores(f, b=0):
@@ -241,7 +246,7 @@ def test_one_step_matches_oracle_tt_step(G, n, cap, mc, k, precision):
 
 
 @pytest.mark.parametrize("n,cap,smax,precision", [(32, 53, 3, "fp32"), (64, 53, 3, "fp32"),
-                                                   (32, 53, 3, "fp64")])
+                                                   (32, 53, 3, "fp64"), (32, 53, 3, "fp32/tf32x3")])
 def test_flat_bounds_where_the_cap_does_not_bind(G, n, cap, smax, precision):
     model = synth.config2(n=n)
     g = oracle_grid(model)
