@@ -42,7 +42,10 @@ UNIT = "filter-steps/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 126 MiB L2 of GB300
 # TT configurations of the accuracy sweep: (rank cap, max shift span, rounding
 # precision); rank cap x span <= 160 (wider shears run in pieces)
-SWEEP = [(16, 10, "fp32"), (32, 5, "fp32"), (48, 3, "fp32"), (16, 10, "fp64")]
+SWEEP = [(16, 10, "fp32", "fp32"), (32, 5, "fp32", "fp32"), (48, 3, "fp32", "fp32"),
+         (16, 10, "fp64", "fp32"), (16, 10, "fp32", "tf32x3"), (16, 10, "fp32", "tf32")]
+# nominal dense TF32 : BF16 tensor rate of the GPU (1.1 : 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def shard_mc_ids(rank: int, world: int, batch: int) -> list[int]:
@@ -604,7 +607,9 @@ def run_config3(args, dev):
     rank cap 32, eps 1e-5, one-mode measurements x_{2i}^2 / 20) with both
     transitions: the re-gridded one (ttgbf_predict: hat shears in pieces,
     Gaussian kernel) and the textbook one (ttgbf_predict_exact: each pair's
-    coupled factor on its 2-site block by the cross, rank 40).  Throughput of
+    coupled factor on its 2-site block by the cross, rank 40), each with the
+    core contractions on the CUDA cores (float32) and on the tensor cores
+    (TF32; split TF32 for the re-gridded one).  Throughput of
     predict + update + estimate for a batch (L2 flushed before each timed
     step, CUDA events).  Accuracy at N = 128 (the full-grid filter's largest
     axis), Monte Carlo run 0: the TT density against the tensor product of
@@ -622,10 +627,10 @@ def run_config3(args, dev):
     zs = measurement_batches(model, list(range(B)), W + K)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    for name, exact in (("regridded", False), ("textbook", True)):
+    for name, exact, con in C3_VARIANTS:
         f = G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=B,
                        rank_cap=model.rank_cap, eps=model.eps, max_shift_span=5, device=dev,
-                       cross_rank=model.rank_cap + 8 if exact else 0)
+                       cross_rank=model.rank_cap + 8 if exact else 0, contraction=con)
         comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
                  for m, t, *_ in model.tables(f.grid_axes())]
         z_dev = torch.tensor(zs, dtype=torch.float32, device=dev)
@@ -651,7 +656,7 @@ def run_config3(args, dev):
             torch.cuda.synchronize(dev)
             ms += a.elapsed_time(b)
         out[name] = {"value": B * K / (ms * 1e-3), "unit": "filter-steps/s", "ms_per_step": ms / K,
-                     "max_rank": int(f.ranks().max())}
+                     "max_rank": int(f.ranks().max()), "contraction": con}
         f.free()
         del f
         torch.cuda.empty_cache()
@@ -679,9 +684,10 @@ def run_config3(args, dev):
                 dens[k][i] = fg.density()
             fg.free()
         refs[ref_name] = dens
-    for name, exact in (("regridded", False), ("textbook", True)):
+    for name, exact, con in C3_VARIANTS:
         f = G.TTFilter(m128.lo, m128.hi, m128.n, m128.m0, np.diag(m128.P0), batch=1, rank_cap=m128.rank_cap,
-                       eps=m128.eps, max_shift_span=5, device=dev, cross_rank=m128.rank_cap + 8 if exact else 0)
+                       eps=m128.eps, max_shift_span=5, device=dev, cross_rank=m128.rank_cap + 8 if exact else 0,
+                       contraction=con)
         comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
                  for m, t, *_ in m128.tables(f.grid_axes())]
         e_text, e_rg = [], []
@@ -702,6 +708,11 @@ def run_config3(args, dev):
                                  "or the re-gridded transition (ttgbf_fg_predict); relative Frobenius error per "
                                  "step")
     return out
+
+
+# config-3 variants: (name, textbook transition, contraction arithmetic)
+C3_VARIANTS = [("regridded", False, "fp32"), ("regridded_tf32x3", False, "tf32x3"),
+               ("regridded_tf32", False, "tf32"), ("textbook", True, "fp32"), ("textbook_tf32", True, "tf32")]
 
 
 def fg_axes(lo, hi, n):
@@ -745,7 +756,7 @@ def tuned_config(G, model, batch, rank_cap, smax, precision):
         return {}
 
 
-def make_tt(G, model, dev, batch, rank_cap, smax, precision, parts=None):
+def make_tt(G, model, dev, batch, rank_cap, smax, precision, parts=None, contraction="fp32"):
     """A TT filter context with the autotuned launch configuration of its shape;
     parts overrides the batch split for this context only."""
     kw = tuned_config(G, model, batch, rank_cap, smax, precision)
@@ -753,7 +764,7 @@ def make_tt(G, model, dev, batch, rank_cap, smax, precision, parts=None):
         kw["parts"] = parts
     return G.TTFilter(model.lo, model.hi, model.n, model.m0, np.diag(model.P0), batch=batch,
                       rank_cap=rank_cap, eps=model.eps, max_shift_span=smax, device=dev,
-                      precision=precision, **kw)
+                      precision=precision, contraction=contraction, **kw)
 
 
 def run_ours(args, rank: int, world: int, local_rank: int, dist):
@@ -764,10 +775,10 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     model = synth.config2()
     B = args.batch
     W, K = args.warmup, args.steps
-    cap, smax, prec = args.rank_cap, args.max_shift_span, args.precision
+    cap, smax, prec, con = args.rank_cap, args.max_shift_span, args.precision, args.contraction
     mc_ids = shard_mc_ids(rank, world, B)
     zs = measurement_batches(model, mc_ids, W + 3 * K)
-    f = make_tt(G, model, dev, B, cap, smax, prec)
+    f = make_tt(G, model, dev, B, cap, smax, prec, contraction=con)
     axes = f.grid_axes()
     comps = [(m, torch.tensor(np.asarray(t), dtype=torch.float32, device=dev))
              for m, t in model.tables(axes)]
@@ -859,7 +870,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA lanes at max clock
-    f1 = make_tt(G, model, dev, B, cap, smax, prec, parts=1)
+    f1 = make_tt(G, model, dev, B, cap, smax, prec, parts=1, contraction=con)
     for k in range(W):
         step(f1, k)
     torch.cuda.synchronize(dev)
@@ -884,6 +895,34 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                f"(clock from {pk_src} peaks); of derived peak"}
 
+    # the core contractions on the tensor cores (tcgen05 kind::tf32, split
+    # TF32): the same single-part profile, the grouped GEMM's flops (2 m n k
+    # per tile, each of the three split products counted once: the
+    # algorithmic product) over its event time, against the TF32 peak
+    log("tensor-core contraction profile")
+    ftc = make_tt(G, model, dev, B, cap, smax, prec, parts=1, contraction="tf32x3")
+    for k in range(W):
+        step(ftc, k)
+    torch.cuda.synchronize(dev)
+    ftc.profile(True)
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        step(ftc, W + i)
+    torch.cuda.synchronize(dev)
+    gtc = ftc.profile_read()["gemm"]
+    ftc.free()
+    del ftc
+    torch.cuda.empty_cache()
+    tf32_peak = float(pk.get("bf16_tflops", 1900.0)) * TF32_PER_BF16
+    ach_tc = gtc["flops"] / (gtc["ms"] * 1e-3) / 1e12 if gtc["ms"] > 0 else 0.0
+    gemm_tc = {"bound": "tensor", "kernel": "k_gemm_tc (tf32x3)", "achieved": ach_tc, "peak": tf32_peak,
+               "unit": "TFLOP/s", "frac": ach_tc / tf32_peak, "tensor_flops_per_flop": 3,
+               "launches": gtc["launches"], "ms_per_launch": gtc["ms"] / max(gtc["launches"], 1),
+               "measured": f"{B} filters as one part on one stream, CUDA events around every grouped "
+                           "GEMM launch, K steps",
+               "peak_source": f"{pk_src} bf16 burst x {TF32_PER_BF16:.3f} (nominal TF32 : BF16); of "
+                              f"{pk_src} (scaled)"}
+
     # the full-grid filter on the same workload (the metric's comparison)
     log("full-grid leg")
     fullgrid = None if args.no_fullgrid else run_fullgrid(args, model, zs, W, K, dev, axes)
@@ -897,11 +936,11 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         log("accuracy leg and rank-cap sweep")
         S = W + K
         bound = 10.0 * model.eps + 1e-5
-        configs = [(cap, smax, prec)] + [c for c in SWEEP if c != (cap, smax, prec)]
+        configs = [(cap, smax, prec, con)] + [c for c in SWEEP if c != (cap, smax, prec, con)]
         runs = []
-        for (rc, sp, pr) in configs:
-            g = make_tt(G, model, dev, B, rc, sp, pr)
-            runs.append({"cfg": (rc, sp, pr), "f": g, "ms": 0.0, "err": []})
+        for (rc, sp, pr, cn) in configs:
+            g = make_tt(G, model, dev, B, rc, sp, pr, contraction=cn)
+            runs.append({"cfg": (rc, sp, pr, cn), "f": g, "ms": 0.0, "err": []})
         for k, P in enumerate(fp64_reference_densities(model, zs, S, dev, axes)):
             for r in runs:
                 g = r["f"]
@@ -914,9 +953,9 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
                     r["err"].append(tt_dense_rel_err(g.export_cores(0), P))
         main_errs = list(runs[0]["err"])
         for r in runs:
-            rc, sp, pr = r["cfg"]
+            rc, sp, pr, cn = r["cfg"]
             r["f"].free()
-            ent = {"rank_cap": rc, "max_shift_span": sp, "precision": pr,
+            ent = {"rank_cap": rc, "max_shift_span": sp, "precision": pr, "contraction": cn,
                    "value": B * K / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / K,
                    "tt_density_rel_fro_err": r["err"][-1], "bound": bound,
                    "matched": r["err"][-1] <= bound}
@@ -938,11 +977,12 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("rank cap 16", f"rank cap {cap}"),
-                   "rounding_precision": prec, "max_shift_span": smax,
+                   "rounding_precision": prec, "contraction": con, "max_shift_span": smax,
                    "launch_config": tuned_config(G, model, B, cap, smax, prec) or "library defaults",
                    "filters_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (independent filters, no collective)"},
         "roofline": roofline,
+        "gemm_tc": gemm_tc,
         "e2e": {"value": B * world * K / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": B * b * 4, "d2h_bytes_per_step": B * (d + d * d + 2) * 8},
         "gpu_launches": launches,
@@ -963,7 +1003,8 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         best = min(ok, key=lambda e: e["ms_per_step"]) if ok else min(
             sweep, key=lambda e: e["tt_density_rel_fro_err"])
         line["matched_error"] = {
-            "met": bool(ok), "config": {k: best[k] for k in ("rank_cap", "max_shift_span", "precision")},
+            "met": bool(ok),
+            "config": {k: best[k] for k in ("rank_cap", "max_shift_span", "precision", "contraction")},
             "value": best["value"], "tt_density_rel_fro_err": best["tt_density_rel_fro_err"],
             "bound": best["bound"], "vs_fullgrid": best.get("vs_fullgrid")}
     if world == 1 and not args.no_cpu_baseline:
@@ -983,6 +1024,8 @@ def main():
     ap.add_argument("--batch", type=int, default=100)
     ap.add_argument("--rank-cap", type=int, default=16)
     ap.add_argument("--max-shift-span", type=int, default=10)
+    ap.add_argument("--contraction", choices=["fp32", "tf32", "tf32x3"], default="fp32",
+                    help="arithmetic of the core contractions (CUDA cores or tcgen05 tensor cores)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="arithmetic of the truncating R factors and SVDs (ttgbf_opts.precision)")
     ap.add_argument("--no-config4", action="store_true", help="skip the uneven-batch leg")
