@@ -116,15 +116,13 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
                : "memory");
 }
 
-// 32 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 16 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -136,32 +134,44 @@ struct TcSrc {
   int ilim;
 };
 
-// Stage k in [k0, k0 + 16) of an operand with R rows into hi (and lo).
-template <int R, bool kSplit>
-__device__ __forceinline__ void tc_stage(const TcSrc& s, int k0, int K, uint8_t* hi, uint8_t* lo) {
-  constexpr int kPer = R * kTcKC / kTcThreads;
+// Element q of this thread's share of an operand chunk with R rows (R a
+// multiple or a divisor of the 128 threads): (i, k) = (i0 + q di, k0 + q dk),
+// consecutive threads along whichever index is contiguous in memory.
+struct TcMap {
+  int i0, k0, di, dk;
+};
+template <int R>
+__device__ __forceinline__ TcMap tc_map(bool kcontig) {
   const int tid = threadIdx.x;
-  float v[kPer];
-  int ii[kPer], kk[kPer];
+  if (kcontig) return TcMap{tid / kTcKC, tid % kTcKC, kTcThreads / kTcKC, 0};
+  if (R >= kTcThreads) return TcMap{tid, 0, 0, 1};  // R == 128: one k per element
+  return TcMap{tid % R, tid / R, 0, kTcThreads / R};
+}
+
+// Global loads of k in [k0, k0 + 16) of an operand with R rows (zero past
+// the operand's edges).
+template <int R>
+__device__ __forceinline__ void tc_load(const TcSrc& s, int k0, int K, float (&v)[R * kTcKC / kTcThreads]) {
+  static_assert(R == kTcThreads || kTcThreads % R == 0, "operand rows");
+  const TcMap m = tc_map<R>(s.sk == 1);
+  const float* p = s.p + (long long)m.i0 * s.si + (long long)(k0 + m.k0) * s.sk;
+  const long long step = (long long)m.di * s.si + (long long)m.dk * s.sk;
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int e = tid + kTcThreads * q;
-    int i, k;
-    if (s.sk == 1) {  // k contiguous in memory: consecutive threads along k
-      i = e / kTcKC;
-      k = e % kTcKC;
-    } else {          // rows contiguous: consecutive threads along the rows
-      k = e / R;
-      i = e % R;
-    }
-    ii[q] = i;
-    kk[q] = k;
-    const int gk = k0 + k;
-    v[q] = (i < s.ilim && gk < K) ? __ldg(s.p + (long long)i * s.si + (long long)gk * s.sk) : 0.f;
+  for (int q = 0; q < R * kTcKC / kTcThreads; ++q) {
+    const bool in = m.i0 + q * m.di < s.ilim && k0 + m.k0 + q * m.dk < K;
+    v[q] = in ? __ldg(p + q * step) : 0.f;
   }
+}
+
+// The loaded values, rounded to TF32, into the staging layout (and their
+// rounded remainders into lo).
+template <int R, bool kSplit>
+__device__ __forceinline__ void tc_store(const TcSrc& s, const float (&v)[R * kTcKC / kTcThreads], uint8_t* hi,
+                                         uint8_t* lo) {
+  const TcMap m = tc_map<R>(s.sk == 1);
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int off = tc_off(ii[q], kk[q]);
+  for (int q = 0; q < R * kTcKC / kTcThreads; ++q) {
+    const int off = tc_off(m.i0 + q * m.di, m.k0 + q * m.dk);
     const uint32_t h = to_tf32(v[q]);
     *reinterpret_cast<uint32_t*>(hi + off) = h;
     if (kSplit) *reinterpret_cast<uint32_t*>(lo + off) = to_tf32(v[q] - __uint_as_float(h));
@@ -169,7 +179,7 @@ __device__ __forceinline__ void tc_stage(const TcSrc& s, int k0, int K, uint8_t*
 }
 
 template <bool kSplit>
-__global__ void __launch_bounds__(kTcThreads) k_gemm_tc(GemmWork w, double* flops) {
+__global__ void __launch_bounds__(kTcThreads, 4) k_gemm_tc(GemmWork w, double* flops) {
   __shared__ __align__(1024) uint8_t s_buf[2][kTcBufBytes];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
@@ -215,6 +225,13 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(GemmWork w, double* flop
       sb = TcSrc{g.A + (long long)s0 * g.lda, g.lda, 1, sht - s0};
     }
     const int nch = (g.k + kTcKC - 1) / kTcKC;
+    // chunk c + 1's global loads are issued before chunk c's MMAs, so their
+    // latency overlaps the tensor core's work and the next buffer wait
+    float va[kTcTileM * kTcKC / kTcThreads], vb[kTcTileN * kTcKC / kTcThreads];
+    if (nch > 0) {
+      tc_load<kTcTileM>(sa, 0, g.k, va);
+      tc_load<kTcTileN>(sb, 0, g.k, vb);
+    }
     for (int c = 0; c < nch; ++c) {
       const int b = c & 1;
       if (c >= 2) {  // the MMAs of chunk c - 2 have read this buffer
@@ -226,11 +243,15 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(GemmWork w, double* flop
         }
       }
       uint8_t* base = s_buf[b];
-      tc_stage<kTcTileM, kSplit>(sa, c * kTcKC, g.k, base, base + kTcABytes + kTcBBytes);
-      tc_stage<kTcTileN, kSplit>(sb, c * kTcKC, g.k, base + kTcABytes, base + 2 * kTcABytes + kTcBBytes);
+      tc_store<kTcTileM, kSplit>(sa, va, base, base + kTcABytes + kTcBBytes);
+      tc_store<kTcTileN, kSplit>(sb, vb, base + kTcABytes, base + 2 * kTcABytes + kTcBBytes);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
       __syncthreads();
+      if (c + 1 < nch) {
+        tc_load<kTcTileM>(sa, (c + 1) * kTcKC, g.k, va);
+        tc_load<kTcTileN>(sb, (c + 1) * kTcKC, g.k, vb);
+      }
       if (tid == 0) {
         tc_fence_after();
         const uint32_t ah = smem_u32(base), bh = ah + kTcABytes;
@@ -265,22 +286,27 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(GemmWork w, double* flop
       if (__syncthreads_or(!ok)) failed = true;
     }
     tc_fence_after();
-    // epilogue: thread (warp, lane) holds tile row 32 warp + lane, 32 columns
+    // epilogue: thread (warp, lane) holds tile row 32 warp + lane; its 32
+    // columns are read in two halves of 16
     const int i = warp * 32 + lane;
-    uint32_t v[32];
-    if (nch > 0 && !failed) {
-      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-    } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = failed ? 0x7fc00000u : 0u;  // NaN marks a tile given up
-    }
-    if (l0 + i < lng) {
+    for (int h = 0; h < kTcTileN / 16; ++h) {
+      uint32_t v[16];
+      if (nch > 0 && !failed) {
+        tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * h, v);
+      } else {
 #pragma unroll
-      for (int j = 0; j < kTcTileN; ++j) {
-        if (s0 + j >= sht) break;
-        const float x = __uint_as_float(v[j]);
-        if (!tr) g.C[(long long)(l0 + i) * g.ldc + s0 + j] = x;
-        else g.C[(long long)(s0 + j) * g.ldc + l0 + i] = x;
+        for (int j = 0; j < 16; ++j) v[j] = failed ? 0x7fc00000u : 0u;  // NaN marks a tile given up
+      }
+      if (l0 + i < lng) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int cj = s0 + 16 * h + j;
+          if (cj >= sht) break;
+          const float x = __uint_as_float(v[j]);
+          if (!tr) g.C[(long long)(l0 + i) * g.ldc + cj] = x;
+          else g.C[(long long)cj * g.ldc + l0 + i] = x;
+        }
       }
     }
     if (tid == 0 && flops != nullptr && !failed) {
