@@ -2802,15 +2802,14 @@ namespace {
 
 // Cache key of a batch shape: grid, batch, rank cap, span, precision, conv,
 // the span of every elementary shear of F on this grid (which sets the rank
-// expansions), and the GPU's name.
+// expansions), the GPU's name, and a contraction mode other than float32.
 std::string tune_key(const ttgbf_grid* g, const ttgbf_opts* o, const double* F) {
   const int d = g->d;
   std::string k = "d=" + std::to_string(d) + ";n=";
   for (int m = 0; m < d; ++m) k += std::to_string(g->n[m]) + (m + 1 < d ? "," : "");
   k += ";batch=" + std::to_string(o->batch) + ";cap=" + std::to_string(o->rank_cap) +
        ";span=" + std::to_string(o->max_shift_span > 0 ? o->max_shift_span : 10) +
-       ";prec=" + std::to_string(o->precision) + ";contract=" + std::to_string(o->contraction) +
-       ";conv=" + std::to_string(o->conv) + ";shears=";
+       ";prec=" + std::to_string(o->precision) + ";conv=" + std::to_string(o->conv) + ";shears=";
   std::vector<double> Lm, D, U;
   if (ldu(F, d, &Lm, &D, &U) == TTGBF_OK) {
     for (int m = 0; m < d; ++m)
@@ -2836,6 +2835,9 @@ std::string tune_key(const ttgbf_grid* g, const ttgbf_opts* o, const double* F) 
     k += ";gpu=" + name;
   }
   cudaGetLastError();
+  // the tensor-core contraction modes key their own entries (float32
+  // contractions keep the key they always had)
+  if (o->contraction != TTGBF_CONTRACT_FP32) k += ";contract=" + std::to_string(o->contraction);
   return k;
 }
 
