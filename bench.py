@@ -44,6 +44,11 @@ L2_FLUSH_BYTES = 256 << 20  # larger than the 126 MiB L2 of GB300
 # precision); rank cap x span <= 160 (wider shears run in pieces)
 SWEEP = [(16, 10, "fp32", "fp32"), (32, 5, "fp32", "fp32"), (48, 3, "fp32", "fp32"),
          (16, 10, "fp64", "fp32"), (16, 10, "fp32", "tf32x3"), (16, 10, "fp32", "tf32")]
+# DRAM bytes read + written by the k_tsqr launches of one config-2 filter step
+# (rank cap 16): one ncu capture of every launch of a 12-filter step
+# (profiles/k_tsqr_traffic_config2_part12.md: 226.7 MB over 12 filters),
+# scaled by the filters a launch processes
+TSQR_DRAM_BYTES_PER_FILTER_STEP = 226.64e6 / 12
 # nominal dense TF32 : BF16 tensor rate of the GPU (1.1 : 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -188,6 +193,21 @@ def fullgrid_bytes_per_step(model) -> int:
     n_scale = sum(1 for op in ops if op[0] == "scale")
     passes_rw = n_shear + n_scale + model.d + 1 + 1
     return cells * 4 * (2 * passes_rw + 1)
+
+
+def tsqr_algorithmic_bytes(model, rank_cap) -> float:
+    """Algorithmic bytes of the same R factors: every rank-expanded (r N) x
+    (r S) unfolding read once in float32."""
+    r = rank_cap
+    tot = 0.0
+    for op in ldu_ops(model.F):
+        if op[0] != "shear":
+            continue
+        _, m, n, a = op
+        S = shear_span(model, m, n, a)
+        N = int(model.n[min(m, n)])
+        tot += abs(m - n) * 4.0 * (r * N) * (r * S)
+    return tot
 
 
 def tsqr_algorithmic_flops(model, rank_cap) -> float:
@@ -886,8 +906,16 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     tsqr = prof1["tsqr"]
     alg = tsqr_algorithmic_flops(model, cap) * B * K  # over the K profiled steps
     achieved = alg / (tsqr["ms"] * 1e-3) / 1e12 if tsqr["ms"] > 0 else 0.0
+    per_step = tsqr["launches"] / K  # k_tsqr launches per step of the one-part context
+    # the captured traffic applies to the workload it was taken on: config 2 at rank cap 16
+    traffic = (TSQR_DRAM_BYTES_PER_FILTER_STEP * B / per_step
+               if cap == 16 and con == "fp32" and prec == "fp32" and per_step > 0 else None)
     roofline = {"bound": "alu", "kernel": "k_tsqr", "achieved": achieved, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                "traffic_note": "bytes per launch: one ncu capture of a 12-filter step's k_tsqr launches "
+                                "(dram__bytes_read.sum + dram__bytes_write.sum) scaled by the filters per "
+                                "launch; a lower bound (L2 holds more of a 12-filter part)",
+                "algorithmic_bytes_per_launch": tsqr_algorithmic_bytes(model, cap) * B / max(per_step, 1),
                 "algorithmic_flops_per_filter_step": tsqr_algorithmic_flops(model, cap),
                 "launches": tsqr["launches"], "ms_per_launch": tsqr["ms"] / max(tsqr["launches"], 1),
                 "measured": f"{B} filters as one part on one stream, CUDA events around every "

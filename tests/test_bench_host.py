@@ -30,6 +30,8 @@ def test_shear_spans_and_algorithmic_flops_of_the_bench_workload():
     expect = 2 * 2048 * 256 * (49 * 1 + 25 * 2 + 49 * 3 + 81 * 1 + 25 * 2 + 25 * 1)
     assert bench.tsqr_algorithmic_flops(model, 16) == expect
     assert abs(expect - 0.4215e9) < 1e6
+    # and their bytes: every (16 * 128) x (16 S) unfolding read once in float32
+    assert bench.tsqr_algorithmic_bytes(model, 16) == 4 * 2048 * 16 * (7 + 5 * 2 + 7 * 3 + 9 + 5 * 2 + 5)
 
 
 def test_tt_dense_rel_err_matches_densified():
