@@ -102,6 +102,7 @@ def test_null_context_calls(lib):
     assert lib.ttgbf_round(None) == -1
     assert lib.ttgbf_normalise(None) == -1
     assert lib.ttgbf_grid_axes(None, None) == -1
+    assert lib.ttgbf_densify(None, 0, None, 0) == -1
 
 
 def test_filter_reports_capacity_before_device(lib):
